@@ -1,0 +1,180 @@
+/*
+ * vga.h -- C ABI of the GB300 (sm_103a) implementation of the voxel-graph diffusion-transformation
+ * method of arXiv 2406.04177 ("A Voxel-based Approach for Simulating Microbial Decomposition in
+ * Soil").
+ *
+ * The calls follow the paper's problem statement: build the graph of pore voxels from a binary
+ * image (Sec. II.A), set the parameters and initial masses (Sec. II.A, Sec. IV.C), advance N time
+ * steps of transformation followed by diffusion (Sec. III), read the masses and their totals.
+ *
+ * Conventions common to every call
+ *  - Every call returns a vga_status: VGA_OK (0) or a negative error code.  vga_strerror() names
+ *    the code; vga_last_error() returns a human-readable detail string for the last failing call
+ *    made by the calling thread.
+ *  - Handles (vga_graph, vga_sim, vga_batch) are owned by the library and released by the matching
+ *    *_free call.  Input arrays are owned by the caller and copied (or read) before the call
+ *    returns unless stated otherwise; output arrays are allocated by the caller.
+ *  - `stream` arguments are cudaStream_t values passed as void*; NULL means the legacy default
+ *    stream.  Work is ordered on that stream.  Calls that hand data back to host memory
+ *    synchronise the stream before returning.  vga_sim_step returns as soon as its work is
+ *    enqueued; errors raised by that work are reported by the next synchronising call.
+ *  - Node order: node i is the i-th kept pore voxel in raster order (x fastest, then y, then z).
+ *    State arrays are structure-of-arrays with 5 rows, row c holding compartment c for all nodes:
+ *    element (c, i) at offset c*n + i.  Compartments: 0 MB, 1 DOM, 2 SOM, 3 FOM, 4 CO2
+ *    (x^1 .. x^5 of Sec. II.A).
+ *  - Neighbour slots, always in this order: -x, +x, -y, +y, -z, +z.
+ *  - Limits: 1 <= nx, ny, nz <= 32768 and nx*ny*nz < 2^31.
+ */
+#ifndef VGA_H
+#define VGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vga_status {
+    VGA_OK = 0,
+    VGA_ERR_INVALID_ARG = -1,   /* bad size, NULL pointer, non-finite or out-of-range parameter */
+    VGA_ERR_OOM = -2,           /* device or host allocation failed */
+    VGA_ERR_CUDA = -3,          /* a CUDA runtime call failed (detail in vga_last_error) */
+    VGA_ERR_UNSTABLE_DT = -4,   /* explicit step beyond the positivity limit D dt max_i sum_j g_ij <= 1 */
+    VGA_ERR_NOT_CONVERGED = -5, /* the implicit solve reached cg_maxit before cg_rtol */
+    VGA_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up (persistent batched kernel) */
+    VGA_ERR_NONFINITE = -7,     /* non-finite value found in a state array */
+    VGA_ERR_UNSUPPORTED = -8    /* combination of options not implemented */
+} vga_status;
+
+/* Name of a status code (static string, never NULL). */
+const char *vga_strerror(int status);
+/* Detail of the last failing call on this thread (static per-thread buffer, never NULL). */
+const char *vga_last_error(void);
+/* Library version as 10000*major + 100*minor + patch. */
+int32_t vga_version(void);
+
+/* ============================================================================================
+ * Graph of pore voxels (Sec. II.A; Sec. III first paragraph; Fig. 2).
+ * V = voxels with I(i,j,k) == 0 (any nonzero value is solid); E = pairs of face-adjacent voxels of
+ * V (6-connectivity).  Connected components are numbered in raster order of their first voxel.
+ * With VGA_KEEP_LARGEST_COMPONENT only the largest component (ties: the lowest number) becomes the
+ * node set; otherwise every pore voxel is a node.  The image border carries no flux.
+ * Integer-only and bit-exact: the result never depends on scheduling.
+ * ============================================================================================ */
+#define VGA_KEEP_LARGEST_COMPONENT 1u
+#define VGA_IMAGE_ON_DEVICE 2u /* `img` is a device pointer instead of a host pointer */
+
+typedef struct vga_graph vga_graph;
+
+/* img: nx*ny*nz bytes in C order [z][y][x], host memory (or device memory with
+ * VGA_IMAGE_ON_DEVICE).  On success *out receives a new graph.  Errors: VGA_ERR_INVALID_ARG
+ * (sizes outside the limits, NULL pointers, unknown flags), VGA_ERR_OOM, VGA_ERR_CUDA. */
+vga_status vga_graph_build(const uint8_t *img, int32_t nx, int32_t ny, int32_t nz, uint32_t flags,
+                           void *stream, vga_graph **out);
+
+/* Node count n, number of pore components, and the id of the largest component (-1 if none).
+ * Any output pointer may be NULL. */
+vga_status vga_graph_info(const vga_graph *g, int64_t *n_nodes, int32_t *n_components,
+                          int32_t *largest_component);
+
+/* Copies the graph to caller-allocated host arrays; each may be NULL to skip it.
+ *   labels[nx*ny*nz]   component id of every pore voxel, -1 for solid voxels
+ *   voxel_of_node[n]   raster index (x + nx*(y + ny*z)) of node i
+ *   nbr[6*n]           node index of the face neighbour of node i in slot d at nbr[6*i + d], or -1
+ *                      when that voxel is solid, outside the image, or not in the node set. */
+vga_status vga_graph_export(const vga_graph *g, int32_t *labels, int64_t *voxel_of_node,
+                            int32_t *nbr);
+
+vga_status vga_graph_free(vga_graph *g);
+
+/* ============================================================================================
+ * Parameters (Sec. II.B, II.C; values of Sec. IV.C).  Units are the caller's, consistently: the
+ * reference workloads use masses in ug C, time in days and lengths in voxels.
+ * ============================================================================================ */
+#define VGA_SCHEME_EXPLICIT 0      /* Scheme 1: m <- (I - D dt L_g) m */
+#define VGA_SCHEME_IMPLICIT_PCG 1  /* Scheme 2: (I + D dt L_g) m_new = m, Jacobi-PCG (Sec. III) */
+#define VGA_TRANSFORM_SYNC 0       /* every flux from the old state, then update (eq. 3 + clamps) */
+#define VGA_TRANSFORM_ASYNC 1      /* sequential growth, mortality, respiration, SOM, FOM */
+
+typedef struct vga_params {
+    double D;       /* DOM diffusion coefficient D_DOM */
+    double dt;      /* time step, shared by transformation and diffusion */
+    double rho;     /* respiration rate */
+    double mu;      /* mortality rate */
+    double beta;    /* fraction of dead biomass returned to DOM, in [0, 1] */
+    double v_som;   /* SOM hydrolysis rate */
+    double v_fom;   /* FOM hydrolysis rate */
+    double v_dom;   /* maximum growth rate (Monod) */
+    double K_dom;   /* half-saturation constant of DOM, > 0, same unit as the masses */
+    int32_t scheme;    /* VGA_SCHEME_* */
+    int32_t transform; /* VGA_TRANSFORM_* */
+    double cg_rtol;    /* implicit only: stop when ||r||_2 <= cg_rtol ||b||_2 */
+    int32_t cg_maxit;  /* implicit only: iteration cap per step */
+    int32_t reserved;  /* set to 0 */
+} vga_params;
+
+/* ============================================================================================
+ * Simulation on one graph (Sec. III).  One time step applies the transformation to every node,
+ * then diffuses the transformed DOM with Scheme 1 or Scheme 2.  State and fluxes are FP32 on the
+ * device; totals are reduced in FP64; the implicit solve iterates in FP64.
+ * ============================================================================================ */
+typedef struct vga_sim vga_sim;
+
+/* Creates a simulation on graph g (which must outlive it) with all masses zero.  Errors:
+ * VGA_ERR_INVALID_ARG (non-finite or negative parameter, beta outside [0,1], K_dom <= 0, dt <= 0,
+ * unknown scheme/transform), VGA_ERR_UNSTABLE_DT (explicit scheme with 6 D dt > 1 under unit
+ * conductances), VGA_ERR_OOM, VGA_ERR_CUDA. */
+vga_status vga_sim_create(const vga_graph *g, const vga_params *p, void *stream, vga_sim **out);
+
+/* Replaces the parameters (same validation as vga_sim_create). */
+vga_status vga_sim_set_params(vga_sim *s, const vga_params *p);
+
+/* Edge conductances g_ij (the voxel form, v_i = v_j = 1, of the Sec. V.A flux with alpha_ij).
+ * Block form: the image is cut into cubes of `block_side` voxels; an edge that crosses the face
+ * between two face-adjacent blocks gets that face's theta, edges inside a block keep 1.
+ * theta (host, FP32) lists the faces normal to x ((nbz, nby, nbx-1) in C order), then normal to
+ * y ((nbz, nby-1, nbx)), then normal to z ((nbz-1, nby, nbx)), with nb* = ceil(n* / block_side);
+ * n_theta must equal that count.  Values must be finite and >= 0.  With the explicit scheme the
+ * call fails with VGA_ERR_UNSTABLE_DT when 6 D dt max(1, max theta) > 1. */
+vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const float *theta,
+                                          int64_t n_theta);
+/* Returns to unit conductances (g_ij = 1, Sec. II.B). */
+vga_status vga_sim_clear_conductances(vga_sim *s);
+
+/* Initial or replacement state X (5 x n, FP64, SoA).  Values are rounded to FP32.  on_device != 0
+ * means x is a device pointer.  Errors: VGA_ERR_NONFINITE if a value is not finite (host input
+ * only; device input is converted unchecked). */
+vga_status vga_sim_set_masses(vga_sim *s, const double *x, int32_t on_device);
+/* Current state X (5 x n, FP64) into caller memory (host, or device if on_device != 0). */
+vga_status vga_sim_get_masses(vga_sim *s, double *x, int32_t on_device);
+/* FP32 variants of the two calls above (same layout, no conversion). */
+vga_status vga_sim_set_state_f32(vga_sim *s, const float *x, int32_t on_device);
+vga_status vga_sim_get_state_f32(vga_sim *s, float *x, int32_t on_device);
+
+/* Advances n_steps >= 0 time steps (Sec. III: transformation, then diffusion of DOM).
+ * Asynchronous on the simulation's stream.  Implicit scheme: synchronises to test convergence
+ * and returns VGA_ERR_NOT_CONVERGED if any solve hit cg_maxit (the state then holds the last
+ * iterate). */
+vga_status vga_sim_step(vga_sim *s, int64_t n_steps);
+
+/* FP64 totals of the 5 compartments over all nodes, into totals[5] (host).  Deterministic. */
+vga_status vga_sim_totals(vga_sim *s, double *totals);
+
+/* Waits for the simulation's stream; reports errors of previously enqueued work. */
+vga_status vga_sim_sync(vga_sim *s);
+
+typedef struct vga_sim_stats {
+    int64_t steps_done;       /* time steps since creation */
+    int64_t cg_iterations;    /* implicit scheme: PCG iterations since creation */
+    double cg_last_relres;    /* implicit scheme: final relative residual of the last solve */
+    int64_t kernel_launches;  /* kernels launched since creation */
+} vga_sim_stats;
+vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out);
+
+vga_status vga_sim_free(vga_sim *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VGA_H */

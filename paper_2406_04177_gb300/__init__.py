@@ -1,0 +1,364 @@
+"""Python binding of libvga, the sm_103a implementation of the voxel-graph diffusion-transformation
+method of arXiv 2406.04177.
+
+This module only marshals arguments: every function named `vga_*` calls the C entry point of the
+same name declared in include/vga.h, and every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: if libvga.so is missing or cannot be loaded the first call
+raises, on purpose.  Build it with `paper_2406_04177_gb300.build.build()` (or the repository's
+`__graft_entry__.build()`).
+
+Arrays: host data are numpy arrays; device data are torch CUDA tensors (their data_ptr() is passed
+with on_device = 1).  Streams are torch.cuda.Stream objects or raw cudaStream_t integers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvga.so")
+
+VGA_OK = 0
+STATUS_NAMES = {0: "VGA_OK", -1: "VGA_ERR_INVALID_ARG", -2: "VGA_ERR_OOM", -3: "VGA_ERR_CUDA",
+                -4: "VGA_ERR_UNSTABLE_DT", -5: "VGA_ERR_NOT_CONVERGED", -6: "VGA_ERR_TIMEOUT",
+                -7: "VGA_ERR_NONFINITE", -8: "VGA_ERR_UNSUPPORTED"}
+VGA_KEEP_LARGEST_COMPONENT = 1
+VGA_IMAGE_ON_DEVICE = 2
+VGA_SCHEME_EXPLICIT = 0
+VGA_SCHEME_IMPLICIT_PCG = 1
+VGA_TRANSFORM_SYNC = 0
+VGA_TRANSFORM_ASYNC = 1
+
+
+class VgaError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        self.name = STATUS_NAMES.get(status, "VGA_ERR_UNKNOWN")
+        super().__init__(f"{where}: {self.name}: {detail}")
+
+
+class vga_params(C.Structure):
+    _fields_ = [("D", C.c_double), ("dt", C.c_double), ("rho", C.c_double), ("mu", C.c_double),
+                ("beta", C.c_double), ("v_som", C.c_double), ("v_fom", C.c_double),
+                ("v_dom", C.c_double), ("K_dom", C.c_double), ("scheme", C.c_int32),
+                ("transform", C.c_int32), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class vga_sim_stats(C.Structure):
+    _fields_ = [("steps_done", C.c_int64), ("cg_iterations", C.c_int64),
+                ("cg_last_relres", C.c_double), ("kernel_launches", C.c_int64)]
+
+
+_P, _I32, _I64, _U32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+# name -> argtypes (every function returns int32 vga_status unless listed in _RESTYPES)
+_SIGNATURES = {
+    "vga_strerror": [C.c_int],
+    "vga_last_error": [],
+    "vga_version": [],
+    "vga_graph_build": [_P, _I32, _I32, _I32, _U32, _P, _P],
+    "vga_graph_info": [_P, _P, _P, _P],
+    "vga_graph_export": [_P, _P, _P, _P],
+    "vga_graph_free": [_P],
+    "vga_sim_create": [_P, _P, _P, _P],
+    "vga_sim_set_params": [_P, _P],
+    "vga_sim_set_block_conductances": [_P, _I32, _P, _I64],
+    "vga_sim_clear_conductances": [_P],
+    "vga_sim_set_masses": [_P, _P, _I32],
+    "vga_sim_get_masses": [_P, _P, _I32],
+    "vga_sim_set_state_f32": [_P, _P, _I32],
+    "vga_sim_get_state_f32": [_P, _P, _I32],
+    "vga_sim_step": [_P, _I64],
+    "vga_sim_totals": [_P, _P],
+    "vga_sim_sync": [_P],
+    "vga_sim_get_stats": [_P, _P],
+    "vga_sim_free": [_P],
+}
+_RESTYPES = {"vga_strerror": C.c_char_p, "vga_last_error": C.c_char_p, "vga_version": C.c_int32}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Loads libvga.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with paper_2406_04177_gb300.build.build() "
+                               "(nvcc for sm_103a); no CPU fallback exists")
+        lib = C.CDLL(p)
+        for name, args in _SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = _RESTYPES.get(name, C.c_int32)
+        _lib = lib
+        return lib
+
+
+def declared_symbols() -> list[str]:
+    return list(_SIGNATURES)
+
+
+def _check(status: int, where: str):
+    if status != VGA_OK:
+        detail = load_library().vga_last_error().decode(errors="replace")
+        raise VgaError(int(status), where, detail)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _host_ptr(a: np.ndarray, dtype, shape_n: int | None = None):
+    if not (isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous):
+        raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+    if shape_n is not None and a.size != shape_n:
+        raise ValueError(f"expected {shape_n} elements, got {a.size}")
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _dev_ptr(t, dtype_name: str, count: int | None = None) -> int:
+    import torch
+
+    want = {"float64": torch.float64, "float32": torch.float32, "uint8": torch.uint8}[dtype_name]
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want and t.is_contiguous()):
+        raise TypeError(f"expected a contiguous CUDA tensor of {want}")
+    if count is not None and t.numel() != count:
+        raise ValueError(f"expected {count} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+# ---- one Python function per C entry point (argument marshalling only) -------------------------
+def vga_strerror(status: int) -> str:
+    return load_library().vga_strerror(int(status)).decode()
+
+
+def vga_last_error() -> str:
+    return load_library().vga_last_error().decode(errors="replace")
+
+
+def vga_version() -> int:
+    return int(load_library().vga_version())
+
+
+def vga_graph_build(img, flags: int = VGA_KEEP_LARGEST_COMPONENT, stream=None) -> C.c_void_p:
+    """img: uint8 [nz, ny, nx] numpy array (host) or CUDA tensor (device); 0 = pore."""
+    lib = load_library()
+    nz, ny, nx = (int(s) for s in img.shape)
+    if isinstance(img, np.ndarray):
+        img = np.ascontiguousarray(img, dtype=np.uint8)  # kept alive until the call returns
+        ptr = _host_ptr(img, np.uint8)
+        flags &= ~VGA_IMAGE_ON_DEVICE
+    else:
+        ptr = _dev_ptr(img, "uint8")
+        flags |= VGA_IMAGE_ON_DEVICE
+    out = C.c_void_p()
+    _check(lib.vga_graph_build(ptr, nx, ny, nz, flags, _stream_ptr(stream), C.byref(out)), "vga_graph_build")
+    return out
+
+
+def vga_graph_info(g) -> tuple[int, int, int]:
+    n, nc, lg = C.c_int64(), C.c_int32(), C.c_int32()
+    _check(load_library().vga_graph_info(g, C.byref(n), C.byref(nc), C.byref(lg)), "vga_graph_info")
+    return n.value, nc.value, lg.value
+
+
+def vga_graph_export(g, labels=None, voxel_of_node=None, nbr=None):
+    lib = load_library()
+    _check(lib.vga_graph_export(g, None if labels is None else _host_ptr(labels, np.int32),
+                                None if voxel_of_node is None else _host_ptr(voxel_of_node, np.int64),
+                                None if nbr is None else _host_ptr(nbr, np.int32)), "vga_graph_export")
+
+
+def vga_graph_free(g):
+    _check(load_library().vga_graph_free(g), "vga_graph_free")
+
+
+def make_params(p: dict) -> vga_params:
+    return vga_params(D=p["D"], dt=p["dt"], rho=p["rho"], mu=p["mu"], beta=p["beta"], v_som=p["v_som"],
+                      v_fom=p["v_fom"], v_dom=p["v_dom"], K_dom=p["K_dom"], scheme=int(p.get("scheme", 0)),
+                      transform=int(p.get("transform", 0)), cg_rtol=float(p.get("cg_rtol", 1e-8)),
+                      cg_maxit=int(p.get("cg_maxit", 500)), reserved=0)
+
+
+def vga_sim_create(g, params: dict, stream=None) -> C.c_void_p:
+    out = C.c_void_p()
+    pp = make_params(params)
+    _check(load_library().vga_sim_create(g, C.byref(pp), _stream_ptr(stream), C.byref(out)), "vga_sim_create")
+    return out
+
+
+def vga_sim_set_params(s, params: dict):
+    pp = make_params(params)
+    _check(load_library().vga_sim_set_params(s, C.byref(pp)), "vga_sim_set_params")
+
+
+def vga_sim_set_block_conductances(s, block_side: int, theta: np.ndarray):
+    theta = np.ascontiguousarray(theta, dtype=np.float32)
+    _check(load_library().vga_sim_set_block_conductances(s, int(block_side), _host_ptr(theta, np.float32),
+                                                         theta.size), "vga_sim_set_block_conductances")
+
+
+def vga_sim_clear_conductances(s):
+    _check(load_library().vga_sim_clear_conductances(s), "vga_sim_clear_conductances")
+
+
+def vga_sim_set_masses(s, x, n: int):
+    if isinstance(x, np.ndarray):
+        _check(load_library().vga_sim_set_masses(s, _host_ptr(x, np.float64, 5 * n), 0), "vga_sim_set_masses")
+    else:
+        _check(load_library().vga_sim_set_masses(s, _dev_ptr(x, "float64", 5 * n), 1), "vga_sim_set_masses")
+
+
+def vga_sim_get_masses(s, out, n: int):
+    if isinstance(out, np.ndarray):
+        _check(load_library().vga_sim_get_masses(s, _host_ptr(out, np.float64, 5 * n), 0), "vga_sim_get_masses")
+    else:
+        _check(load_library().vga_sim_get_masses(s, _dev_ptr(out, "float64", 5 * n), 1), "vga_sim_get_masses")
+
+
+def vga_sim_set_state_f32(s, x, n: int):
+    if isinstance(x, np.ndarray):
+        _check(load_library().vga_sim_set_state_f32(s, _host_ptr(x, np.float32, 5 * n), 0), "vga_sim_set_state_f32")
+    else:
+        _check(load_library().vga_sim_set_state_f32(s, _dev_ptr(x, "float32", 5 * n), 1), "vga_sim_set_state_f32")
+
+
+def vga_sim_get_state_f32(s, out, n: int):
+    if isinstance(out, np.ndarray):
+        _check(load_library().vga_sim_get_state_f32(s, _host_ptr(out, np.float32, 5 * n), 0), "vga_sim_get_state_f32")
+    else:
+        _check(load_library().vga_sim_get_state_f32(s, _dev_ptr(out, "float32", 5 * n), 1), "vga_sim_get_state_f32")
+
+
+def vga_sim_step(s, n_steps: int):
+    _check(load_library().vga_sim_step(s, int(n_steps)), "vga_sim_step")
+
+
+def vga_sim_totals(s) -> np.ndarray:
+    out = np.zeros(5, dtype=np.float64)
+    _check(load_library().vga_sim_totals(s, out.ctypes.data_as(C.c_void_p)), "vga_sim_totals")
+    return out
+
+
+def vga_sim_sync(s):
+    _check(load_library().vga_sim_sync(s), "vga_sim_sync")
+
+
+def vga_sim_get_stats(s) -> dict:
+    st = vga_sim_stats()
+    _check(load_library().vga_sim_get_stats(s, C.byref(st)), "vga_sim_get_stats")
+    return {k: getattr(st, k) for k, _ in vga_sim_stats._fields_}
+
+
+def vga_sim_free(s):
+    _check(load_library().vga_sim_free(s), "vga_sim_free")
+
+
+# ---- handle classes (ownership only) ------------------------------------------------------------
+class Graph:
+    """Owns a vga_graph handle."""
+
+    def __init__(self, img, keep_largest: bool = True, stream=None):
+        self.shape = tuple(int(s) for s in img.shape)
+        self.handle = vga_graph_build(img, VGA_KEEP_LARGEST_COMPONENT if keep_largest else 0, stream)
+        self.n, self.n_components, self.largest = vga_graph_info(self.handle)
+
+    def export(self, labels: bool = True, voxel_of_node: bool = True, nbr: bool = True) -> dict:
+        nvox = int(np.prod(self.shape))
+        out = {}
+        if labels:
+            out["labels"] = np.empty(nvox, dtype=np.int32)
+        if voxel_of_node:
+            out["voxel_of_node"] = np.empty(max(self.n, 0), dtype=np.int64)
+        if nbr:
+            out["nbr"] = np.empty(6 * max(self.n, 0), dtype=np.int32)
+        vga_graph_export(self.handle, out.get("labels"), out.get("voxel_of_node"), out.get("nbr"))
+        if labels:
+            out["labels"] = out["labels"].reshape(self.shape)
+        if nbr:
+            out["nbr"] = out["nbr"].reshape(-1, 6)
+        return out
+
+    def close(self):
+        if self.handle:
+            vga_graph_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Sim:
+    """Owns a vga_sim handle on a Graph (which must stay alive)."""
+
+    def __init__(self, graph: Graph, params: dict, stream=None):
+        self.graph = graph
+        self.n = graph.n
+        self.handle = vga_sim_create(graph.handle, params, stream)
+
+    def set_params(self, params: dict):
+        vga_sim_set_params(self.handle, params)
+
+    def set_block_conductances(self, block_side: int, theta):
+        vga_sim_set_block_conductances(self.handle, block_side, theta)
+
+    def clear_conductances(self):
+        vga_sim_clear_conductances(self.handle)
+
+    def set_masses(self, x):
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+        vga_sim_set_masses(self.handle, x, self.n)
+
+    def get_masses(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty((5, self.n), dtype=np.float64)
+        vga_sim_get_masses(self.handle, out, self.n)
+        return out
+
+    def set_state_f32(self, x):
+        vga_sim_set_state_f32(self.handle, x, self.n)
+
+    def get_state_f32(self, out=None):
+        if out is None:
+            out = np.empty((5, self.n), dtype=np.float32)
+        vga_sim_get_state_f32(self.handle, out, self.n)
+        return out
+
+    def step(self, n_steps: int):
+        vga_sim_step(self.handle, n_steps)
+
+    def totals(self) -> np.ndarray:
+        return vga_sim_totals(self.handle)
+
+    def sync(self):
+        vga_sim_sync(self.handle)
+
+    def stats(self) -> dict:
+        return vga_sim_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            vga_sim_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

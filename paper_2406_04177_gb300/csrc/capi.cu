@@ -1,0 +1,405 @@
+// C ABI entry points of libvga (declared in include/vga.h): argument validation, ownership of the
+// device buffers, stream handling and error reporting.  The arithmetic lives in the kernels of
+// graph_build.cu, step.cu and pcg.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "vga_internal.cuh"
+
+namespace vga {
+
+namespace {
+thread_local std::string g_last_error = "no error";
+constexpr int32_t kDefaultCap = 1024;
+}  // namespace
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+vga_status fail(vga_status s, const std::string &msg) {
+    set_error(msg);
+    return s;
+}
+
+vga_status cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s failed: %s (%s) at %s:%d", what, cudaGetErrorName(e), cudaGetErrorString(e),
+                  file, line);
+    set_error(buf);
+    return e == cudaErrorMemoryAllocation ? VGA_ERR_OOM : VGA_ERR_CUDA;
+}
+
+vga_status dmalloc(void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char buf[256];
+        std::snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
+        set_error(buf);
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? VGA_ERR_OOM : VGA_ERR_CUDA;
+    }
+    return VGA_OK;
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+vga_status graph_build_device(vga_graph *g, const uint8_t *d_img, cudaStream_t st);
+vga_status graph_export_device(const vga_graph *g, int64_t *d_von, int32_t *d_nbr, cudaStream_t st);
+int totals_blocks();
+
+static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
+
+static vga_status validate_params(const vga_params *p, double max_g) {
+    if (!p) return fail(VGA_ERR_INVALID_ARG, "params is NULL");
+    const double vals[] = {p->D, p->rho, p->mu, p->v_som, p->v_fom, p->v_dom};
+    for (double v : vals)
+        if (!finite_nonneg(v)) return fail(VGA_ERR_INVALID_ARG, "rates and D must be finite and >= 0");
+    if (!(std::isfinite(p->dt) && p->dt > 0.0)) return fail(VGA_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (!(std::isfinite(p->beta) && p->beta >= 0.0 && p->beta <= 1.0))
+        return fail(VGA_ERR_INVALID_ARG, "beta must lie in [0, 1]");
+    if (!(std::isfinite(p->K_dom) && p->K_dom > 0.0)) return fail(VGA_ERR_INVALID_ARG, "K_dom must be finite and > 0");
+    if (p->scheme != VGA_SCHEME_EXPLICIT && p->scheme != VGA_SCHEME_IMPLICIT_PCG)
+        return fail(VGA_ERR_INVALID_ARG, "unknown scheme");
+    if (p->transform != VGA_TRANSFORM_SYNC && p->transform != VGA_TRANSFORM_ASYNC)
+        return fail(VGA_ERR_INVALID_ARG, "unknown transform");
+    if (p->scheme == VGA_SCHEME_IMPLICIT_PCG) {
+        if (!(std::isfinite(p->cg_rtol) && p->cg_rtol > 0.0)) return fail(VGA_ERR_INVALID_ARG, "cg_rtol must be > 0");
+        if (p->cg_maxit < 1) return fail(VGA_ERR_INVALID_ARG, "cg_maxit must be >= 1");
+    }
+    // products that become FP32 constants must stay finite
+    const double prods[] = {p->D * p->dt, p->rho * p->dt, p->mu * p->dt, p->v_som * p->dt, p->v_fom * p->dt,
+                            p->v_dom * p->dt};
+    for (double v : prods)
+        if (!(v < 3.0e38)) return fail(VGA_ERR_INVALID_ARG, "rate * dt overflows FP32");
+    if (p->scheme == VGA_SCHEME_EXPLICIT && 6.0 * p->D * p->dt * max_g > 1.0 + 1e-12) {
+        char buf[200];
+        std::snprintf(buf, sizeof(buf),
+                      "explicit scheme unstable: 6 * D * dt * max g = %.6g > 1 (Q would have negative entries)",
+                      6.0 * p->D * p->dt * max_g);
+        return fail(VGA_ERR_UNSTABLE_DT, buf);
+    }
+    return VGA_OK;
+}
+
+}  // namespace vga
+
+using namespace vga;
+
+extern "C" {
+
+const char *vga_strerror(int status) {
+    switch (status) {
+        case VGA_OK: return "VGA_OK";
+        case VGA_ERR_INVALID_ARG: return "VGA_ERR_INVALID_ARG";
+        case VGA_ERR_OOM: return "VGA_ERR_OOM";
+        case VGA_ERR_CUDA: return "VGA_ERR_CUDA";
+        case VGA_ERR_UNSTABLE_DT: return "VGA_ERR_UNSTABLE_DT";
+        case VGA_ERR_NOT_CONVERGED: return "VGA_ERR_NOT_CONVERGED";
+        case VGA_ERR_TIMEOUT: return "VGA_ERR_TIMEOUT";
+        case VGA_ERR_NONFINITE: return "VGA_ERR_NONFINITE";
+        case VGA_ERR_UNSUPPORTED: return "VGA_ERR_UNSUPPORTED";
+        default: return "VGA_ERR_UNKNOWN";
+    }
+}
+
+const char *vga_last_error(void) { return g_last_error.c_str(); }
+
+int32_t vga_version(void) { return 10000; }
+
+// ------------------------------------------------------------------------------------------------
+vga_status vga_graph_build(const uint8_t *img, int32_t nx, int32_t ny, int32_t nz, uint32_t flags, void *stream,
+                           vga_graph **out) {
+    if (!out) return fail(VGA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!img) return fail(VGA_ERR_INVALID_ARG, "img is NULL");
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 32768 || ny > 32768 || nz > 32768)
+        return fail(VGA_ERR_INVALID_ARG, "each image dimension must lie in [1, 32768]");
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    if (nvox >= (int64_t)1 << 31) return fail(VGA_ERR_INVALID_ARG, "nx*ny*nz must be < 2^31");
+    if (flags & ~(VGA_KEEP_LARGEST_COMPONENT | VGA_IMAGE_ON_DEVICE)) return fail(VGA_ERR_INVALID_ARG, "unknown flags");
+    cudaStream_t st = (cudaStream_t)stream;
+    vga_graph *g = new (std::nothrow) vga_graph();
+    if (!g) return fail(VGA_ERR_OOM, "host allocation of the graph handle failed");
+    g->nx = nx;
+    g->ny = ny;
+    g->nz = nz;
+    g->nvox = nvox;
+    g->flags = flags;
+    g->stream = st;
+    uint8_t *d_img = nullptr;
+    vga_status s = VGA_OK;
+    if (flags & VGA_IMAGE_ON_DEVICE) {
+        s = graph_build_device(g, img, st);
+    } else {
+        s = dmalloc((void **)&d_img, (size_t)nvox, "image");
+        if (s == VGA_OK) {
+            const cudaError_t e = cudaMemcpyAsync(d_img, img, (size_t)nvox, cudaMemcpyHostToDevice, st);
+            s = e == cudaSuccess ? graph_build_device(g, d_img, st) : cuda_fail(e, "image upload", __FILE__, __LINE__);
+        }
+    }
+    if (s == VGA_OK) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_fail(e, "graph build", __FILE__, __LINE__);
+    }
+    dfree(d_img);
+    if (s != VGA_OK) {
+        vga_graph_free(g);
+        return s;
+    }
+    *out = g;
+    return VGA_OK;
+}
+
+vga_status vga_graph_info(const vga_graph *g, int64_t *n_nodes, int32_t *n_components, int32_t *largest) {
+    if (!g) return fail(VGA_ERR_INVALID_ARG, "graph is NULL");
+    if (n_nodes) *n_nodes = g->n;
+    if (n_components) *n_components = g->n_components;
+    if (largest) *largest = g->largest;
+    return VGA_OK;
+}
+
+vga_status vga_graph_export(const vga_graph *g, int32_t *labels, int64_t *voxel_of_node, int32_t *nbr) {
+    if (!g) return fail(VGA_ERR_INVALID_ARG, "graph is NULL");
+    cudaStream_t st = g->stream;
+    if (labels) VGA_CUDA(cudaMemcpyAsync(labels, g->labels, sizeof(int32_t) * (size_t)g->nvox, cudaMemcpyDeviceToHost, st));
+    if ((voxel_of_node || nbr) && g->n > 0) {
+        int64_t *d_von = nullptr;
+        int32_t *d_nbr = nullptr;
+        vga_status s = VGA_OK;
+        if (voxel_of_node) s = dmalloc((void **)&d_von, sizeof(int64_t) * (size_t)g->n, "export nodes");
+        if (s == VGA_OK && nbr) s = dmalloc((void **)&d_nbr, sizeof(int32_t) * 6 * (size_t)g->n, "export nbr");
+        if (s == VGA_OK) s = graph_export_device(g, d_von, d_nbr, st);
+        if (s == VGA_OK && voxel_of_node) {
+            const cudaError_t e =
+                cudaMemcpyAsync(voxel_of_node, d_von, sizeof(int64_t) * (size_t)g->n, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) s = cuda_fail(e, "export copy", __FILE__, __LINE__);
+        }
+        if (s == VGA_OK && nbr) {
+            const cudaError_t e =
+                cudaMemcpyAsync(nbr, d_nbr, sizeof(int32_t) * 6 * (size_t)g->n, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) s = cuda_fail(e, "export copy", __FILE__, __LINE__);
+        }
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (s == VGA_OK && e != cudaSuccess) s = cuda_fail(e, "export", __FILE__, __LINE__);
+        dfree(d_von);
+        dfree(d_nbr);
+        return s;
+    }
+    VGA_CUDA(cudaStreamSynchronize(st));
+    return VGA_OK;
+}
+
+vga_status vga_graph_free(vga_graph *g) {
+    if (!g) return VGA_OK;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    dfree(g->labels);
+    dfree(g->mask);
+    dfree(g->pre);
+    delete g;
+    return VGA_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+vga_status vga_sim_create(const vga_graph *g, const vga_params *p, void *stream, vga_sim **out) {
+    if (!out) return fail(VGA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g) return fail(VGA_ERR_INVALID_ARG, "graph is NULL");
+    VGA_TRY(validate_params(p, 1.0));
+    vga_sim *s = new (std::nothrow) vga_sim();
+    if (!s) return fail(VGA_ERR_OOM, "host allocation of the simulation handle failed");
+    s->g = g;
+    s->stream = (cudaStream_t)stream;
+    s->n = g->n;
+    s->npad = ((g->n + 63) / 64) * 64;
+    sim_prepare_params(s, p);
+    vga_status st = VGA_OK;
+    const size_t bytes = sizeof(float) * 5 * (size_t)std::max<int64_t>(s->npad, 64);
+    for (int b = 0; b < 2 && st == VGA_OK; ++b) st = dmalloc((void **)&s->buf[b], bytes, "state");
+    if (st == VGA_OK) st = dmalloc((void **)&s->partials, sizeof(double) * 5 * (size_t)totals_blocks(), "partials");
+    if (st == VGA_OK) st = dmalloc((void **)&s->d_totals, sizeof(double) * 8, "totals");
+    if (st == VGA_OK) {
+        const cudaError_t e = cudaMallocHost((void **)&s->h_totals, sizeof(double) * 8);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMallocHost", __FILE__, __LINE__);
+    }
+    if (st == VGA_OK) st = build_chunks(g->topo(), kDefaultCap, &s->chunks, s->stream);
+    for (int b = 0; b < 2 && st == VGA_OK; ++b) {
+        const cudaError_t e = cudaMemsetAsync(s->buf[b], 0, bytes, s->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
+    }
+    if (st == VGA_OK) {
+        const cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "sim create", __FILE__, __LINE__);
+    }
+    if (st != VGA_OK) {
+        vga_sim_free(s);
+        return st;
+    }
+    *out = s;
+    return VGA_OK;
+}
+
+vga_status vga_sim_set_params(vga_sim *s, const vga_params *p) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    VGA_TRY(validate_params(p, s->max_g));
+    return sim_prepare_params(s, p);
+}
+
+vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const float *theta, int64_t n_theta) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    if (block_side < 1 || !theta) return fail(VGA_ERR_INVALID_ARG, "block_side must be >= 1 and theta non-NULL");
+    const vga_graph *g = s->g;
+    const int32_t nbx = (g->nx + block_side - 1) / block_side, nby = (g->ny + block_side - 1) / block_side,
+                  nbz = (g->nz + block_side - 1) / block_side;
+    const int64_t cx = (int64_t)nbz * nby * (nbx - 1), cy = (int64_t)nbz * (nby - 1) * nbx,
+                  cz = (int64_t)(nbz - 1) * nby * nbx;
+    if (n_theta != cx + cy + cz) {
+        char buf[160];
+        std::snprintf(buf, sizeof(buf), "n_theta = %lld but the block grid has %lld interfaces", (long long)n_theta,
+                      (long long)(cx + cy + cz));
+        return fail(VGA_ERR_INVALID_ARG, buf);
+    }
+    float mx = 1.0f;
+    for (int64_t k = 0; k < n_theta; ++k) {
+        if (!(std::isfinite(theta[k]) && theta[k] >= 0.0f))
+            return fail(VGA_ERR_INVALID_ARG, "theta values must be finite and >= 0");
+        mx = std::max(mx, theta[k]);
+    }
+    if (s->params.scheme == VGA_SCHEME_EXPLICIT && 6.0 * s->params.D * s->params.dt * mx > 1.0 + 1e-12)
+        return fail(VGA_ERR_UNSTABLE_DT, "explicit scheme unstable with these conductances (6 D dt max theta > 1)");
+    if (s->n_theta < n_theta) {
+        dfree(s->theta);
+        s->theta = nullptr;
+        s->n_theta = 0;
+        VGA_TRY(dmalloc((void **)&s->theta, sizeof(float) * (size_t)std::max<int64_t>(n_theta, 1), "theta"));
+        s->n_theta = n_theta;
+    }
+    if (n_theta > 0)
+        VGA_CUDA(cudaMemcpyAsync(s->theta, theta, sizeof(float) * (size_t)n_theta, cudaMemcpyHostToDevice, s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    s->bw.bs = block_side;
+    s->bw.nbx = nbx;
+    s->bw.nby = nby;
+    s->bw.nbz = nbz;
+    s->bw.off_y = cx;
+    s->bw.off_z = cx + cy;
+    s->bw.theta = s->theta;
+    s->wmode = W_BLOCK;
+    s->max_g = mx;
+    return VGA_OK;
+}
+
+vga_status vga_sim_clear_conductances(vga_sim *s) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    s->wmode = W_UNIT;
+    s->max_g = 1.0f;
+    return VGA_OK;
+}
+
+static vga_status ensure_stage(vga_sim *s) {
+    if (!s->stage) VGA_TRY(dmalloc((void **)&s->stage, sizeof(double) * 5 * (size_t)std::max<int64_t>(s->n, 1), "stage"));
+    return VGA_OK;
+}
+
+vga_status vga_sim_set_masses(vga_sim *s, const double *x, int32_t on_device) {
+    if (!s || (!x && s->n > 0)) return fail(VGA_ERR_INVALID_ARG, "sim or x is NULL");
+    if (s->n == 0) return VGA_OK;
+    if (on_device) {
+        VGA_TRY(sim_convert_in(s, x));
+        return VGA_OK;
+    }
+    for (int64_t k = 0; k < 5 * s->n; ++k)
+        if (!std::isfinite(x[k])) return fail(VGA_ERR_NONFINITE, "non-finite value in the input masses");
+    VGA_TRY(ensure_stage(s));
+    VGA_CUDA(cudaMemcpyAsync(s->stage, x, sizeof(double) * 5 * (size_t)s->n, cudaMemcpyHostToDevice, s->stream));
+    VGA_TRY(sim_convert_in(s, s->stage));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    return VGA_OK;
+}
+
+vga_status vga_sim_get_masses(vga_sim *s, double *x, int32_t on_device) {
+    if (!s || (!x && s->n > 0)) return fail(VGA_ERR_INVALID_ARG, "sim or x is NULL");
+    if (s->n == 0) return VGA_OK;
+    if (on_device) return sim_convert_out(s, x);
+    VGA_TRY(ensure_stage(s));
+    VGA_TRY(sim_convert_out(s, s->stage));
+    VGA_CUDA(cudaMemcpyAsync(x, s->stage, sizeof(double) * 5 * (size_t)s->n, cudaMemcpyDeviceToHost, s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    return VGA_OK;
+}
+
+vga_status vga_sim_set_state_f32(vga_sim *s, const float *x, int32_t on_device) {
+    if (!s || (!x && s->n > 0)) return fail(VGA_ERR_INVALID_ARG, "sim or x is NULL");
+    if (s->n == 0) return VGA_OK;
+    if (on_device) return sim_pack_f32(s, const_cast<float *>(x), true);
+    for (int c = 0; c < 5; ++c)
+        VGA_CUDA(cudaMemcpyAsync(s->comp(c), x + (size_t)c * s->n, sizeof(float) * (size_t)s->n, cudaMemcpyHostToDevice,
+                                 s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    return VGA_OK;
+}
+
+vga_status vga_sim_get_state_f32(vga_sim *s, float *x, int32_t on_device) {
+    if (!s || (!x && s->n > 0)) return fail(VGA_ERR_INVALID_ARG, "sim or x is NULL");
+    if (s->n == 0) return VGA_OK;
+    if (on_device) return sim_pack_f32(s, x, false);
+    for (int c = 0; c < 5; ++c)
+        VGA_CUDA(cudaMemcpyAsync(x + (size_t)c * s->n, s->comp(c), sizeof(float) * (size_t)s->n, cudaMemcpyDeviceToHost,
+                                 s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    return VGA_OK;
+}
+
+vga_status vga_sim_step(vga_sim *s, int64_t n_steps) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    if (n_steps < 0) return fail(VGA_ERR_INVALID_ARG, "n_steps must be >= 0");
+    if (s->params.scheme == VGA_SCHEME_IMPLICIT_PCG) return sim_step_implicit(s, n_steps);
+    return sim_step_explicit(s, n_steps);
+}
+
+vga_status vga_sim_totals(vga_sim *s, double *totals) {
+    if (!s || !totals) return fail(VGA_ERR_INVALID_ARG, "sim or totals is NULL");
+    return sim_totals(s, totals);
+}
+
+vga_status vga_sim_sync(vga_sim *s) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    return VGA_OK;
+}
+
+vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out) {
+    if (!s || !out) return fail(VGA_ERR_INVALID_ARG, "sim or out is NULL");
+    out->steps_done = s->steps_done;
+    out->cg_iterations = s->cg_iterations;
+    out->cg_last_relres = s->cg_last_relres;
+    out->kernel_launches = s->launches;
+    return VGA_OK;
+}
+
+vga_status vga_sim_free(vga_sim *s) {
+    if (!s) return VGA_OK;
+    cudaStreamSynchronize(s->stream);
+    dfree(s->buf[0]);
+    dfree(s->buf[1]);
+    dfree(s->partials);
+    dfree(s->d_totals);
+    if (s->h_totals) cudaFreeHost(s->h_totals);
+    dfree(s->stage);
+    dfree(s->theta);
+    dfree(s->cg);
+    dfree(s->cg_scalars);
+    if (s->h_cg) cudaFreeHost(s->h_cg);
+    free_chunks(&s->chunks);
+    delete s;
+    return VGA_OK;
+}
+
+}  // extern "C"

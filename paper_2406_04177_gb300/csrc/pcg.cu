@@ -1,0 +1,290 @@
+// Implicit time stepping: Scheme 2 (Sec. II.B.3b), (I + D dt L_g) m^{k+1} = y, solved matrix-free
+// by the Jacobi-preconditioned conjugate gradient of Sec. III (t_ii = 1 / b_ii), after the
+// transformation of every voxel (Sec. III).
+//
+// The solve runs in FP64 (a relative residual of 1e-8 is below FP32 resolution); the initial
+// guess is the right-hand side y and the stopping test is ||r||_2 <= rtol ||y||_2 on the recurrence
+// residual.  Every reduction is a fixed-order block-partial sum, so results are run-to-run
+// deterministic.  The recurrence scalars live on the device; the host only polls a "done" flag
+// every kBatch iterations, and kernels launched after convergence return at once.
+//
+// Kernels of one iteration (matrix B = I + c L_g, c = D dt):
+//   k_update_p   p = T r + beta p           (elementwise; beta = 0 on the first iteration)
+//   k_spmv       q = B p, partial p.q       (stencil over the chunk decode)
+//   k_scalar_a   alpha = (r.Tr) / (p.q)     (one block)
+//   k_update_xr  x += alpha p, r -= alpha q, partial r.Tr and r.r
+//   k_scalar_b   convergence test, beta     (one block)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "stencil.cuh"
+#include "vga_internal.cuh"
+
+namespace vga {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kEwBlocks = 1024;  // grid of the elementwise kernels (grid-stride loops)
+constexpr int kBatch = 8;        // iterations enqueued between two polls of the done flag
+
+struct CgScalars {
+    double rz, rr, bb, alpha, beta, relres, rtol2;
+    int32_t done, iters, notconv, maxit;
+};
+
+struct CgVecs {
+    double *x, *r, *p, *q, *t;
+};
+
+// b = y2, x = b, r = b - B x = -c L_g b, t = 1 / (1 + c sum_j g_ij); partials (r.Tr, r.r, b.b)
+template <int WM>
+__global__ void __launch_bounds__(kThreads) k_cg_init(Topo t, const int32_t *__restrict__ chunk_row, int32_t cap,
+                                                      double c, BlockWeights bw, const float *__restrict__ y2,
+                                                      CgVecs v, double *__restrict__ part) {
+    extern __shared__ uint32_t smem[];
+    int64_t v0;
+    const int32_t nv = decode_chunk<WM == W_BLOCK>(t, chunk_row, cap, smem, smem + cap, smem + 2 * cap, v0);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int32_t k = threadIdx.x; k < nv; k += blockDim.x) {
+        const int64_t i = v0 + k;
+        const uint32_t sx = smem[k];
+        const int32_t x = (int32_t)(sx & 0xffffu);
+        const uint32_t fl = sx >> 16;
+        const int32_t r = (int32_t)smem[cap + k];
+        int32_t y = 0, z = 0;
+        if (WM == W_BLOCK) {
+            y = (int32_t)(smem[2 * cap + k] & 0xffffu);
+            z = (int32_t)(smem[2 * cap + k] >> 16);
+        }
+        const double bi = (double)__ldg(y2 + i);
+        double lb = 0.0, deg = 0.0;
+        for_each_neighbour(t, i, x, r, fl, [&](int slot, int64_t j) {
+            const double g = (WM == W_UNIT) ? 1.0 : (double)block_theta(bw, slot, x, y, z);
+            lb += g * (bi - (double)__ldg(y2 + j));
+            deg += g;
+        });
+        const double ri = -c * lb;
+        const double ti = 1.0 / (1.0 + c * deg);
+        v.x[i] = bi;
+        v.r[i] = ri;
+        v.t[i] = ti;
+        acc[0] += ri * ti * ri;
+        acc[1] += ri * ri;
+        acc[2] += bi * bi;
+    }
+    __shared__ double out[3];
+    block_sum_store<3>(acc, out);
+    if (threadIdx.x < 3) part[(int64_t)blockIdx.x * 3 + threadIdx.x] = out[threadIdx.x];
+}
+
+// q = B p = p + c L_g p; partial p.q
+template <int WM>
+__global__ void __launch_bounds__(kThreads) k_spmv(Topo t, const int32_t *__restrict__ chunk_row, int32_t cap,
+                                                   double c, BlockWeights bw, const double *__restrict__ p,
+                                                   double *__restrict__ q, double *__restrict__ part,
+                                                   const CgScalars *__restrict__ sc) {
+    if (sc->done) return;
+    extern __shared__ uint32_t smem[];
+    int64_t v0;
+    const int32_t nv = decode_chunk<WM == W_BLOCK>(t, chunk_row, cap, smem, smem + cap, smem + 2 * cap, v0);
+    double acc[1] = {0.0};
+    for (int32_t k = threadIdx.x; k < nv; k += blockDim.x) {
+        const int64_t i = v0 + k;
+        const uint32_t sx = smem[k];
+        const int32_t x = (int32_t)(sx & 0xffffu);
+        const uint32_t fl = sx >> 16;
+        const int32_t r = (int32_t)smem[cap + k];
+        int32_t y = 0, z = 0;
+        if (WM == W_BLOCK) {
+            y = (int32_t)(smem[2 * cap + k] & 0xffffu);
+            z = (int32_t)(smem[2 * cap + k] >> 16);
+        }
+        const double pi = p[i];
+        double lp = 0.0;
+        for_each_neighbour(t, i, x, r, fl, [&](int slot, int64_t j) {
+            const double g = (WM == W_UNIT) ? 1.0 : (double)block_theta(bw, slot, x, y, z);
+            lp += g * (pi - p[j]);
+        });
+        const double qi = pi + c * lp;
+        q[i] = qi;
+        acc[0] += pi * qi;
+    }
+    __shared__ double out[1];
+    block_sum_store<1>(acc, out);
+    if (threadIdx.x == 0) part[blockIdx.x] = out[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_update_p(int64_t n, CgVecs v, const CgScalars *__restrict__ sc,
+                                                       int first) {
+    if (sc->done) return;
+    const double beta = first ? 0.0 : sc->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v.p[i] = v.t[i] * v.r[i] + beta * (first ? 0.0 : v.p[i]);
+}
+
+__global__ void __launch_bounds__(kThreads) k_update_xr(int64_t n, CgVecs v, const CgScalars *__restrict__ sc,
+                                                        double *__restrict__ part) {
+    if (sc->done) return;
+    const double alpha = sc->alpha;
+    double acc[2] = {0.0, 0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        v.x[i] += alpha * v.p[i];
+        const double ri = v.r[i] - alpha * v.q[i];
+        v.r[i] = ri;
+        acc[0] += ri * v.t[i] * ri;
+        acc[1] += ri * ri;
+    }
+    __shared__ double out[2];
+    block_sum_store<2>(acc, out);
+    if (threadIdx.x < 2) part[(int64_t)blockIdx.x * 2 + threadIdx.x] = out[threadIdx.x];
+}
+
+// Deterministic sum of part[k*stride + comp] over k < count by one block.
+__device__ double block_reduce_partials(const double *part, int64_t count, int stride, int comp) {
+    double acc[1] = {0.0};
+    for (int64_t k = threadIdx.x; k < count; k += blockDim.x) acc[0] += part[k * stride + comp];
+    __shared__ double out[1];
+    block_sum_store<1>(acc, out);
+    return out[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_scalar_init(const double *__restrict__ part, int64_t count,
+                                                          CgScalars *sc, double rtol, int maxit) {
+    const double rz = block_reduce_partials(part, count, 3, 0);
+    const double rr = block_reduce_partials(part, count, 3, 1);
+    const double bb = block_reduce_partials(part, count, 3, 2);
+    if (threadIdx.x == 0) {
+        sc->rz = rz;
+        sc->rr = rr;
+        sc->bb = bb;
+        sc->rtol2 = rtol * rtol;
+        sc->iters = 0;
+        sc->notconv = 0;
+        sc->maxit = maxit;
+        sc->alpha = 0.0;
+        sc->beta = 0.0;
+        sc->relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+        sc->done = (bb == 0.0 || rr <= sc->rtol2 * bb) ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_scalar_a(const double *__restrict__ part, int64_t count,
+                                                       CgScalars *sc) {
+    if (sc->done) return;
+    const double pq = block_reduce_partials(part, count, 1, 0);
+    if (threadIdx.x == 0) sc->alpha = sc->rz / pq;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scalar_b(const double *__restrict__ part, int64_t count,
+                                                       CgScalars *sc) {
+    if (sc->done) return;
+    const double rz = block_reduce_partials(part, count, 2, 0);
+    const double rr = block_reduce_partials(part, count, 2, 1);
+    if (threadIdx.x == 0) {
+        sc->iters += 1;
+        sc->rr = rr;
+        sc->relres = sqrt(rr / sc->bb);
+        if (rr <= sc->rtol2 * sc->bb) {
+            sc->done = 1;
+        } else if (sc->iters >= sc->maxit) {
+            sc->done = 1;
+            sc->notconv = 1;
+        } else {
+            sc->beta = rz / sc->rz;
+            sc->rz = rz;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cg_out(int64_t n, const double *__restrict__ x, float *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)x[i];
+}
+
+inline unsigned grid_for(int64_t count, int threads) { return (unsigned)((count + threads - 1) / threads); }
+
+template <int WM>
+vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgScalars *sc) {
+    const Topo t = s->g->topo();
+    const double c = s->params.D * s->params.dt;
+    const size_t smem = sizeof(uint32_t) * (size_t)s->chunks.cap * (WM == W_BLOCK ? 3 : 2);
+    const int G = s->chunks.count;
+    const int ew = (int)std::min<int64_t>(kEwBlocks, (int64_t)grid_for(s->n, kThreads));
+    cudaStream_t st = s->stream;
+    k_cg_init<WM><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, c, s->bw, s->comp(1), v, part_chunk);
+    k_scalar_init<<<1, kThreads, 0, st>>>(part_chunk, G, sc, s->params.cg_rtol, s->params.cg_maxit);
+    VGA_CHECK_LAUNCH();
+    s->launches += 2;
+    CgScalars *h = reinterpret_cast<CgScalars *>(s->h_cg);
+    bool first = true;
+    for (;;) {
+        for (int b = 0; b < kBatch; ++b) {
+            k_update_p<<<ew, kThreads, 0, st>>>(s->n, v, sc, first ? 1 : 0);
+            k_spmv<WM><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, c, s->bw, v.p, v.q, part_chunk, sc);
+            k_scalar_a<<<1, kThreads, 0, st>>>(part_chunk, G, sc);
+            k_update_xr<<<ew, kThreads, 0, st>>>(s->n, v, sc, part_ew);
+            k_scalar_b<<<1, kThreads, 0, st>>>(part_ew, ew, sc);
+            first = false;
+        }
+        VGA_CHECK_LAUNCH();
+        s->launches += 5 * kBatch;
+        VGA_CUDA(cudaMemcpyAsync(h, sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
+        VGA_CUDA(cudaStreamSynchronize(st));
+        if (h->done) break;
+    }
+    k_cg_out<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, v.x, s->spare(1));
+    VGA_CHECK_LAUNCH();
+    ++s->launches;
+    s->cur[1] ^= 1;
+    s->cg_iterations += h->iters;
+    s->cg_last_relres = h->relres;
+    return h->notconv ? VGA_ERR_NOT_CONVERGED : VGA_OK;
+}
+
+}  // namespace
+
+vga_status sim_step_implicit(vga_sim *s, int64_t n_steps) {
+    if (n_steps <= 0 || s->n == 0) {
+        s->steps_done += std::max<int64_t>(n_steps, 0);
+        return VGA_OK;
+    }
+    const int64_t G = s->chunks.count;
+    const int64_t need = 5 * s->npad + 3 * std::max<int64_t>(G, 1) + 2 * kEwBlocks;
+    if (s->cg_count < need) {
+        dfree(s->cg);
+        s->cg = nullptr;
+        s->cg_count = 0;
+        VGA_TRY(dmalloc((void **)&s->cg, sizeof(double) * (size_t)need, "PCG vectors"));
+        s->cg_count = need;
+    }
+    if (!s->cg_scalars) VGA_TRY(dmalloc((void **)&s->cg_scalars, sizeof(CgScalars) + 64, "PCG scalars"));
+    if (!s->h_cg) VGA_CUDA(cudaMallocHost((void **)&s->h_cg, sizeof(CgScalars) + 64));
+    CgVecs v;
+    v.x = s->cg;
+    v.r = v.x + s->npad;
+    v.p = v.r + s->npad;
+    v.q = v.p + s->npad;
+    v.t = v.q + s->npad;
+    double *part_chunk = v.t + s->npad;
+    double *part_ew = part_chunk + 3 * std::max<int64_t>(G, 1);
+    CgScalars *sc = reinterpret_cast<CgScalars *>(s->cg_scalars);
+    vga_status worst = VGA_OK;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        VGA_TRY(sim_transform_pass(s));
+        const vga_status st = (s->wmode == W_BLOCK) ? solve<W_BLOCK>(s, v, part_chunk, part_ew, sc)
+                                                    : solve<W_UNIT>(s, v, part_chunk, part_ew, sc);
+        if (st == VGA_ERR_NOT_CONVERGED) {
+            worst = st;
+        } else if (st != VGA_OK) {
+            return st;
+        }
+        s->steps_done += 1;
+    }
+    if (worst != VGA_OK) return fail(worst, "implicit solve reached cg_maxit before cg_rtol");
+    return VGA_OK;
+}
+
+}  // namespace vga

@@ -1,0 +1,178 @@
+// Internal declarations shared by the CUDA translation units of libvga (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/vga.h"
+
+namespace vga {
+
+// ---------------------------------------------------------------------------------------------
+// Error reporting: every failing path records a detail string and returns a vga_status.
+// ---------------------------------------------------------------------------------------------
+void set_error(const std::string &msg);
+vga_status fail(vga_status s, const std::string &msg);
+vga_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define VGA_CUDA(call)                                                         \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return ::vga::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define VGA_CHECK_LAUNCH() VGA_CUDA(cudaGetLastError())
+
+#define VGA_TRY(expr)                                \
+    do {                                             \
+        vga_status s_ = (expr);                      \
+        if (s_ != VGA_OK) return s_;                 \
+    } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// Topology of the node set on the device.
+//
+// The image is seen as nrows = ny*nz rows of nx voxels; each row is padded to W = ceil(nx/32)
+// 32-bit words.  Bit b of word (r, w) is set iff voxel x = 32w + b of row r is a node.  pre[q] is
+// the node index of the first node at or after word q in raster order (an exclusive prefix sum of
+// the word popcounts), with pre[nrows*W] = n.  A node's index is pre[q] + popc(word below its bit),
+// so the neighbour in any row is found from two words without a per-node table.
+// ---------------------------------------------------------------------------------------------
+struct Topo {
+    int32_t nx, ny, nz, W;
+    int32_t nrows;
+    int64_t n;
+    const uint32_t *mask;  // nrows*W words
+    const int32_t *pre;    // nrows*W + 1
+};
+
+// Chunking of the node range for the stencil kernels: chunk g holds nodes [g*cap, (g+1)*cap) and
+// spans image rows chunk_row[g] .. chunk_row[g+1] (inclusive; chunk_row[G] is the row of node n-1).
+struct Chunks {
+    int32_t cap = 0;
+    int32_t count = 0;
+    int32_t *row = nullptr;  // count + 1 entries (device)
+};
+
+// Float parameters of one time step (products with dt taken in FP64 on the host, then rounded).
+struct StepParams {
+    float a;      // v_dom * dt
+    float K;      // K_dom
+    float r;      // rho * dt
+    float m;      // mu * dt
+    float beta;   // beta
+    float omb;    // 1 - beta
+    float f;      // v_fom * dt
+    float s;      // v_som * dt
+    float c;      // D * dt
+    int transform;
+};
+
+// Input and output compartment arrays of one pass over the state.
+struct StateIO {
+    const float *in[5];
+    float *out[5];
+};
+
+// Edge-weight modes of the stencil.
+enum WeightMode { W_UNIT = 0, W_BLOCK = 1 };
+
+struct BlockWeights {
+    int32_t bs = 0;              // block side
+    int32_t nbx = 0, nby = 0, nbz = 0;
+    int64_t off_y = 0, off_z = 0;  // offsets of the y- and z-normal faces in theta
+    const float *theta = nullptr;  // device
+};
+
+// ---------------------------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t count = 0;
+};
+
+vga_status dmalloc(void **p, size_t bytes, const char *what);
+void dfree(void *p);
+
+// Exclusive prefix sum of popcount(words[q]) over q in [0, nwords): out[q], out[nwords] = total.
+// `scratch` must hold scan_scratch_ints(nwords) ints.
+size_t scan_scratch_ints(int64_t nwords);
+vga_status scan_popc(const uint32_t *words, int64_t nwords, int32_t *out, int32_t *scratch,
+                     cudaStream_t st);
+
+// Builds the chunk table of `topo` for chunk size cap (device work, one launch).
+vga_status build_chunks(const Topo &topo, int32_t cap, Chunks *ch, cudaStream_t st);
+void free_chunks(Chunks *ch);
+
+}  // namespace vga
+
+// ---------------------------------------------------------------------------------------------
+// Library-owned handle types (opaque in the C ABI).
+// ---------------------------------------------------------------------------------------------
+struct vga_graph {
+    int32_t nx = 0, ny = 0, nz = 0;
+    int64_t nvox = 0;
+    int64_t n = 0;
+    int32_t n_components = 0;
+    int32_t largest = -1;
+    uint32_t flags = 0;
+    int32_t *labels = nullptr;  // device, nvox
+    uint32_t *mask = nullptr;   // device, nrows*W
+    int32_t *pre = nullptr;     // device, nrows*W + 1
+    cudaStream_t stream = nullptr;
+    vga::Topo topo() const;
+};
+
+struct vga_sim {
+    const vga_graph *g = nullptr;
+    vga_params params{};
+    vga::StepParams sp{};
+    cudaStream_t stream = nullptr;
+    int64_t n = 0;
+    int64_t npad = 0;         // row stride of the state arrays (multiple of 64 floats)
+    float *buf[2] = {nullptr, nullptr};  // two state buffers of 5*npad floats
+    int cur[5] = {0, 0, 0, 0, 0};        // which buffer holds compartment c
+    vga::Chunks chunks;
+    // conductances
+    int wmode = vga::W_UNIT;
+    vga::BlockWeights bw;
+    float *theta = nullptr;
+    int64_t n_theta = 0;
+    float max_g = 1.0f;
+    // reductions
+    double *partials = nullptr;  // per-block FP64 partial sums
+    int64_t partials_cap = 0;
+    double *d_totals = nullptr;  // 8 doubles (device)
+    double *h_totals = nullptr;  // pinned host mirror
+    // staging for FP64 input/output
+    double *stage = nullptr;
+    // implicit-scheme work vectors (FP64), allocated on first use
+    double *cg = nullptr;
+    int64_t cg_count = 0;
+    double *cg_scalars = nullptr;  // device scalars of the PCG recurrence
+    double *h_cg = nullptr;        // pinned mirror of the PCG scalars
+    int64_t steps_done = 0;
+    int64_t cg_iterations = 0;
+    double cg_last_relres = 0.0;
+    int64_t launches = 0;
+
+    float *comp(int c) { return buf[cur[c]] + (size_t)c * npad; }
+    float *spare(int c) { return buf[1 - cur[c]] + (size_t)c * npad; }
+};
+
+namespace vga {
+// step.cu
+vga_status sim_prepare_params(vga_sim *s, const vga_params *p);
+vga_status sim_step_explicit(vga_sim *s, int64_t n_steps);
+vga_status sim_totals(vga_sim *s, double *h_out);
+vga_status sim_convert_in(vga_sim *s, const double *d_x);    // device FP64 (5 x n) -> state
+vga_status sim_convert_out(vga_sim *s, double *d_x);         // state -> device FP64 (5 x n)
+vga_status sim_pack_f32(vga_sim *s, float *d_x, bool to_state);
+vga_status sim_transform_pass(vga_sim *s);  // Y = T(X) for every node, all compartments swapped
+// pcg.cu
+vga_status sim_step_implicit(vga_sim *s, int64_t n_steps);
+}  // namespace vga

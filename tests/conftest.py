@@ -18,3 +18,15 @@ def oracle_lib():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def vga():
+    """The CUDA library (built in-tree if stale).  GPU tests fail loudly when it cannot run."""
+    from paper_2406_04177_gb300 import build
+
+    build.build()
+    import paper_2406_04177_gb300 as v
+
+    v.load_library()
+    return v

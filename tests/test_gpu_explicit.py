@@ -1,0 +1,186 @@
+"""Explicit synchronous/asynchronous stepping on the GPU (FP32 state) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from tests.helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL_L2 = 1e-5     # relative L2 per compartment against FP64
+TOL_DRIFT = 1e-7  # relative total-mass drift
+
+
+def _setup(vga, oracle_lib, shape, por, seed, keep=True, organic=False):
+    img = synth.pore_mask(shape, por, seed)
+    og = oracle_lib.graph_build(img, keep_largest=keep)
+    g = vga.Graph(img, keep_largest=keep)
+    assert g.n == og.n
+    X0 = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), seed,
+                              with_organic_matter=organic)
+    return img, og, g, X0
+
+
+def _assert_close(got, ref, tol=TOL_L2):
+    for c in range(5):
+        assert rel_l2(got[c], ref[c]) <= tol, (c, rel_l2(got[c], ref[c]))
+
+
+def test_c1_64cubed_1000_steps(vga, oracle_lib):
+    """64^3, 17% porosity, largest component, paper parameters, dt = 0.9 h^2/(6D), 1000 steps."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (64, 64, 64), 0.17, 1)
+    p = synth.paper_params()
+    sim = vga.Sim(g, p)
+    sim.set_masses(X0)
+    sim.step(1000)
+    got = sim.get_masses()
+    ref = oracle_lib.explicit_run(og.nbr, p, X0, 1000)
+    _assert_close(got, ref)
+    tot = sim.totals()
+    assert abs(tot.sum() - X0.sum()) <= TOL_DRIFT * X0.sum()
+    assert np.allclose(tot, oracle_lib.totals(ref), rtol=1e-6, atol=1e-12)
+    assert got.min() >= 0.0
+
+
+def test_ten_thousand_steps_drift_and_error(vga, oracle_lib):
+    """10^4 steps (the long-run configuration) on a 48^3 mask: relative L2 and drift every 2000."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (48, 48, 48), 0.2, 2, organic=True)
+    p = synth.paper_params()
+    sim = vga.Sim(g, p)
+    sim.set_masses(X0)
+    ref = X0.copy()
+    for _ in range(5):
+        sim.step(2000)
+        ref = oracle_lib.explicit_run(og.nbr, p, ref, 2000)
+        got = sim.get_masses()
+        _assert_close(got, ref)
+        assert abs(sim.totals().sum() - X0.sum()) <= TOL_DRIFT * X0.sum()
+
+
+@pytest.mark.parametrize("transform", [0, 1])
+def test_transform_variants(vga, oracle_lib, transform):
+    img, og, g, X0 = _setup(vga, oracle_lib, (40, 36, 44), 0.22, 3, organic=True)
+    p = synth.paper_params(transform=transform)
+    sim = vga.Sim(g, p)
+    sim.set_masses(X0)
+    sim.step(300)
+    _assert_close(sim.get_masses(), oracle_lib.explicit_run(og.nbr, p, X0, 300, transform=transform))
+
+
+def test_clamps_active(vga, oracle_lib):
+    """Rates large enough that every clamp of the synchronous listing fires (dyadic-free values)."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (20, 24, 28), 0.3, 4, organic=True)
+    X0[0] = np.where(X0[1] > 0, X0[1] * 3.0, X0[0]).astype(np.float32)
+    p = dict(D=1.0, dt=0.12, rho=3.0, mu=6.0, beta=0.55, v_som=9.0, v_fom=11.0, v_dom=40.0, K_dom=1e-5,
+             scheme=0, transform=0)
+    sim = vga.Sim(g, p)
+    sim.set_masses(X0)
+    sim.step(50)
+    _assert_close(sim.get_masses(), oracle_lib.explicit_run(og.nbr, p, X0, 50), tol=2e-5)
+
+
+def test_block_conductances(vga, oracle_lib):
+    img, og, g, X0 = _setup(vga, oracle_lib, (32, 32, 32), 0.22, 5, organic=True)
+    bs = 8
+    nb = oracle_lib.block_grid(img.shape, bs)
+    theta = synth.block_conductances(nb, 7)
+    p = synth.paper_params(dt=0.9 / (6 * synth.D_DOM * theta.max()))
+    sim = vga.Sim(g, p)
+    sim.set_block_conductances(bs, theta.astype(np.float32))
+    sim.set_masses(X0)
+    sim.step(400)
+    g6 = oracle_lib.block_face_weights(img.shape, bs, og.voxel_of_node, og.nbr, theta)
+    _assert_close(sim.get_masses(), oracle_lib.explicit_run(og.nbr, p, X0, 400, g6=g6))
+
+
+@pytest.mark.parametrize("shape,por", [((1, 1, 1), 0.0), ((1, 1, 3000), 0.0), ((3, 2, 5), 0.5),
+                                       ((5, 40, 45), 0.55), ((2, 3, 1100), 0.1)])
+def test_small_and_ragged(vga, oracle_lib, shape, por):
+    """Single voxel, a long 1D path (several chunks, ragged tail), tiny graphs, several components."""
+    rng = np.random.default_rng(11)
+    img = (rng.random(shape) < por).astype(np.uint8)
+    for keep in (True, False):
+        og = oracle_lib.graph_build(img, keep_largest=keep)
+        g = vga.Graph(img, keep_largest=keep)
+        X0 = synth.random_masses(og.n, 3, scale=1e-3, density=0.5)
+        p = synth.paper_params()
+        sim = vga.Sim(g, p)
+        sim.set_masses(X0)
+        sim.step(37)
+        _assert_close(sim.get_masses(), oracle_lib.explicit_run(og.nbr, p, X0, 37))
+
+
+def test_empty_graph(vga):
+    g = vga.Graph(np.ones((4, 4, 4), dtype=np.uint8))
+    assert g.n == 0
+    sim = vga.Sim(g, synth.paper_params())
+    sim.set_masses(np.zeros((5, 0)))
+    sim.step(10)
+    assert np.all(sim.totals() == 0.0)
+    assert sim.get_masses().shape == (5, 0)
+
+
+def test_zero_and_one_step(vga, oracle_lib):
+    img, og, g, X0 = _setup(vga, oracle_lib, (16, 16, 16), 0.3, 6)
+    p = synth.paper_params()
+    sim = vga.Sim(g, p)
+    sim.set_masses(X0)
+    sim.step(0)
+    assert np.array_equal(sim.get_masses(), X0)
+    sim.step(1)
+    _assert_close(sim.get_masses(), oracle_lib.explicit_run(og.nbr, p, X0, 1), tol=1e-6)
+
+
+def test_unstable_dt_rejected(vga):
+    g = vga.Graph(np.zeros((3, 3, 3), dtype=np.uint8))
+    p = synth.paper_params(dt=1.01 / (6 * synth.D_DOM))
+    with pytest.raises(vga.VgaError) as e:
+        vga.Sim(g, p)
+    assert e.value.name == "VGA_ERR_UNSTABLE_DT"
+    bad = synth.paper_params()
+    bad["K_dom"] = 0.0
+    with pytest.raises(vga.VgaError) as e:
+        vga.Sim(g, bad)
+    assert e.value.name == "VGA_ERR_INVALID_ARG"
+    sim = vga.Sim(g, synth.paper_params())
+    X = np.zeros((5, g.n))
+    X[1, 0] = np.nan
+    with pytest.raises(vga.VgaError) as e:
+        sim.set_masses(X)
+    assert e.value.name == "VGA_ERR_NONFINITE"
+
+
+def test_resume_is_bit_exact(vga, oracle_lib):
+    """N steps equal N/2 steps, save (FP32 state), restore into a new simulation, N/2 steps."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (30, 34, 38), 0.25, 8, organic=True)
+    p = synth.paper_params()
+    a = vga.Sim(g, p)
+    a.set_masses(X0)
+    a.step(120)
+    full = a.get_state_f32()
+    b = vga.Sim(g, p)
+    b.set_masses(X0)
+    b.step(60)
+    saved = b.get_state_f32()
+    c = vga.Sim(g, p)
+    c.set_state_f32(saved)
+    c.step(60)
+    assert np.array_equal(c.get_state_f32(), full)
+
+
+def test_device_state_io(vga, oracle_lib):
+    import torch
+
+    img, og, g, X0 = _setup(vga, oracle_lib, (24, 24, 24), 0.25, 9)
+    p = synth.paper_params()
+    sim = vga.Sim(g, p)
+    sim.set_masses(torch.from_numpy(X0).cuda())
+    sim.step(25)
+    out = torch.empty((5, g.n), dtype=torch.float64, device="cuda")
+    sim.get_masses(out)
+    torch.cuda.synchronize()
+    _assert_close(out.cpu().numpy(), oracle_lib.explicit_run(og.nbr, p, X0, 25))
+    f32 = torch.empty((5, g.n), dtype=torch.float32, device="cuda")
+    sim.get_state_f32(f32)
+    torch.cuda.synchronize()
+    assert np.array_equal(f32.cpu().numpy().astype(np.float64), out.cpu().numpy())

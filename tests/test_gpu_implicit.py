@@ -1,0 +1,73 @@
+"""Implicit scheme (Scheme 2 by Jacobi-PCG) on the GPU against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import synth
+from tests.helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(vga, oracle_lib, shape, por, seed):
+    img = synth.pore_mask(shape, por, seed)
+    og = oracle_lib.graph_build(img)
+    g = vga.Graph(img)
+    X0 = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), seed,
+                              with_organic_matter=True)
+    return img, og, g, X0
+
+
+def test_implicit_ten_times_explicit_limit(vga, oracle_lib):
+    """dt = 10 x the explicit limit (D dt = 1.5), rtol 1e-8: the configuration of the paper-scale run."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (48, 48, 48), 0.17, 1)
+    p = synth.paper_params(dt=10 * 0.9 / (6 * synth.D_DOM), scheme=1, cg_rtol=1e-8, cg_maxit=500)
+    sim = vga.Sim(g, p)
+    sim.set_masses(X0)
+    sim.step(20)
+    got = sim.get_masses()
+    ref, status, iters, worst = oracle_lib.implicit_run(og.nbr, p, X0, 20, rtol=1e-12)
+    assert status == 0
+    for c in range(5):
+        assert rel_l2(got[c], ref[c]) <= 1e-5, c
+    st = sim.stats()
+    assert 0 < st["cg_iterations"] <= 20 * 100
+    assert st["cg_last_relres"] <= 1e-8
+    assert abs(sim.totals().sum() - X0.sum()) <= 1e-7 * X0.sum()
+
+
+def test_implicit_block_weights_and_async(vga, oracle_lib):
+    img, og, g, X0 = _setup(vga, oracle_lib, (24, 32, 24), 0.25, 2)
+    bs = 8
+    nb = oracle_lib.block_grid(img.shape, bs)
+    theta = synth.block_conductances(nb, 3)
+    p = synth.paper_params(dt=5 * 0.9 / (6 * synth.D_DOM), scheme=1, transform=1, cg_rtol=1e-10)
+    sim = vga.Sim(g, p)
+    sim.set_block_conductances(bs, theta.astype(np.float32))
+    sim.set_masses(X0)
+    sim.step(8)
+    g6 = oracle_lib.block_face_weights(img.shape, bs, og.voxel_of_node, og.nbr, theta)
+    ref, status, _, _ = oracle_lib.implicit_run(og.nbr, p, X0, 8, rtol=1e-13, g6=g6, transform=1)
+    got = sim.get_masses()
+    for c in range(5):
+        assert rel_l2(got[c], ref[c]) <= 1e-5, c
+
+
+def test_not_converged_reported(vga, oracle_lib):
+    img, og, g, X0 = _setup(vga, oracle_lib, (24, 24, 24), 0.25, 3)
+    p = synth.paper_params(dt=50 * 0.9 / (6 * synth.D_DOM), scheme=1, cg_rtol=1e-14, cg_maxit=2)
+    sim = vga.Sim(g, p)
+    sim.set_masses(X0)
+    with pytest.raises(vga.VgaError) as e:
+        sim.step(1)
+    assert e.value.name == "VGA_ERR_NOT_CONVERGED"
+
+
+def test_zero_dom(vga):
+    g = vga.Graph(np.zeros((6, 6, 6), dtype=np.uint8))
+    X = np.zeros((5, g.n))
+    X[0] = 1e-4
+    p = synth.paper_params(dt=1e-4, scheme=1)
+    sim = vga.Sim(g, p)
+    sim.set_masses(X)
+    sim.step(3)
+    assert np.isfinite(sim.get_masses()).all()
