@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the voxel-graph diffusion-transformation step (arXiv 2406.04177).
+
+Workload: a 512^3 pore image at 17% porosity (Gaussian-smoothed white noise, sigma = 2 voxels,
+largest 6-connected component kept), the Sec. IV.C parameters and initial masses, dt = 0.9/(6D)
+(explicit synchronous scheme).  One benchmark step = `--substeps` explicit time steps on the GPU
+(FP32 state) followed by the FP64 compartment-mass reduction.  The metric is pore-voxel-steps/s
+(PVS/s): nodes x time steps / second.
+
+Printed: one JSON line (rank 0).  Keys beyond the base contract:
+  roofline       fused explicit kernel: algorithmic bytes (40 B per node) / mean launch time,
+                 timed with CUDA events on its stream during the timed region
+  cpu_baseline   the FP64 oracle on the host cores over a bounded number of time steps
+  error_vs_fp64  GPU after those same steps against the oracle (relative L2 per compartment,
+                 total-mass drift)
+  e2e            the same metric through the C ABI with host buffers (upload, step, download)
+  implicit, graph_build   the other hot-path rows on the same workload (untimed region)
+
+`--impl reference` times the FP64 oracle itself (host cores) on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "pore-voxel-steps/s fwd & adjoint at 512³, % HBM roofline, at stated err vs FP64"
+UNIT = "pore-voxel-steps/s"
+BYTES_PER_PVS = 40  # five FP32 compartments read and written per node and time step
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--substeps", type=int, default=500, help="explicit time steps per benchmark step")
+    ap.add_argument("--side", type=int, default=512)
+    ap.add_argument("--porosity", type=float, default=0.17)
+    ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
+    ap.add_argument("--no-extras", action="store_true", help="skip the implicit and graph-build measurements")
+    return ap.parse_args()
+
+
+def workload_name(a) -> str:
+    return (f"explicit synchronous forward, {a.side}^3 pore image, Gaussian-smoothed white noise (sigma 2) "
+            f"at {a.porosity:.0%} porosity, largest 6-connected component, seed {a.seed}, Sec. IV.C rates, "
+            f"dt = 0.9/(6D)")
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("step.cu", "stencil.cuh", "physics.cuh", "vga_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2406_04177_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(n_nodes: int):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary, scaled to this
+    workload by the node count; None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_node"]) * n_nodes
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of the GPU this process uses, taken while the timed region
+    runs."""
+
+    FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.lines: list[str] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            bus = parts[0].lower()
+            if self.bus_id and not (bus.endswith(self.bus_id[-12:]) or self.bus_id.endswith(bus[-12:])):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_workload(a, dev: bool):
+    import synth
+
+    t0 = time.time()
+    img = synth.pore_mask((a.side, a.side, a.side), a.porosity, a.seed)
+    return img, time.time() - t0
+
+
+def run_cpu_baseline(a, img, X0, gpu_after=None):
+    """Times the FP64 oracle (all host cores) on the first M explicit steps of the workload and,
+    if GPU results for the same M steps are given, compares them.  Returns (baseline, error)."""
+    import oracle
+    import synth
+
+    og = oracle.graph_build(img, keep_largest=True)
+    p = synth.paper_params()
+    t0 = time.time()
+    X1 = oracle.explicit_run(og.nbr, p, X0, 1)
+    t1 = time.time() - t0
+    m = int(max(2, min(60, round(a.cpu_seconds / max(t1, 1e-3)))))
+    t0 = time.time()
+    Xm = oracle.explicit_run(og.nbr, p, X1, m - 1)
+    dt = time.time() - t0
+    rate = og.n * (m - 1) / dt
+    base = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{m - 1} explicit steps of the {a.side}^3 workload (after 1 untimed step), FP64, "
+                      f"OpenMP over the host cores"}
+    return base, og, Xm, m
+
+
+def rel_l2(a, b):
+    nb = float(np.linalg.norm(b))
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.abs(a - b).max())
+
+
+def bench_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2406_04177_gb300 as vga
+    import synth
+
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    vga.load_library()
+    stream = torch.cuda.current_stream()
+
+    img, t_mask = build_workload(a, True)
+    d_img = torch.from_numpy(img).cuda()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    g = vga.Graph(d_img, keep_largest=True, stream=stream)
+    t_graph = time.time() - t0
+    del d_img
+    ex = g.export(labels=False, nbr=False)
+    kept = synth.kept_mask_from_nodes(img.shape, ex["voxel_of_node"])
+    X0 = synth.initial_masses(kept, a.seed)
+    n = g.n
+    params = synth.paper_params()
+    sim = vga.Sim(g, params, stream=stream)
+    x0_dev = torch.from_numpy(X0).cuda()
+    sim.set_masses(x0_dev)
+    tot0 = sim.totals()
+
+    S = a.substeps
+    for _ in range(a.warmup):
+        sim.step(S)
+        sim.totals()
+    sim.enable_timing(True)
+    sim.read_timing(reset=True)
+    launches0 = sim.stats()["kernel_launches"]
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+        bus = f"{torch.cuda.get_device_properties(local).pci_domain_id:08x}:{bus:02x}:" \
+              f"{torch.cuda.get_device_properties(local).pci_device_id:02x}.0"
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        sim.step(S)
+        sim.totals()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = sim.stats()["kernel_launches"] - launches0
+    timing = sim.read_timing(reset=True)
+    sim.enable_timing(False)
+    tot1 = sim.totals()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * S * a.steps / (ms / 1e3)
+
+    fused_ms, fused_count = timing["fused_step"]
+    mean_launch_s = fused_ms / max(fused_count, 1) / 1e3
+    peak, peak_src = load_peaks()
+    achieved = BYTES_PER_PVS * n / mean_launch_s / 1e9
+    traffic = recorded_traffic(n)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_stencil<fused> (diffuse stored transformed DOM, then transform)",
+                "algorithmic_bytes_per_launch": BYTES_PER_PVS * n, "mean_launch_ms": mean_launch_s * 1e3,
+                "launches_timed": fused_count, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+                if peak_src == "measured" else "fallback 6.8 TB/s",
+                "pvs_x40B_over_peak": value / world * BYTES_PER_PVS / (peak * 1e9)}
+
+    # ---- end to end through the C ABI with host buffers (outside the timed region) ----
+    xh = torch.from_numpy(X0.astype(np.float32)).pin_memory()
+    outh = torch.empty((5, n), dtype=torch.float32).pin_memory()
+    xh_np, outh_np = xh.numpy(), outh.numpy()
+    e2e_iters = max(2, min(a.steps, 5))
+    sim.set_state_f32(xh_np)
+    sim.step(S)
+    sim.get_state_f32(outh_np)
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_iters):
+        sim.set_state_f32(xh_np)
+        sim.step(S)
+        sim.totals()
+        sim.get_state_f32(outh_np)
+    w1 = time.perf_counter()
+    e2e_val = world * n * S * e2e_iters / (w1 - w0)
+    e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 4),
+           "d2h_bytes_per_step": int(outh.numel() * 4 + 5 * 8),
+           "how": "per step: vga_sim_set_state_f32 from pinned host memory, vga_sim_step(substeps), "
+                  "vga_sim_totals, vga_sim_get_state_f32 to pinned host memory; wall clock"}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+           "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": workload_name(a), "grid": [a.side] * 3, "n_nodes": n,
+                      "time_steps_per_step": S, "l2": "inputs larger than L2: two FP32 state buffers of "
+                      f"{5 * 4 * n / 1e6:.0f} MB each", "parallelism": "replicas" if world > 1 else "single GPU"},
+           "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+           "kernel_time_ms": {k: v[0] for k, v in timing.items() if v[1]},
+           "drift_timed_region": float(abs(tot1.sum() - tot0.sum()) / tot0.sum())}
+
+    if not a.no_extras:
+        extras = {}
+        extras["graph_build"] = {"seconds": t_graph, "n_nodes": n, "n_components": g.n_components,
+                                 "mask_seconds": t_mask, "note": "device image input, includes one stream sync"}
+        # implicit scheme (Scheme 2 by PCG) at 10x the explicit limit, rtol 1e-8
+        pi = synth.paper_params(dt=10 * 0.9 / (6 * synth.D_DOM), scheme=1, cg_rtol=1e-8, cg_maxit=500)
+        simi = vga.Sim(g, pi, stream=stream)
+        simi.set_masses(x0_dev)
+        simi.step(1)
+        simi.sync()
+        it0 = simi.stats()["cg_iterations"]
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        nimp = 3
+        simi.step(nimp)
+        simi.sync()
+        w1 = time.perf_counter()
+        st = simi.stats()
+        extras["implicit"] = {"value": n * nimp / (w1 - w0), "unit": UNIT + " (one solve = one step)",
+                              "cg_iterations_per_step": (st["cg_iterations"] - it0) / nimp,
+                              "last_relres": st["cg_last_relres"], "dt_over_explicit_limit": 10 / 0.9 * 0.9,
+                              "rtol": 1e-8}
+        simi.close()
+        out.update(extras)
+
+    if rank == 0 and world == 1 or (rank == 0 and world > 1):
+        # cpu baseline (rank 0, N = 1 only) and the FP64 error of the same steps
+        if world == 1:
+            base, og, Xm, m = run_cpu_baseline(a, img, X0)
+            assert og.n == n
+            simc = vga.Sim(g, params, stream=stream)
+            simc.set_masses(x0_dev)
+            simc.step(m)
+            got = simc.get_masses()
+            out["cpu_baseline"] = base
+            out["error_vs_fp64"] = {"time_steps": m, "rel_l2": [rel_l2(got[c], Xm[c]) for c in range(5)],
+                                    "drift": float(abs(simc.totals().sum() - X0.sum()) / X0.sum()),
+                                    "compared": "every node, every compartment, against the FP64 oracle"}
+            simc.close()
+        print(json.dumps(out), flush=True)
+    sim.close()
+    g.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def bench_reference(a):
+    """The FP64 oracle (host cores) timed on the same workload: each step = one explicit time step
+    of the full 512^3 state."""
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    import oracle
+    import synth
+
+    img, _ = build_workload(a, False)
+    og = oracle.graph_build(img, keep_largest=True)
+    X = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), a.seed)
+    p = synth.paper_params()
+    for _ in range(a.warmup):
+        X = oracle.explicit_run(og.nbr, p, X, 1)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        X = oracle.explicit_run(og.nbr, p, X, 1)
+    dt = time.perf_counter() - t0
+    value = og.n * a.steps / dt
+    cores = oracle.num_threads()
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_name(a), "grid": [a.side] * 3, "n_nodes": og.n, "time_steps_per_step": 1,
+                      "parallelism": "host cores (OpenMP)"},
+           "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                            "sample": f"{a.steps} explicit time steps of the {a.side}^3 workload"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        bench_reference(a)
+    else:
+        bench_ours(a)
+
+
+if __name__ == "__main__":
+    main()

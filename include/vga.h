@@ -95,6 +95,12 @@ vga_status vga_graph_free(vga_graph *g);
 #define VGA_SCHEME_IMPLICIT_PCG 1  /* Scheme 2: (I + D dt L_g) m_new = m, Jacobi-PCG (Sec. III) */
 #define VGA_TRANSFORM_SYNC 0       /* every flux from the old state, then update (eq. 3 + clamps) */
 #define VGA_TRANSFORM_ASYNC 1      /* sequential growth, mortality, respiration, SOM, FOM */
+/* Storage of the state.  One explicit step changes a compartment by 1e-6 .. 1e-8 of its value at
+ * the paper's time step, which FP32 rounding biases step after step.  The default keeps, next to
+ * every FP32 value, a BF16 residual of its rounding error (about 33 significant bits, 6 bytes per
+ * value); VGA_STATE_F32 stores the FP32 value alone (4 bytes, errors grow with the step count). */
+#define VGA_STATE_COMPENSATED 0
+#define VGA_STATE_F32 1
 
 typedef struct vga_params {
     double D;       /* DOM diffusion coefficient D_DOM */
@@ -110,7 +116,7 @@ typedef struct vga_params {
     int32_t transform; /* VGA_TRANSFORM_* */
     double cg_rtol;    /* implicit only: stop when ||r||_2 <= cg_rtol ||b||_2 */
     int32_t cg_maxit;  /* implicit only: iteration cap per step */
-    int32_t reserved;  /* set to 0 */
+    int32_t state_precision; /* VGA_STATE_* */
 } vga_params;
 
 /* ============================================================================================
@@ -147,9 +153,18 @@ vga_status vga_sim_clear_conductances(vga_sim *s);
 vga_status vga_sim_set_masses(vga_sim *s, const double *x, int32_t on_device);
 /* Current state X (5 x n, FP64) into caller memory (host, or device if on_device != 0). */
 vga_status vga_sim_get_masses(vga_sim *s, double *x, int32_t on_device);
-/* FP32 variants of the two calls above (same layout, no conversion). */
+/* FP32 variants of the two calls above (same layout).  Set: residuals become zero.  Get: the value
+ * rounded to FP32. */
 vga_status vga_sim_set_state_f32(vga_sim *s, const float *x, int32_t on_device);
 vga_status vga_sim_get_state_f32(vga_sim *s, float *x, int32_t on_device);
+
+/* Exact checkpoint of the state: the FP32 values, their residuals and the step counter, in a
+ * caller-allocated host buffer of vga_sim_state_bytes() bytes (format private to the library,
+ * valid for a simulation on the same graph with the same state_precision).  Restoring it and
+ * stepping reproduces an uninterrupted run bit for bit. */
+vga_status vga_sim_state_bytes(const vga_sim *s, int64_t *bytes);
+vga_status vga_sim_save_state(vga_sim *s, void *buf, int64_t bytes);
+vga_status vga_sim_load_state(vga_sim *s, const void *buf, int64_t bytes);
 
 /* Advances n_steps >= 0 time steps (Sec. III: transformation, then diffusion of DOM).
  * Asynchronous on the simulation's stream.  Implicit scheme: synchronises to test convergence
@@ -170,6 +185,26 @@ typedef struct vga_sim_stats {
     int64_t kernel_launches;  /* kernels launched since creation */
 } vga_sim_stats;
 vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out);
+
+/* Kernel timing.  When enabled, the library records a CUDA event pair on the simulation's stream
+ * around every kernel it launches and accumulates the elapsed times per kernel kind; reading them
+ * synchronises the stream.  Kinds: */
+#define VGA_KERNEL_FUSED_STEP 0    /* explicit pass: diffuse stored transformed DOM, transform */
+#define VGA_KERNEL_TRANSFORM 1     /* transformation-only pass (first pass of a step call) */
+#define VGA_KERNEL_DIFFUSE 2       /* diffusion-only pass (last pass of a step call) */
+#define VGA_KERNEL_TOTALS 3        /* FP64 compartment totals */
+#define VGA_KERNEL_PCG_STENCIL 4   /* implicit: initial residual and B p products */
+#define VGA_KERNEL_PCG_VECTOR 5    /* implicit: vector updates and scalar reductions */
+#define VGA_KERNEL_ADJOINT 6       /* reverse step of the discrete adjoint */
+#define VGA_KERNEL_OTHER 7         /* conversions, packing, losses */
+#define VGA_KERNEL_KINDS 8
+typedef struct vga_kernel_timing {
+    double ms[VGA_KERNEL_KINDS];        /* summed event-to-event milliseconds per kind */
+    int64_t launches[VGA_KERNEL_KINDS]; /* timed launches per kind */
+} vga_kernel_timing;
+vga_status vga_sim_enable_timing(vga_sim *s, int32_t on);
+/* Copies the accumulated timings into *out (after synchronising); reset != 0 clears them. */
+vga_status vga_sim_read_timing(vga_sim *s, vga_kernel_timing *out, int32_t reset);
 
 vga_status vga_sim_free(vga_sim *s);
 

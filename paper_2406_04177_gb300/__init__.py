@@ -31,6 +31,8 @@ VGA_SCHEME_EXPLICIT = 0
 VGA_SCHEME_IMPLICIT_PCG = 1
 VGA_TRANSFORM_SYNC = 0
 VGA_TRANSFORM_ASYNC = 1
+VGA_STATE_COMPENSATED = 0
+VGA_STATE_F32 = 1
 
 
 class VgaError(RuntimeError):
@@ -45,12 +47,21 @@ class vga_params(C.Structure):
                 ("beta", C.c_double), ("v_som", C.c_double), ("v_fom", C.c_double),
                 ("v_dom", C.c_double), ("K_dom", C.c_double), ("scheme", C.c_int32),
                 ("transform", C.c_int32), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("state_precision", C.c_int32)]
 
 
 class vga_sim_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("cg_iterations", C.c_int64),
                 ("cg_last_relres", C.c_double), ("kernel_launches", C.c_int64)]
+
+
+VGA_KERNEL_KINDS = 8
+KERNEL_KIND_NAMES = ("fused_step", "transform", "diffuse", "totals", "pcg_stencil", "pcg_vector", "adjoint",
+                     "other")
+
+
+class vga_kernel_timing(C.Structure):
+    _fields_ = [("ms", C.c_double * VGA_KERNEL_KINDS), ("launches", C.c_int64 * VGA_KERNEL_KINDS)]
 
 
 _P, _I32, _I64, _U32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
@@ -71,10 +82,15 @@ _SIGNATURES = {
     "vga_sim_get_masses": [_P, _P, _I32],
     "vga_sim_set_state_f32": [_P, _P, _I32],
     "vga_sim_get_state_f32": [_P, _P, _I32],
+    "vga_sim_state_bytes": [_P, _P],
+    "vga_sim_save_state": [_P, _P, _I64],
+    "vga_sim_load_state": [_P, _P, _I64],
     "vga_sim_step": [_P, _I64],
     "vga_sim_totals": [_P, _P],
     "vga_sim_sync": [_P],
     "vga_sim_get_stats": [_P, _P],
+    "vga_sim_enable_timing": [_P, _I32],
+    "vga_sim_read_timing": [_P, _P, _I32],
     "vga_sim_free": [_P],
 }
 _RESTYPES = {"vga_strerror": C.c_char_p, "vga_last_error": C.c_char_p, "vga_version": C.c_int32}
@@ -189,7 +205,7 @@ def make_params(p: dict) -> vga_params:
     return vga_params(D=p["D"], dt=p["dt"], rho=p["rho"], mu=p["mu"], beta=p["beta"], v_som=p["v_som"],
                       v_fom=p["v_fom"], v_dom=p["v_dom"], K_dom=p["K_dom"], scheme=int(p.get("scheme", 0)),
                       transform=int(p.get("transform", 0)), cg_rtol=float(p.get("cg_rtol", 1e-8)),
-                      cg_maxit=int(p.get("cg_maxit", 500)), reserved=0)
+                      cg_maxit=int(p.get("cg_maxit", 500)), state_precision=int(p.get("state_precision", 0)))
 
 
 def vga_sim_create(g, params: dict, stream=None) -> C.c_void_p:
@@ -242,6 +258,24 @@ def vga_sim_get_state_f32(s, out, n: int):
         _check(load_library().vga_sim_get_state_f32(s, _dev_ptr(out, "float32", 5 * n), 1), "vga_sim_get_state_f32")
 
 
+def vga_sim_state_bytes(s) -> int:
+    v = C.c_int64()
+    _check(load_library().vga_sim_state_bytes(s, C.byref(v)), "vga_sim_state_bytes")
+    return v.value
+
+
+def vga_sim_save_state(s) -> bytes:
+    nb = vga_sim_state_bytes(s)
+    buf = (C.c_char * nb)()
+    _check(load_library().vga_sim_save_state(s, buf, nb), "vga_sim_save_state")
+    return bytes(buf)
+
+
+def vga_sim_load_state(s, data: bytes):
+    buf = C.create_string_buffer(data, len(data))
+    _check(load_library().vga_sim_load_state(s, buf, len(data)), "vga_sim_load_state")
+
+
 def vga_sim_step(s, n_steps: int):
     _check(load_library().vga_sim_step(s, int(n_steps)), "vga_sim_step")
 
@@ -260,6 +294,17 @@ def vga_sim_get_stats(s) -> dict:
     st = vga_sim_stats()
     _check(load_library().vga_sim_get_stats(s, C.byref(st)), "vga_sim_get_stats")
     return {k: getattr(st, k) for k, _ in vga_sim_stats._fields_}
+
+
+def vga_sim_enable_timing(s, on: bool = True):
+    _check(load_library().vga_sim_enable_timing(s, 1 if on else 0), "vga_sim_enable_timing")
+
+
+def vga_sim_read_timing(s, reset: bool = False) -> dict:
+    """{kind name: (total ms, launches)} of the kernels timed since the last reset."""
+    kt = vga_kernel_timing()
+    _check(load_library().vga_sim_read_timing(s, C.byref(kt), 1 if reset else 0), "vga_sim_read_timing")
+    return {KERNEL_KIND_NAMES[k]: (kt.ms[k], int(kt.launches[k])) for k in range(VGA_KERNEL_KINDS)}
 
 
 def vga_sim_free(s):
@@ -343,6 +388,12 @@ class Sim:
     def step(self, n_steps: int):
         vga_sim_step(self.handle, n_steps)
 
+    def save_state(self) -> bytes:
+        return vga_sim_save_state(self.handle)
+
+    def load_state(self, data: bytes):
+        vga_sim_load_state(self.handle, data)
+
     def totals(self) -> np.ndarray:
         return vga_sim_totals(self.handle)
 
@@ -351,6 +402,12 @@ class Sim:
 
     def stats(self) -> dict:
         return vga_sim_get_stats(self.handle)
+
+    def enable_timing(self, on: bool = True):
+        vga_sim_enable_timing(self.handle, on)
+
+    def read_timing(self, reset: bool = False) -> dict:
+        return vga_sim_read_timing(self.handle, reset)
 
     def close(self):
         if self.handle:

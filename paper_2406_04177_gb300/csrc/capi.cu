@@ -55,6 +55,53 @@ vga_status graph_build_device(vga_graph *g, const uint8_t *d_img, cudaStream_t s
 vga_status graph_export_device(const vga_graph *g, int64_t *d_von, int32_t *d_nbr, cudaStream_t st);
 int totals_blocks();
 
+static cudaEvent_t pool_event(vga_sim *s) {
+    if (!s->event_pool.empty()) {
+        cudaEvent_t e = s->event_pool.back();
+        s->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+void timing_begin(vga_sim *s, int kind) {
+    if (!s->timing) return;
+    s->timing_a = pool_event(s);
+    s->timing_kind = kind;
+    if (s->timing_a) cudaEventRecord(s->timing_a, s->stream);
+}
+
+void timing_end(vga_sim *s) {
+    if (!s->timing || !s->timing_a) return;
+    cudaEvent_t b = pool_event(s);
+    if (!b) return;
+    cudaEventRecord(b, s->stream);
+    s->pending.push_back({s->timing_a, b, s->timing_kind});
+    s->timing_a = nullptr;
+}
+
+static vga_status harvest_timing(vga_sim *s) {
+    if (s->pending.empty()) return VGA_OK;
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    for (auto &p : s->pending) {
+        float ms = 0.0f;
+        VGA_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+        if (p.kind >= 0 && p.kind < VGA_KERNEL_KINDS) {
+            s->kt_ms[p.kind] += ms;
+            s->kt_count[p.kind] += 1;
+        }
+        s->event_pool.push_back(p.a);
+        s->event_pool.push_back(p.b);
+    }
+    s->pending.clear();
+    return VGA_OK;
+}
+
 static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 
 static vga_status validate_params(const vga_params *p, double max_g) {
@@ -70,6 +117,8 @@ static vga_status validate_params(const vga_params *p, double max_g) {
         return fail(VGA_ERR_INVALID_ARG, "unknown scheme");
     if (p->transform != VGA_TRANSFORM_SYNC && p->transform != VGA_TRANSFORM_ASYNC)
         return fail(VGA_ERR_INVALID_ARG, "unknown transform");
+    if (p->state_precision != VGA_STATE_COMPENSATED && p->state_precision != VGA_STATE_F32)
+        return fail(VGA_ERR_INVALID_ARG, "unknown state_precision");
     if (p->scheme == VGA_SCHEME_IMPLICIT_PCG) {
         if (!(std::isfinite(p->cg_rtol) && p->cg_rtol > 0.0)) return fail(VGA_ERR_INVALID_ARG, "cg_rtol must be > 0");
         if (p->cg_maxit < 1) return fail(VGA_ERR_INVALID_ARG, "cg_maxit must be >= 1");
@@ -222,7 +271,9 @@ vga_status vga_sim_create(const vga_graph *g, const vga_params *p, void *stream,
     sim_prepare_params(s, p);
     vga_status st = VGA_OK;
     const size_t bytes = sizeof(float) * 5 * (size_t)std::max<int64_t>(s->npad, 64);
+    const size_t lbytes = sizeof(uint16_t) * 5 * (size_t)std::max<int64_t>(s->npad, 64);
     for (int b = 0; b < 2 && st == VGA_OK; ++b) st = dmalloc((void **)&s->buf[b], bytes, "state");
+    for (int b = 0; b < 2 && st == VGA_OK; ++b) st = dmalloc((void **)&s->lbuf[b], lbytes, "state residuals");
     if (st == VGA_OK) st = dmalloc((void **)&s->partials, sizeof(double) * 5 * (size_t)totals_blocks(), "partials");
     if (st == VGA_OK) st = dmalloc((void **)&s->d_totals, sizeof(double) * 8, "totals");
     if (st == VGA_OK) {
@@ -231,7 +282,8 @@ vga_status vga_sim_create(const vga_graph *g, const vga_params *p, void *stream,
     }
     if (st == VGA_OK) st = build_chunks(g->topo(), kDefaultCap, &s->chunks, s->stream);
     for (int b = 0; b < 2 && st == VGA_OK; ++b) {
-        const cudaError_t e = cudaMemsetAsync(s->buf[b], 0, bytes, s->stream);
+        cudaError_t e = cudaMemsetAsync(s->buf[b], 0, bytes, s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->lbuf[b], 0, lbytes, s->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
     }
     if (st == VGA_OK) {
@@ -249,6 +301,12 @@ vga_status vga_sim_create(const vga_graph *g, const vga_params *p, void *stream,
 vga_status vga_sim_set_params(vga_sim *s, const vga_params *p) {
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
     VGA_TRY(validate_params(p, s->max_g));
+    if (p->state_precision != s->params.state_precision) {
+        // residuals are meaningless across a precision change: start them at zero
+        for (int b = 0; b < 2; ++b)
+            VGA_CUDA(cudaMemsetAsync(s->lbuf[b], 0, sizeof(uint16_t) * 5 * (size_t)std::max<int64_t>(s->npad, 64),
+                                     s->stream));
+    }
     return sim_prepare_params(s, p);
 }
 
@@ -339,9 +397,10 @@ vga_status vga_sim_set_state_f32(vga_sim *s, const float *x, int32_t on_device) 
     if (!s || (!x && s->n > 0)) return fail(VGA_ERR_INVALID_ARG, "sim or x is NULL");
     if (s->n == 0) return VGA_OK;
     if (on_device) return sim_pack_f32(s, const_cast<float *>(x), true);
-    for (int c = 0; c < 5; ++c)
-        VGA_CUDA(cudaMemcpyAsync(s->comp(c), x + (size_t)c * s->n, sizeof(float) * (size_t)s->n, cudaMemcpyHostToDevice,
-                                 s->stream));
+    VGA_TRY(ensure_stage(s));
+    float *st = reinterpret_cast<float *>(s->stage);
+    VGA_CUDA(cudaMemcpyAsync(st, x, sizeof(float) * 5 * (size_t)s->n, cudaMemcpyHostToDevice, s->stream));
+    VGA_TRY(sim_pack_f32(s, st, true));
     VGA_CUDA(cudaStreamSynchronize(s->stream));
     return VGA_OK;
 }
@@ -350,10 +409,72 @@ vga_status vga_sim_get_state_f32(vga_sim *s, float *x, int32_t on_device) {
     if (!s || (!x && s->n > 0)) return fail(VGA_ERR_INVALID_ARG, "sim or x is NULL");
     if (s->n == 0) return VGA_OK;
     if (on_device) return sim_pack_f32(s, x, false);
-    for (int c = 0; c < 5; ++c)
-        VGA_CUDA(cudaMemcpyAsync(x + (size_t)c * s->n, s->comp(c), sizeof(float) * (size_t)s->n, cudaMemcpyDeviceToHost,
-                                 s->stream));
+    VGA_TRY(ensure_stage(s));
+    float *st = reinterpret_cast<float *>(s->stage);
+    VGA_TRY(sim_pack_f32(s, st, false));
+    VGA_CUDA(cudaMemcpyAsync(x, st, sizeof(float) * 5 * (size_t)s->n, cudaMemcpyDeviceToHost, s->stream));
     VGA_CUDA(cudaStreamSynchronize(s->stream));
+    return VGA_OK;
+}
+
+namespace {
+struct StateHeader {
+    char magic[8];
+    int64_t n;
+    int64_t steps_done;
+    int32_t precision;
+    int32_t pad;
+};
+}  // namespace
+
+vga_status vga_sim_state_bytes(const vga_sim *s, int64_t *bytes) {
+    if (!s || !bytes) return fail(VGA_ERR_INVALID_ARG, "sim or bytes is NULL");
+    *bytes = (int64_t)sizeof(StateHeader) + 5 * s->n * (int64_t)(sizeof(float) + sizeof(uint16_t));
+    return VGA_OK;
+}
+
+vga_status vga_sim_save_state(vga_sim *s, void *buf, int64_t bytes) {
+    int64_t need = 0;
+    VGA_TRY(vga_sim_state_bytes(s, &need));
+    if (!buf || bytes < need) return fail(VGA_ERR_INVALID_ARG, "buffer NULL or smaller than vga_sim_state_bytes");
+    StateHeader hd{};
+    std::memcpy(hd.magic, "VGASTATE", 8);
+    hd.n = s->n;
+    hd.steps_done = s->steps_done;
+    hd.precision = s->params.state_precision;
+    std::memcpy(buf, &hd, sizeof(hd));
+    char *p = static_cast<char *>(buf) + sizeof(hd);
+    for (int c = 0; c < 5; ++c)
+        VGA_CUDA(cudaMemcpyAsync(p + (size_t)c * s->n * sizeof(float), s->comp(c), sizeof(float) * (size_t)s->n,
+                                 cudaMemcpyDeviceToHost, s->stream));
+    p += 5 * (size_t)s->n * sizeof(float);
+    for (int c = 0; c < 5; ++c)
+        VGA_CUDA(cudaMemcpyAsync(p + (size_t)c * s->n * sizeof(uint16_t), s->lcomp(c), sizeof(uint16_t) * (size_t)s->n,
+                                 cudaMemcpyDeviceToHost, s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    return VGA_OK;
+}
+
+vga_status vga_sim_load_state(vga_sim *s, const void *buf, int64_t bytes) {
+    int64_t need = 0;
+    VGA_TRY(vga_sim_state_bytes(s, &need));
+    if (!buf || bytes < need) return fail(VGA_ERR_INVALID_ARG, "buffer NULL or smaller than vga_sim_state_bytes");
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (std::memcmp(hd.magic, "VGASTATE", 8) != 0 || hd.n != s->n)
+        return fail(VGA_ERR_INVALID_ARG, "not a state of this graph (magic or node count differs)");
+    if (hd.precision != s->params.state_precision)
+        return fail(VGA_ERR_INVALID_ARG, "state was saved with another state_precision");
+    const char *p = static_cast<const char *>(buf) + sizeof(hd);
+    for (int c = 0; c < 5; ++c)
+        VGA_CUDA(cudaMemcpyAsync(s->comp(c), p + (size_t)c * s->n * sizeof(float), sizeof(float) * (size_t)s->n,
+                                 cudaMemcpyHostToDevice, s->stream));
+    p += 5 * (size_t)s->n * sizeof(float);
+    for (int c = 0; c < 5; ++c)
+        VGA_CUDA(cudaMemcpyAsync(s->lcomp(c), p + (size_t)c * s->n * sizeof(uint16_t), sizeof(uint16_t) * (size_t)s->n,
+                                 cudaMemcpyHostToDevice, s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    s->steps_done = hd.steps_done;
     return VGA_OK;
 }
 
@@ -384,11 +505,38 @@ vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out) {
     return VGA_OK;
 }
 
+vga_status vga_sim_enable_timing(vga_sim *s, int32_t on) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    s->timing = on != 0;
+    return VGA_OK;
+}
+
+vga_status vga_sim_read_timing(vga_sim *s, vga_kernel_timing *out, int32_t reset) {
+    if (!s || !out) return fail(VGA_ERR_INVALID_ARG, "sim or out is NULL");
+    VGA_TRY(harvest_timing(s));
+    for (int k = 0; k < VGA_KERNEL_KINDS; ++k) {
+        out->ms[k] = s->kt_ms[k];
+        out->launches[k] = s->kt_count[k];
+        if (reset) {
+            s->kt_ms[k] = 0.0;
+            s->kt_count[k] = 0;
+        }
+    }
+    return VGA_OK;
+}
+
 vga_status vga_sim_free(vga_sim *s) {
     if (!s) return VGA_OK;
     cudaStreamSynchronize(s->stream);
+    for (auto &p : s->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : s->event_pool) cudaEventDestroy(e);
     dfree(s->buf[0]);
     dfree(s->buf[1]);
+    dfree(s->lbuf[0]);
+    dfree(s->lbuf[1]);
     dfree(s->partials);
     dfree(s->d_totals);
     if (s->h_totals) cudaFreeHost(s->h_totals);

@@ -40,30 +40,33 @@ struct CgVecs {
 };
 
 // b = y2, x = b, r = b - B x = -c L_g b, t = 1 / (1 + c sum_j g_ij); partials (r.Tr, r.r, b.b)
-template <int WM>
+template <int WM, int PREC>
 __global__ void __launch_bounds__(kThreads) k_cg_init(Topo t, const int32_t *__restrict__ chunk_row, int32_t cap,
                                                       double c, BlockWeights bw, const float *__restrict__ y2,
-                                                      CgVecs v, double *__restrict__ part) {
+                                                      const uint16_t *__restrict__ y2l, CgVecs v,
+                                                      double *__restrict__ part) {
     extern __shared__ uint32_t smem[];
+    int32_t *s_nb = reinterpret_cast<int32_t *>(smem + cap);
     int64_t v0;
-    const int32_t nv = decode_chunk<WM == W_BLOCK>(t, chunk_row, cap, smem, smem + cap, smem + 2 * cap, v0);
+    const int32_t nv = decode_chunk<WM == W_BLOCK>(t, chunk_row, cap, smem, s_nb, smem + 5 * cap, v0);
     double acc[3] = {0.0, 0.0, 0.0};
     for (int32_t k = threadIdx.x; k < nv; k += blockDim.x) {
         const int64_t i = v0 + k;
-        const uint32_t sx = smem[k];
-        const int32_t x = (int32_t)(sx & 0xffffu);
-        const uint32_t fl = sx >> 16;
-        const int32_t r = (int32_t)smem[cap + k];
-        int32_t y = 0, z = 0;
+        const uint32_t info = smem[k];
+        const uint32_t fl = info >> 16;
+        int32_t x = 0, y = 0, z = 0;
         if (WM == W_BLOCK) {
-            y = (int32_t)(smem[2 * cap + k] & 0xffffu);
-            z = (int32_t)(smem[2 * cap + k] >> 16);
+            x = (int32_t)(info & 0xffffu);
+            y = (int32_t)(smem[5 * cap + k] & 0xffffu);
+            z = (int32_t)(smem[5 * cap + k] >> 16);
         }
-        const double bi = (double)__ldg(y2 + i);
+        const double bi = (double)__ldg(y2 + i) + (PREC == P_COMP ? (double)bf16_bits_to_float(__ldg(y2l + i)) : 0.0);
         double lb = 0.0, deg = 0.0;
-        for_each_neighbour(t, i, x, r, fl, [&](int slot, int64_t j) {
+        for_each_neighbour(i, k, fl, s_nb, cap, [&](int slot, int64_t j) {
             const double g = (WM == W_UNIT) ? 1.0 : (double)block_theta(bw, slot, x, y, z);
-            lb += g * (bi - (double)__ldg(y2 + j));
+            const double bj =
+                (double)__ldg(y2 + j) + (PREC == P_COMP ? (double)bf16_bits_to_float(__ldg(y2l + j)) : 0.0);
+            lb += g * (bi - bj);
             deg += g;
         });
         const double ri = -c * lb;
@@ -88,23 +91,23 @@ __global__ void __launch_bounds__(kThreads) k_spmv(Topo t, const int32_t *__rest
                                                    const CgScalars *__restrict__ sc) {
     if (sc->done) return;
     extern __shared__ uint32_t smem[];
+    int32_t *s_nb = reinterpret_cast<int32_t *>(smem + cap);
     int64_t v0;
-    const int32_t nv = decode_chunk<WM == W_BLOCK>(t, chunk_row, cap, smem, smem + cap, smem + 2 * cap, v0);
+    const int32_t nv = decode_chunk<WM == W_BLOCK>(t, chunk_row, cap, smem, s_nb, smem + 5 * cap, v0);
     double acc[1] = {0.0};
     for (int32_t k = threadIdx.x; k < nv; k += blockDim.x) {
         const int64_t i = v0 + k;
-        const uint32_t sx = smem[k];
-        const int32_t x = (int32_t)(sx & 0xffffu);
-        const uint32_t fl = sx >> 16;
-        const int32_t r = (int32_t)smem[cap + k];
-        int32_t y = 0, z = 0;
+        const uint32_t info = smem[k];
+        const uint32_t fl = info >> 16;
+        int32_t x = 0, y = 0, z = 0;
         if (WM == W_BLOCK) {
-            y = (int32_t)(smem[2 * cap + k] & 0xffffu);
-            z = (int32_t)(smem[2 * cap + k] >> 16);
+            x = (int32_t)(info & 0xffffu);
+            y = (int32_t)(smem[5 * cap + k] & 0xffffu);
+            z = (int32_t)(smem[5 * cap + k] >> 16);
         }
         const double pi = p[i];
         double lp = 0.0;
-        for_each_neighbour(t, i, x, r, fl, [&](int slot, int64_t j) {
+        for_each_neighbour(i, k, fl, s_nb, cap, [&](int slot, int64_t j) {
             const double g = (WM == W_UNIT) ? 1.0 : (double)block_theta(bw, slot, x, y, z);
             lp += g * (pi - p[j]);
         });
@@ -199,22 +202,30 @@ __global__ void __launch_bounds__(kThreads) k_scalar_b(const double *__restrict_
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_cg_out(int64_t n, const double *__restrict__ x, float *__restrict__ out) {
+__global__ void __launch_bounds__(kThreads) k_cg_out(int64_t n, const double *__restrict__ x, float *__restrict__ out,
+                                                     uint16_t *__restrict__ outl, int comp) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)x[i];
+    if (i >= n) return;
+    const double v = x[i];
+    const float h = (float)v;
+    out[i] = h;
+    if (comp) outl[i] = float_to_bf16_bits((float)(v - (double)h));
 }
 
 inline unsigned grid_for(int64_t count, int threads) { return (unsigned)((count + threads - 1) / threads); }
 
-template <int WM>
+template <int WM, int PREC>
 vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgScalars *sc) {
     const Topo t = s->g->topo();
     const double c = s->params.D * s->params.dt;
-    const size_t smem = sizeof(uint32_t) * (size_t)s->chunks.cap * (WM == W_BLOCK ? 3 : 2);
+    const size_t smem = sizeof(uint32_t) * (size_t)s->chunks.cap * decode_words(WM == W_BLOCK);
     const int G = s->chunks.count;
     const int ew = (int)std::min<int64_t>(kEwBlocks, (int64_t)grid_for(s->n, kThreads));
     cudaStream_t st = s->stream;
-    k_cg_init<WM><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, c, s->bw, s->comp(1), v, part_chunk);
+    timing_begin(s, VGA_KERNEL_PCG_STENCIL);
+    k_cg_init<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, c, s->bw, s->comp(1),
+                                                   s->lcomp(1), v, part_chunk);
+    timing_end(s);
     k_scalar_init<<<1, kThreads, 0, st>>>(part_chunk, G, sc, s->params.cg_rtol, s->params.cg_maxit);
     VGA_CHECK_LAUNCH();
     s->launches += 2;
@@ -222,11 +233,17 @@ vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgSc
     bool first = true;
     for (;;) {
         for (int b = 0; b < kBatch; ++b) {
+            timing_begin(s, VGA_KERNEL_PCG_VECTOR);
             k_update_p<<<ew, kThreads, 0, st>>>(s->n, v, sc, first ? 1 : 0);
+            timing_end(s);
+            timing_begin(s, VGA_KERNEL_PCG_STENCIL);
             k_spmv<WM><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, c, s->bw, v.p, v.q, part_chunk, sc);
+            timing_end(s);
+            timing_begin(s, VGA_KERNEL_PCG_VECTOR);
             k_scalar_a<<<1, kThreads, 0, st>>>(part_chunk, G, sc);
             k_update_xr<<<ew, kThreads, 0, st>>>(s->n, v, sc, part_ew);
             k_scalar_b<<<1, kThreads, 0, st>>>(part_ew, ew, sc);
+            timing_end(s);
             first = false;
         }
         VGA_CHECK_LAUNCH();
@@ -235,7 +252,7 @@ vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgSc
         VGA_CUDA(cudaStreamSynchronize(st));
         if (h->done) break;
     }
-    k_cg_out<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, v.x, s->spare(1));
+    k_cg_out<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, v.x, s->spare(1), s->lspare(1), PREC == P_COMP);
     VGA_CHECK_LAUNCH();
     ++s->launches;
     s->cur[1] ^= 1;
@@ -274,8 +291,12 @@ vga_status sim_step_implicit(vga_sim *s, int64_t n_steps) {
     vga_status worst = VGA_OK;
     for (int64_t k = 0; k < n_steps; ++k) {
         VGA_TRY(sim_transform_pass(s));
-        const vga_status st = (s->wmode == W_BLOCK) ? solve<W_BLOCK>(s, v, part_chunk, part_ew, sc)
-                                                    : solve<W_UNIT>(s, v, part_chunk, part_ew, sc);
+        const bool comp = s->precision() == P_COMP;
+        vga_status st;
+        if (s->wmode == W_BLOCK)
+            st = comp ? solve<W_BLOCK, P_COMP>(s, v, part_chunk, part_ew, sc) : solve<W_BLOCK, P_F32>(s, v, part_chunk, part_ew, sc);
+        else
+            st = comp ? solve<W_UNIT, P_COMP>(s, v, part_chunk, part_ew, sc) : solve<W_UNIT, P_F32>(s, v, part_chunk, part_ew, sc);
         if (st == VGA_ERR_NOT_CONVERGED) {
             worst = st;
         } else if (st != VGA_OK) {

@@ -1,9 +1,14 @@
 // Chunk decoding and neighbour walk shared by every stencil kernel.
 //
-// A block owns the chunk of nodes [v0, v0 + nv).  decode_chunk() scans the row-bitmask words of the
-// rows the chunk spans and writes, for each of its nodes, x | (boundary flags << 16) and the image
-// row into shared memory (and y | z << 16 when the caller needs block coordinates).  Boundary flag
-// bits: 1 = y > 0, 2 = y < ny-1, 4 = z > 0, 8 = z < nz-1.
+// A block owns the chunk of nodes [v0, v0 + nv).  decode_chunk() visits the row-bitmask words of
+// the image rows the chunk spans.  For one word (32 voxels of one row) it loads the words at the
+// same x in the rows above/below (y +- 1) and in the neighbouring planes (z +- 1) together with
+// their prefix entries; the index of every neighbour of every node in the word then follows from a
+// popcount.  Per node it writes to shared memory:
+//   s_info[k]        x | (neighbour-existence bits << 16), bit order -x, +x, -y, +y, -z, +z
+//   s_nb[d*cap + k]  node index of the -y, +y, -z, +z neighbour (d = 0..3) when it exists
+//   s_yz[k]          y | z << 16 (only when the caller needs block coordinates)
+// so the stencil loop itself issues only independent loads of neighbour values.
 #pragma once
 
 #include "physics.cuh"
@@ -11,33 +16,57 @@
 
 namespace vga {
 
+// Shared-memory words per node used by decode_chunk.
+__host__ __device__ constexpr int decode_words(bool need_yz) { return need_yz ? 6 : 5; }
+
 template <bool NEED_YZ>
 __device__ __forceinline__ int32_t decode_chunk(const Topo &t, const int32_t *__restrict__ chunk_row, int32_t cap,
-                                                uint32_t *s_x, uint32_t *s_row, uint32_t *s_yz, int64_t &v0_out) {
+                                                uint32_t *s_info, int32_t *s_nb, uint32_t *s_yz, int64_t &v0_out) {
     const int64_t v0 = (int64_t)blockIdx.x * cap;
     const int64_t v1 = min(v0 + (int64_t)cap, t.n);
     const int32_t nv = (int32_t)(v1 - v0);
     const int32_t r0 = chunk_row[blockIdx.x], r1 = chunk_row[blockIdx.x + 1];
-    const int32_t nw = (r1 - r0 + 1) * t.W;
+    const int32_t W = t.W;
+    const int32_t nw = (r1 - r0 + 1) * W;
     for (int32_t q = threadIdx.x; q < nw; q += blockDim.x) {
-        const int32_t rr = q / t.W;
-        const int32_t w = q - rr * t.W;
+        const int32_t rr = q / W;
+        const int32_t w = q - rr * W;
         const int32_t r = r0 + rr;
-        const int32_t wq = r * t.W + w;
-        uint32_t m = __ldg(t.mask + wq);
+        const int32_t wq = r * W + w;
+        const uint32_t m = __ldg(t.mask + wq);
         if (!m) continue;
         const int64_t p0 = __ldg(t.pre + wq);
         if (p0 >= v1 || p0 + __popc(m) <= v0) continue;
         const int32_t z = r / t.ny, y = r - z * t.ny;
-        const uint32_t fl = (uint32_t)(y > 0) | ((uint32_t)(y < t.ny - 1) << 1) | ((uint32_t)(z > 0) << 2) |
-                            ((uint32_t)(z < t.nz - 1) << 3);
+        // neighbour words and their prefix entries (0 where the row does not exist)
+        uint32_t mn[4] = {0u, 0u, 0u, 0u};
+        int32_t pn[4] = {0, 0, 0, 0};
+        if (y > 0) { mn[0] = __ldg(t.mask + wq - W); pn[0] = __ldg(t.pre + wq - W); }
+        if (y < t.ny - 1) { mn[1] = __ldg(t.mask + wq + W); pn[1] = __ldg(t.pre + wq + W); }
+        const int32_t plane = t.ny * W;
+        if (z > 0) { mn[2] = __ldg(t.mask + wq - plane); pn[2] = __ldg(t.pre + wq - plane); }
+        if (z < t.nz - 1) { mn[3] = __ldg(t.mask + wq + plane); pn[3] = __ldg(t.pre + wq + plane); }
+        // x neighbours: bit b of mleft/mright tells whether voxel x-1 / x+1 is a node
+        const uint32_t prev31 = (w > 0) ? (__ldg(t.mask + wq - 1) >> 31) : 0u;
+        const uint32_t next0 = (w < W - 1) ? (__ldg(t.mask + wq + 1) & 1u) : 0u;
+        const uint32_t mleft = (m << 1) | prev31;
+        const uint32_t mright = (m >> 1) | (next0 << 31);
         int64_t idx = p0 - v0;
-        while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
+        uint32_t mm = m;
+        while (mm) {
+            const int b = __ffs(mm) - 1;
+            mm &= mm - 1;
             if (idx >= 0 && idx < nv) {
-                s_x[idx] = (uint32_t)(32 * w + b) | (fl << 16);
-                s_row[idx] = (uint32_t)r;
+                const uint32_t bit = 1u << b, below = bit - 1u;
+                uint32_t fl = ((mleft >> b) & 1u) | (((mright >> b) & 1u) << 1);
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    if (mn[d] & bit) {
+                        fl |= 4u << d;
+                        s_nb[d * cap + idx] = pn[d] + __popc(mn[d] & below);
+                    }
+                }
+                s_info[idx] = (uint32_t)(32 * w + b) | (fl << 16);
                 if (NEED_YZ) s_yz[idx] = (uint32_t)y | ((uint32_t)z << 16);
             }
             ++idx;
@@ -48,28 +77,17 @@ __device__ __forceinline__ int32_t decode_chunk(const Topo &t, const int32_t *__
     return nv;
 }
 
-// Calls f(slot, j) for every existing neighbour j of node i (at x in image row r, boundary flags
-// fl), in slot order -x, +x, -y, +y, -z, +z.
+// Calls f(slot, j) for every existing neighbour j of the k-th node of the chunk (global index i),
+// in slot order -x, +x, -y, +y, -z, +z.
 template <class F>
-__device__ __forceinline__ void for_each_neighbour(const Topo &t, int64_t i, int32_t x, int32_t r, uint32_t fl, F &&f) {
-    if (x > 0 && is_node(t, r, x - 1)) f(0, i - 1);
-    if (x < t.nx - 1 && is_node(t, r, x + 1)) f(1, i + 1);
-    if (fl & 1u) {
-        const int64_t j = node_in_row(t, r - 1, x);
-        if (j >= 0) f(2, j);
-    }
-    if (fl & 2u) {
-        const int64_t j = node_in_row(t, r + 1, x);
-        if (j >= 0) f(3, j);
-    }
-    if (fl & 4u) {
-        const int64_t j = node_in_row(t, r - t.ny, x);
-        if (j >= 0) f(4, j);
-    }
-    if (fl & 8u) {
-        const int64_t j = node_in_row(t, r + t.ny, x);
-        if (j >= 0) f(5, j);
-    }
+__device__ __forceinline__ void for_each_neighbour(int64_t i, int32_t k, uint32_t fl, const int32_t *s_nb, int32_t cap,
+                                                   F &&f) {
+    if (fl & 1u) f(0, i - 1);
+    if (fl & 2u) f(1, i + 1);
+    if (fl & 4u) f(2, (int64_t)s_nb[k]);
+    if (fl & 8u) f(3, (int64_t)s_nb[cap + k]);
+    if (fl & 16u) f(4, (int64_t)s_nb[2 * cap + k]);
+    if (fl & 32u) f(5, (int64_t)s_nb[3 * cap + k]);
 }
 
 // Conductance of the edge leaving a node at (x, y, z) through `slot` under block weights: theta of

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/vga.h"
 
@@ -72,8 +73,10 @@ struct StepParams {
 
 // Input and output compartment arrays of one pass over the state.
 struct StateIO {
-    const float *in[5];
+    const float *in[5];      // FP32 values
     float *out[5];
+    const uint16_t *lin[5];  // BF16 residuals (compensated precision only)
+    uint16_t *lout[5];
 };
 
 // Edge-weight modes of the stencil.
@@ -134,8 +137,9 @@ struct vga_sim {
     cudaStream_t stream = nullptr;
     int64_t n = 0;
     int64_t npad = 0;         // row stride of the state arrays (multiple of 64 floats)
-    float *buf[2] = {nullptr, nullptr};  // two state buffers of 5*npad floats
-    int cur[5] = {0, 0, 0, 0, 0};        // which buffer holds compartment c
+    float *buf[2] = {nullptr, nullptr};     // two state buffers of 5*npad FP32 values
+    uint16_t *lbuf[2] = {nullptr, nullptr}; // their BF16 residuals (compensated precision)
+    int cur[5] = {0, 0, 0, 0, 0};           // which buffer holds compartment c
     vga::Chunks chunks;
     // conductances
     int wmode = vga::W_UNIT;
@@ -159,12 +163,30 @@ struct vga_sim {
     int64_t cg_iterations = 0;
     double cg_last_relres = 0.0;
     int64_t launches = 0;
+    // optional per-kernel CUDA-event timing (vga_sim_enable_timing)
+    bool timing = false;
+    struct Pending {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double kt_ms[VGA_KERNEL_KINDS] = {};
+    int64_t kt_count[VGA_KERNEL_KINDS] = {};
+    cudaEvent_t timing_a = nullptr;
+    int timing_kind = -1;
 
     float *comp(int c) { return buf[cur[c]] + (size_t)c * npad; }
     float *spare(int c) { return buf[1 - cur[c]] + (size_t)c * npad; }
+    uint16_t *lcomp(int c) { return lbuf[cur[c]] + (size_t)c * npad; }
+    uint16_t *lspare(int c) { return lbuf[1 - cur[c]] + (size_t)c * npad; }
+    int precision() const { return params.state_precision; }
 };
 
 namespace vga {
+// capi.cu: event timing around one kernel launch (no-op unless timing is enabled)
+void timing_begin(vga_sim *s, int kind);
+void timing_end(vga_sim *s);
 // step.cu
 vga_status sim_prepare_params(vga_sim *s, const vga_params *p);
 vga_status sim_step_explicit(vga_sim *s, int64_t n_steps);
@@ -173,6 +195,8 @@ vga_status sim_convert_in(vga_sim *s, const double *d_x);    // device FP64 (5 x
 vga_status sim_convert_out(vga_sim *s, double *d_x);         // state -> device FP64 (5 x n)
 vga_status sim_pack_f32(vga_sim *s, float *d_x, bool to_state);
 vga_status sim_transform_pass(vga_sim *s);  // Y = T(X) for every node, all compartments swapped
+StateIO state_io(vga_sim *s);          // current buffers in, spare buffers out
+StateIO state_io_inplace(vga_sim *s);  // current buffers in and out
 // pcg.cu
 vga_status sim_step_implicit(vga_sim *s, int64_t n_steps);
 }  // namespace vga
