@@ -186,6 +186,39 @@ typedef struct vga_sim_stats {
 } vga_sim_stats;
 vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out);
 
+/* ============================================================================================
+ * Discrete adjoint of the explicit scheme with synchronous transformation (compensated state).
+ * The reverse of one step X^{k+1} = (y1, Q_g y2, y3, y4, y5), y = T(X^k), Q_g = I - D dt L_g:
+ *   mu = (lam1, Q_g lam2, lam3, lam4, lam5), dL/dX^k = J_T(X^k)^T mu,
+ * with FP64 gradients with respect to D, the seven rate constants, and the block conductances
+ * theta (the voxel form of the Sec. V.A conductances; the one-step closed forms of Sec. V.A are the
+ * special case of a single diffusion step).
+ * ============================================================================================ */
+
+/* Advances n_steps from the current state X^0, storing a checkpoint every ckpt_every steps; the
+ * simulation ends at X^N exactly as vga_sim_step would leave it.  Device memory: one state per
+ * checkpoint (30 bytes per node) plus ckpt_every recorded steps (24 bytes per node each).
+ * Errors: VGA_ERR_UNSUPPORTED unless scheme = explicit, transform = sync and state_precision =
+ * compensated; VGA_ERR_INVALID_ARG for n_steps < 0 or ckpt_every < 1. */
+vga_status vga_adjoint_forward(vga_sim *s, int64_t n_steps, int32_t ckpt_every);
+
+/* Back-propagates dL_dXN (5 x n FP64, host or device as on_device says) through the steps of the
+ * last vga_adjoint_forward.  Outputs: dL_dX0 (5 x n FP64 in the same memory space, or NULL);
+ * grad_params[8] (host) = dL/d(D, rho, mu, beta, v_som, v_fom, v_dom, K_dom); grad_theta (host,
+ * n_theta doubles in the layout of vga_sim_set_block_conductances, or NULL; zero without block
+ * conductances).  The state stays at X^N.  Errors: VGA_ERR_INVALID_ARG if no forward pass was run
+ * or the parameters or conductances changed since. */
+vga_status vga_adjoint_backward(vga_sim *s, const double *dL_dXN, int32_t on_device, double *dL_dX0,
+                                double *grad_params, double *grad_theta);
+
+/* Block-mass objective: the image is cut into cubes of block_side voxels; for every compartment c
+ * in comp_mask (bit c) and block b, M_cb = sum of x^c over the nodes of b.
+ * L = sum_cb (M_cb - target_cb)^2.  target (host): one row of nblocks values per selected
+ * compartment, in increasing c, blocks in C order (nbz, nby, nbx).  Outputs: *loss (host),
+ * block_mass (host, same layout as target, or NULL), dL_dX (device, 5 x n FP64, or NULL). */
+vga_status vga_loss_block_mass(vga_sim *s, int32_t block_side, uint32_t comp_mask, const double *target,
+                               double *loss, double *block_mass, double *dL_dX);
+
 /* Kernel timing.  When enabled, the library records a CUDA event pair on the simulation's stream
  * around every kernel it launches and accumulates the elapsed times per kernel kind; reading them
  * synchronises the stream.  Kinds: */

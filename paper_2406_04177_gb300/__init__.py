@@ -89,6 +89,9 @@ _SIGNATURES = {
     "vga_sim_totals": [_P, _P],
     "vga_sim_sync": [_P],
     "vga_sim_get_stats": [_P, _P],
+    "vga_adjoint_forward": [_P, _I64, _I32],
+    "vga_adjoint_backward": [_P, _P, _I32, _P, _P, _P],
+    "vga_loss_block_mass": [_P, _I32, _U32, _P, _P, _P, _P],
     "vga_sim_enable_timing": [_P, _I32],
     "vga_sim_read_timing": [_P, _P, _I32],
     "vga_sim_free": [_P],
@@ -296,6 +299,45 @@ def vga_sim_get_stats(s) -> dict:
     return {k: getattr(st, k) for k, _ in vga_sim_stats._fields_}
 
 
+GRAD_NAMES = ("D", "rho", "mu", "beta", "v_som", "v_fom", "v_dom", "K_dom")
+
+
+def vga_adjoint_forward(s, n_steps: int, ckpt_every: int):
+    _check(load_library().vga_adjoint_forward(s, int(n_steps), int(ckpt_every)), "vga_adjoint_forward")
+
+
+def vga_adjoint_backward(s, dL_dXN, n: int, dL_dX0=None, n_theta: int = 0):
+    """Returns (grad dict, grad_theta numpy array or None); fills dL_dX0 if given (same memory
+    space as dL_dXN)."""
+    grad = np.zeros(8, dtype=np.float64)
+    gth = np.zeros(max(n_theta, 1), dtype=np.float64) if n_theta > 0 else None
+    if isinstance(dL_dXN, np.ndarray):
+        src = _host_ptr(dL_dXN, np.float64, 5 * n)
+        dst = None if dL_dX0 is None else _host_ptr(dL_dX0, np.float64, 5 * n)
+        dev = 0
+    else:
+        src = _dev_ptr(dL_dXN, "float64", 5 * n)
+        dst = None if dL_dX0 is None else _dev_ptr(dL_dX0, "float64", 5 * n)
+        dev = 1
+    _check(load_library().vga_adjoint_backward(s, src, dev, dst, grad.ctypes.data_as(C.c_void_p),
+                                               None if gth is None else gth.ctypes.data_as(C.c_void_p)),
+           "vga_adjoint_backward")
+    return dict(zip(GRAD_NAMES, grad.tolist())), gth
+
+
+def vga_loss_block_mass(s, block_side: int, comp_mask: int, target: np.ndarray, n: int, dL_dX=None,
+                        want_mass: bool = False):
+    """Returns (loss, block masses or None); writes dL/dX into the CUDA tensor dL_dX if given."""
+    target = np.ascontiguousarray(target, dtype=np.float64)
+    loss = C.c_double()
+    mass = np.empty_like(target) if want_mass else None
+    _check(load_library().vga_loss_block_mass(s, int(block_side), int(comp_mask), _host_ptr(target, np.float64),
+                                              C.byref(loss), None if mass is None else _host_ptr(mass, np.float64),
+                                              None if dL_dX is None else _dev_ptr(dL_dX, "float64", 5 * n)),
+           "vga_loss_block_mass")
+    return loss.value, mass
+
+
 def vga_sim_enable_timing(s, on: bool = True):
     _check(load_library().vga_sim_enable_timing(s, 1 if on else 0), "vga_sim_enable_timing")
 
@@ -402,6 +444,15 @@ class Sim:
 
     def stats(self) -> dict:
         return vga_sim_get_stats(self.handle)
+
+    def adjoint_forward(self, n_steps: int, ckpt_every: int = 100):
+        vga_adjoint_forward(self.handle, n_steps, ckpt_every)
+
+    def adjoint_backward(self, dL_dXN, dL_dX0=None, n_theta: int = 0):
+        return vga_adjoint_backward(self.handle, dL_dXN, self.n, dL_dX0, n_theta)
+
+    def loss_block_mass(self, block_side: int, comp_mask: int, target, dL_dX=None, want_mass: bool = False):
+        return vga_loss_block_mass(self.handle, block_side, comp_mask, target, self.n, dL_dX, want_mass)
 
     def enable_timing(self, on: bool = True):
         vga_sim_enable_timing(self.handle, on)

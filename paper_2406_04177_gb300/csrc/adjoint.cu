@@ -1,0 +1,529 @@
+// Discrete adjoint of the explicit synchronous time step, with checkpointing, and the block-mass
+// objective used to fit block conductances.
+//
+// Forward step k: Y = T(X^k) voxel by voxel, X^{k+1} = (y1, Q_g y2, y3, y4, y5) with
+// Q_g = I - D dt L_g (Scheme 1 with edge conductances, Sec. II.B.3a and the weighted flux of
+// Sec. V.A).  Q_g is symmetric, so the reverse of step k is
+//     mu = (lam1, Q_g lam2, lam3, lam4, lam5)             (lam = dL/dX^{k+1})
+//     dL/dX^k = J_T(X^k)^T mu                              (transform_sync_reverse)
+// with parameter gradients
+//     dL/dD        += -dt sum_i lam2_i (L_g y2)_i
+//     dL/dtheta_f  += -D dt sum_{edges e crossing face f} (y2_i - y2_j)(lam2_i - lam2_j)
+//     dL/drates    += w . df/drate                         (transform_sync_reverse)
+// This is the multi-step, transformation-coupled form of the closed-form gradients of Sec. V.A.
+//
+// Memory: the forward stores the state every `ckpt` steps; each segment is recomputed once from
+// its checkpoint, recording X^k (FP32) and the transformed DOM y2^k, and then reversed step by
+// step.  The adjoint state is carried like the forward state (FP32 value + BF16 residual) and every
+// parameter gradient is accumulated in FP64 (per-block partials, FP64 atomics for the faces).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "physics.cuh"
+#include "stencil.cuh"
+#include "vga_internal.cuh"
+
+namespace vga {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPar = GR_COUNT + 1;  // per-block partial slots: 7 rate slots + D
+
+struct Rec {
+    float *x;   // 5 x npad FP32 values of X^k (recording target, or NULL)
+    float *y2;  // npad transformed DOM of step k (recording target)
+};
+
+// Transformation-only pass that also records y2 = T(X)_2.
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_transform_rec(int64_t n, StepParams p, StateIO io, float *rec_y2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V x[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) x[c] = vload<PREC>(io.in[c], io.lin[c], i);
+    transform_sync<PREC>(x[0], x[1], x[2], x[3], x[4], p);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) vstore<PREC>(io.out[c], io.lout[c], i, x[c]);
+    rec_y2[i] = __fadd_rn(x[1].h, x[1].l);
+}
+
+// Fused pass (diffuse, transform) that records X^{k} (after diffusion, before the transformation)
+// and y2^k.  Same arithmetic as the forward fused pass, so the recomputed trajectory is identical.
+template <int WM, int PREC>
+__global__ void __launch_bounds__(kThreads) k_fused_rec(Topo t, const int32_t *__restrict__ chunk_row, int32_t cap,
+                                                        StepParams p, BlockWeights bw, StateIO io, int64_t npad,
+                                                        Rec rec) {
+    extern __shared__ uint32_t smem[];
+    int32_t *s_nb = reinterpret_cast<int32_t *>(smem + cap);
+    int64_t v0;
+    const int32_t nv = decode_chunk<WM == W_BLOCK>(t, chunk_row, cap, smem, s_nb, smem + 5 * cap, v0);
+    const float *__restrict__ Y2 = io.in[1];
+    for (int32_t k = threadIdx.x; k < nv; k += blockDim.x) {
+        const int64_t i = v0 + k;
+        const uint32_t info = smem[k];
+        const uint32_t fl = info >> 16;
+        int32_t x = 0, y = 0, z = 0;
+        if (WM == W_BLOCK) {
+            x = (int32_t)(info & 0xffffu);
+            y = (int32_t)(smem[5 * cap + k] & 0xffffu);
+            z = (int32_t)(smem[5 * cap + k] >> 16);
+        }
+        V x2 = vload<PREC>(Y2, io.lin[1], i);
+        const float yi = x2.h;
+        float acc = 0.0f;
+        for_each_neighbour(i, k, fl, s_nb, cap, [&](int slot, int64_t j) {
+            const float d = __fsub_rn(yi, __ldg(Y2 + j));
+            if (WM == W_UNIT) acc = __fadd_rn(acc, d);
+            else acc = __fmaf_rn(block_theta(bw, slot, x, y, z), d, acc);
+        });
+        vadd<PREC>(x2, __fmul_rn(-p.c, acc));
+        vround<PREC>(x2);
+        V x1 = vload<PREC>(io.in[0], io.lin[0], i), x3 = vload<PREC>(io.in[2], io.lin[2], i),
+          x4 = vload<PREC>(io.in[3], io.lin[3], i), x5 = vload<PREC>(io.in[4], io.lin[4], i);
+        rec.x[i] = __fadd_rn(x1.h, x1.l);
+        rec.x[npad + i] = __fadd_rn(x2.h, x2.l);
+        rec.x[2 * npad + i] = __fadd_rn(x3.h, x3.l);
+        rec.x[3 * npad + i] = __fadd_rn(x4.h, x4.l);
+        rec.x[4 * npad + i] = __fadd_rn(x5.h, x5.l);
+        transform_sync<PREC>(x1, x2, x3, x4, x5, p);
+        vstore<PREC>(io.out[0], io.lout[0], i, x1);
+        vstore<PREC>(io.out[1], io.lout[1], i, x2);
+        vstore<PREC>(io.out[2], io.lout[2], i, x3);
+        vstore<PREC>(io.out[3], io.lout[3], i, x4);
+        vstore<PREC>(io.out[4], io.lout[4], i, x5);
+        rec.y2[i] = __fadd_rn(x2.h, x2.l);
+    }
+}
+
+// One reverse step.  lam (io.in) = dL/dX^{k+1}; writes dL/dX^k (io.out).  xk: recorded X^k values,
+// y2k: recorded transformed DOM of step k.
+template <int WM, int PREC>
+__global__ void __launch_bounds__(kThreads) k_adjoint_step(Topo t, const int32_t *__restrict__ chunk_row, int32_t cap,
+                                                           StepParams p, BlockWeights bw, StateIO io, int64_t npad,
+                                                           const float *__restrict__ xk, const float *__restrict__ y2k,
+                                                           double *__restrict__ gpart, double *__restrict__ gtheta) {
+    extern __shared__ uint32_t smem[];
+    int32_t *s_nb = reinterpret_cast<int32_t *>(smem + cap);
+    int64_t v0;
+    const int32_t nv = decode_chunk<WM == W_BLOCK>(t, chunk_row, cap, smem, s_nb, smem + 5 * cap, v0);
+    const float *__restrict__ L2 = io.in[1];
+    double acc[kPar];
+#pragma unroll
+    for (int q = 0; q < kPar; ++q) acc[q] = 0.0;
+    const double mc = -(double)p.c;
+    for (int32_t k = threadIdx.x; k < nv; k += blockDim.x) {
+        const int64_t i = v0 + k;
+        const uint32_t info = smem[k];
+        const uint32_t fl = info >> 16;
+        int32_t x = 0, y = 0, z = 0;
+        if (WM == W_BLOCK) {
+            x = (int32_t)(info & 0xffffu);
+            y = (int32_t)(smem[5 * cap + k] & 0xffffu);
+            z = (int32_t)(smem[5 * cap + k] >> 16);
+        }
+        V mu[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) mu[c] = vload<PREC>(io.in[c], io.lin[c], i);
+        const float li = mu[1].h;
+        const float yi = __ldg(y2k + i);
+        float lsum = 0.0f, ysum = 0.0f;
+        for_each_neighbour(i, k, fl, s_nb, cap, [&](int slot, int64_t j) {
+            const float g = (WM == W_UNIT) ? 1.0f : block_theta(bw, slot, x, y, z);
+            const float dl = __fsub_rn(li, __ldg(L2 + j));
+            const float dy = __fsub_rn(yi, __ldg(y2k + j));
+            lsum = __fmaf_rn(g, dl, lsum);
+            ysum = __fmaf_rn(g, dy, ysum);
+            if (WM == W_BLOCK && (slot & 1)) {  // +x, +y, +z: each edge once
+                const int64_t f = block_face(bw, slot, x, y, z);
+                if (f >= 0) atomicAdd(gtheta + f, mc * (double)dy * (double)dl);
+            }
+        });
+        acc[GR_COUNT] -= (double)li * (double)ysum;  // times dt on the host: dL/dD
+        vadd<PREC>(mu[1], __fmul_rn(-p.c, lsum));    // mu2 = Q_g lam2
+        float xs[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) xs[c] = __ldg(xk + c * npad + i);
+        float gr[GR_COUNT];
+#pragma unroll
+        for (int q = 0; q < GR_COUNT; ++q) gr[q] = 0.0f;
+        V lam[5];
+        transform_sync_reverse<PREC>(xs, mu, lam, gr, p);
+#pragma unroll
+        for (int q = 0; q < GR_COUNT; ++q) acc[q] += (double)gr[q];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) vstore<PREC>(io.out[c], io.lout[c], i, lam[c]);
+    }
+    __shared__ double out[kPar];
+    block_sum_store<kPar>(acc, out);
+    if (threadIdx.x < kPar) gpart[(int64_t)blockIdx.x * kPar + threadIdx.x] += out[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kThreads) k_reduce_gpart(const double *__restrict__ gpart, int G,
+                                                           double *__restrict__ out) {
+    double s[kPar];
+#pragma unroll
+    for (int q = 0; q < kPar; ++q) s[q] = 0.0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x)
+#pragma unroll
+        for (int q = 0; q < kPar; ++q) s[q] += gpart[(int64_t)b * kPar + q];
+    __shared__ double o[kPar];
+    block_sum_store<kPar>(s, o);
+    if (threadIdx.x < kPar) out[threadIdx.x] = o[threadIdx.x];
+}
+
+// ---- block-mass objective ----------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_block_mass(Topo t, const int32_t *__restrict__ chunk_row, int32_t cap,
+                                                         BlockWeights bw, StateIO io, int comp_mask,
+                                                         double *__restrict__ mass, int64_t nblocks) {
+    extern __shared__ uint32_t smem[];
+    int32_t *s_nb = reinterpret_cast<int32_t *>(smem + cap);
+    int64_t v0;
+    const int32_t nv = decode_chunk<true>(t, chunk_row, cap, smem, s_nb, smem + 5 * cap, v0);
+    for (int32_t k = threadIdx.x; k < nv; k += blockDim.x) {
+        const int64_t i = v0 + k;
+        const int32_t x = (int32_t)(smem[k] & 0xffffu);
+        const int32_t y = (int32_t)(smem[5 * cap + k] & 0xffffu), z = (int32_t)(smem[5 * cap + k] >> 16);
+        const int64_t b = ((int64_t)(z / bw.bs) * bw.nby + y / bw.bs) * bw.nbx + x / bw.bs;
+        int slot = 0;
+        for (int c = 0; c < 5; ++c) {
+            if (!((comp_mask >> c) & 1)) continue;
+            const double v = (double)io.in[c][i] + (double)bf16_bits_to_float(io.lin[c][i]);
+            atomicAdd(mass + slot * nblocks + b, v);
+            ++slot;
+        }
+    }
+}
+
+// r = mass - target over all selected blocks; block partial sums of r^2
+__global__ void __launch_bounds__(kThreads) k_block_resid(const double *__restrict__ mass, const double *__restrict__ target,
+                                                          int64_t count, double *__restrict__ resid,
+                                                          double *__restrict__ part) {
+    double acc[1] = {0.0};
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x) {
+        const double r = mass[q] - target[q];
+        resid[q] = r;
+        acc[0] += r * r;
+    }
+    __shared__ double o[1];
+    block_sum_store<1>(acc, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = o[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_sum_parts(const double *__restrict__ part, int count, double *out) {
+    double acc[1] = {0.0};
+    for (int q = threadIdx.x; q < count; q += blockDim.x) acc[0] += part[q];
+    __shared__ double o[1];
+    block_sum_store<1>(acc, o);
+    if (threadIdx.x == 0) out[0] = o[0];
+}
+
+// dL/dX_c,i = 2 r_c,b(i) for the selected compartments, 0 for the others.
+__global__ void __launch_bounds__(kThreads) k_block_mass_grad(Topo t, const int32_t *__restrict__ chunk_row,
+                                                              int32_t cap, BlockWeights bw, int comp_mask,
+                                                              const double *__restrict__ resid, int64_t nblocks,
+                                                              double *__restrict__ dldx) {
+    extern __shared__ uint32_t smem[];
+    int32_t *s_nb = reinterpret_cast<int32_t *>(smem + cap);
+    int64_t v0;
+    const int32_t nv = decode_chunk<true>(t, chunk_row, cap, smem, s_nb, smem + 5 * cap, v0);
+    const int64_t n = t.n;
+    for (int32_t k = threadIdx.x; k < nv; k += blockDim.x) {
+        const int64_t i = v0 + k;
+        const int32_t x = (int32_t)(smem[k] & 0xffffu);
+        const int32_t y = (int32_t)(smem[5 * cap + k] & 0xffffu), z = (int32_t)(smem[5 * cap + k] >> 16);
+        const int64_t b = ((int64_t)(z / bw.bs) * bw.nby + y / bw.bs) * bw.nbx + x / bw.bs;
+        int slot = 0;
+        for (int c = 0; c < 5; ++c) {
+            double g = 0.0;
+            if ((comp_mask >> c) & 1) {
+                g = 2.0 * resid[slot * nblocks + b];
+                ++slot;
+            }
+            dldx[c * n + i] = g;
+        }
+    }
+}
+
+// FP64 (5 x n) -> compensated buffers with row stride npad
+__global__ void k_lam_in(int64_t n, const double *__restrict__ x, StateIO io) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        const double v = x[c * n + i];
+        const float h = (float)v;
+        io.out[c][i] = h;
+        io.lout[c][i] = float_to_bf16_bits((float)(v - (double)h));
+    }
+}
+
+__global__ void k_lam_out(int64_t n, double *__restrict__ x, StateIO io) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) x[c * n + i] = (double)io.in[c][i] + (double)bf16_bits_to_float(io.lin[c][i]);
+}
+
+inline unsigned grid_for(int64_t count, int threads) { return (unsigned)((count + threads - 1) / threads); }
+
+// Pair of FP32 + BF16 buffers for 5 compartments with row stride npad.
+struct PairBuf {
+    float *h = nullptr;
+    uint16_t *l = nullptr;
+};
+
+StateIO io_from(PairBuf in, PairBuf out, int64_t npad) {
+    StateIO io;
+    for (int c = 0; c < 5; ++c) {
+        io.in[c] = in.h + (size_t)c * npad;
+        io.lin[c] = in.l + (size_t)c * npad;
+        io.out[c] = out.h + (size_t)c * npad;
+        io.lout[c] = out.l + (size_t)c * npad;
+    }
+    return io;
+}
+
+}  // namespace
+
+// Adjoint work buffers, owned by the simulation and kept between calls.
+struct AdjointBuffers {
+    int64_t npad = 0, nseg = 0, ckpt = 0, G = 0, ntheta = 0;
+    // the forward pass the checkpoints belong to
+    bool valid = false;
+    int64_t N = 0, cur_ckpt = 0, param_gen = -1;
+    char *ck = nullptr;    // nseg checkpoints, each 5*npad floats + 5*npad u16
+    float *rec_x = nullptr;   // ckpt x 5 x npad
+    float *rec_y2 = nullptr;  // ckpt x npad
+    PairBuf work[2];
+    PairBuf lam[2];
+    double *gpart = nullptr;  // G x kPar
+    double *gtheta = nullptr; // ntheta
+    double *gsum = nullptr;   // kPar
+    double *lamstage = nullptr;  // 5 n FP64 (host-pointer staging)
+};
+
+void adjoint_free(AdjointBuffers *a) {
+    if (!a) return;
+    dfree(a->ck);
+    dfree(a->rec_x);
+    dfree(a->rec_y2);
+    for (int b = 0; b < 2; ++b) {
+        dfree(a->work[b].h);
+        dfree(a->work[b].l);
+        dfree(a->lam[b].h);
+        dfree(a->lam[b].l);
+    }
+    dfree(a->gpart);
+    dfree(a->gtheta);
+    dfree(a->gsum);
+    dfree(a->lamstage);
+    delete a;
+}
+
+static vga_status ensure_adjoint(vga_sim *s, int64_t nseg, int64_t ckpt) {
+    AdjointBuffers *a = s->adj;
+    const int64_t npad = s->npad, G = s->chunks.count, ntheta = std::max<int64_t>(s->n_theta, 1);
+    if (a && a->npad == npad && a->nseg >= nseg && a->ckpt >= ckpt && a->G == G && a->ntheta >= ntheta) return VGA_OK;
+    adjoint_free(a);
+    s->adj = nullptr;
+    a = new (std::nothrow) AdjointBuffers();
+    if (!a) return fail(VGA_ERR_OOM, "host allocation of the adjoint buffers failed");
+    s->adj = a;
+    a->npad = npad;
+    a->nseg = nseg;
+    a->ckpt = ckpt;
+    a->G = G;
+    a->ntheta = ntheta;
+    const size_t pairb = 5 * (size_t)npad * (sizeof(float) + sizeof(uint16_t));
+    VGA_TRY(dmalloc((void **)&a->ck, pairb * (size_t)nseg, "adjoint checkpoints"));
+    VGA_TRY(dmalloc((void **)&a->rec_x, sizeof(float) * 5 * (size_t)npad * (size_t)ckpt, "adjoint records"));
+    VGA_TRY(dmalloc((void **)&a->rec_y2, sizeof(float) * (size_t)npad * (size_t)ckpt, "adjoint records"));
+    for (int b = 0; b < 2; ++b) {
+        VGA_TRY(dmalloc((void **)&a->work[b].h, sizeof(float) * 5 * (size_t)npad, "adjoint work"));
+        VGA_TRY(dmalloc((void **)&a->work[b].l, sizeof(uint16_t) * 5 * (size_t)npad, "adjoint work"));
+        VGA_TRY(dmalloc((void **)&a->lam[b].h, sizeof(float) * 5 * (size_t)npad, "adjoint state"));
+        VGA_TRY(dmalloc((void **)&a->lam[b].l, sizeof(uint16_t) * 5 * (size_t)npad, "adjoint state"));
+    }
+    VGA_TRY(dmalloc((void **)&a->gpart, sizeof(double) * kPar * (size_t)std::max<int64_t>(G, 1), "gradient partials"));
+    VGA_TRY(dmalloc((void **)&a->gtheta, sizeof(double) * (size_t)ntheta, "theta gradient"));
+    VGA_TRY(dmalloc((void **)&a->gsum, sizeof(double) * kPar, "gradient sums"));
+    return VGA_OK;
+}
+
+static PairBuf ck_slot(AdjointBuffers *a, int64_t s) {
+    const size_t pairb = 5 * (size_t)a->npad * (sizeof(float) + sizeof(uint16_t));
+    PairBuf p;
+    p.h = reinterpret_cast<float *>(a->ck + pairb * (size_t)s);
+    p.l = reinterpret_cast<uint16_t *>(a->ck + pairb * (size_t)s + 5 * (size_t)a->npad * sizeof(float));
+    return p;
+}
+
+// Copies the simulation's current state into a pair buffer (or back).
+static vga_status copy_state(vga_sim *s, PairBuf p, bool to_sim) {
+    for (int c = 0; c < 5; ++c) {
+        float *h = p.h + (size_t)c * s->npad;
+        uint16_t *l = p.l + (size_t)c * s->npad;
+        if (to_sim) {
+            VGA_CUDA(cudaMemcpyAsync(s->comp(c), h, sizeof(float) * (size_t)s->n, cudaMemcpyDeviceToDevice, s->stream));
+            VGA_CUDA(cudaMemcpyAsync(s->lcomp(c), l, sizeof(uint16_t) * (size_t)s->n, cudaMemcpyDeviceToDevice,
+                                     s->stream));
+        } else {
+            VGA_CUDA(cudaMemcpyAsync(h, s->comp(c), sizeof(float) * (size_t)s->n, cudaMemcpyDeviceToDevice, s->stream));
+            VGA_CUDA(cudaMemcpyAsync(l, s->lcomp(c), sizeof(uint16_t) * (size_t)s->n, cudaMemcpyDeviceToDevice,
+                                     s->stream));
+        }
+    }
+    return VGA_OK;
+}
+
+vga_status sim_adjoint_forward(vga_sim *s, int64_t N, int64_t ckpt) {
+    const int64_t nseg = N > 0 ? (N + ckpt - 1) / ckpt : 0;
+    VGA_TRY(ensure_adjoint(s, std::max<int64_t>(nseg, 1), ckpt));
+    AdjointBuffers *a = s->adj;
+    a->valid = false;
+    for (int64_t sg = 0; sg < nseg; ++sg) {
+        VGA_TRY(copy_state(s, ck_slot(a, sg), false));
+        const int64_t len = std::min(ckpt, N - sg * ckpt);
+        VGA_TRY(sim_step_explicit(s, len));
+    }
+    a->N = N;
+    a->cur_ckpt = ckpt;
+    a->param_gen = s->param_gen;
+    a->valid = true;
+    return VGA_OK;
+}
+
+template <int WM>
+static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double *d_lam0, double *grad8,
+                                        double *h_gtheta) {
+    constexpr int PREC = P_COMP;
+    AdjointBuffers *a = s->adj;
+    const int64_t N = a->N, ckpt = a->cur_ckpt;
+    const int64_t nseg = N > 0 ? (N + ckpt - 1) / ckpt : 0;
+    const Topo t = s->g->topo();
+    const int G = s->chunks.count;
+    const size_t smem = sizeof(uint32_t) * (size_t)s->chunks.cap * decode_words(WM == W_BLOCK);
+    const int64_t npad = s->npad;
+    cudaStream_t st = s->stream;
+
+    k_lam_in<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, d_lamN, io_from(a->lam[0], a->lam[0], npad));
+    VGA_CHECK_LAUNCH();
+    VGA_CUDA(cudaMemsetAsync(a->gpart, 0, sizeof(double) * kPar * (size_t)std::max(G, 1), st));
+    VGA_CUDA(cudaMemsetAsync(a->gtheta, 0, sizeof(double) * (size_t)a->ntheta, st));
+    int lb = 0;
+    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+        const int64_t len = std::min(ckpt, N - sg * ckpt);
+        // recompute the segment, recording X^k and y2^k for k = 0 .. len-1 (relative to its start)
+        PairBuf cks = ck_slot(a, sg);
+        Rec rec;
+        timing_begin(s, VGA_KERNEL_TRANSFORM);
+        k_transform_rec<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->sp, io_from(cks, a->work[0], npad),
+                                                                            a->rec_y2);
+        timing_end(s);
+        VGA_CHECK_LAUNCH();
+        ++s->launches;
+        int wb = 0;
+        for (int64_t j = 1; j < len; ++j) {
+            rec.x = a->rec_x + (size_t)j * 5 * npad;
+            rec.y2 = a->rec_y2 + (size_t)j * npad;
+            timing_begin(s, VGA_KERNEL_FUSED_STEP);
+            k_fused_rec<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
+                                                            io_from(a->work[wb], a->work[1 - wb], npad), npad, rec);
+            timing_end(s);
+            VGA_CHECK_LAUNCH();
+            ++s->launches;
+            wb = 1 - wb;
+        }
+        // reverse
+        for (int64_t j = len - 1; j >= 0; --j) {
+            const float *xk = (j == 0) ? cks.h : a->rec_x + (size_t)j * 5 * npad;
+            timing_begin(s, VGA_KERNEL_ADJOINT);
+            k_adjoint_step<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
+                                                               io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
+                                                               a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
+            timing_end(s);
+            VGA_CHECK_LAUNCH();
+            ++s->launches;
+            lb = 1 - lb;
+        }
+    }
+    if (d_lam0) {
+        k_lam_out<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, d_lam0, io_from(a->lam[lb], a->lam[lb], npad));
+        VGA_CHECK_LAUNCH();
+    }
+    k_reduce_gpart<<<1, kThreads, 0, st>>>(a->gpart, G, a->gsum);
+    VGA_CHECK_LAUNCH();
+    s->launches += 2;
+    double h[kPar];
+    VGA_CUDA(cudaMemcpyAsync(h, a->gsum, sizeof(double) * kPar, cudaMemcpyDeviceToHost, st));
+    if (h_gtheta && s->n_theta > 0 && s->wmode == W_BLOCK)
+        VGA_CUDA(cudaMemcpyAsync(h_gtheta, a->gtheta, sizeof(double) * (size_t)s->n_theta, cudaMemcpyDeviceToHost, st));
+    VGA_CUDA(cudaStreamSynchronize(st));
+    const double dt = s->params.dt;
+    // order: D, rho, mu, beta, v_som, v_fom, v_dom, K_dom
+    grad8[0] = h[GR_COUNT] * dt;
+    grad8[1] = h[GR_R] * dt;
+    grad8[2] = h[GR_M] * dt;
+    grad8[3] = h[GR_BETA];
+    grad8[4] = h[GR_S] * dt;
+    grad8[5] = h[GR_F] * dt;
+    grad8[6] = h[GR_A] * dt;
+    grad8[7] = h[GR_K];
+    return VGA_OK;
+}
+
+vga_status sim_adjoint_backward(vga_sim *s, const double *d_lamN, double *d_lam0, double *grad8, double *h_gtheta) {
+    if (!s->adj || !s->adj->valid) return fail(VGA_ERR_INVALID_ARG, "no adjoint forward pass to reverse");
+    if (s->adj->param_gen != s->param_gen)
+        return fail(VGA_ERR_INVALID_ARG, "parameters or conductances changed since the adjoint forward pass");
+    if (s->wmode == W_BLOCK) return adjoint_backward_impl<W_BLOCK>(s, d_lamN, d_lam0, grad8, h_gtheta);
+    return adjoint_backward_impl<W_UNIT>(s, d_lamN, d_lam0, grad8, h_gtheta);
+}
+
+// Block masses of the selected compartments, the objective L = sum (mass - target)^2 and, if
+// d_dldx != NULL, dL/dX (5 x n FP64, device).  d_work: 2*count + 64 doubles of device scratch.
+vga_status sim_block_mass_loss(vga_sim *s, int32_t bs, uint32_t comp_mask, const double *d_target, double *d_work,
+                               double *h_loss, double *h_mass, double *d_dldx) {
+    const vga_graph *g = s->g;
+    BlockWeights bw;
+    bw.bs = bs;
+    bw.nbx = (g->nx + bs - 1) / bs;
+    bw.nby = (g->ny + bs - 1) / bs;
+    bw.nbz = (g->nz + bs - 1) / bs;
+    const int64_t nblocks = (int64_t)bw.nbx * bw.nby * bw.nbz;
+    int nsel = 0;
+    for (int c = 0; c < 5; ++c) nsel += (comp_mask >> c) & 1;
+    const int64_t count = nsel * nblocks;
+    double *mass = d_work, *resid = d_work + count, *part = d_work + 2 * count;
+    const Topo t = g->topo();
+    const size_t smem = sizeof(uint32_t) * (size_t)s->chunks.cap * decode_words(true);
+    cudaStream_t st = s->stream;
+    VGA_CUDA(cudaMemsetAsync(mass, 0, sizeof(double) * (size_t)count, st));
+    if (s->n > 0) {
+        k_block_mass<<<s->chunks.count, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, bw, state_io_inplace(s),
+                                                            (int)comp_mask, mass, nblocks);
+        VGA_CHECK_LAUNCH();
+    }
+    const int rb = (int)std::min<int64_t>(32, std::max<int64_t>(1, (count + kThreads - 1) / kThreads));
+    k_block_resid<<<rb, kThreads, 0, st>>>(mass, d_target, count, resid, part);
+    k_sum_parts<<<1, kThreads, 0, st>>>(part, rb, part + 32);
+    VGA_CHECK_LAUNCH();
+    s->launches += 3;
+    if (d_dldx && s->n > 0) {
+        k_block_mass_grad<<<s->chunks.count, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, bw, (int)comp_mask,
+                                                                 resid, nblocks, d_dldx);
+        VGA_CHECK_LAUNCH();
+        ++s->launches;
+    }
+    VGA_CUDA(cudaMemcpyAsync(h_loss, part + 32, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (h_mass) VGA_CUDA(cudaMemcpyAsync(h_mass, mass, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, st));
+    VGA_CUDA(cudaStreamSynchronize(st));
+    return VGA_OK;
+}
+
+}  // namespace vga

@@ -301,6 +301,7 @@ vga_status vga_sim_create(const vga_graph *g, const vga_params *p, void *stream,
 vga_status vga_sim_set_params(vga_sim *s, const vga_params *p) {
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
     VGA_TRY(validate_params(p, s->max_g));
+    ++s->param_gen;
     if (p->state_precision != s->params.state_precision) {
         // residuals are meaningless across a precision change: start them at zero
         for (int b = 0; b < 2; ++b)
@@ -351,6 +352,7 @@ vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const 
     s->bw.theta = s->theta;
     s->wmode = W_BLOCK;
     s->max_g = mx;
+    ++s->param_gen;
     return VGA_OK;
 }
 
@@ -358,6 +360,7 @@ vga_status vga_sim_clear_conductances(vga_sim *s) {
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
     s->wmode = W_UNIT;
     s->max_g = 1.0f;
+    ++s->param_gen;
     return VGA_OK;
 }
 
@@ -505,6 +508,61 @@ vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out) {
     return VGA_OK;
 }
 
+vga_status vga_adjoint_forward(vga_sim *s, int64_t n_steps, int32_t ckpt_every) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    if (n_steps < 0 || ckpt_every < 1) return fail(VGA_ERR_INVALID_ARG, "n_steps must be >= 0 and ckpt_every >= 1");
+    if (s->params.scheme != VGA_SCHEME_EXPLICIT || s->params.transform != VGA_TRANSFORM_SYNC ||
+        s->params.state_precision != VGA_STATE_COMPENSATED)
+        return fail(VGA_ERR_UNSUPPORTED,
+                    "the adjoint covers the explicit scheme, synchronous transformation, compensated state");
+    return sim_adjoint_forward(s, n_steps, ckpt_every);
+}
+
+vga_status vga_adjoint_backward(vga_sim *s, const double *dL_dXN, int32_t on_device, double *dL_dX0,
+                                double *grad_params, double *grad_theta) {
+    if (!s || !grad_params || (!dL_dXN && s->n > 0)) return fail(VGA_ERR_INVALID_ARG, "sim, dL_dXN or grad_params is NULL");
+    const double *d_in = dL_dXN;
+    double *d_out = dL_dX0;
+    if (!on_device && s->n > 0) {
+        VGA_TRY(ensure_stage(s));
+        VGA_CUDA(cudaMemcpyAsync(s->stage, dL_dXN, sizeof(double) * 5 * (size_t)s->n, cudaMemcpyHostToDevice,
+                                 s->stream));
+        d_in = s->stage;
+        d_out = dL_dX0 ? s->stage : nullptr;  // overwritten only after lambda^N has been read
+    }
+    VGA_TRY(sim_adjoint_backward(s, d_in, d_out, grad_params, grad_theta));
+    if (!on_device && dL_dX0 && s->n > 0) {
+        VGA_CUDA(cudaMemcpyAsync(dL_dX0, s->stage, sizeof(double) * 5 * (size_t)s->n, cudaMemcpyDeviceToHost,
+                                 s->stream));
+        VGA_CUDA(cudaStreamSynchronize(s->stream));
+    }
+    return VGA_OK;
+}
+
+vga_status vga_loss_block_mass(vga_sim *s, int32_t block_side, uint32_t comp_mask, const double *target,
+                               double *loss, double *block_mass, double *dL_dX) {
+    if (!s || !target || !loss) return fail(VGA_ERR_INVALID_ARG, "sim, target or loss is NULL");
+    if (block_side < 1 || comp_mask == 0 || (comp_mask & ~31u))
+        return fail(VGA_ERR_INVALID_ARG, "block_side must be >= 1 and comp_mask a non-empty subset of 0..4");
+    const vga_graph *g = s->g;
+    const int64_t nb = (int64_t)((g->nx + block_side - 1) / block_side) * ((g->ny + block_side - 1) / block_side) *
+                       ((g->nz + block_side - 1) / block_side);
+    int nsel = 0;
+    for (int c = 0; c < 5; ++c) nsel += (comp_mask >> c) & 1;
+    const int64_t count = nsel * nb;
+    const int64_t need = 3 * count + 64;
+    if (s->loss_cap < need) {
+        dfree(s->loss_work);
+        s->loss_work = nullptr;
+        s->loss_cap = 0;
+        VGA_TRY(dmalloc((void **)&s->loss_work, sizeof(double) * (size_t)need, "loss work"));
+        s->loss_cap = need;
+    }
+    double *d_target = s->loss_work + 2 * count + 64;
+    VGA_CUDA(cudaMemcpyAsync(d_target, target, sizeof(double) * (size_t)count, cudaMemcpyHostToDevice, s->stream));
+    return sim_block_mass_loss(s, block_side, comp_mask, d_target, s->loss_work, loss, block_mass, dL_dX);
+}
+
 vga_status vga_sim_enable_timing(vga_sim *s, int32_t on) {
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
     s->timing = on != 0;
@@ -544,6 +602,8 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->theta);
     dfree(s->cg);
     dfree(s->cg_scalars);
+    dfree(s->loss_work);
+    adjoint_free(s->adj);
     if (s->h_cg) cudaFreeHost(s->h_cg);
     free_chunks(&s->chunks);
     delete s;

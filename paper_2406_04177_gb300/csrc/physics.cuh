@@ -73,6 +73,19 @@ __device__ __forceinline__ void vstore(float *__restrict__ H, uint16_t *__restri
     }
 }
 
+// Rounds a pair to exactly what vstore followed by vload yields, so a value kept in registers across
+// two stages of one pass behaves as if it had been stored in between (a run split into several
+// calls then reproduces an uninterrupted run bit for bit).
+template <int PREC>
+__device__ __forceinline__ void vround(V &v) {
+    if (PREC == P_COMP) {
+        const float s = __fadd_rn(v.h, v.l);
+        const float r = __fadd_rn(__fsub_rn(v.h, s), v.l);
+        v.h = s;
+        v.l = bf16_bits_to_float(float_to_bf16_bits(r));
+    }
+}
+
 // Synchronous transformation (Sec. II.C eq. 3 with the clamps of the Appendix A listing that
 // computes every flux from the old state): uptake <= DOM; respiration + mortality <= MB with
 // mortality served first; FOM and SOM turnover <= FOM and SOM.  Fluxes use the FP32 part h.
@@ -168,6 +181,80 @@ template <int TR, int PREC>
 __device__ __forceinline__ void transform(V &x1, V &x2, V &x3, V &x4, V &x5, const StepParams &p) {
     if (TR == 0) transform_sync<PREC>(x1, x2, x3, x4, x5, p);
     else transform_async<PREC>(x1, x2, x3, x4, x5, p);
+}
+
+}  // namespace vga
+
+namespace vga {
+
+// Rate-gradient slots accumulated by the reverse transformation.  The first five are derivatives
+// with respect to the dt-products (v_dom dt, rho dt, mu dt, v_fom dt, v_som dt); the caller scales
+// them by dt to obtain derivatives with respect to the rates.
+enum { GR_A = 0, GR_R, GR_M, GR_F, GR_S, GR_BETA, GR_K, GR_COUNT };
+
+// Reverse of transform_sync at the pre-transformation state x (FP32 values).  The transformation
+// is y = x + S f(x) with fluxes f = (uptake, morta, resp, turnFOM, turnSOM); with w = S^T mu the
+// adjoint of x is mu + (df/dx)^T w, and w . df/dtheta are the rate gradients.  Every derivative
+// follows the branch the forward clamps took at x.
+template <int PREC>
+__device__ __forceinline__ void transform_sync_reverse(const float (&x)[5], const V (&mu)[5], V (&lam)[5],
+                                                       float (&gr)[GR_COUNT], const StepParams &p) {
+    const float x1 = x[0], x2 = x[1], x3 = x[2], x4 = x[3];
+    const float kx = __fadd_rn(p.K, x2);
+    const float sat = __fdividef(x2, kx);
+    const float u0 = __fmul_rn(__fmul_rn(p.a, sat), x1);
+    const bool upt_clamped = u0 > x2;
+    const float r0 = __fmul_rn(p.r, x1), m0 = __fmul_rn(p.m, x1);
+    int mr_case = 0;  // 0: free, 1: morta = x1 and resp = 0, 2: resp = x1 - morta
+    if (__fadd_rn(r0, m0) > x1) mr_case = (m0 > x1) ? 1 : 2;
+    const float morta = (mr_case == 1) ? x1 : m0;
+    const bool tF_clamped = __fmul_rn(p.f, x4) > x4;
+    const bool tS_clamped = __fmul_rn(p.s, x3) > x3;
+
+    const float w_upt = __fsub_rn(mu[0].h, mu[1].h);
+    const float w_mor = __fadd_rn(__fadd_rn(-mu[0].h, __fmul_rn(p.beta, mu[1].h)), __fmul_rn(p.omb, mu[2].h));
+    const float w_resp = __fsub_rn(mu[4].h, mu[0].h);
+    const float w_tF = __fsub_rn(mu[1].h, mu[3].h);
+    const float w_tS = __fsub_rn(mu[1].h, mu[2].h);
+
+    float d[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (upt_clamped) {
+        d[1] = __fadd_rn(d[1], w_upt);
+    } else {
+        const float inv2 = __fdividef(1.0f, __fmul_rn(kx, kx));
+        d[0] = __fadd_rn(d[0], __fmul_rn(w_upt, __fmul_rn(p.a, sat)));
+        d[1] = __fadd_rn(d[1], __fmul_rn(w_upt, __fmul_rn(__fmul_rn(__fmul_rn(p.a, x1), p.K), inv2)));
+        gr[GR_A] = __fadd_rn(gr[GR_A], __fmul_rn(w_upt, __fmul_rn(sat, x1)));
+        gr[GR_K] = __fsub_rn(gr[GR_K], __fmul_rn(w_upt, __fmul_rn(__fmul_rn(__fmul_rn(p.a, x2), x1), inv2)));
+    }
+    if (mr_case == 0) {
+        d[0] = __fadd_rn(d[0], __fadd_rn(__fmul_rn(w_mor, p.m), __fmul_rn(w_resp, p.r)));
+        gr[GR_M] = __fadd_rn(gr[GR_M], __fmul_rn(w_mor, x1));
+        gr[GR_R] = __fadd_rn(gr[GR_R], __fmul_rn(w_resp, x1));
+    } else if (mr_case == 1) {
+        d[0] = __fadd_rn(d[0], w_mor);
+    } else {
+        d[0] = __fadd_rn(d[0], __fadd_rn(__fmul_rn(w_mor, p.m), __fmul_rn(w_resp, __fsub_rn(1.0f, p.m))));
+        gr[GR_M] = __fadd_rn(gr[GR_M], __fmul_rn(__fsub_rn(w_mor, w_resp), x1));
+    }
+    gr[GR_BETA] = __fadd_rn(gr[GR_BETA], __fmul_rn(__fsub_rn(mu[1].h, mu[2].h), morta));
+    if (tF_clamped) {
+        d[3] = __fadd_rn(d[3], w_tF);
+    } else {
+        d[3] = __fadd_rn(d[3], __fmul_rn(w_tF, p.f));
+        gr[GR_F] = __fadd_rn(gr[GR_F], __fmul_rn(w_tF, x4));
+    }
+    if (tS_clamped) {
+        d[2] = __fadd_rn(d[2], w_tS);
+    } else {
+        d[2] = __fadd_rn(d[2], __fmul_rn(w_tS, p.s));
+        gr[GR_S] = __fadd_rn(gr[GR_S], __fmul_rn(w_tS, x3));
+    }
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        lam[c] = mu[c];
+        vadd<PREC>(lam[c], d[c]);
+    }
 }
 
 }  // namespace vga

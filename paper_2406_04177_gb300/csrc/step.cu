@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Topo t, const int32_t *__r
         });
         vadd<PREC>(x2, __fmul_rn(-p.c, acc));  // Scheme 1: y_i - D dt sum_j g_ij (y_i - y_j)
         if (MODE == 1) {
+            vround<PREC>(x2);  // as if X^{k+1} had been stored (split runs stay bit-identical)
             V x1 = vload<PREC>(io.in[0], io.lin[0], i), x3 = vload<PREC>(io.in[2], io.lin[2], i),
               x4 = vload<PREC>(io.in[3], io.lin[3], i), x5 = vload<PREC>(io.in[4], io.lin[4], i);
             transform<TR, PREC>(x1, x2, x3, x4, x5, p);

@@ -111,6 +111,9 @@ vga_status scan_popc(const uint32_t *words, int64_t nwords, int32_t *out, int32_
 vga_status build_chunks(const Topo &topo, int32_t cap, Chunks *ch, cudaStream_t st);
 void free_chunks(Chunks *ch);
 
+struct AdjointBuffers;
+void adjoint_free(AdjointBuffers *a);
+
 }  // namespace vga
 
 // ---------------------------------------------------------------------------------------------
@@ -175,6 +178,11 @@ struct vga_sim {
     int64_t kt_count[VGA_KERNEL_KINDS] = {};
     cudaEvent_t timing_a = nullptr;
     int timing_kind = -1;
+    // adjoint work buffers (adjoint.cu), allocated on first use
+    vga::AdjointBuffers *adj = nullptr;
+    double *loss_work = nullptr;  // block-mass objective scratch
+    int64_t loss_cap = 0;
+    int64_t param_gen = 0;  // bumped by every change of parameters or conductances
 
     float *comp(int c) { return buf[cur[c]] + (size_t)c * npad; }
     float *spare(int c) { return buf[1 - cur[c]] + (size_t)c * npad; }
@@ -199,4 +207,9 @@ StateIO state_io(vga_sim *s);          // current buffers in, spare buffers out
 StateIO state_io_inplace(vga_sim *s);  // current buffers in and out
 // pcg.cu
 vga_status sim_step_implicit(vga_sim *s, int64_t n_steps);
+// adjoint.cu
+vga_status sim_adjoint_forward(vga_sim *s, int64_t N, int64_t ckpt);
+vga_status sim_adjoint_backward(vga_sim *s, const double *d_lamN, double *d_lam0, double *grad8, double *h_gtheta);
+vga_status sim_block_mass_loss(vga_sim *s, int32_t bs, uint32_t comp_mask, const double *d_target, double *d_work,
+                               double *h_loss, double *h_mass, double *d_dldx);
 }  // namespace vga
