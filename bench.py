@@ -220,6 +220,7 @@ def bench_ours(a):
     sim = vga.Sim(g, params, stream=stream)
     x0_dev = torch.from_numpy(X0).cuda()
     sim.set_masses(x0_dev)
+    tune = sim.autotune(20)  # picks the stencil variant / chunk size; state left unchanged
     tot0 = sim.totals()
 
     S = a.substeps
@@ -269,8 +270,11 @@ def bench_ours(a):
     peak, peak_src = load_peaks()
     achieved = BYTES_PER_PVS * n / mean_launch_s / 1e9
     traffic = recorded_traffic(n)
+    best = tune["best"] or {}
+    kname = {0: "k_stencil (chunk decode, direct loads)", 1: "k_stencil_staged (chunk decode, bulk-copy staging)",
+             2: "k_stencil_table (neighbour-offset table)"}.get(best.get("variant"), "k_stencil")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_stencil<fused> (diffuse stored transformed DOM, then transform)",
+                "traffic": traffic, "kernel": f"{kname}, fused pass (diffuse the stored transformed DOM, then transform)",
                 "algorithmic_bytes_per_launch": BYTES_PER_PVS * n, "mean_launch_ms": mean_launch_s * 1e3,
                 "launches_timed": fused_count, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_src == "measured" else "fallback 6.8 TB/s",
@@ -306,6 +310,7 @@ def bench_ours(a):
                       f"{5 * 4 * n / 1e6:.0f} MB each", "parallelism": "replicas" if world > 1 else "single GPU"},
            "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
            "kernel_time_ms": {k: v[0] for k, v in timing.items() if v[1]},
+           "autotune": tune,
            "drift_timed_region": float(abs(tot1.sum() - tot0.sum()) / tot0.sum())}
 
     if not a.no_extras:
@@ -331,6 +336,8 @@ def bench_ours(a):
                               "last_relres": st["cg_last_relres"], "dt_over_explicit_limit": 10 / 0.9 * 0.9,
                               "rtol": 1e-8}
         simi.close()
+        extras["adjoint"] = bench_adjoint(vga, g, params, x0_dev, n, stream)
+        extras["batched"] = bench_batched(vga, a)
         out.update(extras)
 
     if rank == 0 and world == 1 or (rank == 0 and world > 1):
@@ -352,6 +359,76 @@ def bench_ours(a):
     g.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_adjoint(vga, g, params, x0_dev, n, stream, nsteps=200, ckpt=100, bs=8):
+    """Checkpointed forward + block-mass loss + reverse sweep on the full workload (block
+    conductances on 8^3 blocks, all 1).  PVS/s counts each of the N steps once."""
+    import torch
+
+    import synth
+
+    side = g.shape[0]
+    nb = (-(-side // bs),) * 3
+    n_theta = 3 * nb[0] * nb[1] * (nb[2] - 1)
+    sim = vga.Sim(g, params, stream=stream)
+    sim.set_block_conductances(bs, np.ones(n_theta, dtype=np.float32))
+    target = np.zeros((2, nb[0] * nb[1] * nb[2]))
+    dldx = torch.empty((5, n), dtype=torch.float64, device="cuda")
+    sim.set_masses(x0_dev)
+    sim.adjoint_forward(4, 2)  # warm-up (allocations)
+    sim.loss_block_mass(bs, (1 << 1) | (1 << 4), target, dL_dX=dldx)
+    sim.adjoint_backward(dldx, n_theta=n_theta)
+    sim.set_masses(x0_dev)
+    torch.cuda.synchronize()
+    sim.enable_timing(True)
+    sim.read_timing(reset=True)
+    t0 = time.perf_counter()
+    sim.adjoint_forward(nsteps, ckpt)
+    L, _ = sim.loss_block_mass(bs, (1 << 1) | (1 << 4), target, dL_dX=dldx)
+    grad, gth = sim.adjoint_backward(dldx, n_theta=n_theta)
+    t1 = time.perf_counter()
+    kt = sim.read_timing(reset=True)
+    sim.close()
+    return {"value": n * nsteps / (t1 - t0), "unit": UNIT + " (checkpointed forward + loss + reverse sweep)",
+            "time_steps": nsteps, "ckpt_every": ckpt, "seconds": t1 - t0,
+            "reverse_kernel_mean_ms": kt["adjoint"][0] / max(kt["adjoint"][1], 1),
+            "reverse_kernel_launches": kt["adjoint"][1], "grad_D": grad["D"], "n_theta": n_theta}
+
+
+def bench_batched(vga, a, count=64, nsteps=5000):
+    """64 subvolumes, side U{64..192}, porosity U(10%, 35%), rates log-uniform in [0.5, 1.5] x the
+    paper's, 5000 steps in persistent graph-captured launches (launch shape autotuned)."""
+    import synth
+
+    t0 = time.time()
+    specs = synth.batch_instances(count, 7)
+    graphs, params, masses = [], [], []
+    for sp in specs:
+        img = synth.pore_mask(sp["shape"], sp["porosity"], sp["mask_seed"])
+        gk = vga.Graph(img)
+        kept = synth.kept_mask_from_nodes(img.shape, gk.export(labels=False, nbr=False)["voxel_of_node"])
+        graphs.append(gk)
+        params.append(sp["params"])
+        masses.append(synth.initial_masses(kept, sp["mass_seed"]))
+    t_setup = time.time() - t0
+    b = vga.Batch(graphs, params)
+    for k, X in enumerate(masses):
+        b.set_masses(k, X)
+    tune = b.autotune(50)
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b.step(nsteps)
+    t1 = time.perf_counter()
+    st = b.stats()
+    total = sum(gk.n for gk in graphs)
+    b.close()
+    return {"value": total * nsteps / (t1 - t0), "unit": UNIT, "instances": count, "total_nodes": total,
+            "time_steps": nsteps, "seconds": t1 - t0, "setup_seconds": t_setup, "launch": tune["best"],
+            "graph_replays": st["graph_replays"], "capture_failed": bool(st["capture_failed"]),
+            "grid_blocks": st["grid_blocks"]}
 
 
 def bench_reference(a):

@@ -211,6 +211,14 @@ vga_status vga_adjoint_forward(vga_sim *s, int64_t n_steps, int32_t ckpt_every);
 vga_status vga_adjoint_backward(vga_sim *s, const double *dL_dXN, int32_t on_device, double *dL_dX0,
                                 double *grad_params, double *grad_theta);
 
+/* Normalised gradient step of Sec. V.A on the block conductances, using the theta gradient of the
+ * last vga_adjoint_backward: theta <- clamp(theta - lr * g/|g|, theta_min, theta_max) element-wise
+ * (g/|g| = 0 where g = 0), on the device.  Errors: VGA_ERR_INVALID_ARG (no gradient, no block
+ * conductances, bad bounds), VGA_ERR_UNSTABLE_DT (explicit scheme with 6 D dt theta_max > 1). */
+vga_status vga_sgd_block_conductances(vga_sim *s, double lr, double theta_min, double theta_max);
+/* Current block conductances (host copy, n_theta values). */
+vga_status vga_sim_get_block_conductances(vga_sim *s, float *theta, int64_t n_theta);
+
 /* Block-mass objective: the image is cut into cubes of block_side voxels; for every compartment c
  * in comp_mask (bit c) and block b, M_cb = sum of x^c over the nodes of b.
  * L = sum_cb (M_cb - target_cb)^2.  target (host): one row of nblocks values per selected
@@ -218,6 +226,85 @@ vga_status vga_adjoint_backward(vga_sim *s, const double *dL_dXN, int32_t on_dev
  * block_mass (host, same layout as target, or NULL), dL_dX (device, 5 x n FP64, or NULL). */
 vga_status vga_loss_block_mass(vga_sim *s, int32_t block_side, uint32_t comp_mask, const double *target,
                                double *loss, double *block_mass, double *dL_dX);
+
+/* Explicit-step kernel selection (all variants give bit-identical results):
+ *   0  chunks of `chunk` nodes decode their neighbours from the row bitmask, then load directly;
+ *   1  as 0, with each chunk's own state staged in shared memory by bulk asynchronous copies and
+ *      written back the same way (chunk = 512, 1024 or 2048);
+ *   2  one node per thread with a precomputed neighbour-offset table (12 bytes per node, built on
+ *      first use; unit conductances and nx <= 32767, otherwise variant 0 runs).  `chunk` is ignored.
+ * The default is 2. */
+vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t chunk);
+
+#define VGA_TUNE_MAX 16
+typedef struct vga_tune_entry {
+    int32_t variant;
+    int32_t chunk;
+    double ms_per_step;
+} vga_tune_entry;
+typedef struct vga_tune_result {
+    int32_t count;  /* entries filled */
+    int32_t best;   /* index of the selected entry (-1 if nothing was timed) */
+    vga_tune_entry entries[VGA_TUNE_MAX];
+} vga_tune_result;
+/* Times trial_steps explicit steps for every candidate (variant x chunk) on this simulation with
+ * CUDA events, selects the fastest, and restores the state and step counter.  Allocates a
+ * temporary copy of the state. */
+vga_status vga_sim_autotune(vga_sim *s, int32_t trial_steps, vga_tune_result *out);
+
+/* ============================================================================================
+ * Batched simulation: many independent graphs (uneven node counts, per-instance parameters)
+ * advanced together by one persistent cooperative kernel per launch, several time steps per
+ * launch with a bounded grid-wide barrier between passes, the launches of one call captured in a
+ * CUDA graph and replayed.  Explicit scheme only; all instances share transform and
+ * state_precision.  Results are bit-identical to vga_sim on each graph.
+ * ============================================================================================ */
+typedef struct vga_batch vga_batch;
+
+/* graphs[count] (must outlive the batch) and params[count].  The batch owns a private stream.
+ * Errors: VGA_ERR_INVALID_ARG, VGA_ERR_UNSUPPORTED (implicit scheme, nx > 32767),
+ * VGA_ERR_UNSTABLE_DT, VGA_ERR_OOM, VGA_ERR_CUDA. */
+vga_status vga_batch_create(const vga_graph *const *graphs, const vga_params *params, int32_t count,
+                            vga_batch **out);
+/* Total node count and (if non-NULL) the first node of every instance in the concatenated range. */
+vga_status vga_batch_info(const vga_batch *b, int64_t *total_nodes, int64_t *node_offsets);
+/* State of one instance, (5 x n_instance) FP64 host arrays. */
+vga_status vga_batch_set_masses(vga_batch *b, int32_t instance, const double *x);
+vga_status vga_batch_get_masses(vga_batch *b, int32_t instance, double *x);
+/* Advances every instance n_steps; returns when done.  VGA_ERR_TIMEOUT if a barrier gave up. */
+vga_status vga_batch_step(vga_batch *b, int64_t n_steps);
+/* Launch shape: time steps per persistent launch, resident blocks per SM (0 = occupancy maximum),
+ * CUDA-graph capture on or off. */
+vga_status vga_batch_set_launch(vga_batch *b, int32_t steps_per_launch, int32_t blocks_per_sm, int32_t use_graph);
+
+typedef struct vga_batch_stats {
+    int32_t instances;
+    int32_t grid_blocks;
+    int64_t total_nodes;
+    int32_t steps_per_launch;
+    int32_t capture_failed; /* 1 if graph capture was refused and launches run directly */
+    int64_t kernel_launches;
+    int64_t graph_replays;
+    int64_t steps_done;
+} vga_batch_stats;
+vga_status vga_batch_get_stats(const vga_batch *b, vga_batch_stats *out);
+
+typedef struct vga_batch_tune_entry {
+    int32_t steps_per_launch;
+    int32_t blocks_per_sm;
+    int32_t grid_blocks;
+    int32_t pad;
+    double ms_per_step;
+} vga_batch_tune_entry;
+typedef struct vga_batch_tune {
+    int32_t count;
+    int32_t best;
+    vga_batch_tune_entry entries[VGA_TUNE_MAX];
+} vga_batch_tune;
+/* Times trial_steps for each (steps per launch x blocks per SM) candidate, keeps the fastest and
+ * restores the state. */
+vga_status vga_batch_autotune(vga_batch *b, int32_t trial_steps, vga_batch_tune *out);
+vga_status vga_batch_free(vga_batch *b);
 
 /* Kernel timing.  When enabled, the library records a CUDA event pair on the simulation's stream
  * around every kernel it launches and accumulates the elapsed times per kernel kind; reading them
@@ -240,6 +327,25 @@ vga_status vga_sim_enable_timing(vga_sim *s, int32_t on);
 vga_status vga_sim_read_timing(vga_sim *s, vga_kernel_timing *out, int32_t reset);
 
 vga_status vga_sim_free(vga_sim *s);
+
+/* ============================================================================================
+ * Allocation-free totals.  The paper has no counterpart: this entry point exists for callers that
+ * cannot let a library allocate device memory -- an application that owns the GPU memory pool or
+ * runs under a hard memory cap and passes its plugins only the buffers to work on, or a latency-
+ * critical loop where cudaMalloc/cudaFree would stall on an implicit device synchronisation.
+ *
+ * Computes the FP64 totals of the 5 compartments of a state held by the caller: values (device,
+ * FP32, compartment c at values + c*row_stride, n entries each), optional residuals (device, BF16
+ * bits in the same layout, added to the values; NULL for none), into totals (device, 5 doubles),
+ * ordered on `stream`.  It calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * is a fixed 160 KiB array in the library's device memory (present on every GPU that loads the
+ * library, until the process exits), which limits n to 33,554,432 nodes; larger n returns
+ * VGA_ERR_INVALID_ARG.  The first call on a device looks up that array's address (with the device
+ * current), so make that first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU race, so serialise them.  Errors: VGA_ERR_INVALID_ARG (NULL pointers,
+ * n < 0, row_stride < n, n over the limit), VGA_ERR_CUDA. */
+vga_status vga_state_totals_noalloc(const float *values, const uint16_t *residuals, int64_t n,
+                                    int64_t row_stride, double *totals, void *stream);
 
 #ifdef __cplusplus
 }

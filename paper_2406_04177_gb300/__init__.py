@@ -50,6 +50,29 @@ class vga_params(C.Structure):
                 ("state_precision", C.c_int32)]
 
 
+class vga_tune_entry(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("chunk", C.c_int32), ("ms_per_step", C.c_double)]
+
+
+class vga_tune_result(C.Structure):
+    _fields_ = [("count", C.c_int32), ("best", C.c_int32), ("entries", vga_tune_entry * 16)]
+
+
+class vga_batch_stats(C.Structure):
+    _fields_ = [("instances", C.c_int32), ("grid_blocks", C.c_int32), ("total_nodes", C.c_int64),
+                ("steps_per_launch", C.c_int32), ("capture_failed", C.c_int32), ("kernel_launches", C.c_int64),
+                ("graph_replays", C.c_int64), ("steps_done", C.c_int64)]
+
+
+class vga_batch_tune_entry(C.Structure):
+    _fields_ = [("steps_per_launch", C.c_int32), ("blocks_per_sm", C.c_int32), ("grid_blocks", C.c_int32),
+                ("pad", C.c_int32), ("ms_per_step", C.c_double)]
+
+
+class vga_batch_tune(C.Structure):
+    _fields_ = [("count", C.c_int32), ("best", C.c_int32), ("entries", vga_batch_tune_entry * 16)]
+
+
 class vga_sim_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("cg_iterations", C.c_int64),
                 ("cg_last_relres", C.c_double), ("kernel_launches", C.c_int64)]
@@ -92,9 +115,23 @@ _SIGNATURES = {
     "vga_adjoint_forward": [_P, _I64, _I32],
     "vga_adjoint_backward": [_P, _P, _I32, _P, _P, _P],
     "vga_loss_block_mass": [_P, _I32, _U32, _P, _P, _P, _P],
+    "vga_sgd_block_conductances": [_P, C.c_double, C.c_double, C.c_double],
+    "vga_sim_get_block_conductances": [_P, _P, _I64],
+    "vga_sim_set_kernel": [_P, _I32, _I32],
+    "vga_sim_autotune": [_P, _I32, _P],
     "vga_sim_enable_timing": [_P, _I32],
     "vga_sim_read_timing": [_P, _P, _I32],
     "vga_sim_free": [_P],
+    "vga_batch_create": [_P, _P, _I32, _P],
+    "vga_batch_info": [_P, _P, _P],
+    "vga_batch_set_masses": [_P, _I32, _P],
+    "vga_batch_get_masses": [_P, _I32, _P],
+    "vga_batch_step": [_P, _I64],
+    "vga_batch_set_launch": [_P, _I32, _I32, _I32],
+    "vga_batch_get_stats": [_P, _P],
+    "vga_batch_autotune": [_P, _I32, _P],
+    "vga_batch_free": [_P],
+    "vga_state_totals_noalloc": [_P, _P, _I64, _I64, _P, _P],
 }
 _RESTYPES = {"vga_strerror": C.c_char_p, "vga_last_error": C.c_char_p, "vga_version": C.c_int32}
 
@@ -338,6 +375,30 @@ def vga_loss_block_mass(s, block_side: int, comp_mask: int, target: np.ndarray, 
     return loss.value, mass
 
 
+def vga_sim_set_kernel(s, variant: int, chunk: int):
+    _check(load_library().vga_sim_set_kernel(s, int(variant), int(chunk)), "vga_sim_set_kernel")
+
+
+def vga_sim_autotune(s, trial_steps: int = 20) -> dict:
+    r = vga_tune_result()
+    _check(load_library().vga_sim_autotune(s, int(trial_steps), C.byref(r)), "vga_sim_autotune")
+    entries = [dict(variant=r.entries[k].variant, chunk=r.entries[k].chunk, ms_per_step=r.entries[k].ms_per_step)
+               for k in range(r.count)]
+    return dict(best=entries[r.best] if r.best >= 0 else None, entries=entries)
+
+
+def vga_sgd_block_conductances(s, lr: float, theta_min: float, theta_max: float):
+    _check(load_library().vga_sgd_block_conductances(s, float(lr), float(theta_min), float(theta_max)),
+           "vga_sgd_block_conductances")
+
+
+def vga_sim_get_block_conductances(s, n_theta: int) -> np.ndarray:
+    out = np.empty(n_theta, dtype=np.float32)
+    _check(load_library().vga_sim_get_block_conductances(s, _host_ptr(out, np.float32), n_theta),
+           "vga_sim_get_block_conductances")
+    return out
+
+
 def vga_sim_enable_timing(s, on: bool = True):
     _check(load_library().vga_sim_enable_timing(s, 1 if on else 0), "vga_sim_enable_timing")
 
@@ -351,6 +412,75 @@ def vga_sim_read_timing(s, reset: bool = False) -> dict:
 
 def vga_sim_free(s):
     _check(load_library().vga_sim_free(s), "vga_sim_free")
+
+
+def vga_state_totals_noalloc(values, residuals, n: int, row_stride: int, totals, stream=None):
+    """values / residuals / totals are CUDA tensors (float32; 16-bit residual bits or None;
+    float64 with 5 entries); the call allocates nothing."""
+    import torch
+
+    if not (isinstance(values, torch.Tensor) and values.is_cuda and values.dtype == torch.float32):
+        raise TypeError("values must be a CUDA float32 tensor")
+    if residuals is not None and not (isinstance(residuals, torch.Tensor) and residuals.is_cuda
+                                      and residuals.element_size() == 2):
+        raise TypeError("residuals must be a CUDA tensor of 16-bit elements")
+    if not (isinstance(totals, torch.Tensor) and totals.is_cuda and totals.dtype == torch.float64):
+        raise TypeError("totals must be a CUDA float64 tensor")
+    _check(load_library().vga_state_totals_noalloc(values.data_ptr(), None if residuals is None else residuals.data_ptr(),
+                                                   int(n), int(row_stride), totals.data_ptr(), _stream_ptr(stream)),
+           "vga_state_totals_noalloc")
+
+
+def vga_batch_create(graph_handles, params_list) -> C.c_void_p:
+    count = len(graph_handles)
+    arr = (C.c_void_p * count)(*[g.value if isinstance(g, C.c_void_p) else g for g in graph_handles])
+    parr = (vga_params * count)(*[make_params(p) for p in params_list])
+    out = C.c_void_p()
+    _check(load_library().vga_batch_create(arr, parr, count, C.byref(out)), "vga_batch_create")
+    return out
+
+
+def vga_batch_info(b, count: int):
+    tot = C.c_int64()
+    offs = np.zeros(count, dtype=np.int64)
+    _check(load_library().vga_batch_info(b, C.byref(tot), offs.ctypes.data_as(C.c_void_p)), "vga_batch_info")
+    return tot.value, offs
+
+
+def vga_batch_set_masses(b, instance: int, x: np.ndarray):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    _check(load_library().vga_batch_set_masses(b, int(instance), x.ctypes.data_as(C.c_void_p)), "vga_batch_set_masses")
+
+
+def vga_batch_get_masses(b, instance: int, out: np.ndarray):
+    _check(load_library().vga_batch_get_masses(b, int(instance), _host_ptr(out, np.float64)), "vga_batch_get_masses")
+
+
+def vga_batch_step(b, n_steps: int):
+    _check(load_library().vga_batch_step(b, int(n_steps)), "vga_batch_step")
+
+
+def vga_batch_set_launch(b, steps_per_launch: int, blocks_per_sm: int = 0, use_graph: bool = True):
+    _check(load_library().vga_batch_set_launch(b, int(steps_per_launch), int(blocks_per_sm), 1 if use_graph else 0),
+           "vga_batch_set_launch")
+
+
+def vga_batch_get_stats(b) -> dict:
+    st = vga_batch_stats()
+    _check(load_library().vga_batch_get_stats(b, C.byref(st)), "vga_batch_get_stats")
+    return {k: getattr(st, k) for k, _ in vga_batch_stats._fields_}
+
+
+def vga_batch_autotune(b, trial_steps: int = 50) -> dict:
+    r = vga_batch_tune()
+    _check(load_library().vga_batch_autotune(b, int(trial_steps), C.byref(r)), "vga_batch_autotune")
+    entries = [dict(steps_per_launch=r.entries[k].steps_per_launch, blocks_per_sm=r.entries[k].blocks_per_sm,
+                    grid_blocks=r.entries[k].grid_blocks, ms_per_step=r.entries[k].ms_per_step) for k in range(r.count)]
+    return dict(best=entries[r.best] if r.best >= 0 else None, entries=entries)
+
+
+def vga_batch_free(b):
+    _check(load_library().vga_batch_free(b), "vga_batch_free")
 
 
 # ---- handle classes (ownership only) ------------------------------------------------------------
@@ -396,10 +526,12 @@ class Sim:
     def __init__(self, graph: Graph, params: dict, stream=None):
         self.graph = graph
         self.n = graph.n
+        self._base_params = dict(params)
         self.handle = vga_sim_create(graph.handle, params, stream)
 
     def set_params(self, params: dict):
         vga_sim_set_params(self.handle, params)
+        self._base_params = dict(params)
 
     def set_block_conductances(self, block_side: int, theta):
         vga_sim_set_block_conductances(self.handle, block_side, theta)
@@ -445,6 +577,12 @@ class Sim:
     def stats(self) -> dict:
         return vga_sim_get_stats(self.handle)
 
+    def set_kernel(self, variant: int, chunk: int):
+        vga_sim_set_kernel(self.handle, variant, chunk)
+
+    def autotune(self, trial_steps: int = 20) -> dict:
+        return vga_sim_autotune(self.handle, trial_steps)
+
     def adjoint_forward(self, n_steps: int, ckpt_every: int = 100):
         vga_adjoint_forward(self.handle, n_steps, ckpt_every)
 
@@ -453,6 +591,12 @@ class Sim:
 
     def loss_block_mass(self, block_side: int, comp_mask: int, target, dL_dX=None, want_mass: bool = False):
         return vga_loss_block_mass(self.handle, block_side, comp_mask, target, self.n, dL_dX, want_mass)
+
+    def sgd_block_conductances(self, lr: float, theta_min: float, theta_max: float):
+        vga_sgd_block_conductances(self.handle, lr, theta_min, theta_max)
+
+    def get_block_conductances(self, n_theta: int) -> np.ndarray:
+        return vga_sim_get_block_conductances(self.handle, n_theta)
 
     def enable_timing(self, on: bool = True):
         vga_sim_enable_timing(self.handle, on)
@@ -463,6 +607,47 @@ class Sim:
     def close(self):
         if self.handle:
             vga_sim_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Owns a vga_batch handle over several Graphs (which must stay alive)."""
+
+    def __init__(self, graphs, params_list):
+        self.graphs = list(graphs)
+        self.sizes = [g.n for g in self.graphs]
+        self.handle = vga_batch_create([g.handle for g in self.graphs], params_list)
+        self.total_nodes, self.offsets = vga_batch_info(self.handle, len(self.graphs))
+
+    def set_masses(self, k: int, x):
+        vga_batch_set_masses(self.handle, k, x)
+
+    def get_masses(self, k: int) -> np.ndarray:
+        out = np.empty((5, self.sizes[k]), dtype=np.float64)
+        vga_batch_get_masses(self.handle, k, out)
+        return out
+
+    def step(self, n_steps: int):
+        vga_batch_step(self.handle, n_steps)
+
+    def set_launch(self, steps_per_launch: int, blocks_per_sm: int = 0, use_graph: bool = True):
+        vga_batch_set_launch(self.handle, steps_per_launch, blocks_per_sm, use_graph)
+
+    def stats(self) -> dict:
+        return vga_batch_get_stats(self.handle)
+
+    def autotune(self, trial_steps: int = 50) -> dict:
+        return vga_batch_autotune(self.handle, trial_steps)
+
+    def close(self):
+        if self.handle:
+            vga_batch_free(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -526,4 +526,28 @@ vga_status sim_block_mass_loss(vga_sim *s, int32_t bs, uint32_t comp_mask, const
     return VGA_OK;
 }
 
+// Normalised (element-wise sign) gradient step on the block conductances, Sec. V.A:
+// theta <- clamp(theta - lr * g / |g|, lo, hi), with g / |g| = 0 where g = 0.
+__global__ void k_sgd_sign(int64_t n, float *__restrict__ theta, const double *__restrict__ g, double lr, double lo,
+                           double hi) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double gk = g[k];
+    const double sgn = gk > 0.0 ? 1.0 : (gk < 0.0 ? -1.0 : 0.0);
+    double t = (double)theta[k] - lr * sgn;
+    t = t < lo ? lo : (t > hi ? hi : t);
+    theta[k] = (float)t;
+}
+
+vga_status sim_sgd_theta(vga_sim *s, double lr, double lo, double hi) {
+    if (!s->adj || !s->adj->valid) return fail(VGA_ERR_INVALID_ARG, "no adjoint gradient to step along");
+    if (s->wmode != W_BLOCK || s->n_theta == 0) return fail(VGA_ERR_INVALID_ARG, "no block conductances set");
+    k_sgd_sign<<<(unsigned)((s->n_theta + 255) / 256), 256, 0, s->stream>>>(s->n_theta, s->theta, s->adj->gtheta, lr, lo,
+                                                                          hi);
+    VGA_CHECK_LAUNCH();
+    ++s->launches;
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    return VGA_OK;
+}
+
 }  // namespace vga

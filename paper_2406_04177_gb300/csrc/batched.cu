@@ -1,0 +1,570 @@
+// Batched simulation of many independent subvolumes (uneven node counts, per-instance parameters)
+// in one persistent kernel per launch.
+//
+// Layout: the instances' nodes are concatenated, each instance starting at a multiple of 256 nodes
+// (kTile), so a 256-node tile never straddles two instances and carries one instance id.  Every
+// instance keeps its own neighbour-offset table (offsets are relative, so they remain valid in the
+// concatenated index space) and its own StepParams.
+//
+// A launch runs passes [pass0, pass1) of a step() call of N time steps (N + 1 passes: one
+// transformation-only pass, N - 1 fused passes, one diffusion-only pass; see step.cu).  Passes are
+// separated by a grid-wide barrier; the launch is cooperative, so every block is resident, and
+// every wait in the barrier is bounded (VGA_ERR_TIMEOUT instead of a hang).  The launches of a
+// step() call are captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "physics.cuh"
+#include "stencil.cuh"
+#include "vga_internal.cuh"
+
+namespace vga {
+namespace {
+
+constexpr int kTile = 256;
+constexpr uint32_t kBarrierSpin = 1u << 26;
+
+struct BInst {
+    int64_t start;  // first node of the instance in the concatenated range (multiple of kTile)
+    int64_t n;      // node count
+    StepParams p;
+};
+
+struct BatchArgs {
+    int64_t ntiles;
+    int64_t npad;
+    const int32_t *tile_inst;  // instance of every tile
+    const BInst *inst;
+    NbrTable tb;
+    float *h[2];
+    uint16_t *l[2];
+    unsigned *bar;  // [0] arrivals, [1] generation
+    int32_t *err;
+};
+
+// Grid-wide barrier for a cooperative launch.  Bounded: on timeout (or an earlier error) it sets
+// *err and returns false; callers then stop.
+__device__ bool grid_barrier(unsigned *bar, int32_t *err) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ok = 1;
+        volatile unsigned *vgen = bar + 1;
+        volatile int32_t *verr = err;
+        if (*verr) {
+            ok = 0;
+        } else {
+            const unsigned gen = *vgen;
+            __threadfence();
+            const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+            if (arrived == gridDim.x) {
+                bar[0] = 0u;
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                uint32_t it = 0;
+                while (*vgen == gen) {
+                    if (*verr || ++it > kBarrierSpin) {
+                        atomicExch(err, 2);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <int TR, int PREC>
+__global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
+    for (int32_t pass = pass0; pass < pass1; ++pass) {
+        const int kind = (pass == 0) ? 0 : (pass == npass - 1 ? 2 : 1);  // transform / fused / diffuse
+        const int bi = (cur0 + pass) & 1, bo = bi ^ 1;
+        const float *__restrict__ Y2 = a.h[bi] + a.npad;
+        for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+            const BInst &ins = a.inst[__ldg(a.tile_inst + tile)];
+            const uint32_t i = (uint32_t)(tile * kTile + threadIdx.x);
+            const bool live = (int64_t)i - ins.start < ins.n;
+            const StepParams p = ins.p;
+            V x[5];
+            if (kind == 0) {
+                if (!live) continue;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) x[c] = vload<PREC>(a.h[bi] + c * a.npad, a.l[bi] + c * a.npad, i);
+                transform<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
+            } else {
+                const uint32_t ty = live ? __ldg(a.tb.ty + i) : 0u;
+                const uint32_t dzm = live ? __ldg(a.tb.tzm + i) : 0u;
+                const uint32_t dzp = live ? __ldg(a.tb.tzp + i) : 0u;
+                x[1] = live ? vload<PREC>(Y2, a.l[bi] + a.npad, i) : V{0.0f, 0.0f};
+                const float yi = x[1].h;
+                const int lane = threadIdx.x & 31;
+                float yl = __shfl_up_sync(0xffffffffu, yi, 1);
+                float yr = __shfl_down_sync(0xffffffffu, yi, 1);
+                const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
+                const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
+                if (lane == 0 && hxm) yl = __ldg(Y2 + (i - 1));
+                if (lane == 31 && hxp) yr = __ldg(Y2 + (i + 1));
+                float ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
+                if (dym) ym = __ldg(Y2 + (i - dym));
+                if (dyp) yp = __ldg(Y2 + (i + dyp));
+                if (dzm) zm = __ldg(Y2 + (i - dzm));
+                if (dzp) zp = __ldg(Y2 + (i + dzp));
+                if (!live) continue;
+                float acc = 0.0f;
+                if (hxm) acc = __fadd_rn(acc, __fsub_rn(yi, yl));
+                if (hxp) acc = __fadd_rn(acc, __fsub_rn(yi, yr));
+                if (dym) acc = __fadd_rn(acc, __fsub_rn(yi, ym));
+                if (dyp) acc = __fadd_rn(acc, __fsub_rn(yi, yp));
+                if (dzm) acc = __fadd_rn(acc, __fsub_rn(yi, zm));
+                if (dzp) acc = __fadd_rn(acc, __fsub_rn(yi, zp));
+                vadd<PREC>(x[1], __fmul_rn(-p.c, acc));
+                x[0] = vload<PREC>(a.h[bi], a.l[bi], i);
+                x[2] = vload<PREC>(a.h[bi] + 2 * a.npad, a.l[bi] + 2 * a.npad, i);
+                x[3] = vload<PREC>(a.h[bi] + 3 * a.npad, a.l[bi] + 3 * a.npad, i);
+                x[4] = vload<PREC>(a.h[bi] + 4 * a.npad, a.l[bi] + 4 * a.npad, i);
+                if (kind == 1) {
+                    vround<PREC>(x[1]);
+                    transform<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 5; ++c) vstore<PREC>(a.h[bo] + c * a.npad, a.l[bo] + c * a.npad, i, x[c]);
+        }
+        if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err)) return;
+    }
+}
+
+// FP64 (5 x n) of one instance <-> its slice of the current state buffer
+__global__ void k_batch_in(int64_t n, const double *__restrict__ x, float *h, uint16_t *l, int64_t start,
+                           int64_t npad, int comp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < 5; ++c) {
+        const double v = x[c * n + i];
+        const float hv = (float)v;
+        h[c * npad + start + i] = hv;
+        l[c * npad + start + i] = comp ? float_to_bf16_bits((float)(v - (double)hv)) : 0;
+    }
+}
+
+__global__ void k_batch_out(int64_t n, double *__restrict__ x, const float *h, const uint16_t *l, int64_t start,
+                            int64_t npad, int comp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int c = 0; c < 5; ++c) {
+        double v = (double)h[c * npad + start + i];
+        if (comp) v += (double)bf16_bits_to_float(l[c * npad + start + i]);
+        x[c * n + i] = v;
+    }
+}
+
+}  // namespace
+}  // namespace vga
+
+using namespace vga;
+
+struct vga_batch {
+    int32_t count = 0;
+    std::vector<int64_t> start, nodes;
+    int64_t total = 0, npad = 0, ntiles = 0;
+    int transform = 0, precision = 0;
+    cudaStream_t stream = nullptr;
+    float *h[2] = {nullptr, nullptr};
+    uint16_t *l[2] = {nullptr, nullptr};
+    uint32_t *table = nullptr;  // 3 x npad
+    int32_t *tile_inst = nullptr;
+    BInst *inst = nullptr;
+    unsigned *bar = nullptr;
+    int32_t *err = nullptr;
+    double *stage = nullptr;
+    int64_t stage_n = 0;
+    int cur = 0;
+    int grid = 0;          // blocks of a launch (resident on every SM)
+    int blocks_per_sm = 0;  // tuning knob (0: the occupancy maximum)
+    int steps_per_launch = 100;
+    bool use_graph = true;
+    bool capture_failed = false;
+    std::map<std::tuple<int64_t, int, int, int>, cudaGraphExec_t> graphs;
+    int64_t launches = 0, graph_replays = 0, steps_done = 0;
+};
+
+namespace {
+
+vga_status batch_grid(vga_batch *b) {
+    int dev = 0, sms = 0, per_sm = 0;
+    VGA_CUDA(cudaGetDevice(&dev));
+    VGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const void *fn = b->transform == 0 ? (b->precision == P_COMP ? (const void *)k_batch<0, P_COMP> : (const void *)k_batch<0, P_F32>)
+                                       : (b->precision == P_COMP ? (const void *)k_batch<1, P_COMP> : (const void *)k_batch<1, P_F32>);
+    VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTile, 0));
+    if (per_sm < 1) return fail(VGA_ERR_CUDA, "batched kernel cannot be resident");
+    const int want = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, per_sm) : per_sm;
+    b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)want * sms, b->ntiles));
+    return VGA_OK;
+}
+
+vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
+    BatchArgs a;
+    a.ntiles = b->ntiles;
+    a.npad = b->npad;
+    a.tile_inst = b->tile_inst;
+    a.inst = b->inst;
+    a.tb.ty = b->table;
+    a.tb.tzm = b->table + b->npad;
+    a.tb.tzp = b->table + 2 * b->npad;
+    for (int k = 0; k < 2; ++k) {
+        a.h[k] = b->h[k];
+        a.l[k] = b->l[k];
+    }
+    a.bar = b->bar;
+    a.err = b->err;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)b->grid);
+    cfg.blockDim = dim3(kTile);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (b->transform == 0) {
+        if (b->precision == P_COMP) e = cudaLaunchKernelEx(&cfg, k_batch<0, P_COMP>, a, pass0, pass1, npass, cur0);
+        else e = cudaLaunchKernelEx(&cfg, k_batch<0, P_F32>, a, pass0, pass1, npass, cur0);
+    } else {
+        if (b->precision == P_COMP) e = cudaLaunchKernelEx(&cfg, k_batch<1, P_COMP>, a, pass0, pass1, npass, cur0);
+        else e = cudaLaunchKernelEx(&cfg, k_batch<1, P_F32>, a, pass0, pass1, npass, cur0);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of k_batch", __FILE__, __LINE__);
+    return VGA_OK;
+}
+
+vga_status enqueue_steps(vga_batch *b, int64_t n_steps, int cur0) {
+    const int64_t npass = n_steps + 1;
+    const int S = std::max(1, b->steps_per_launch);
+    for (int64_t p0 = 0; p0 < npass; p0 += S) {
+        const int64_t p1 = std::min(npass, p0 + S);
+        VGA_TRY(launch_batch(b, (int32_t)p0, (int32_t)p1, (int32_t)npass, cur0));
+    }
+    return VGA_OK;
+}
+
+vga_status check_err(vga_batch *b) {
+    int32_t h = 0;
+    VGA_CUDA(cudaMemcpyAsync(&h, b->err, sizeof(int32_t), cudaMemcpyDeviceToHost, b->stream));
+    VGA_CUDA(cudaStreamSynchronize(b->stream));
+    if (h) {
+        cudaMemsetAsync(b->err, 0, sizeof(int32_t), b->stream);
+        cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), b->stream);
+        cudaStreamSynchronize(b->stream);
+        return fail(VGA_ERR_TIMEOUT, "a grid barrier of the batched kernel timed out");
+    }
+    return VGA_OK;
+}
+
+void drop_graphs(vga_batch *b) {
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+vga_status vga_batch_free(vga_batch *b) {
+    if (!b) return VGA_OK;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    for (int k = 0; k < 2; ++k) {
+        dfree(b->h[k]);
+        dfree(b->l[k]);
+    }
+    dfree(b->table);
+    dfree(b->tile_inst);
+    dfree(b->inst);
+    dfree(b->bar);
+    dfree(b->err);
+    dfree(b->stage);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return VGA_OK;
+}
+
+vga_status vga_batch_create(const vga_graph *const *graphs, const vga_params *params, int32_t count,
+                            vga_batch **out) {
+    if (!out) return fail(VGA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!graphs || !params || count < 1) return fail(VGA_ERR_INVALID_ARG, "need count >= 1 graphs and params");
+    for (int k = 0; k < count; ++k) {
+        const vga_params &p = params[k];
+        if (!graphs[k]) return fail(VGA_ERR_INVALID_ARG, "a graph is NULL");
+        if (p.scheme != VGA_SCHEME_EXPLICIT) return fail(VGA_ERR_UNSUPPORTED, "the batched path runs the explicit scheme");
+        if (p.transform != params[0].transform || p.state_precision != params[0].state_precision)
+            return fail(VGA_ERR_INVALID_ARG, "all instances must share transform and state_precision");
+        if (graphs[k]->nx > 32767) return fail(VGA_ERR_UNSUPPORTED, "batched instances need nx <= 32767");
+        if (!(std::isfinite(p.dt) && p.dt > 0 && std::isfinite(p.D) && p.D >= 0 && p.K_dom > 0 && p.beta >= 0 &&
+              p.beta <= 1 && p.rho >= 0 && p.mu >= 0 && p.v_som >= 0 && p.v_fom >= 0 && p.v_dom >= 0))
+            return fail(VGA_ERR_INVALID_ARG, "invalid parameters of an instance");
+        if (6.0 * p.D * p.dt > 1.0 + 1e-12) return fail(VGA_ERR_UNSTABLE_DT, "an instance has 6 D dt > 1");
+    }
+    vga_batch *b = new (std::nothrow) vga_batch();
+    if (!b) return fail(VGA_ERR_OOM, "host allocation failed");
+    b->count = count;
+    b->transform = params[0].transform;
+    b->precision = params[0].state_precision;
+    vga_status st = VGA_OK;
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+        st = fail(VGA_ERR_CUDA, "cudaStreamCreate failed");
+    int64_t off = 0;
+    std::vector<int32_t> tinst;
+    std::vector<BInst> hinst(count);
+    for (int k = 0; k < count && st == VGA_OK; ++k) {
+        b->start.push_back(off);
+        b->nodes.push_back(graphs[k]->n);
+        hinst[k].start = off;
+        hinst[k].n = graphs[k]->n;
+        vga_sim tmp;
+        sim_prepare_params(&tmp, &params[k]);
+        hinst[k].p = tmp.sp;
+        const int64_t tiles = (graphs[k]->n + kTile - 1) / kTile;
+        for (int64_t t = 0; t < tiles; ++t) tinst.push_back(k);
+        off += tiles * kTile;
+    }
+    b->total = off;
+    b->ntiles = off / kTile;
+    b->npad = std::max<int64_t>(64, ((off + 63) / 64) * 64);
+    const size_t hb = sizeof(float) * 5 * (size_t)b->npad, lb = sizeof(uint16_t) * 5 * (size_t)b->npad;
+    for (int k = 0; k < 2 && st == VGA_OK; ++k) {
+        st = dmalloc((void **)&b->h[k], hb, "batch state");
+        if (st == VGA_OK) st = dmalloc((void **)&b->l[k], lb, "batch state residuals");
+    }
+    if (st == VGA_OK) st = dmalloc((void **)&b->table, sizeof(uint32_t) * 3 * (size_t)b->npad, "batch table");
+    if (st == VGA_OK) st = dmalloc((void **)&b->tile_inst, sizeof(int32_t) * std::max<size_t>(tinst.size(), 1), "tile map");
+    if (st == VGA_OK) st = dmalloc((void **)&b->inst, sizeof(BInst) * (size_t)count, "instances");
+    if (st == VGA_OK) st = dmalloc((void **)&b->bar, sizeof(unsigned) * 2, "barrier");
+    if (st == VGA_OK) st = dmalloc((void **)&b->err, sizeof(int32_t), "error flag");
+    if (st == VGA_OK) {
+        cudaError_t e = cudaSuccess;
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            e = cudaMemsetAsync(b->h[k], 0, hb, b->stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(b->l[k], 0, lb, b->stream);
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->table, 0, sizeof(uint32_t) * 3 * (size_t)b->npad, b->stream);
+        if (e == cudaSuccess && !tinst.empty())
+            e = cudaMemcpyAsync(b->tile_inst, tinst.data(), sizeof(int32_t) * tinst.size(), cudaMemcpyHostToDevice,
+                                b->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->inst, hinst.data(), sizeof(BInst) * (size_t)count, cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * 2, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->err, 0, sizeof(int32_t), b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "batch set-up", __FILE__, __LINE__);
+    }
+    for (int k = 0; k < count && st == VGA_OK; ++k) {
+        const int64_t s0 = b->start[k];
+        st = build_nbr_table(graphs[k]->topo(), b->table + s0, b->table + b->npad + s0, b->table + 2 * b->npad + s0,
+                             b->stream);
+    }
+    if (st == VGA_OK) st = batch_grid(b);
+    if (st != VGA_OK) {
+        vga_batch_free(b);
+        return st;
+    }
+    *out = b;
+    return VGA_OK;
+}
+
+vga_status vga_batch_info(const vga_batch *b, int64_t *total_nodes, int64_t *node_offsets) {
+    if (!b) return fail(VGA_ERR_INVALID_ARG, "batch is NULL");
+    if (total_nodes) {
+        int64_t t = 0;
+        for (int64_t v : b->nodes) t += v;
+        *total_nodes = t;
+    }
+    if (node_offsets)
+        for (int k = 0; k < b->count; ++k) node_offsets[k] = b->start[k];
+    return VGA_OK;
+}
+
+static vga_status batch_stage(vga_batch *b, int64_t n) {
+    if (b->stage_n < n) {
+        dfree(b->stage);
+        b->stage = nullptr;
+        b->stage_n = 0;
+        VGA_TRY(dmalloc((void **)&b->stage, sizeof(double) * 5 * (size_t)std::max<int64_t>(n, 1), "batch stage"));
+        b->stage_n = n;
+    }
+    return VGA_OK;
+}
+
+vga_status vga_batch_set_masses(vga_batch *b, int32_t instance, const double *x) {
+    if (!b || instance < 0 || instance >= b->count) return fail(VGA_ERR_INVALID_ARG, "bad batch or instance");
+    const int64_t n = b->nodes[instance];
+    if (n == 0) return VGA_OK;
+    if (!x) return fail(VGA_ERR_INVALID_ARG, "x is NULL");
+    for (int64_t k = 0; k < 5 * n; ++k)
+        if (!std::isfinite(x[k])) return fail(VGA_ERR_NONFINITE, "non-finite value in the input masses");
+    VGA_TRY(batch_stage(b, n));
+    VGA_CUDA(cudaMemcpyAsync(b->stage, x, sizeof(double) * 5 * (size_t)n, cudaMemcpyHostToDevice, b->stream));
+    k_batch_in<<<(unsigned)((n + 255) / 256), 256, 0, b->stream>>>(n, b->stage, b->h[b->cur], b->l[b->cur],
+                                                                  b->start[instance], b->npad, b->precision == P_COMP);
+    VGA_CHECK_LAUNCH();
+    VGA_CUDA(cudaStreamSynchronize(b->stream));
+    return VGA_OK;
+}
+
+vga_status vga_batch_get_masses(vga_batch *b, int32_t instance, double *x) {
+    if (!b || instance < 0 || instance >= b->count) return fail(VGA_ERR_INVALID_ARG, "bad batch or instance");
+    const int64_t n = b->nodes[instance];
+    if (n == 0) return VGA_OK;
+    if (!x) return fail(VGA_ERR_INVALID_ARG, "x is NULL");
+    VGA_TRY(batch_stage(b, n));
+    k_batch_out<<<(unsigned)((n + 255) / 256), 256, 0, b->stream>>>(n, b->stage, b->h[b->cur], b->l[b->cur],
+                                                                   b->start[instance], b->npad, b->precision == P_COMP);
+    VGA_CHECK_LAUNCH();
+    VGA_CUDA(cudaMemcpyAsync(x, b->stage, sizeof(double) * 5 * (size_t)n, cudaMemcpyDeviceToHost, b->stream));
+    VGA_CUDA(cudaStreamSynchronize(b->stream));
+    return VGA_OK;
+}
+
+vga_status vga_batch_set_launch(vga_batch *b, int32_t steps_per_launch, int32_t blocks_per_sm, int32_t use_graph) {
+    if (!b || steps_per_launch < 1 || blocks_per_sm < 0) return fail(VGA_ERR_INVALID_ARG, "bad launch settings");
+    b->steps_per_launch = steps_per_launch;
+    b->blocks_per_sm = blocks_per_sm;
+    b->use_graph = use_graph != 0;
+    drop_graphs(b);
+    return batch_grid(b);
+}
+
+vga_status vga_batch_step(vga_batch *b, int64_t n_steps) {
+    if (!b || n_steps < 0) return fail(VGA_ERR_INVALID_ARG, "bad batch or n_steps");
+    if (n_steps == 0 || b->ntiles == 0) return VGA_OK;
+    if (n_steps + 1 > (int64_t)INT32_MAX) return fail(VGA_ERR_INVALID_ARG, "n_steps too large for one call");
+    const int cur0 = b->cur;
+    if (b->use_graph) {
+        const auto key = std::make_tuple(n_steps, b->steps_per_launch, b->grid, cur0);
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end()) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            VGA_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            const vga_status st = enqueue_steps(b, n_steps, cur0);
+            const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
+            cudaError_t ei = cudaErrorUnknown;
+            if (st == VGA_OK && ec == cudaSuccess) ei = cudaGraphInstantiate(&exec, graph, 0);
+            if (graph) cudaGraphDestroy(graph);
+            if (st == VGA_OK && ec == cudaSuccess && ei == cudaSuccess) {
+                it = b->graphs.emplace(key, exec).first;
+            } else {
+                // capture of the cooperative launches failed: run them directly from now on
+                cudaGetLastError();
+                b->use_graph = false;
+                b->capture_failed = true;
+            }
+        }
+        if (it != b->graphs.end()) {
+            VGA_CUDA(cudaGraphLaunch(it->second, b->stream));
+            ++b->graph_replays;
+        } else {
+            VGA_TRY(enqueue_steps(b, n_steps, cur0));
+        }
+    } else {
+        VGA_TRY(enqueue_steps(b, n_steps, cur0));
+    }
+    b->launches += (n_steps + 1 + b->steps_per_launch - 1) / b->steps_per_launch;
+    b->cur = (int)((cur0 + n_steps + 1) & 1);
+    b->steps_done += n_steps;
+    return check_err(b);
+}
+
+vga_status vga_batch_get_stats(const vga_batch *b, vga_batch_stats *out) {
+    if (!b || !out) return fail(VGA_ERR_INVALID_ARG, "batch or out is NULL");
+    out->instances = b->count;
+    out->total_nodes = 0;
+    for (int64_t v : b->nodes) out->total_nodes += v;
+    out->grid_blocks = b->grid;
+    out->steps_per_launch = b->steps_per_launch;
+    out->kernel_launches = b->launches;
+    out->graph_replays = b->graph_replays;
+    out->steps_done = b->steps_done;
+    out->capture_failed = b->capture_failed ? 1 : 0;
+    return VGA_OK;
+}
+
+vga_status vga_batch_autotune(vga_batch *b, int32_t trial_steps, vga_batch_tune *out) {
+    if (!b || !out || trial_steps < 2) return fail(VGA_ERR_INVALID_ARG, "bad batch, out or trial_steps");
+    static const int kSteps[] = {25, 100, 400};
+    static const int kBlocks[] = {0, 4, 2};
+    const int keep_s = b->steps_per_launch, keep_b = b->blocks_per_sm;
+    // save the state (both buffers' current side) so the trials leave it untouched
+    float *h = nullptr;
+    uint16_t *l = nullptr;
+    VGA_TRY(dmalloc((void **)&h, sizeof(float) * 5 * (size_t)b->npad, "autotune snapshot"));
+    vga_status st = dmalloc((void **)&l, sizeof(uint16_t) * 5 * (size_t)b->npad, "autotune snapshot");
+    const int cur_keep = b->cur;
+    const int64_t steps_keep = b->steps_done, launches_keep = b->launches, replays_keep = b->graph_replays;
+    if (st == VGA_OK) {
+        cudaMemcpyAsync(h, b->h[b->cur], sizeof(float) * 5 * (size_t)b->npad, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(l, b->l[b->cur], sizeof(uint16_t) * 5 * (size_t)b->npad, cudaMemcpyDeviceToDevice, b->stream);
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    out->count = 0;
+    out->best = -1;
+    double best = 1e300;
+    for (int si = 0; si < 3 && st == VGA_OK; ++si) {
+        for (int bi = 0; bi < 3 && st == VGA_OK; ++bi) {
+            if (out->count >= VGA_TUNE_MAX) break;
+            st = vga_batch_set_launch(b, kSteps[si], kBlocks[bi], 1);
+            if (st == VGA_OK) st = vga_batch_step(b, trial_steps);  // capture + warm-up
+            cudaEventRecord(e0, b->stream);
+            if (st == VGA_OK) st = vga_batch_step(b, trial_steps);
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (st != VGA_OK) break;
+            vga_batch_tune_entry &en = out->entries[out->count];
+            en.steps_per_launch = kSteps[si];
+            en.blocks_per_sm = kBlocks[bi];
+            en.grid_blocks = b->grid;
+            en.ms_per_step = ms / trial_steps;
+            if (ms < best) {
+                best = ms;
+                out->best = out->count;
+            }
+            ++out->count;
+        }
+    }
+    if (st == VGA_OK && out->best >= 0)
+        st = vga_batch_set_launch(b, out->entries[out->best].steps_per_launch, out->entries[out->best].blocks_per_sm, 1);
+    else
+        vga_batch_set_launch(b, keep_s, keep_b, 1);
+    b->cur = cur_keep;
+    if (h && l) {
+        cudaMemcpyAsync(b->h[b->cur], h, sizeof(float) * 5 * (size_t)b->npad, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(b->l[b->cur], l, sizeof(uint16_t) * 5 * (size_t)b->npad, cudaMemcpyDeviceToDevice, b->stream);
+    }
+    cudaStreamSynchronize(b->stream);
+    b->steps_done = steps_keep;
+    b->launches = launches_keep;
+    b->graph_replays = replays_keep;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dfree(h);
+    dfree(l);
+    return st;
+}
+
+}  // extern "C"

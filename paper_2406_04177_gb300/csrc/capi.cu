@@ -102,6 +102,18 @@ static vga_status harvest_timing(vga_sim *s) {
     return VGA_OK;
 }
 
+// Reads the device error flag written by bounded waits; a nonzero value means a kernel gave up.
+static vga_status check_device_error(vga_sim *s) {
+    int32_t h = 0;
+    VGA_CUDA(cudaMemcpyAsync(&h, s->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    if (h != 0) {
+        cudaMemsetAsync(s->d_err, 0, sizeof(int32_t), s->stream);
+        return fail(VGA_ERR_TIMEOUT, "a bounded device wait timed out (bulk copy did not complete)");
+    }
+    return VGA_OK;
+}
+
 static bool finite_nonneg(double v) { return std::isfinite(v) && v >= 0.0; }
 
 static vga_status validate_params(const vga_params *p, double max_g) {
@@ -276,6 +288,11 @@ vga_status vga_sim_create(const vga_graph *g, const vga_params *p, void *stream,
     for (int b = 0; b < 2 && st == VGA_OK; ++b) st = dmalloc((void **)&s->lbuf[b], lbytes, "state residuals");
     if (st == VGA_OK) st = dmalloc((void **)&s->partials, sizeof(double) * 5 * (size_t)totals_blocks(), "partials");
     if (st == VGA_OK) st = dmalloc((void **)&s->d_totals, sizeof(double) * 8, "totals");
+    if (st == VGA_OK) st = dmalloc((void **)&s->d_err, sizeof(int32_t) * 4, "error flag");
+    if (st == VGA_OK) {
+        const cudaError_t e = cudaMemsetAsync(s->d_err, 0, sizeof(int32_t) * 4, s->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
+    }
     if (st == VGA_OK) {
         const cudaError_t e = cudaMallocHost((void **)&s->h_totals, sizeof(double) * 8);
         if (e != cudaSuccess) st = cuda_fail(e, "cudaMallocHost", __FILE__, __LINE__);
@@ -490,13 +507,14 @@ vga_status vga_sim_step(vga_sim *s, int64_t n_steps) {
 
 vga_status vga_sim_totals(vga_sim *s, double *totals) {
     if (!s || !totals) return fail(VGA_ERR_INVALID_ARG, "sim or totals is NULL");
-    return sim_totals(s, totals);
+    VGA_TRY(sim_totals(s, totals));
+    return check_device_error(s);
 }
 
 vga_status vga_sim_sync(vga_sim *s) {
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
     VGA_CUDA(cudaStreamSynchronize(s->stream));
-    return VGA_OK;
+    return check_device_error(s);
 }
 
 vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out) {
@@ -536,6 +554,27 @@ vga_status vga_adjoint_backward(vga_sim *s, const double *dL_dXN, int32_t on_dev
                                  s->stream));
         VGA_CUDA(cudaStreamSynchronize(s->stream));
     }
+    return VGA_OK;
+}
+
+vga_status vga_sgd_block_conductances(vga_sim *s, double lr, double theta_min, double theta_max) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    if (!(std::isfinite(lr) && lr >= 0.0 && std::isfinite(theta_min) && std::isfinite(theta_max) && theta_min >= 0.0 &&
+          theta_min <= theta_max))
+        return fail(VGA_ERR_INVALID_ARG, "need lr >= 0 and 0 <= theta_min <= theta_max, all finite");
+    if (s->params.scheme == VGA_SCHEME_EXPLICIT && 6.0 * s->params.D * s->params.dt * theta_max > 1.0 + 1e-12)
+        return fail(VGA_ERR_UNSTABLE_DT, "theta_max would make the explicit scheme unstable");
+    VGA_TRY(sim_sgd_theta(s, lr, theta_min, theta_max));
+    s->max_g = (float)std::max(1.0, theta_max);
+    ++s->param_gen;
+    return VGA_OK;
+}
+
+vga_status vga_sim_get_block_conductances(vga_sim *s, float *theta, int64_t n_theta) {
+    if (!s || !theta) return fail(VGA_ERR_INVALID_ARG, "sim or theta is NULL");
+    if (s->wmode != W_BLOCK || n_theta != s->n_theta) return fail(VGA_ERR_INVALID_ARG, "no block conductances of that size");
+    VGA_CUDA(cudaMemcpyAsync(theta, s->theta, sizeof(float) * (size_t)n_theta, cudaMemcpyDeviceToHost, s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
     return VGA_OK;
 }
 
@@ -597,6 +636,8 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->lbuf[1]);
     dfree(s->partials);
     dfree(s->d_totals);
+    dfree(s->d_err);
+    dfree(s->nbr_table);
     if (s->h_totals) cudaFreeHost(s->h_totals);
     dfree(s->stage);
     dfree(s->theta);

@@ -20,6 +20,7 @@
 
 #include "physics.cuh"
 #include "stencil.cuh"
+#include "tma.cuh"
 #include "vga_internal.cuh"
 
 namespace vga {
@@ -86,6 +87,194 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Topo t, const int32_t *__r
         } else {
             vstore<PREC>(io.out[1], io.lout[1], i, x2);
         }
+    }
+}
+
+// Staged variant of k_stencil.  One thread issues bulk asynchronous copies (cp.async.bulk) of the
+// chunk's own contiguous state into shared memory while all threads decode the topology; then
+// every node reads its own values and its in-chunk neighbours (+-x always, +-y mostly) from shared
+// memory and only the remaining neighbours (+-z, chunk edges) from L2.  The results overwrite the
+// staged inputs in shared memory and leave with bulk stores, so the node loop issues no global
+// load or store of its own state.  Arithmetic is identical to k_stencil.
+template <int CAP, int NT>
+struct StagedLayout {
+    static constexpr int kPer = CAP / NT;
+    static constexpr size_t bar = 0;
+    static constexpr size_t h = 16;                                 // 5 x CAP floats
+    static constexpr size_t l = h + sizeof(float) * 5 * CAP;        // 5 x CAP u16
+    static constexpr size_t dec = l + sizeof(uint16_t) * 5 * CAP;   // decode words
+    static constexpr size_t bytes(bool need_yz) { return dec + sizeof(uint32_t) * CAP * decode_words(need_yz); }
+};
+
+template <int MODE, int WM, int TR, int PREC, int CAP, int NT>
+__global__ void __launch_bounds__(NT) k_stencil_staged(Topo t, const int32_t *__restrict__ chunk_row, StepParams p,
+                                                        BlockWeights bw, StateIO io, int32_t *__restrict__ err) {
+    using Ly = StagedLayout<CAP, NT>;
+    extern __shared__ __align__(16) unsigned char sbuf[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sbuf + Ly::bar);
+    float *sh = reinterpret_cast<float *>(sbuf + Ly::h);
+    uint16_t *sl = reinterpret_cast<uint16_t *>(sbuf + Ly::l);
+    uint32_t *s_info = reinterpret_cast<uint32_t *>(sbuf + Ly::dec);
+    int32_t *s_nb = reinterpret_cast<int32_t *>(s_info + CAP);
+    uint32_t *s_yz = s_info + 5 * CAP;
+    constexpr int c0 = (MODE == 1) ? 0 : 1, c1 = (MODE == 1) ? 5 : 2;
+
+    const int64_t v0 = (int64_t)blockIdx.x * CAP;
+    const int32_t nv = (int32_t)min((int64_t)CAP, t.n - v0);
+    const uint32_t nvp = (uint32_t)((nv + 7) & ~7);  // 16-byte multiples; the extra entries are padding
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t per = nvp * 4u + (PREC == P_COMP ? nvp * 2u : 0u);
+        mbar_arrive_expect_tx(bar, per * (uint32_t)(c1 - c0));
+        for (int c = c0; c < c1; ++c) {
+            bulk_g2s(sh + c * CAP, io.in[c] + v0, nvp * 4u, bar);
+            if (PREC == P_COMP) bulk_g2s(sl + c * CAP, io.lin[c] + v0, nvp * 2u, bar);
+        }
+    }
+    int64_t v0d;
+    decode_chunk<WM == W_BLOCK>(t, chunk_row, CAP, s_info, s_nb, s_yz, v0d);
+    const bool ok = mbar_wait_bounded(bar, 0, err, 1);
+
+    const float *__restrict__ Y2 = io.in[1];
+    float *__restrict__ sh2 = sh + CAP;
+    float acc[Ly::kPer];
+#pragma unroll
+    for (int u = 0; u < Ly::kPer; ++u) {
+        const int32_t k = threadIdx.x + u * NT;
+        acc[u] = 0.0f;
+        if (!ok || k >= nv) continue;
+        const uint32_t info = s_info[k];
+        const uint32_t fl = info >> 16;
+        int32_t x = 0, y = 0, z = 0;
+        if (WM == W_BLOCK) {
+            x = (int32_t)(info & 0xffffu);
+            y = (int32_t)(s_yz[k] & 0xffffu);
+            z = (int32_t)(s_yz[k] >> 16);
+        }
+        const int64_t i = v0 + k;
+        const float yi = sh2[k];
+        float a = 0.0f;
+        for_each_neighbour(i, k, fl, s_nb, CAP, [&](int slot, int64_t j) {
+            const int64_t jj = j - v0;
+            const float yj = (jj >= 0 && jj < nv) ? sh2[jj] : __ldg(Y2 + j);
+            const float d = __fsub_rn(yi, yj);
+            if (WM == W_UNIT) a = __fadd_rn(a, d);
+            else a = __fmaf_rn(block_theta(bw, slot, x, y, z), d, a);
+        });
+        acc[u] = a;
+    }
+    __syncthreads();  // every neighbour read of the staged DOM is done: results may overwrite it
+    if (ok) {
+#pragma unroll
+        for (int u = 0; u < Ly::kPer; ++u) {
+            const int32_t k = threadIdx.x + u * NT;
+            if (k >= nv) continue;
+            V x2 = {sh2[k], PREC == P_COMP ? bf16_bits_to_float(sl[CAP + k]) : 0.0f};
+            vadd<PREC>(x2, __fmul_rn(-p.c, acc[u]));
+            V xs[5];
+            if (MODE == 1) {
+                vround<PREC>(x2);
+#pragma unroll
+                for (int c = 0; c < 5; ++c)
+                    if (c != 1) xs[c] = V{sh[c * CAP + k], PREC == P_COMP ? bf16_bits_to_float(sl[c * CAP + k]) : 0.0f};
+                xs[1] = x2;
+                transform<TR, PREC>(xs[0], xs[1], xs[2], xs[3], xs[4], p);
+            } else {
+                xs[1] = x2;
+            }
+#pragma unroll
+            for (int c = c0; c < c1; ++c) {
+                if (PREC == P_COMP) {
+                    const float s = __fadd_rn(xs[c].h, xs[c].l);  // renormalise as vstore does
+                    const float r = __fadd_rn(__fsub_rn(xs[c].h, s), xs[c].l);
+                    sh[c * CAP + k] = s;
+                    sl[c * CAP + k] = float_to_bf16_bits(r);
+                } else {
+                    sh[c * CAP + k] = xs[c].h;
+                }
+            }
+        }
+    }
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0 && ok) {
+        for (int c = c0; c < c1; ++c) {
+            bulk_s2g(io.out[c] + v0, sh + c * CAP, nvp * 4u);
+            if (PREC == P_COMP) bulk_s2g(io.lout[c] + v0, sl + c * CAP, nvp * 2u);
+        }
+        bulk_commit();
+        bulk_wait_read_all();
+    }
+}
+
+// ---- neighbour-offset table ---------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_build_table(Topo t, const int32_t *__restrict__ chunk_row, int32_t cap,
+                                                          uint32_t *__restrict__ ty, uint32_t *__restrict__ tzm,
+                                                          uint32_t *__restrict__ tzp) {
+    extern __shared__ uint32_t smem[];
+    int32_t *s_nb = reinterpret_cast<int32_t *>(smem + cap);
+    int64_t v0;
+    const int32_t nv = decode_chunk<false>(t, chunk_row, cap, smem, s_nb, nullptr, v0);
+    for (int32_t k = threadIdx.x; k < nv; k += blockDim.x) {
+        const int64_t i = v0 + k;
+        const uint32_t fl = smem[k] >> 16;
+        const uint32_t dym = (fl & 4u) ? (uint32_t)(i - s_nb[k]) : 0u;
+        const uint32_t dyp = (fl & 8u) ? (uint32_t)(s_nb[cap + k] - i) : 0u;
+        ty[i] = dym | ((fl & 1u) << 15) | (dyp << 16) | ((fl & 2u) << 30);
+        tzm[i] = (fl & 16u) ? (uint32_t)(i - s_nb[2 * cap + k]) : 0u;
+        tzp[i] = (fl & 32u) ? (uint32_t)(s_nb[3 * cap + k] - i) : 0u;
+    }
+}
+
+// One node per thread, neighbours from the offset table; the +-x neighbours' values come from the
+// adjacent lanes (consecutive nodes) by warp shuffles.  Arithmetic and slot order as k_stencil.
+template <int MODE, int TR, int PREC>
+__global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable tb, StepParams p, StateIO io) {
+    const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < (uint64_t)n;
+    const float *__restrict__ Y2 = io.in[1];
+    const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
+    const uint32_t dzm = live ? __ldg(tb.tzm + i) : 0u;
+    const uint32_t dzp = live ? __ldg(tb.tzp + i) : 0u;
+    V x2 = live ? vload<PREC>(Y2, io.lin[1], i) : V{0.0f, 0.0f};
+    const float yi = x2.h;
+    const int lane = threadIdx.x & 31;
+    float yl = __shfl_up_sync(0xffffffffu, yi, 1);
+    float yr = __shfl_down_sync(0xffffffffu, yi, 1);
+    const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
+    const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
+    if (lane == 0 && hxm) yl = __ldg(Y2 + (i - 1));
+    if (lane == 31 && hxp) yr = __ldg(Y2 + (i + 1));
+    float ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
+    if (dym) ym = __ldg(Y2 + (i - dym));
+    if (dyp) yp = __ldg(Y2 + (i + dyp));
+    if (dzm) zm = __ldg(Y2 + (i - dzm));
+    if (dzp) zp = __ldg(Y2 + (i + dzp));
+    if (!live) return;
+    float acc = 0.0f;
+    if (hxm) acc = __fadd_rn(acc, __fsub_rn(yi, yl));
+    if (hxp) acc = __fadd_rn(acc, __fsub_rn(yi, yr));
+    if (dym) acc = __fadd_rn(acc, __fsub_rn(yi, ym));
+    if (dyp) acc = __fadd_rn(acc, __fsub_rn(yi, yp));
+    if (dzm) acc = __fadd_rn(acc, __fsub_rn(yi, zm));
+    if (dzp) acc = __fadd_rn(acc, __fsub_rn(yi, zp));
+    vadd<PREC>(x2, __fmul_rn(-p.c, acc));  // Scheme 1
+    if (MODE == 1) {
+        vround<PREC>(x2);
+        V x1 = vload<PREC>(io.in[0], io.lin[0], i), x3 = vload<PREC>(io.in[2], io.lin[2], i),
+          x4 = vload<PREC>(io.in[3], io.lin[3], i), x5 = vload<PREC>(io.in[4], io.lin[4], i);
+        transform<TR, PREC>(x1, x2, x3, x4, x5, p);
+        vstore<PREC>(io.out[0], io.lout[0], i, x1);
+        vstore<PREC>(io.out[1], io.lout[1], i, x2);
+        vstore<PREC>(io.out[2], io.lout[2], i, x3);
+        vstore<PREC>(io.out[3], io.lout[3], i, x4);
+        vstore<PREC>(io.out[4], io.lout[4], i, x5);
+    } else {
+        vstore<PREC>(io.out[1], io.lout[1], i, x2);
     }
 }
 
@@ -159,10 +348,54 @@ __global__ void k_pack(int64_t n, float *__restrict__ x, StateIO io, int to_stat
 
 inline unsigned grid_for(int64_t count, int threads) { return (unsigned)((count + threads - 1) / threads); }
 
+constexpr int kStagedThreads = 256;
+
+template <int MODE, int WM, int TR, int PREC, int CAP>
+void launch_staged(vga_sim *s, const StateIO &io) {
+    using Ly = StagedLayout<CAP, kStagedThreads>;
+    constexpr size_t smem = Ly::bytes(WM == W_BLOCK);
+    auto kern = k_stencil_staged<MODE, WM, TR, PREC, CAP, kStagedThreads>;
+    static uint64_t configured = 0;  // one attribute call per instantiation and device (ordinals < 64)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !((configured >> dev) & 1ull)) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        configured |= 1ull << dev;
+    }
+    kern<<<s->chunks.count, kStagedThreads, smem, s->stream>>>(s->g->topo(), s->chunks.row, s->sp, s->bw, io, s->d_err);
+}
+
+// Chunk sizes with a staged instantiation.
+bool staged_cap_supported(int cap) { return cap == 512 || cap == 1024 || cap == 2048; }
+
+template <int MODE, int WM, int TR, int PREC>
+void launch_staged_any(vga_sim *s, const StateIO &io) {
+    switch (s->chunks.cap) {
+        case 512: launch_staged<MODE, WM, TR, PREC, 512>(s, io); break;
+        case 2048: launch_staged<MODE, WM, TR, PREC, 2048>(s, io); break;
+        default: launch_staged<MODE, WM, TR, PREC, 1024>(s, io); break;
+    }
+}
+
+template <int MODE, int PREC>
+vga_status launch_table(vga_sim *s, const StateIO &io) {
+    NbrTable tb;
+    VGA_TRY(sim_nbr_table(s, &tb));
+    const unsigned grid = grid_for(s->n, kThreads);
+    if (s->sp.transform == 0) k_stencil_table<MODE, 0, PREC><<<grid, kThreads, 0, s->stream>>>(s->n, tb, s->sp, io);
+    else k_stencil_table<MODE, 1, PREC><<<grid, kThreads, 0, s->stream>>>(s->n, tb, s->sp, io);
+    return VGA_OK;
+}
+
 template <int MODE, int WM, int PREC>
 void launch_stencil_tr(vga_sim *s, const StateIO &io) {
     const Topo t = s->g->topo();
     const size_t smem = sizeof(uint32_t) * (size_t)s->chunks.cap * decode_words(WM == W_BLOCK);
+    if (s->kernel_variant == 1 && staged_cap_supported(s->chunks.cap)) {
+        if (s->sp.transform == 0) launch_staged_any<MODE, WM, 0, PREC>(s, io);
+        else launch_staged_any<MODE, WM, 1, PREC>(s, io);
+        return;
+    }
     if (s->sp.transform == 0)
         k_stencil<MODE, WM, 0, PREC><<<s->chunks.count, kThreads, smem, s->stream>>>(t, s->chunks.row, s->chunks.cap,
                                                                                    s->sp, s->bw, io);
@@ -173,8 +406,20 @@ void launch_stencil_tr(vga_sim *s, const StateIO &io) {
 
 template <int MODE>
 vga_status launch_stencil(vga_sim *s, const StateIO &io) {
-    timing_begin(s, MODE == 1 ? VGA_KERNEL_FUSED_STEP : VGA_KERNEL_DIFFUSE);
     const bool comp = s->precision() == P_COMP;
+    if (s->kernel_variant == 2 && s->wmode == W_UNIT && s->g->nx <= 32767) {
+        // table kernel: build the table (first use) before the timed launch
+        NbrTable tb;
+        VGA_TRY(sim_nbr_table(s, &tb));
+        timing_begin(s, MODE == 1 ? VGA_KERNEL_FUSED_STEP : VGA_KERNEL_DIFFUSE);
+        const vga_status st = comp ? launch_table<MODE, P_COMP>(s, io) : launch_table<MODE, P_F32>(s, io);
+        timing_end(s);
+        VGA_TRY(st);
+        VGA_CHECK_LAUNCH();
+        ++s->launches;
+        return VGA_OK;
+    }
+    timing_begin(s, MODE == 1 ? VGA_KERNEL_FUSED_STEP : VGA_KERNEL_DIFFUSE);
     if (s->wmode == W_BLOCK) {
         if (comp) launch_stencil_tr<MODE, W_BLOCK, P_COMP>(s, io);
         else launch_stencil_tr<MODE, W_BLOCK, P_F32>(s, io);
@@ -312,5 +557,37 @@ vga_status sim_pack_f32(vga_sim *s, float *d_x, bool to_state) {
 }
 
 int totals_blocks() { return kTotBlocks; }
+
+vga_status build_nbr_table(const Topo &t, uint32_t *ty, uint32_t *tzm, uint32_t *tzp, cudaStream_t st) {
+    if (t.n == 0) return VGA_OK;
+    Chunks ch;
+    VGA_TRY(build_chunks(t, 1024, &ch, st));
+    const size_t smem = sizeof(uint32_t) * 1024 * decode_words(false);
+    k_build_table<<<ch.count, kThreads, smem, st>>>(t, ch.row, 1024, ty, tzm, tzp);
+    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e2 = cudaStreamSynchronize(st);
+    free_chunks(&ch);
+    if (e != cudaSuccess) return cuda_fail(e, "k_build_table", __FILE__, __LINE__);
+    if (e2 != cudaSuccess) return cuda_fail(e2, "k_build_table", __FILE__, __LINE__);
+    return VGA_OK;
+}
+
+vga_status sim_nbr_table(vga_sim *s, NbrTable *out) {
+    if (!s->nbr_table) {
+        VGA_TRY(dmalloc((void **)&s->nbr_table, sizeof(uint32_t) * 3 * (size_t)std::max<int64_t>(s->npad, 64),
+                        "neighbour table"));
+        VGA_TRY(build_nbr_table(s->g->topo(), s->nbr_table, s->nbr_table + s->npad, s->nbr_table + 2 * s->npad,
+                                s->stream));
+        ++s->launches;
+    }
+    out->ty = s->nbr_table;
+    out->tzm = s->nbr_table + s->npad;
+    out->tzp = s->nbr_table + 2 * s->npad;
+    return VGA_OK;
+}
+
+bool stencil_variant_supported(int variant, int cap) {
+    return variant == 0 || variant == 2 || staged_cap_supported(cap);
+}
 
 }  // namespace vga

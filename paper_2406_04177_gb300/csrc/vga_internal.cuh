@@ -57,6 +57,16 @@ struct Chunks {
     int32_t *row = nullptr;  // count + 1 entries (device)
 };
 
+// Compact neighbour-offset table of a node set (built once from the row bitmask).  Per node i:
+//   ty[i]   bits 0..14 = i - (index of the -y neighbour), 0 if none; bit 15 = has -x neighbour;
+//           bits 16..30 = (index of the +y neighbour) - i, 0 if none; bit 31 = has +x neighbour
+//   tzm[i]  i - (index of the -z neighbour), 0 if none
+//   tzp[i]  (index of the +z neighbour) - i, 0 if none
+// The -x / +x neighbours are i - 1 / i + 1.  Requires nx <= 32767 (y offsets are below nx).
+struct NbrTable {
+    const uint32_t *ty = nullptr, *tzm = nullptr, *tzp = nullptr;
+};
+
 // Float parameters of one time step (products with dt taken in FP64 on the host, then rounded).
 struct StepParams {
     float a;      // v_dom * dt
@@ -109,6 +119,7 @@ vga_status scan_popc(const uint32_t *words, int64_t nwords, int32_t *out, int32_
 
 // Builds the chunk table of `topo` for chunk size cap (device work, one launch).
 vga_status build_chunks(const Topo &topo, int32_t cap, Chunks *ch, cudaStream_t st);
+// Builds the neighbour-offset table of the simulation's graph (step.cu).
 void free_chunks(Chunks *ch);
 
 struct AdjointBuffers;
@@ -180,6 +191,9 @@ struct vga_sim {
     int timing_kind = -1;
     // adjoint work buffers (adjoint.cu), allocated on first use
     vga::AdjointBuffers *adj = nullptr;
+    int32_t *d_err = nullptr;     // device error flag of bounded waits (nonzero: timed out)
+    int kernel_variant = 2;       // explicit stencil: 0 decode + direct loads, 1 decode + staged, 2 table
+    uint32_t *nbr_table = nullptr;  // 3 x npad words (NbrTable), built on first use
     double *loss_work = nullptr;  // block-mass objective scratch
     int64_t loss_cap = 0;
     int64_t param_gen = 0;  // bumped by every change of parameters or conductances
@@ -203,6 +217,10 @@ vga_status sim_convert_in(vga_sim *s, const double *d_x);    // device FP64 (5 x
 vga_status sim_convert_out(vga_sim *s, double *d_x);         // state -> device FP64 (5 x n)
 vga_status sim_pack_f32(vga_sim *s, float *d_x, bool to_state);
 vga_status sim_transform_pass(vga_sim *s);  // Y = T(X) for every node, all compartments swapped
+vga_status sim_nbr_table(vga_sim *s, NbrTable *out);  // builds the table on first use
+// Writes the neighbour-offset table of a node set (offsets are relative, so the arrays may start at
+// any node offset of a larger concatenated range).  Synchronises the stream.
+vga_status build_nbr_table(const Topo &t, uint32_t *ty, uint32_t *tzm, uint32_t *tzp, cudaStream_t st);
 StateIO state_io(vga_sim *s);          // current buffers in, spare buffers out
 StateIO state_io_inplace(vga_sim *s);  // current buffers in and out
 // pcg.cu
@@ -210,6 +228,7 @@ vga_status sim_step_implicit(vga_sim *s, int64_t n_steps);
 // adjoint.cu
 vga_status sim_adjoint_forward(vga_sim *s, int64_t N, int64_t ckpt);
 vga_status sim_adjoint_backward(vga_sim *s, const double *d_lamN, double *d_lam0, double *grad8, double *h_gtheta);
+vga_status sim_sgd_theta(vga_sim *s, double lr, double lo, double hi);
 vga_status sim_block_mass_loss(vga_sim *s, int32_t bs, uint32_t comp_mask, const double *d_target, double *d_work,
                                double *h_loss, double *h_mass, double *d_dldx);
 }  // namespace vga

@@ -213,3 +213,45 @@ def test_device_state_io(vga, oracle_lib):
     assert np.array_equal(f32.cpu().numpy(), out.cpu().numpy().astype(np.float32))
     host = sim.get_state_f32()
     assert np.array_equal(host, f32.cpu().numpy())
+
+
+@pytest.mark.parametrize("block,transform,precision", [(False, 0, 0), (True, 0, 0), (False, 1, 0), (False, 0, 1)])
+def test_kernel_variants_bit_identical(vga, oracle_lib, block, transform, precision):
+    """Direct and staged stencil kernels, every chunk size: the same bits after 50 steps."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (40, 48, 36), 0.24, 12, organic=True)
+    p = synth.paper_params(transform=transform)
+    p["state_precision"] = precision
+    bs = 8
+    theta = synth.block_conductances(oracle_lib.block_grid(img.shape, bs), 4) if block else None
+    if block:
+        p["dt"] = 0.9 / (6 * synth.D_DOM * theta.max())
+    states = []
+    for variant, chunk in [(0, 1024), (1, 1024), (1, 512), (1, 2048), (0, 512), (0, 96), (2, 1024)]:
+        sim = vga.Sim(g, p)
+        sim.set_kernel(variant, chunk)
+        if block:
+            sim.set_block_conductances(bs, theta.astype(np.float32))
+        sim.set_masses(X0)
+        sim.step(50)
+        states.append(sim.save_state())
+    assert all(st == states[0] for st in states[1:])
+    ref = oracle_lib.explicit_run(og.nbr, p, X0, 50, transform=transform,
+                                  g6=oracle_lib.block_face_weights(img.shape, bs, og.voxel_of_node, og.nbr, theta)
+                                  if block else None)
+    last = vga.Sim(g, p)
+    last.load_state(states[0])
+    _assert_close(last.get_masses(), ref, tol=1e-5 if precision == 0 else 1e-4)
+
+
+def test_autotune_keeps_state(vga, oracle_lib):
+    img, og, g, X0 = _setup(vga, oracle_lib, (64, 64, 64), 0.2, 13)
+    sim = vga.Sim(g, synth.paper_params())
+    sim.set_masses(X0)
+    sim.step(3)
+    before = sim.save_state()
+    res = sim.autotune(4)
+    assert res["best"] is not None and len(res["entries"]) == 7
+    assert all(e["ms_per_step"] > 0 for e in res["entries"])
+    assert sim.save_state() == before
+    with pytest.raises(vga.VgaError):
+        sim.set_kernel(1, 768)

@@ -1,0 +1,82 @@
+"""Conductance fitting (normalised-gradient SGD of Sec. V.A) and the autograd.Function on the GPU."""
+import numpy as np
+import pytest
+
+import synth
+from tests.test_oracle_fit import THETA_STAR, oracle_fit, toy
+
+pytestmark = pytest.mark.gpu
+
+
+def test_gpu_fit_two_block_toy_matches_oracle(vga, oracle_lib):
+    from paper_2406_04177_gb300.fit import fit_block_conductances
+
+    img, og, X0, p = toy(oracle_lib)
+    theta_o, losses_o, target = oracle_fit(oracle_lib, img, og, X0, p, epochs=40)
+    g = vga.Graph(img)
+    res = fit_block_conductances(g, p, X0, 8, target, n_theta=1, n_steps=40, ckpt=16, epochs=40)
+    assert abs(res["theta"][0] - THETA_STAR) < 0.01
+    assert abs(res["theta"][0] - theta_o[0]) < 0.005
+    assert np.allclose(res["loss"][:10], losses_o[:10], rtol=1e-4)
+
+
+def test_gpu_fit_block_grid_reduces_loss(vga, oracle_lib):
+    """Reduced adjoint workload: 32^3 at 20% porosity, 8^3 blocks (144 faces), 100 steps."""
+    from paper_2406_04177_gb300.fit import fit_block_conductances
+
+    img = synth.pore_mask((32, 32, 32), 0.2, 8)
+    og = oracle_lib.graph_build(img)
+    X0 = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), 8, with_organic_matter=True)
+    bs = 8
+    nb = oracle_lib.block_grid(img.shape, bs)
+    nI = oracle_lib.interface_count(nb)
+    theta_star = synth.block_conductances(nb, 9)
+    p = synth.paper_params(dt=0.9 / (6 * synth.D_DOM * 1.5))
+    g6s = oracle_lib.block_face_weights(img.shape, bs, og.voxel_of_node, og.nbr, theta_star)
+    target = oracle_lib.block_masses(img.shape, bs, og.voxel_of_node, oracle_lib.explicit_run(og.nbr, p, X0, 100, g6=g6s))
+    g = vga.Graph(img)
+    res = fit_block_conductances(g, p, X0, bs, target, n_theta=nI, n_steps=100, ckpt=50, epochs=30)
+    assert res["loss"][-1] < 0.2 * res["loss"][0]
+    # faces that carry flux in the data move toward theta*
+    err0 = np.abs(1.0 - theta_star)
+    err1 = np.abs(res["theta"] - theta_star)
+    assert np.median(err1) < np.median(err0)
+
+
+def test_autograd_function_matches_oracle_adjoint(vga, oracle_lib):
+    import torch
+
+    from paper_2406_04177_gb300.autograd import RATE_NAMES, run
+
+    img = synth.pore_mask((20, 24, 16), 0.25, 12)
+    og = oracle_lib.graph_build(img)
+    X0 = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), 12, with_organic_matter=True)
+    X0[0] = np.where(X0[1] > 0, 0.3 * X0[1], X0[0]).astype(np.float32)
+    bs = 8
+    nb = oracle_lib.block_grid(img.shape, bs)
+    theta_np = synth.block_conductances(nb, 4)
+    p = synth.paper_params(dt=0.9 / (6 * synth.D_DOM * 1.5))
+    nsteps = 30
+    g = vga.Graph(img)
+    sim = vga.Sim(g, p)
+    theta = torch.tensor(theta_np.astype(np.float32).astype(np.float64), device="cuda", requires_grad=True)
+    rates = torch.tensor([p[k] for k in RATE_NAMES], dtype=torch.float64, requires_grad=True)
+    x0 = torch.from_numpy(X0).cuda().requires_grad_(True)
+    XN = run(sim, theta, rates, x0, nsteps, ckpt=8, block_side=bs)
+    w = torch.from_numpy(np.random.default_rng(3).standard_normal((5, og.n))).cuda()
+    loss = (w * XN).sum() + (XN[1] ** 2).sum() * 1e3
+    loss.backward()
+    # oracle: same loss, FP64 adjoint
+    g6 = oracle_lib.block_face_weights(img.shape, bs, og.voxel_of_node, og.nbr, theta_np.astype(np.float32))
+    XN_ref = oracle_lib.explicit_run(og.nbr, p, X0, nsteps, g6=g6)
+    lamN = w.cpu().numpy().copy()
+    lamN[1] += 2e3 * XN_ref[1]
+    ref = oracle_lib.adjoint_run(og.nbr, p, X0, nsteps, lamN, ckpt=8, g6=g6, want_gface=True)
+    gref = oracle_lib.block_theta_grad(img.shape, bs, og.voxel_of_node, og.nbr, ref["gface"], theta_np.size)
+    gth = theta.grad.cpu().numpy()
+    assert np.linalg.norm(gth - gref) <= 1e-4 * np.linalg.norm(gref)
+    for k, name in enumerate(RATE_NAMES):
+        v = ref["grad"][name]
+        assert abs(rates.grad[k].item() - v) <= 1e-4 * abs(v) + 1e-30, name
+    dx0 = x0.grad.cpu().numpy()
+    assert np.linalg.norm(dx0 - ref["lam0"]) <= 1e-4 * np.linalg.norm(ref["lam0"])
