@@ -51,7 +51,9 @@ def parse_args():
     ap.add_argument("--porosity", type=float, default=0.17)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target length of the CPU-baseline sample")
-    ap.add_argument("--no-extras", action="store_true", help="skip the implicit and graph-build measurements")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the graph-build, implicit, adjoint and batched measurements")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (for profiler runs)")
     return ap.parse_args()
 
 
@@ -342,7 +344,7 @@ def bench_ours(a):
 
     if rank == 0 and world == 1 or (rank == 0 and world > 1):
         # cpu baseline (rank 0, N = 1 only) and the FP64 error of the same steps
-        if world == 1:
+        if world == 1 and not a.no_cpu:
             base, og, Xm, m = run_cpu_baseline(a, img, X0)
             assert og.n == n
             simc = vga.Sim(g, params, stream=stream)

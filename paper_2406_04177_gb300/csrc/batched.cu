@@ -127,14 +127,23 @@ __global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int
                 if (dzm) acc = __fadd_rn(acc, __fsub_rn(yi, zm));
                 if (dzp) acc = __fadd_rn(acc, __fsub_rn(yi, zp));
                 vadd<PREC>(x[1], __fmul_rn(-p.c, acc));
+                if (kind == 2) {
+                    // diffusion-only pass: DOM is new, the other compartments move bit for bit
+                    vstore<PREC>(a.h[bo] + a.npad, a.l[bo] + a.npad, i, x[1]);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) {
+                        if (c == 1) continue;
+                        a.h[bo][c * a.npad + i] = a.h[bi][c * a.npad + i];
+                        if (PREC == P_COMP) a.l[bo][c * a.npad + i] = a.l[bi][c * a.npad + i];
+                    }
+                    continue;
+                }
                 x[0] = vload<PREC>(a.h[bi], a.l[bi], i);
                 x[2] = vload<PREC>(a.h[bi] + 2 * a.npad, a.l[bi] + 2 * a.npad, i);
                 x[3] = vload<PREC>(a.h[bi] + 3 * a.npad, a.l[bi] + 3 * a.npad, i);
                 x[4] = vload<PREC>(a.h[bi] + 4 * a.npad, a.l[bi] + 4 * a.npad, i);
-                if (kind == 1) {
-                    vround<PREC>(x[1]);
-                    transform<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
-                }
+                vround<PREC>(x[1]);
+                transform<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
             }
 #pragma unroll
             for (int c = 0; c < 5; ++c) vstore<PREC>(a.h[bo] + c * a.npad, a.l[bo] + c * a.npad, i, x[c]);

@@ -120,6 +120,82 @@ __global__ void __launch_bounds__(kThreads) k_spmv(Topo t, const int32_t *__rest
     if (threadIdx.x == 0) part[blockIdx.x] = out[0];
 }
 
+// Table-driven versions of the two stencil kernels (unit conductances): one node per thread,
+// neighbours from the offset table, +-x values by warp shuffles.  Same arithmetic and slot order.
+__device__ __forceinline__ double nbr_sum_table(NbrTable tb, uint32_t i, bool live, double vi,
+                                                const double *__restrict__ v, double &deg) {
+    const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
+    const uint32_t dzm = live ? __ldg(tb.tzm + i) : 0u;
+    const uint32_t dzp = live ? __ldg(tb.tzp + i) : 0u;
+    const int lane = threadIdx.x & 31;
+    double vl = __shfl_up_sync(0xffffffffu, vi, 1);
+    double vr = __shfl_down_sync(0xffffffffu, vi, 1);
+    const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
+    const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
+    if (lane == 0 && hxm) vl = v[i - 1];
+    if (lane == 31 && hxp) vr = v[i + 1];
+    double s = 0.0;
+    deg = 0.0;
+    if (hxm) { s += vi - vl; deg += 1.0; }
+    if (hxp) { s += vi - vr; deg += 1.0; }
+    if (dym) { s += vi - v[i - dym]; deg += 1.0; }
+    if (dyp) { s += vi - v[i + dyp]; deg += 1.0; }
+    if (dzm) { s += vi - v[i - dzm]; deg += 1.0; }
+    if (dzp) { s += vi - v[i + dzp]; deg += 1.0; }
+    return s;
+}
+
+// x = b (the right-hand side y2 as FP64)
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_cg_rhs(int64_t n, const float *__restrict__ y2,
+                                                     const uint16_t *__restrict__ y2l, double *__restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = (double)__ldg(y2 + i) + (PREC == P_COMP ? (double)bf16_bits_to_float(__ldg(y2l + i)) : 0.0);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_cg_init_table_b(int64_t n, NbrTable tb, double c, CgVecs v,
+                                                              double *__restrict__ part) {
+    const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < (uint64_t)n;
+    const double bi = live ? v.x[i] : 0.0;
+    double deg = 0.0;
+    const double lb = nbr_sum_table(tb, i, live, bi, v.x, deg);
+    double acc[3] = {0.0, 0.0, 0.0};
+    if (live) {
+        const double ri = -c * lb;
+        const double ti = 1.0 / (1.0 + c * deg);
+        v.r[i] = ri;
+        v.t[i] = ti;
+        acc[0] = ri * ti * ri;
+        acc[1] = ri * ri;
+        acc[2] = bi * bi;
+    }
+    __shared__ double out[3];
+    block_sum_store<3>(acc, out);
+    if (threadIdx.x < 3) part[(int64_t)blockIdx.x * 3 + threadIdx.x] = out[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kThreads) k_spmv_table(int64_t n, NbrTable tb, double c, const double *__restrict__ p,
+                                                         double *__restrict__ q, double *__restrict__ part,
+                                                         const CgScalars *__restrict__ sc) {
+    if (sc->done) return;
+    const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < (uint64_t)n;
+    const double pi = live ? p[i] : 0.0;
+    double deg;
+    const double lp = nbr_sum_table(tb, i, live, pi, p, deg);
+    double acc[1] = {0.0};
+    if (live) {
+        const double qi = pi + c * lp;
+        q[i] = qi;
+        acc[0] = pi * qi;
+    }
+    __shared__ double out[1];
+    block_sum_store<1>(acc, out);
+    if (threadIdx.x == 0) part[blockIdx.x] = out[0];
+}
+
 __global__ void __launch_bounds__(kThreads) k_update_p(int64_t n, CgVecs v, const CgScalars *__restrict__ sc,
                                                        int first) {
     if (sc->done) return;
@@ -222,11 +298,20 @@ vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgSc
     const int G = s->chunks.count;
     const int ew = (int)std::min<int64_t>(kEwBlocks, (int64_t)grid_for(s->n, kThreads));
     cudaStream_t st = s->stream;
+    const bool table = (WM == W_UNIT) && s->g->nx <= 32767;
+    NbrTable tb;
+    if (table) VGA_TRY(sim_nbr_table(s, &tb));
+    const int Gs = table ? (int)grid_for(s->n, kThreads) : G;  // blocks of the stencil kernels
     timing_begin(s, VGA_KERNEL_PCG_STENCIL);
-    k_cg_init<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, c, s->bw, s->comp(1),
-                                                   s->lcomp(1), v, part_chunk);
+    if (table) {
+        k_cg_rhs<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->comp(1), s->lcomp(1), v.x);
+        k_cg_init_table_b<PREC><<<Gs, kThreads, 0, st>>>(s->n, tb, c, v, part_chunk);
+    } else {
+        k_cg_init<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, c, s->bw, s->comp(1),
+                                                       s->lcomp(1), v, part_chunk);
+    }
     timing_end(s);
-    k_scalar_init<<<1, kThreads, 0, st>>>(part_chunk, G, sc, s->params.cg_rtol, s->params.cg_maxit);
+    k_scalar_init<<<1, kThreads, 0, st>>>(part_chunk, Gs, sc, s->params.cg_rtol, s->params.cg_maxit);
     VGA_CHECK_LAUNCH();
     s->launches += 2;
     CgScalars *h = reinterpret_cast<CgScalars *>(s->h_cg);
@@ -237,10 +322,11 @@ vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgSc
             k_update_p<<<ew, kThreads, 0, st>>>(s->n, v, sc, first ? 1 : 0);
             timing_end(s);
             timing_begin(s, VGA_KERNEL_PCG_STENCIL);
-            k_spmv<WM><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, c, s->bw, v.p, v.q, part_chunk, sc);
+            if (table) k_spmv_table<<<Gs, kThreads, 0, st>>>(s->n, tb, c, v.p, v.q, part_chunk, sc);
+            else k_spmv<WM><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, c, s->bw, v.p, v.q, part_chunk, sc);
             timing_end(s);
             timing_begin(s, VGA_KERNEL_PCG_VECTOR);
-            k_scalar_a<<<1, kThreads, 0, st>>>(part_chunk, G, sc);
+            k_scalar_a<<<1, kThreads, 0, st>>>(part_chunk, Gs, sc);
             k_update_xr<<<ew, kThreads, 0, st>>>(s->n, v, sc, part_ew);
             k_scalar_b<<<1, kThreads, 0, st>>>(part_ew, ew, sc);
             timing_end(s);
@@ -268,7 +354,7 @@ vga_status sim_step_implicit(vga_sim *s, int64_t n_steps) {
         s->steps_done += std::max<int64_t>(n_steps, 0);
         return VGA_OK;
     }
-    const int64_t G = s->chunks.count;
+    const int64_t G = std::max<int64_t>(s->chunks.count, (s->n + kThreads - 1) / kThreads);
     const int64_t need = 5 * s->npad + 3 * std::max<int64_t>(G, 1) + 2 * kEwBlocks;
     if (s->cg_count < need) {
         dfree(s->cg);
