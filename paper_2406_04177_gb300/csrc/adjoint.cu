@@ -163,6 +163,130 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_step(Topo t, const int32_t
     if (threadIdx.x < kPar) gpart[(int64_t)blockIdx.x * kPar + threadIdx.x] += out[threadIdx.x];
 }
 
+// Values of the six neighbours of node i from the offset table (0 where absent); +-x by shuffles.
+struct Nb6 {
+    float v[6];
+    uint32_t mask;  // bit d: neighbour in slot d exists
+};
+
+__device__ __forceinline__ Nb6 gather6(const NbrTable &tb, uint32_t i, bool live, float vi,
+                                       const float *__restrict__ a) {
+    Nb6 r;
+    const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
+    const uint32_t dzm = live ? __ldg(tb.tzm + i) : 0u;
+    const uint32_t dzp = live ? __ldg(tb.tzp + i) : 0u;
+    const int lane = threadIdx.x & 31;
+    float vl = __shfl_up_sync(0xffffffffu, vi, 1);
+    float vr = __shfl_down_sync(0xffffffffu, vi, 1);
+    const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
+    const uint32_t hxm = (ty >> 15) & 1u, hxp = ty >> 31;
+    if (lane == 0 && hxm) vl = __ldg(a + (i - 1));
+    if (lane == 31 && hxp) vr = __ldg(a + (i + 1));
+    r.v[0] = vl;
+    r.v[1] = vr;
+    r.v[2] = dym ? __ldg(a + (i - dym)) : 0.0f;
+    r.v[3] = dyp ? __ldg(a + (i + dyp)) : 0.0f;
+    r.v[4] = dzm ? __ldg(a + (i - dzm)) : 0.0f;
+    r.v[5] = dzp ? __ldg(a + (i + dzp)) : 0.0f;
+    r.mask = hxm | (hxp << 1) | ((uint32_t)(dym != 0) << 2) | ((uint32_t)(dyp != 0) << 3) |
+             ((uint32_t)(dzm != 0) << 4) | ((uint32_t)(dzp != 0) << 5);
+    return r;
+}
+
+// Table-driven fused pass with recording (same arithmetic as k_fused_rec and the forward).
+template <int WM, int PREC>
+__global__ void __launch_bounds__(kThreads) k_fused_rec_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+                                                              StateIO io, int64_t npad, Rec rec) {
+    const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < (uint64_t)n;
+    const float *__restrict__ Y2 = io.in[1];
+    V x2 = live ? vload<PREC>(Y2, io.lin[1], i) : V{0.0f, 0.0f};
+    const float yi = x2.h;
+    const Nb6 nb = gather6(tb, i, live, yi, Y2);
+    if (!live) return;
+    const uint32_t bn = (WM == W_BLOCK) ? __ldg(bt.node + i) : 0u;
+    float acc = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        if (!((nb.mask >> d) & 1u)) continue;
+        const float dd = __fsub_rn(yi, nb.v[d]);
+        if (WM == W_UNIT) acc = __fadd_rn(acc, dd);
+        else acc = __fmaf_rn(table_theta(bt, bn, d), dd, acc);
+    }
+    vadd<PREC>(x2, __fmul_rn(-p.c, acc));
+    vround<PREC>(x2);
+    V x1 = vload<PREC>(io.in[0], io.lin[0], i), x3 = vload<PREC>(io.in[2], io.lin[2], i),
+      x4 = vload<PREC>(io.in[3], io.lin[3], i), x5 = vload<PREC>(io.in[4], io.lin[4], i);
+    rec.x[i] = __fadd_rn(x1.h, x1.l);
+    rec.x[npad + i] = __fadd_rn(x2.h, x2.l);
+    rec.x[2 * npad + i] = __fadd_rn(x3.h, x3.l);
+    rec.x[3 * npad + i] = __fadd_rn(x4.h, x4.l);
+    rec.x[4 * npad + i] = __fadd_rn(x5.h, x5.l);
+    transform_sync<PREC>(x1, x2, x3, x4, x5, p);
+    vstore<PREC>(io.out[0], io.lout[0], i, x1);
+    vstore<PREC>(io.out[1], io.lout[1], i, x2);
+    vstore<PREC>(io.out[2], io.lout[2], i, x3);
+    vstore<PREC>(io.out[3], io.lout[3], i, x4);
+    vstore<PREC>(io.out[4], io.lout[4], i, x5);
+    rec.y2[i] = __fadd_rn(x2.h, x2.l);
+}
+
+// Table-driven reverse step (same arithmetic as k_adjoint_step).
+template <int WM, int PREC>
+__global__ void __launch_bounds__(kThreads) k_adjoint_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+                                                            StateIO io, int64_t npad, const float *__restrict__ xk,
+                                                            const float *__restrict__ y2k, double *__restrict__ gpart,
+                                                            double *__restrict__ gtheta) {
+    const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < (uint64_t)n;
+    const float *__restrict__ L2 = io.in[1];
+    V mu[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) mu[c] = live ? vload<PREC>(io.in[c], io.lin[c], i) : V{0.0f, 0.0f};
+    const float li = mu[1].h;
+    const float yi = live ? __ldg(y2k + i) : 0.0f;
+    const Nb6 nl = gather6(tb, i, live, li, L2);
+    const Nb6 ny = gather6(tb, i, live, yi, y2k);
+    double acc[kPar];
+#pragma unroll
+    for (int q = 0; q < kPar; ++q) acc[q] = 0.0;
+    if (live) {
+        const uint32_t bn = (WM == W_BLOCK) ? __ldg(bt.node + i) : 0u;
+        const double mc = -(double)p.c;
+        float lsum = 0.0f, ysum = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            if (!((nl.mask >> d) & 1u)) continue;
+            const float g = (WM == W_UNIT) ? 1.0f : table_theta(bt, bn, d);
+            const float dl = __fsub_rn(li, nl.v[d]);
+            const float dy = __fsub_rn(yi, ny.v[d]);
+            lsum = __fmaf_rn(g, dl, lsum);
+            ysum = __fmaf_rn(g, dy, ysum);
+            if (WM == W_BLOCK && (d & 1)) {  // +x, +y, +z: each edge once
+                const int32_t f = table_face(bt, bn, d);
+                if (f >= 0) atomicAdd(gtheta + f, mc * (double)dy * (double)dl);
+            }
+        }
+        acc[GR_COUNT] -= (double)li * (double)ysum;
+        vadd<PREC>(mu[1], __fmul_rn(-p.c, lsum));
+        float xs[5];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) xs[c] = __ldg(xk + c * npad + i);
+        float gr[GR_COUNT];
+#pragma unroll
+        for (int q = 0; q < GR_COUNT; ++q) gr[q] = 0.0f;
+        V lam[5];
+        transform_sync_reverse<PREC>(xs, mu, lam, gr, p);
+#pragma unroll
+        for (int q = 0; q < GR_COUNT; ++q) acc[q] += (double)gr[q];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) vstore<PREC>(io.out[c], io.lout[c], i, lam[c]);
+    }
+    __shared__ double out[kPar];
+    block_sum_store<kPar>(acc, out);
+    if (threadIdx.x < kPar) gpart[(int64_t)blockIdx.x * kPar + threadIdx.x] += out[threadIdx.x];
+}
+
 __global__ void __launch_bounds__(kThreads) k_reduce_gpart(const double *__restrict__ gpart, int G,
                                                            double *__restrict__ out) {
     double s[kPar];
@@ -327,7 +451,8 @@ void adjoint_free(AdjointBuffers *a) {
 
 static vga_status ensure_adjoint(vga_sim *s, int64_t nseg, int64_t ckpt) {
     AdjointBuffers *a = s->adj;
-    const int64_t npad = s->npad, G = s->chunks.count, ntheta = std::max<int64_t>(s->n_theta, 1);
+    const int64_t npad = s->npad, ntheta = std::max<int64_t>(s->n_theta, 1);
+    const int64_t G = std::max<int64_t>(s->chunks.count, (s->n + kThreads - 1) / kThreads);
     if (a && a->npad == npad && a->nseg >= nseg && a->ckpt >= ckpt && a->G == G && a->ntheta >= ntheta) return VGA_OK;
     adjoint_free(a);
     s->adj = nullptr;
@@ -406,7 +531,12 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     const int64_t N = a->N, ckpt = a->cur_ckpt;
     const int64_t nseg = N > 0 ? (N + ckpt - 1) / ckpt : 0;
     const Topo t = s->g->topo();
-    const int G = s->chunks.count;
+    NbrTable tb;
+    BlockTable bt;
+    bool table = s->g->nx <= 32767;
+    if (table) VGA_TRY(sim_nbr_table(s, &tb));
+    if (table && WM == W_BLOCK) VGA_TRY(sim_block_table(s, &bt, &table));
+    const int G = table ? (int)((s->n + kThreads - 1) / kThreads) : s->chunks.count;
     const size_t smem = sizeof(uint32_t) * (size_t)s->chunks.cap * decode_words(WM == W_BLOCK);
     const int64_t npad = s->npad;
     cudaStream_t st = s->stream;
@@ -432,8 +562,12 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
             rec.x = a->rec_x + (size_t)j * 5 * npad;
             rec.y2 = a->rec_y2 + (size_t)j * npad;
             timing_begin(s, VGA_KERNEL_FUSED_STEP);
-            k_fused_rec<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
-                                                            io_from(a->work[wb], a->work[1 - wb], npad), npad, rec);
+            if (table)
+                k_fused_rec_table<WM, PREC><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
+                                                                   io_from(a->work[wb], a->work[1 - wb], npad), npad, rec);
+            else
+                k_fused_rec<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
+                                                                io_from(a->work[wb], a->work[1 - wb], npad), npad, rec);
             timing_end(s);
             VGA_CHECK_LAUNCH();
             ++s->launches;
@@ -443,9 +577,14 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
         for (int64_t j = len - 1; j >= 0; --j) {
             const float *xk = (j == 0) ? cks.h : a->rec_x + (size_t)j * 5 * npad;
             timing_begin(s, VGA_KERNEL_ADJOINT);
-            k_adjoint_step<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
-                                                               io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
-                                                               a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
+            if (table)
+                k_adjoint_table<WM, PREC><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
+                                                                 io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
+                                                                 a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
+            else
+                k_adjoint_step<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
+                                                                   io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
+                                                                   a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
             timing_end(s);
             VGA_CHECK_LAUNCH();
             ++s->launches;

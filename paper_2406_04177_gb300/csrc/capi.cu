@@ -360,6 +360,7 @@ vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const 
     if (n_theta > 0)
         VGA_CUDA(cudaMemcpyAsync(s->theta, theta, sizeof(float) * (size_t)n_theta, cudaMemcpyHostToDevice, s->stream));
     VGA_CUDA(cudaStreamSynchronize(s->stream));
+    if (s->bw.bs != block_side) s->btable_bs = 0;
     s->bw.bs = block_side;
     s->bw.nbx = nbx;
     s->bw.nby = nby;
@@ -638,6 +639,8 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->d_totals);
     dfree(s->d_err);
     dfree(s->nbr_table);
+    dfree(s->bnode);
+    dfree(s->bface);
     if (s->h_totals) cudaFreeHost(s->h_totals);
     dfree(s->stage);
     dfree(s->theta);

@@ -230,12 +230,46 @@ __global__ void __launch_bounds__(kThreads) k_build_table(Topo t, const int32_t 
     }
 }
 
+__global__ void __launch_bounds__(kThreads) k_build_bnode(Topo t, const int32_t *__restrict__ chunk_row, int32_t cap,
+                                                          int32_t bs, int32_t nbx, int32_t nby,
+                                                          uint32_t *__restrict__ bnode) {
+    extern __shared__ uint32_t smem[];
+    int32_t *s_nb = reinterpret_cast<int32_t *>(smem + cap);
+    int64_t v0;
+    const int32_t nv = decode_chunk<true>(t, chunk_row, cap, smem, s_nb, smem + 5 * cap, v0);
+    for (int32_t k = threadIdx.x; k < nv; k += blockDim.x) {
+        const int32_t x = (int32_t)(smem[k] & 0xffffu);
+        const int32_t y = (int32_t)(smem[5 * cap + k] & 0xffffu), z = (int32_t)(smem[5 * cap + k] >> 16);
+        const uint32_t b = (uint32_t)(((int64_t)(z / bs) * nby + y / bs) * nbx + x / bs);
+        const uint32_t fb = (uint32_t)(x % bs == 0) | ((uint32_t)((x + 1) % bs == 0) << 1) |
+                            ((uint32_t)(y % bs == 0) << 2) | ((uint32_t)((y + 1) % bs == 0) << 3) |
+                            ((uint32_t)(z % bs == 0) << 4) | ((uint32_t)((z + 1) % bs == 0) << 5);
+        bnode[v0 + k] = b | (fb << 26);
+    }
+}
+
+__global__ void k_build_bface(BlockWeights bw, int32_t *__restrict__ face) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nb = (int64_t)bw.nbx * bw.nby * bw.nbz;
+    if (b >= nb) return;
+    const int32_t bx = (int32_t)(b % bw.nbx), by = (int32_t)((b / bw.nbx) % bw.nby), bz = (int32_t)(b / ((int64_t)bw.nbx * bw.nby));
+    int32_t *f = face + 6 * b;
+    f[0] = bx > 0 ? (int32_t)(((int64_t)bz * bw.nby + by) * (bw.nbx - 1) + bx - 1) : -1;
+    f[1] = bx < bw.nbx - 1 ? (int32_t)(((int64_t)bz * bw.nby + by) * (bw.nbx - 1) + bx) : -1;
+    f[2] = by > 0 ? (int32_t)(bw.off_y + ((int64_t)bz * (bw.nby - 1) + by - 1) * bw.nbx + bx) : -1;
+    f[3] = by < bw.nby - 1 ? (int32_t)(bw.off_y + ((int64_t)bz * (bw.nby - 1) + by) * bw.nbx + bx) : -1;
+    f[4] = bz > 0 ? (int32_t)(bw.off_z + ((int64_t)(bz - 1) * bw.nby + by) * bw.nbx + bx) : -1;
+    f[5] = bz < bw.nbz - 1 ? (int32_t)(bw.off_z + ((int64_t)bz * bw.nby + by) * bw.nbx + bx) : -1;
+}
+
 // One node per thread, neighbours from the offset table; the +-x neighbours' values come from the
 // adjacent lanes (consecutive nodes) by warp shuffles.  Arithmetic and slot order as k_stencil.
-template <int MODE, int TR, int PREC>
-__global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable tb, StepParams p, StateIO io) {
+template <int MODE, int WM, int TR, int PREC>
+__global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+                                                            StateIO io) {
     const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool live = i < (uint64_t)n;
+    const uint32_t bn = (WM == W_BLOCK && live) ? __ldg(bt.node + i) : 0u;
     const float *__restrict__ Y2 = io.in[1];
     const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
     const uint32_t dzm = live ? __ldg(tb.tzm + i) : 0u;
@@ -256,12 +290,17 @@ __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable 
     if (dzp) zp = __ldg(Y2 + (i + dzp));
     if (!live) return;
     float acc = 0.0f;
-    if (hxm) acc = __fadd_rn(acc, __fsub_rn(yi, yl));
-    if (hxp) acc = __fadd_rn(acc, __fsub_rn(yi, yr));
-    if (dym) acc = __fadd_rn(acc, __fsub_rn(yi, ym));
-    if (dyp) acc = __fadd_rn(acc, __fsub_rn(yi, yp));
-    if (dzm) acc = __fadd_rn(acc, __fsub_rn(yi, zm));
-    if (dzp) acc = __fadd_rn(acc, __fsub_rn(yi, zp));
+    auto add = [&](int slot, float yj) {
+        const float d = __fsub_rn(yi, yj);
+        if (WM == W_UNIT) acc = __fadd_rn(acc, d);
+        else acc = __fmaf_rn(table_theta(bt, bn, slot), d, acc);
+    };
+    if (hxm) add(0, yl);
+    if (hxp) add(1, yr);
+    if (dym) add(2, ym);
+    if (dyp) add(3, yp);
+    if (dzm) add(4, zm);
+    if (dzp) add(5, zp);
     vadd<PREC>(x2, __fmul_rn(-p.c, acc));  // Scheme 1
     if (MODE == 1) {
         vround<PREC>(x2);
@@ -377,13 +416,11 @@ void launch_staged_any(vga_sim *s, const StateIO &io) {
     }
 }
 
-template <int MODE, int PREC>
-vga_status launch_table(vga_sim *s, const StateIO &io) {
-    NbrTable tb;
-    VGA_TRY(sim_nbr_table(s, &tb));
+template <int MODE, int WM, int PREC>
+vga_status launch_table(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
     const unsigned grid = grid_for(s->n, kThreads);
-    if (s->sp.transform == 0) k_stencil_table<MODE, 0, PREC><<<grid, kThreads, 0, s->stream>>>(s->n, tb, s->sp, io);
-    else k_stencil_table<MODE, 1, PREC><<<grid, kThreads, 0, s->stream>>>(s->n, tb, s->sp, io);
+    if (s->sp.transform == 0) k_stencil_table<MODE, WM, 0, PREC><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
+    else k_stencil_table<MODE, WM, 1, PREC><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
     return VGA_OK;
 }
 
@@ -407,17 +444,26 @@ void launch_stencil_tr(vga_sim *s, const StateIO &io) {
 template <int MODE>
 vga_status launch_stencil(vga_sim *s, const StateIO &io) {
     const bool comp = s->precision() == P_COMP;
-    if (s->kernel_variant == 2 && s->wmode == W_UNIT && s->g->nx <= 32767) {
-        // table kernel: build the table (first use) before the timed launch
+    if (s->kernel_variant == 2 && s->g->nx <= 32767) {
+        // table kernels: build the tables (first use) before the timed launch
         NbrTable tb;
+        BlockTable bt;
+        bool block_ok = true;
         VGA_TRY(sim_nbr_table(s, &tb));
-        timing_begin(s, MODE == 1 ? VGA_KERNEL_FUSED_STEP : VGA_KERNEL_DIFFUSE);
-        const vga_status st = comp ? launch_table<MODE, P_COMP>(s, io) : launch_table<MODE, P_F32>(s, io);
-        timing_end(s);
-        VGA_TRY(st);
-        VGA_CHECK_LAUNCH();
-        ++s->launches;
-        return VGA_OK;
+        if (s->wmode == W_BLOCK) VGA_TRY(sim_block_table(s, &bt, &block_ok));
+        if (block_ok) {
+            timing_begin(s, MODE == 1 ? VGA_KERNEL_FUSED_STEP : VGA_KERNEL_DIFFUSE);
+            vga_status st;
+            if (s->wmode == W_BLOCK)
+                st = comp ? launch_table<MODE, W_BLOCK, P_COMP>(s, io, tb, bt) : launch_table<MODE, W_BLOCK, P_F32>(s, io, tb, bt);
+            else
+                st = comp ? launch_table<MODE, W_UNIT, P_COMP>(s, io, tb, bt) : launch_table<MODE, W_UNIT, P_F32>(s, io, tb, bt);
+            timing_end(s);
+            VGA_TRY(st);
+            VGA_CHECK_LAUNCH();
+            ++s->launches;
+            return VGA_OK;
+        }
     }
     timing_begin(s, MODE == 1 ? VGA_KERNEL_FUSED_STEP : VGA_KERNEL_DIFFUSE);
     if (s->wmode == W_BLOCK) {
@@ -569,6 +615,43 @@ vga_status build_nbr_table(const Topo &t, uint32_t *ty, uint32_t *tzm, uint32_t 
     free_chunks(&ch);
     if (e != cudaSuccess) return cuda_fail(e, "k_build_table", __FILE__, __LINE__);
     if (e2 != cudaSuccess) return cuda_fail(e2, "k_build_table", __FILE__, __LINE__);
+    return VGA_OK;
+}
+
+vga_status sim_block_table(vga_sim *s, BlockTable *out, bool *ok) {
+    *ok = false;
+    if (s->wmode != W_BLOCK) return VGA_OK;
+    const int64_t nb = (int64_t)s->bw.nbx * s->bw.nby * s->bw.nbz;
+    if (nb >= kMaxTableBlocks) return VGA_OK;
+    if (s->btable_bs != s->bw.bs) {
+        dfree(s->bnode);
+        dfree(s->bface);
+        s->bnode = nullptr;
+        s->bface = nullptr;
+        s->btable_bs = 0;
+        VGA_TRY(dmalloc((void **)&s->bnode, sizeof(uint32_t) * (size_t)std::max<int64_t>(s->npad, 64), "block table"));
+        VGA_TRY(dmalloc((void **)&s->bface, sizeof(int32_t) * 6 * (size_t)std::max<int64_t>(nb, 1), "block faces"));
+        k_build_bface<<<(unsigned)((nb + kThreads - 1) / kThreads), kThreads, 0, s->stream>>>(s->bw, s->bface);
+        VGA_CHECK_LAUNCH();
+        if (s->n > 0) {
+            Chunks ch;
+            VGA_TRY(build_chunks(s->g->topo(), 1024, &ch, s->stream));
+            const size_t smem = sizeof(uint32_t) * 1024 * decode_words(true);
+            k_build_bnode<<<ch.count, kThreads, smem, s->stream>>>(s->g->topo(), ch.row, 1024, s->bw.bs, s->bw.nbx,
+                                                                 s->bw.nby, s->bnode);
+            const cudaError_t e = cudaGetLastError();
+            const cudaError_t e2 = cudaStreamSynchronize(s->stream);
+            free_chunks(&ch);
+            if (e != cudaSuccess) return cuda_fail(e, "k_build_bnode", __FILE__, __LINE__);
+            if (e2 != cudaSuccess) return cuda_fail(e2, "k_build_bnode", __FILE__, __LINE__);
+        }
+        s->launches += 2;
+        s->btable_bs = s->bw.bs;
+    }
+    out->node = s->bnode;
+    out->face = s->bface;
+    out->theta = s->bw.theta;
+    *ok = true;
     return VGA_OK;
 }
 

@@ -67,6 +67,16 @@ struct NbrTable {
     const uint32_t *ty = nullptr, *tzm = nullptr, *tzp = nullptr;
 };
 
+// Block conductances in table form.  node[i] = block id (bits 0..25) | bit 26+d set when the edge
+// leaving node i through slot d crosses a block face; face[6*b + d] = index into theta of face d of
+// block b (or -1 at the image border).
+struct BlockTable {
+    const uint32_t *node = nullptr;
+    const int32_t *face = nullptr;
+    const float *theta = nullptr;
+};
+constexpr int64_t kMaxTableBlocks = (int64_t)1 << 26;
+
 // Float parameters of one time step (products with dt taken in FP64 on the host, then rounded).
 struct StepParams {
     float a;      // v_dom * dt
@@ -194,6 +204,9 @@ struct vga_sim {
     int32_t *d_err = nullptr;     // device error flag of bounded waits (nonzero: timed out)
     int kernel_variant = 2;       // explicit stencil: 0 decode + direct loads, 1 decode + staged, 2 table
     uint32_t *nbr_table = nullptr;  // 3 x npad words (NbrTable), built on first use
+    uint32_t *bnode = nullptr;      // BlockTable.node (npad), built for the current block side
+    int32_t *bface = nullptr;       // BlockTable.face (6 x blocks)
+    int32_t btable_bs = 0;          // block side the block table was built for (0: none)
     double *loss_work = nullptr;  // block-mass objective scratch
     int64_t loss_cap = 0;
     int64_t param_gen = 0;  // bumped by every change of parameters or conductances
@@ -218,6 +231,9 @@ vga_status sim_convert_out(vga_sim *s, double *d_x);         // state -> device 
 vga_status sim_pack_f32(vga_sim *s, float *d_x, bool to_state);
 vga_status sim_transform_pass(vga_sim *s);  // Y = T(X) for every node, all compartments swapped
 vga_status sim_nbr_table(vga_sim *s, NbrTable *out);  // builds the table on first use
+// Builds (if needed) and returns the block table of the current block conductances; false if the
+// block grid is too large for it (the decode kernels are used then).
+vga_status sim_block_table(vga_sim *s, BlockTable *out, bool *ok);
 // Writes the neighbour-offset table of a node set (offsets are relative, so the arrays may start at
 // any node offset of a larger concatenated range).  Synchronises the stream.
 vga_status build_nbr_table(const Topo &t, uint32_t *ty, uint32_t *tzm, uint32_t *tzp, cudaStream_t st);
