@@ -32,6 +32,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kPar = GR_COUNT + 1;  // per-block partial slots: 7 rate slots + D
+constexpr int kAdjBlocks = 2432;     // grid of the table-driven reverse step (16 per SM on 152 SMs)
 
 struct Rec {
     float *x;   // 5 x npad FP32 values of X^k (recording target, or NULL)
@@ -231,42 +232,72 @@ __global__ void __launch_bounds__(kThreads) k_fused_rec_table(int64_t n, NbrTabl
     rec.y2[i] = __fadd_rn(x2.h, x2.l);
 }
 
-// Table-driven reverse step (same arithmetic as k_adjoint_step).
+// Adds v to gtheta[f] for every lane with f >= 0, combining lanes of the warp that hit the same
+// face first (neighbouring nodes on one block face share it) so that one atomic per face and warp
+// reaches memory.  Must be called by all 32 lanes.
+__device__ __forceinline__ void face_atomic_add(double *gtheta, int32_t f, double v) {
+    const unsigned act = __ballot_sync(0xffffffffu, f >= 0);
+    if (!act) return;
+    const int lane = threadIdx.x & 31;
+    const unsigned peers = __match_any_sync(0xffffffffu, f);
+    const bool leader = (f >= 0) && (lane == __ffs(peers) - 1);
+    double sum = v;
+    unsigned rest = act;
+    while (rest) {
+        const int src = __ffs(rest) - 1;
+        rest &= rest - 1;
+        const double t = __shfl_sync(0xffffffffu, v, src);
+        if (leader && src != lane && ((peers >> src) & 1u)) sum += t;
+    }
+    if (leader) atomicAdd(gtheta + f, sum);
+}
+
+// Table-driven reverse step (same arithmetic as k_adjoint_step), grid-stride over 256-node tiles.
 template <int WM, int PREC>
 __global__ void __launch_bounds__(kThreads) k_adjoint_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                             StateIO io, int64_t npad, const float *__restrict__ xk,
                                                             const float *__restrict__ y2k, double *__restrict__ gpart,
                                                             double *__restrict__ gtheta) {
-    const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < (uint64_t)n;
     const float *__restrict__ L2 = io.in[1];
-    V mu[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) mu[c] = live ? vload<PREC>(io.in[c], io.lin[c], i) : V{0.0f, 0.0f};
-    const float li = mu[1].h;
-    const float yi = live ? __ldg(y2k + i) : 0.0f;
-    const Nb6 nl = gather6(tb, i, live, li, L2);
-    const Nb6 ny = gather6(tb, i, live, yi, y2k);
     double acc[kPar];
 #pragma unroll
     for (int q = 0; q < kPar; ++q) acc[q] = 0.0;
-    if (live) {
-        const uint32_t bn = (WM == W_BLOCK) ? __ldg(bt.node + i) : 0u;
-        const double mc = -(double)p.c;
-        float lsum = 0.0f, ysum = 0.0f;
+    const double mc = -(double)p.c;
+    const int64_t ntile = (n + kThreads - 1) / kThreads;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
+        const bool live = i < (uint64_t)n;
+        V mu[5];
 #pragma unroll
-        for (int d = 0; d < 6; ++d) {
-            if (!((nl.mask >> d) & 1u)) continue;
-            const float g = (WM == W_UNIT) ? 1.0f : table_theta(bt, bn, d);
-            const float dl = __fsub_rn(li, nl.v[d]);
-            const float dy = __fsub_rn(yi, ny.v[d]);
-            lsum = __fmaf_rn(g, dl, lsum);
-            ysum = __fmaf_rn(g, dy, ysum);
-            if (WM == W_BLOCK && (d & 1)) {  // +x, +y, +z: each edge once
-                const int32_t f = table_face(bt, bn, d);
-                if (f >= 0) atomicAdd(gtheta + f, mc * (double)dy * (double)dl);
+        for (int c = 0; c < 5; ++c) mu[c] = live ? vload<PREC>(io.in[c], io.lin[c], i) : V{0.0f, 0.0f};
+        const float li = mu[1].h;
+        const float yi = live ? __ldg(y2k + i) : 0.0f;
+        const Nb6 nl = gather6(tb, i, live, li, L2);
+        const Nb6 ny = gather6(tb, i, live, yi, y2k);
+        const uint32_t bn = (WM == W_BLOCK && live) ? __ldg(bt.node + i) : 0u;
+        float lsum = 0.0f, ysum = 0.0f;
+        int32_t face[3] = {-1, -1, -1};
+        double fval[3] = {0.0, 0.0, 0.0};
+        if (live) {
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                if (!((nl.mask >> d) & 1u)) continue;
+                const float g = (WM == W_UNIT) ? 1.0f : table_theta(bt, bn, d);
+                const float dl = __fsub_rn(li, nl.v[d]);
+                const float dy = __fsub_rn(yi, ny.v[d]);
+                lsum = __fmaf_rn(g, dl, lsum);
+                ysum = __fmaf_rn(g, dy, ysum);
+                if (WM == W_BLOCK && (d & 1)) {  // +x, +y, +z: each edge once
+                    face[d >> 1] = table_face(bt, bn, d);
+                    fval[d >> 1] = mc * (double)dy * (double)dl;
+                }
             }
         }
+        if (WM == W_BLOCK) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) face_atomic_add(gtheta, face[q], fval[q]);
+        }
+        if (!live) continue;
         acc[GR_COUNT] -= (double)li * (double)ysum;
         vadd<PREC>(mu[1], __fmul_rn(-p.c, lsum));
         float xs[5];
@@ -536,7 +567,9 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     bool table = s->g->nx <= 32767;
     if (table) VGA_TRY(sim_nbr_table(s, &tb));
     if (table && WM == W_BLOCK) VGA_TRY(sim_block_table(s, &bt, &table));
-    const int G = table ? (int)((s->n + kThreads - 1) / kThreads) : s->chunks.count;
+    const int Gt = (int)std::min<int64_t>(kAdjBlocks, (s->n + kThreads - 1) / kThreads);  // grid of the table kernels
+    const int Gf = (int)((s->n + kThreads - 1) / kThreads);
+    const int G = table ? Gt : s->chunks.count;  // blocks writing gradient partials
     const size_t smem = sizeof(uint32_t) * (size_t)s->chunks.cap * decode_words(WM == W_BLOCK);
     const int64_t npad = s->npad;
     cudaStream_t st = s->stream;
@@ -563,7 +596,7 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
             rec.y2 = a->rec_y2 + (size_t)j * npad;
             timing_begin(s, VGA_KERNEL_FUSED_STEP);
             if (table)
-                k_fused_rec_table<WM, PREC><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
+                k_fused_rec_table<WM, PREC><<<Gf, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
                                                                    io_from(a->work[wb], a->work[1 - wb], npad), npad, rec);
             else
                 k_fused_rec<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,

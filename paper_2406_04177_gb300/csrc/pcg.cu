@@ -153,23 +153,28 @@ __global__ void __launch_bounds__(kThreads) k_cg_rhs(int64_t n, const float *__r
     if (i < n) x[i] = (double)__ldg(y2 + i) + (PREC == P_COMP ? (double)bf16_bits_to_float(__ldg(y2l + i)) : 0.0);
 }
 
+// Grid-stride loops over 256-node tiles (lanes = consecutive nodes) on a fixed grid, so the block
+// partials stay few and the single-block scalar kernels stay short.
 template <int PREC>
 __global__ void __launch_bounds__(kThreads) k_cg_init_table_b(int64_t n, NbrTable tb, double c, CgVecs v,
                                                               double *__restrict__ part) {
-    const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < (uint64_t)n;
-    const double bi = live ? v.x[i] : 0.0;
-    double deg = 0.0;
-    const double lb = nbr_sum_table(tb, i, live, bi, v.x, deg);
     double acc[3] = {0.0, 0.0, 0.0};
-    if (live) {
-        const double ri = -c * lb;
-        const double ti = 1.0 / (1.0 + c * deg);
-        v.r[i] = ri;
-        v.t[i] = ti;
-        acc[0] = ri * ti * ri;
-        acc[1] = ri * ri;
-        acc[2] = bi * bi;
+    const int64_t ntile = (n + kThreads - 1) / kThreads;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
+        const bool live = i < (uint64_t)n;
+        const double bi = live ? v.x[i] : 0.0;
+        double deg = 0.0;
+        const double lb = nbr_sum_table(tb, i, live, bi, v.x, deg);
+        if (live) {
+            const double ri = -c * lb;
+            const double ti = 1.0 / (1.0 + c * deg);
+            v.r[i] = ri;
+            v.t[i] = ti;
+            acc[0] += ri * ti * ri;
+            acc[1] += ri * ri;
+            acc[2] += bi * bi;
+        }
     }
     __shared__ double out[3];
     block_sum_store<3>(acc, out);
@@ -180,16 +185,19 @@ __global__ void __launch_bounds__(kThreads) k_spmv_table(int64_t n, NbrTable tb,
                                                          double *__restrict__ q, double *__restrict__ part,
                                                          const CgScalars *__restrict__ sc) {
     if (sc->done) return;
-    const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < (uint64_t)n;
-    const double pi = live ? p[i] : 0.0;
-    double deg;
-    const double lp = nbr_sum_table(tb, i, live, pi, p, deg);
     double acc[1] = {0.0};
-    if (live) {
-        const double qi = pi + c * lp;
-        q[i] = qi;
-        acc[0] = pi * qi;
+    const int64_t ntile = (n + kThreads - 1) / kThreads;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
+        const bool live = i < (uint64_t)n;
+        const double pi = live ? p[i] : 0.0;
+        double deg;
+        const double lp = nbr_sum_table(tb, i, live, pi, p, deg);
+        if (live) {
+            const double qi = pi + c * lp;
+            q[i] = qi;
+            acc[0] += pi * qi;
+        }
     }
     __shared__ double out[1];
     block_sum_store<1>(acc, out);
@@ -301,7 +309,7 @@ vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgSc
     const bool table = (WM == W_UNIT) && s->g->nx <= 32767;
     NbrTable tb;
     if (table) VGA_TRY(sim_nbr_table(s, &tb));
-    const int Gs = table ? (int)grid_for(s->n, kThreads) : G;  // blocks of the stencil kernels
+    const int Gs = table ? (int)std::min<int64_t>(kEwBlocks, grid_for(s->n, kThreads)) : G;  // stencil grid
     timing_begin(s, VGA_KERNEL_PCG_STENCIL);
     if (table) {
         k_cg_rhs<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->comp(1), s->lcomp(1), v.x);
