@@ -104,7 +104,7 @@ vga_status vga_graph_free(vga_graph *g);
 
 typedef struct vga_params {
     double D;       /* DOM diffusion coefficient D_DOM */
-    double dt;      /* time step, shared by transformation and diffusion */
+    double dt;      /* time step of the diffusion (and of the transformation unless dt_transform > 0) */
     double rho;     /* respiration rate */
     double mu;      /* mortality rate */
     double beta;    /* fraction of dead biomass returned to DOM, in [0, 1] */
@@ -117,6 +117,16 @@ typedef struct vga_params {
     double cg_rtol;    /* implicit only: stop when ||r||_2 <= cg_rtol ||b||_2 */
     int32_t cg_maxit;  /* implicit only: iteration cap per step */
     int32_t state_precision; /* VGA_STATE_* */
+    /* Transformation step (Sec. III: when the two processes use different steps, the one with
+     * the smaller step is repeated; Table 1 test 3 uses 0.1 s diffusion, 0.43 s transformation).
+     * 0 means dt.  Otherwise the simulation keeps a global clock: diffusion step k covers
+     * [k dt, (k+1) dt) and is preceded by one transformation of step dt_transform for each tick
+     * m * dt_transform (m = 0, 1, ...) in that interval, i.e. ceil((k+1) r - 1e-9) -
+     * ceil(k r - 1e-9) of them with r = dt / dt_transform (zero, one or several).  k counts every
+     * step taken since creation (vga_sim_get_stats steps_done, restored by vga_sim_load_state).
+     * Supported by vga_sim_step with either scheme; the adjoint and the batch reject it
+     * (VGA_ERR_UNSUPPORTED). */
+    double dt_transform;
 } vga_params;
 
 /* ============================================================================================

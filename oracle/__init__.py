@@ -73,6 +73,10 @@ def _load():
             lib.vo_adjoint_run.restype = C.c_int
             lib.vo_adjoint_run.argtypes = [I64, P, P, P, P, I64, I64, P, P, P, P, P]
             lib.vo_num_threads.restype = C.c_int
+            lib.vo_ticks_before.restype = I64
+            lib.vo_ticks_before.argtypes = [I64, D, D]
+            lib.vo_run_subcycled.restype = C.c_int
+            lib.vo_run_subcycled.argtypes = [I64, P, P, P, C.c_int, C.c_int, P, I64, D, I64, D, C.c_int, P]
             _lib = lib
     return _lib
 
@@ -158,6 +162,29 @@ def explicit_run(nbr: np.ndarray, p: dict, X: np.ndarray, nsteps: int, g6=None,
     if _load().vo_explicit_run(n, _ptr(nbr), _ptr(g), C.byref(pp), int(transform), _ptr(Xo), int(nsteps)):
         raise MemoryError("oracle explicit run failed")
     return Xo
+
+
+def run_subcycled(nbr, p: dict, X: np.ndarray, nsteps: int, dt_transform: float, step0: int = 0,
+                  g6=None, transform: int = 0, scheme: int = 0, rtol: float = 1e-10, maxit: int = 10000) -> np.ndarray:
+    """Steps of p['dt'] (scheme 0: Scheme 1, scheme 1: Scheme 2 by PCG) with the transformation on
+    its own step dt_transform (Sec. III, global-clock reading); step0 = diffusion steps already taken."""
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    n = nbr.shape[0]
+    Xo = np.ascontiguousarray(X, dtype=np.float64).reshape(5, n).copy()
+    pp = _params(p)
+    it = C.c_int64(0)
+    st = _load().vo_run_subcycled(n, _ptr(nbr), _ptr(_g6(g6, n)), C.byref(pp), int(transform), int(scheme), _ptr(Xo),
+                                  int(nsteps), float(dt_transform), int(step0), float(rtol), int(maxit), C.byref(it))
+    if st < 0:
+        raise MemoryError("oracle sub-cycled run failed")
+    if st > 0:
+        raise RuntimeError("oracle PCG did not converge")
+    return Xo
+
+
+def ticks_before(k: int, dt: float, dt_transform: float) -> int:
+    """Transformation ticks in [0, k dt) under the global-clock reading."""
+    return int(_load().vo_ticks_before(int(k), float(dt), float(dt_transform)))
 
 
 def diffuse_explicit(nbr, c: float, m: np.ndarray, g6=None) -> np.ndarray:

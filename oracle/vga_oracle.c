@@ -583,3 +583,48 @@ int vo_adjoint_run(int64_t n, const int32_t *nbr, const double *g6, const vo_par
     free(ck); free(seg); free(lam); free(y2); free(gthr);
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------------
+ * Different time steps for transformation and diffusion (Sec. III: the process with the smaller
+ * step is iterated; Table 1 tests 2-4).  Reading: a global clock.  Diffusion advances by dt per
+ * step; the transformation, with its own step dt_transform, fires once for every tick
+ * m * dt_transform (m = 0, 1, ...) in [k dt, (k+1) dt), before diffusion step k.  The number of
+ * ticks in [0, k dt) is ceil(k r) with r = dt / dt_transform (a 1e-9 guard absorbs rounding of r).
+ * step0 is the number of diffusion steps already taken (the clock's origin).
+ * ---------------------------------------------------------------------------------------- */
+int64_t vo_ticks_before(int64_t k, double dt, double dt_transform) {
+    if (k <= 0) return 0;
+    const double r = dt / dt_transform;
+    return (int64_t)ceil((double)k * r - 1e-9);
+}
+
+int vo_run_subcycled(int64_t n, const int32_t *nbr, const double *g6, const vo_params *p, int transform,
+                     int scheme, double *X, int64_t nsteps, double dt_transform, int64_t step0,
+                     double rtol, int maxit, int64_t *total_iters) {
+    double *y2 = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    if (!y2) return -1;
+    vo_params pt = *p;
+    pt.dt = dt_transform;  /* the transformation uses its own step */
+    const double c = p->D * p->dt;
+    int status = 0;
+    int64_t tot = 0;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        const int64_t kk = step0 + k;
+        const int64_t ticks = vo_ticks_before(kk + 1, p->dt, dt_transform) - vo_ticks_before(kk, p->dt, dt_transform);
+        for (int64_t m = 0; m < ticks; ++m) transform_all(n, &pt, transform, X);
+        memcpy(y2, X + n, sizeof(double) * (size_t)n);
+        if (scheme == 0) {
+            vo_diffuse_explicit(n, nbr, g6, c, y2, X + n);
+        } else {
+            int it = 0;
+            double rr = 0.0;
+            const int st = vo_pcg_solve(n, nbr, g6, c, y2, X + n, rtol, maxit, &it, &rr);
+            if (st < 0) { free(y2); return -1; }
+            if (st) status = 1;
+            tot += it;
+        }
+    }
+    if (total_iters) *total_iters = tot;
+    free(y2);
+    return status;
+}

@@ -47,7 +47,7 @@ class vga_params(C.Structure):
                 ("beta", C.c_double), ("v_som", C.c_double), ("v_fom", C.c_double),
                 ("v_dom", C.c_double), ("K_dom", C.c_double), ("scheme", C.c_int32),
                 ("transform", C.c_int32), ("cg_rtol", C.c_double), ("cg_maxit", C.c_int32),
-                ("state_precision", C.c_int32)]
+                ("state_precision", C.c_int32), ("dt_transform", C.c_double)]
 
 
 class vga_tune_entry(C.Structure):
@@ -245,7 +245,8 @@ def make_params(p: dict) -> vga_params:
     return vga_params(D=p["D"], dt=p["dt"], rho=p["rho"], mu=p["mu"], beta=p["beta"], v_som=p["v_som"],
                       v_fom=p["v_fom"], v_dom=p["v_dom"], K_dom=p["K_dom"], scheme=int(p.get("scheme", 0)),
                       transform=int(p.get("transform", 0)), cg_rtol=float(p.get("cg_rtol", 1e-8)),
-                      cg_maxit=int(p.get("cg_maxit", 500)), state_precision=int(p.get("state_precision", 0)))
+                      cg_maxit=int(p.get("cg_maxit", 500)), state_precision=int(p.get("state_precision", 0)),
+                      dt_transform=float(p.get("dt_transform", 0.0)))
 
 
 def vga_sim_create(g, params: dict, stream=None) -> C.c_void_p:

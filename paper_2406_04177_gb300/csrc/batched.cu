@@ -325,6 +325,8 @@ vga_status vga_batch_create(const vga_graph *const *graphs, const vga_params *pa
               p.beta <= 1 && p.rho >= 0 && p.mu >= 0 && p.v_som >= 0 && p.v_fom >= 0 && p.v_dom >= 0))
             return fail(VGA_ERR_INVALID_ARG, "invalid parameters of an instance");
         if (6.0 * p.D * p.dt > 1.0 + 1e-12) return fail(VGA_ERR_UNSTABLE_DT, "an instance has 6 D dt > 1");
+        if (!(p.dt_transform == 0.0 || p.dt_transform == p.dt))
+            return fail(VGA_ERR_UNSUPPORTED, "batched instances need dt_transform = 0 (one common step)");
     }
     vga_batch *b = new (std::nothrow) vga_batch();
     if (!b) return fail(VGA_ERR_OOM, "host allocation failed");

@@ -122,6 +122,9 @@ static vga_status validate_params(const vga_params *p, double max_g) {
     for (double v : vals)
         if (!finite_nonneg(v)) return fail(VGA_ERR_INVALID_ARG, "rates and D must be finite and >= 0");
     if (!(std::isfinite(p->dt) && p->dt > 0.0)) return fail(VGA_ERR_INVALID_ARG, "dt must be finite and > 0");
+    if (!finite_nonneg(p->dt_transform)) return fail(VGA_ERR_INVALID_ARG, "dt_transform must be finite and >= 0");
+    const double dtt = p->dt_transform > 0.0 ? p->dt_transform : p->dt;
+    if (!(p->dt / dtt < 1.0e6)) return fail(VGA_ERR_INVALID_ARG, "dt / dt_transform must stay below 1e6");
     if (!(std::isfinite(p->beta) && p->beta >= 0.0 && p->beta <= 1.0))
         return fail(VGA_ERR_INVALID_ARG, "beta must lie in [0, 1]");
     if (!(std::isfinite(p->K_dom) && p->K_dom > 0.0)) return fail(VGA_ERR_INVALID_ARG, "K_dom must be finite and > 0");
@@ -136,8 +139,8 @@ static vga_status validate_params(const vga_params *p, double max_g) {
         if (p->cg_maxit < 1) return fail(VGA_ERR_INVALID_ARG, "cg_maxit must be >= 1");
     }
     // products that become FP32 constants must stay finite
-    const double prods[] = {p->D * p->dt, p->rho * p->dt, p->mu * p->dt, p->v_som * p->dt, p->v_fom * p->dt,
-                            p->v_dom * p->dt};
+    const double prods[] = {p->D * p->dt, p->rho * dtt, p->mu * dtt, p->v_som * dtt, p->v_fom * dtt,
+                            p->v_dom * dtt};
     for (double v : prods)
         if (!(v < 3.0e38)) return fail(VGA_ERR_INVALID_ARG, "rate * dt overflows FP32");
     if (p->scheme == VGA_SCHEME_EXPLICIT && 6.0 * p->D * p->dt * max_g > 1.0 + 1e-12) {
@@ -534,6 +537,7 @@ vga_status vga_adjoint_forward(vga_sim *s, int64_t n_steps, int32_t ckpt_every) 
         s->params.state_precision != VGA_STATE_COMPENSATED)
         return fail(VGA_ERR_UNSUPPORTED,
                     "the adjoint covers the explicit scheme, synchronous transformation, compensated state");
+    if (s->subcycled()) return fail(VGA_ERR_UNSUPPORTED, "the adjoint needs dt_transform = 0 (one common step)");
     return sim_adjoint_forward(s, n_steps, ckpt_every);
 }
 

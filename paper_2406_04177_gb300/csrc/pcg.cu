@@ -384,7 +384,14 @@ vga_status sim_step_implicit(vga_sim *s, int64_t n_steps) {
     CgScalars *sc = reinterpret_cast<CgScalars *>(s->cg_scalars);
     vga_status worst = VGA_OK;
     for (int64_t k = 0; k < n_steps; ++k) {
-        VGA_TRY(sim_transform_pass(s));
+        if (s->subcycled()) {
+            s->sp.ntrans = sim_ticks_of_step(s, s->steps_done);
+            const vga_status ts = sim_transform_pass(s);
+            s->sp.ntrans = 1;
+            VGA_TRY(ts);
+        } else {
+            VGA_TRY(sim_transform_pass(s));
+        }
         const bool comp = s->precision() == P_COMP;
         vga_status st;
         if (s->wmode == W_BLOCK)

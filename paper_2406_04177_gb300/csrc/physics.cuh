@@ -183,6 +183,13 @@ __device__ __forceinline__ void transform(V &x1, V &x2, V &x3, V &x4, V &x5, con
     else transform_async<PREC>(x1, x2, x3, x4, x5, p);
 }
 
+// p.ntrans transformations of step dt_transform (the rates in p are already scaled by it).
+template <int TR, int PREC>
+__device__ __forceinline__ void transform_n(V &x1, V &x2, V &x3, V &x4, V &x5, const StepParams &p) {
+#pragma unroll 1
+    for (int t = 0; t < p.ntrans; ++t) transform<TR, PREC>(x1, x2, x3, x4, x5, p);
+}
+
 }  // namespace vga
 
 namespace vga {

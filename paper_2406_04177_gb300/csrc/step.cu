@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kThreads) k_transform(int64_t n, StepParams p,
     V x[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) x[c] = vload<PREC>(io.in[c], io.lin[c], i);
-    transform<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
+    transform_n<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
 #pragma unroll
     for (int c = 0; c < 5; ++c) vstore<PREC>(io.out[c], io.lout[c], i, x[c]);
 }
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Topo t, const int32_t *__r
             vround<PREC>(x2);  // as if X^{k+1} had been stored (split runs stay bit-identical)
             V x1 = vload<PREC>(io.in[0], io.lin[0], i), x3 = vload<PREC>(io.in[2], io.lin[2], i),
               x4 = vload<PREC>(io.in[3], io.lin[3], i), x5 = vload<PREC>(io.in[4], io.lin[4], i);
-            transform<TR, PREC>(x1, x2, x3, x4, x5, p);
+            transform_n<TR, PREC>(x1, x2, x3, x4, x5, p);
             vstore<PREC>(io.out[0], io.lout[0], i, x1);
             vstore<PREC>(io.out[1], io.lout[1], i, x2);
             vstore<PREC>(io.out[2], io.lout[2], i, x3);
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(NT) k_stencil_staged(Topo t, const int32_t *__
                 for (int c = 0; c < 5; ++c)
                     if (c != 1) xs[c] = V{sh[c * CAP + k], PREC == P_COMP ? bf16_bits_to_float(sl[c * CAP + k]) : 0.0f};
                 xs[1] = x2;
-                transform<TR, PREC>(xs[0], xs[1], xs[2], xs[3], xs[4], p);
+                transform_n<TR, PREC>(xs[0], xs[1], xs[2], xs[3], xs[4], p);
             } else {
                 xs[1] = x2;
             }
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable 
         vround<PREC>(x2);
         V x1 = vload<PREC>(io.in[0], io.lin[0], i), x3 = vload<PREC>(io.in[2], io.lin[2], i),
           x4 = vload<PREC>(io.in[3], io.lin[3], i), x5 = vload<PREC>(io.in[4], io.lin[4], i);
-        transform<TR, PREC>(x1, x2, x3, x4, x5, p);
+        transform_n<TR, PREC>(x1, x2, x3, x4, x5, p);
         vstore<PREC>(io.out[0], io.lout[0], i, x1);
         vstore<PREC>(io.out[1], io.lout[1], i, x2);
         vstore<PREC>(io.out[2], io.lout[2], i, x3);
@@ -505,22 +505,37 @@ StateIO state_io_inplace(vga_sim *s) {
 
 vga_status sim_prepare_params(vga_sim *s, const vga_params *p) {
     StepParams sp;
-    sp.a = (float)(p->v_dom * p->dt);
+    const double dtt = p->dt_transform > 0.0 ? p->dt_transform : p->dt;
+    sp.a = (float)(p->v_dom * dtt);
     sp.K = (float)p->K_dom;
-    sp.r = (float)(p->rho * p->dt);
-    sp.m = (float)(p->mu * p->dt);
+    sp.r = (float)(p->rho * dtt);
+    sp.m = (float)(p->mu * dtt);
     sp.beta = (float)p->beta;
     sp.omb = (float)(1.0 - p->beta);
-    sp.f = (float)(p->v_fom * p->dt);
-    sp.s = (float)(p->v_som * p->dt);
+    sp.f = (float)(p->v_fom * dtt);
+    sp.s = (float)(p->v_som * dtt);
     sp.c = (float)(p->D * p->dt);
     sp.transform = p->transform;
+    sp.ntrans = 1;
     s->sp = sp;
     s->params = *p;
     return VGA_OK;
 }
 
+int64_t sim_ticks_before(const vga_sim *s, int64_t k) {
+    if (!s->subcycled()) return k;
+    if (k <= 0) return 0;
+    const double r = s->params.dt / s->params.dt_transform;
+    const double kr = (double)k * r;
+    return (int64_t)std::ceil(kr - 1e-9);
+}
+
+int sim_ticks_of_step(const vga_sim *s, int64_t k) {
+    return (int)(sim_ticks_before(s, k + 1) - sim_ticks_before(s, k));
+}
+
 vga_status sim_transform_pass(vga_sim *s) {
+    if (s->sp.ntrans == 0) return VGA_OK;  // identity: leave the state where it is
     StateIO io = state_io(s);
     const unsigned grid = grid_for(s->n, kThreads);
     const bool comp = s->precision() == P_COMP;
@@ -544,8 +559,17 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
         s->steps_done += std::max<int64_t>(n_steps, 0);
         return VGA_OK;
     }
+    const bool sub = s->subcycled();
+    const int64_t k0 = s->steps_done;
+    // ntrans is reset on every exit so that no other path sees a sub-cycled count
+    struct Reset {
+        StepParams &sp;
+        ~Reset() { sp.ntrans = 1; }
+    } reset{s->sp};
+    if (sub) s->sp.ntrans = sim_ticks_of_step(s, k0);
     VGA_TRY(sim_transform_pass(s));
     for (int64_t k = 1; k < n_steps; ++k) {
+        if (sub) s->sp.ntrans = sim_ticks_of_step(s, k0 + k);
         VGA_TRY(launch_stencil<1>(s, state_io(s)));
         for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
     }

@@ -89,6 +89,7 @@ struct StepParams {
     float s;      // v_som * dt
     float c;      // D * dt
     int transform;
+    int ntrans;   // transformations applied per pass (1; 0 or more when the steps differ)
 };
 
 // Input and output compartment arrays of one pass over the state.
@@ -216,6 +217,8 @@ struct vga_sim {
     uint16_t *lcomp(int c) { return lbuf[cur[c]] + (size_t)c * npad; }
     uint16_t *lspare(int c) { return lbuf[1 - cur[c]] + (size_t)c * npad; }
     int precision() const { return params.state_precision; }
+    // transformation and diffusion on different steps (global clock of vga_params.dt_transform)
+    bool subcycled() const { return params.dt_transform > 0.0 && params.dt_transform != params.dt; }
 };
 
 namespace vga {
@@ -230,6 +233,8 @@ vga_status sim_convert_in(vga_sim *s, const double *d_x);    // device FP64 (5 x
 vga_status sim_convert_out(vga_sim *s, double *d_x);         // state -> device FP64 (5 x n)
 vga_status sim_pack_f32(vga_sim *s, float *d_x, bool to_state);
 vga_status sim_transform_pass(vga_sim *s);  // Y = T(X) for every node, all compartments swapped
+int64_t sim_ticks_before(const vga_sim *s, int64_t k);  // transformations in the first k steps
+int sim_ticks_of_step(const vga_sim *s, int64_t k);      // transformations before diffusion step k
 vga_status sim_nbr_table(vga_sim *s, NbrTable *out);  // builds the table on first use
 // Builds (if needed) and returns the block table of the current block conductances; false if the
 // block grid is too large for it (the decode kernels are used then).

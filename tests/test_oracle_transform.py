@@ -174,3 +174,41 @@ def test_paper_constants(oracle_lib):
     assert round(100 * v["initial_mb_ug"] / tot, 3) == v["mb_percent"]
     # the largest stable explicit step of Sec. IV.C (0.1 s) lies below the positivity limit 1/(6D)
     assert v["largest_explicit_dt_s"] < 86400.0 / (6 * v["D_dom_voxel2_per_day"])
+
+
+def test_subcycling_reading(oracle_lib):
+    """Different transformation and diffusion steps (Sec. III, Table 1): equal steps reproduce the
+    plain run exactly; the tick count follows the global clock (0.1 s diffusion, 0.43 s
+    transformation: ticks at 0, 0.43, 0.86, ... s); with only FOM hydrolysis active, FOM after N
+    steps is x4_0 (1 - v_FOM dt_T)^(ticks before N dt)."""
+    import numpy as np
+
+    img = np.zeros((3, 4, 5), dtype=np.uint8)
+    g = oracle_lib.graph_build(img)
+    X0 = synth.random_masses(g.n, 5, scale=1e-3, density=0.8)
+    p = synth.paper_params()
+    a = oracle_lib.explicit_run(g.nbr, p, X0, 37)
+    b = oracle_lib.run_subcycled(g.nbr, p, X0, 37, dt_transform=p["dt"])
+    assert np.array_equal(a, b)
+    s = 1.0 / 86400.0
+    ticks = [oracle_lib.ticks_before(k, 0.1 * s, 0.43 * s) for k in range(10)]
+    assert ticks == [0, 1, 1, 1, 1, 2, 2, 2, 2, 3]  # multiples of 0.43 below 0, 0.1, ..., 0.9 s
+    assert [oracle_lib.ticks_before(k, 2.0, 1.0) for k in range(4)] == [0, 2, 4, 6]
+    q = dict(p, rho=0.0, mu=0.0, v_som=0.0, v_dom=0.0, D=0.0, v_fom=3e3, dt=0.1 * s)
+    X = np.zeros((5, g.n))
+    X[3] = 1.0
+    out = oracle_lib.run_subcycled(g.nbr, q, X, 50, dt_transform=0.43 * s)
+    nt = oracle_lib.ticks_before(50, 0.1 * s, 0.43 * s)
+    assert nt == 12
+    assert np.allclose(out[3], (1 - 3e3 * 0.43 * s) ** nt, rtol=1e-13)
+    # splitting the run keeps the clock
+    dtt = 4.3 * p["dt"]
+    half = oracle_lib.run_subcycled(g.nbr, p, X0, 20, dt_transform=dtt)
+    rest = oracle_lib.run_subcycled(g.nbr, p, half, 17, dt_transform=dtt, step0=20)
+    full = oracle_lib.run_subcycled(g.nbr, p, X0, 37, dt_transform=dtt)
+    assert np.array_equal(rest, full)
+    # the implicit scheme with equal steps reproduces the plain implicit run
+    ai = oracle_lib.implicit_run(g.nbr, synth.paper_params(dt=1.0 / 86400), X0, 5, rtol=1e-12)[0]
+    bi = oracle_lib.run_subcycled(g.nbr, synth.paper_params(dt=1.0 / 86400), X0, 5, dt_transform=1.0 / 86400,
+                                  scheme=1, rtol=1e-12)
+    assert np.allclose(ai, bi, rtol=1e-11, atol=0)  # PCG dot products may sum in another order
