@@ -222,7 +222,7 @@ def bench_ours(a):
     sim = vga.Sim(g, params, stream=stream)
     x0_dev = torch.from_numpy(X0).cuda()
     sim.set_masses(x0_dev)
-    tune = sim.autotune(20)  # picks the stencil variant / chunk size; state left unchanged
+    tune = sim.autotune(100)  # picks the stencil variant / chunk / wavefront shape; state left unchanged
     tot0 = sim.totals()
 
     S = a.substeps
@@ -273,12 +273,16 @@ def bench_ours(a):
     achieved = BYTES_PER_PVS * n / mean_launch_s / 1e9
     traffic = recorded_traffic(n)
     best = tune["best"] or {}
+    variant = best.get("variant")
     kname = {0: "k_stencil (chunk decode, direct loads)", 1: "k_stencil_staged (chunk decode, bulk-copy staging)",
-             2: "k_stencil_table (neighbour-offset table)"}.get(best.get("variant"), "k_stencil")
+             2: "k_stencil_table (neighbour-offset table)",
+             3: f"k_wave (neighbour-offset table; {S - 1} fused passes per persistent launch as an L2 wavefront, "
+                f"chunks of {best.get('chunk')} nodes, {best.get('depth')} passes per block)"}.get(variant, "k_stencil")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": f"{kname}, fused pass (diffuse the stored transformed DOM, then transform)",
-                "algorithmic_bytes_per_launch": BYTES_PER_PVS * n, "mean_launch_ms": mean_launch_s * 1e3,
-                "launches_timed": fused_count, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+                "algorithmic_bytes_per_pass": BYTES_PER_PVS * n, "mean_pass_ms": mean_launch_s * 1e3,
+                "passes_timed": fused_count, "passes_per_launch": (S - 1) if variant == 3 else 1,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_src == "measured" else "fallback 6.8 TB/s",
                 "pvs_x40B_over_peak": value / world * BYTES_PER_PVS / (peak * 1e9)}
 
@@ -340,6 +344,7 @@ def bench_ours(a):
         simi.close()
         extras["adjoint"] = bench_adjoint(vga, g, params, x0_dev, n, stream)
         extras["batched"] = bench_batched(vga, a)
+        extras["pngm"] = bench_pngm(vga, g, n, stream)
         out.update(extras)
 
     if rank == 0 and world == 1 or (rank == 0 and world > 1):
@@ -431,6 +436,77 @@ def bench_batched(vga, a, count=64, nsteps=5000):
             "time_steps": nsteps, "seconds": t1 - t0, "setup_seconds": t_setup, "launch": tune["best"],
             "graph_replays": st["graph_replays"], "capture_failed": bool(st["capture_failed"]),
             "grid_blocks": st["grid_blocks"]}
+
+
+def bench_pngm(vga, g, n, stream, bs=16, scenarios=2, records=12, epochs=1000):
+    """Coarse-model calibration of Sec. V.B on the full workload: primitives = the pore nodes of
+    each 16^3 cube; DOM scenarios diffused at 0.1 s and recorded every 10 s (100 steps) as
+    primitive masses; 1000 normalised SGD epochs of 4 pairs on Objective 2; 10 Scheme 4 steps of
+    10 s.  The restriction kernel is timed with CUDA events on the simulation's stream
+    (algorithmic bytes: 4 B label + 6 B compensated DOM per node)."""
+    import torch
+
+    import synth
+    from paper_2406_04177_gb300 import fit
+
+    t0 = time.perf_counter()
+    vox = g.export(labels=False, nbr=False)["voxel_of_node"]
+    lab, q = synth.block_primitives(g.shape, vox, bs)
+    del vox
+    t1 = time.perf_counter()
+    pg = vga.Pngm(g, lab, q, stream=stream)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    p = synth.diffusion_params(0.1)
+    scen = [synth.dom_scenario(n, 500 + s) for s in range(scenarios)]
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    data, pairs = fit.pngm_dataset(g, pg, p, scen, steps_per_record=100, records=records, stream=stream)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    # restriction kernel alone
+    sim = vga.Sim(g, p, stream=stream)
+    sim.set_masses(scen[0])
+    out = torch.empty(q, dtype=torch.float64, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    for _ in range(3):
+        pg.restrict(sim, 1, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record(st)
+    for _ in range(reps):
+        pg.restrict(sim, 1, out)
+    e1.record(st)
+    e1.synchronize()
+    r_ms = e0.elapsed_time(e1) / reps
+    sim.close()
+    dt_c = 10.0 / 86400.0
+    theta0 = pg.get_theta()
+    torch.cuda.synchronize()
+    t5 = time.perf_counter()
+    res = fit.fit_pngm(pg, data, pairs, p["D"], dt_c, objective=2, epochs=epochs,
+                       lr0=0.05 * float(np.mean(theta0)), halve_every=10, seed=1)
+    t6 = time.perf_counter()
+    m = data[records].clone()
+    torch.cuda.synchronize()
+    t7 = time.perf_counter()
+    pg.step(m, 10, 1, p["D"], dt_c, cg_rtol=1e-10, cg_maxit=5000)
+    t8 = time.perf_counter()
+    info = pg.info()
+    pg.close()
+    restrict_bytes = 10 * n
+    return {"q": q, "n_slots": info["n_slots"], "block_side": bs, "labels_seconds": t1 - t0,
+            "coarse_graph_seconds": t2 - t1,
+            "data": {"scenarios": scenarios, "records": records, "steps_per_record": 100, "dt_s": 0.1,
+                     "seconds": t4 - t3, "value": n * scenarios * records * 100 / (t4 - t3),
+                     "unit": UNIT + " (voxel run incl. restriction every 100 steps)"},
+            "restrict": {"mean_ms": r_ms, "algorithmic_bytes": restrict_bytes,
+                         "achieved_gbs": restrict_bytes / (r_ms * 1e-3) / 1e9},
+            "fit": {"epochs": epochs, "pairs_per_epoch": 4, "seconds": t6 - t5,
+                    "epochs_per_s": epochs / (t6 - t5), "loss_first": float(res["loss"][0]),
+                    "loss_last": float(res["loss"][-1]), "loss_min": float(np.min(res["loss"]))},
+            "scheme4": {"steps": 10, "dt_s": 10.0, "seconds": t8 - t7,
+                        "cg_iterations": info["last_cg_iterations"], "last_relres": info["last_cg_relres"]}}
 
 
 def bench_reference(a):

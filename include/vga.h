@@ -41,7 +41,7 @@ typedef enum vga_status {
     VGA_ERR_CUDA = -3,          /* a CUDA runtime call failed (detail in vga_last_error) */
     VGA_ERR_UNSTABLE_DT = -4,   /* explicit step beyond the positivity limit D dt max_i sum_j g_ij <= 1 */
     VGA_ERR_NOT_CONVERGED = -5, /* the implicit solve reached cg_maxit before cg_rtol */
-    VGA_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up (persistent batched kernel) */
+    VGA_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up (persistent kernels) */
     VGA_ERR_NONFINITE = -7,     /* non-finite value found in a state array */
     VGA_ERR_UNSUPPORTED = -8    /* combination of options not implemented */
 } vga_status;
@@ -242,14 +242,27 @@ vga_status vga_loss_block_mass(vga_sim *s, int32_t block_side, uint32_t comp_mas
  *   1  as 0, with each chunk's own state staged in shared memory by bulk asynchronous copies and
  *      written back the same way (chunk = 512, 1024 or 2048);
  *   2  one node per thread with a precomputed neighbour-offset table (12 bytes per node, built on
- *      first use; unit conductances and nx <= 32767, otherwise variant 0 runs).  `chunk` is ignored.
+ *      first use; nx <= 32767, otherwise variant 0 runs).  `chunk` is ignored;
+ *   3  the table passes of one vga_sim_step call run inside one persistent cooperative launch as a
+ *      wavefront over chunks of `chunk` nodes (a multiple of 256), so that each pass reads the
+ *      previous pass's output from L2; 4 passes per block, CTAs per SM from the occupancy (see
+ *      vga_sim_set_wavefront).  Not used when dt_transform differs from dt (variant 2 runs).
  * The default is 2. */
 vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t chunk);
+
+/* Selects variant 3 with `chunk` nodes per work item (multiple of 256 in [256, 8192]), `depth`
+ * passes per block of the skewed order (1..64: the passes whose intermediate states stay in L2),
+ * and ctas_per_sm persistent CTAs per SM (0 = as many as fit).  Every wait of the persistent
+ * kernel is bounded; one that gives up makes the next synchronising call return VGA_ERR_TIMEOUT
+ * (the state is then undefined). */
+vga_status vga_sim_set_wavefront(vga_sim *s, int32_t chunk, int32_t depth, int32_t ctas_per_sm);
 
 #define VGA_TUNE_MAX 16
 typedef struct vga_tune_entry {
     int32_t variant;
     int32_t chunk;
+    int32_t depth;        /* variant 3: passes per block; 0 otherwise */
+    int32_t ctas_per_sm;  /* variant 3: CTAs per SM (0 = occupancy); 0 otherwise */
     double ms_per_step;
 } vga_tune_entry;
 typedef struct vga_tune_result {
@@ -337,6 +350,95 @@ vga_status vga_sim_enable_timing(vga_sim *s, int32_t on);
 vga_status vga_sim_read_timing(vga_sim *s, vga_kernel_timing *out, int32_t reset);
 
 vga_status vga_sim_free(vga_sim *s);
+
+/* ============================================================================================
+ * Coarse primitive-graph diffusion model (PNGM) and its calibration from voxel data (Sec. V.A).
+ *
+ * The pore voxels are partitioned into q primitives (one label per node).  Primitive i has volume
+ * v_i = its voxel count; primitives joined by at least one voxel face are adjacent, with S_ij
+ * shared faces and d_ij = distance between their voxel centroids.  Masses follow
+ *   Scheme 3 (explicit)  m_i^{k+1} = m_i^k - c sum_j theta_ij (m_i^k / v_i - m_j^k / v_j)
+ *   Scheme 4 (implicit)  m_i^k = m_i^{k+1} + c sum_j theta_ij (m_i^{k+1} / v_i - m_j^{k+1} / v_j)
+ * with c = D dt.  The conductances theta are stored per ordered pair (i, j) in CSR order (rows
+ * by i, columns ascending), "slots"; their initial value is S_ij / d_ij (Sec. V.B).  Calibration
+ * minimises, over l pairs (X^p, Y^p) of primitive mass vectors one coarse step apart,
+ *   Objective 1  L1 = 1/(l q) sum_p sum_i (y_i - x_i + c sum_j theta_ij (x_i/v_i - x_j/v_j))^2
+ *   Objective 2  L2 = 1/(l q) sum_p sum_i (x_i - y_i - c sum_j theta_ij (y_i/v_i - y_j/v_j))^2
+ * by the normalised update theta_s <- theta_s - lr sign(dL/dtheta_s) (sign(0) = 0).  The gradient
+ * per slot (i, j) involves row i only; with tied != 0 slots (i, j) and (j, i) share the sum of
+ * their two gradients, which keeps theta symmetric.  dL2/dtheta_ij = -(2 c / (l q)) sum_p
+ * r_i (y_i/v_i - y_j/v_j): the sign is that of the residual's derivative.
+ * ============================================================================================ */
+typedef struct vga_pngm vga_pngm;
+
+typedef struct vga_pngm_info {
+    int32_t q;                   /* primitives */
+    int32_t n_slots;             /* ordered adjacent pairs (twice the undirected pairs) */
+    int64_t n_nodes;             /* nodes of the graph */
+    int64_t cross_faces;         /* voxel faces between different primitives */
+    int32_t symmetric;           /* 1 if theta_ij == theta_ji for every pair */
+    int64_t last_cg_iterations;  /* Scheme 4: PCG iterations summed over the last vga_pngm_step */
+    double last_cg_relres;       /* Scheme 4: relative residual of its last solve */
+} vga_pngm_info;
+
+/* Builds the coarse graph of graph g under the partition labels[n] (int32, values in [0, q), host
+ * memory, or device memory when on_device != 0; copied, so the caller keeps ownership).  Every
+ * primitive must hold at least one node.  Volumes, face counts and centroids are exact integer
+ * sums; theta starts at S_ij / d_ij.  Work is ordered on `stream` (NULL = default stream), which
+ * the handle keeps for its own calls; the call synchronises it.  Errors: VGA_ERR_INVALID_ARG
+ * (q < 1, q > n, a label outside [0, q), an empty primitive, NULL pointers), VGA_ERR_UNSUPPORTED
+ * (more than 2^31 - 1 slots), VGA_ERR_OOM, VGA_ERR_CUDA. */
+vga_status vga_pngm_create(const vga_graph *g, const int32_t *labels, int32_t on_device, int32_t q, void *stream,
+                           vga_pngm **out);
+
+vga_status vga_pngm_get_info(const vga_pngm *pg, vga_pngm_info *out);
+
+/* Copies the geometry to host arrays (each may be NULL): volumes[q], centroids[3q] as (x, y, z)
+ * per primitive in voxel units, row_ptr[q+1], col[n_slots], rev[n_slots] (slot of (j, i)),
+ * surface[n_slots] = S_ij, distance[n_slots] = d_ij. */
+vga_status vga_pngm_export(const vga_pngm *pg, double *volumes, double *centroids, int32_t *row_ptr, int32_t *col,
+                           int32_t *rev, double *surface, double *distance);
+
+/* Replaces / reads theta[n_slots] (FP64, host, or device when on_device != 0).  Values must be
+ * finite.  Errors: VGA_ERR_INVALID_ARG, VGA_ERR_CUDA. */
+vga_status vga_pngm_set_theta(vga_pngm *pg, const double *theta, int32_t on_device);
+vga_status vga_pngm_get_theta(const vga_pngm *pg, double *theta, int32_t on_device);
+
+/* Primitive masses of compartment comp (0..4) of simulation s (which must run on the same graph):
+ * d_out[i] = sum of the node masses of primitive i (device, FP64, q entries; overwritten), ordered
+ * on the simulation's stream.  Summation order is not fixed (FP64 atomics).  Errors:
+ * VGA_ERR_INVALID_ARG, VGA_ERR_CUDA. */
+vga_status vga_pngm_restrict(vga_pngm *pg, vga_sim *s, int32_t comp, double *d_out);
+
+/* n_steps coarse steps of d_m[q] (device, FP64, in place) with c = D dt: scheme
+ * VGA_SCHEME_EXPLICIT = Scheme 3 (FP64, rounding as written), VGA_SCHEME_IMPLICIT_PCG = Scheme 4,
+ * solved as (V + c L) u = m^k, m^{k+1} = V u by Jacobi-PCG (start u = m^k / v, stop when
+ * ||r||_2 <= cg_rtol ||m^k||_2 or after cg_maxit iterations).  Scheme 4 needs symmetric theta.
+ * Synchronises the handle's stream.  Errors: VGA_ERR_INVALID_ARG, VGA_ERR_UNSUPPORTED (Scheme 4
+ * with theta_ij != theta_ji), VGA_ERR_NOT_CONVERGED (a solve hit cg_maxit; m holds its last
+ * iterate), VGA_ERR_CUDA. */
+vga_status vga_pngm_step(vga_pngm *pg, double *d_m, int64_t n_steps, int32_t scheme, double D, double dt, double cg_rtol,
+                         int32_t cg_maxit);
+
+/* Objective 1 or 2 (objective_kind) over the l pairs X^p = record pairs[2p], Y^p = record
+ * pairs[2p+1] of d_data (device, FP64, n_records x q, row-major); pairs is a host array of 2l
+ * record indices.  *loss (host, may be NULL) receives the objective; d_grad (device, n_slots,
+ * may be NULL) its gradient per slot (tied: summed over (i, j) and (j, i)).  Synchronises the
+ * handle's stream.  Errors: VGA_ERR_INVALID_ARG (kind, l < 1, an index outside [0, n_records),
+ * D < 0, dt <= 0), VGA_ERR_CUDA. */
+vga_status vga_pngm_objective(vga_pngm *pg, int32_t objective_kind, const double *d_data, int64_t n_records,
+                              const int32_t *pairs, int32_t l, double D, double dt, int32_t tied, double *loss,
+                              double *d_grad);
+
+/* One normalised SGD update of theta on the objective over the given pairs (as
+ * vga_pngm_objective): theta_s <- max(theta_s - lr sign(g_s), theta_min).  theta_min = -INFINITY
+ * gives the paper's update; 0 keeps conductances non-negative, which Scheme 4 needs to stay
+ * positive definite.  *loss_before receives the objective before the update. */
+vga_status vga_pngm_sgd_step(vga_pngm *pg, int32_t objective_kind, const double *d_data, int64_t n_records,
+                             const int32_t *pairs, int32_t l, double D, double dt, double lr, double theta_min,
+                             int32_t tied, double *loss_before);
+
+vga_status vga_pngm_free(vga_pngm *pg);
 
 /* ============================================================================================
  * Allocation-free totals.  The paper has no counterpart: this entry point exists for callers that

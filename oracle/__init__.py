@@ -46,7 +46,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP on).  Returns the library path."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
+        subprocess.run(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
                        check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH

@@ -24,7 +24,8 @@ Readings of the paper applied here:
       2 r_i / (l q); the printed formula lacks the minus sign, which would make the normalised
       update climb the loss.
   P6  Normalised SGD: theta <- theta - lr g / |g| per parameter; a parameter with g = 0 is left
-      unchanged (g / |g| is undefined there).
+      unchanged (g / |g| is undefined there).  An optional lower bound theta_min (the paper sets
+      none) keeps conductances non-negative.
 """
 from __future__ import annotations
 
@@ -152,8 +153,9 @@ def objective(kind: int, cg: dict, theta: np.ndarray, X: np.ndarray, Y: np.ndarr
 
 
 def sgd_step(kind: int, cg: dict, theta: np.ndarray, X: np.ndarray, Y: np.ndarray, c: float, lr: float,
-             tied: bool = False):
-    """One normalised-gradient update (reading P6).  Returns (new theta, loss before the update)."""
+             tied: bool = False, theta_min: float = -np.inf):
+    """One normalised-gradient update (reading P6), bounded below by theta_min.  Returns (new
+    theta, loss before the update)."""
     loss, g = objective(kind, cg, theta, X, Y, c, tied=tied)
     step = np.where(g > 0, 1.0, np.where(g < 0, -1.0, 0.0))
-    return theta - lr * step, loss
+    return np.maximum(theta - lr * step, theta_min), loss

@@ -51,7 +51,8 @@ class vga_params(C.Structure):
 
 
 class vga_tune_entry(C.Structure):
-    _fields_ = [("variant", C.c_int32), ("chunk", C.c_int32), ("ms_per_step", C.c_double)]
+    _fields_ = [("variant", C.c_int32), ("chunk", C.c_int32), ("depth", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("ms_per_step", C.c_double)]
 
 
 class vga_tune_result(C.Structure):
@@ -118,6 +119,7 @@ _SIGNATURES = {
     "vga_sgd_block_conductances": [_P, C.c_double, C.c_double, C.c_double],
     "vga_sim_get_block_conductances": [_P, _P, _I64],
     "vga_sim_set_kernel": [_P, _I32, _I32],
+    "vga_sim_set_wavefront": [_P, _I32, _I32, _I32],
     "vga_sim_autotune": [_P, _I32, _P],
     "vga_sim_enable_timing": [_P, _I32],
     "vga_sim_read_timing": [_P, _P, _I32],
@@ -132,6 +134,16 @@ _SIGNATURES = {
     "vga_batch_autotune": [_P, _I32, _P],
     "vga_batch_free": [_P],
     "vga_state_totals_noalloc": [_P, _P, _I64, _I64, _P, _P],
+    "vga_pngm_create": [_P, _P, _I32, _I32, _P, _P],
+    "vga_pngm_get_info": [_P, _P],
+    "vga_pngm_export": [_P, _P, _P, _P, _P, _P, _P, _P],
+    "vga_pngm_set_theta": [_P, _P, _I32],
+    "vga_pngm_get_theta": [_P, _P, _I32],
+    "vga_pngm_restrict": [_P, _P, _I32, _P],
+    "vga_pngm_step": [_P, _P, _I64, _I32, C.c_double, C.c_double, C.c_double, _I32],
+    "vga_pngm_objective": [_P, _I32, _P, _I64, _P, _I32, C.c_double, C.c_double, _I32, _P, _P],
+    "vga_pngm_sgd_step": [_P, _I32, _P, _I64, _P, _I32, C.c_double, C.c_double, C.c_double, C.c_double, _I32, _P],
+    "vga_pngm_free": [_P],
 }
 _RESTYPES = {"vga_strerror": C.c_char_p, "vga_last_error": C.c_char_p, "vga_version": C.c_int32}
 
@@ -380,10 +392,15 @@ def vga_sim_set_kernel(s, variant: int, chunk: int):
     _check(load_library().vga_sim_set_kernel(s, int(variant), int(chunk)), "vga_sim_set_kernel")
 
 
+def vga_sim_set_wavefront(s, chunk: int, depth: int, ctas_per_sm: int = 0):
+    _check(load_library().vga_sim_set_wavefront(s, int(chunk), int(depth), int(ctas_per_sm)), "vga_sim_set_wavefront")
+
+
 def vga_sim_autotune(s, trial_steps: int = 20) -> dict:
     r = vga_tune_result()
     _check(load_library().vga_sim_autotune(s, int(trial_steps), C.byref(r)), "vga_sim_autotune")
-    entries = [dict(variant=r.entries[k].variant, chunk=r.entries[k].chunk, ms_per_step=r.entries[k].ms_per_step)
+    entries = [dict(variant=r.entries[k].variant, chunk=r.entries[k].chunk, depth=r.entries[k].depth,
+                    ctas_per_sm=r.entries[k].ctas_per_sm, ms_per_step=r.entries[k].ms_per_step)
                for k in range(r.count)]
     return dict(best=entries[r.best] if r.best >= 0 else None, entries=entries)
 
@@ -485,6 +502,18 @@ def vga_batch_free(b):
 
 
 # ---- handle classes (ownership only) ------------------------------------------------------------
+class vga_pngm_info(C.Structure):
+    _fields_ = [("q", C.c_int32), ("n_slots", C.c_int32), ("n_nodes", C.c_int64), ("cross_faces", C.c_int64),
+                ("symmetric", C.c_int32), ("last_cg_iterations", C.c_int64), ("last_cg_relres", C.c_double)]
+
+
+def _pairs_array(pairs) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    if a.shape[0] < 1:
+        raise ValueError("need at least one pair")
+    return a
+
+
 class Graph:
     """Owns a vga_graph handle."""
 
@@ -581,6 +610,9 @@ class Sim:
     def set_kernel(self, variant: int, chunk: int):
         vga_sim_set_kernel(self.handle, variant, chunk)
 
+    def set_wavefront(self, chunk: int, depth: int, ctas_per_sm: int = 0):
+        vga_sim_set_wavefront(self.handle, chunk, depth, ctas_per_sm)
+
     def autotune(self, trial_steps: int = 20) -> dict:
         return vga_sim_autotune(self.handle, trial_steps)
 
@@ -649,6 +681,146 @@ class Batch:
     def close(self):
         if self.handle:
             vga_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+
+# ---- coarse primitive-graph model (Sec. V.A) ----------------------------------------------------
+def vga_pngm_create(g, labels, q: int, n: int, stream=None):
+    """labels: int32 numpy array (host) or contiguous int32 CUDA tensor of n entries."""
+    if isinstance(labels, np.ndarray):
+        lab = np.ascontiguousarray(labels, dtype=np.int32)
+        if lab.size != n:
+            raise ValueError("labels must have one entry per node")
+        ptr, on_dev = lab.ctypes.data, 0
+    else:
+        import torch
+
+        if not (isinstance(labels, torch.Tensor) and labels.is_cuda and labels.dtype == torch.int32
+                and labels.is_contiguous() and labels.numel() == n):
+            raise TypeError("labels must be an int32 numpy array or contiguous CUDA tensor of n entries")
+        ptr, on_dev = labels.data_ptr(), 1
+    h = C.c_void_p()
+    _check(load_library().vga_pngm_create(g, ptr, on_dev, int(q), _stream_ptr(stream), C.byref(h)), "vga_pngm_create")
+    return h
+
+
+def vga_pngm_get_info(h) -> dict:
+    st = vga_pngm_info()
+    _check(load_library().vga_pngm_get_info(h, C.byref(st)), "vga_pngm_get_info")
+    return {k: getattr(st, k) for k, _ in vga_pngm_info._fields_}
+
+
+def vga_pngm_export(h, q: int, n_slots: int) -> dict:
+    out = dict(vol=np.empty(q), centroid=np.empty((q, 3)), row_ptr=np.empty(q + 1, dtype=np.int32),
+               col=np.empty(n_slots, dtype=np.int32), rev=np.empty(n_slots, dtype=np.int32), S=np.empty(n_slots),
+               dist=np.empty(n_slots))
+    _check(load_library().vga_pngm_export(h, out["vol"].ctypes.data, out["centroid"].ctypes.data,
+                                          out["row_ptr"].ctypes.data, out["col"].ctypes.data, out["rev"].ctypes.data,
+                                          out["S"].ctypes.data, out["dist"].ctypes.data), "vga_pngm_export")
+    return out
+
+
+def vga_pngm_set_theta(h, theta, n_slots: int):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    if th.size != n_slots:
+        raise ValueError(f"theta needs {n_slots} entries")
+    _check(load_library().vga_pngm_set_theta(h, th.ctypes.data, 0), "vga_pngm_set_theta")
+
+
+def vga_pngm_get_theta(h, n_slots: int) -> np.ndarray:
+    out = np.empty(n_slots)
+    _check(load_library().vga_pngm_get_theta(h, out.ctypes.data, 0), "vga_pngm_get_theta")
+    return out
+
+
+def vga_pngm_restrict(h, sim, comp: int, out, q: int):
+    _check(load_library().vga_pngm_restrict(h, sim, int(comp), _dev_ptr(out, "float64", q)), "vga_pngm_restrict")
+    return out
+
+
+def vga_pngm_step(h, m, q: int, n_steps: int, scheme: int, D: float, dt: float, cg_rtol: float = 1e-12,
+                  cg_maxit: int = 10000):
+    _check(load_library().vga_pngm_step(h, _dev_ptr(m, "float64", q), int(n_steps), int(scheme), float(D), float(dt),
+                                        float(cg_rtol), int(cg_maxit)), "vga_pngm_step")
+    return m
+
+
+def _pngm_data(data, q: int) -> int:
+    if data.dim() != 2 or data.shape[1] != q:
+        raise ValueError(f"data must be (records, {q})")
+    return _dev_ptr(data, "float64")
+
+
+def vga_pngm_objective(h, q: int, n_slots: int, kind: int, data, pairs, D: float, dt: float, tied: bool = False,
+                       grad=None) -> float:
+    p = _pairs_array(pairs)
+    loss = C.c_double(0.0)
+    _check(load_library().vga_pngm_objective(h, int(kind), _pngm_data(data, q), int(data.shape[0]), p.ctypes.data,
+                                             p.shape[0], float(D), float(dt), 1 if tied else 0, C.byref(loss),
+                                             None if grad is None else _dev_ptr(grad, "float64", n_slots)),
+           "vga_pngm_objective")
+    return loss.value
+
+
+def vga_pngm_sgd_step(h, q: int, kind: int, data, pairs, D: float, dt: float, lr: float, tied: bool = False,
+                      theta_min: float = -np.inf) -> float:
+    p = _pairs_array(pairs)
+    loss = C.c_double(0.0)
+    _check(load_library().vga_pngm_sgd_step(h, int(kind), _pngm_data(data, q), int(data.shape[0]), p.ctypes.data,
+                                            p.shape[0], float(D), float(dt), float(lr), float(theta_min),
+                                            1 if tied else 0, C.byref(loss)), "vga_pngm_sgd_step")
+    return loss.value
+
+
+def vga_pngm_free(h):
+    _check(load_library().vga_pngm_free(h), "vga_pngm_free")
+
+
+class Pngm:
+    """Owns a vga_pngm handle: the coarse primitive graph of a node partition on a Graph (which
+    must stay alive).  Device vectors (masses, data, gradients) are torch CUDA float64 tensors."""
+
+    def __init__(self, graph: Graph, labels, q: int, stream=None):
+        self.graph = graph
+        self.handle = vga_pngm_create(graph.handle, labels, q, graph.n, stream)
+        self.q = int(q)
+        self.n_slots = self.info()["n_slots"]
+
+    def info(self) -> dict:
+        return vga_pngm_get_info(self.handle)
+
+    def export(self) -> dict:
+        return vga_pngm_export(self.handle, self.q, self.n_slots)
+
+    def get_theta(self) -> np.ndarray:
+        return vga_pngm_get_theta(self.handle, self.n_slots)
+
+    def set_theta(self, theta):
+        vga_pngm_set_theta(self.handle, theta, self.n_slots)
+
+    def restrict(self, sim: "Sim", comp: int, out):
+        return vga_pngm_restrict(self.handle, sim.handle, comp, out, self.q)
+
+    def step(self, m, n_steps: int, scheme: int, D: float, dt: float, cg_rtol: float = 1e-12, cg_maxit: int = 10000):
+        return vga_pngm_step(self.handle, m, self.q, n_steps, scheme, D, dt, cg_rtol, cg_maxit)
+
+    def objective(self, kind: int, data, pairs, D: float, dt: float, tied: bool = False, grad=None) -> float:
+        return vga_pngm_objective(self.handle, self.q, self.n_slots, kind, data, pairs, D, dt, tied, grad)
+
+    def sgd_step(self, kind: int, data, pairs, D: float, dt: float, lr: float, tied: bool = False,
+                 theta_min: float = -np.inf) -> float:
+        return vga_pngm_sgd_step(self.handle, self.q, kind, data, pairs, D, dt, lr, tied, theta_min)
+
+    def close(self):
+        if self.handle:
+            vga_pngm_free(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -17,8 +17,11 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libvga.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Host code is compiled without floating-point contraction: g++ fuses a*b + c into an FMA on
+# aarch64 by default (also under -std=c++17), which would make host-side doubles (centroid
+# distances, step clocks) depend on the build machine.
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr", "-Werror", "all-warnings"]
+              "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr", "-Werror", "all-warnings"]
 
 
 def _nvcc() -> str:

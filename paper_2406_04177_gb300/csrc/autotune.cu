@@ -14,10 +14,13 @@ bool stencil_variant_supported(int variant, int cap);
 namespace {
 
 struct Candidate {
-    int variant, cap;
+    int variant, cap, depth, ctas;  // depth, ctas: wavefront passes per block and CTAs per SM
 };
 
-constexpr Candidate kCandidates[] = {{2, 1024}, {1, 1024}, {1, 512}, {1, 2048}, {0, 1024}, {0, 512}, {0, 2048}};
+constexpr Candidate kCandidates[] = {{2, 1024, 0, 0}, {1, 1024, 0, 0}, {0, 1024, 0, 0}, {0, 512, 0, 0},
+                                     {3, 256, 4, 0},  {3, 512, 4, 0},  {3, 512, 8, 0},  {3, 256, 8, 0},
+                                     {3, 1024, 4, 0}, {3, 512, 2, 0},  {3, 512, 4, 4},  {3, 256, 16, 0},
+                                     {3, 512, 16, 0}, {3, 1024, 8, 2}};
 
 vga_status snapshot(vga_sim *s, float *h, uint16_t *l, bool restore) {
     for (int c = 0; c < 5; ++c) {
@@ -36,8 +39,14 @@ vga_status snapshot(vga_sim *s, float *h, uint16_t *l, bool restore) {
     return VGA_OK;
 }
 
-vga_status select_kernel(vga_sim *s, int variant, int cap) {
-    if (s->chunks.cap != cap) VGA_TRY(build_chunks(s->g->topo(), cap, &s->chunks, s->stream));
+vga_status select_kernel(vga_sim *s, int variant, int cap, int depth = 0, int ctas = 0) {
+    if (variant == 3) {
+        s->wave_chunk = cap;
+        s->wave_depth = depth;
+        s->wave_ctas = ctas;
+    } else if (s->chunks.cap != cap) {
+        VGA_TRY(build_chunks(s->g->topo(), cap, &s->chunks, s->stream));
+    }
     s->kernel_variant = variant;
     return VGA_OK;
 }
@@ -49,13 +58,26 @@ using namespace vga;
 
 extern "C" vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t chunk) {
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
-    if (variant < 0 || variant > 2 || chunk < 32 || chunk > 8192 || (chunk & 31))
-        return fail(VGA_ERR_INVALID_ARG, "variant must be 0, 1 or 2 and chunk a multiple of 32 in [32, 8192]");
+    if (variant < 0 || variant > 3 || chunk < 32 || chunk > 8192 || (chunk & 31))
+        return fail(VGA_ERR_INVALID_ARG, "variant must lie in [0, 3] and chunk be a multiple of 32 in [32, 8192]");
+    if (variant == 3) {
+        if (!wave_params_valid(chunk, 4, 0)) return fail(VGA_ERR_INVALID_ARG, "wavefront chunks are multiples of 256");
+        VGA_TRY(select_kernel(s, 3, chunk, 4, 0));
+        return VGA_OK;
+    }
     if (!stencil_variant_supported(variant, chunk))
         return fail(VGA_ERR_UNSUPPORTED, "the staged kernel exists for chunks of 512, 1024 and 2048 nodes");
     VGA_TRY(select_kernel(s, variant, chunk));
     VGA_CUDA(cudaStreamSynchronize(s->stream));
     return VGA_OK;
+}
+
+extern "C" vga_status vga_sim_set_wavefront(vga_sim *s, int32_t chunk, int32_t depth, int32_t ctas_per_sm) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    if (!wave_params_valid(chunk, depth, ctas_per_sm))
+        return fail(VGA_ERR_INVALID_ARG,
+                    "chunk must be a multiple of 256 in [256, 8192], depth in [1, 64], ctas_per_sm in [0, 32]");
+    return select_kernel(s, 3, chunk, depth, ctas_per_sm);
 }
 
 extern "C" vga_status vga_sim_autotune(vga_sim *s, int32_t trial_steps, vga_tune_result *out) {
@@ -72,13 +94,14 @@ extern "C" vga_status vga_sim_autotune(vga_sim *s, int32_t trial_steps, vga_tune
     if (st == VGA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = fail(VGA_ERR_CUDA, "cudaEventCreate failed");
     const int64_t steps0 = s->steps_done;
-    const int keep_variant = s->kernel_variant, keep_cap = s->chunks.cap;
+    const int keep_variant = s->kernel_variant, keep_cap = s->chunks.cap, keep_wc = s->wave_chunk,
+              keep_wd = s->wave_depth, keep_wk = s->wave_ctas;
     if (st == VGA_OK) st = snapshot(s, h, l, false);
     double best = 1e300;
     int nc = 0;
     for (const Candidate &c : kCandidates) {
         if (st != VGA_OK || nc >= VGA_TUNE_MAX) break;
-        st = select_kernel(s, c.variant, c.cap);
+        st = select_kernel(s, c.variant, c.cap, c.depth, c.ctas);
         if (st == VGA_OK) st = sim_step_explicit(s, 2);  // warm-up (instantiation, attributes)
         if (st == VGA_OK) st = snapshot(s, h, l, true);
         if (st != VGA_OK) break;
@@ -92,6 +115,8 @@ extern "C" vga_status vga_sim_autotune(vga_sim *s, int32_t trial_steps, vga_tune
         if (st != VGA_OK) break;
         out->entries[nc].variant = c.variant;
         out->entries[nc].chunk = c.cap;
+        out->entries[nc].depth = c.depth;
+        out->entries[nc].ctas_per_sm = c.ctas;
         out->entries[nc].ms_per_step = ms / trial_steps;
         if (ms < best) {
             best = ms;
@@ -101,9 +126,10 @@ extern "C" vga_status vga_sim_autotune(vga_sim *s, int32_t trial_steps, vga_tune
     }
     out->count = nc;
     if (st == VGA_OK && out->best >= 0)
-        st = select_kernel(s, out->entries[out->best].variant, out->entries[out->best].chunk);
+        st = select_kernel(s, out->entries[out->best].variant, out->entries[out->best].chunk,
+                           out->entries[out->best].depth, out->entries[out->best].ctas_per_sm);
     else if (st != VGA_OK)
-        select_kernel(s, keep_variant, keep_cap);
+        keep_variant == 3 ? select_kernel(s, 3, keep_wc, keep_wd, keep_wk) : select_kernel(s, keep_variant, keep_cap);
     s->steps_done = steps0;
     if (st == VGA_OK) {
         const cudaError_t e = cudaStreamSynchronize(s->stream);

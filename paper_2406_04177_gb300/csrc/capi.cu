@@ -76,14 +76,16 @@ void timing_begin(vga_sim *s, int kind) {
     if (s->timing_a) cudaEventRecord(s->timing_a, s->stream);
 }
 
-void timing_end(vga_sim *s) {
+void timing_end_weighted(vga_sim *s, int64_t passes) {
     if (!s->timing || !s->timing_a) return;
     cudaEvent_t b = pool_event(s);
     if (!b) return;
     cudaEventRecord(b, s->stream);
-    s->pending.push_back({s->timing_a, b, s->timing_kind});
+    s->pending.push_back({s->timing_a, b, s->timing_kind, passes});
     s->timing_a = nullptr;
 }
+
+void timing_end(vga_sim *s) { timing_end_weighted(s, 1); }
 
 static vga_status harvest_timing(vga_sim *s) {
     if (s->pending.empty()) return VGA_OK;
@@ -93,7 +95,7 @@ static vga_status harvest_timing(vga_sim *s) {
         VGA_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
         if (p.kind >= 0 && p.kind < VGA_KERNEL_KINDS) {
             s->kt_ms[p.kind] += ms;
-            s->kt_count[p.kind] += 1;
+            s->kt_count[p.kind] += p.passes;
         }
         s->event_pool.push_back(p.a);
         s->event_pool.push_back(p.b);
@@ -109,7 +111,8 @@ static vga_status check_device_error(vga_sim *s) {
     VGA_CUDA(cudaStreamSynchronize(s->stream));
     if (h != 0) {
         cudaMemsetAsync(s->d_err, 0, sizeof(int32_t), s->stream);
-        return fail(VGA_ERR_TIMEOUT, "a bounded device wait timed out (bulk copy did not complete)");
+        return fail(VGA_ERR_TIMEOUT, h == 2 ? "a bounded device wait timed out (wavefront dependency)"
+                                            : "a bounded device wait timed out (bulk copy did not complete)");
     }
     return VGA_OK;
 }
@@ -651,6 +654,8 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->cg);
     dfree(s->cg_scalars);
     dfree(s->loss_work);
+    dfree(s->wave_dep);
+    dfree(s->wave_order);
     adjoint_free(s->adj);
     if (s->h_cg) cudaFreeHost(s->h_cg);
     free_chunks(&s->chunks);

@@ -165,4 +165,78 @@ __device__ __forceinline__ void block_sum_store(const double (&v)[K], double *ou
     __syncthreads();
 }
 
+// Load path of state arrays: LD_NC reads through the read-only (non-coherent) data cache; LD_CG
+// reads at L2, as a kernel must for values that other blocks of the same launch have written.
+enum LoadPath { LD_NC = 0, LD_CG = 1 };
+
+template <int LP>
+__device__ __forceinline__ float ld_state(const float *p) {
+    if (LP == LD_NC) return __ldg(p);
+    return __ldcg(p);
+}
+
+template <int PREC, int LP>
+__device__ __forceinline__ V vload_path(const float *__restrict__ H, const uint16_t *__restrict__ L, int64_t i) {
+    if (LP == LD_NC) return vload<PREC>(H, L, i);
+    V v;
+    v.h = __ldcg(H + i);
+    v.l = (PREC == P_COMP) ? bf16_bits_to_float(__ldcg(L + i)) : 0.0f;
+    return v;
+}
+
+// One node of a table-driven pass: MODE 1 diffuses the stored transformed DOM (Scheme 1) and
+// transforms the result; MODE 2 only diffuses.  Neighbours come from the offset table; the +-x
+// neighbours' values from the adjacent lanes (consecutive nodes) by warp shuffles.  Arithmetic and
+// slot order as k_stencil.  Must be called by all 32 lanes of a warp (live = node exists).
+template <int MODE, int WM, int TR, int PREC, int LP>
+__device__ __forceinline__ void table_node(uint32_t i, bool live, const NbrTable &tb, const BlockTable &bt,
+                                           const StepParams &p, const StateIO &io) {
+    const uint32_t bn = (WM == W_BLOCK && live) ? __ldg(bt.node + i) : 0u;
+    const float *__restrict__ Y2 = io.in[1];
+    const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
+    const uint32_t dzm = live ? __ldg(tb.tzm + i) : 0u;
+    const uint32_t dzp = live ? __ldg(tb.tzp + i) : 0u;
+    V x2 = live ? vload_path<PREC, LP>(Y2, io.lin[1], i) : V{0.0f, 0.0f};
+    const float yi = x2.h;
+    const int lane = threadIdx.x & 31;
+    float yl = __shfl_up_sync(0xffffffffu, yi, 1);
+    float yr = __shfl_down_sync(0xffffffffu, yi, 1);
+    const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
+    const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
+    if (lane == 0 && hxm) yl = ld_state<LP>(Y2 + (i - 1));
+    if (lane == 31 && hxp) yr = ld_state<LP>(Y2 + (i + 1));
+    float ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
+    if (dym) ym = ld_state<LP>(Y2 + (i - dym));
+    if (dyp) yp = ld_state<LP>(Y2 + (i + dyp));
+    if (dzm) zm = ld_state<LP>(Y2 + (i - dzm));
+    if (dzp) zp = ld_state<LP>(Y2 + (i + dzp));
+    if (!live) return;
+    float acc = 0.0f;
+    auto add = [&](int slot, float yj) {
+        const float d = __fsub_rn(yi, yj);
+        if (WM == W_UNIT) acc = __fadd_rn(acc, d);
+        else acc = __fmaf_rn(table_theta(bt, bn, slot), d, acc);
+    };
+    if (hxm) add(0, yl);
+    if (hxp) add(1, yr);
+    if (dym) add(2, ym);
+    if (dyp) add(3, yp);
+    if (dzm) add(4, zm);
+    if (dzp) add(5, zp);
+    vadd<PREC>(x2, __fmul_rn(-p.c, acc));  // Scheme 1
+    if (MODE == 1) {
+        vround<PREC>(x2);
+        V x1 = vload_path<PREC, LP>(io.in[0], io.lin[0], i), x3 = vload_path<PREC, LP>(io.in[2], io.lin[2], i),
+          x4 = vload_path<PREC, LP>(io.in[3], io.lin[3], i), x5 = vload_path<PREC, LP>(io.in[4], io.lin[4], i);
+        transform_n<TR, PREC>(x1, x2, x3, x4, x5, p);
+        vstore<PREC>(io.out[0], io.lout[0], i, x1);
+        vstore<PREC>(io.out[1], io.lout[1], i, x2);
+        vstore<PREC>(io.out[2], io.lout[2], i, x3);
+        vstore<PREC>(io.out[3], io.lout[3], i, x4);
+        vstore<PREC>(io.out[4], io.lout[4], i, x5);
+    } else {
+        vstore<PREC>(io.out[1], io.lout[1], i, x2);
+    }
+}
+
 }  // namespace vga

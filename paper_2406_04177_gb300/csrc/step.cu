@@ -262,59 +262,12 @@ __global__ void k_build_bface(BlockWeights bw, int32_t *__restrict__ face) {
     f[5] = bz < bw.nbz - 1 ? (int32_t)(bw.off_z + ((int64_t)bz * bw.nby + by) * bw.nbx + bx) : -1;
 }
 
-// One node per thread, neighbours from the offset table; the +-x neighbours' values come from the
-// adjacent lanes (consecutive nodes) by warp shuffles.  Arithmetic and slot order as k_stencil.
+// One node per thread, neighbours from the offset table (table_node).
 template <int MODE, int WM, int TR, int PREC>
 __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                             StateIO io) {
     const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < (uint64_t)n;
-    const uint32_t bn = (WM == W_BLOCK && live) ? __ldg(bt.node + i) : 0u;
-    const float *__restrict__ Y2 = io.in[1];
-    const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
-    const uint32_t dzm = live ? __ldg(tb.tzm + i) : 0u;
-    const uint32_t dzp = live ? __ldg(tb.tzp + i) : 0u;
-    V x2 = live ? vload<PREC>(Y2, io.lin[1], i) : V{0.0f, 0.0f};
-    const float yi = x2.h;
-    const int lane = threadIdx.x & 31;
-    float yl = __shfl_up_sync(0xffffffffu, yi, 1);
-    float yr = __shfl_down_sync(0xffffffffu, yi, 1);
-    const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
-    const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
-    if (lane == 0 && hxm) yl = __ldg(Y2 + (i - 1));
-    if (lane == 31 && hxp) yr = __ldg(Y2 + (i + 1));
-    float ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
-    if (dym) ym = __ldg(Y2 + (i - dym));
-    if (dyp) yp = __ldg(Y2 + (i + dyp));
-    if (dzm) zm = __ldg(Y2 + (i - dzm));
-    if (dzp) zp = __ldg(Y2 + (i + dzp));
-    if (!live) return;
-    float acc = 0.0f;
-    auto add = [&](int slot, float yj) {
-        const float d = __fsub_rn(yi, yj);
-        if (WM == W_UNIT) acc = __fadd_rn(acc, d);
-        else acc = __fmaf_rn(table_theta(bt, bn, slot), d, acc);
-    };
-    if (hxm) add(0, yl);
-    if (hxp) add(1, yr);
-    if (dym) add(2, ym);
-    if (dyp) add(3, yp);
-    if (dzm) add(4, zm);
-    if (dzp) add(5, zp);
-    vadd<PREC>(x2, __fmul_rn(-p.c, acc));  // Scheme 1
-    if (MODE == 1) {
-        vround<PREC>(x2);
-        V x1 = vload<PREC>(io.in[0], io.lin[0], i), x3 = vload<PREC>(io.in[2], io.lin[2], i),
-          x4 = vload<PREC>(io.in[3], io.lin[3], i), x5 = vload<PREC>(io.in[4], io.lin[4], i);
-        transform_n<TR, PREC>(x1, x2, x3, x4, x5, p);
-        vstore<PREC>(io.out[0], io.lout[0], i, x1);
-        vstore<PREC>(io.out[1], io.lout[1], i, x2);
-        vstore<PREC>(io.out[2], io.lout[2], i, x3);
-        vstore<PREC>(io.out[3], io.lout[3], i, x4);
-        vstore<PREC>(io.out[4], io.lout[4], i, x5);
-    } else {
-        vstore<PREC>(io.out[1], io.lout[1], i, x2);
-    }
+    table_node<MODE, WM, TR, PREC, LD_NC>(i, i < (uint64_t)n, tb, bt, p, io);
 }
 
 // ---- FP64 totals ---------------------------------------------------------------------------
@@ -444,7 +397,7 @@ void launch_stencil_tr(vga_sim *s, const StateIO &io) {
 template <int MODE>
 vga_status launch_stencil(vga_sim *s, const StateIO &io) {
     const bool comp = s->precision() == P_COMP;
-    if (s->kernel_variant == 2 && s->g->nx <= 32767) {
+    if ((s->kernel_variant == 2 || s->kernel_variant == 3) && s->g->nx <= 32767) {
         // table kernels: build the tables (first use) before the timed launch
         NbrTable tb;
         BlockTable bt;
@@ -568,10 +521,14 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
     } reset{s->sp};
     if (sub) s->sp.ntrans = sim_ticks_of_step(s, k0);
     VGA_TRY(sim_transform_pass(s));
-    for (int64_t k = 1; k < n_steps; ++k) {
-        if (sub) s->sp.ntrans = sim_ticks_of_step(s, k0 + k);
-        VGA_TRY(launch_stencil<1>(s, state_io(s)));
-        for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
+    if (s->kernel_variant == 3 && !sub && s->g->nx <= 32767 && n_steps > 1) {
+        VGA_TRY(sim_wave_fused(s, n_steps - 1));
+    } else {
+        for (int64_t k = 1; k < n_steps; ++k) {
+            if (sub) s->sp.ntrans = sim_ticks_of_step(s, k0 + k);
+            VGA_TRY(launch_stencil<1>(s, state_io(s)));
+            for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
+        }
     }
     VGA_TRY(launch_stencil<2>(s, state_io(s)));
     s->cur[1] ^= 1;

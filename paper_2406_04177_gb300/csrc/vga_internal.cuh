@@ -193,6 +193,7 @@ struct vga_sim {
     struct Pending {
         cudaEvent_t a, b;
         int kind;
+        int64_t passes;  // time steps the timed launch covered (a wavefront launch runs many)
     };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
@@ -203,7 +204,13 @@ struct vga_sim {
     // adjoint work buffers (adjoint.cu), allocated on first use
     vga::AdjointBuffers *adj = nullptr;
     int32_t *d_err = nullptr;     // device error flag of bounded waits (nonzero: timed out)
-    int kernel_variant = 2;       // explicit stencil: 0 decode + direct loads, 1 decode + staged, 2 table
+    int kernel_variant = 2;       // explicit stencil: 0 decode + direct loads, 1 decode + staged, 2 table,
+                                  // 3 table passes as an L2 wavefront (wave.cu)
+    int wave_chunk = 512, wave_depth = 4, wave_ctas = 0;  // wavefront chunk, passes per block, CTAs/SM
+    int32_t *wave_dep = nullptr;      // per chunk: lowest and highest chunk its neighbours lie in; flags
+    int32_t *wave_order = nullptr;    // skewed item order of one block of passes
+    int wave_built_chunk = 0, wave_built_depth = 0, wave_built_lag = -1;
+    int32_t wave_reach = 0;
     uint32_t *nbr_table = nullptr;  // 3 x npad words (NbrTable), built on first use
     uint32_t *bnode = nullptr;      // BlockTable.node (npad), built for the current block side
     int32_t *bface = nullptr;       // BlockTable.face (6 x blocks)
@@ -225,6 +232,7 @@ namespace vga {
 // capi.cu: event timing around one kernel launch (no-op unless timing is enabled)
 void timing_begin(vga_sim *s, int kind);
 void timing_end(vga_sim *s);
+void timing_end_weighted(vga_sim *s, int64_t passes);  // the launch covered `passes` time steps
 // step.cu
 vga_status sim_prepare_params(vga_sim *s, const vga_params *p);
 vga_status sim_step_explicit(vga_sim *s, int64_t n_steps);
@@ -236,6 +244,9 @@ vga_status sim_transform_pass(vga_sim *s);  // Y = T(X) for every node, all comp
 int64_t sim_ticks_before(const vga_sim *s, int64_t k);  // transformations in the first k steps
 int sim_ticks_of_step(const vga_sim *s, int64_t k);      // transformations before diffusion step k
 vga_status sim_nbr_table(vga_sim *s, NbrTable *out);  // builds the table on first use
+// wave.cu: P fused passes as one wavefront launch (flips the buffers when P is odd)
+vga_status sim_wave_fused(vga_sim *s, int64_t P);
+bool wave_params_valid(int chunk, int depth, int ctas_per_sm);
 // Builds (if needed) and returns the block table of the current block conductances; false if the
 // block grid is too large for it (the decode kernels are used then).
 vga_status sim_block_table(vga_sim *s, BlockTable *out, bool *ok);

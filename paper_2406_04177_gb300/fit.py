@@ -51,3 +51,53 @@ def fit_block_conductances(graph, params: dict, X0, block_side: int, target: np.
     theta = sim.get_block_conductances(n_theta)
     sim.close()
     return dict(theta=theta, loss=np.array(losses), lr=np.array(lrs))
+
+
+# ---- coarse primitive-graph model (Sec. V.A, V.B) ----------------------------------------------
+def pngm_dataset(graph, pngm, params: dict, scenarios, steps_per_record: int, records: int, stream=None):
+    """Voxel-graph data for the coarse model (Sec. V.B): for every initial state in `scenarios`
+    ((5, n) float64 arrays or CUDA tensors), run the voxel simulation and store the primitive
+    masses of DOM every `steps_per_record` steps, `records` + 1 times (t = 0 included).  Returns
+    (data (S*(records+1), q) CUDA float64 tensor, pairs (S*records, 2) int32 array of consecutive
+    records of one scenario)."""
+    import torch
+
+    q = pngm.q
+    S = len(scenarios)
+    data = torch.empty((S * (records + 1), q), dtype=torch.float64, device="cuda")
+    pairs = []
+    sim = Sim(graph, params, stream=stream)
+    for s, X0 in enumerate(scenarios):
+        sim.set_masses(X0)
+        base = s * (records + 1)
+        pngm.restrict(sim, 1, data[base])
+        for r in range(records):
+            sim.step(steps_per_record)
+            pngm.restrict(sim, 1, data[base + r + 1])
+            pairs.append((base + r, base + r + 1))
+    sim.sync()
+    sim.close()
+    return data, np.asarray(pairs, dtype=np.int32)
+
+
+def fit_pngm(pngm, data, pairs: np.ndarray, D: float, dt: float, objective: int = 2, epochs: int = 1000,
+             batch: int = 4, lr0: float = 0.1, halve_every: int = 10, tied: bool = True, seed: int = 0,
+             theta_min: float = 0.0, callback=None) -> dict:
+    """Normalised SGD on Objective 1 or 2 (Sec. V.B: 1000 epochs of 4 random data pairs, lr 0.1
+    halved every 10 epochs).  dt is the coarse step (the spacing of consecutive records).  The
+    pairs of each epoch are drawn without replacement from a PCG64(seed) stream.  Conductances are
+    kept >= theta_min (non-negative by default, so Scheme 4 stays positive definite).  Returns
+    dict(loss (per epoch, before its update), lr, theta (final))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    losses, lrs = [], []
+    lr = lr0
+    for epoch in range(epochs):
+        if epoch > 0 and halve_every > 0 and epoch % halve_every == 0:
+            lr *= 0.5
+        idx = rng.choice(len(pairs), size=min(batch, len(pairs)), replace=False)
+        loss = pngm.sgd_step(objective, data, pairs[idx], D, dt, lr, tied=tied, theta_min=theta_min)
+        losses.append(loss)
+        lrs.append(lr)
+        if callback is not None:
+            callback(epoch, loss, lr)
+    return dict(loss=np.asarray(losses), lr=np.asarray(lrs), theta=pngm.get_theta())

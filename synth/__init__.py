@@ -192,3 +192,38 @@ def batch_instances(count: int, seed: int, side_lo: int = 64, side_hi: int = 192
         out.append(dict(shape=(side, side, side), porosity=por, mask_seed=100 + i,
                         mass_seed=1000 + i, params=paper_params(scale=scale)))
     return out
+
+
+def block_primitives(shape, voxel_of_node: np.ndarray, block_side: int):
+    """Synthetic primitive partition for the coarse model: every node belongs to the cube of
+    `block_side` voxels that contains it; non-empty cubes are numbered in raster order of the cube
+    grid.  Returns (labels int32 per node, q)."""
+    nz, ny, nx = (int(s) for s in shape)
+    bs = int(block_side)
+    nbx, nby = -(-nx // bs), -(-ny // bs)
+    v = np.asarray(voxel_of_node, dtype=np.int64)
+    x, y, z = v % nx, (v // nx) % ny, v // (nx * ny)
+    blk = ((z // bs) * nby + y // bs) * nbx + x // bs
+    used, labels = np.unique(blk, return_inverse=True)
+    return labels.astype(np.int32), int(used.size)
+
+
+def diffusion_params(dt_seconds: float = 0.1) -> dict:
+    """Pure DOM diffusion (every transformation rate 0) with the Sec. IV.C coefficient and a step
+    given in seconds (the coarse-model data of Sec. V.B use 0.1 s)."""
+    p = paper_params(dt=dt_seconds / 86400.0)
+    p.update(rho=0.0, mu=0.0, v_som=0.0, v_fom=0.0, v_dom=0.0)
+    return p
+
+
+def dom_scenario(n: int, seed: int, total: float = M_DOM_TOTAL, fraction: float = 0.05) -> np.ndarray:
+    """One data scenario of Sec. V.B: a random total mass M0 ~ U(0.5, 1.5) * total spread over a
+    random `fraction` of the nodes with U(0, 1) weights; DOM only.  Returns (5, n) float64."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m0 = total * rng.uniform(0.5, 1.5)
+    k = max(1, int(round(fraction * n)))
+    idx = rng.choice(n, size=k, replace=False)
+    w = rng.random(k)
+    X = np.zeros((5, n))
+    X[1, idx] = m0 * w / w.sum()
+    return X

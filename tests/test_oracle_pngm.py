@@ -180,3 +180,13 @@ def test_sign_sgd_recovers_conductances(oracle_lib):
     assert final < 1e-4 * first
     assert np.allclose(th, th_true, rtol=2e-2)
     assert np.array_equal(th, th[cg["rev"]])
+
+
+def test_sgd_lower_bound(oracle_lib):
+    """theta_min bounds the update from below and changes nothing above it."""
+    cg, th, X, c = _setup_pairs(oracle_lib)
+    Y = np.stack([pngm.scheme3(cg, th * 0.8, x, c) for x in X])
+    free, _ = pngm.sgd_step(1, cg, th, X, Y, c, lr=10.0)
+    low, _ = pngm.sgd_step(1, cg, th, X, Y, c, lr=10.0, theta_min=0.0)
+    assert np.array_equal(low, np.where(free < 0.0, 0.0, free))
+    assert free.min() < 0.0 <= low.min()
