@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the graph-build, implicit, adjoint and batched measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (for profiler runs)")
+    ap.add_argument("--kernel", default=None,
+                    help="fix the explicit kernel instead of autotuning: 'variant:chunk' or '3:chunk:depth:ctas'")
     return ap.parse_args()
 
 
@@ -222,7 +224,17 @@ def bench_ours(a):
     sim = vga.Sim(g, params, stream=stream)
     x0_dev = torch.from_numpy(X0).cuda()
     sim.set_masses(x0_dev)
-    tune = sim.autotune(100)  # picks the stencil variant / chunk / wavefront shape; state left unchanged
+    if a.kernel:
+        f = [int(v) for v in a.kernel.split(":")]
+        if f[0] == 3:
+            sim.set_wavefront(f[1], f[2], f[3] if len(f) > 3 else 0)
+            best = dict(variant=3, chunk=f[1], depth=f[2], ctas_per_sm=f[3] if len(f) > 3 else 0)
+        else:
+            sim.set_kernel(f[0], f[1] if len(f) > 1 else 1024)
+            best = dict(variant=f[0], chunk=f[1] if len(f) > 1 else 1024, depth=0, ctas_per_sm=0)
+        tune = {"best": best, "entries": [], "fixed": True}
+    else:
+        tune = sim.autotune(100)  # picks the stencil variant / chunk / wavefront shape; state left unchanged
     tot0 = sim.totals()
 
     S = a.substeps

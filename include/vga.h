@@ -250,7 +250,8 @@ vga_status vga_loss_block_mass(vga_sim *s, int32_t block_side, uint32_t comp_mas
  * The default is 2. */
 vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t chunk);
 
-/* Selects variant 3 with `chunk` nodes per work item (multiple of 256 in [256, 8192]), `depth`
+/* Selects variant 3 with `chunk` nodes per work item (a power of two in [256, 8192]; CTAs of
+ * min(chunk, 1024) threads), `depth`
  * passes per block of the skewed order (1..64: the passes whose intermediate states stay in L2),
  * and ctas_per_sm persistent CTAs per SM (0 = as many as fit).  Every wait of the persistent
  * kernel is bounded; one that gives up makes the next synchronising call return VGA_ERR_TIMEOUT

@@ -17,10 +17,9 @@ struct Candidate {
     int variant, cap, depth, ctas;  // depth, ctas: wavefront passes per block and CTAs per SM
 };
 
-constexpr Candidate kCandidates[] = {{2, 1024, 0, 0}, {1, 1024, 0, 0}, {0, 1024, 0, 0}, {0, 512, 0, 0},
-                                     {3, 256, 4, 0},  {3, 512, 4, 0},  {3, 512, 8, 0},  {3, 256, 8, 0},
-                                     {3, 1024, 4, 0}, {3, 512, 2, 0},  {3, 512, 4, 4},  {3, 256, 16, 0},
-                                     {3, 512, 16, 0}, {3, 1024, 8, 2}};
+constexpr Candidate kCandidates[] = {{2, 1024, 0, 0}, {1, 1024, 0, 0}, {1, 512, 0, 0},  {1, 2048, 0, 0},
+                                     {0, 1024, 0, 0}, {0, 512, 0, 0},  {0, 2048, 0, 0}, {3, 1024, 2, 0},
+                                     {3, 512, 4, 0},  {3, 256, 4, 0}};
 
 vga_status snapshot(vga_sim *s, float *h, uint16_t *l, bool restore) {
     for (int c = 0; c < 5; ++c) {
@@ -61,7 +60,7 @@ extern "C" vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t ch
     if (variant < 0 || variant > 3 || chunk < 32 || chunk > 8192 || (chunk & 31))
         return fail(VGA_ERR_INVALID_ARG, "variant must lie in [0, 3] and chunk be a multiple of 32 in [32, 8192]");
     if (variant == 3) {
-        if (!wave_params_valid(chunk, 4, 0)) return fail(VGA_ERR_INVALID_ARG, "wavefront chunks are multiples of 256");
+        if (!wave_params_valid(chunk, 4, 0)) return fail(VGA_ERR_INVALID_ARG, "wavefront chunks are powers of two >= 256");
         VGA_TRY(select_kernel(s, 3, chunk, 4, 0));
         return VGA_OK;
     }
@@ -76,7 +75,7 @@ extern "C" vga_status vga_sim_set_wavefront(vga_sim *s, int32_t chunk, int32_t d
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
     if (!wave_params_valid(chunk, depth, ctas_per_sm))
         return fail(VGA_ERR_INVALID_ARG,
-                    "chunk must be a multiple of 256 in [256, 8192], depth in [1, 64], ctas_per_sm in [0, 32]");
+                    "chunk must be a power of two in [256, 8192], depth in [1, 64], ctas_per_sm in [0, 32]");
     return select_kernel(s, 3, chunk, depth, ctas_per_sm);
 }
 

@@ -2,24 +2,28 @@
 // several fused passes run inside one persistent kernel as a wavefront over chunks of nodes, so
 // that the state one pass writes is read back by the next pass from L2 instead of HBM.
 //
-// Work item (s, j) = fused pass s over the nodes of chunk j (C consecutive nodes).  Pass s reads
-// buffer set s & 1 and writes the other set.  Item (s, j) may run once pass s - 1 has completed
-// every chunk in [dep_lo[j], dep_hi[j]], the chunks that neighbours of chunk j's nodes lie in:
-// that covers the transformed DOM it reads (read after write) and every reader of the values it
+// Dependencies are tracked per chunk of C consecutive nodes; work is done per warp item, 32
+// consecutive nodes.  Item (s, j, w) = fused pass s over warp item w of chunk j.  Pass s reads
+// buffer set s & 1 and writes the other set.  An item may run once pass s - 1 has completed every
+// chunk in [dep_lo[j], dep_hi[j]], the chunks that neighbours of chunk j's nodes lie in: that
+// covers the transformed DOM it reads (read after write) and every reader of the values it
 // overwrites (write after read: chunk j's values are read only by chunks whose neighbours reach
-// j, and adjacency is symmetric).  flags[j] counts the passes chunk j has completed in this
-// launch; the CTA's threads check the dependency range in parallel.
+// j, and adjacency is symmetric).  count[j] counts the warp items of chunk j completed in this
+// launch over all passes; pass s is complete for chunk j exactly when count[j] >= (s + 1) nw_j
+// (nw_j = warp items of chunk j), because no item of pass s + 1 in chunk j can start before pass
+// s of chunk j is complete (j lies in its own dependency range).
 //
 // Items are numbered (tickets) in a skewed order: passes are grouped in blocks of T; inside a
-// block, diagonal d holds the items (t, d - t L) for t = 0..T-1, with L larger than any dependency
-// reach (max dep_hi[j] - j) plus the diagonals that the grid works on at once.  Every item depends
-// only on items with smaller tickets.  CTA b takes tickets b, b + G, b + 2G, ... in order, so the
-// lowest unfinished ticket always has its dependencies complete and the launch makes progress;
-// the waits are bounded nonetheless (a spin limit sets the device error flag and every CTA
-// returns).
+// block, diagonal d holds the chunks (t, d - t L) for t = 0..T-1, each contributing its warp items
+// consecutively, with L larger than any dependency reach (max dep_hi[j] - j) plus the chunks the
+// grid works on at once.  Every item depends only on items with smaller tickets.  Warp g of the
+// grid takes tickets g, g + W, g + 2W, ... in order, so the lowest unfinished ticket always has
+// its dependencies complete and the launch makes progress; the waits are bounded nonetheless (a
+// spin limit sets the device error flag and the warps return).  Warps never wait for one another
+// inside a CTA, so a warp's dependency check or memory latency overlaps the other warps' work.
 //
 // The arithmetic per node is table_node (bit-identical to the one-pass-per-launch table kernel);
-// state loads go through L2 (ld.global.cg) because other CTAs of the launch wrote them.
+// state loads go through L2 (ld.global.cg) because other warps of the launch wrote them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,88 +35,82 @@
 namespace vga {
 namespace {
 
-constexpr int kWaveThreads = 256;
 constexpr int kWaveSpin = 1 << 21;  // dependency polls before a wait gives up (>= 0.25 s with the sleeps)
+constexpr int kWaveThreads = 256;   // 8 independent warps per CTA
 
 struct WaveArgs {
     int64_t n;
-    int32_t C;     // nodes per chunk (multiple of kWaveThreads)
+    int32_t C;     // nodes per chunk (a power of two >= 256): dependency granularity
     int32_t T;     // passes per block of the skewed order
     int32_t P;     // fused passes in this launch
     int32_t nord;  // entries of order (T x chunks)
     const int32_t *order;  // (t << 24) | j in ticket order within one block of T passes
     const int32_t *dep;    // per chunk: dep_lo at 2j, dep_hi at 2j + 1
-    uint32_t *flags;       // per chunk: passes completed in this launch (zero at launch)
+    uint32_t *count;       // per chunk: warp items completed in this launch (zero at launch)
     int32_t *err;
 };
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t *p) { return *(const volatile uint32_t *)p; }
 __device__ __forceinline__ int32_t ld_volatile_i32(const int32_t *p) { return *(const volatile int32_t *)p; }
-
-template <int WM, int TR, int PREC>
-__device__ __forceinline__ void wave_chunk(const WaveArgs &a, int32_t j, const NbrTable &tb, const BlockTable &bt,
-                                           const StepParams &p, const StateIO &io) {
-    const int64_t base = (int64_t)j * a.C;
-    for (int32_t k = 0; k < a.C; k += kWaveThreads) {
-        const int64_t i = base + k + threadIdx.x;
-        table_node<1, WM, TR, PREC, LD_CG>((uint32_t)i, i < a.n, tb, bt, p, io);
-    }
-}
 
 template <int WM, int TR, int PREC>
 __global__ void __launch_bounds__(kWaveThreads) k_wave(WaveArgs a, NbrTable tb, BlockTable bt, StepParams p,
                                                        StateIO io0, StateIO io1) {
-    __shared__ int32_t s_stop;
-    const unsigned long long total = (unsigned long long)((a.P + a.T - 1) / a.T) * (unsigned long long)a.nord;
-    if (threadIdx.x == 0) s_stop = 0;
-    __syncthreads();
-    for (unsigned long long t = blockIdx.x; t < total; t += gridDim.x) {
-        const int32_t blk = (int32_t)(t / (unsigned long long)a.nord);
-        const int32_t e = __ldg(a.order + (t - (unsigned long long)blk * a.nord));
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nwarps = (unsigned long long)gridDim.x * (kWaveThreads / 32);
+    const unsigned long long gw = (unsigned long long)blockIdx.x * (kWaveThreads / 32) + (threadIdx.x >> 5);
+    const int32_t wpc = a.C >> 5;  // warp items per full chunk
+    const int32_t J = a.nord / a.T;
+    const uint32_t w_last = (uint32_t)(((a.n - (int64_t)(J - 1) * a.C) + 31) >> 5);  // warp items of the last chunk
+    const unsigned long long per_blk = (unsigned long long)a.nord * wpc;
+    const unsigned long long total = (unsigned long long)((a.P + a.T - 1) / a.T) * per_blk;
+    for (unsigned long long t = gw; t < total; t += nwarps) {
+        const int32_t blk = (int32_t)(t / per_blk);
+        const unsigned long long r = t - (unsigned long long)blk * per_blk;
+        const int32_t e = __ldg(a.order + (int32_t)(r / (unsigned)wpc));
+        const int32_t w = (int32_t)(r % (unsigned)wpc);
         const int32_t s = blk * a.T + (e >> 24);
         const int32_t j = e & 0xffffff;
-        if (s >= a.P) continue;  // the last block may hold fewer than T passes (uniform per CTA)
+        const int64_t i0 = (int64_t)j * a.C + (int64_t)w * 32;
+        if (s >= a.P || i0 >= a.n) continue;  // warp-uniform
         if (s > 0) {
             const int32_t lo = __ldg(a.dep + 2 * j), hi = __ldg(a.dep + 2 * j + 1);
             for (int it = 0;; ++it) {
-                int ok = 1;
-                for (int32_t q = lo + (int32_t)threadIdx.x; q <= hi; q += blockDim.x)
-                    if (ld_acquire_u32(a.flags + q) < (uint32_t)s) {
-                        ok = 0;
+                bool ok = true;
+                for (int32_t q = lo + lane; q <= hi; q += 32) {
+                    const uint32_t need = (uint32_t)s * (q == J - 1 ? w_last : (uint32_t)wpc);
+                    if (ld_volatile_u32(a.count + q) < need) {
+                        ok = false;
                         break;
                     }
-                if (__syncthreads_and(ok)) break;
-                if (threadIdx.x == 0 && (it > kWaveSpin || ld_volatile_i32(a.err))) {
-                    atomicExch(a.err, 2);
-                    s_stop = 1;
                 }
-                __syncthreads();
-                if (s_stop) return;
-                __nanosleep(128);
+                if (__all_sync(0xffffffffu, ok)) break;
+                int stop = 0;
+                if (lane == 0 && (it > kWaveSpin || ld_volatile_i32(a.err))) {
+                    atomicExch(a.err, 2);
+                    stop = 1;
+                }
+                if (__shfl_sync(0xffffffffu, stop, 0)) return;
+                __nanosleep(64);
             }
+            __threadfence();  // order the observed counts before the state loads
         }
-        if (s & 1) wave_chunk<WM, TR, PREC>(a, j, tb, bt, p, io1);
-        else wave_chunk<WM, TR, PREC>(a, j, tb, bt, p, io0);
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        const int64_t i = i0 + lane;
+        if (s & 1) table_node<1, WM, TR, PREC, LD_CG>((uint32_t)i, i < a.n, tb, bt, p, io1);
+        else table_node<1, WM, TR, PREC, LD_CG>((uint32_t)i, i < a.n, tb, bt, p, io0);
+        __syncwarp();
+        if (lane == 0) {
             __threadfence();
-            st_release_u32(a.flags + j, (uint32_t)s + 1u);
+            atomicAdd(a.count + j, 1u);
         }
     }
 }
 
 // dep[2j], dep[2j+1] = chunks of the lowest- and highest-index neighbours of chunk j's nodes
 // (chunk j itself included).
-__global__ void __launch_bounds__(kWaveThreads) k_wave_deps(int64_t n, NbrTable tb, int32_t C, int32_t *dep) {
+constexpr int kDepThreads = 256;
+
+__global__ void __launch_bounds__(kDepThreads) k_wave_deps(int64_t n, NbrTable tb, int32_t C, int32_t *dep) {
     const int32_t j = blockIdx.x;
     const int64_t base = (int64_t)j * C;
     int64_t hi = base, lo = base;
@@ -132,7 +130,7 @@ __global__ void __launch_bounds__(kWaveThreads) k_wave_deps(int64_t n, NbrTable 
         hi = max(hi, h);
         lo = min(lo, l);
     }
-    __shared__ long long sh[2][kWaveThreads / 32];
+    __shared__ long long sh[2][kDepThreads / 32];
     for (int o = 16; o > 0; o >>= 1) {
         hi = max(hi, (int64_t)__shfl_down_sync(0xffffffffu, (long long)hi, o));
         lo = min(lo, (int64_t)__shfl_down_sync(0xffffffffu, (long long)lo, o));
@@ -153,39 +151,20 @@ __global__ void __launch_bounds__(kWaveThreads) k_wave_deps(int64_t n, NbrTable 
     }
 }
 
-template <int WM, int PREC>
-vga_status launch_wave(vga_sim *s, const WaveArgs &a, const NbrTable &tb, const BlockTable &bt, const StateIO &io0,
-                       const StateIO &io1, int grid) {
-    void *kern = s->sp.transform == 0 ? (void *)k_wave<WM, 0, PREC> : (void *)k_wave<WM, 1, PREC>;
-    WaveArgs aa = a;
-    NbrTable t2 = tb;
-    BlockTable b2 = bt;
-    StepParams p2 = s->sp;
-    StateIO i0 = io0, i1 = io1;
-    void *args[] = {&aa, &t2, &b2, &p2, &i0, &i1};
-    VGA_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kWaveThreads), args, 0, s->stream));
-    return VGA_OK;
-}
-
-int wave_occupancy(int wm, int prec, int tr) {
-    int occ = 0;
-    const void *k = nullptr;
+void *wave_kernel_for(int wm, int prec, int tr) {
     if (wm == W_UNIT) {
-        if (prec == P_COMP) k = tr ? (const void *)k_wave<W_UNIT, 1, P_COMP> : (const void *)k_wave<W_UNIT, 0, P_COMP>;
-        else k = tr ? (const void *)k_wave<W_UNIT, 1, P_F32> : (const void *)k_wave<W_UNIT, 0, P_F32>;
-    } else {
-        if (prec == P_COMP) k = tr ? (const void *)k_wave<W_BLOCK, 1, P_COMP> : (const void *)k_wave<W_BLOCK, 0, P_COMP>;
-        else k = tr ? (const void *)k_wave<W_BLOCK, 1, P_F32> : (const void *)k_wave<W_BLOCK, 0, P_F32>;
+        if (prec == P_COMP) return tr ? (void *)k_wave<W_UNIT, 1, P_COMP> : (void *)k_wave<W_UNIT, 0, P_COMP>;
+        return tr ? (void *)k_wave<W_UNIT, 1, P_F32> : (void *)k_wave<W_UNIT, 0, P_F32>;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kWaveThreads, 0) != cudaSuccess) return 0;
-    return occ;
+    if (prec == P_COMP) return tr ? (void *)k_wave<W_BLOCK, 1, P_COMP> : (void *)k_wave<W_BLOCK, 0, P_COMP>;
+    return tr ? (void *)k_wave<W_BLOCK, 1, P_F32> : (void *)k_wave<W_BLOCK, 0, P_F32>;
 }
 
 }  // namespace
 
 bool wave_params_valid(int chunk, int depth, int ctas_per_sm) {
-    return chunk >= kWaveThreads && chunk <= 8192 && chunk % kWaveThreads == 0 && depth >= 1 && depth <= 64 &&
-           ctas_per_sm >= 0 && ctas_per_sm <= 32;
+    const bool pow2 = chunk > 0 && (chunk & (chunk - 1)) == 0;
+    return pow2 && chunk >= 256 && chunk <= 8192 && depth >= 1 && depth <= 64 && ctas_per_sm >= 0 && ctas_per_sm <= 32;
 }
 
 // Runs P fused passes (the passes 1..P of a step(P + 1) call) as one wavefront launch.  On return
@@ -202,21 +181,25 @@ vga_status sim_wave_fused(vga_sim *s, int64_t P) {
     const int C = s->wave_chunk, T = s->wave_depth;
     const int64_t J64 = (s->n + C - 1) / C;
     if (J64 >= (1 << 24)) return fail(VGA_ERR_UNSUPPORTED, "too many chunks for the wavefront order");
+    if (P * (C / 32) >= ((int64_t)1 << 31)) return fail(VGA_ERR_INVALID_ARG, "too many passes for one wavefront launch");
     const int32_t J = (int32_t)J64;
     int dev = 0, nsm = 0;
     VGA_CUDA(cudaGetDevice(&dev));
     VGA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const int occ = wave_occupancy(s->wmode, s->precision(), s->sp.transform);
-    if (occ < 1) return fail(VGA_ERR_CUDA, "wavefront kernel occupancy query failed");
+    void *kern = wave_kernel_for(s->wmode, s->precision(), s->sp.transform);
+    int occ = 0;
+    VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWaveThreads, 0));
+    if (occ < 1) return fail(VGA_ERR_CUDA, "wavefront kernel does not fit on an SM");
     const int per_sm = s->wave_ctas > 0 ? std::min(s->wave_ctas, occ) : occ;
-    const int grid = (int)std::min<int64_t>((int64_t)per_sm * nsm, std::max<int64_t>(J64, 1));
+    const int64_t witems = (s->n + 31) / 32;
+    const int grid = (int)std::min<int64_t>((int64_t)per_sm * nsm, std::max<int64_t>((witems + 7) / 8, 1));
     // dependency ranges per chunk (once per chunk size), then one completion flag per chunk
     if (s->wave_built_chunk != C) {
         dfree(s->wave_dep);
         s->wave_dep = nullptr;
         s->wave_built_chunk = 0;
         VGA_TRY(dmalloc((void **)&s->wave_dep, sizeof(int32_t) * 3 * (size_t)J, "wavefront dependencies"));
-        k_wave_deps<<<J, kWaveThreads, 0, s->stream>>>(s->n, tb, C, s->wave_dep);
+        k_wave_deps<<<J, kDepThreads, 0, s->stream>>>(s->n, tb, C, s->wave_dep);
         VGA_CHECK_LAUNCH();
         std::vector<int32_t> h(2 * (size_t)J);
         VGA_CUDA(cudaMemcpyAsync(h.data(), s->wave_dep, sizeof(int32_t) * 2 * (size_t)J, cudaMemcpyDeviceToHost,
@@ -228,8 +211,10 @@ vga_status sim_wave_fused(vga_sim *s, int64_t P) {
         s->wave_built_chunk = C;
         s->wave_built_lag = -1;
     }
-    // skewed order: lag = reach + 1 + the diagonals the grid works on at once (+ margin)
-    const int32_t lag = s->wave_reach + 1 + (grid + T - 1) / T + 4;
+    // skewed order: lag = reach + 1 + 1.5 times the chunk diagonals the grid's warps work on at
+    // once (+ margin), so an item's dependencies were issued well before it
+    const int64_t chunks_in_flight = ((int64_t)grid * (kWaveThreads / 32) + (C / 32) - 1) / (C / 32);
+    const int32_t lag = s->wave_reach + 1 + (int32_t)((3 * chunks_in_flight + 2 * T - 1) / (2 * T)) + 4;
     if (s->wave_built_lag != lag || s->wave_built_depth != T) {
         std::vector<int32_t> ord;
         ord.reserve((size_t)T * J);
@@ -249,8 +234,8 @@ vga_status sim_wave_fused(vga_sim *s, int64_t P) {
         s->wave_built_lag = lag;
         s->wave_built_depth = T;
     }
-    uint32_t *flags = reinterpret_cast<uint32_t *>(s->wave_dep + 2 * (size_t)J);
-    VGA_CUDA(cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (size_t)J, s->stream));
+    uint32_t *count = reinterpret_cast<uint32_t *>(s->wave_dep + 2 * (size_t)J);
+    VGA_CUDA(cudaMemsetAsync(count, 0, sizeof(uint32_t) * (size_t)J, s->stream));
     WaveArgs a;
     a.n = s->n;
     a.C = C;
@@ -259,7 +244,7 @@ vga_status sim_wave_fused(vga_sim *s, int64_t P) {
     a.nord = T * J;
     a.order = s->wave_order;
     a.dep = s->wave_dep;
-    a.flags = flags;
+    a.count = count;
     a.err = s->d_err;
     StateIO io0, io1;
     for (int c = 0; c < 5; ++c) {
@@ -272,17 +257,12 @@ vga_status sim_wave_fused(vga_sim *s, int64_t P) {
         io1.lin[c] = s->lspare(c);
         io1.lout[c] = s->lcomp(c);
     }
-    const bool comp = s->precision() == P_COMP;
+    StepParams sp = s->sp;
+    void *args[] = {&a, &tb, &bt, &sp, &io0, &io1};
     timing_begin(s, VGA_KERNEL_FUSED_STEP);
-    vga_status st;
-    if (s->wmode == W_BLOCK)
-        st = comp ? launch_wave<W_BLOCK, P_COMP>(s, a, tb, bt, io0, io1, grid)
-                  : launch_wave<W_BLOCK, P_F32>(s, a, tb, bt, io0, io1, grid);
-    else
-        st = comp ? launch_wave<W_UNIT, P_COMP>(s, a, tb, bt, io0, io1, grid)
-                  : launch_wave<W_UNIT, P_F32>(s, a, tb, bt, io0, io1, grid);
+    const cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kWaveThreads), args, 0, s->stream);
     timing_end_weighted(s, P);
-    VGA_TRY(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(k_wave)", __FILE__, __LINE__);
     ++s->launches;
     if (P & 1)
         for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;

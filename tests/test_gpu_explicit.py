@@ -250,7 +250,7 @@ def test_autotune_keeps_state(vga, oracle_lib):
     sim.step(3)
     before = sim.save_state()
     res = sim.autotune(4)
-    assert res["best"] is not None and len(res["entries"]) == 14
+    assert res["best"] is not None and len(res["entries"]) == 10
     assert all(e["ms_per_step"] > 0 for e in res["entries"])
     assert sim.save_state() == before
     with pytest.raises(vga.VgaError):
