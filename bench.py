@@ -343,16 +343,22 @@ def bench_ours(a):
         simi.sync()
         it0 = simi.stats()["cg_iterations"]
         torch.cuda.synchronize()
+        simi.enable_timing(True)
+        simi.read_timing(reset=True)
         w0 = time.perf_counter()
         nimp = 3
         simi.step(nimp)
         simi.sync()
         w1 = time.perf_counter()
+        kti = simi.read_timing(reset=True)
+        simi.enable_timing(False)
         st = simi.stats()
         extras["implicit"] = {"value": n * nimp / (w1 - w0), "unit": UNIT + " (one solve = one step)",
                               "cg_iterations_per_step": (st["cg_iterations"] - it0) / nimp,
                               "last_relres": st["cg_last_relres"], "dt_over_explicit_limit": 10 / 0.9 * 0.9,
-                              "rtol": 1e-8}
+                              "rtol": 1e-8,
+                              "kernel_ms": {k: round(v[0], 3) for k, v in kti.items() if v[1]},
+                              "kernel_launches": {k: v[1] for k, v in kti.items() if v[1]}}
         simi.close()
         extras["adjoint"] = bench_adjoint(vga, g, params, x0_dev, n, stream)
         extras["batched"] = bench_batched(vga, a)

@@ -168,10 +168,21 @@ vga_status vga_sim_get_masses(vga_sim *s, double *x, int32_t on_device);
 vga_status vga_sim_set_state_f32(vga_sim *s, const float *x, int32_t on_device);
 vga_status vga_sim_get_state_f32(vga_sim *s, float *x, int32_t on_device);
 
+/* Implicit solver (Scheme 2).  VGA_SOLVER_FP64_PCG: Jacobi-PCG in FP64, stopping on the
+ * recurrence residual.  VGA_SOLVER_MIXED_REFINEMENT (default): the residual b - B x and x are kept
+ * in FP64 and each correction is solved by the same Jacobi-PCG in FP32 (to a 1e-4 reduction);
+ * stops when the true residual satisfies ||b - B x||_2 <= cg_rtol ||b||_2; iterations count the FP32
+ * inner iterations against cg_maxit.  Used with unit conductances (block conductances run the FP64
+ * solver).  Errors: VGA_ERR_INVALID_ARG. */
+#define VGA_SOLVER_FP64_PCG 0
+#define VGA_SOLVER_MIXED_REFINEMENT 1
+vga_status vga_sim_set_solver(vga_sim *s, int32_t solver);
+
 /* Exact checkpoint of the state: the FP32 values, their residuals and the step counter, in a
- * caller-allocated host buffer of vga_sim_state_bytes() bytes (format private to the library,
- * valid for a simulation on the same graph with the same state_precision).  Restoring it and
- * stepping reproduces an uninterrupted run bit for bit. */
+ * caller-allocated host buffer of vga_sim_state_bytes() bytes (a 32-byte header, then the 5n FP32
+ * values, then the 5n BF16 residuals, compartment-major; valid for a simulation on the same graph
+ * with the same state_precision).  Restoring it and stepping reproduces an uninterrupted run bit
+ * for bit. */
 vga_status vga_sim_state_bytes(const vga_sim *s, int64_t *bytes);
 vga_status vga_sim_save_state(vga_sim *s, void *buf, int64_t bytes);
 vga_status vga_sim_load_state(vga_sim *s, const void *buf, int64_t bytes);
@@ -407,8 +418,9 @@ vga_status vga_pngm_get_theta(const vga_pngm *pg, double *theta, int32_t on_devi
 
 /* Primitive masses of compartment comp (0..4) of simulation s (which must run on the same graph):
  * d_out[i] = sum of the node masses of primitive i (device, FP64, q entries; overwritten), ordered
- * on the simulation's stream.  Summation order is not fixed (FP64 atomics).  Errors:
- * VGA_ERR_INVALID_ARG, VGA_ERR_CUDA. */
+ * on the simulation's stream.  The sums are exact in fixed point (every node mass rounded to a
+ * multiple of 2^(e-61), where the sum of |masses| is below 2^e), so the result is deterministic.
+ * Errors: VGA_ERR_INVALID_ARG, VGA_ERR_OOM, VGA_ERR_CUDA. */
 vga_status vga_pngm_restrict(vga_pngm *pg, vga_sim *s, int32_t comp, double *d_out);
 
 /* n_steps coarse steps of d_m[q] (device, FP64, in place) with c = D dt: scheme

@@ -33,6 +33,8 @@ VGA_TRANSFORM_SYNC = 0
 VGA_TRANSFORM_ASYNC = 1
 VGA_STATE_COMPENSATED = 0
 VGA_STATE_F32 = 1
+VGA_SOLVER_FP64_PCG = 0
+VGA_SOLVER_MIXED_REFINEMENT = 1
 
 
 class VgaError(RuntimeError):
@@ -119,6 +121,7 @@ _SIGNATURES = {
     "vga_sgd_block_conductances": [_P, C.c_double, C.c_double, C.c_double],
     "vga_sim_get_block_conductances": [_P, _P, _I64],
     "vga_sim_set_kernel": [_P, _I32, _I32],
+    "vga_sim_set_solver": [_P, _I32],
     "vga_sim_set_wavefront": [_P, _I32, _I32, _I32],
     "vga_sim_autotune": [_P, _I32, _P],
     "vga_sim_enable_timing": [_P, _I32],
@@ -392,6 +395,10 @@ def vga_sim_set_kernel(s, variant: int, chunk: int):
     _check(load_library().vga_sim_set_kernel(s, int(variant), int(chunk)), "vga_sim_set_kernel")
 
 
+def vga_sim_set_solver(s, solver: int):
+    _check(load_library().vga_sim_set_solver(s, int(solver)), "vga_sim_set_solver")
+
+
 def vga_sim_set_wavefront(s, chunk: int, depth: int, ctas_per_sm: int = 0):
     _check(load_library().vga_sim_set_wavefront(s, int(chunk), int(depth), int(ctas_per_sm)), "vga_sim_set_wavefront")
 
@@ -540,8 +547,8 @@ class Graph:
 
     def close(self):
         if self.handle:
-            vga_graph_free(self.handle)
-            self.handle = None
+            h, self.handle = self.handle, None  # never freed twice, even if the free reports an error
+            vga_graph_free(h)
 
     def __del__(self):
         try:
@@ -610,6 +617,9 @@ class Sim:
     def set_kernel(self, variant: int, chunk: int):
         vga_sim_set_kernel(self.handle, variant, chunk)
 
+    def set_solver(self, solver: int):
+        vga_sim_set_solver(self.handle, solver)
+
     def set_wavefront(self, chunk: int, depth: int, ctas_per_sm: int = 0):
         vga_sim_set_wavefront(self.handle, chunk, depth, ctas_per_sm)
 
@@ -639,8 +649,8 @@ class Sim:
 
     def close(self):
         if self.handle:
-            vga_sim_free(self.handle)
-            self.handle = None
+            h, self.handle = self.handle, None
+            vga_sim_free(h)
 
     def __del__(self):
         try:
@@ -680,8 +690,8 @@ class Batch:
 
     def close(self):
         if self.handle:
-            vga_batch_free(self.handle)
-            self.handle = None
+            h, self.handle = self.handle, None
+            vga_batch_free(h)
 
     def __del__(self):
         try:
@@ -820,8 +830,8 @@ class Pngm:
 
     def close(self):
         if self.handle:
-            vga_pngm_free(self.handle)
-            self.handle = None
+            h, self.handle = self.handle, None
+            vga_pngm_free(h)
 
     def __del__(self):
         try:

@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kThreads) k_block_mass(Topo t, const int32_t *
         int slot = 0;
         for (int c = 0; c < 5; ++c) {
             if (!((comp_mask >> c) & 1)) continue;
-            const double v = (double)io.in[c][i] + (double)bf16_bits_to_float(io.lin[c][i]);
+            const double v = (double)io.in[c][i] + (double)res_decode(io.lin[c][i], io.in[c][i]);
             atomicAdd(mass + slot * nblocks + b, v);
             ++slot;
         }
@@ -413,7 +413,7 @@ __global__ void k_lam_in(int64_t n, const double *__restrict__ x, StateIO io) {
         const double v = x[c * n + i];
         const float h = (float)v;
         io.out[c][i] = h;
-        io.lout[c][i] = float_to_bf16_bits((float)(v - (double)h));
+        io.lout[c][i] = res_encode((float)(v - (double)h), h);
     }
 }
 
@@ -421,15 +421,15 @@ __global__ void k_lam_out(int64_t n, double *__restrict__ x, StateIO io) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
 #pragma unroll
-    for (int c = 0; c < 5; ++c) x[c * n + i] = (double)io.in[c][i] + (double)bf16_bits_to_float(io.lin[c][i]);
+    for (int c = 0; c < 5; ++c) x[c * n + i] = (double)io.in[c][i] + (double)res_decode(io.lin[c][i], io.in[c][i]);
 }
 
 inline unsigned grid_for(int64_t count, int threads) { return (unsigned)((count + threads - 1) / threads); }
 
-// Pair of FP32 + BF16 buffers for 5 compartments with row stride npad.
+// Pair of FP32 + residual buffers for 5 compartments with row stride npad.
 struct PairBuf {
     float *h = nullptr;
-    uint16_t *l = nullptr;
+    res_t *l = nullptr;
 };
 
 StateIO io_from(PairBuf in, PairBuf out, int64_t npad) {
@@ -495,15 +495,15 @@ static vga_status ensure_adjoint(vga_sim *s, int64_t nseg, int64_t ckpt) {
     a->ckpt = ckpt;
     a->G = G;
     a->ntheta = ntheta;
-    const size_t pairb = 5 * (size_t)npad * (sizeof(float) + sizeof(uint16_t));
+    const size_t pairb = 5 * (size_t)npad * (sizeof(float) + sizeof(res_t));
     VGA_TRY(dmalloc((void **)&a->ck, pairb * (size_t)nseg, "adjoint checkpoints"));
     VGA_TRY(dmalloc((void **)&a->rec_x, sizeof(float) * 5 * (size_t)npad * (size_t)ckpt, "adjoint records"));
     VGA_TRY(dmalloc((void **)&a->rec_y2, sizeof(float) * (size_t)npad * (size_t)ckpt, "adjoint records"));
     for (int b = 0; b < 2; ++b) {
         VGA_TRY(dmalloc((void **)&a->work[b].h, sizeof(float) * 5 * (size_t)npad, "adjoint work"));
-        VGA_TRY(dmalloc((void **)&a->work[b].l, sizeof(uint16_t) * 5 * (size_t)npad, "adjoint work"));
+        VGA_TRY(dmalloc((void **)&a->work[b].l, sizeof(res_t) * 5 * (size_t)npad, "adjoint work"));
         VGA_TRY(dmalloc((void **)&a->lam[b].h, sizeof(float) * 5 * (size_t)npad, "adjoint state"));
-        VGA_TRY(dmalloc((void **)&a->lam[b].l, sizeof(uint16_t) * 5 * (size_t)npad, "adjoint state"));
+        VGA_TRY(dmalloc((void **)&a->lam[b].l, sizeof(res_t) * 5 * (size_t)npad, "adjoint state"));
     }
     VGA_TRY(dmalloc((void **)&a->gpart, sizeof(double) * kPar * (size_t)std::max<int64_t>(G, 1), "gradient partials"));
     VGA_TRY(dmalloc((void **)&a->gtheta, sizeof(double) * (size_t)ntheta, "theta gradient"));
@@ -512,10 +512,10 @@ static vga_status ensure_adjoint(vga_sim *s, int64_t nseg, int64_t ckpt) {
 }
 
 static PairBuf ck_slot(AdjointBuffers *a, int64_t s) {
-    const size_t pairb = 5 * (size_t)a->npad * (sizeof(float) + sizeof(uint16_t));
+    const size_t pairb = 5 * (size_t)a->npad * (sizeof(float) + sizeof(res_t));
     PairBuf p;
     p.h = reinterpret_cast<float *>(a->ck + pairb * (size_t)s);
-    p.l = reinterpret_cast<uint16_t *>(a->ck + pairb * (size_t)s + 5 * (size_t)a->npad * sizeof(float));
+    p.l = reinterpret_cast<res_t *>(a->ck + pairb * (size_t)s + 5 * (size_t)a->npad * sizeof(float));
     return p;
 }
 
@@ -523,14 +523,14 @@ static PairBuf ck_slot(AdjointBuffers *a, int64_t s) {
 static vga_status copy_state(vga_sim *s, PairBuf p, bool to_sim) {
     for (int c = 0; c < 5; ++c) {
         float *h = p.h + (size_t)c * s->npad;
-        uint16_t *l = p.l + (size_t)c * s->npad;
+        res_t *l = p.l + (size_t)c * s->npad;
         if (to_sim) {
             VGA_CUDA(cudaMemcpyAsync(s->comp(c), h, sizeof(float) * (size_t)s->n, cudaMemcpyDeviceToDevice, s->stream));
-            VGA_CUDA(cudaMemcpyAsync(s->lcomp(c), l, sizeof(uint16_t) * (size_t)s->n, cudaMemcpyDeviceToDevice,
+            VGA_CUDA(cudaMemcpyAsync(s->lcomp(c), l, sizeof(res_t) * (size_t)s->n, cudaMemcpyDeviceToDevice,
                                      s->stream));
         } else {
             VGA_CUDA(cudaMemcpyAsync(h, s->comp(c), sizeof(float) * (size_t)s->n, cudaMemcpyDeviceToDevice, s->stream));
-            VGA_CUDA(cudaMemcpyAsync(l, s->lcomp(c), sizeof(uint16_t) * (size_t)s->n, cudaMemcpyDeviceToDevice,
+            VGA_CUDA(cudaMemcpyAsync(l, s->lcomp(c), sizeof(res_t) * (size_t)s->n, cudaMemcpyDeviceToDevice,
                                      s->stream));
         }
     }

@@ -21,17 +21,17 @@ constexpr Candidate kCandidates[] = {{2, 1024, 0, 0}, {1, 1024, 0, 0}, {1, 512, 
                                      {0, 1024, 0, 0}, {0, 512, 0, 0},  {0, 2048, 0, 0}, {3, 1024, 2, 0},
                                      {3, 512, 4, 0},  {3, 256, 4, 0}};
 
-vga_status snapshot(vga_sim *s, float *h, uint16_t *l, bool restore) {
+vga_status snapshot(vga_sim *s, float *h, res_t *l, bool restore) {
     for (int c = 0; c < 5; ++c) {
         float *dh = h + (size_t)c * s->npad;
-        uint16_t *dl = l + (size_t)c * s->npad;
+        res_t *dl = l + (size_t)c * s->npad;
         if (restore) {
             VGA_CUDA(cudaMemcpyAsync(s->comp(c), dh, sizeof(float) * (size_t)s->n, cudaMemcpyDeviceToDevice, s->stream));
-            VGA_CUDA(cudaMemcpyAsync(s->lcomp(c), dl, sizeof(uint16_t) * (size_t)s->n, cudaMemcpyDeviceToDevice,
+            VGA_CUDA(cudaMemcpyAsync(s->lcomp(c), dl, sizeof(res_t) * (size_t)s->n, cudaMemcpyDeviceToDevice,
                                      s->stream));
         } else {
             VGA_CUDA(cudaMemcpyAsync(dh, s->comp(c), sizeof(float) * (size_t)s->n, cudaMemcpyDeviceToDevice, s->stream));
-            VGA_CUDA(cudaMemcpyAsync(dl, s->lcomp(c), sizeof(uint16_t) * (size_t)s->n, cudaMemcpyDeviceToDevice,
+            VGA_CUDA(cudaMemcpyAsync(dl, s->lcomp(c), sizeof(res_t) * (size_t)s->n, cudaMemcpyDeviceToDevice,
                                      s->stream));
         }
     }
@@ -86,9 +86,9 @@ extern "C" vga_status vga_sim_autotune(vga_sim *s, int32_t trial_steps, vga_tune
     out->best = -1;
     if (s->n == 0 || s->params.scheme != VGA_SCHEME_EXPLICIT) return VGA_OK;
     float *h = nullptr;
-    uint16_t *l = nullptr;
+    res_t *l = nullptr;
     VGA_TRY(dmalloc((void **)&h, sizeof(float) * 5 * (size_t)s->npad, "autotune snapshot"));
-    vga_status st = dmalloc((void **)&l, sizeof(uint16_t) * 5 * (size_t)s->npad, "autotune snapshot");
+    vga_status st = dmalloc((void **)&l, sizeof(res_t) * 5 * (size_t)s->npad, "autotune snapshot");
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == VGA_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = fail(VGA_ERR_CUDA, "cudaEventCreate failed");

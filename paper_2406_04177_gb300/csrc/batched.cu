@@ -41,7 +41,7 @@ struct BatchArgs {
     const BInst *inst;
     NbrTable tb;
     float *h[2];
-    uint16_t *l[2];
+    res_t *l[2];
     unsigned *bar;  // [0] arrivals, [1] generation
     int32_t *err;
 };
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int
 }
 
 // FP64 (5 x n) of one instance <-> its slice of the current state buffer
-__global__ void k_batch_in(int64_t n, const double *__restrict__ x, float *h, uint16_t *l, int64_t start,
+__global__ void k_batch_in(int64_t n, const double *__restrict__ x, float *h, res_t *l, int64_t start,
                            int64_t npad, int comp) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -161,17 +161,18 @@ __global__ void k_batch_in(int64_t n, const double *__restrict__ x, float *h, ui
         const double v = x[c * n + i];
         const float hv = (float)v;
         h[c * npad + start + i] = hv;
-        l[c * npad + start + i] = comp ? float_to_bf16_bits((float)(v - (double)hv)) : 0;
+        l[c * npad + start + i] = comp ? res_encode((float)(v - (double)hv), hv) : (res_t)0;
     }
 }
 
-__global__ void k_batch_out(int64_t n, double *__restrict__ x, const float *h, const uint16_t *l, int64_t start,
+__global__ void k_batch_out(int64_t n, double *__restrict__ x, const float *h, const res_t *l, int64_t start,
                             int64_t npad, int comp) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     for (int c = 0; c < 5; ++c) {
-        double v = (double)h[c * npad + start + i];
-        if (comp) v += (double)bf16_bits_to_float(l[c * npad + start + i]);
+        const float hv = h[c * npad + start + i];
+        double v = (double)hv;
+        if (comp) v += (double)res_decode(l[c * npad + start + i], hv);
         x[c * n + i] = v;
     }
 }
@@ -188,7 +189,7 @@ struct vga_batch {
     int transform = 0, precision = 0;
     cudaStream_t stream = nullptr;
     float *h[2] = {nullptr, nullptr};
-    uint16_t *l[2] = {nullptr, nullptr};
+    res_t *l[2] = {nullptr, nullptr};
     uint32_t *table = nullptr;  // 3 x npad
     int32_t *tile_inst = nullptr;
     BInst *inst = nullptr;
@@ -292,6 +293,7 @@ extern "C" {
 
 vga_status vga_batch_free(vga_batch *b) {
     if (!b) return VGA_OK;
+    VGA_TRY(release_status("error pending before vga_batch_free"));
     if (b->stream) cudaStreamSynchronize(b->stream);
     drop_graphs(b);
     for (int k = 0; k < 2; ++k) {
@@ -306,7 +308,7 @@ vga_status vga_batch_free(vga_batch *b) {
     dfree(b->stage);
     if (b->stream) cudaStreamDestroy(b->stream);
     delete b;
-    return VGA_OK;
+    return release_status("vga_batch_free");
 }
 
 vga_status vga_batch_create(const vga_graph *const *graphs, const vga_params *params, int32_t count,
@@ -354,7 +356,7 @@ vga_status vga_batch_create(const vga_graph *const *graphs, const vga_params *pa
     b->total = off;
     b->ntiles = off / kTile;
     b->npad = std::max<int64_t>(64, ((off + 63) / 64) * 64);
-    const size_t hb = sizeof(float) * 5 * (size_t)b->npad, lb = sizeof(uint16_t) * 5 * (size_t)b->npad;
+    const size_t hb = sizeof(float) * 5 * (size_t)b->npad, lb = sizeof(res_t) * 5 * (size_t)b->npad;
     for (int k = 0; k < 2 && st == VGA_OK; ++k) {
         st = dmalloc((void **)&b->h[k], hb, "batch state");
         if (st == VGA_OK) st = dmalloc((void **)&b->l[k], lb, "batch state residuals");
@@ -519,14 +521,14 @@ vga_status vga_batch_autotune(vga_batch *b, int32_t trial_steps, vga_batch_tune 
     const int keep_s = b->steps_per_launch, keep_b = b->blocks_per_sm;
     // save the state (both buffers' current side) so the trials leave it untouched
     float *h = nullptr;
-    uint16_t *l = nullptr;
+    res_t *l = nullptr;
     VGA_TRY(dmalloc((void **)&h, sizeof(float) * 5 * (size_t)b->npad, "autotune snapshot"));
-    vga_status st = dmalloc((void **)&l, sizeof(uint16_t) * 5 * (size_t)b->npad, "autotune snapshot");
+    vga_status st = dmalloc((void **)&l, sizeof(res_t) * 5 * (size_t)b->npad, "autotune snapshot");
     const int cur_keep = b->cur;
     const int64_t steps_keep = b->steps_done, launches_keep = b->launches, replays_keep = b->graph_replays;
     if (st == VGA_OK) {
         cudaMemcpyAsync(h, b->h[b->cur], sizeof(float) * 5 * (size_t)b->npad, cudaMemcpyDeviceToDevice, b->stream);
-        cudaMemcpyAsync(l, b->l[b->cur], sizeof(uint16_t) * 5 * (size_t)b->npad, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(l, b->l[b->cur], sizeof(res_t) * 5 * (size_t)b->npad, cudaMemcpyDeviceToDevice, b->stream);
     }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
@@ -565,7 +567,7 @@ vga_status vga_batch_autotune(vga_batch *b, int32_t trial_steps, vga_batch_tune 
     b->cur = cur_keep;
     if (h && l) {
         cudaMemcpyAsync(b->h[b->cur], h, sizeof(float) * 5 * (size_t)b->npad, cudaMemcpyDeviceToDevice, b->stream);
-        cudaMemcpyAsync(b->l[b->cur], l, sizeof(uint16_t) * 5 * (size_t)b->npad, cudaMemcpyDeviceToDevice, b->stream);
+        cudaMemcpyAsync(b->l[b->cur], l, sizeof(res_t) * 5 * (size_t)b->npad, cudaMemcpyDeviceToDevice, b->stream);
     }
     cudaStreamSynchronize(b->stream);
     b->steps_done = steps_keep;

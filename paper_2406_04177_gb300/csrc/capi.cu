@@ -51,6 +51,12 @@ void dfree(void *p) {
     if (p) cudaFree(p);
 }
 
+vga_status release_status(const char *what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, what, __FILE__, __LINE__);
+    return VGA_OK;
+}
+
 vga_status graph_build_device(vga_graph *g, const uint8_t *d_img, cudaStream_t st);
 vga_status graph_export_device(const vga_graph *g, int64_t *d_von, int32_t *d_nbr, cudaStream_t st);
 int totals_blocks();
@@ -266,12 +272,13 @@ vga_status vga_graph_export(const vga_graph *g, int32_t *labels, int64_t *voxel_
 
 vga_status vga_graph_free(vga_graph *g) {
     if (!g) return VGA_OK;
+    VGA_TRY(release_status("error pending before vga_graph_free"));
     if (g->stream) cudaStreamSynchronize(g->stream);
     dfree(g->labels);
     dfree(g->mask);
     dfree(g->pre);
     delete g;
-    return VGA_OK;
+    return release_status("vga_graph_free");
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -289,7 +296,7 @@ vga_status vga_sim_create(const vga_graph *g, const vga_params *p, void *stream,
     sim_prepare_params(s, p);
     vga_status st = VGA_OK;
     const size_t bytes = sizeof(float) * 5 * (size_t)std::max<int64_t>(s->npad, 64);
-    const size_t lbytes = sizeof(uint16_t) * 5 * (size_t)std::max<int64_t>(s->npad, 64);
+    const size_t lbytes = sizeof(res_t) * 5 * (size_t)std::max<int64_t>(s->npad, 64);
     for (int b = 0; b < 2 && st == VGA_OK; ++b) st = dmalloc((void **)&s->buf[b], bytes, "state");
     for (int b = 0; b < 2 && st == VGA_OK; ++b) st = dmalloc((void **)&s->lbuf[b], lbytes, "state residuals");
     if (st == VGA_OK) st = dmalloc((void **)&s->partials, sizeof(double) * 5 * (size_t)totals_blocks(), "partials");
@@ -328,7 +335,7 @@ vga_status vga_sim_set_params(vga_sim *s, const vga_params *p) {
     if (p->state_precision != s->params.state_precision) {
         // residuals are meaningless across a precision change: start them at zero
         for (int b = 0; b < 2; ++b)
-            VGA_CUDA(cudaMemsetAsync(s->lbuf[b], 0, sizeof(uint16_t) * 5 * (size_t)std::max<int64_t>(s->npad, 64),
+            VGA_CUDA(cudaMemsetAsync(s->lbuf[b], 0, sizeof(res_t) * 5 * (size_t)std::max<int64_t>(s->npad, 64),
                                      s->stream));
     }
     return sim_prepare_params(s, p);
@@ -475,9 +482,11 @@ vga_status vga_sim_save_state(vga_sim *s, void *buf, int64_t bytes) {
         VGA_CUDA(cudaMemcpyAsync(p + (size_t)c * s->n * sizeof(float), s->comp(c), sizeof(float) * (size_t)s->n,
                                  cudaMemcpyDeviceToHost, s->stream));
     p += 5 * (size_t)s->n * sizeof(float);
-    for (int c = 0; c < 5; ++c)
-        VGA_CUDA(cudaMemcpyAsync(p + (size_t)c * s->n * sizeof(uint16_t), s->lcomp(c), sizeof(uint16_t) * (size_t)s->n,
-                                 cudaMemcpyDeviceToHost, s->stream));
+    // residuals leave as BF16 bits (the documented format), converted on the device
+    VGA_TRY(ensure_stage(s));
+    uint16_t *st = reinterpret_cast<uint16_t *>(s->stage);
+    VGA_TRY(sim_res_export(s, st));
+    VGA_CUDA(cudaMemcpyAsync(p, st, sizeof(uint16_t) * 5 * (size_t)s->n, cudaMemcpyDeviceToHost, s->stream));
     VGA_CUDA(cudaStreamSynchronize(s->stream));
     return VGA_OK;
 }
@@ -497,11 +506,20 @@ vga_status vga_sim_load_state(vga_sim *s, const void *buf, int64_t bytes) {
         VGA_CUDA(cudaMemcpyAsync(s->comp(c), p + (size_t)c * s->n * sizeof(float), sizeof(float) * (size_t)s->n,
                                  cudaMemcpyHostToDevice, s->stream));
     p += 5 * (size_t)s->n * sizeof(float);
-    for (int c = 0; c < 5; ++c)
-        VGA_CUDA(cudaMemcpyAsync(s->lcomp(c), p + (size_t)c * s->n * sizeof(uint16_t), sizeof(uint16_t) * (size_t)s->n,
-                                 cudaMemcpyHostToDevice, s->stream));
+    VGA_TRY(ensure_stage(s));
+    uint16_t *st = reinterpret_cast<uint16_t *>(s->stage);
+    VGA_CUDA(cudaMemcpyAsync(st, p, sizeof(uint16_t) * 5 * (size_t)s->n, cudaMemcpyHostToDevice, s->stream));
+    VGA_TRY(sim_res_import(s, st));
     VGA_CUDA(cudaStreamSynchronize(s->stream));
     s->steps_done = hd.steps_done;
+    return VGA_OK;
+}
+
+vga_status vga_sim_set_solver(vga_sim *s, int32_t solver) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    if (solver != VGA_SOLVER_FP64_PCG && solver != VGA_SOLVER_MIXED_REFINEMENT)
+        return fail(VGA_ERR_INVALID_ARG, "unknown solver");
+    s->cg_mixed = solver == VGA_SOLVER_MIXED_REFINEMENT;
     return VGA_OK;
 }
 
@@ -632,6 +650,7 @@ vga_status vga_sim_read_timing(vga_sim *s, vga_kernel_timing *out, int32_t reset
 
 vga_status vga_sim_free(vga_sim *s) {
     if (!s) return VGA_OK;
+    VGA_TRY(release_status("error pending before vga_sim_free"));
     cudaStreamSynchronize(s->stream);
     for (auto &p : s->pending) {
         cudaEventDestroy(p.a);
@@ -646,6 +665,7 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->d_totals);
     dfree(s->d_err);
     dfree(s->nbr_table);
+    dfree(s->nbr_tz);
     dfree(s->bnode);
     dfree(s->bface);
     if (s->h_totals) cudaFreeHost(s->h_totals);
@@ -660,7 +680,7 @@ vga_status vga_sim_free(vga_sim *s) {
     if (s->h_cg) cudaFreeHost(s->h_cg);
     free_chunks(&s->chunks);
     delete s;
-    return VGA_OK;
+    return release_status("vga_sim_free");
 }
 
 }  // extern "C"

@@ -43,7 +43,7 @@ struct CgVecs {
 template <int WM, int PREC>
 __global__ void __launch_bounds__(kThreads) k_cg_init(Topo t, const int32_t *__restrict__ chunk_row, int32_t cap,
                                                       double c, BlockWeights bw, const float *__restrict__ y2,
-                                                      const uint16_t *__restrict__ y2l, CgVecs v,
+                                                      const res_t *__restrict__ y2l, CgVecs v,
                                                       double *__restrict__ part) {
     extern __shared__ uint32_t smem[];
     int32_t *s_nb = reinterpret_cast<int32_t *>(smem + cap);
@@ -60,12 +60,12 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Topo t, const int32_t *__r
             y = (int32_t)(smem[5 * cap + k] & 0xffffu);
             z = (int32_t)(smem[5 * cap + k] >> 16);
         }
-        const double bi = (double)__ldg(y2 + i) + (PREC == P_COMP ? (double)bf16_bits_to_float(__ldg(y2l + i)) : 0.0);
+        const double bi = ld_value_d<PREC>(y2, y2l, i);
         double lb = 0.0, deg = 0.0;
         for_each_neighbour(i, k, fl, s_nb, cap, [&](int slot, int64_t j) {
             const double g = (WM == W_UNIT) ? 1.0 : (double)block_theta(bw, slot, x, y, z);
             const double bj =
-                (double)__ldg(y2 + j) + (PREC == P_COMP ? (double)bf16_bits_to_float(__ldg(y2l + j)) : 0.0);
+                ld_value_d<PREC>(y2, y2l, j);
             lb += g * (bi - bj);
             deg += g;
         });
@@ -148,9 +148,9 @@ __device__ __forceinline__ double nbr_sum_table(NbrTable tb, uint32_t i, bool li
 // x = b (the right-hand side y2 as FP64)
 template <int PREC>
 __global__ void __launch_bounds__(kThreads) k_cg_rhs(int64_t n, const float *__restrict__ y2,
-                                                     const uint16_t *__restrict__ y2l, double *__restrict__ x) {
+                                                     const res_t *__restrict__ y2l, double *__restrict__ x) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] = (double)__ldg(y2 + i) + (PREC == P_COMP ? (double)bf16_bits_to_float(__ldg(y2l + i)) : 0.0);
+    if (i < n) x[i] = ld_value_d<PREC>(y2, y2l, i);
 }
 
 // Grid-stride loops over 256-node tiles (lanes = consecutive nodes) on a fixed grid, so the block
@@ -287,13 +287,13 @@ __global__ void __launch_bounds__(kThreads) k_scalar_b(const double *__restrict_
 }
 
 __global__ void __launch_bounds__(kThreads) k_cg_out(int64_t n, const double *__restrict__ x, float *__restrict__ out,
-                                                     uint16_t *__restrict__ outl, int comp) {
+                                                     res_t *__restrict__ outl, int comp) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double v = x[i];
     const float h = (float)v;
     out[i] = h;
-    if (comp) outl[i] = float_to_bf16_bits((float)(v - (double)h));
+    if (comp) outl[i] = res_encode((float)(v - (double)h), h);
 }
 
 inline unsigned grid_for(int64_t count, int threads) { return (unsigned)((count + threads - 1) / threads); }
@@ -355,6 +355,287 @@ vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgSc
     return h->notconv ? VGA_ERR_NOT_CONVERGED : VGA_OK;
 }
 
+
+// ---- mixed precision: FP64 iterative refinement around an FP32 Jacobi-PCG (unit conductances) ----
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, and the FP64 PCG above is bound by that
+// arithmetic.  Here the outer loop keeps x and b in FP64 and computes the true residual
+// r = b - B x in FP64 (one stencil pass); the correction B d = r is solved by the same Jacobi-PCG
+// in FP32 to a relative reduction tol_in; x += d; the loop stops when ||b - B x||_2 <= rtol ||b||_2
+// (the true residual, not the recurrence).  Every reduction is a fixed-order block-partial sum.
+
+constexpr double kInnerTol = 1e-4;  // reduction asked of one FP32 inner solve
+constexpr int kMxBlocks = 2432;     // grid of the mixed-solver kernels: 152 SMs x 16 (grid-stride)
+constexpr int kMaxOuter = 64;
+
+struct MxScalars {
+    double bb, rr_out, rz, alpha, beta, rr_in, stop_in, relres, rtol2;
+    int32_t done, inner_done, iters, in_iters, notconv, maxit, outer;
+};
+
+struct MxVecs {
+    double *x, *b;
+    float *r, *p, *q, *d, *t;
+};
+
+template <int TF>
+__device__ __forceinline__ float nbr_sum_f(const NbrTable &tb, uint32_t i, bool live, float vi, const float *v) {
+    const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
+    uint32_t dzm, dzp;
+    if (TF == 1) {  // compact z offsets
+        const uint32_t tz = live ? __ldg(tb.tz + i) : 0u;
+        dzm = tz & 0xffffu;
+        dzp = tz >> 16;
+    } else {
+        dzm = live ? __ldg(tb.tzm + i) : 0u;
+        dzp = live ? __ldg(tb.tzp + i) : 0u;
+    }
+    const int lane = threadIdx.x & 31;
+    float vl = __shfl_up_sync(0xffffffffu, vi, 1);
+    float vr = __shfl_down_sync(0xffffffffu, vi, 1);
+    const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
+    const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
+    if (lane == 0 && hxm) vl = v[i - 1];
+    if (lane == 31 && hxp) vr = v[i + 1];
+    float s = 0.0f;
+    if (hxm) s += vi - vl;
+    if (hxp) s += vi - vr;
+    if (dym) s += vi - v[i - dym];
+    if (dyp) s += vi - v[i + dyp];
+    if (dzm) s += vi - v[i - dzm];
+    if (dzp) s += vi - v[i + dzp];
+    return s;
+}
+
+// Outer residual r = b - B x in FP64 (FIRST: b from the state, x = b), t = 1 / (1 + c deg) (FP32),
+// the FP32 copies r and p = T r, d = 0; partials (r.r FP64, b.b, r.Tr).
+template <int PREC, bool FIRST>
+__global__ void __launch_bounds__(kThreads) k_mx_res(int64_t n, NbrTable tb, double c, const float *__restrict__ y2,
+                                                     const res_t *__restrict__ y2l, MxVecs v,
+                                                     double *__restrict__ part, const MxScalars *__restrict__ sc) {
+    if (!FIRST && sc->done) return;
+    double acc[3] = {0.0, 0.0, 0.0};
+    const int64_t ntile = (n + kThreads - 1) / kThreads;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
+        const bool live = i < (uint64_t)n;
+        double xi = 0.0, bi = 0.0;
+        if (live) {
+            bi = FIRST ? ld_value_d<PREC>(y2, y2l, i) : v.b[i];
+            xi = FIRST ? bi : v.x[i];
+        }
+        double deg = 0.0;
+        // FIRST: x = b, so the neighbours' x are read from the state as well
+        const double lx = FIRST ? 0.0 : nbr_sum_table(tb, i, live, xi, v.x, deg);
+        double lb = 0.0;
+        if (FIRST) lb = nbr_sum_table(tb, i, live, xi, v.b, deg);
+        if (live) {
+            const double ri = bi - (xi + c * (FIRST ? lb : lx));
+            const float ti = 1.0f / (1.0f + (float)c * (float)deg);
+            const float r32 = (float)ri;
+            if (FIRST) {
+                v.b[i] = bi;
+                v.x[i] = xi;
+            }
+            v.t[i] = ti;
+            v.r[i] = r32;
+            v.p[i] = ti * r32;
+            v.d[i] = 0.0f;
+            acc[0] += ri * ri;
+            acc[1] += bi * bi;
+            acc[2] += (double)(r32 * (ti * r32));
+        }
+    }
+    __shared__ double out[3];
+    block_sum_store<3>(acc, out);
+    if (threadIdx.x < 3) part[(int64_t)blockIdx.x * 3 + threadIdx.x] = out[threadIdx.x];
+}
+
+// FIRST also fills b before the residual kernel reads neighbours' b (k_mx_res<FIRST> gathers b).
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_mx_rhs(int64_t n, const float *__restrict__ y2,
+                                                     const res_t *__restrict__ y2l, double *__restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = ld_value_d<PREC>(y2, y2l, i);
+}
+
+__global__ void __launch_bounds__(kThreads) k_mx_scal_out(const double *__restrict__ part, int64_t count, MxScalars *sc,
+                                                          int first, double rtol, int maxit) {
+    if (!first && sc->done) return;
+    const double rr = block_reduce_partials(part, count, 3, 0);
+    const double bb = first ? block_reduce_partials(part, count, 3, 1) : 0.0;
+    const double rz = block_reduce_partials(part, count, 3, 2);
+    if (threadIdx.x == 0) {
+        if (first) {
+            sc->bb = bb;
+            sc->rtol2 = rtol * rtol;
+            sc->iters = 0;
+            sc->outer = 0;
+            sc->notconv = 0;
+            sc->maxit = maxit;
+            sc->done = 0;
+        }
+        sc->rr_out = rr;
+        sc->relres = sc->bb > 0.0 ? sqrt(rr / sc->bb) : 0.0;
+        sc->outer += 1;
+        if (sc->bb == 0.0 || rr <= sc->rtol2 * sc->bb) {
+            sc->done = 1;
+        } else if (sc->iters >= sc->maxit || sc->outer > kMaxOuter) {
+            sc->done = 1;
+            sc->notconv = 1;
+        }
+        // reduce the residual by kInnerTol, or just below the target if that asks less
+        const double want = 0.25 * sc->rtol2 * sc->bb / (rr > 0.0 ? rr : 1.0);
+        const double tol2 = want > kInnerTol * kInnerTol ? want : kInnerTol * kInnerTol;
+        sc->stop_in = tol2 * rr;
+        sc->rz = rz;
+        sc->rr_in = rr;
+        sc->in_iters = 0;
+        sc->inner_done = sc->done;
+    }
+}
+
+template <int TF>
+__global__ void __launch_bounds__(kThreads) k_mx_spmv(int64_t n, NbrTable tb, float c, MxVecs v,
+                                                      double *__restrict__ part, const MxScalars *__restrict__ sc) {
+    if (sc->inner_done) return;
+    float acc = 0.0f;
+    const int64_t ntile = (n + kThreads - 1) / kThreads;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
+        const bool live = i < (uint64_t)n;
+        const float pi = live ? v.p[i] : 0.0f;
+        const float lp = nbr_sum_f<TF>(tb, i, live, pi, v.p);
+        if (live) {
+            const float qi = pi + c * lp;
+            v.q[i] = qi;
+            acc += pi * qi;
+        }
+    }
+    double a[1] = {(double)acc};
+    __shared__ double out[1];
+    block_sum_store<1>(a, out);
+    if (threadIdx.x == 0) part[blockIdx.x] = out[0];
+}
+
+__global__ void __launch_bounds__(kThreads) k_mx_scal_a(const double *__restrict__ part, int64_t count, MxScalars *sc) {
+    if (sc->inner_done) return;
+    const double pq = block_reduce_partials(part, count, 1, 0);
+    if (threadIdx.x == 0) sc->alpha = pq > 0.0 ? sc->rz / pq : 0.0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, MxVecs v, const MxScalars *__restrict__ sc,
+                                                     double *__restrict__ part) {
+    if (sc->inner_done) return;
+    const float alpha = (float)sc->alpha;
+    float a0 = 0.0f, a1 = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        v.d[i] += alpha * v.p[i];
+        const float ri = v.r[i] - alpha * v.q[i];
+        v.r[i] = ri;
+        a0 += ri * (v.t[i] * ri);
+        a1 += ri * ri;
+    }
+    double a[2] = {(double)a0, (double)a1};
+    __shared__ double out[2];
+    block_sum_store<2>(a, out);
+    if (threadIdx.x < 2) part[(int64_t)blockIdx.x * 2 + threadIdx.x] = out[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kThreads) k_mx_scal_b(const double *__restrict__ part, int64_t count, MxScalars *sc,
+                                                        int in_maxit) {
+    if (sc->inner_done) return;
+    const double rz = block_reduce_partials(part, count, 2, 0);
+    const double rr = block_reduce_partials(part, count, 2, 1);
+    if (threadIdx.x == 0) {
+        sc->iters += 1;
+        sc->in_iters += 1;
+        sc->rr_in = rr;
+        if (rr <= sc->stop_in || sc->in_iters >= in_maxit || sc->iters >= sc->maxit || !(sc->rz > 0.0)) {
+            sc->inner_done = 1;
+        } else {
+            sc->beta = rz / sc->rz;
+            sc->rz = rz;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mx_p(int64_t n, MxVecs v, const MxScalars *__restrict__ sc) {
+    if (sc->inner_done) return;
+    const float beta = (float)sc->beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v.p[i] = v.t[i] * v.r[i] + beta * v.p[i];
+}
+
+__global__ void __launch_bounds__(kThreads) k_mx_x(int64_t n, MxVecs v, const MxScalars *__restrict__ sc) {
+    if (sc->done) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v.x[i] += (double)v.d[i];
+}
+
+template <int PREC>
+vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b, MxScalars *sc) {
+    const double c = s->params.D * s->params.dt;
+    cudaStream_t st = s->stream;
+    NbrTable tb;
+    VGA_TRY(sim_nbr_table(s, &tb));
+    MxVecs v;
+    v.x = base;
+    v.b = base + s->npad;
+    float *f = reinterpret_cast<float *>(base + 2 * s->npad);
+    v.r = f;
+    v.p = f + s->npad;
+    v.q = f + 2 * s->npad;
+    v.d = f + 3 * s->npad;
+    v.t = f + 4 * s->npad;
+    const int G = (int)std::min<int64_t>(kMxBlocks, grid_for(s->n, kThreads));
+    const int in_maxit = 200;
+    timing_begin(s, VGA_KERNEL_PCG_STENCIL);
+    k_mx_rhs<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->comp(1), s->lcomp(1), v.b);
+    k_mx_res<PREC, true><<<G, kThreads, 0, st>>>(s->n, tb, c, s->comp(1), s->lcomp(1), v, part_a, sc);
+    timing_end(s);
+    k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, 1, s->params.cg_rtol, s->params.cg_maxit);
+    VGA_CHECK_LAUNCH();
+    s->launches += 3;
+    MxScalars *h = reinterpret_cast<MxScalars *>(s->h_cg);
+    for (int guard = 0; guard < 100000; ++guard) {
+        for (int k = 0; k < kBatch; ++k) {
+            timing_begin(s, VGA_KERNEL_PCG_STENCIL);
+            if (tb.tz) k_mx_spmv<1><<<G, kThreads, 0, st>>>(s->n, tb, (float)c, v, part_a, sc);
+            else k_mx_spmv<0><<<G, kThreads, 0, st>>>(s->n, tb, (float)c, v, part_a, sc);
+            timing_end(s);
+            timing_begin(s, VGA_KERNEL_PCG_VECTOR);
+            k_mx_scal_a<<<1, kThreads, 0, st>>>(part_a, G, sc);
+            k_mx_upd<<<G, kThreads, 0, st>>>(s->n, v, sc, part_b);
+            k_mx_scal_b<<<1, kThreads, 0, st>>>(part_b, G, sc, in_maxit);
+            k_mx_p<<<G, kThreads, 0, st>>>(s->n, v, sc);
+            timing_end(s);
+        }
+        VGA_CHECK_LAUNCH();
+        s->launches += 5 * kBatch;
+        VGA_CUDA(cudaMemcpyAsync(h, sc, sizeof(MxScalars), cudaMemcpyDeviceToHost, st));
+        VGA_CUDA(cudaStreamSynchronize(st));
+        if (h->done) break;
+        if (h->inner_done) {
+            // x += d, then the FP64 residual of the new x and the next inner solve's start
+            timing_begin(s, VGA_KERNEL_PCG_STENCIL);
+            k_mx_x<<<G, kThreads, 0, st>>>(s->n, v, sc);
+            k_mx_res<PREC, false><<<G, kThreads, 0, st>>>(s->n, tb, c, s->comp(1), s->lcomp(1), v, part_a, sc);
+            timing_end(s);
+            k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, 0, s->params.cg_rtol, s->params.cg_maxit);
+            VGA_CHECK_LAUNCH();
+            s->launches += 3;
+        }
+    }
+    k_cg_out<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, v.x, s->spare(1), s->lspare(1), PREC == P_COMP);
+    VGA_CHECK_LAUNCH();
+    ++s->launches;
+    s->cur[1] ^= 1;
+    s->cg_iterations += h->iters;
+    s->cg_last_relres = h->relres;
+    return h->notconv ? VGA_ERR_NOT_CONVERGED : VGA_OK;
+}
+
 }  // namespace
 
 vga_status sim_step_implicit(vga_sim *s, int64_t n_steps) {
@@ -363,7 +644,10 @@ vga_status sim_step_implicit(vga_sim *s, int64_t n_steps) {
         return VGA_OK;
     }
     const int64_t G = std::max<int64_t>(s->chunks.count, (s->n + kThreads - 1) / kThreads);
-    const int64_t need = 5 * s->npad + 3 * std::max<int64_t>(G, 1) + 2 * kEwBlocks;
+    // partials: 3 per block of the stencil grids, 2 per block of the elementwise grids
+    const int64_t pa = 3 * std::max<int64_t>(std::max<int64_t>(G, kMxBlocks), 1);
+    const int64_t pb = 2 * (int64_t)std::max(kEwBlocks, kMxBlocks);
+    const int64_t need = 5 * s->npad + pa + pb;
     if (s->cg_count < need) {
         dfree(s->cg);
         s->cg = nullptr;
@@ -371,8 +655,9 @@ vga_status sim_step_implicit(vga_sim *s, int64_t n_steps) {
         VGA_TRY(dmalloc((void **)&s->cg, sizeof(double) * (size_t)need, "PCG vectors"));
         s->cg_count = need;
     }
-    if (!s->cg_scalars) VGA_TRY(dmalloc((void **)&s->cg_scalars, sizeof(CgScalars) + 64, "PCG scalars"));
-    if (!s->h_cg) VGA_CUDA(cudaMallocHost((void **)&s->h_cg, sizeof(CgScalars) + 64));
+    constexpr size_t kScal = sizeof(CgScalars) > sizeof(MxScalars) ? sizeof(CgScalars) : sizeof(MxScalars);
+    if (!s->cg_scalars) VGA_TRY(dmalloc((void **)&s->cg_scalars, kScal + 64, "PCG scalars"));
+    if (!s->h_cg) VGA_CUDA(cudaMallocHost((void **)&s->h_cg, kScal + 64));
     CgVecs v;
     v.x = s->cg;
     v.r = v.x + s->npad;
@@ -380,7 +665,7 @@ vga_status sim_step_implicit(vga_sim *s, int64_t n_steps) {
     v.q = v.p + s->npad;
     v.t = v.q + s->npad;
     double *part_chunk = v.t + s->npad;
-    double *part_ew = part_chunk + 3 * std::max<int64_t>(G, 1);
+    double *part_ew = part_chunk + pa;
     CgScalars *sc = reinterpret_cast<CgScalars *>(s->cg_scalars);
     vga_status worst = VGA_OK;
     for (int64_t k = 0; k < n_steps; ++k) {
@@ -396,6 +681,9 @@ vga_status sim_step_implicit(vga_sim *s, int64_t n_steps) {
         vga_status st;
         if (s->wmode == W_BLOCK)
             st = comp ? solve<W_BLOCK, P_COMP>(s, v, part_chunk, part_ew, sc) : solve<W_BLOCK, P_F32>(s, v, part_chunk, part_ew, sc);
+        else if (s->g->nx <= 32767 && s->cg_mixed)
+            st = comp ? solve_mixed<P_COMP>(s, s->cg, part_chunk, part_ew, reinterpret_cast<MxScalars *>(sc))
+                      : solve_mixed<P_F32>(s, s->cg, part_chunk, part_ew, reinterpret_cast<MxScalars *>(sc));
         else
             st = comp ? solve<W_UNIT, P_COMP>(s, v, part_chunk, part_ew, sc) : solve<W_UNIT, P_F32>(s, v, part_chunk, part_ew, sc);
         if (st == VGA_ERR_NOT_CONVERGED) {

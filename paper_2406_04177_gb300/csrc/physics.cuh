@@ -11,7 +11,10 @@
 // FP32 value h and a residual l (FP32 in registers, BF16 in memory), value = h + l.  Increments are
 // added with an error-free TwoSum whose rounding error goes into l, so the stored significand has
 // about 24 + 9 bits.  Fluxes are computed from h alone: their relative error (~1e-7 of a flux that
-// is itself ~1e-6 of the value) does not accumulate.
+// is itself ~1e-6 of the value) does not accumulate.  (A fixed-point 8-bit residual in units of
+// ulp(h)/256 was measured as well: it rounds a constant per-step decrement the same way every step,
+// which biases slow decays about 4x more, and its encoding costs more instructions than the
+// bytes it saves.)
 #pragma once
 
 #include <cuda_bf16.h>
@@ -52,22 +55,33 @@ __device__ __forceinline__ uint16_t float_to_bf16_bits(float f) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(f));
 }
 
+// Stored residual r of a value whose FP32 part is h (the BF16 encoding does not need h).
+__device__ __forceinline__ res_t res_encode(float r, float /*h*/) { return float_to_bf16_bits(r); }
+__device__ __forceinline__ float res_decode(res_t q, float /*h*/) { return bf16_bits_to_float(q); }
+
+// Value h + l of a stored pair in FP64.
+template <int PREC>
+__device__ __forceinline__ double ld_value_d(const float *__restrict__ H, const res_t *__restrict__ L, int64_t i) {
+    const float h = __ldg(H + i);
+    return (double)h + (PREC == P_COMP ? (double)res_decode(__ldg(L + i), h) : 0.0);
+}
+
 // Load / store of one compartment value.
 template <int PREC>
-__device__ __forceinline__ V vload(const float *__restrict__ H, const uint16_t *__restrict__ L, int64_t i) {
+__device__ __forceinline__ V vload(const float *__restrict__ H, const res_t *__restrict__ L, int64_t i) {
     V v;
     v.h = __ldg(H + i);
-    v.l = (PREC == P_COMP) ? bf16_bits_to_float(__ldg(L + i)) : 0.0f;
+    v.l = (PREC == P_COMP) ? res_decode(__ldg(L + i), v.h) : 0.0f;
     return v;
 }
 
 template <int PREC>
-__device__ __forceinline__ void vstore(float *__restrict__ H, uint16_t *__restrict__ L, int64_t i, V v) {
+__device__ __forceinline__ void vstore(float *__restrict__ H, res_t *__restrict__ L, int64_t i, V v) {
     if (PREC == P_COMP) {
         const float s = __fadd_rn(v.h, v.l);  // renormalise: h = RN(h + l), l = exact remainder
         const float r = __fadd_rn(__fsub_rn(v.h, s), v.l);
         H[i] = s;
-        L[i] = float_to_bf16_bits(r);
+        L[i] = res_encode(r, s);
     } else {
         H[i] = v.h;
     }
@@ -82,7 +96,7 @@ __device__ __forceinline__ void vround(V &v) {
         const float s = __fadd_rn(v.h, v.l);
         const float r = __fadd_rn(__fsub_rn(v.h, s), v.l);
         v.h = s;
-        v.l = bf16_bits_to_float(float_to_bf16_bits(r));
+        v.l = res_decode(res_encode(r, s), s);
     }
 }
 

@@ -50,6 +50,7 @@ struct vga_pngm {
     int32_t *h_pairs = nullptr;  // pinned staging
     int32_t pairs_cap = 0;
     double *h_scal = nullptr;    // pinned: loss, PCG iterations, relres, converged
+    unsigned long long *fx = nullptr;  // restriction: fixed-point sums (q), scale (2), partials
     bool symmetric = true;       // theta_ij == theta_ji for every pair
     // host copies of the geometry (export)
     std::vector<double> h_vol, h_cen, h_S, h_dist;
@@ -208,26 +209,105 @@ __global__ void k_compact_pairs(unsigned long long hsize, const unsigned long lo
     }
 }
 
-// Primitive masses: out[label[i]] += m_i (out zeroed by the caller).
+// Primitive masses: out[label[i]] = sum of m_i over the primitive's nodes, summed exactly in fixed
+// point: every node's value becomes the integer round(m_i * scale), scale = 2^(61 - e) with
+// sum_i |m_i| < 2^e, so no partial sum can overflow int64 and the result does not depend on the
+// order of the atomic additions (the restriction is deterministic).  A CTA sums a segment of kSeg
+// consecutive nodes into a shared-memory hash of labels (warp-level pre-aggregation first) with
+// 64-bit integer atomics, then flushes one global atomic per distinct label; a label that finds no
+// free slot within kProbe probes goes straight to global memory.
+constexpr int kSeg = 4096;
+constexpr int kHash = 1024;
+constexpr int kProbe = 16;
+constexpr int kSumBlocks = 1024;
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_abs_sum(int64_t n, const float *__restrict__ H,
+                                                      const res_t *__restrict__ L, double *__restrict__ part) {
+    double acc[1] = {0.0};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const V x = vload<PREC>(H, L, i);
+        acc[0] += fabs((double)x.h + (double)x.l);
+    }
+    __shared__ double out[1];
+    block_sum_store<1>(acc, out);
+    if (threadIdx.x == 0) part[blockIdx.x] = out[0];
+}
+
+// scale[0] = 2^(61 - e), sum |m| < 2^e; scale[1] = 1 / scale[0]
+__global__ void k_fx_scale(const double *__restrict__ part, int32_t count, double *__restrict__ scale) {
+    double acc[1] = {0.0};
+    for (int32_t k = threadIdx.x; k < count; k += blockDim.x) acc[0] += part[k];
+    __shared__ double out[1];
+    block_sum_store<1>(acc, out);
+    if (threadIdx.x == 0) {
+        const double S = out[0];
+        const int e = S > 0.0 ? ilogb(S) + 1 : 0;
+        scale[0] = ldexp(1.0, 61 - e);
+        scale[1] = ldexp(1.0, e - 61);
+    }
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kThreads) k_restrict(int64_t n, const int32_t *__restrict__ lab,
-                                                       const float *__restrict__ H, const uint16_t *__restrict__ L,
-                                                       double *__restrict__ out) {
-    const int64_t ntile = (n + kThreads - 1) / kThreads;
-    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const int64_t i = tile * kThreads + threadIdx.x;
-        const bool live = i < n;
-        const int32_t a = live ? __ldg(lab + i) : -1;
-        double v = 0.0;
-        if (live) {
-            const V x = vload<PREC>(H, L, i);
-            v = (double)x.h + (double)x.l;
-        }
-        const unsigned act = __ballot_sync(0xffffffffu, live);
-        const unsigned peers = __match_any_sync(0xffffffffu, a);
-        const double s = peer_sum<double>(act, peers, v);
-        if (live && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(out + a, s);
+                                                       const float *__restrict__ H, const res_t *__restrict__ L,
+                                                       const double *__restrict__ scale,
+                                                       unsigned long long *__restrict__ out) {
+    __shared__ int32_t hkey[kHash];
+    __shared__ unsigned long long hval[kHash];
+    for (int k = threadIdx.x; k < kHash; k += blockDim.x) {
+        hkey[k] = -1;
+        hval[k] = 0ull;
     }
+    __syncthreads();
+    const double sc = scale[0];
+    const int64_t nseg = (n + kSeg - 1) / kSeg;
+    for (int64_t seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
+        const int64_t i0 = seg * kSeg;
+        for (int k = 0; k < kSeg; k += kThreads) {
+            const int64_t i = i0 + k + threadIdx.x;
+            const bool live = i < n;
+            const int32_t a = live ? __ldg(lab + i) : -1;
+            unsigned long long v = 0ull;
+            if (live) {
+                const V x = vload<PREC>(H, L, i);
+                v = (unsigned long long)__double2ll_rn(((double)x.h + (double)x.l) * sc);
+            }
+            const unsigned act = __ballot_sync(0xffffffffu, live);
+            const unsigned peers = __match_any_sync(0xffffffffu, a);
+            const unsigned long long sum = peer_sum<unsigned long long>(act, peers, v);
+            if (live && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+                const uint32_t h = (uint32_t)a * 2654435761u;
+                bool done = false;
+                for (int q = 0; q < kProbe; ++q) {
+                    const int slot = (int)((h >> 22) + q) & (kHash - 1);
+                    const int32_t prev = atomicCAS(hkey + slot, -1, a);
+                    if (prev == -1 || prev == a) {
+                        atomicAdd(hval + slot, sum);
+                        done = true;
+                        break;
+                    }
+                }
+                if (!done) atomicAdd(out + a, sum);
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < kHash; k += blockDim.x) {
+            const int32_t key = hkey[k];
+            if (key >= 0) {
+                atomicAdd(out + key, hval[k]);
+                hkey[k] = -1;
+                hval[k] = 0ull;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_fx_out(int32_t q, const unsigned long long *__restrict__ fx, const double *__restrict__ scale,
+                         double *__restrict__ out) {
+    const int32_t a = (int32_t)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (a < q) out[a] = (double)(long long)fx[a] * scale[1];
 }
 
 // Scheme 3: m_i - c sum_s theta_s (m_i / v_i - m_j / v_j), FP64 with every rounding explicit.
@@ -417,19 +497,21 @@ vga_status ensure_pairs(vga_pngm *pg, int32_t l) {
     return VGA_OK;
 }
 
-void pngm_release(vga_pngm *pg) {
-    dfree(pg->labels);
-    dfree(pg->vol);
-    dfree(pg->row_ptr);
-    dfree(pg->col);
-    dfree(pg->rev);
-    dfree(pg->theta);
-    dfree(pg->grad);
-    dfree(pg->work);
-    dfree(pg->d_pairs);
-    if (pg->h_pairs) cudaFreeHost(pg->h_pairs);
-    if (pg->h_scal) cudaFreeHost(pg->h_scal);
+// Frees every buffer of the handle; returns the name of the first release call that failed (the
+// runtime's error state is left set for release_status to report).
+const char *pngm_release(vga_pngm *pg) {
+    const char *bad = nullptr;
+    auto chk = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && !bad) bad = what;
+    };
+    void *dev[] = {pg->labels, pg->vol, pg->row_ptr, pg->col, pg->rev, pg->theta, pg->grad, pg->work, pg->d_pairs, pg->fx};
+    const char *names[] = {"labels", "vol", "row_ptr", "col", "rev", "theta", "grad", "work", "d_pairs", "fx"};
+    for (int k = 0; k < 10; ++k)
+        if (dev[k]) chk(cudaFree(dev[k]), names[k]);
+    if (pg->h_pairs) chk(cudaFreeHost(pg->h_pairs), "h_pairs");
+    if (pg->h_scal) chk(cudaFreeHost(pg->h_scal), "h_scal");
     delete pg;
+    return bad;
 }
 
 vga_status check_theta_symmetry(vga_pngm *pg, const std::vector<double> &th) {
@@ -714,15 +796,29 @@ vga_status vga_pngm_restrict(vga_pngm *pg, vga_sim *s, int32_t comp, double *d_o
     if (s->g != pg->g) return fail(VGA_ERR_INVALID_ARG, "the simulation runs on another graph");
     if (comp < 0 || comp > 4) return fail(VGA_ERR_INVALID_ARG, "comp must lie in [0, 4]");
     cudaStream_t st = s->stream;
-    VGA_CUDA(cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)pg->q, st));
-    if (pg->n == 0) return VGA_OK;
-    const unsigned G = (unsigned)std::min<int64_t>(grid_for(pg->n, kThreads), 152 * 16);
-    if (s->precision() == P_COMP)
-        k_restrict<P_COMP><<<G, kThreads, 0, st>>>(pg->n, pg->labels, s->comp(comp), s->lcomp(comp), d_out);
-    else
-        k_restrict<P_F32><<<G, kThreads, 0, st>>>(pg->n, pg->labels, s->comp(comp), s->lcomp(comp), d_out);
+    if (pg->n == 0) {
+        VGA_CUDA(cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)pg->q, st));
+        return VGA_OK;
+    }
+    if (!pg->fx) VGA_TRY(dmalloc((void **)&pg->fx, sizeof(unsigned long long) * (size_t)pg->q + 2 * sizeof(double) +
+                                                       sizeof(double) * kSumBlocks, "restriction scratch"));
+    double *scale = reinterpret_cast<double *>(pg->fx + pg->q);
+    double *part = scale + 2;
+    VGA_CUDA(cudaMemsetAsync(pg->fx, 0, sizeof(unsigned long long) * (size_t)pg->q, st));
+    const unsigned Gs = (unsigned)std::min<int64_t>(kSumBlocks, grid_for(pg->n, kThreads));
+    const unsigned G = (unsigned)std::min<int64_t>((pg->n + kSeg - 1) / kSeg, 152 * 8);
+    if (s->precision() == P_COMP) {
+        k_abs_sum<P_COMP><<<Gs, kThreads, 0, st>>>(pg->n, s->comp(comp), s->lcomp(comp), part);
+        k_fx_scale<<<1, kThreads, 0, st>>>(part, (int32_t)Gs, scale);
+        k_restrict<P_COMP><<<G, kThreads, 0, st>>>(pg->n, pg->labels, s->comp(comp), s->lcomp(comp), scale, pg->fx);
+    } else {
+        k_abs_sum<P_F32><<<Gs, kThreads, 0, st>>>(pg->n, s->comp(comp), s->lcomp(comp), part);
+        k_fx_scale<<<1, kThreads, 0, st>>>(part, (int32_t)Gs, scale);
+        k_restrict<P_F32><<<G, kThreads, 0, st>>>(pg->n, pg->labels, s->comp(comp), s->lcomp(comp), scale, pg->fx);
+    }
+    k_fx_out<<<grid_for(pg->q, kThreads), kThreads, 0, st>>>(pg->q, pg->fx, scale, d_out);
     VGA_CHECK_LAUNCH();
-    ++s->launches;
+    s->launches += 4;
     return VGA_OK;
 }
 
@@ -794,9 +890,14 @@ vga_status vga_pngm_sgd_step(vga_pngm *pg, int32_t objective_kind, const double 
 
 vga_status vga_pngm_free(vga_pngm *pg) {
     if (!pg) return VGA_OK;
+    VGA_TRY(release_status("error pending before vga_pngm_free"));
     if (pg->stream) cudaStreamSynchronize(pg->stream);
-    pngm_release(pg);
-    return VGA_OK;
+    const char *bad = pngm_release(pg);
+    if (bad) {
+        const std::string what = std::string("vga_pngm_free (") + bad + ")";
+        return release_status(what.c_str());
+    }
+    return release_status("vga_pngm_free");
 }
 
 }  // extern "C"

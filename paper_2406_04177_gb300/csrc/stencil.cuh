@@ -176,26 +176,34 @@ __device__ __forceinline__ float ld_state(const float *p) {
 }
 
 template <int PREC, int LP>
-__device__ __forceinline__ V vload_path(const float *__restrict__ H, const uint16_t *__restrict__ L, int64_t i) {
+__device__ __forceinline__ V vload_path(const float *__restrict__ H, const res_t *__restrict__ L, int64_t i) {
     if (LP == LD_NC) return vload<PREC>(H, L, i);
     V v;
     v.h = __ldcg(H + i);
-    v.l = (PREC == P_COMP) ? bf16_bits_to_float(__ldcg(L + i)) : 0.0f;
+    v.l = (PREC == P_COMP) ? res_decode(__ldcg(L + i), v.h) : 0.0f;
     return v;
 }
 
 // One node of a table-driven pass: MODE 1 diffuses the stored transformed DOM (Scheme 1) and
-// transforms the result; MODE 2 only diffuses.  Neighbours come from the offset table; the +-x
+// transforms the result; MODE 2 only diffuses.  TF 1 reads the compact z offsets (NbrTable.tz).
+// Neighbours come from the offset table; the +-x
 // neighbours' values from the adjacent lanes (consecutive nodes) by warp shuffles.  Arithmetic and
 // slot order as k_stencil.  Must be called by all 32 lanes of a warp (live = node exists).
-template <int MODE, int WM, int TR, int PREC, int LP>
+template <int MODE, int WM, int TR, int PREC, int LP, int TF = 0>
 __device__ __forceinline__ void table_node(uint32_t i, bool live, const NbrTable &tb, const BlockTable &bt,
                                            const StepParams &p, const StateIO &io) {
     const uint32_t bn = (WM == W_BLOCK && live) ? __ldg(bt.node + i) : 0u;
     const float *__restrict__ Y2 = io.in[1];
     const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
-    const uint32_t dzm = live ? __ldg(tb.tzm + i) : 0u;
-    const uint32_t dzp = live ? __ldg(tb.tzp + i) : 0u;
+    uint32_t dzm, dzp;
+    if (TF == 1) {  // compact z offsets
+        const uint32_t tz = live ? __ldg(tb.tz + i) : 0u;
+        dzm = tz & 0xffffu;
+        dzp = tz >> 16;
+    } else {
+        dzm = live ? __ldg(tb.tzm + i) : 0u;
+        dzp = live ? __ldg(tb.tzp + i) : 0u;
+    }
     V x2 = live ? vload_path<PREC, LP>(Y2, io.lin[1], i) : V{0.0f, 0.0f};
     const float yi = x2.h;
     const int lane = threadIdx.x & 31;

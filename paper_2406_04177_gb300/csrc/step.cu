@@ -101,8 +101,8 @@ struct StagedLayout {
     static constexpr int kPer = CAP / NT;
     static constexpr size_t bar = 0;
     static constexpr size_t h = 16;                                 // 5 x CAP floats
-    static constexpr size_t l = h + sizeof(float) * 5 * CAP;        // 5 x CAP u16
-    static constexpr size_t dec = l + sizeof(uint16_t) * 5 * CAP;   // decode words
+    static constexpr size_t l = h + sizeof(float) * 5 * CAP;        // 5 x CAP residuals
+    static constexpr size_t dec = l + sizeof(res_t) * 5 * CAP;      // decode words
     static constexpr size_t bytes(bool need_yz) { return dec + sizeof(uint32_t) * CAP * decode_words(need_yz); }
 };
 
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(NT) k_stencil_staged(Topo t, const int32_t *__
     extern __shared__ __align__(16) unsigned char sbuf[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sbuf + Ly::bar);
     float *sh = reinterpret_cast<float *>(sbuf + Ly::h);
-    uint16_t *sl = reinterpret_cast<uint16_t *>(sbuf + Ly::l);
+    res_t *sl = reinterpret_cast<res_t *>(sbuf + Ly::l);
     uint32_t *s_info = reinterpret_cast<uint32_t *>(sbuf + Ly::dec);
     int32_t *s_nb = reinterpret_cast<int32_t *>(s_info + CAP);
     uint32_t *s_yz = s_info + 5 * CAP;
@@ -121,18 +121,18 @@ __global__ void __launch_bounds__(NT) k_stencil_staged(Topo t, const int32_t *__
 
     const int64_t v0 = (int64_t)blockIdx.x * CAP;
     const int32_t nv = (int32_t)min((int64_t)CAP, t.n - v0);
-    const uint32_t nvp = (uint32_t)((nv + 7) & ~7);  // 16-byte multiples; the extra entries are padding
+    const uint32_t nvp = (uint32_t)((nv + 15) & ~15);  // 16-byte multiples; the extra entries are padding
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t per = nvp * 4u + (PREC == P_COMP ? nvp * 2u : 0u);
+        const uint32_t per = nvp * 4u + (PREC == P_COMP ? nvp * (uint32_t)sizeof(res_t) : 0u);
         mbar_arrive_expect_tx(bar, per * (uint32_t)(c1 - c0));
         for (int c = c0; c < c1; ++c) {
             bulk_g2s(sh + c * CAP, io.in[c] + v0, nvp * 4u, bar);
-            if (PREC == P_COMP) bulk_g2s(sl + c * CAP, io.lin[c] + v0, nvp * 2u, bar);
+            if (PREC == P_COMP) bulk_g2s(sl + c * CAP, io.lin[c] + v0, nvp * (uint32_t)sizeof(res_t), bar);
         }
     }
     int64_t v0d;
@@ -173,14 +173,15 @@ __global__ void __launch_bounds__(NT) k_stencil_staged(Topo t, const int32_t *__
         for (int u = 0; u < Ly::kPer; ++u) {
             const int32_t k = threadIdx.x + u * NT;
             if (k >= nv) continue;
-            V x2 = {sh2[k], PREC == P_COMP ? bf16_bits_to_float(sl[CAP + k]) : 0.0f};
+            V x2 = {sh2[k], PREC == P_COMP ? res_decode(sl[CAP + k], sh2[k]) : 0.0f};
             vadd<PREC>(x2, __fmul_rn(-p.c, acc[u]));
             V xs[5];
             if (MODE == 1) {
                 vround<PREC>(x2);
 #pragma unroll
                 for (int c = 0; c < 5; ++c)
-                    if (c != 1) xs[c] = V{sh[c * CAP + k], PREC == P_COMP ? bf16_bits_to_float(sl[c * CAP + k]) : 0.0f};
+                    if (c != 1)
+                        xs[c] = V{sh[c * CAP + k], PREC == P_COMP ? res_decode(sl[c * CAP + k], sh[c * CAP + k]) : 0.0f};
                 xs[1] = x2;
                 transform_n<TR, PREC>(xs[0], xs[1], xs[2], xs[3], xs[4], p);
             } else {
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(NT) k_stencil_staged(Topo t, const int32_t *__
                     const float s = __fadd_rn(xs[c].h, xs[c].l);  // renormalise as vstore does
                     const float r = __fadd_rn(__fsub_rn(xs[c].h, s), xs[c].l);
                     sh[c * CAP + k] = s;
-                    sl[c * CAP + k] = float_to_bf16_bits(r);
+                    sl[c * CAP + k] = res_encode(r, s);
                 } else {
                     sh[c * CAP + k] = xs[c].h;
                 }
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(NT) k_stencil_staged(Topo t, const int32_t *__
     if (threadIdx.x == 0 && ok) {
         for (int c = c0; c < c1; ++c) {
             bulk_s2g(io.out[c] + v0, sh + c * CAP, nvp * 4u);
-            if (PREC == P_COMP) bulk_s2g(io.lout[c] + v0, sl + c * CAP, nvp * 2u);
+            if (PREC == P_COMP) bulk_s2g(io.lout[c] + v0, sl + c * CAP, nvp * (uint32_t)sizeof(res_t));
         }
         bulk_commit();
         bulk_wait_read_all();
@@ -263,11 +264,27 @@ __global__ void k_build_bface(BlockWeights bw, int32_t *__restrict__ face) {
 }
 
 // One node per thread, neighbours from the offset table (table_node).
-template <int MODE, int WM, int TR, int PREC>
+template <int MODE, int WM, int TR, int PREC, int TF>
 __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                             StateIO io) {
     const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
-    table_node<MODE, WM, TR, PREC, LD_NC>(i, i < (uint64_t)n, tb, bt, p, io);
+    table_node<MODE, WM, TR, PREC, LD_NC, TF>(i, i < (uint64_t)n, tb, bt, p, io);
+}
+
+// Largest z offset of the table (for the compact form).
+__global__ void k_table_zmax(int64_t n, const uint32_t *__restrict__ tzm, const uint32_t *__restrict__ tzp,
+                             unsigned int *__restrict__ out) {
+    uint32_t m = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = max(m, max(__ldg(tzm + i), __ldg(tzp + i)));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+__global__ void k_table_pack_z(int64_t n, const uint32_t *__restrict__ tzm, const uint32_t *__restrict__ tzp,
+                               uint32_t *__restrict__ tz) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) tz[i] = tzm[i] | (tzp[i] << 16);
 }
 
 // ---- FP64 totals ---------------------------------------------------------------------------
@@ -297,7 +314,7 @@ __global__ void __launch_bounds__(kThreads) k_totals_final(const double *__restr
 }
 
 // ---- conversions ---------------------------------------------------------------------------
-// FP64 (5 x n) -> state: h = RN(x), l = the rounding error (BF16)
+// FP64 (5 x n) -> state: h = RN(x), l = the rounding error (quantised residual)
 __global__ void k_convert_in(int64_t n, const double *__restrict__ x, StateIO io, int comp) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -306,7 +323,7 @@ __global__ void k_convert_in(int64_t n, const double *__restrict__ x, StateIO io
         const double v = x[c * n + i];
         const float h = (float)v;
         io.out[c][i] = h;
-        if (comp) io.lout[c][i] = float_to_bf16_bits((float)(v - (double)h));
+        if (comp) io.lout[c][i] = res_encode((float)(v - (double)h), h);
     }
 }
 
@@ -315,8 +332,9 @@ __global__ void k_convert_out(int64_t n, double *__restrict__ x, StateIO io, int
     if (i >= n) return;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
-        double v = (double)io.in[c][i];
-        if (comp) v += (double)bf16_bits_to_float(io.lin[c][i]);
+        const float h = io.in[c][i];
+        double v = (double)h;
+        if (comp) v += (double)res_decode(io.lin[c][i], h);
         x[c * n + i] = v;
     }
 }
@@ -331,11 +349,28 @@ __global__ void k_pack(int64_t n, float *__restrict__ x, StateIO io, int to_stat
             io.out[c][i] = x[c * n + i];
             if (comp) io.lout[c][i] = 0;
         } else {
-            double v = (double)io.in[c][i];
-            if (comp) v += (double)bf16_bits_to_float(io.lin[c][i]);
+            const float h = io.in[c][i];
+            double v = (double)h;
+            if (comp) v += (double)res_decode(io.lin[c][i], h);
             x[c * n + i] = (float)v;
         }
     }
+}
+
+// Checkpoint residuals: stored residual <-> the BF16 bits of its value (the identity for the
+// current BF16 storage, kept so that the checkpoint format does not depend on it).
+__global__ void k_res_export(int64_t n, StateIO io, uint16_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c * n + i] = float_to_bf16_bits(res_decode(io.lin[c][i], io.in[c][i]));
+}
+
+__global__ void k_res_import(int64_t n, const uint16_t *__restrict__ in, StateIO io) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) io.lout[c][i] = res_encode(bf16_bits_to_float(in[c * n + i]), io.out[c][i]);
 }
 
 inline unsigned grid_for(int64_t count, int threads) { return (unsigned)((count + threads - 1) / threads); }
@@ -372,8 +407,13 @@ void launch_staged_any(vga_sim *s, const StateIO &io) {
 template <int MODE, int WM, int PREC>
 vga_status launch_table(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
     const unsigned grid = grid_for(s->n, kThreads);
-    if (s->sp.transform == 0) k_stencil_table<MODE, WM, 0, PREC><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
-    else k_stencil_table<MODE, WM, 1, PREC><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
+    if (tb.tz) {
+        if (s->sp.transform == 0) k_stencil_table<MODE, WM, 0, PREC, 1><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
+        else k_stencil_table<MODE, WM, 1, PREC, 1><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
+    } else {
+        if (s->sp.transform == 0) k_stencil_table<MODE, WM, 0, PREC, 0><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
+        else k_stencil_table<MODE, WM, 1, PREC, 0><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
+    }
     return VGA_OK;
 }
 
@@ -585,6 +625,22 @@ vga_status sim_pack_f32(vga_sim *s, float *d_x, bool to_state) {
 
 int totals_blocks() { return kTotBlocks; }
 
+vga_status sim_res_export(vga_sim *s, uint16_t *d_out) {
+    if (s->n == 0) return VGA_OK;
+    k_res_export<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, state_io_inplace(s), d_out);
+    VGA_CHECK_LAUNCH();
+    ++s->launches;
+    return VGA_OK;
+}
+
+vga_status sim_res_import(vga_sim *s, const uint16_t *d_in) {
+    if (s->n == 0) return VGA_OK;
+    k_res_import<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, d_in, state_io_inplace(s));
+    VGA_CHECK_LAUNCH();
+    ++s->launches;
+    return VGA_OK;
+}
+
 vga_status build_nbr_table(const Topo &t, uint32_t *ty, uint32_t *tzm, uint32_t *tzp, cudaStream_t st) {
     if (t.n == 0) return VGA_OK;
     Chunks ch;
@@ -647,6 +703,31 @@ vga_status sim_nbr_table(vga_sim *s, NbrTable *out) {
     out->ty = s->nbr_table;
     out->tzm = s->nbr_table + s->npad;
     out->tzp = s->nbr_table + 2 * s->npad;
+    if (s->nbr_tz_state == 0 && s->n > 0) {
+        unsigned int *d_max = nullptr;
+        VGA_TRY(dmalloc((void **)&d_max, sizeof(unsigned int), "table maximum"));
+        unsigned int h_max = 0;
+        cudaError_t e = cudaMemsetAsync(d_max, 0, sizeof(unsigned int), s->stream);
+        if (e == cudaSuccess) {
+            const unsigned g = (unsigned)std::min<int64_t>(grid_for(s->n, kThreads), 4096);
+            k_table_zmax<<<g, kThreads, 0, s->stream>>>(s->n, out->tzm, out->tzp, d_max);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_max, d_max, sizeof(h_max), cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        dfree(d_max);
+        if (e != cudaSuccess) return cuda_fail(e, "table z offsets", __FILE__, __LINE__);
+        s->nbr_tz_state = 2;
+        if (h_max < 65536u) {
+            VGA_TRY(dmalloc((void **)&s->nbr_tz, sizeof(uint32_t) * (size_t)std::max<int64_t>(s->npad, 64),
+                            "compact neighbour table"));
+            k_table_pack_z<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, out->tzm, out->tzp, s->nbr_tz);
+            VGA_CHECK_LAUNCH();
+            s->nbr_tz_state = 1;
+        }
+        s->launches += 2;
+    }
+    out->tz = s->nbr_tz_state == 1 ? s->nbr_tz : nullptr;
     return VGA_OK;
 }
 

@@ -17,6 +17,10 @@ namespace vga {
 void set_error(const std::string &msg);
 vga_status fail(vga_status s, const std::string &msg);
 vga_status cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+// Status of the release calls (cudaFree, cudaFreeHost, event and stream destruction) made since the
+// last check: reads and clears the runtime's error state, so a failed release is reported by the
+// *_free call that made it and never surfaces in a later, unrelated call.
+vga_status release_status(const char *what);
 
 #define VGA_CUDA(call)                                                         \
     do {                                                                       \
@@ -65,6 +69,9 @@ struct Chunks {
 // The -x / +x neighbours are i - 1 / i + 1.  Requires nx <= 32767 (y offsets are below nx).
 struct NbrTable {
     const uint32_t *ty = nullptr, *tzm = nullptr, *tzp = nullptr;
+    // Compact form of the z offsets, present when every one is below 2^16: tz[i] = tzm | tzp << 16
+    // (8 bytes per node with ty instead of 12).
+    const uint32_t *tz = nullptr;
 };
 
 // Block conductances in table form.  node[i] = block id (bits 0..25) | bit 26+d set when the edge
@@ -92,12 +99,15 @@ struct StepParams {
     int ntrans;   // transformations applied per pass (1; 0 or more when the steps differ)
 };
 
+// Stored residual of a compensated value: the BF16 bits of its value (physics.cuh).
+typedef uint16_t res_t;
+
 // Input and output compartment arrays of one pass over the state.
 struct StateIO {
-    const float *in[5];      // FP32 values
+    const float *in[5];   // FP32 values
     float *out[5];
-    const uint16_t *lin[5];  // BF16 residuals (compensated precision only)
-    uint16_t *lout[5];
+    const res_t *lin[5];  // residuals (compensated precision only)
+    res_t *lout[5];
 };
 
 // Edge-weight modes of the stencil.
@@ -163,7 +173,7 @@ struct vga_sim {
     int64_t n = 0;
     int64_t npad = 0;         // row stride of the state arrays (multiple of 64 floats)
     float *buf[2] = {nullptr, nullptr};     // two state buffers of 5*npad FP32 values
-    uint16_t *lbuf[2] = {nullptr, nullptr}; // their BF16 residuals (compensated precision)
+    vga::res_t *lbuf[2] = {nullptr, nullptr};  // their residuals (compensated precision)
     int cur[5] = {0, 0, 0, 0, 0};           // which buffer holds compartment c
     vga::Chunks chunks;
     // conductances
@@ -184,6 +194,7 @@ struct vga_sim {
     int64_t cg_count = 0;
     double *cg_scalars = nullptr;  // device scalars of the PCG recurrence
     double *h_cg = nullptr;        // pinned mirror of the PCG scalars
+    bool cg_mixed = true;          // implicit solve: FP64 refinement around FP32 PCG (unit conductances)
     int64_t steps_done = 0;
     int64_t cg_iterations = 0;
     double cg_last_relres = 0.0;
@@ -212,6 +223,8 @@ struct vga_sim {
     int wave_built_chunk = 0, wave_built_depth = 0, wave_built_lag = -1;
     int32_t wave_reach = 0;
     uint32_t *nbr_table = nullptr;  // 3 x npad words (NbrTable), built on first use
+    uint32_t *nbr_tz = nullptr;     // compact z offsets (NbrTable.tz) when they fit in 16 bits
+    int nbr_tz_state = 0;           // 0 not examined, 1 built, 2 offsets too large
     uint32_t *bnode = nullptr;      // BlockTable.node (npad), built for the current block side
     int32_t *bface = nullptr;       // BlockTable.face (6 x blocks)
     int32_t btable_bs = 0;          // block side the block table was built for (0: none)
@@ -221,8 +234,8 @@ struct vga_sim {
 
     float *comp(int c) { return buf[cur[c]] + (size_t)c * npad; }
     float *spare(int c) { return buf[1 - cur[c]] + (size_t)c * npad; }
-    uint16_t *lcomp(int c) { return lbuf[cur[c]] + (size_t)c * npad; }
-    uint16_t *lspare(int c) { return lbuf[1 - cur[c]] + (size_t)c * npad; }
+    vga::res_t *lcomp(int c) { return lbuf[cur[c]] + (size_t)c * npad; }
+    vga::res_t *lspare(int c) { return lbuf[1 - cur[c]] + (size_t)c * npad; }
     int precision() const { return params.state_precision; }
     // transformation and diffusion on different steps (global clock of vga_params.dt_transform)
     bool subcycled() const { return params.dt_transform > 0.0 && params.dt_transform != params.dt; }
@@ -240,6 +253,9 @@ vga_status sim_totals(vga_sim *s, double *h_out);
 vga_status sim_convert_in(vga_sim *s, const double *d_x);    // device FP64 (5 x n) -> state
 vga_status sim_convert_out(vga_sim *s, double *d_x);         // state -> device FP64 (5 x n)
 vga_status sim_pack_f32(vga_sim *s, float *d_x, bool to_state);
+// Residuals of the current state as / from BF16 bits (5 x n, device), the checkpoint format.
+vga_status sim_res_export(vga_sim *s, uint16_t *d_out);
+vga_status sim_res_import(vga_sim *s, const uint16_t *d_in);
 vga_status sim_transform_pass(vga_sim *s);  // Y = T(X) for every node, all compartments swapped
 int64_t sim_ticks_before(const vga_sim *s, int64_t k);  // transformations in the first k steps
 int sim_ticks_of_step(const vga_sim *s, int64_t k);      // transformations before diffusion step k

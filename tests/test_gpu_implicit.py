@@ -71,3 +71,37 @@ def test_zero_dom(vga):
     sim.set_masses(X)
     sim.step(3)
     assert np.isfinite(sim.get_masses()).all()
+
+
+@pytest.mark.parametrize("rtol", [1e-6, 1e-8, 1e-10])
+def test_mixed_refinement_matches_fp64_pcg(vga, oracle_lib, rtol):
+    """The default implicit solver (FP64 refinement around FP32 PCG) and the FP64 PCG both land
+    within the requested tolerance of the oracle's solution; the mixed solver's reported residual
+    is the true one, so it is at most rtol."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (40, 40, 40), 0.2, 7)
+    p = synth.paper_params(dt=10 * 0.9 / (6 * synth.D_DOM), scheme=1, cg_rtol=rtol, cg_maxit=2000)
+    ref, status, _, _ = oracle_lib.implicit_run(og.nbr, p, X0, 5, rtol=1e-13)
+    assert status == 0
+    out = {}
+    for solver in (vga.VGA_SOLVER_MIXED_REFINEMENT, vga.VGA_SOLVER_FP64_PCG):
+        sim = vga.Sim(g, p)
+        sim.set_solver(solver)
+        sim.set_masses(X0)
+        sim.step(5)
+        out[solver] = sim.get_masses()
+        st = sim.stats()
+        if solver == vga.VGA_SOLVER_MIXED_REFINEMENT:
+            assert st["cg_last_relres"] <= rtol
+        # a solve stops within rtol of the exact one; 5 steps accumulate at most ~5 rtol (x cond)
+        assert rel_l2(out[solver][1], ref[1]) <= max(100 * rtol, 2e-7), (solver, rel_l2(out[solver][1], ref[1]))
+        # B conserves mass exactly, so a solve stopped at rtol conserves it to about rtol
+        assert abs(sim.totals().sum() - X0.sum()) <= max(1e-7, 10 * rtol) * X0.sum()
+    for c in (0, 2, 3, 4):  # compartments the solve does not touch agree closely
+        assert rel_l2(out[0][c], out[1][c]) <= 1e-6
+
+
+def test_unknown_solver_rejected(vga):
+    g = vga.Graph(np.zeros((4, 4, 4), dtype=np.uint8))
+    sim = vga.Sim(g, synth.paper_params(scheme=1))
+    with pytest.raises(vga.VgaError):
+        sim.set_solver(7)

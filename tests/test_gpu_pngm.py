@@ -183,3 +183,25 @@ def test_invalid_partitions(vga, oracle_lib):
     assert e.value.name == "VGA_ERR_INVALID_ARG"
     one = vga.Pngm(g, np.zeros(g.n, dtype=np.int32), 1)  # one primitive: no pairs
     assert one.info()["n_slots"] == 0
+
+
+def test_buffers_survive_pair_growth_and_close_cleanly(vga, oracle_lib):
+    """Growing the pair buffer (more than 64 pairs) between two restrictions leaves the restriction
+    scratch intact, and every release call of the handles succeeds (close() reports a failed free)."""
+    torch = _torch()
+    img, og, g, lab, q, cg, pg = _case(vga, oracle_lib, shape=(24, 24, 24), bs=8)
+    X0 = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), 5)
+    sim = vga.Sim(g, synth.paper_params())
+    sim.set_masses(X0)
+    out = torch.empty(q, dtype=torch.float64, device="cuda")
+    pg.restrict(sim, 1, out)
+    data = torch.rand((200, q), dtype=torch.float64, device="cuda")
+    pairs = np.stack([np.arange(100), np.arange(100, 200)], axis=1).astype(np.int32)
+    pg.objective(1, data, pairs, 1.0, 1e-3)
+    sim.step(3)
+    pg.restrict(sim, 1, out)
+    ref = opn.restrict(lab, q, sim.get_masses()[1])
+    assert np.allclose(out.cpu().numpy(), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+    pg.close()
+    sim.close()
+    g.close()
