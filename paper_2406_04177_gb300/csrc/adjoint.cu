@@ -232,24 +232,46 @@ __global__ void __launch_bounds__(kThreads) k_fused_rec_table(int64_t n, NbrTabl
     rec.y2[i] = __fadd_rn(x2.h, x2.l);
 }
 
+// Compensated FP32 accumulator (TwoSum into a second float): GB300 issues FP64 at a small fraction of
+// its FP32 rate, and a per-thread sum of ~100 terms carried this way keeps ~45 significant bits.
+struct CAcc {
+    float s = 0.0f, c = 0.0f;
+};
+
+__device__ __forceinline__ void cacc_add(CAcc &a, float x) {
+    const float t = __fadd_rn(a.s, x);
+    const float bp = __fsub_rn(t, a.s);
+    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(x, bp));
+    a.s = t;
+    a.c = __fadd_rn(a.c, err);
+}
+
+// x * y added exactly (TwoProd by FMA: the product's rounding error is a second float).
+__device__ __forceinline__ void cacc_add_prod(CAcc &a, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float e = __fmaf_rn(x, y, -p);
+    cacc_add(a, p);
+    a.c = __fadd_rn(a.c, e);
+}
+
 // Adds v to gtheta[f] for every lane with f >= 0, combining lanes of the warp that hit the same
-// face first (neighbouring nodes on one block face share it) so that one atomic per face and warp
-// reaches memory.  Must be called by all 32 lanes.
-__device__ __forceinline__ void face_atomic_add(double *gtheta, int32_t f, double v) {
+// face first in FP32 (neighbouring nodes on one block face share it) so that one FP64 atomic per
+// face and warp reaches memory.  Must be called by all 32 lanes.
+__device__ __forceinline__ void face_atomic_add_f(double *gtheta, int32_t f, float v) {
     const unsigned act = __ballot_sync(0xffffffffu, f >= 0);
     if (!act) return;
     const int lane = threadIdx.x & 31;
     const unsigned peers = __match_any_sync(0xffffffffu, f);
     const bool leader = (f >= 0) && (lane == __ffs(peers) - 1);
-    double sum = v;
+    float sum = v;
     unsigned rest = act;
     while (rest) {
         const int src = __ffs(rest) - 1;
         rest &= rest - 1;
-        const double t = __shfl_sync(0xffffffffu, v, src);
-        if (leader && src != lane && ((peers >> src) & 1u)) sum += t;
+        const float t = __shfl_sync(0xffffffffu, v, src);
+        if (leader && src != lane && ((peers >> src) & 1u)) sum = __fadd_rn(sum, t);
     }
-    if (leader) atomicAdd(gtheta + f, sum);
+    if (leader) atomicAdd(gtheta + f, (double)sum);
 }
 
 // Table-driven reverse step (same arithmetic as k_adjoint_step), grid-stride over 256-node tiles.
@@ -259,10 +281,8 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_table(int64_t n, NbrTable 
                                                             const float *__restrict__ y2k, double *__restrict__ gpart,
                                                             double *__restrict__ gtheta) {
     const float *__restrict__ L2 = io.in[1];
-    double acc[kPar];
-#pragma unroll
-    for (int q = 0; q < kPar; ++q) acc[q] = 0.0;
-    const double mc = -(double)p.c;
+    CAcc acc[kPar];  // compensated FP32 per thread, reduced in FP64 per block
+    const float mc = -p.c;
     const int64_t ntile = (n + kThreads - 1) / kThreads;
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
@@ -277,7 +297,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_table(int64_t n, NbrTable 
         const uint32_t bn = (WM == W_BLOCK && live) ? __ldg(bt.node + i) : 0u;
         float lsum = 0.0f, ysum = 0.0f;
         int32_t face[3] = {-1, -1, -1};
-        double fval[3] = {0.0, 0.0, 0.0};
+        float fval[3] = {0.0f, 0.0f, 0.0f};
         if (live) {
 #pragma unroll
             for (int d = 0; d < 6; ++d) {
@@ -289,16 +309,16 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_table(int64_t n, NbrTable 
                 ysum = __fmaf_rn(g, dy, ysum);
                 if (WM == W_BLOCK && (d & 1)) {  // +x, +y, +z: each edge once
                     face[d >> 1] = table_face(bt, bn, d);
-                    fval[d >> 1] = mc * (double)dy * (double)dl;
+                    fval[d >> 1] = __fmul_rn(__fmul_rn(mc, dy), dl);
                 }
             }
         }
         if (WM == W_BLOCK) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) face_atomic_add(gtheta, face[q], fval[q]);
+            for (int q = 0; q < 3; ++q) face_atomic_add_f(gtheta, face[q], fval[q]);
         }
         if (!live) continue;
-        acc[GR_COUNT] -= (double)li * (double)ysum;
+        cacc_add_prod(acc[GR_COUNT], -li, ysum);
         vadd<PREC>(mu[1], __fmul_rn(-p.c, lsum));
         float xs[5];
 #pragma unroll
@@ -309,12 +329,15 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_table(int64_t n, NbrTable 
         V lam[5];
         transform_sync_reverse<PREC>(xs, mu, lam, gr, p);
 #pragma unroll
-        for (int q = 0; q < GR_COUNT; ++q) acc[q] += (double)gr[q];
+        for (int q = 0; q < GR_COUNT; ++q) cacc_add(acc[q], gr[q]);
 #pragma unroll
         for (int c = 0; c < 5; ++c) vstore<PREC>(io.out[c], io.lout[c], i, lam[c]);
     }
+    double accd[kPar];
+#pragma unroll
+    for (int q = 0; q < kPar; ++q) accd[q] = (double)acc[q].s + (double)acc[q].c;
     __shared__ double out[kPar];
-    block_sum_store<kPar>(acc, out);
+    block_sum_store<kPar>(accd, out);
     if (threadIdx.x < kPar) gpart[(int64_t)blockIdx.x * kPar + threadIdx.x] += out[threadIdx.x];
 }
 
