@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (for profiler runs)")
     ap.add_argument("--extras", default="graph_build,implicit,adjoint,batched,pngm",
                     help="comma-separated subset of the extra measurements to run")
+    ap.add_argument("--adj-steps", type=int, default=200, help="time steps of the adjoint measurement")
+    ap.add_argument("--adj-ckpt", type=int, default=100, help="checkpoint spacing of the adjoint measurement")
     ap.add_argument("--kernel", default=None,
                     help="fix the explicit kernel instead of autotuning: 'variant:chunk' or '3:chunk:depth:ctas'")
     return ap.parse_args()
@@ -342,7 +344,7 @@ def bench_ours(a):
         if "implicit" in want:
             extras["implicit"] = bench_implicit(vga, g, x0_dev, n, stream)
         if "adjoint" in want:
-            extras["adjoint"] = bench_adjoint(vga, g, params, x0_dev, n, stream)
+            extras["adjoint"] = bench_adjoint(vga, g, params, x0_dev, n, stream, a.adj_steps, a.adj_ckpt)
         if "batched" in want:
             extras["batched"] = bench_batched(vga, a)
         if "pngm" in want:

@@ -276,7 +276,7 @@ __device__ __forceinline__ void face_atomic_add_f(double *gtheta, int32_t f, flo
 
 // Table-driven reverse step (same arithmetic as k_adjoint_step), grid-stride over 256-node tiles.
 template <int WM, int PREC>
-__global__ void __launch_bounds__(kThreads) k_adjoint_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+__global__ void __launch_bounds__(kThreads, 5) k_adjoint_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                             StateIO io, int64_t npad, const float *__restrict__ xk,
                                                             const float *__restrict__ y2k, double *__restrict__ gpart,
                                                             double *__restrict__ gtheta) {
