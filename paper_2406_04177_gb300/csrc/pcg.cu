@@ -379,7 +379,8 @@ struct MxVecs {
 };
 
 template <int TF>
-__device__ __forceinline__ float nbr_sum_f(const NbrTable &tb, uint32_t i, bool live, float vi, const float *v) {
+__device__ __forceinline__ float nbr_sum_f(const NbrTable &tb, uint32_t i, bool live, float vi,
+                                           const float *__restrict__ v) {
     const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
     uint32_t dzm, dzp;
     if (TF == 1) {  // compact z offsets
@@ -500,15 +501,18 @@ __global__ void __launch_bounds__(kThreads) k_mx_spmv(int64_t n, NbrTable tb, fl
                                                       double *__restrict__ part, const MxScalars *__restrict__ sc) {
     if (sc->inner_done) return;
     float acc = 0.0f;
+    const float *__restrict__ p = v.p;
+    float *__restrict__ q = v.q;
     const int64_t ntile = (n + kThreads - 1) / kThreads;
+#pragma unroll 2
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
         const bool live = i < (uint64_t)n;
-        const float pi = live ? v.p[i] : 0.0f;
-        const float lp = nbr_sum_f<TF>(tb, i, live, pi, v.p);
+        const float pi = live ? __ldg(p + i) : 0.0f;
+        const float lp = nbr_sum_f<TF>(tb, i, live, pi, p);
         if (live) {
             const float qi = pi + c * lp;
-            v.q[i] = qi;
+            q[i] = qi;
             acc += pi * qi;
         }
     }
@@ -524,12 +528,38 @@ __global__ void __launch_bounds__(kThreads) k_mx_scal_a(const double *__restrict
     if (threadIdx.x == 0) sc->alpha = pq > 0.0 ? sc->rz / pq : 0.0;
 }
 
+// The streaming kernels below move four nodes per thread and access (16-byte vectors: every FP32
+// array starts on a 16-byte boundary); the n % 4 last nodes go through a scalar tail, so the padding
+// after node n never enters a sum.
 __global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, MxVecs v, const MxScalars *__restrict__ sc,
                                                      double *__restrict__ part) {
     if (sc->inner_done) return;
     const float alpha = (float)sc->alpha;
     float a0 = 0.0f, a1 = 0.0f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n4 = n >> 2;
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    float4 *__restrict__ d4 = reinterpret_cast<float4 *>(v.d);
+    float4 *__restrict__ r4 = reinterpret_cast<float4 *>(v.r);
+    const float4 *__restrict__ p4 = reinterpret_cast<const float4 *>(v.p);
+    const float4 *__restrict__ q4 = reinterpret_cast<const float4 *>(v.q);
+    const float4 *__restrict__ t4 = reinterpret_cast<const float4 *>(v.t);
+    for (int64_t k = g0; k < n4; k += gs) {
+        float4 d = d4[k], r = r4[k];
+        const float4 p = p4[k], q = q4[k], t = t4[k];
+        d.x += alpha * p.x;
+        d.y += alpha * p.y;
+        d.z += alpha * p.z;
+        d.w += alpha * p.w;
+        r.x -= alpha * q.x;
+        r.y -= alpha * q.y;
+        r.z -= alpha * q.z;
+        r.w -= alpha * q.w;
+        d4[k] = d;
+        r4[k] = r;
+        a0 += r.x * (t.x * r.x) + r.y * (t.y * r.y) + r.z * (t.z * r.z) + r.w * (t.w * r.w);
+        a1 += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
+    }
+    for (int64_t i = 4 * n4 + g0; i < n; i += gs) {
         v.d[i] += alpha * v.p[i];
         const float ri = v.r[i] - alpha * v.q[i];
         v.r[i] = ri;
@@ -563,14 +593,37 @@ __global__ void __launch_bounds__(kThreads) k_mx_scal_b(const double *__restrict
 __global__ void __launch_bounds__(kThreads) k_mx_p(int64_t n, MxVecs v, const MxScalars *__restrict__ sc) {
     if (sc->inner_done) return;
     const float beta = (float)sc->beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v.p[i] = v.t[i] * v.r[i] + beta * v.p[i];
+    const int64_t n4 = n >> 2;
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    float4 *__restrict__ p4 = reinterpret_cast<float4 *>(v.p);
+    const float4 *__restrict__ r4 = reinterpret_cast<const float4 *>(v.r);
+    const float4 *__restrict__ t4 = reinterpret_cast<const float4 *>(v.t);
+    for (int64_t k = g0; k < n4; k += gs) {
+        float4 p = p4[k];
+        const float4 r = r4[k], t = t4[k];
+        p.x = t.x * r.x + beta * p.x;
+        p.y = t.y * r.y + beta * p.y;
+        p.z = t.z * r.z + beta * p.z;
+        p.w = t.w * r.w + beta * p.w;
+        p4[k] = p;
+    }
+    for (int64_t i = 4 * n4 + g0; i < n; i += gs) v.p[i] = v.t[i] * v.r[i] + beta * v.p[i];
 }
 
 __global__ void __launch_bounds__(kThreads) k_mx_x(int64_t n, MxVecs v, const MxScalars *__restrict__ sc) {
     if (sc->done) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        v.x[i] += (double)v.d[i];
+    const int64_t n2 = n >> 1;
+    const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
+    double2 *__restrict__ x2 = reinterpret_cast<double2 *>(v.x);
+    const float2 *__restrict__ d2 = reinterpret_cast<const float2 *>(v.d);
+    for (int64_t k = g0; k < n2; k += gs) {
+        double2 x = x2[k];
+        const float2 d = d2[k];
+        x.x += (double)d.x;
+        x.y += (double)d.y;
+        x2[k] = x;
+    }
+    for (int64_t i = 2 * n2 + g0; i < n; i += gs) v.x[i] += (double)v.d[i];
 }
 
 template <int PREC>
