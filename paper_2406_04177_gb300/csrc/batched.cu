@@ -83,7 +83,7 @@ __device__ bool grid_barrier(unsigned *bar, int32_t *err) {
     return ok != 0;
 }
 
-template <int TR, int PREC>
+template <int TR, int PREC, int TF>
 __global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
     for (int32_t pass = pass0; pass < pass1; ++pass) {
         const int kind = (pass == 0) ? 0 : (pass == npass - 1 ? 2 : 1);  // transform / fused / diffuse
@@ -102,8 +102,15 @@ __global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int
                 transform<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
             } else {
                 const uint32_t ty = live ? __ldg(a.tb.ty + i) : 0u;
-                const uint32_t dzm = live ? __ldg(a.tb.tzm + i) : 0u;
-                const uint32_t dzp = live ? __ldg(a.tb.tzp + i) : 0u;
+                uint32_t dzm, dzp;
+                if (TF == 1) {  // compact z offsets
+                    const uint32_t tz = live ? __ldg(a.tb.tz + i) : 0u;
+                    dzm = tz & 0xffffu;
+                    dzp = tz >> 16;
+                } else {
+                    dzm = live ? __ldg(a.tb.tzm + i) : 0u;
+                    dzp = live ? __ldg(a.tb.tzp + i) : 0u;
+                }
                 x[1] = live ? vload<PREC>(Y2, a.l[bi] + a.npad, i) : V{0.0f, 0.0f};
                 const float yi = x[1].h;
                 const int lane = threadIdx.x & 31;
@@ -191,6 +198,7 @@ struct vga_batch {
     float *h[2] = {nullptr, nullptr};
     res_t *l[2] = {nullptr, nullptr};
     uint32_t *table = nullptr;  // 3 x npad
+    uint32_t *tz = nullptr;     // compact z offsets (npad) when they fit in 16 bits
     int32_t *tile_inst = nullptr;
     BInst *inst = nullptr;
     unsigned *bar = nullptr;
@@ -209,12 +217,28 @@ struct vga_batch {
 
 namespace {
 
+template <int TFV>
+const void *batch_kernel(const vga_batch *b) {
+    return b->transform == 0 ? (b->precision == P_COMP ? (const void *)k_batch<0, P_COMP, TFV> : (const void *)k_batch<0, P_F32, TFV>)
+                             : (b->precision == P_COMP ? (const void *)k_batch<1, P_COMP, TFV> : (const void *)k_batch<1, P_F32, TFV>);
+}
+
+template <int TFV>
+cudaError_t batch_launch_tf(const vga_batch *b, const cudaLaunchConfig_t &cfg, const BatchArgs &a, int32_t pass0,
+                            int32_t pass1, int32_t npass, int32_t cur0) {
+    if (b->transform == 0) {
+        if (b->precision == P_COMP) return cudaLaunchKernelEx(&cfg, k_batch<0, P_COMP, TFV>, a, pass0, pass1, npass, cur0);
+        return cudaLaunchKernelEx(&cfg, k_batch<0, P_F32, TFV>, a, pass0, pass1, npass, cur0);
+    }
+    if (b->precision == P_COMP) return cudaLaunchKernelEx(&cfg, k_batch<1, P_COMP, TFV>, a, pass0, pass1, npass, cur0);
+    return cudaLaunchKernelEx(&cfg, k_batch<1, P_F32, TFV>, a, pass0, pass1, npass, cur0);
+}
+
 vga_status batch_grid(vga_batch *b) {
     int dev = 0, sms = 0, per_sm = 0;
     VGA_CUDA(cudaGetDevice(&dev));
     VGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const void *fn = b->transform == 0 ? (b->precision == P_COMP ? (const void *)k_batch<0, P_COMP> : (const void *)k_batch<0, P_F32>)
-                                       : (b->precision == P_COMP ? (const void *)k_batch<1, P_COMP> : (const void *)k_batch<1, P_F32>);
+    const void *fn = b->tz ? batch_kernel<1>(b) : batch_kernel<0>(b);
     VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTile, 0));
     if (per_sm < 1) return fail(VGA_ERR_CUDA, "batched kernel cannot be resident");
     const int want = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, per_sm) : per_sm;
@@ -231,6 +255,7 @@ vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npas
     a.tb.ty = b->table;
     a.tb.tzm = b->table + b->npad;
     a.tb.tzp = b->table + 2 * b->npad;
+    a.tb.tz = b->tz;
     for (int k = 0; k < 2; ++k) {
         a.h[k] = b->h[k];
         a.l[k] = b->l[k];
@@ -247,14 +272,8 @@ vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npas
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e;
-    if (b->transform == 0) {
-        if (b->precision == P_COMP) e = cudaLaunchKernelEx(&cfg, k_batch<0, P_COMP>, a, pass0, pass1, npass, cur0);
-        else e = cudaLaunchKernelEx(&cfg, k_batch<0, P_F32>, a, pass0, pass1, npass, cur0);
-    } else {
-        if (b->precision == P_COMP) e = cudaLaunchKernelEx(&cfg, k_batch<1, P_COMP>, a, pass0, pass1, npass, cur0);
-        else e = cudaLaunchKernelEx(&cfg, k_batch<1, P_F32>, a, pass0, pass1, npass, cur0);
-    }
+    const cudaError_t e = b->tz ? batch_launch_tf<1>(b, cfg, a, pass0, pass1, npass, cur0)
+                                : batch_launch_tf<0>(b, cfg, a, pass0, pass1, npass, cur0);
     if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of k_batch", __FILE__, __LINE__);
     return VGA_OK;
 }
@@ -301,6 +320,7 @@ vga_status vga_batch_free(vga_batch *b) {
         dfree(b->l[k]);
     }
     dfree(b->table);
+    dfree(b->tz);
     dfree(b->tile_inst);
     dfree(b->inst);
     dfree(b->bar);
@@ -388,6 +408,8 @@ vga_status vga_batch_create(const vga_graph *const *graphs, const vga_params *pa
         st = build_nbr_table(graphs[k]->topo(), b->table + s0, b->table + b->npad + s0, b->table + 2 * b->npad + s0,
                              b->stream);
     }
+    // padding entries between instances are zero, so the compact form covers the whole range
+    if (st == VGA_OK) st = build_compact_z(b->npad, b->npad, b->table + b->npad, b->table + 2 * b->npad, &b->tz, b->stream);
     if (st == VGA_OK) st = batch_grid(b);
     if (st != VGA_OK) {
         vga_batch_free(b);

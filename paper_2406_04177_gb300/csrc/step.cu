@@ -704,30 +704,35 @@ vga_status sim_nbr_table(vga_sim *s, NbrTable *out) {
     out->tzm = s->nbr_table + s->npad;
     out->tzp = s->nbr_table + 2 * s->npad;
     if (s->nbr_tz_state == 0 && s->n > 0) {
-        unsigned int *d_max = nullptr;
-        VGA_TRY(dmalloc((void **)&d_max, sizeof(unsigned int), "table maximum"));
-        unsigned int h_max = 0;
-        cudaError_t e = cudaMemsetAsync(d_max, 0, sizeof(unsigned int), s->stream);
-        if (e == cudaSuccess) {
-            const unsigned g = (unsigned)std::min<int64_t>(grid_for(s->n, kThreads), 4096);
-            k_table_zmax<<<g, kThreads, 0, s->stream>>>(s->n, out->tzm, out->tzp, d_max);
-            e = cudaGetLastError();
-        }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&h_max, d_max, sizeof(h_max), cudaMemcpyDeviceToHost, s->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-        dfree(d_max);
-        if (e != cudaSuccess) return cuda_fail(e, "table z offsets", __FILE__, __LINE__);
-        s->nbr_tz_state = 2;
-        if (h_max < 65536u) {
-            VGA_TRY(dmalloc((void **)&s->nbr_tz, sizeof(uint32_t) * (size_t)std::max<int64_t>(s->npad, 64),
-                            "compact neighbour table"));
-            k_table_pack_z<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, out->tzm, out->tzp, s->nbr_tz);
-            VGA_CHECK_LAUNCH();
-            s->nbr_tz_state = 1;
-        }
+        VGA_TRY(build_compact_z(s->n, std::max<int64_t>(s->npad, 64), out->tzm, out->tzp, &s->nbr_tz, s->stream));
+        s->nbr_tz_state = s->nbr_tz ? 1 : 2;
         s->launches += 2;
     }
     out->tz = s->nbr_tz_state == 1 ? s->nbr_tz : nullptr;
+    return VGA_OK;
+}
+
+vga_status build_compact_z(int64_t n, int64_t cap, const uint32_t *tzm, const uint32_t *tzp, uint32_t **out,
+                           cudaStream_t st) {
+    *out = nullptr;
+    if (n <= 0) return VGA_OK;
+    unsigned int *d_max = nullptr;
+    VGA_TRY(dmalloc((void **)&d_max, sizeof(unsigned int), "table maximum"));
+    unsigned int h_max = 0;
+    cudaError_t e = cudaMemsetAsync(d_max, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) {
+        const unsigned g = (unsigned)std::min<int64_t>(grid_for(n, kThreads), 4096);
+        k_table_zmax<<<g, kThreads, 0, st>>>(n, tzm, tzp, d_max);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_max, d_max, sizeof(h_max), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dfree(d_max);
+    if (e != cudaSuccess) return cuda_fail(e, "table z offsets", __FILE__, __LINE__);
+    if (h_max >= 65536u) return VGA_OK;
+    VGA_TRY(dmalloc((void **)out, sizeof(uint32_t) * (size_t)cap, "compact neighbour table"));
+    k_table_pack_z<<<grid_for(n, kThreads), kThreads, 0, st>>>(n, tzm, tzp, *out);
+    VGA_CHECK_LAUNCH();
     return VGA_OK;
 }
 

@@ -269,6 +269,10 @@ vga_status sim_block_table(vga_sim *s, BlockTable *out, bool *ok);
 // Writes the neighbour-offset table of a node set (offsets are relative, so the arrays may start at
 // any node offset of a larger concatenated range).  Synchronises the stream.
 vga_status build_nbr_table(const Topo &t, uint32_t *ty, uint32_t *tzm, uint32_t *tzp, cudaStream_t st);
+// Compact z offsets (NbrTable.tz) of a table of n entries (allocating cap entries) when every z
+// offset is below 2^16; *out stays NULL otherwise.
+vga_status build_compact_z(int64_t n, int64_t cap, const uint32_t *tzm, const uint32_t *tzp, uint32_t **out,
+                           cudaStream_t st);
 StateIO state_io(vga_sim *s);          // current buffers in, spare buffers out
 StateIO state_io_inplace(vga_sim *s);  // current buffers in and out
 // pcg.cu

@@ -118,3 +118,98 @@ def test_adjoint_gradient_matches_finite_difference_512(vga, full):
     fd = (loss(p["D"] + h) - loss(p["D"] - h)) / (2 * h)
     assert np.isclose(loss(p["D"]), L0, rtol=1e-9)
     assert np.isclose(grad["D"], fd, rtol=2e-3), (grad["D"], fd)
+
+
+def test_config_256_ten_thousand_steps(vga, oracle_lib):
+    """The FP32-state forward configuration: 256^3 at 20% porosity, 10^4 explicit steps, relative L2
+    and total-mass drift against the FP64 oracle every 2000 steps."""
+    from tests.helpers import rel_l2
+
+    img = synth.pore_mask((256, 256, 256), 0.20, 7)
+    og = oracle_lib.graph_build(img, keep_largest=True)
+    g = vga.Graph(img)
+    X0 = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), 7)
+    p = synth.paper_params()
+    sim = vga.Sim(g, p)
+    sim.set_masses(X0)
+    sim.autotune(20)
+    ref = X0.copy()
+    for _ in range(5):
+        sim.step(2000)
+        ref = oracle_lib.explicit_run(og.nbr, p, ref, 2000)
+        got = sim.get_masses()
+        for c in range(5):
+            if np.abs(ref[c]).max() > 0:
+                assert rel_l2(got[c], ref[c]) <= 1e-5, c
+        assert abs(sim.totals().sum() - X0.sum()) <= 1e-7 * X0.sum()
+
+
+def test_config_batched_full(vga, oracle_lib):
+    """The batched configuration: 64 subvolumes (sides 64..192, porosity 10..35%, rates within
+    +-50%), 5000 steps in persistent launches; the three smallest instances against the FP64 oracle,
+    every instance's total mass conserved."""
+    from tests.helpers import rel_l2
+
+    specs = synth.batch_instances(64, 7)
+    graphs, params, masses, imgs = [], [], [], []
+    ogs = []
+    for sp in specs:
+        img = synth.pore_mask(sp["shape"], sp["porosity"], sp["mask_seed"])
+        og = oracle_lib.graph_build(img, keep_largest=True)  # inputs come from the oracle side only
+        graphs.append(vga.Graph(img))
+        params.append(sp["params"])
+        masses.append(synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), sp["mass_seed"]))
+        imgs.append(img)
+        ogs.append(og)
+    b = vga.Batch(graphs, params)
+    for k, X in enumerate(masses):
+        b.set_masses(k, X)
+    b.autotune(20)
+    b.step(5000)
+    smallest = np.argsort([gk.n for gk in graphs])[:3]
+    for k in range(64):
+        got = b.get_masses(k)
+        assert abs(got.sum() - masses[k].sum()) <= 1e-7 * masses[k].sum(), k
+        if k in smallest:
+            ref = oracle_lib.explicit_run(ogs[k].nbr, params[k], masses[k], 5000)
+            for c in range(5):
+                if np.abs(ref[c]).max() > 0:
+                    assert rel_l2(got[c], ref[c]) <= 1e-5, (k, c)
+
+
+def test_config_adjoint_128(vga, oracle_lib):
+    """The adjoint configuration: 128^3 at 17% porosity, 2000 explicit steps, loss = squared error of
+    the final 8^3-block DOM and CO2 masses against a seeded target run, 16^3 block-to-block
+    conductances, checkpoints every 100: gradients against the oracle's FP64 adjoint."""
+    import torch
+
+    from tests.helpers import rel_l2
+
+    img = synth.pore_mask((128, 128, 128), 0.17, 5)
+    og = oracle_lib.graph_build(img)
+    g = vga.Graph(img)
+    X0 = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), 5,
+                              with_organic_matter=True)
+    bs, N = 8, 2000
+    nb = oracle_lib.block_grid(img.shape, bs)
+    theta_star = synth.block_conductances(nb, 5)
+    p = synth.paper_params(dt=0.9 / (6 * synth.D_DOM * 1.5))
+    g6s = oracle_lib.block_face_weights(img.shape, bs, og.voxel_of_node, og.nbr, theta_star)
+    target = oracle_lib.block_masses(img.shape, bs, og.voxel_of_node, oracle_lib.explicit_run(og.nbr, p, X0, N, g6=g6s))
+    theta = np.ones(theta_star.size)
+    g6 = oracle_lib.block_face_weights(img.shape, bs, og.voxel_of_node, og.nbr, theta)
+    XN = oracle_lib.explicit_run(og.nbr, p, X0, N, g6=g6)
+    L_ref, lamN = oracle_lib.block_mass_loss(img.shape, bs, og.voxel_of_node, XN, target)
+    ref = oracle_lib.adjoint_run(og.nbr, p, X0, N, lamN, ckpt=100, g6=g6, want_gface=True)
+    gref = oracle_lib.block_theta_grad(img.shape, bs, og.voxel_of_node, og.nbr, ref["gface"], theta.size)
+    sim = vga.Sim(g, p)
+    sim.set_block_conductances(bs, theta.astype(np.float32))
+    sim.set_masses(X0)
+    sim.adjoint_forward(N, 100)
+    dldx = torch.empty((5, og.n), dtype=torch.float64, device="cuda")
+    L, _ = sim.loss_block_mass(bs, (1 << 1) | (1 << 4), target, dL_dX=dldx)
+    assert np.isclose(L, L_ref, rtol=1e-4)
+    grad, gth = sim.adjoint_backward(dldx, n_theta=theta.size)
+    assert rel_l2(gth, gref) <= 1e-4
+    for name in ("D", "rho", "mu", "v_dom"):
+        assert np.isclose(grad[name], ref["grad"][name], rtol=1e-4), name
