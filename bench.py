@@ -566,11 +566,11 @@ def bench_reference(a):
     dt = time.perf_counter() - t0
     value = og.n * a.steps / dt
     cores = oracle.num_threads()
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": a.steps,
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": workload_name(a), "grid": [a.side] * 3, "n_nodes": og.n, "time_steps_per_step": 1,
-                      "parallelism": "host cores (OpenMP)"},
+                      "parallelism": "host cores (OpenMP); the oracle uses no GPU"},
            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
                             "sample": f"{a.steps} explicit time steps of the {a.side}^3 workload"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -1,7 +1,7 @@
 """Pins of the oracle's microbial transformation (Sec. II.C eq. 3; Appendix A listings).
 
 Hand-worked single-voxel cases use dyadic numbers so every intermediate value is exact in binary
-floating point; each expected value is derived in the comment from the listing's lines.
+floating point; each expected value is derived in the comment from the listing's steps.
 """
 import numpy as np
 import pytest
