@@ -257,8 +257,11 @@ vga_status vga_loss_block_mass(vga_sim *s, int32_t block_side, uint32_t comp_mas
  *   3  the table passes of one vga_sim_step call run inside one persistent cooperative launch as a
  *      wavefront over chunks of `chunk` nodes (a multiple of 256), so that each pass reads the
  *      previous pass's output from L2; 4 passes per block, CTAs per SM from the occupancy (see
- *      vga_sim_set_wavefront).  Not used when dt_transform differs from dt (variant 2 runs).
- * The default is 2. */
+ *      vga_sim_set_wavefront).  Not used when dt_transform differs from dt (variant 2 runs);
+ *   4  as 2 with two consecutive nodes per thread, the per-node streams moved as 8-byte vectors
+ *      (FP32 values, table words) and 4-byte vectors (residuals);
+ *   5  as 2 with four consecutive nodes per thread, 16-byte and 8-byte vectors.
+ * For 4 and 5 `chunk` is ignored.  The default is 5 (the fastest at 512^3 on GB300). */
 vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t chunk);
 
 /* Selects variant 3 with `chunk` nodes per work item (a power of two in [256, 8192]; CTAs of

@@ -26,6 +26,7 @@ namespace vga {
 namespace {
 
 constexpr int kTile = 256;
+constexpr int kBatchGroup = 4;  // nodes per thread in the fused passes
 constexpr uint32_t kBarrierSpin = 1u << 26;
 
 struct BInst {
@@ -89,6 +90,35 @@ __global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int
         const int kind = (pass == 0) ? 0 : (pass == npass - 1 ? 2 : 1);  // transform / fused / diffuse
         const int bi = (cur0 + pass) & 1, bo = bi ^ 1;
         const float *__restrict__ Y2 = a.h[bi] + a.npad;
+        if (kind == 1) {
+            // fused pass: kBatchGroup consecutive nodes per thread (table_vec).  Instances start on
+            // tile boundaries, so a group never straddles two; every thread of a block runs the
+            // same number of iterations (the warp-wide shuffles need all lanes).
+            StateIO io;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                io.in[c] = a.h[bi] + c * a.npad;
+                io.lin[c] = a.l[bi] + c * a.npad;
+                io.out[c] = a.h[bo] + c * a.npad;
+                io.lout[c] = a.l[bo] + c * a.npad;
+            }
+            constexpr int KG = kBatchGroup;
+            const int64_t nsuper = (a.ntiles + KG - 1) / KG;  // kTile * KG nodes per block iteration
+            for (int64_t sup = blockIdx.x; sup < nsuper; sup += gridDim.x) {
+                const uint32_t i0 = (uint32_t)(sup * kTile * KG + (int64_t)threadIdx.x * KG);
+                const int64_t tile = (int64_t)i0 / kTile;
+                uint32_t end = 0;  // one past the instance's last node (0: no instance here)
+                StepParams p = {};
+                if (tile < a.ntiles) {
+                    const BInst &ins = a.inst[__ldg(a.tile_inst + tile)];
+                    end = (uint32_t)(ins.start + ins.n);
+                    p = ins.p;
+                }
+                table_vec<1, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, p, io);
+            }
+            if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err)) return;
+            continue;
+        }
         for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
             const BInst &ins = a.inst[__ldg(a.tile_inst + tile)];
             const uint32_t i = (uint32_t)(tile * kTile + threadIdx.x);
@@ -373,6 +403,7 @@ vga_status vga_batch_create(const vga_graph *const *graphs, const vga_params *pa
         for (int64_t t = 0; t < tiles; ++t) tinst.push_back(k);
         off += tiles * kTile;
     }
+    if (st == VGA_OK && off >= ((int64_t)1 << 31)) st = fail(VGA_ERR_UNSUPPORTED, "a batch holds fewer than 2^31 nodes");
     b->total = off;
     b->ntiles = off / kTile;
     b->npad = std::max<int64_t>(64, ((off + 63) / 64) * 64);

@@ -247,4 +247,218 @@ __device__ __forceinline__ void table_node(uint32_t i, bool live, const NbrTable
     }
 }
 
+// Vector access to K consecutive 32-bit words (K = 2: 8 bytes, K = 4: 16 bytes) and K consecutive
+// residuals; p must be aligned to the vector size.
+template <int K>
+__device__ __forceinline__ void ldg_words(const uint32_t *p, uint32_t (&o)[K]) {
+    if (K == 2) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+        o[0] = w.x;
+        o[1] = w.y;
+    } else {
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(p));
+        o[0] = w.x;
+        o[1] = w.y;
+        o[K > 2 ? 2 : 0] = w.z;
+        o[K > 3 ? 3 : 0] = w.w;
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void ldg_floats(const float *p, float (&o)[K]) {
+    uint32_t w[K];
+    ldg_words<K>(reinterpret_cast<const uint32_t *>(p), w);
+#pragma unroll
+    for (int k = 0; k < K; ++k) o[k] = __uint_as_float(w[k]);
+}
+
+template <int K>
+__device__ __forceinline__ void st_floats(float *p, const float (&v)[K]) {
+    if (K == 2) *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+    else *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[K > 2 ? 2 : 0], v[K > 3 ? 3 : 0]);
+}
+
+template <int K>
+__device__ __forceinline__ void ldg_res(const res_t *p, res_t (&o)[K]) {
+    if (K == 2) {
+        const uint32_t w = __ldg(reinterpret_cast<const unsigned int *>(p));
+        o[0] = (res_t)(w & 0xffffu);
+        o[1] = (res_t)(w >> 16);
+    } else {
+        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(p));
+        o[0] = (res_t)(w.x & 0xffffu);
+        o[1] = (res_t)(w.x >> 16);
+        o[K > 2 ? 2 : 0] = (res_t)(w.y & 0xffffu);
+        o[K > 3 ? 3 : 0] = (res_t)(w.y >> 16);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void st_res(res_t *p, const res_t (&v)[K]) {
+    if (K == 2) {
+        *reinterpret_cast<unsigned int *>(p) = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
+    } else {
+        *reinterpret_cast<uint2 *>(p) = make_uint2((uint32_t)v[0] | ((uint32_t)v[1] << 16),
+                                                   (uint32_t)v[K > 2 ? 2 : 0] | ((uint32_t)v[K > 3 ? 3 : 0] << 16));
+    }
+}
+
+// K stored values i0 .. i0 + K - 1.  FULL: all K exist, one vector access per array; otherwise one
+// access per live value (i0 + k < n).  Arithmetic as vload / vstore.
+template <int PREC, int K, bool FULL>
+__device__ __forceinline__ void vload_k(const float *__restrict__ H, const res_t *__restrict__ L, uint32_t i0,
+                                        uint32_t n, V (&v)[K]) {
+    if (FULL) {
+        float h[K];
+        ldg_floats<K>(H + i0, h);
+        res_t q[K];
+        if (PREC == P_COMP) ldg_res<K>(L + i0, q);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            v[k].h = h[k];
+            v[k].l = (PREC == P_COMP) ? res_decode(q[k], h[k]) : 0.0f;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[k] = i0 + k < n ? vload<PREC>(H, L, i0 + k) : V{0.0f, 0.0f};
+    }
+}
+
+template <int PREC, int K, bool FULL>
+__device__ __forceinline__ void vstore_k(float *__restrict__ H, res_t *__restrict__ L, uint32_t i0, uint32_t n,
+                                         const V (&v)[K]) {
+    if (FULL) {
+        float h[K];
+        res_t q[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (PREC == P_COMP) {  // renormalise as vstore
+                h[k] = __fadd_rn(v[k].h, v[k].l);
+                q[k] = res_encode(__fadd_rn(__fsub_rn(v[k].h, h[k]), v[k].l), h[k]);
+            } else {
+                h[k] = v[k].h;
+            }
+        }
+        st_floats<K>(H + i0, h);
+        if (PREC == P_COMP) st_res<K>(L + i0, q);
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (i0 + k < n) vstore<PREC>(H, L, i0 + k, v[k]);
+    }
+}
+
+template <int K, bool FULL>
+__device__ __forceinline__ void ldg_words_k(const uint32_t *__restrict__ p, uint32_t i0, uint32_t n,
+                                            uint32_t (&o)[K]) {
+    if (FULL) {
+        ldg_words<K>(p + i0, o);
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) o[k] = i0 + k < n ? __ldg(p + i0 + k) : 0u;
+    }
+}
+
+// Per-node streams of a group of K nodes: offset table, block ids and the stored DOM.
+template <int WM, int PREC, int TF, int K, bool FULL>
+__device__ __forceinline__ void group_load(uint32_t i0, uint32_t n, const NbrTable &tb, const BlockTable &bt,
+                                           const StateIO &io, uint32_t (&ty)[K], uint32_t (&zm)[K],
+                                           uint32_t (&zp)[K], uint32_t (&bn)[K], V (&x2)[K]) {
+    ldg_words_k<K, FULL>(tb.ty, i0, n, ty);
+    if (TF == 1) {
+        ldg_words_k<K, FULL>(tb.tz, i0, n, zm);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            zp[k] = zm[k] >> 16;
+            zm[k] &= 0xffffu;
+        }
+    } else {
+        ldg_words_k<K, FULL>(tb.tzm, i0, n, zm);
+        ldg_words_k<K, FULL>(tb.tzp, i0, n, zp);
+    }
+    if (WM == W_BLOCK) ldg_words_k<K, FULL>(bt.node, i0, n, bn);
+    vload_k<PREC, K, FULL>(io.in[1], io.lin[1], i0, n, x2);
+}
+
+// Transformation and stores of a group (MODE 1), or the DOM store alone (MODE 2).
+template <int MODE, int TR, int PREC, int K, bool FULL>
+__device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const StepParams &p, const StateIO &io,
+                                             V (&x2)[K]) {
+    if (MODE == 1) {
+        V x1[K], x3[K], x4[K], x5[K];
+        vload_k<PREC, K, FULL>(io.in[0], io.lin[0], i0, n, x1);
+        vload_k<PREC, K, FULL>(io.in[2], io.lin[2], i0, n, x3);
+        vload_k<PREC, K, FULL>(io.in[3], io.lin[3], i0, n, x4);
+        vload_k<PREC, K, FULL>(io.in[4], io.lin[4], i0, n, x5);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            vround<PREC>(x2[k]);
+            transform_n<TR, PREC>(x1[k], x2[k], x3[k], x4[k], x5[k], p);
+        }
+        vstore_k<PREC, K, FULL>(io.out[0], io.lout[0], i0, n, x1);
+        vstore_k<PREC, K, FULL>(io.out[1], io.lout[1], i0, n, x2);
+        vstore_k<PREC, K, FULL>(io.out[2], io.lout[2], i0, n, x3);
+        vstore_k<PREC, K, FULL>(io.out[3], io.lout[3], i0, n, x4);
+        vstore_k<PREC, K, FULL>(io.out[4], io.lout[4], i0, n, x5);
+    } else {
+        vstore_k<PREC, K, FULL>(io.out[1], io.lout[1], i0, n, x2);
+    }
+}
+
+// K consecutive nodes per thread (i0 a multiple of K, K = 2 or 4): table_node for nodes i0 ..
+// i0 + K - 1, the per-node streams (offset table, block ids, the five compartments) read and
+// written as 8- or 16-byte FP32 / table vectors and 4- or 8-byte residual vectors, so a warp moves
+// 32 K nodes per memory instruction.  Groups with all K nodes take a branch-free vector path; only
+// the last group of the range takes the per-node path.  The -x neighbour of the first node is the
+// previous lane's last node and the +x neighbour of the last node the next lane's first node.
+// Arithmetic and slot order per node are those of table_node, so the results are the same bits.
+// Rows and tables start on 16-byte boundaries (row strides are multiples of 64 values).  Must be
+// called by all 32 lanes of a warp.
+template <int MODE, int WM, int TR, int PREC, int TF, int K>
+__device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTable &tb, const BlockTable &bt,
+                                          const StepParams &p, const StateIO &io) {
+    const bool full = i0 + K <= n;
+    const float *__restrict__ Y2 = io.in[1];
+    uint32_t ty[K], zm[K], zp[K], bn[K];
+    V x2[K];
+    if (full) group_load<WM, PREC, TF, K, true>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
+    else group_load<WM, PREC, TF, K, false>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
+    float y[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) y[k] = x2[k].h;
+    const int lane = threadIdx.x & 31;
+    float yl = __shfl_up_sync(0xffffffffu, y[K - 1], 1);  // node i0 - 1
+    float yr = __shfl_down_sync(0xffffffffu, y[0], 1);    // node i0 + K
+    if (lane == 0 && ((ty[0] >> 15) & 1u)) yl = __ldg(Y2 + (i0 - 1));
+    if (lane == 31 && (ty[K - 1] >> 31)) yr = __ldg(Y2 + (i0 + K));
+    float ym[K], yp[K], zv[K], zw[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const uint32_t dym = ty[k] & 0x7fffu, dyp = (ty[k] >> 16) & 0x7fffu;
+        ym[k] = dym ? __ldg(Y2 + (i0 + k - dym)) : 0.0f;
+        yp[k] = dyp ? __ldg(Y2 + (i0 + k + dyp)) : 0.0f;
+        zv[k] = zm[k] ? __ldg(Y2 + (i0 + k - zm[k])) : 0.0f;
+        zw[k] = zp[k] ? __ldg(Y2 + (i0 + k + zp[k])) : 0.0f;
+    }
+    if (i0 >= n) return;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float acc = 0.0f;
+        auto add = [&](int slot, float yj) {
+            const float d = __fsub_rn(y[k], yj);
+            if (WM == W_UNIT) acc = __fadd_rn(acc, d);
+            else acc = __fmaf_rn(table_theta(bt, bn[k], slot), d, acc);
+        };
+        if ((ty[k] >> 15) & 1u) add(0, k == 0 ? yl : y[k > 0 ? k - 1 : 0]);
+        if (ty[k] >> 31) add(1, k == K - 1 ? yr : y[k < K - 1 ? k + 1 : 0]);
+        if (ty[k] & 0x7fffu) add(2, ym[k]);
+        if ((ty[k] >> 16) & 0x7fffu) add(3, yp[k]);
+        if (zm[k]) add(4, zv[k]);
+        if (zp[k]) add(5, zw[k]);
+        vadd<PREC>(x2[k], __fmul_rn(-p.c, acc));  // Scheme 1
+    }
+    if (full) group_finish<MODE, TR, PREC, K, true>(i0, n, p, io, x2);
+    else group_finish<MODE, TR, PREC, K, false>(i0, n, p, io, x2);
+}
+
 }  // namespace vga

@@ -271,6 +271,14 @@ __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable 
     table_node<MODE, WM, TR, PREC, LD_NC, TF>(i, i < (uint64_t)n, tb, bt, p, io);
 }
 
+// K consecutive nodes per thread (table_vec); n < 2^31, so K * thread index fits 32 bits.
+template <int MODE, int WM, int TR, int PREC, int TF, int K>
+__global__ void __launch_bounds__(kThreads) k_stencil_tablev(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+                                                             StateIO io) {
+    const uint32_t i0 = (uint32_t)K * ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x);
+    table_vec<MODE, WM, TR, PREC, TF, K>(i0, (uint32_t)n, tb, bt, p, io);
+}
+
 // Largest z offset of the table (for the compact form).
 __global__ void k_table_zmax(int64_t n, const uint32_t *__restrict__ tzm, const uint32_t *__restrict__ tzp,
                              unsigned int *__restrict__ out) {
@@ -404,8 +412,28 @@ void launch_staged_any(vga_sim *s, const StateIO &io) {
     }
 }
 
+template <int MODE, int WM, int PREC, int K>
+void launch_tablev(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
+    const unsigned grid = grid_for((s->n + K - 1) / K, kThreads);
+    if (tb.tz) {
+        if (s->sp.transform == 0) k_stencil_tablev<MODE, WM, 0, PREC, 1, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
+        else k_stencil_tablev<MODE, WM, 1, PREC, 1, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
+    } else {
+        if (s->sp.transform == 0) k_stencil_tablev<MODE, WM, 0, PREC, 0, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
+        else k_stencil_tablev<MODE, WM, 1, PREC, 0, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
+    }
+}
+
 template <int MODE, int WM, int PREC>
 vga_status launch_table(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
+    if (s->kernel_variant == 4) {
+        launch_tablev<MODE, WM, PREC, 2>(s, io, tb, bt);
+        return VGA_OK;
+    }
+    if (s->kernel_variant == 5) {
+        launch_tablev<MODE, WM, PREC, 4>(s, io, tb, bt);
+        return VGA_OK;
+    }
     const unsigned grid = grid_for(s->n, kThreads);
     if (tb.tz) {
         if (s->sp.transform == 0) k_stencil_table<MODE, WM, 0, PREC, 1><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
@@ -437,7 +465,7 @@ void launch_stencil_tr(vga_sim *s, const StateIO &io) {
 template <int MODE>
 vga_status launch_stencil(vga_sim *s, const StateIO &io) {
     const bool comp = s->precision() == P_COMP;
-    if ((s->kernel_variant == 2 || s->kernel_variant == 3) && s->g->nx <= 32767) {
+    if (s->kernel_variant >= 2 && s->g->nx <= 32767) {
         // table kernels: build the tables (first use) before the timed launch
         NbrTable tb;
         BlockTable bt;
@@ -737,7 +765,7 @@ vga_status build_compact_z(int64_t n, int64_t cap, const uint32_t *tzm, const ui
 }
 
 bool stencil_variant_supported(int variant, int cap) {
-    return variant == 0 || variant == 2 || staged_cap_supported(cap);
+    return variant == 0 || variant == 2 || variant == 4 || variant == 5 || staged_cap_supported(cap);
 }
 
 }  // namespace vga

@@ -215,8 +215,9 @@ struct vga_sim {
     // adjoint work buffers (adjoint.cu), allocated on first use
     vga::AdjointBuffers *adj = nullptr;
     int32_t *d_err = nullptr;     // device error flag of bounded waits (nonzero: timed out)
-    int kernel_variant = 2;       // explicit stencil: 0 decode + direct loads, 1 decode + staged, 2 table,
-                                  // 3 table passes as an L2 wavefront (wave.cu)
+    int kernel_variant = 5;       // explicit stencil: 0 decode + direct loads, 1 decode + staged, 2 table,
+                                  // 3 table passes as an L2 wavefront (wave.cu), 4 / 5 table, two /
+                                  // four nodes per thread
     int wave_chunk = 512, wave_depth = 4, wave_ctas = 0;  // wavefront chunk, passes per block, CTAs/SM
     int32_t *wave_dep = nullptr;      // per chunk: lowest and highest chunk its neighbours lie in; flags
     int32_t *wave_order = nullptr;    // skewed item order of one block of passes

@@ -217,7 +217,8 @@ def test_device_state_io(vga, oracle_lib):
 
 @pytest.mark.parametrize("block,transform,precision", [(False, 0, 0), (True, 0, 0), (False, 1, 0), (False, 0, 1)])
 def test_kernel_variants_bit_identical(vga, oracle_lib, block, transform, precision):
-    """Direct and staged stencil kernels, every chunk size: the same bits after 50 steps."""
+    """Decode, staged and table stencil kernels (one and two nodes per thread), every chunk size:
+    the same bits after 50 steps."""
     img, og, g, X0 = _setup(vga, oracle_lib, (40, 48, 36), 0.24, 12, organic=True)
     p = synth.paper_params(transform=transform)
     p["state_precision"] = precision
@@ -226,7 +227,7 @@ def test_kernel_variants_bit_identical(vga, oracle_lib, block, transform, precis
     if block:
         p["dt"] = 0.9 / (6 * synth.D_DOM * theta.max())
     states = []
-    for variant, chunk in [(0, 1024), (1, 1024), (1, 512), (1, 2048), (0, 512), (0, 96), (2, 1024)]:
+    for variant, chunk in [(0, 1024), (1, 1024), (1, 512), (1, 2048), (0, 512), (0, 96), (2, 1024), (4, 1024), (5, 1024)]:
         sim = vga.Sim(g, p)
         sim.set_kernel(variant, chunk)
         if block:
@@ -250,7 +251,7 @@ def test_autotune_keeps_state(vga, oracle_lib):
     sim.step(3)
     before = sim.save_state()
     res = sim.autotune(4)
-    assert res["best"] is not None and len(res["entries"]) == 10
+    assert res["best"] is not None and len(res["entries"]) == 12
     assert all(e["ms_per_step"] > 0 for e in res["entries"])
     assert sim.save_state() == before
     with pytest.raises(vga.VgaError):
@@ -267,11 +268,39 @@ def test_wide_z_offsets(vga, oracle_lib):
     X0 = synth.random_masses(g.n, 9, scale=1e-3, density=0.5)
     p = synth.paper_params()
     outs = []
-    for variant in (2, 0):
+    for variant in (2, 4, 5, 0):
         sim = vga.Sim(g, p)
         sim.set_kernel(variant, 1024)
         sim.set_masses(X0)
         sim.step(12)
         outs.append(sim.get_masses())
-    assert np.array_equal(outs[0], outs[1])
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])
     _assert_close(outs[0], oracle_lib.explicit_run(og.nbr, p, X0, 12))
+
+
+@pytest.mark.parametrize("nx", [1, 2, 3, 31, 63, 64, 65, 97])
+def test_pair_kernel_ragged_rows(vga, oracle_lib, nx):
+    """Two and four nodes per thread: a single x-row of nx nodes (a chain along x, so +-x
+    neighbours cross group and warp boundaries, and counts that are not a multiple of the group
+    leave a partial last group) plus a plane of scattered voxels; the same bits as one node per
+    thread, and the oracle's values."""
+    img = np.ones((3, 5, nx), dtype=np.uint8)  # 0 = pore
+    img[1, 2, :] = 0
+    rng = np.random.default_rng(nx)
+    img[2] = rng.random((5, nx)) >= 0.5
+    og = oracle_lib.graph_build(img, keep_largest=False)
+    g = vga.Graph(img, keep_largest=False)
+    assert g.n == og.n
+    X0 = synth.random_masses(g.n, nx, scale=1e-3, density=0.7)
+    p = synth.paper_params()
+    outs = []
+    for variant in (2, 4, 5):
+        sim = vga.Sim(g, p)
+        sim.set_kernel(variant, 1024)
+        sim.set_masses(X0)
+        sim.step(7)
+        outs.append(sim.save_state())
+    assert outs[0] == outs[1] and outs[0] == outs[2]
+    last = vga.Sim(g, p)
+    last.load_state(outs[1])
+    _assert_close(last.get_masses(), oracle_lib.explicit_run(og.nbr, p, X0, 7))
