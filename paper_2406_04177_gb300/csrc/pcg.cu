@@ -363,6 +363,15 @@ vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgSc
 // r = b - B x in FP64 (one stencil pass); the correction B d = r is solved by the same Jacobi-PCG
 // in FP32 to a relative reduction tol_in; x += d; the loop stops when ||b - B x||_2 <= rtol ||b||_2
 // (the true residual, not the recurrence).  Every reduction is a fixed-order block-partial sum.
+//
+// Kernels of one inner iteration (three launches; no single-block scalar kernels):
+//   k_mx_spmv   q = B p (four nodes per thread), partial p.q; the last block to finish forms alpha
+//   k_mx_upd    d += alpha p, r -= alpha q, partials r.Tr and r.r; the last block tests the inner
+//               stop and forms beta
+//   k_mx_p      p = T r + beta p
+// "Last block": each block stores its partials, fences, and takes a ticket from a counter; the
+// block that draws the final ticket sums all partials in block order (so the result does not
+// depend on which block that is) and resets the counter.  No block waits for another.
 
 constexpr double kInnerTol = 1e-4;  // reduction asked of one FP32 inner solve
 constexpr int kMxBlocks = 2432;     // grid of the mixed-solver kernels: 152 SMs x 16 (grid-stride)
@@ -371,7 +380,35 @@ constexpr int kMaxOuter = 64;
 struct MxScalars {
     double bb, rr_out, rz, alpha, beta, rr_in, stop_in, relres, rtol2;
     int32_t done, inner_done, iters, in_iters, notconv, maxit, outer;
+    uint32_t ticket_a, ticket_b;  // arrival counters of the last-block reductions (0 between launches)
 };
+
+// Deterministic sum of part[k*stride + comp] over k < count by one block, read at L2 (the partials
+// were written by other blocks of the same launch).
+__device__ double block_reduce_partials_cg(const double *part, int64_t count, int stride, int comp) {
+    double acc[1] = {0.0};
+    for (int64_t k = threadIdx.x; k < count; k += blockDim.x) acc[0] += __ldcg(part + k * stride + comp);
+    __shared__ double out[1];
+    block_sum_store<1>(acc, out);
+    return out[0];
+}
+
+// Called by every thread once the block's partials are stored: true in the block that arrives
+// last, which then sees every block's partials.  The counter is reset for the next launch.  No
+// block waits for another.
+__device__ __forceinline__ bool last_block(uint32_t *ticket) {
+    __shared__ int last;
+    __threadfence();  // the partials stored by this thread are visible before the arrival
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1) ? 1 : 0;
+        if (last) *ticket = 0u;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last != 0;
+}
 
 struct MxVecs {
     double *x, *b;
@@ -408,42 +445,71 @@ __device__ __forceinline__ float nbr_sum_f(const NbrTable &tb, uint32_t i, bool 
     return s;
 }
 
-// Outer residual r = b - B x in FP64 (FIRST: b from the state, x = b), t = 1 / (1 + c deg) (FP32),
-// the FP32 copies r and p = T r, d = 0; partials (r.r FP64, b.b, r.Tr).
-template <int PREC, bool FIRST>
-__global__ void __launch_bounds__(kThreads) k_mx_res(int64_t n, NbrTable tb, double c, const float *__restrict__ y2,
-                                                     const res_t *__restrict__ y2l, MxVecs v,
+// Neighbours of node i from the offset table: the sum of their values (FP64) and their count.
+template <int TF>
+__device__ __forceinline__ double nbr_vals_d(const NbrTable &tb, uint32_t i, bool live, double vi,
+                                             const double *__restrict__ v, int &deg) {
+    const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
+    uint32_t dzm, dzp;
+    if (TF == 1) {
+        const uint32_t tz = live ? __ldg(tb.tz + i) : 0u;
+        dzm = tz & 0xffffu;
+        dzp = tz >> 16;
+    } else {
+        dzm = live ? __ldg(tb.tzm + i) : 0u;
+        dzp = live ? __ldg(tb.tzp + i) : 0u;
+    }
+    const int lane = threadIdx.x & 31;
+    double vl = __shfl_up_sync(0xffffffffu, vi, 1);
+    double vr = __shfl_down_sync(0xffffffffu, vi, 1);
+    const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
+    const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
+    if (lane == 0 && hxm) vl = __ldg(v + (i - 1));
+    if (lane == 31 && hxp) vr = __ldg(v + (i + 1));
+    double s = 0.0;
+    if (hxm) s += vl;
+    if (hxp) s += vr;
+    if (dym) s += __ldg(v + (i - dym));
+    if (dyp) s += __ldg(v + (i + dyp));
+    if (dzm) s += __ldg(v + (i - dzm));
+    if (dzp) s += __ldg(v + (i + dzp));
+    deg = (int)hxm + (int)hxp + (dym != 0) + (dyp != 0) + (dzm != 0) + (dzp != 0);
+    return s;
+}
+
+// Outer residual r = b - B x in FP64 (FIRST: x = b), t = 1 / (1 + c deg) (FP32), the FP32 copies r
+// and p = T r, d = 0; partials (r.r FP64, b.b (FIRST), r.Tr).  GB300 runs FP64 at a small fraction
+// of its FP32 rate and this pass is bound by it, so (L x)_i is formed as deg x_i - sum_j x_j (one
+// FMA after the neighbour sum) and the degree is counted in integers.
+template <bool FIRST, int TF>
+__global__ void __launch_bounds__(kThreads) k_mx_res(int64_t n, NbrTable tb, double c, MxVecs v,
                                                      double *__restrict__ part, const MxScalars *__restrict__ sc) {
     if (!FIRST && sc->done) return;
     double acc[3] = {0.0, 0.0, 0.0};
     const int64_t ntile = (n + kThreads - 1) / kThreads;
+    const double *__restrict__ xs = FIRST ? v.b : v.x;  // FIRST: x = b, read from b (filled by k_mx_rhs)
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
         const bool live = i < (uint64_t)n;
         double xi = 0.0, bi = 0.0;
         if (live) {
-            bi = FIRST ? ld_value_d<PREC>(y2, y2l, i) : v.b[i];
-            xi = FIRST ? bi : v.x[i];
+            bi = __ldg(v.b + i);
+            xi = FIRST ? bi : __ldg(v.x + i);
         }
-        double deg = 0.0;
-        // FIRST: x = b, so the neighbours' x are read from the state as well
-        const double lx = FIRST ? 0.0 : nbr_sum_table(tb, i, live, xi, v.x, deg);
-        double lb = 0.0;
-        if (FIRST) lb = nbr_sum_table(tb, i, live, xi, v.b, deg);
+        int deg = 0;
+        const double sx = nbr_vals_d<TF>(tb, i, live, xi, xs, deg);
         if (live) {
-            const double ri = bi - (xi + c * (FIRST ? lb : lx));
+            const double lx = fma((double)deg, xi, -sx);
+            const double ri = fma(-c, lx, bi - xi);
             const float ti = 1.0f / (1.0f + (float)c * (float)deg);
             const float r32 = (float)ri;
-            if (FIRST) {
-                v.b[i] = bi;
-                v.x[i] = xi;
-            }
+            if (FIRST) v.x[i] = xi;
             v.t[i] = ti;
             v.r[i] = r32;
             v.p[i] = ti * r32;
             v.d[i] = 0.0f;
-            acc[0] += ri * ri;
-            acc[1] += bi * bi;
+            acc[0] = fma(ri, ri, acc[0]);
+            if (FIRST) acc[1] = fma(bi, bi, acc[1]);
             acc[2] += (double)(r32 * (ti * r32));
         }
     }
@@ -493,46 +559,99 @@ __global__ void __launch_bounds__(kThreads) k_mx_scal_out(const double *__restri
         sc->rr_in = rr;
         sc->in_iters = 0;
         sc->inner_done = sc->done;
+        sc->ticket_a = 0u;
+        sc->ticket_b = 0u;
     }
 }
 
+// q = B p in FP32 with four consecutive nodes per thread (16-byte accesses of p, q and the offset
+// table; the -x neighbour of the first node and the +x neighbour of the last come from the adjacent
+// lanes), partial p.q; the block that finishes last forms alpha = r.Tr / p.q.
 template <int TF>
 __global__ void __launch_bounds__(kThreads) k_mx_spmv(int64_t n, NbrTable tb, float c, MxVecs v,
-                                                      double *__restrict__ part, const MxScalars *__restrict__ sc) {
+                                                      double *__restrict__ part, MxScalars *sc) {
     if (sc->inner_done) return;
+    constexpr int K = 4;
     float acc = 0.0f;
     const float *__restrict__ p = v.p;
     float *__restrict__ q = v.q;
-    const int64_t ntile = (n + kThreads - 1) / kThreads;
-#pragma unroll 2
-    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
-        const bool live = i < (uint64_t)n;
-        const float pi = live ? __ldg(p + i) : 0.0f;
-        const float lp = nbr_sum_f<TF>(tb, i, live, pi, p);
-        if (live) {
-            const float qi = pi + c * lp;
-            q[i] = qi;
-            acc += pi * qi;
+    const uint32_t nn = (uint32_t)n;
+    const int lane = threadIdx.x & 31;
+    const int64_t nsup = (n + (int64_t)kThreads * K - 1) / ((int64_t)kThreads * K);
+    for (int64_t sup = blockIdx.x; sup < nsup; sup += gridDim.x) {
+        const uint32_t i0 = (uint32_t)(sup * kThreads * K + (int64_t)threadIdx.x * K);
+        const bool full = i0 + K <= nn;
+        float pv[K];
+        uint32_t ty[K], zm[K], zp[K];
+        if (full) {
+            ldg_floats<K>(p + i0, pv);
+            ldg_words_k<K, true>(tb.ty, i0, nn, ty);
+            if (TF == 1) {
+                ldg_words_k<K, true>(tb.tz, i0, nn, zm);
+            } else {
+                ldg_words_k<K, true>(tb.tzm, i0, nn, zm);
+                ldg_words_k<K, true>(tb.tzp, i0, nn, zp);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k) pv[k] = i0 + k < nn ? __ldg(p + i0 + k) : 0.0f;
+            ldg_words_k<K, false>(tb.ty, i0, nn, ty);
+            if (TF == 1) {
+                ldg_words_k<K, false>(tb.tz, i0, nn, zm);
+            } else {
+                ldg_words_k<K, false>(tb.tzm, i0, nn, zm);
+                ldg_words_k<K, false>(tb.tzp, i0, nn, zp);
+            }
+        }
+        if (TF == 1) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                zp[k] = zm[k] >> 16;
+                zm[k] &= 0xffffu;
+            }
+        }
+        float pl = __shfl_up_sync(0xffffffffu, pv[K - 1], 1);
+        float pr = __shfl_down_sync(0xffffffffu, pv[0], 1);
+        if (lane == 0 && ((ty[0] >> 15) & 1u)) pl = __ldg(p + (i0 - 1));
+        if (lane == 31 && (ty[K - 1] >> 31)) pr = __ldg(p + (i0 + K));
+        float qv[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const uint32_t dym = ty[k] & 0x7fffu, dyp = (ty[k] >> 16) & 0x7fffu;
+            const float vi = pv[k];
+            float sum = 0.0f;
+            if ((ty[k] >> 15) & 1u) sum += vi - (k == 0 ? pl : pv[k > 0 ? k - 1 : 0]);
+            if (ty[k] >> 31) sum += vi - (k == K - 1 ? pr : pv[k < K - 1 ? k + 1 : 0]);
+            if (dym) sum += vi - __ldg(p + (i0 + k - dym));
+            if (dyp) sum += vi - __ldg(p + (i0 + k + dyp));
+            if (zm[k]) sum += vi - __ldg(p + (i0 + k - zm[k]));
+            if (zp[k]) sum += vi - __ldg(p + (i0 + k + zp[k]));
+            qv[k] = vi + c * sum;
+            if (i0 + k < nn) acc += vi * qv[k];
+        }
+        if (full) {
+            st_floats<K>(q + i0, qv);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (i0 + k < nn) q[i0 + k] = qv[k];
         }
     }
     double a[1] = {(double)acc};
     __shared__ double out[1];
     block_sum_store<1>(a, out);
     if (threadIdx.x == 0) part[blockIdx.x] = out[0];
-}
-
-__global__ void __launch_bounds__(kThreads) k_mx_scal_a(const double *__restrict__ part, int64_t count, MxScalars *sc) {
-    if (sc->inner_done) return;
-    const double pq = block_reduce_partials(part, count, 1, 0);
-    if (threadIdx.x == 0) sc->alpha = pq > 0.0 ? sc->rz / pq : 0.0;
+    if (last_block(&sc->ticket_a)) {
+        const double pq = block_reduce_partials_cg(part, gridDim.x, 1, 0);
+        if (threadIdx.x == 0) sc->alpha = pq > 0.0 ? sc->rz / pq : 0.0;
+    }
 }
 
 // The streaming kernels below move four nodes per thread and access (16-byte vectors: every FP32
 // array starts on a 16-byte boundary); the n % 4 last nodes go through a scalar tail, so the padding
 // after node n never enters a sum.
-__global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, MxVecs v, const MxScalars *__restrict__ sc,
-                                                     double *__restrict__ part) {
+__global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, MxVecs v, MxScalars *sc, double *__restrict__ part,
+                                                     int in_maxit) {
     if (sc->inner_done) return;
     const float alpha = (float)sc->alpha;
     float a0 = 0.0f, a1 = 0.0f;
@@ -570,22 +689,21 @@ __global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, MxVecs v, const 
     __shared__ double out[2];
     block_sum_store<2>(a, out);
     if (threadIdx.x < 2) part[(int64_t)blockIdx.x * 2 + threadIdx.x] = out[threadIdx.x];
-}
-
-__global__ void __launch_bounds__(kThreads) k_mx_scal_b(const double *__restrict__ part, int64_t count, MxScalars *sc,
-                                                        int in_maxit) {
-    if (sc->inner_done) return;
-    const double rz = block_reduce_partials(part, count, 2, 0);
-    const double rr = block_reduce_partials(part, count, 2, 1);
-    if (threadIdx.x == 0) {
-        sc->iters += 1;
-        sc->in_iters += 1;
-        sc->rr_in = rr;
-        if (rr <= sc->stop_in || sc->in_iters >= in_maxit || sc->iters >= sc->maxit || !(sc->rz > 0.0)) {
-            sc->inner_done = 1;
-        } else {
-            sc->beta = rz / sc->rz;
-            sc->rz = rz;
+    // the last block: inner convergence test and beta (every block has passed its inner_done test
+    // before the last one arrives, so none of this launch sees the update)
+    if (last_block(&sc->ticket_b)) {
+        const double rz = block_reduce_partials_cg(part, gridDim.x, 2, 0);
+        const double rr = block_reduce_partials_cg(part, gridDim.x, 2, 1);
+        if (threadIdx.x == 0) {
+            sc->iters += 1;
+            sc->in_iters += 1;
+            sc->rr_in = rr;
+            if (rr <= sc->stop_in || sc->in_iters >= in_maxit || sc->iters >= sc->maxit || !(sc->rz > 0.0)) {
+                sc->inner_done = 1;
+            } else {
+                sc->beta = rz / sc->rz;
+                sc->rz = rz;
+            }
         }
     }
 }
@@ -645,7 +763,8 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
     const int in_maxit = 200;
     timing_begin(s, VGA_KERNEL_PCG_STENCIL);
     k_mx_rhs<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->comp(1), s->lcomp(1), v.b);
-    k_mx_res<PREC, true><<<G, kThreads, 0, st>>>(s->n, tb, c, s->comp(1), s->lcomp(1), v, part_a, sc);
+    if (tb.tz) k_mx_res<true, 1><<<G, kThreads, 0, st>>>(s->n, tb, c, v, part_a, sc);
+    else k_mx_res<true, 0><<<G, kThreads, 0, st>>>(s->n, tb, c, v, part_a, sc);
     timing_end(s);
     k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, 1, s->params.cg_rtol, s->params.cg_maxit);
     VGA_CHECK_LAUNCH();
@@ -658,14 +777,12 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
             else k_mx_spmv<0><<<G, kThreads, 0, st>>>(s->n, tb, (float)c, v, part_a, sc);
             timing_end(s);
             timing_begin(s, VGA_KERNEL_PCG_VECTOR);
-            k_mx_scal_a<<<1, kThreads, 0, st>>>(part_a, G, sc);
-            k_mx_upd<<<G, kThreads, 0, st>>>(s->n, v, sc, part_b);
-            k_mx_scal_b<<<1, kThreads, 0, st>>>(part_b, G, sc, in_maxit);
+            k_mx_upd<<<G, kThreads, 0, st>>>(s->n, v, sc, part_b, in_maxit);
             k_mx_p<<<G, kThreads, 0, st>>>(s->n, v, sc);
             timing_end(s);
         }
         VGA_CHECK_LAUNCH();
-        s->launches += 5 * kBatch;
+        s->launches += 3 * kBatch;
         VGA_CUDA(cudaMemcpyAsync(h, sc, sizeof(MxScalars), cudaMemcpyDeviceToHost, st));
         VGA_CUDA(cudaStreamSynchronize(st));
         if (h->done) break;
@@ -673,7 +790,8 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
             // x += d, then the FP64 residual of the new x and the next inner solve's start
             timing_begin(s, VGA_KERNEL_PCG_STENCIL);
             k_mx_x<<<G, kThreads, 0, st>>>(s->n, v, sc);
-            k_mx_res<PREC, false><<<G, kThreads, 0, st>>>(s->n, tb, c, s->comp(1), s->lcomp(1), v, part_a, sc);
+            if (tb.tz) k_mx_res<false, 1><<<G, kThreads, 0, st>>>(s->n, tb, c, v, part_a, sc);
+            else k_mx_res<false, 0><<<G, kThreads, 0, st>>>(s->n, tb, c, v, part_a, sc);
             timing_end(s);
             k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, 0, s->params.cg_rtol, s->params.cg_maxit);
             VGA_CHECK_LAUNCH();
