@@ -373,7 +373,7 @@ def bench_ours(a):
 
 
 def bench_implicit(vga, g, x0_dev, n, stream, nimp=3):
-    """Scheme 2 at 10x the explicit limit, rtol 1e-8, default solver (FP64 refinement around FP32
+    """Scheme 2 at 10x the explicit limit, rtol 1e-8, default solver (float-float refinement around FP32
     PCG); kernel times by kind from the library's CUDA-event timing."""
     import torch
 
@@ -403,7 +403,9 @@ def bench_implicit(vga, g, x0_dev, n, stream, nimp=3):
     return {"value": n * nimp / (w1 - w0), "unit": UNIT + " (one solve = one step)",
             "cg_iterations_per_step": (it1 - it0) / nimp,
             "last_relres": st["cg_last_relres"], "dt_over_explicit_limit": 10.0, "rtol": 1e-8,
-            "solver": "FP64 refinement around FP32 Jacobi-PCG (true residual)",
+            "solver": "float-float refinement around FP32 Jacobi-PCG (true residual)",
+            "loops": "device (one CUDA graph per step, conditional while nodes)" if st["graph_launches"] > 0
+            else "host-driven",
             "kernel_ms": {k: round(v[0], 3) for k, v in kti.items() if v[1]},
             "kernel_launches": {k: v[1] for k, v in kti.items() if v[1]}}
 

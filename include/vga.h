@@ -169,13 +169,20 @@ vga_status vga_sim_set_state_f32(vga_sim *s, const float *x, int32_t on_device);
 vga_status vga_sim_get_state_f32(vga_sim *s, float *x, int32_t on_device);
 
 /* Implicit solver (Scheme 2).  VGA_SOLVER_FP64_PCG: Jacobi-PCG in FP64, stopping on the
- * recurrence residual.  VGA_SOLVER_MIXED_REFINEMENT (default): the residual b - B x and x are kept
- * in FP64 and each correction is solved by the same Jacobi-PCG in FP32 (to a 1e-4 reduction);
+ * recurrence residual.  VGA_SOLVER_MIXED_REFINEMENT (default): x, b and the residual b - B x are
+ * kept in float-float (two FP32 numbers, about 48 significant bits, computed with error-free FP32
+ * operations) and each correction is solved by the same Jacobi-PCG in FP32 (to a 1e-4 reduction);
  * stops when the true residual satisfies ||b - B x||_2 <= cg_rtol ||b||_2; iterations count the FP32
  * inner iterations against cg_maxit.  Used with unit conductances (block conductances run the FP64
- * solver).  Errors: VGA_ERR_INVALID_ARG. */
+ * solver).  The whole mixed solve runs as one CUDA graph whose outer and inner loops are
+ * conditional (while) nodes set by the solver's own kernels, so the host synchronises once per
+ * time step; where the driver cannot build such a graph the solve falls back to the host-driven
+ * loop.  VGA_SOLVER_MIXED_HOST_LOOP: the same solver with its loops driven from the host (the done
+ * flags polled every 8 inner iterations); the same kernels in the same order, so the same bits.
+ * Errors: VGA_ERR_INVALID_ARG. */
 #define VGA_SOLVER_FP64_PCG 0
 #define VGA_SOLVER_MIXED_REFINEMENT 1
+#define VGA_SOLVER_MIXED_HOST_LOOP 2
 vga_status vga_sim_set_solver(vga_sim *s, int32_t solver);
 
 /* Exact checkpoint of the state: the FP32 values, their residuals and the step counter, in a
@@ -203,7 +210,8 @@ typedef struct vga_sim_stats {
     int64_t steps_done;       /* time steps since creation */
     int64_t cg_iterations;    /* implicit scheme: PCG iterations since creation */
     double cg_last_relres;    /* implicit scheme: final relative residual of the last solve */
-    int64_t kernel_launches;  /* kernels launched since creation */
+    int64_t kernel_launches;  /* kernels launched since creation (inside a graph: kernels it ran) */
+    int64_t graph_launches;   /* implicit scheme: CUDA graph launches of the mixed solve */
 } vga_sim_stats;
 vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out);
 

@@ -35,6 +35,7 @@ VGA_STATE_COMPENSATED = 0
 VGA_STATE_F32 = 1
 VGA_SOLVER_FP64_PCG = 0
 VGA_SOLVER_MIXED_REFINEMENT = 1
+VGA_SOLVER_MIXED_HOST_LOOP = 2
 
 
 class VgaError(RuntimeError):
@@ -78,7 +79,7 @@ class vga_batch_tune(C.Structure):
 
 class vga_sim_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("cg_iterations", C.c_int64),
-                ("cg_last_relres", C.c_double), ("kernel_launches", C.c_int64)]
+                ("cg_last_relres", C.c_double), ("kernel_launches", C.c_int64), ("graph_launches", C.c_int64)]
 
 
 VGA_KERNEL_KINDS = 8

@@ -517,9 +517,10 @@ vga_status vga_sim_load_state(vga_sim *s, const void *buf, int64_t bytes) {
 
 vga_status vga_sim_set_solver(vga_sim *s, int32_t solver) {
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
-    if (solver != VGA_SOLVER_FP64_PCG && solver != VGA_SOLVER_MIXED_REFINEMENT)
+    if (solver != VGA_SOLVER_FP64_PCG && solver != VGA_SOLVER_MIXED_REFINEMENT && solver != VGA_SOLVER_MIXED_HOST_LOOP)
         return fail(VGA_ERR_INVALID_ARG, "unknown solver");
-    s->cg_mixed = solver == VGA_SOLVER_MIXED_REFINEMENT;
+    s->cg_mixed = solver != VGA_SOLVER_FP64_PCG;
+    s->cg_host_loop = solver == VGA_SOLVER_MIXED_HOST_LOOP;
     return VGA_OK;
 }
 
@@ -548,6 +549,7 @@ vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out) {
     out->cg_iterations = s->cg_iterations;
     out->cg_last_relres = s->cg_last_relres;
     out->kernel_launches = s->launches;
+    out->graph_launches = s->graph_launches;
     return VGA_OK;
 }
 
@@ -672,6 +674,7 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->stage);
     dfree(s->theta);
     dfree(s->cg);
+    sim_mx_graph_release(s);
     dfree(s->cg_scalars);
     dfree(s->loss_work);
     dfree(s->wave_dep);

@@ -18,6 +18,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
+#include <new>
+#include <tuple>
+#include <utility>
 
 #include "stencil.cuh"
 #include "vga_internal.cuh"
@@ -356,19 +360,23 @@ vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgSc
 }
 
 
-// ---- mixed precision: FP64 iterative refinement around an FP32 Jacobi-PCG (unit conductances) ----
+// ---- mixed precision: float-float iterative refinement around an FP32 Jacobi-PCG (unit conductances) ----
 //
 // GB300 executes FP64 at a small fraction of its FP32 rate, and the FP64 PCG above is bound by that
-// arithmetic.  Here the outer loop keeps x and b in FP64 and computes the true residual
-// r = b - B x in FP64 (one stencil pass); the correction B d = r is solved by the same Jacobi-PCG
-// in FP32 to a relative reduction tol_in; x += d; the loop stops when ||b - B x||_2 <= rtol ||b||_2
-// (the true residual, not the recurrence).  Every reduction is a fixed-order block-partial sum.
+// arithmetic.  Here the outer loop keeps x and b as unevaluated sums of two FP32 numbers (hi + lo,
+// about 48 significant bits) and forms the true residual r = b - B x in that arithmetic with FP32
+// instructions (error-free TwoSum and FMA products); the correction B d = r is solved by the same
+// Jacobi-PCG in FP32 to a relative reduction tol_in; x += d; the loop stops when
+// ||b - B x||_2 <= rtol ||b||_2 (the true residual, not the recurrence; ||r||^2 and ||b||^2 are
+// accumulated in FP64).  Every reduction is a fixed-order block-partial sum.
 //
 // Kernels of one inner iteration (three launches; no single-block scalar kernels):
 //   k_mx_spmv   q = B p (four nodes per thread), partial p.q; the last block to finish forms alpha
 //   k_mx_upd    d += alpha p, r -= alpha q, partials r.Tr and r.r; the last block tests the inner
 //               stop and forms beta
 //   k_mx_p      p = T r + beta p
+// The Jacobi scaling T = diag(1 / (1 + c deg_i)) is not stored: each node keeps its degree in one
+// byte and the kernels look t up in a 7-entry table computed by the same expression everywhere.
 // "Last block": each block stores its partials, fences, and takes a ticket from a counter; the
 // block that draws the final ticket sums all partials in block order (so the result does not
 // depend on which block that is) and resets the counter.  No block waits for another.
@@ -381,6 +389,15 @@ struct MxScalars {
     double bb, rr_out, rz, alpha, beta, rr_in, stop_in, relres, rtol2;
     int32_t done, inner_done, iters, in_iters, notconv, maxit, outer;
     uint32_t ticket_a, ticket_b;  // arrival counters of the last-block reductions (0 between launches)
+    int32_t fresh;                // set by the first residual pass: the next k_mx_scal_out starts a solve
+    int32_t guard;                // inner iterations of this solve (a bound on the device-side loops)
+};
+
+// Device-side loops (the solve as one CUDA graph): the kernels that decide whether a loop goes on
+// set the while-node conditions.  cond = 0 outside a graph (host-driven loop).
+struct MxLoop {
+    cudaGraphConditionalHandle outer, inner;
+    int cond;
 };
 
 // Deterministic sum of part[k*stride + comp] over k < count by one block, read at L2 (the partials
@@ -410,45 +427,47 @@ __device__ __forceinline__ bool last_block(uint32_t *ticket) {
     return last != 0;
 }
 
+// x and b: hi and lo parts; r, p, q, d: the FP32 inner solve; deg: node degree (0..6).
 struct MxVecs {
-    double *x, *b;
-    float *r, *p, *q, *d, *t;
+    float *xh, *xl, *bh, *bl;
+    float *r, *p, *q, *d;
+    uint8_t *deg;
 };
 
-template <int TF>
-__device__ __forceinline__ float nbr_sum_f(const NbrTable &tb, uint32_t i, bool live, float vi,
-                                           const float *__restrict__ v) {
-    const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
-    uint32_t dzm, dzp;
-    if (TF == 1) {  // compact z offsets
-        const uint32_t tz = live ? __ldg(tb.tz + i) : 0u;
-        dzm = tz & 0xffffu;
-        dzp = tz >> 16;
-    } else {
-        dzm = live ? __ldg(tb.tzm + i) : 0u;
-        dzp = live ? __ldg(tb.tzp + i) : 0u;
-    }
-    const int lane = threadIdx.x & 31;
-    float vl = __shfl_up_sync(0xffffffffu, vi, 1);
-    float vr = __shfl_down_sync(0xffffffffu, vi, 1);
-    const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
-    const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
-    if (lane == 0 && hxm) vl = v[i - 1];
-    if (lane == 31 && hxp) vr = v[i + 1];
-    float s = 0.0f;
-    if (hxm) s += vi - vl;
-    if (hxp) s += vi - vr;
-    if (dym) s += vi - v[i - dym];
-    if (dyp) s += vi - v[i + dyp];
-    if (dzm) s += vi - v[i - dzm];
-    if (dzp) s += vi - v[i + dzp];
-    return s;
+// Jacobi scaling t = 1 / (1 + c deg) (Sec. III: t_ii = 1 / b_ii), one expression for every kernel.
+__device__ __forceinline__ float jacobi_t(float c, int deg) {
+    return __fdiv_rn(1.0f, __fmaf_rn(c, (float)deg, 1.0f));
 }
 
-// Neighbours of node i from the offset table: the sum of their values (FP64) and their count.
+// Float-float values h + l and their error-free building blocks: TwoSum (Knuth) and the product
+// error of a fused multiply-add.  Round-to-nearest intrinsics keep the compiler from contracting
+// or reordering them.
+struct FF {
+    float h, l;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ FF ff_sub(FF a, FF b) {
+    const FF s = two_sum(a.h, -b.h);
+    return two_sum(s.h, __fadd_rn(s.l, __fsub_rn(a.l, b.l)));
+}
+
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const float p = __fmul_rn(a.h, b.h);
+    const float e = __fmaf_rn(a.h, b.h, -p);
+    return two_sum(p, __fadd_rn(e, __fadd_rn(__fmul_rn(a.h, b.l), __fmul_rn(a.l, b.h))));
+}
+
+// Sum over the neighbours of node i of x_j in float-float (TwoSum chain of the high parts; low parts
+// and the chain's errors added in FP32), and their number.
 template <int TF>
-__device__ __forceinline__ double nbr_vals_d(const NbrTable &tb, uint32_t i, bool live, double vi,
-                                             const double *__restrict__ v, int &deg) {
+__device__ __forceinline__ FF nbr_sum_ff(const NbrTable &tb, uint32_t i, bool live, FF xi,
+                                         const float *__restrict__ xh, const float *__restrict__ xl, int &deg) {
     const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
     uint32_t dzm, dzp;
     if (TF == 1) {
@@ -460,75 +479,111 @@ __device__ __forceinline__ double nbr_vals_d(const NbrTable &tb, uint32_t i, boo
         dzp = live ? __ldg(tb.tzp + i) : 0u;
     }
     const int lane = threadIdx.x & 31;
-    double vl = __shfl_up_sync(0xffffffffu, vi, 1);
-    double vr = __shfl_down_sync(0xffffffffu, vi, 1);
+    float hl = __shfl_up_sync(0xffffffffu, xi.h, 1), ll = __shfl_up_sync(0xffffffffu, xi.l, 1);
+    float hr = __shfl_down_sync(0xffffffffu, xi.h, 1), lr = __shfl_down_sync(0xffffffffu, xi.l, 1);
     const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
     const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
-    if (lane == 0 && hxm) vl = __ldg(v + (i - 1));
-    if (lane == 31 && hxp) vr = __ldg(v + (i + 1));
-    double s = 0.0;
-    if (hxm) s += vl;
-    if (hxp) s += vr;
-    if (dym) s += __ldg(v + (i - dym));
-    if (dyp) s += __ldg(v + (i + dyp));
-    if (dzm) s += __ldg(v + (i - dzm));
-    if (dzp) s += __ldg(v + (i + dzp));
+    if (lane == 0 && hxm) {
+        hl = __ldg(xh + (i - 1));
+        ll = __ldg(xl + (i - 1));
+    }
+    if (lane == 31 && hxp) {
+        hr = __ldg(xh + (i + 1));
+        lr = __ldg(xl + (i + 1));
+    }
+    FF s = {0.0f, 0.0f};
+    auto add = [&](float h, float l) {
+        const FF t = two_sum(s.h, h);
+        s.h = t.h;
+        s.l = __fadd_rn(s.l, __fadd_rn(t.l, l));
+    };
+    if (hxm) add(hl, ll);
+    if (hxp) add(hr, lr);
+    if (dym) add(__ldg(xh + (i - dym)), __ldg(xl + (i - dym)));
+    if (dyp) add(__ldg(xh + (i + dyp)), __ldg(xl + (i + dyp)));
+    if (dzm) add(__ldg(xh + (i - dzm)), __ldg(xl + (i - dzm)));
+    if (dzp) add(__ldg(xh + (i + dzp)), __ldg(xl + (i + dzp)));
     deg = (int)hxm + (int)hxp + (dym != 0) + (dyp != 0) + (dzm != 0) + (dzp != 0);
     return s;
 }
 
-// Outer residual r = b - B x in FP64 (FIRST: x = b), t = 1 / (1 + c deg) (FP32), the FP32 copies r
-// and p = T r, d = 0; partials (r.r FP64, b.b (FIRST), r.Tr).  GB300 runs FP64 at a small fraction
-// of its FP32 rate and this pass is bound by it, so (L x)_i is formed as deg x_i - sum_j x_j (one
-// FMA after the neighbour sum) and the degree is counted in integers.
+// Outer residual r = b - B x = b - x - c (deg x_i - sum_j x_j) in float-float (FIRST: x = b, so
+// r = -c L b), rounded to FP32 for the inner solve; deg, p = T r, d = 0; partials (r.r and b.b
+// (FIRST) in FP64, r.Tr).  FP32 instructions only per node, apart from the two FP64 squares.
 template <bool FIRST, int TF>
-__global__ void __launch_bounds__(kThreads) k_mx_res(int64_t n, NbrTable tb, double c, MxVecs v,
-                                                     double *__restrict__ part, const MxScalars *__restrict__ sc) {
+__global__ void __launch_bounds__(kThreads) k_mx_res(int64_t n, NbrTable tb, FF c, MxVecs v,
+                                                     double *__restrict__ part, MxScalars *sc) {
     if (!FIRST && sc->done) return;
-    double acc[3] = {0.0, 0.0, 0.0};
+    if (FIRST && blockIdx.x == 0 && threadIdx.x == 0) sc->fresh = 1;
+    double rr = 0.0, bb = 0.0;
+    float rz = 0.0f;
     const int64_t ntile = (n + kThreads - 1) / kThreads;
-    const double *__restrict__ xs = FIRST ? v.b : v.x;  // FIRST: x = b, read from b (filled by k_mx_rhs)
+    const float *__restrict__ sh = FIRST ? v.bh : v.xh;  // FIRST: x = b, neighbours read from b
+    const float *__restrict__ sl = FIRST ? v.bl : v.xl;
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
         const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
         const bool live = i < (uint64_t)n;
-        double xi = 0.0, bi = 0.0;
+        FF xi = {0.0f, 0.0f}, bi = {0.0f, 0.0f};
         if (live) {
-            bi = __ldg(v.b + i);
-            xi = FIRST ? bi : __ldg(v.x + i);
+            bi = {__ldg(v.bh + i), __ldg(v.bl + i)};
+            xi = FIRST ? bi : FF{__ldg(v.xh + i), __ldg(v.xl + i)};
         }
         int deg = 0;
-        const double sx = nbr_vals_d<TF>(tb, i, live, xi, xs, deg);
+        const FF sx = nbr_sum_ff<TF>(tb, i, live, xi, sh, sl, deg);
         if (live) {
-            const double lx = fma((double)deg, xi, -sx);
-            const double ri = fma(-c, lx, bi - xi);
-            const float ti = 1.0f / (1.0f + (float)c * (float)deg);
-            const float r32 = (float)ri;
-            if (FIRST) v.x[i] = xi;
-            v.t[i] = ti;
+            const float fd = (float)deg;
+            const float ph = __fmul_rn(fd, xi.h);
+            const FF dx = two_sum(ph, __fadd_rn(__fmaf_rn(fd, xi.h, -ph), __fmul_rn(fd, xi.l)));  // deg x_i
+            const FF cl = ff_mul(c, ff_sub(dx, sx));                                             // c (L x)_i
+            const FF r = FIRST ? FF{-cl.h, -cl.l} : ff_sub(ff_sub(bi, xi), cl);
+            const float r32 = __fadd_rn(r.h, r.l);
+            const float ti = jacobi_t(c.h, deg);
+            if (FIRST) {
+                v.xh[i] = bi.h;
+                v.xl[i] = bi.l;
+            }
+            v.deg[i] = (uint8_t)deg;
             v.r[i] = r32;
-            v.p[i] = ti * r32;
+            v.p[i] = __fmul_rn(ti, r32);
             v.d[i] = 0.0f;
-            acc[0] = fma(ri, ri, acc[0]);
-            if (FIRST) acc[1] = fma(bi, bi, acc[1]);
-            acc[2] += (double)(r32 * (ti * r32));
+            rr = fma((double)r32, (double)r32, rr);
+            if (FIRST) {
+                const double b = (double)bi.h + (double)bi.l;
+                bb = fma(b, b, bb);
+            }
+            rz = __fmaf_rn(r32, __fmul_rn(ti, r32), rz);
         }
     }
+    double acc[3] = {rr, bb, (double)rz};
     __shared__ double out[3];
     block_sum_store<3>(acc, out);
     if (threadIdx.x < 3) part[(int64_t)blockIdx.x * 3 + threadIdx.x] = out[threadIdx.x];
 }
 
-// FIRST also fills b before the residual kernel reads neighbours' b (k_mx_res<FIRST> gathers b).
+// b = the stored DOM after the transformation: FP32 value and its residual as hi and lo.
 template <int PREC>
 __global__ void __launch_bounds__(kThreads) k_mx_rhs(int64_t n, const float *__restrict__ y2,
-                                                     const res_t *__restrict__ y2l, double *__restrict__ b) {
+                                                     const res_t *__restrict__ y2l, float *__restrict__ bh,
+                                                     float *__restrict__ bl) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = ld_value_d<PREC>(y2, y2l, i);
+    if (i >= n) return;
+    const float h = __ldg(y2 + i);
+    bh[i] = h;
+    bl[i] = (PREC == P_COMP) ? res_decode(__ldg(y2l + i), h) : 0.0f;
 }
 
+// Start of an outer iteration: the residual norms, the outer stop test, the next inner solve's
+// tolerance; sets both loop conditions to "not done".
 __global__ void __launch_bounds__(kThreads) k_mx_scal_out(const double *__restrict__ part, int64_t count, MxScalars *sc,
-                                                          int first, double rtol, int maxit) {
-    if (!first && sc->done) return;
+                                                          double rtol, int maxit, MxLoop loop) {
+    const int first = sc->fresh;
+    if (!first && sc->done) {
+        if (loop.cond && threadIdx.x == 0) {
+            cudaGraphSetConditional(loop.inner, 0u);
+            cudaGraphSetConditional(loop.outer, 0u);
+        }
+        return;
+    }
     const double rr = block_reduce_partials(part, count, 3, 0);
     const double bb = first ? block_reduce_partials(part, count, 3, 1) : 0.0;
     const double rz = block_reduce_partials(part, count, 3, 2);
@@ -541,6 +596,8 @@ __global__ void __launch_bounds__(kThreads) k_mx_scal_out(const double *__restri
             sc->notconv = 0;
             sc->maxit = maxit;
             sc->done = 0;
+            sc->guard = 0;
+            sc->fresh = 0;
         }
         sc->rr_out = rr;
         sc->relres = sc->bb > 0.0 ? sqrt(rr / sc->bb) : 0.0;
@@ -561,6 +618,10 @@ __global__ void __launch_bounds__(kThreads) k_mx_scal_out(const double *__restri
         sc->inner_done = sc->done;
         sc->ticket_a = 0u;
         sc->ticket_b = 0u;
+        if (loop.cond) {
+            cudaGraphSetConditional(loop.inner, sc->done ? 0u : 1u);
+            cudaGraphSetConditional(loop.outer, sc->done ? 0u : 1u);
+        }
     }
 }
 
@@ -648,11 +709,18 @@ __global__ void __launch_bounds__(kThreads) k_mx_spmv(int64_t n, NbrTable tb, fl
 }
 
 // The streaming kernels below move four nodes per thread and access (16-byte vectors: every FP32
-// array starts on a 16-byte boundary); the n % 4 last nodes go through a scalar tail, so the padding
-// after node n never enters a sum.
-__global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, MxVecs v, MxScalars *sc, double *__restrict__ part,
-                                                     int in_maxit) {
-    if (sc->inner_done) return;
+// array starts on a 16-byte boundary, the degrees on a 4-byte one); the n % 4 last nodes go through
+// a scalar tail, so the padding after node n never enters a sum.  c is the FP32 c of the inner
+// solve (the Jacobi table is built from it).
+__global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, float c, MxVecs v, MxScalars *sc,
+                                                     double *__restrict__ part, int in_maxit, MxLoop loop) {
+    if (sc->inner_done) {
+        if (loop.cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop.inner, 0u);
+        return;
+    }
+    __shared__ float tdeg[8];
+    if (threadIdx.x < 8) tdeg[threadIdx.x] = jacobi_t(c, (int)threadIdx.x);
+    __syncthreads();
     const float alpha = (float)sc->alpha;
     float a0 = 0.0f, a1 = 0.0f;
     const int64_t n4 = n >> 2;
@@ -661,10 +729,11 @@ __global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, MxVecs v, MxScal
     float4 *__restrict__ r4 = reinterpret_cast<float4 *>(v.r);
     const float4 *__restrict__ p4 = reinterpret_cast<const float4 *>(v.p);
     const float4 *__restrict__ q4 = reinterpret_cast<const float4 *>(v.q);
-    const float4 *__restrict__ t4 = reinterpret_cast<const float4 *>(v.t);
+    const uchar4 *__restrict__ g4 = reinterpret_cast<const uchar4 *>(v.deg);
     for (int64_t k = g0; k < n4; k += gs) {
         float4 d = d4[k], r = r4[k];
-        const float4 p = p4[k], q = q4[k], t = t4[k];
+        const float4 p = p4[k], q = q4[k];
+        const uchar4 g = g4[k];
         d.x += alpha * p.x;
         d.y += alpha * p.y;
         d.z += alpha * p.z;
@@ -675,14 +744,14 @@ __global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, MxVecs v, MxScal
         r.w -= alpha * q.w;
         d4[k] = d;
         r4[k] = r;
-        a0 += r.x * (t.x * r.x) + r.y * (t.y * r.y) + r.z * (t.z * r.z) + r.w * (t.w * r.w);
+        a0 += r.x * (tdeg[g.x] * r.x) + r.y * (tdeg[g.y] * r.y) + r.z * (tdeg[g.z] * r.z) + r.w * (tdeg[g.w] * r.w);
         a1 += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
     }
     for (int64_t i = 4 * n4 + g0; i < n; i += gs) {
         v.d[i] += alpha * v.p[i];
         const float ri = v.r[i] - alpha * v.q[i];
         v.r[i] = ri;
-        a0 += ri * (v.t[i] * ri);
+        a0 += ri * (tdeg[v.deg[i]] * ri);
         a1 += ri * ri;
     }
     double a[2] = {(double)a0, (double)a1};
@@ -704,81 +773,277 @@ __global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, MxVecs v, MxScal
                 sc->beta = rz / sc->rz;
                 sc->rz = rz;
             }
+            // the iteration limits above end every loop; this bound holds even if they did not
+            if (++sc->guard > (kMaxOuter + 2) * (in_maxit + 1)) {
+                sc->inner_done = 1;
+                sc->done = 1;
+                sc->notconv = 1;
+            }
+            if (loop.cond) cudaGraphSetConditional(loop.inner, sc->inner_done ? 0u : 1u);
         }
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_mx_p(int64_t n, MxVecs v, const MxScalars *__restrict__ sc) {
+__global__ void __launch_bounds__(kThreads) k_mx_p(int64_t n, float c, MxVecs v, const MxScalars *__restrict__ sc) {
     if (sc->inner_done) return;
+    __shared__ float tdeg[8];
+    if (threadIdx.x < 8) tdeg[threadIdx.x] = jacobi_t(c, (int)threadIdx.x);
+    __syncthreads();
     const float beta = (float)sc->beta;
     const int64_t n4 = n >> 2;
     const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
     float4 *__restrict__ p4 = reinterpret_cast<float4 *>(v.p);
     const float4 *__restrict__ r4 = reinterpret_cast<const float4 *>(v.r);
-    const float4 *__restrict__ t4 = reinterpret_cast<const float4 *>(v.t);
+    const uchar4 *__restrict__ g4 = reinterpret_cast<const uchar4 *>(v.deg);
     for (int64_t k = g0; k < n4; k += gs) {
         float4 p = p4[k];
-        const float4 r = r4[k], t = t4[k];
-        p.x = t.x * r.x + beta * p.x;
-        p.y = t.y * r.y + beta * p.y;
-        p.z = t.z * r.z + beta * p.z;
-        p.w = t.w * r.w + beta * p.w;
+        const float4 r = r4[k];
+        const uchar4 g = g4[k];
+        p.x = tdeg[g.x] * r.x + beta * p.x;
+        p.y = tdeg[g.y] * r.y + beta * p.y;
+        p.z = tdeg[g.z] * r.z + beta * p.z;
+        p.w = tdeg[g.w] * r.w + beta * p.w;
         p4[k] = p;
     }
-    for (int64_t i = 4 * n4 + g0; i < n; i += gs) v.p[i] = v.t[i] * v.r[i] + beta * v.p[i];
+    for (int64_t i = 4 * n4 + g0; i < n; i += gs) v.p[i] = tdeg[v.deg[i]] * v.r[i] + beta * v.p[i];
+}
+
+// x += d in float-float (TwoSum of the high part and d, then renormalised).
+__device__ __forceinline__ void ff_add_f(float &xh, float &xl, float d) {
+    const FF s = two_sum(xh, d);
+    const FF t = two_sum(s.h, __fadd_rn(s.l, xl));
+    xh = t.h;
+    xl = t.l;
 }
 
 __global__ void __launch_bounds__(kThreads) k_mx_x(int64_t n, MxVecs v, const MxScalars *__restrict__ sc) {
     if (sc->done) return;
-    const int64_t n2 = n >> 1;
+    const int64_t n4 = n >> 2;
     const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
-    double2 *__restrict__ x2 = reinterpret_cast<double2 *>(v.x);
-    const float2 *__restrict__ d2 = reinterpret_cast<const float2 *>(v.d);
-    for (int64_t k = g0; k < n2; k += gs) {
-        double2 x = x2[k];
-        const float2 d = d2[k];
-        x.x += (double)d.x;
-        x.y += (double)d.y;
-        x2[k] = x;
+    float4 *__restrict__ h4 = reinterpret_cast<float4 *>(v.xh);
+    float4 *__restrict__ l4 = reinterpret_cast<float4 *>(v.xl);
+    const float4 *__restrict__ d4 = reinterpret_cast<const float4 *>(v.d);
+    for (int64_t k = g0; k < n4; k += gs) {
+        float4 h = h4[k], l = l4[k];
+        const float4 d = d4[k];
+        ff_add_f(h.x, l.x, d.x);
+        ff_add_f(h.y, l.y, d.y);
+        ff_add_f(h.z, l.z, d.z);
+        ff_add_f(h.w, l.w, d.w);
+        h4[k] = h;
+        l4[k] = l;
     }
-    for (int64_t i = 2 * n2 + g0; i < n; i += gs) v.x[i] += (double)v.d[i];
+    for (int64_t i = 4 * n4 + g0; i < n; i += gs) ff_add_f(v.xh[i], v.xl[i], v.d[i]);
+}
+
+// The solution as the new stored DOM: h = RN(xh + xl) and the exact remainder as residual.
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_mx_out(int64_t n, MxVecs v, float *__restrict__ out,
+                                                     res_t *__restrict__ outl) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const FF s = two_sum(v.xh[i], v.xl[i]);
+    out[i] = s.h;
+    if (PREC == P_COMP) outl[i] = res_encode(s.l, s.h);
+}
+
+// ---- the mixed solve as one CUDA graph -------------------------------------------------------
+//
+//   k_mx_rhs -> k_mx_res<first> -> WHILE(outer) { k_mx_scal_out -> WHILE(inner) { k_mx_spmv ->
+//   k_mx_upd -> k_mx_p } -> k_mx_x -> k_mx_res } -> k_mx_out
+//
+// k_mx_scal_out sets both conditions to "not done" at the start of every outer iteration and
+// k_mx_upd clears the inner one when the inner solve stops, so the host launches the graph and
+// synchronises once per time step instead of polling every kBatch iterations.  Each loop is
+// bounded by the iteration limits (in_maxit, cg_maxit, kMaxOuter) and by the guard counter.  The
+// state buffers alternate between steps, so one graph is kept per parity of the DOM buffer.
+
+template <typename Tuple, size_t... I>
+void kernel_arg_ptrs(Tuple &t, void **a, std::index_sequence<I...>) {
+    ((a[I] = (void *)&std::get<I>(t)), ...);
+}
+
+// Adds a kernel node (kThreads threads per block) that depends on *dep (if not NULL).  The node
+// copies the argument values.
+template <typename... P, typename... A>
+cudaError_t add_kernel(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *dep, void (*fn)(P...),
+                       unsigned grid, A... a) {
+    static_assert(sizeof...(P) == sizeof...(A), "kernel argument count");
+    std::tuple<P...> vals(static_cast<P>(a)...);
+    void *args[sizeof...(P) > 0 ? sizeof...(P) : 1];
+    kernel_arg_ptrs(vals, args, std::index_sequence_for<P...>{});
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)fn;
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(kThreads);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    return cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &kp);
+}
+
+// Adds a while node after *dep; its body graph is returned in *body.
+cudaError_t add_while(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_t *dep,
+                      cudaGraphConditionalHandle h, cudaGraph_t *body) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    const cudaError_t e = cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &cp);
+    if (e == cudaSuccess) *body = cp.conditional.phGraph_out[0];
+    return e;
+}
+
+struct MxGraphKey {
+    const void *ptr[12];
+    int64_t n;
+    double c, rtol;
+    int32_t maxit, G, prec, tf;
+};
+
+struct MxGraphCache {
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    MxGraphKey key[2];
+};
+
+void mx_graph_drop(MxGraphCache *gc, int slot) {
+    if (gc->exec[slot]) cudaGraphExecDestroy(gc->exec[slot]);
+    if (gc->graph[slot]) cudaGraphDestroy(gc->graph[slot]);
+    gc->exec[slot] = nullptr;
+    gc->graph[slot] = nullptr;
+}
+
+template <int PREC, int TF>
+cudaError_t mx_graph_build(vga_sim *s, const MxVecs &v, const NbrTable &tb, FF cff, int G, int in_maxit,
+                           double *part_a, double *part_b, MxScalars *sc, cudaGraph_t *gout) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    MxLoop loop = {0, 0, 1};
+    cudaGraphNode_t n_rhs, n_res0, n_outer, n_out, n_scal, n_inner, n_x, n_res, n_spmv, n_upd, n_p;
+    cudaGraph_t body_o = nullptr, body_i = nullptr;
+    const unsigned ge = grid_for(s->n, kThreads);
+    const double rtol = s->params.cg_rtol;
+    const int maxit = s->params.cg_maxit;
+    const float ch = cff.h;
+#define MX_TRY(x)                        \
+    do {                                 \
+        e = (x);                         \
+        if (e != cudaSuccess) goto fail; \
+    } while (0)
+    MX_TRY(cudaGraphConditionalHandleCreate(&loop.outer, g, 1u, cudaGraphCondAssignDefault));
+    MX_TRY(add_kernel(&n_rhs, g, nullptr, k_mx_rhs<PREC>, ge, s->n, s->comp(1), s->lcomp(1), v.bh, v.bl));
+    MX_TRY(add_kernel(&n_res0, g, &n_rhs, k_mx_res<true, TF>, G, s->n, tb, cff, v, part_a, sc));
+    MX_TRY(add_while(&n_outer, g, &n_res0, loop.outer, &body_o));
+    MX_TRY(add_kernel(&n_out, g, &n_outer, k_mx_out<PREC>, ge, s->n, v, s->spare(1), s->lspare(1)));
+    MX_TRY(cudaGraphConditionalHandleCreate(&loop.inner, body_o, 0u, 0u));
+    MX_TRY(add_kernel(&n_scal, body_o, nullptr, k_mx_scal_out, 1u, part_a, (int64_t)G, sc, rtol, maxit, loop));
+    MX_TRY(add_while(&n_inner, body_o, &n_scal, loop.inner, &body_i));
+    MX_TRY(add_kernel(&n_x, body_o, &n_inner, k_mx_x, G, s->n, v, sc));
+    MX_TRY(add_kernel(&n_res, body_o, &n_x, k_mx_res<false, TF>, G, s->n, tb, cff, v, part_a, sc));
+    MX_TRY(add_kernel(&n_spmv, body_i, nullptr, k_mx_spmv<TF>, G, s->n, tb, ch, v, part_a, sc));
+    MX_TRY(add_kernel(&n_upd, body_i, &n_spmv, k_mx_upd, G, s->n, ch, v, sc, part_b, in_maxit, loop));
+    MX_TRY(add_kernel(&n_p, body_i, &n_upd, k_mx_p, G, s->n, ch, v, sc));
+#undef MX_TRY
+    *gout = g;
+    return cudaSuccess;
+fail:
+    cudaGraphDestroy(g);
+    return e;
 }
 
 template <int PREC>
 vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b, MxScalars *sc) {
     const double c = s->params.D * s->params.dt;
+    const float ch = (float)c;
+    const FF cff = {ch, (float)(c - (double)ch)};
     cudaStream_t st = s->stream;
     NbrTable tb;
     VGA_TRY(sim_nbr_table(s, &tb));
+    // 8.25 npad FP32 words inside the 5 npad doubles of the vector buffer
     MxVecs v;
-    v.x = base;
-    v.b = base + s->npad;
-    float *f = reinterpret_cast<float *>(base + 2 * s->npad);
-    v.r = f;
-    v.p = f + s->npad;
-    v.q = f + 2 * s->npad;
-    v.d = f + 3 * s->npad;
-    v.t = f + 4 * s->npad;
+    float *f = reinterpret_cast<float *>(base);
+    v.xh = f;
+    v.xl = f + s->npad;
+    v.bh = f + 2 * s->npad;
+    v.bl = f + 3 * s->npad;
+    v.r = f + 4 * s->npad;
+    v.p = f + 5 * s->npad;
+    v.q = f + 6 * s->npad;
+    v.d = f + 7 * s->npad;
+    v.deg = reinterpret_cast<uint8_t *>(f + 8 * s->npad);
     const int G = (int)std::min<int64_t>(kMxBlocks, grid_for(s->n, kThreads));
     const int in_maxit = 200;
+    MxScalars *h = reinterpret_cast<MxScalars *>(s->h_cg);
+
+    if (!s->cg_host_loop && !s->mx_graph_failed) {
+        if (!s->mx_graph) s->mx_graph = new (std::nothrow) MxGraphCache();
+        MxGraphCache *gc = static_cast<MxGraphCache *>(s->mx_graph);
+        if (gc) {
+            const int slot = s->cur[1] & 1;
+            MxGraphKey key;
+            std::memset(&key, 0, sizeof(key));
+            const void *ptrs[12] = {base, part_a, part_b, sc, s->comp(1), s->lcomp(1), s->spare(1), s->lspare(1),
+                                    tb.ty, tb.tz, tb.tzm, tb.tzp};
+            std::memcpy(key.ptr, ptrs, sizeof(ptrs));
+            key.n = s->n;
+            key.c = c;
+            key.rtol = s->params.cg_rtol;
+            key.maxit = s->params.cg_maxit;
+            key.G = G;
+            key.prec = PREC;
+            key.tf = tb.tz ? 1 : 0;
+            if (!gc->exec[slot] || std::memcmp(&key, &gc->key[slot], sizeof(key)) != 0) {
+                mx_graph_drop(gc, slot);
+                cudaError_t e = tb.tz ? mx_graph_build<PREC, 1>(s, v, tb, cff, G, in_maxit, part_a, part_b, sc, &gc->graph[slot])
+                                      : mx_graph_build<PREC, 0>(s, v, tb, cff, G, in_maxit, part_a, part_b, sc, &gc->graph[slot]);
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&gc->exec[slot], gc->graph[slot], 0);
+                if (e == cudaSuccess) {
+                    gc->key[slot] = key;
+                } else {
+                    // no conditional graph nodes here: keep the host-driven loop from now on
+                    mx_graph_drop(gc, slot);
+                    (void)cudaGetLastError();
+                    s->mx_graph_failed = true;
+                }
+            }
+            if (gc->exec[slot]) {
+                timing_begin(s, VGA_KERNEL_PCG_STENCIL);
+                VGA_CUDA(cudaGraphLaunch(gc->exec[slot], st));
+                timing_end(s);
+                VGA_CUDA(cudaMemcpyAsync(h, sc, sizeof(MxScalars), cudaMemcpyDeviceToHost, st));
+                VGA_CUDA(cudaStreamSynchronize(st));
+                s->graph_launches += 1;
+                s->launches += 3 + 3 * (int64_t)h->outer + 3 * (int64_t)h->iters;  // kernels the graph ran
+                s->cur[1] ^= 1;
+                s->cg_iterations += h->iters;
+                s->cg_last_relres = h->relres;
+                return h->notconv ? VGA_ERR_NOT_CONVERGED : VGA_OK;
+            }
+        }
+    }
+
+    // host-driven loop: the same kernels, the done flags polled every kBatch inner iterations
+    const MxLoop noloop = {0, 0, 0};
     timing_begin(s, VGA_KERNEL_PCG_STENCIL);
-    k_mx_rhs<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->comp(1), s->lcomp(1), v.b);
-    if (tb.tz) k_mx_res<true, 1><<<G, kThreads, 0, st>>>(s->n, tb, c, v, part_a, sc);
-    else k_mx_res<true, 0><<<G, kThreads, 0, st>>>(s->n, tb, c, v, part_a, sc);
+    k_mx_rhs<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->comp(1), s->lcomp(1), v.bh, v.bl);
+    if (tb.tz) k_mx_res<true, 1><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
+    else k_mx_res<true, 0><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
     timing_end(s);
-    k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, 1, s->params.cg_rtol, s->params.cg_maxit);
+    k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, s->params.cg_rtol, s->params.cg_maxit, noloop);
     VGA_CHECK_LAUNCH();
     s->launches += 3;
-    MxScalars *h = reinterpret_cast<MxScalars *>(s->h_cg);
     for (int guard = 0; guard < 100000; ++guard) {
         for (int k = 0; k < kBatch; ++k) {
             timing_begin(s, VGA_KERNEL_PCG_STENCIL);
-            if (tb.tz) k_mx_spmv<1><<<G, kThreads, 0, st>>>(s->n, tb, (float)c, v, part_a, sc);
-            else k_mx_spmv<0><<<G, kThreads, 0, st>>>(s->n, tb, (float)c, v, part_a, sc);
+            if (tb.tz) k_mx_spmv<1><<<G, kThreads, 0, st>>>(s->n, tb, ch, v, part_a, sc);
+            else k_mx_spmv<0><<<G, kThreads, 0, st>>>(s->n, tb, ch, v, part_a, sc);
             timing_end(s);
             timing_begin(s, VGA_KERNEL_PCG_VECTOR);
-            k_mx_upd<<<G, kThreads, 0, st>>>(s->n, v, sc, part_b, in_maxit);
-            k_mx_p<<<G, kThreads, 0, st>>>(s->n, v, sc);
+            k_mx_upd<<<G, kThreads, 0, st>>>(s->n, ch, v, sc, part_b, in_maxit, noloop);
+            k_mx_p<<<G, kThreads, 0, st>>>(s->n, ch, v, sc);
             timing_end(s);
         }
         VGA_CHECK_LAUNCH();
@@ -787,18 +1052,18 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
         VGA_CUDA(cudaStreamSynchronize(st));
         if (h->done) break;
         if (h->inner_done) {
-            // x += d, then the FP64 residual of the new x and the next inner solve's start
+            // x += d, then the true residual of the new x and the next inner solve's start
             timing_begin(s, VGA_KERNEL_PCG_STENCIL);
             k_mx_x<<<G, kThreads, 0, st>>>(s->n, v, sc);
-            if (tb.tz) k_mx_res<false, 1><<<G, kThreads, 0, st>>>(s->n, tb, c, v, part_a, sc);
-            else k_mx_res<false, 0><<<G, kThreads, 0, st>>>(s->n, tb, c, v, part_a, sc);
+            if (tb.tz) k_mx_res<false, 1><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
+            else k_mx_res<false, 0><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
             timing_end(s);
-            k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, 0, s->params.cg_rtol, s->params.cg_maxit);
+            k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, s->params.cg_rtol, s->params.cg_maxit, noloop);
             VGA_CHECK_LAUNCH();
             s->launches += 3;
         }
     }
-    k_cg_out<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, v.x, s->spare(1), s->lspare(1), PREC == P_COMP);
+    k_mx_out<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, v, s->spare(1), s->lspare(1));
     VGA_CHECK_LAUNCH();
     ++s->launches;
     s->cur[1] ^= 1;
@@ -808,6 +1073,15 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
 }
 
 }  // namespace
+
+void sim_mx_graph_release(vga_sim *s) {
+    MxGraphCache *gc = static_cast<MxGraphCache *>(s->mx_graph);
+    if (!gc) return;
+    mx_graph_drop(gc, 0);
+    mx_graph_drop(gc, 1);
+    delete gc;
+    s->mx_graph = nullptr;
+}
 
 vga_status sim_step_implicit(vga_sim *s, int64_t n_steps) {
     if (n_steps <= 0 || s->n == 0) {

@@ -194,7 +194,11 @@ struct vga_sim {
     int64_t cg_count = 0;
     double *cg_scalars = nullptr;  // device scalars of the PCG recurrence
     double *h_cg = nullptr;        // pinned mirror of the PCG scalars
-    bool cg_mixed = true;          // implicit solve: FP64 refinement around FP32 PCG (unit conductances)
+    bool cg_mixed = true;          // implicit solve: float-float refinement around FP32 PCG (unit conductances)
+    bool cg_host_loop = false;     // mixed solve: loop driven from the host instead of one CUDA graph
+    bool mx_graph_failed = false;  // graph construction failed once: host-driven loop from then on
+    void *mx_graph = nullptr;      // cached graphs of the mixed solve (pcg.cu)
+    int64_t graph_launches = 0;    // CUDA graph launches of the mixed solve
     int64_t steps_done = 0;
     int64_t cg_iterations = 0;
     double cg_last_relres = 0.0;
@@ -278,6 +282,7 @@ StateIO state_io(vga_sim *s);          // current buffers in, spare buffers out
 StateIO state_io_inplace(vga_sim *s);  // current buffers in and out
 // pcg.cu
 vga_status sim_step_implicit(vga_sim *s, int64_t n_steps);
+void sim_mx_graph_release(vga_sim *s);  // the cached graphs of the mixed solve
 // adjoint.cu
 vga_status sim_adjoint_forward(vga_sim *s, int64_t N, int64_t ckpt);
 vga_status sim_adjoint_backward(vga_sim *s, const double *d_lamN, double *d_lam0, double *grad8, double *h_gtheta);

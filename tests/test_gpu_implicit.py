@@ -52,10 +52,14 @@ def test_implicit_block_weights_and_async(vga, oracle_lib):
         assert rel_l2(got[c], ref[c]) <= 1e-5, c
 
 
-def test_not_converged_reported(vga, oracle_lib):
+@pytest.mark.parametrize("solver", [1, 2, 0])
+def test_not_converged_reported(vga, oracle_lib, solver):
+    """cg_maxit reached before cg_rtol: every solver, including the graph-driven loops, stops and
+    reports it."""
     img, og, g, X0 = _setup(vga, oracle_lib, (24, 24, 24), 0.25, 3)
     p = synth.paper_params(dt=50 * 0.9 / (6 * synth.D_DOM), scheme=1, cg_rtol=1e-14, cg_maxit=2)
     sim = vga.Sim(g, p)
+    sim.set_solver(solver)
     sim.set_masses(X0)
     with pytest.raises(vga.VgaError) as e:
         sim.step(1)
@@ -75,7 +79,7 @@ def test_zero_dom(vga):
 
 @pytest.mark.parametrize("rtol", [1e-6, 1e-8, 1e-10])
 def test_mixed_refinement_matches_fp64_pcg(vga, oracle_lib, rtol):
-    """The default implicit solver (FP64 refinement around FP32 PCG) and the FP64 PCG both land
+    """The default implicit solver (float-float refinement around FP32 PCG) and the FP64 PCG both land
     within the requested tolerance of the oracle's solution; the mixed solver's reported residual
     is the true one, so it is at most rtol."""
     img, og, g, X0 = _setup(vga, oracle_lib, (40, 40, 40), 0.2, 7)
@@ -105,3 +109,33 @@ def test_unknown_solver_rejected(vga):
     sim = vga.Sim(g, synth.paper_params(scheme=1))
     with pytest.raises(vga.VgaError):
         sim.set_solver(7)
+
+
+def test_mixed_graph_loop_matches_host_loop(vga, oracle_lib):
+    """The mixed solve as one CUDA graph (device-side while loops) and driven from the host run the
+    same kernels in the same order: the same bits and iteration counts, over an odd number of steps
+    (both DOM buffer parities, cached graphs reused), and one graph launch per step."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (40, 36, 44), 0.2, 11)
+    p = synth.paper_params(dt=10 * 0.9 / (6 * synth.D_DOM), scheme=1, cg_rtol=1e-9, cg_maxit=2000)
+    out, stats = {}, {}
+    for solver in (vga.VGA_SOLVER_MIXED_REFINEMENT, vga.VGA_SOLVER_MIXED_HOST_LOOP):
+        sim = vga.Sim(g, p)
+        sim.set_solver(solver)
+        sim.set_masses(X0)
+        for k in (1, 2, 4):
+            sim.step(k)
+        out[solver] = sim.save_state()
+        stats[solver] = sim.stats()
+        sim.close()
+    assert out[1] == out[2]
+    assert stats[1]["cg_iterations"] == stats[2]["cg_iterations"] > 0
+    assert stats[1]["cg_last_relres"] == stats[2]["cg_last_relres"] <= 1e-9
+    assert stats[1]["graph_launches"] == 7
+    assert stats[2]["graph_launches"] == 0
+    ref, status, _, _ = oracle_lib.implicit_run(og.nbr, p, X0, 7, rtol=1e-13)
+    assert status == 0
+    last = vga.Sim(g, p)
+    last.load_state(out[1])
+    got = last.get_masses()
+    for c in range(5):
+        assert rel_l2(got[c], ref[c]) <= 1e-5, c
