@@ -292,6 +292,8 @@ def bench_ours(a):
     variant = best.get("variant")
     kname = {0: "k_stencil (chunk decode, direct loads)", 1: "k_stencil_staged (chunk decode, bulk-copy staging)",
              2: "k_stencil_table (neighbour-offset table)",
+             4: "k_stencil_tablev (neighbour-offset table, two nodes per thread, 8-byte vector streams)",
+             5: "k_stencil_tablev (neighbour-offset table, four nodes per thread, 16-byte vector streams)",
              3: f"k_wave (neighbour-offset table; {S - 1} fused passes per persistent launch as an L2 wavefront, "
                 f"chunks of {best.get('chunk')} nodes, {best.get('depth')} passes per block)"}.get(variant, "k_stencil")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -18,6 +18,7 @@
 #include <tuple>
 #include <vector>
 
+#include "grid_sync.cuh"
 #include "physics.cuh"
 #include "stencil.cuh"
 #include "vga_internal.cuh"
@@ -27,7 +28,6 @@ namespace {
 
 constexpr int kTile = 256;
 constexpr int kBatchGroup = 4;  // nodes per thread in the fused passes
-constexpr uint32_t kBarrierSpin = 1u << 26;
 
 struct BInst {
     int64_t start;  // first node of the instance in the concatenated range (multiple of kTile)
@@ -46,43 +46,6 @@ struct BatchArgs {
     unsigned *bar;  // [0] arrivals, [1] generation
     int32_t *err;
 };
-
-// Grid-wide barrier for a cooperative launch.  Bounded: on timeout (or an earlier error) it sets
-// *err and returns false; callers then stop.
-__device__ bool grid_barrier(unsigned *bar, int32_t *err) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ok = 1;
-        volatile unsigned *vgen = bar + 1;
-        volatile int32_t *verr = err;
-        if (*verr) {
-            ok = 0;
-        } else {
-            const unsigned gen = *vgen;
-            __threadfence();
-            const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-            if (arrived == gridDim.x) {
-                bar[0] = 0u;
-                __threadfence();
-                atomicAdd(bar + 1, 1u);
-            } else {
-                uint32_t it = 0;
-                while (*vgen == gen) {
-                    if (*verr || ++it > kBarrierSpin) {
-                        atomicExch(err, 2);
-                        ok = 0;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            __threadfence();
-        }
-    }
-    __syncthreads();
-    return ok != 0;
-}
 
 template <int TR, int PREC, int TF>
 __global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
