@@ -177,10 +177,8 @@ vga_status vga_sim_get_state_f32(vga_sim *s, float *x, int32_t on_device);
  * solver).  The whole mixed solve runs as one CUDA graph whose outer and inner loops are
  * conditional (while) nodes set by the solver's own kernels, so the host synchronises once per
  * time step; where the driver cannot build such a graph the solve falls back to the host-driven
- * loop.  The inner solve is one persistent cooperative kernel (grid barriers that give up after a
- * bounded wait: VGA_ERR_TIMEOUT).  VGA_SOLVER_MIXED_HOST_LOOP: the same solver with its outer loop
- * driven from the host (one synchronisation per outer iteration); the same kernels in the same
- * order, so the same bits.
+ * loop.  VGA_SOLVER_MIXED_HOST_LOOP: the same solver with its loops driven from the host (the done
+ * flags polled every 8 inner iterations); the same kernels in the same order, so the same bits.
  * Errors: VGA_ERR_INVALID_ARG. */
 #define VGA_SOLVER_FP64_PCG 0
 #define VGA_SOLVER_MIXED_REFINEMENT 1

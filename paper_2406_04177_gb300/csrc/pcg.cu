@@ -23,7 +23,6 @@
 #include <tuple>
 #include <utility>
 
-#include "grid_sync.cuh"
 #include "stencil.cuh"
 #include "vga_internal.cuh"
 
@@ -371,10 +370,16 @@ vga_status solve(vga_sim *s, CgVecs v, double *part_chunk, double *part_ew, CgSc
 // ||b - B x||_2 <= rtol ||b||_2 (the true residual, not the recurrence; ||r||^2 and ||b||^2 are
 // accumulated in FP64).  Every reduction is a fixed-order block-partial sum.
 //
-// One outer iteration: k_mx_scal_out (norms, stop test), k_mx_inner (the whole inner solve in one
-// persistent launch), k_mx_x (x += d), k_mx_res (the next true residual).  The Jacobi scaling
-// T = diag(1 / (1 + c deg_i)) is not stored: each node keeps its degree in one byte and the kernels
-// look t up in a 7-entry table computed by the same expression everywhere.
+// Kernels of one inner iteration (three launches; no single-block scalar kernels):
+//   k_mx_spmv   q = B p (four nodes per thread), partial p.q; the last block to finish forms alpha
+//   k_mx_upd    d += alpha p, r -= alpha q, partials r.Tr and r.r; the last block tests the inner
+//               stop and forms beta
+//   k_mx_p      p = T r + beta p
+// The Jacobi scaling T = diag(1 / (1 + c deg_i)) is not stored: each node keeps its degree in one
+// byte and the kernels look t up in a 7-entry table computed by the same expression everywhere.
+// "Last block": each block stores its partials, fences, and takes a ticket from a counter; the
+// block that draws the final ticket sums all partials in block order (so the result does not
+// depend on which block that is) and resets the counter.  No block waits for another.
 
 constexpr double kInnerTol = 1e-4;  // reduction asked of one FP32 inner solve
 constexpr int kMxBlocks = 2432;     // grid of the mixed-solver kernels: 152 SMs x 16 (grid-stride)
@@ -383,16 +388,15 @@ constexpr int kMaxOuter = 64;
 struct MxScalars {
     double bb, rr_out, rz, alpha, beta, rr_in, stop_in, relres, rtol2;
     int32_t done, inner_done, iters, in_iters, notconv, maxit, outer;
-    int32_t fresh;  // set by the first residual pass: the next k_mx_scal_out starts a solve
-    int32_t guard;  // inner iterations of this solve (a bound on the loops)
-    unsigned bar[2];  // grid barrier of the persistent inner solve (arrivals, generation)
-    int32_t err;      // nonzero: a grid barrier gave up
+    uint32_t ticket_a, ticket_b;  // arrival counters of the last-block reductions (0 between launches)
+    int32_t fresh;                // set by the first residual pass: the next k_mx_scal_out starts a solve
+    int32_t guard;                // inner iterations of this solve (a bound on the device-side loops)
 };
 
-// The outer loop on the device (the solve as one CUDA graph): k_mx_scal_out sets the while-node
-// condition.  cond = 0 outside a graph (host-driven loop).
+// Device-side loops (the solve as one CUDA graph): the kernels that decide whether a loop goes on
+// set the while-node conditions.  cond = 0 outside a graph (host-driven loop).
 struct MxLoop {
-    cudaGraphConditionalHandle outer;
+    cudaGraphConditionalHandle outer, inner;
     int cond;
 };
 
@@ -404,6 +408,23 @@ __device__ double block_reduce_partials_cg(const double *part, int64_t count, in
     __shared__ double out[1];
     block_sum_store<1>(acc, out);
     return out[0];
+}
+
+// Called by every thread once the block's partials are stored: true in the block that arrives
+// last, which then sees every block's partials.  The counter is reset for the next launch.  No
+// block waits for another.
+__device__ __forceinline__ bool last_block(uint32_t *ticket) {
+    __shared__ int last;
+    __threadfence();  // the partials stored by this thread are visible before the arrival
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t t = atomicAdd(ticket, 1u);
+        last = (t == gridDim.x - 1) ? 1 : 0;
+        if (last) *ticket = 0u;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last != 0;
 }
 
 // x and b: hi and lo parts; r, p, q, d: the FP32 inner solve; deg: node degree (0..6).
@@ -557,7 +578,10 @@ __global__ void __launch_bounds__(kThreads) k_mx_scal_out(const double *__restri
                                                           double rtol, int maxit, MxLoop loop) {
     const int first = sc->fresh;
     if (!first && sc->done) {
-        if (loop.cond && threadIdx.x == 0) cudaGraphSetConditional(loop.outer, 0u);
+        if (loop.cond && threadIdx.x == 0) {
+            cudaGraphSetConditional(loop.inner, 0u);
+            cudaGraphSetConditional(loop.outer, 0u);
+        }
         return;
     }
     const double rr = block_reduce_partials(part, count, 3, 0);
@@ -574,9 +598,6 @@ __global__ void __launch_bounds__(kThreads) k_mx_scal_out(const double *__restri
             sc->done = 0;
             sc->guard = 0;
             sc->fresh = 0;
-            sc->bar[0] = 0u;
-            sc->bar[1] = 0u;
-            sc->err = 0;
         }
         sc->rr_out = rr;
         sc->relres = sc->bb > 0.0 ? sqrt(rr / sc->bb) : 0.0;
@@ -595,43 +616,36 @@ __global__ void __launch_bounds__(kThreads) k_mx_scal_out(const double *__restri
         sc->rr_in = rr;
         sc->in_iters = 0;
         sc->inner_done = sc->done;
-        if (loop.cond) cudaGraphSetConditional(loop.outer, sc->done ? 0u : 1u);
+        sc->ticket_a = 0u;
+        sc->ticket_b = 0u;
+        if (loop.cond) {
+            cudaGraphSetConditional(loop.inner, sc->done ? 0u : 1u);
+            cudaGraphSetConditional(loop.outer, sc->done ? 0u : 1u);
+        }
     }
 }
 
-// ---- the inner FP32 Jacobi-PCG as one persistent cooperative kernel ---------------------------
-//
-// One iteration = three phases over the grid, separated by grid barriers:
-//   A  q = B p (four nodes per thread), block partials of p.q
-//   B  d += alpha p, r -= alpha q, block partials of r.Tr and r.r
-//   C  p = T r + beta p
-// After A and B every block sums all block partials itself, in block order, so every block holds
-// the same alpha, beta and stop decision without any further exchange.  The launch keeps all its
-// blocks resident (cooperative launch, grid = resident blocks), each barrier is bounded
-// (grid_sync.cuh), and the loop ends at the inner stop, at in_maxit, at cg_maxit, or on a barrier
-// that gave up (sc->err; the solve then reports VGA_ERR_TIMEOUT).
-
-// Phase A over this block's share of the nodes: q = B p in FP32; returns the thread's part of p.q.
+// q = B p in FP32 with four consecutive nodes per thread (16-byte accesses of p, q and the offset
+// table; the -x neighbour of the first node and the +x neighbour of the last come from the adjacent
+// lanes), partial p.q; the block that finishes last forms alpha = r.Tr / p.q.
 template <int TF>
-__device__ __forceinline__ float inner_spmv(uint32_t nn, const NbrTable &tb, float c, const MxVecs &v) {
+__global__ void __launch_bounds__(kThreads) k_mx_spmv(int64_t n, NbrTable tb, float c, MxVecs v,
+                                                      double *__restrict__ part, MxScalars *sc) {
+    if (sc->inner_done) return;
     constexpr int K = 4;
     float acc = 0.0f;
     const float *__restrict__ p = v.p;
     float *__restrict__ q = v.q;
+    const uint32_t nn = (uint32_t)n;
     const int lane = threadIdx.x & 31;
-    const int64_t nsup = ((int64_t)nn + (int64_t)kThreads * K - 1) / ((int64_t)kThreads * K);
+    const int64_t nsup = (n + (int64_t)kThreads * K - 1) / ((int64_t)kThreads * K);
     for (int64_t sup = blockIdx.x; sup < nsup; sup += gridDim.x) {
         const uint32_t i0 = (uint32_t)(sup * kThreads * K + (int64_t)threadIdx.x * K);
         const bool full = i0 + K <= nn;
         float pv[K];
         uint32_t ty[K], zm[K], zp[K];
         if (full) {
-            // p was written earlier in this launch: read it at L2 (not through the read-only cache)
-            const float4 w = __ldcg(reinterpret_cast<const float4 *>(p + i0));
-            pv[0] = w.x;
-            pv[1] = w.y;
-            pv[2] = w.z;
-            pv[3] = w.w;
+            ldg_floats<K>(p + i0, pv);
             ldg_words_k<K, true>(tb.ty, i0, nn, ty);
             if (TF == 1) {
                 ldg_words_k<K, true>(tb.tz, i0, nn, zm);
@@ -641,7 +655,7 @@ __device__ __forceinline__ float inner_spmv(uint32_t nn, const NbrTable &tb, flo
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < K; ++k) pv[k] = i0 + k < nn ? __ldcg(p + i0 + k) : 0.0f;
+            for (int k = 0; k < K; ++k) pv[k] = i0 + k < nn ? __ldg(p + i0 + k) : 0.0f;
             ldg_words_k<K, false>(tb.ty, i0, nn, ty);
             if (TF == 1) {
                 ldg_words_k<K, false>(tb.tz, i0, nn, zm);
@@ -659,8 +673,8 @@ __device__ __forceinline__ float inner_spmv(uint32_t nn, const NbrTable &tb, flo
         }
         float pl = __shfl_up_sync(0xffffffffu, pv[K - 1], 1);
         float pr = __shfl_down_sync(0xffffffffu, pv[0], 1);
-        if (lane == 0 && ((ty[0] >> 15) & 1u)) pl = __ldcg(p + (i0 - 1));
-        if (lane == 31 && (ty[K - 1] >> 31)) pr = __ldcg(p + (i0 + K));
+        if (lane == 0 && ((ty[0] >> 15) & 1u)) pl = __ldg(p + (i0 - 1));
+        if (lane == 31 && (ty[K - 1] >> 31)) pr = __ldg(p + (i0 + K));
         float qv[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -669,30 +683,46 @@ __device__ __forceinline__ float inner_spmv(uint32_t nn, const NbrTable &tb, flo
             float sum = 0.0f;
             if ((ty[k] >> 15) & 1u) sum += vi - (k == 0 ? pl : pv[k > 0 ? k - 1 : 0]);
             if (ty[k] >> 31) sum += vi - (k == K - 1 ? pr : pv[k < K - 1 ? k + 1 : 0]);
-            if (dym) sum += vi - __ldcg(p + (i0 + k - dym));
-            if (dyp) sum += vi - __ldcg(p + (i0 + k + dyp));
-            if (zm[k]) sum += vi - __ldcg(p + (i0 + k - zm[k]));
-            if (zp[k]) sum += vi - __ldcg(p + (i0 + k + zp[k]));
+            if (dym) sum += vi - __ldg(p + (i0 + k - dym));
+            if (dyp) sum += vi - __ldg(p + (i0 + k + dyp));
+            if (zm[k]) sum += vi - __ldg(p + (i0 + k - zm[k]));
+            if (zp[k]) sum += vi - __ldg(p + (i0 + k + zp[k]));
             qv[k] = vi + c * sum;
             if (i0 + k < nn) acc += vi * qv[k];
         }
         if (full) {
-            *reinterpret_cast<float4 *>(q + i0) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+            st_floats<K>(q + i0, qv);
         } else {
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 if (i0 + k < nn) q[i0 + k] = qv[k];
         }
     }
-    return acc;
+    double a[1] = {(double)acc};
+    __shared__ double out[1];
+    block_sum_store<1>(a, out);
+    if (threadIdx.x == 0) part[blockIdx.x] = out[0];
+    if (last_block(&sc->ticket_a)) {
+        const double pq = block_reduce_partials_cg(part, gridDim.x, 1, 0);
+        if (threadIdx.x == 0) sc->alpha = pq > 0.0 ? sc->rz / pq : 0.0;
+    }
 }
 
-// Phase B (four nodes per thread and access; the n % 4 last nodes through a scalar tail):
-// d += alpha p, r -= alpha q; the thread's parts of r.Tr (a0) and r.r (a1).
-__device__ __forceinline__ void inner_update(int64_t n, float alpha, const float *tdeg, const MxVecs &v, float &a0,
-                                             float &a1) {
-    a0 = 0.0f;
-    a1 = 0.0f;
+// The streaming kernels below move four nodes per thread and access (16-byte vectors: every FP32
+// array starts on a 16-byte boundary, the degrees on a 4-byte one); the n % 4 last nodes go through
+// a scalar tail, so the padding after node n never enters a sum.  c is the FP32 c of the inner
+// solve (the Jacobi table is built from it).
+__global__ void __launch_bounds__(kThreads) k_mx_upd(int64_t n, float c, MxVecs v, MxScalars *sc,
+                                                     double *__restrict__ part, int in_maxit, MxLoop loop) {
+    if (sc->inner_done) {
+        if (loop.cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(loop.inner, 0u);
+        return;
+    }
+    __shared__ float tdeg[8];
+    if (threadIdx.x < 8) tdeg[threadIdx.x] = jacobi_t(c, (int)threadIdx.x);
+    __syncthreads();
+    const float alpha = (float)sc->alpha;
+    float a0 = 0.0f, a1 = 0.0f;
     const int64_t n4 = n >> 2;
     const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
     float4 *__restrict__ d4 = reinterpret_cast<float4 *>(v.d);
@@ -701,9 +731,9 @@ __device__ __forceinline__ void inner_update(int64_t n, float alpha, const float
     const float4 *__restrict__ q4 = reinterpret_cast<const float4 *>(v.q);
     const uchar4 *__restrict__ g4 = reinterpret_cast<const uchar4 *>(v.deg);
     for (int64_t k = g0; k < n4; k += gs) {
-        float4 d = __ldcg(d4 + k), r = __ldcg(r4 + k);
-        const float4 p = __ldcg(p4 + k), q = __ldcg(q4 + k);
-        const uchar4 g = __ldcg(g4 + k);
+        float4 d = d4[k], r = r4[k];
+        const float4 p = p4[k], q = q4[k];
+        const uchar4 g = g4[k];
         d.x += alpha * p.x;
         d.y += alpha * p.y;
         d.z += alpha * p.z;
@@ -718,99 +748,64 @@ __device__ __forceinline__ void inner_update(int64_t n, float alpha, const float
         a1 += r.x * r.x + r.y * r.y + r.z * r.z + r.w * r.w;
     }
     for (int64_t i = 4 * n4 + g0; i < n; i += gs) {
-        v.d[i] = __ldcg(v.d + i) + alpha * __ldcg(v.p + i);
-        const float ri = __ldcg(v.r + i) - alpha * __ldcg(v.q + i);
+        v.d[i] += alpha * v.p[i];
+        const float ri = v.r[i] - alpha * v.q[i];
         v.r[i] = ri;
-        a0 += ri * (tdeg[__ldcg(v.deg + i)] * ri);
+        a0 += ri * (tdeg[v.deg[i]] * ri);
         a1 += ri * ri;
+    }
+    double a[2] = {(double)a0, (double)a1};
+    __shared__ double out[2];
+    block_sum_store<2>(a, out);
+    if (threadIdx.x < 2) part[(int64_t)blockIdx.x * 2 + threadIdx.x] = out[threadIdx.x];
+    // the last block: inner convergence test and beta (every block has passed its inner_done test
+    // before the last one arrives, so none of this launch sees the update)
+    if (last_block(&sc->ticket_b)) {
+        const double rz = block_reduce_partials_cg(part, gridDim.x, 2, 0);
+        const double rr = block_reduce_partials_cg(part, gridDim.x, 2, 1);
+        if (threadIdx.x == 0) {
+            sc->iters += 1;
+            sc->in_iters += 1;
+            sc->rr_in = rr;
+            if (rr <= sc->stop_in || sc->in_iters >= in_maxit || sc->iters >= sc->maxit || !(sc->rz > 0.0)) {
+                sc->inner_done = 1;
+            } else {
+                sc->beta = rz / sc->rz;
+                sc->rz = rz;
+            }
+            // the iteration limits above end every loop; this bound holds even if they did not
+            if (++sc->guard > (kMaxOuter + 2) * (in_maxit + 1)) {
+                sc->inner_done = 1;
+                sc->done = 1;
+                sc->notconv = 1;
+            }
+            if (loop.cond) cudaGraphSetConditional(loop.inner, sc->inner_done ? 0u : 1u);
+        }
     }
 }
 
-// Phase C: p = T r + beta p.
-__device__ __forceinline__ void inner_direction(int64_t n, float beta, const float *tdeg, const MxVecs &v) {
+__global__ void __launch_bounds__(kThreads) k_mx_p(int64_t n, float c, MxVecs v, const MxScalars *__restrict__ sc) {
+    if (sc->inner_done) return;
+    __shared__ float tdeg[8];
+    if (threadIdx.x < 8) tdeg[threadIdx.x] = jacobi_t(c, (int)threadIdx.x);
+    __syncthreads();
+    const float beta = (float)sc->beta;
     const int64_t n4 = n >> 2;
     const int64_t g0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, gs = (int64_t)gridDim.x * blockDim.x;
     float4 *__restrict__ p4 = reinterpret_cast<float4 *>(v.p);
     const float4 *__restrict__ r4 = reinterpret_cast<const float4 *>(v.r);
     const uchar4 *__restrict__ g4 = reinterpret_cast<const uchar4 *>(v.deg);
     for (int64_t k = g0; k < n4; k += gs) {
-        float4 p = __ldcg(p4 + k);
-        const float4 r = __ldcg(r4 + k);
-        const uchar4 g = __ldcg(g4 + k);
+        float4 p = p4[k];
+        const float4 r = r4[k];
+        const uchar4 g = g4[k];
         p.x = tdeg[g.x] * r.x + beta * p.x;
         p.y = tdeg[g.y] * r.y + beta * p.y;
         p.z = tdeg[g.z] * r.z + beta * p.z;
         p.w = tdeg[g.w] * r.w + beta * p.w;
         p4[k] = p;
     }
-    for (int64_t i = 4 * n4 + g0; i < n; i += gs)
-        v.p[i] = tdeg[__ldcg(v.deg + i)] * __ldcg(v.r + i) + beta * __ldcg(v.p + i);
-}
-
-// The inner solve B d = r (d = 0, p = T r on entry, from k_mx_res).  part_a: one partial per
-// block, part_b: two; both at least gridDim.x long.
-template <int TF>
-__global__ void __launch_bounds__(kThreads, 5) k_mx_inner(int64_t n, NbrTable tb, float c, MxVecs v, MxScalars *sc,
-                                                       double *__restrict__ part_a, double *__restrict__ part_b,
-                                                       int in_maxit) {
-    if (sc->inner_done) return;  // set before the launch: the same in every block
-    __shared__ float tdeg[8];
-    if (threadIdx.x < 8) tdeg[threadIdx.x] = jacobi_t(c, (int)threadIdx.x);
-    __syncthreads();
-    double rz = sc->rz;
-    const double stop_in = sc->stop_in;
-    const int maxit = sc->maxit;
-    int iters = sc->iters, in_iters = sc->in_iters, guard = sc->guard;
-    double rr = sc->rr_in;
-    bool ok = true;
-    for (;;) {
-        // A
-        {
-            double a[1] = {(double)inner_spmv<TF>((uint32_t)n, tb, c, v)};
-            __shared__ double out[1];
-            block_sum_store<1>(a, out);
-            if (threadIdx.x == 0) part_a[blockIdx.x] = out[0];
-        }
-        if (!(ok = grid_barrier(sc->bar, &sc->err))) break;
-        const double pq = block_reduce_partials_cg(part_a, gridDim.x, 1, 0);
-        const double alpha = pq > 0.0 ? rz / pq : 0.0;
-        // B
-        {
-            float a0, a1;
-            inner_update(n, (float)alpha, tdeg, v, a0, a1);
-            double a[2] = {(double)a0, (double)a1};
-            __shared__ double out[2];
-            block_sum_store<2>(a, out);
-            if (threadIdx.x < 2) part_b[(int64_t)blockIdx.x * 2 + threadIdx.x] = out[threadIdx.x];
-        }
-        if (!(ok = grid_barrier(sc->bar, &sc->err))) break;
-        const double rzn = block_reduce_partials_cg(part_b, gridDim.x, 2, 0);
-        rr = block_reduce_partials_cg(part_b, gridDim.x, 2, 1);
-        ++iters;
-        ++in_iters;
-        ++guard;  // the limits below end the loop; the guard bounds it even if they did not
-        if (rr <= stop_in || in_iters >= in_maxit || iters >= maxit || !(rz > 0.0) ||
-            guard > (kMaxOuter + 2) * (in_maxit + 1))
-            break;
-        const double beta = rzn / rz;
-        rz = rzn;
-        // C
-        inner_direction(n, (float)beta, tdeg, v);
-        if (!(ok = grid_barrier(sc->bar, &sc->err))) break;
-    }
-    // every block leaves with the same counters; block 0 records them
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        sc->iters = iters;
-        sc->in_iters = in_iters;
-        sc->guard = guard;
-        sc->rr_in = rr;
-        sc->rz = rz;
-        sc->inner_done = 1;
-        if (!ok || guard > (kMaxOuter + 2) * (in_maxit + 1)) {
-            sc->done = 1;
-            sc->notconv = 1;
-        }
-    }
+    for (int64_t i = 4 * n4 + g0; i < n; i += gs) v.p[i] = tdeg[v.deg[i]] * v.r[i] + beta * v.p[i];
 }
 
 // x += d in float-float (TwoSum of the high part and d, then renormalised).
@@ -854,13 +849,14 @@ __global__ void __launch_bounds__(kThreads) k_mx_out(int64_t n, MxVecs v, float 
 
 // ---- the mixed solve as one CUDA graph -------------------------------------------------------
 //
-//   k_mx_rhs -> k_mx_res<first> -> WHILE(outer) { k_mx_scal_out -> k_mx_inner -> k_mx_x ->
-//   k_mx_res } -> k_mx_out
+//   k_mx_rhs -> k_mx_res<first> -> WHILE(outer) { k_mx_scal_out -> WHILE(inner) { k_mx_spmv ->
+//   k_mx_upd -> k_mx_p } -> k_mx_x -> k_mx_res } -> k_mx_out
 //
-// k_mx_scal_out sets the loop condition to "not done" at the start of every outer iteration, so
-// the host launches the graph and synchronises once per time step.  The loop is bounded by
-// kMaxOuter and cg_maxit.  The state buffers alternate between steps, so one graph is kept per
-// parity of the DOM buffer.
+// k_mx_scal_out sets both conditions to "not done" at the start of every outer iteration and
+// k_mx_upd clears the inner one when the inner solve stops, so the host launches the graph and
+// synchronises once per time step instead of polling every kBatch iterations.  Each loop is
+// bounded by the iteration limits (in_maxit, cg_maxit, kMaxOuter) and by the guard counter.  The
+// state buffers alternate between steps, so one graph is kept per parity of the DOM buffer.
 
 template <typename Tuple, size_t... I>
 void kernel_arg_ptrs(Tuple &t, void **a, std::index_sequence<I...>) {
@@ -899,36 +895,6 @@ cudaError_t add_while(cudaGraphNode_t *node, cudaGraph_t g, const cudaGraphNode_
     return e;
 }
 
-// Blocks of k_mx_inner that are resident at once (the grid of its cooperative launch), at most the
-// kMxBlocks that the partial buffers hold; 0 if it cannot be resident.
-template <int TF>
-int mx_inner_grid() {
-    int dev = 0, sms = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mx_inner<TF>, kThreads, 0) != cudaSuccess) return 0;
-    return std::min(per_sm * sms, kMxBlocks);
-}
-
-// Cooperative launch of the inner solve.
-template <int TF>
-cudaError_t mx_inner_launch(vga_sim *s, const NbrTable &tb, float c, const MxVecs &v, MxScalars *sc, double *part_a,
-                            double *part_b, int in_maxit) {
-    const int Gi = mx_inner_grid<TF>();
-    if (Gi < 1) return cudaErrorInvalidConfiguration;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)Gi);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_mx_inner<TF>, s->n, tb, c, v, sc, part_a, part_b, in_maxit);
-}
-
 struct MxGraphKey {
     const void *ptr[12];
     int64_t n;
@@ -955,20 +921,13 @@ cudaError_t mx_graph_build(vga_sim *s, const MxVecs &v, const NbrTable &tb, FF c
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return e;
-    MxLoop loop = {0, 1};
-    cudaGraphNode_t n_rhs, n_res0, n_outer, n_out, n_scal, n_inner, n_x, n_res;
-    cudaGraph_t body_o = nullptr;
-    cudaLaunchAttributeValue coop = {};
-    coop.cooperative = 1;
+    MxLoop loop = {0, 0, 1};
+    cudaGraphNode_t n_rhs, n_res0, n_outer, n_out, n_scal, n_inner, n_x, n_res, n_spmv, n_upd, n_p;
+    cudaGraph_t body_o = nullptr, body_i = nullptr;
     const unsigned ge = grid_for(s->n, kThreads);
     const double rtol = s->params.cg_rtol;
     const int maxit = s->params.cg_maxit;
     const float ch = cff.h;
-    const int Gi = mx_inner_grid<TF>();
-    if (Gi < 1) {
-        cudaGraphDestroy(g);
-        return cudaErrorInvalidConfiguration;
-    }
 #define MX_TRY(x)                        \
     do {                                 \
         e = (x);                         \
@@ -979,12 +938,14 @@ cudaError_t mx_graph_build(vga_sim *s, const MxVecs &v, const NbrTable &tb, FF c
     MX_TRY(add_kernel(&n_res0, g, &n_rhs, k_mx_res<true, TF>, G, s->n, tb, cff, v, part_a, sc));
     MX_TRY(add_while(&n_outer, g, &n_res0, loop.outer, &body_o));
     MX_TRY(add_kernel(&n_out, g, &n_outer, k_mx_out<PREC>, ge, s->n, v, s->spare(1), s->lspare(1)));
+    MX_TRY(cudaGraphConditionalHandleCreate(&loop.inner, body_o, 0u, 0u));
     MX_TRY(add_kernel(&n_scal, body_o, nullptr, k_mx_scal_out, 1u, part_a, (int64_t)G, sc, rtol, maxit, loop));
-    MX_TRY(add_kernel(&n_inner, body_o, &n_scal, k_mx_inner<TF>, (unsigned)Gi, s->n, tb, ch, v, sc, part_a, part_b,
-                      in_maxit));
-    MX_TRY(cudaGraphKernelNodeSetAttribute(n_inner, cudaLaunchAttributeCooperative, &coop));
+    MX_TRY(add_while(&n_inner, body_o, &n_scal, loop.inner, &body_i));
     MX_TRY(add_kernel(&n_x, body_o, &n_inner, k_mx_x, G, s->n, v, sc));
     MX_TRY(add_kernel(&n_res, body_o, &n_x, k_mx_res<false, TF>, G, s->n, tb, cff, v, part_a, sc));
+    MX_TRY(add_kernel(&n_spmv, body_i, nullptr, k_mx_spmv<TF>, G, s->n, tb, ch, v, part_a, sc));
+    MX_TRY(add_kernel(&n_upd, body_i, &n_spmv, k_mx_upd, G, s->n, ch, v, sc, part_b, in_maxit, loop));
+    MX_TRY(add_kernel(&n_p, body_i, &n_upd, k_mx_p, G, s->n, ch, v, sc));
 #undef MX_TRY
     *gout = g;
     return cudaSuccess;
@@ -1055,8 +1016,7 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
                 VGA_CUDA(cudaMemcpyAsync(h, sc, sizeof(MxScalars), cudaMemcpyDeviceToHost, st));
                 VGA_CUDA(cudaStreamSynchronize(st));
                 s->graph_launches += 1;
-                s->launches += 3 + 4 * (int64_t)h->outer;  // kernels the graph ran
-                if (h->err) return fail(VGA_ERR_TIMEOUT, "a grid barrier of the implicit solver timed out");
+                s->launches += 3 + 3 * (int64_t)h->outer + 3 * (int64_t)h->iters;  // kernels the graph ran
                 s->cur[1] ^= 1;
                 s->cg_iterations += h->iters;
                 s->cg_last_relres = h->relres;
@@ -1065,8 +1025,8 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
         }
     }
 
-    // host-driven loop: the same kernels; the host waits for the end of each outer iteration
-    const MxLoop noloop = {0, 0};
+    // host-driven loop: the same kernels, the done flags polled every kBatch inner iterations
+    const MxLoop noloop = {0, 0, 0};
     timing_begin(s, VGA_KERNEL_PCG_STENCIL);
     k_mx_rhs<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->comp(1), s->lcomp(1), v.bh, v.bl);
     if (tb.tz) k_mx_res<true, 1><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
@@ -1075,24 +1035,33 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
     k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, s->params.cg_rtol, s->params.cg_maxit, noloop);
     VGA_CHECK_LAUNCH();
     s->launches += 3;
-    for (int outer = 0; outer <= kMaxOuter + 1; ++outer) {
-        // one outer iteration; after convergence the remaining kernels return at once
-        timing_begin(s, VGA_KERNEL_PCG_VECTOR);
-        VGA_CUDA(tb.tz ? mx_inner_launch<1>(s, tb, ch, v, sc, part_a, part_b, in_maxit)
-                       : mx_inner_launch<0>(s, tb, ch, v, sc, part_a, part_b, in_maxit));
-        timing_end(s);
-        timing_begin(s, VGA_KERNEL_PCG_STENCIL);
-        k_mx_x<<<G, kThreads, 0, st>>>(s->n, v, sc);
-        if (tb.tz) k_mx_res<false, 1><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
-        else k_mx_res<false, 0><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
-        timing_end(s);
-        k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, s->params.cg_rtol, s->params.cg_maxit, noloop);
+    for (int guard = 0; guard < 100000; ++guard) {
+        for (int k = 0; k < kBatch; ++k) {
+            timing_begin(s, VGA_KERNEL_PCG_STENCIL);
+            if (tb.tz) k_mx_spmv<1><<<G, kThreads, 0, st>>>(s->n, tb, ch, v, part_a, sc);
+            else k_mx_spmv<0><<<G, kThreads, 0, st>>>(s->n, tb, ch, v, part_a, sc);
+            timing_end(s);
+            timing_begin(s, VGA_KERNEL_PCG_VECTOR);
+            k_mx_upd<<<G, kThreads, 0, st>>>(s->n, ch, v, sc, part_b, in_maxit, noloop);
+            k_mx_p<<<G, kThreads, 0, st>>>(s->n, ch, v, sc);
+            timing_end(s);
+        }
         VGA_CHECK_LAUNCH();
-        s->launches += 4;
+        s->launches += 3 * kBatch;
         VGA_CUDA(cudaMemcpyAsync(h, sc, sizeof(MxScalars), cudaMemcpyDeviceToHost, st));
         VGA_CUDA(cudaStreamSynchronize(st));
-        if (h->err) return fail(VGA_ERR_TIMEOUT, "a grid barrier of the implicit solver timed out");
         if (h->done) break;
+        if (h->inner_done) {
+            // x += d, then the true residual of the new x and the next inner solve's start
+            timing_begin(s, VGA_KERNEL_PCG_STENCIL);
+            k_mx_x<<<G, kThreads, 0, st>>>(s->n, v, sc);
+            if (tb.tz) k_mx_res<false, 1><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
+            else k_mx_res<false, 0><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
+            timing_end(s);
+            k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, s->params.cg_rtol, s->params.cg_maxit, noloop);
+            VGA_CHECK_LAUNCH();
+            s->launches += 3;
+        }
     }
     k_mx_out<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, v, s->spare(1), s->lspare(1));
     VGA_CHECK_LAUNCH();
