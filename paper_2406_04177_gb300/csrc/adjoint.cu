@@ -170,12 +170,21 @@ struct Nb6 {
     uint32_t mask;  // bit d: neighbour in slot d exists
 };
 
+// TF 1: compact z offsets (NbrTable.tz).
+template <int TF>
 __device__ __forceinline__ Nb6 gather6(const NbrTable &tb, uint32_t i, bool live, float vi,
                                        const float *__restrict__ a) {
     Nb6 r;
     const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
-    const uint32_t dzm = live ? __ldg(tb.tzm + i) : 0u;
-    const uint32_t dzp = live ? __ldg(tb.tzp + i) : 0u;
+    uint32_t dzm, dzp;
+    if (TF == 1) {
+        const uint32_t tz = live ? __ldg(tb.tz + i) : 0u;
+        dzm = tz & 0xffffu;
+        dzp = tz >> 16;
+    } else {
+        dzm = live ? __ldg(tb.tzm + i) : 0u;
+        dzp = live ? __ldg(tb.tzp + i) : 0u;
+    }
     const int lane = threadIdx.x & 31;
     float vl = __shfl_up_sync(0xffffffffu, vi, 1);
     float vr = __shfl_down_sync(0xffffffffu, vi, 1);
@@ -194,42 +203,13 @@ __device__ __forceinline__ Nb6 gather6(const NbrTable &tb, uint32_t i, bool live
     return r;
 }
 
-// Table-driven fused pass with recording (same arithmetic as k_fused_rec and the forward).
-template <int WM, int PREC>
-__global__ void __launch_bounds__(kThreads) k_fused_rec_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
-                                                              StateIO io, int64_t npad, Rec rec) {
-    const uint32_t i = (uint32_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < (uint64_t)n;
-    const float *__restrict__ Y2 = io.in[1];
-    V x2 = live ? vload<PREC>(Y2, io.lin[1], i) : V{0.0f, 0.0f};
-    const float yi = x2.h;
-    const Nb6 nb = gather6(tb, i, live, yi, Y2);
-    if (!live) return;
-    const uint32_t bn = (WM == W_BLOCK) ? __ldg(bt.node + i) : 0u;
-    float acc = 0.0f;
-#pragma unroll
-    for (int d = 0; d < 6; ++d) {
-        if (!((nb.mask >> d) & 1u)) continue;
-        const float dd = __fsub_rn(yi, nb.v[d]);
-        if (WM == W_UNIT) acc = __fadd_rn(acc, dd);
-        else acc = __fmaf_rn(table_theta(bt, bn, d), dd, acc);
-    }
-    vadd<PREC>(x2, __fmul_rn(-p.c, acc));
-    vround<PREC>(x2);
-    V x1 = vload<PREC>(io.in[0], io.lin[0], i), x3 = vload<PREC>(io.in[2], io.lin[2], i),
-      x4 = vload<PREC>(io.in[3], io.lin[3], i), x5 = vload<PREC>(io.in[4], io.lin[4], i);
-    rec.x[i] = __fadd_rn(x1.h, x1.l);
-    rec.x[npad + i] = __fadd_rn(x2.h, x2.l);
-    rec.x[2 * npad + i] = __fadd_rn(x3.h, x3.l);
-    rec.x[3 * npad + i] = __fadd_rn(x4.h, x4.l);
-    rec.x[4 * npad + i] = __fadd_rn(x5.h, x5.l);
-    transform_sync<PREC>(x1, x2, x3, x4, x5, p);
-    vstore<PREC>(io.out[0], io.lout[0], i, x1);
-    vstore<PREC>(io.out[1], io.lout[1], i, x2);
-    vstore<PREC>(io.out[2], io.lout[2], i, x3);
-    vstore<PREC>(io.out[3], io.lout[3], i, x4);
-    vstore<PREC>(io.out[4], io.lout[4], i, x5);
-    rec.y2[i] = __fadd_rn(x2.h, x2.l);
+// Table-driven fused pass with recording: four nodes per thread (table_vec, the forward's own body, so the recomputed
+// trajectory is the forward's bit for bit), recording X^k and y2^k as vectors.
+template <int WM, int PREC, int TF>
+__global__ void __launch_bounds__(kThreads) k_fused_rec_vec(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+                                                            StateIO io, PassRecord rec) {
+    const uint32_t i0 = 4u * ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x);
+    table_vec<1, WM, 0, PREC, TF, 4, true>(i0, (uint32_t)n, tb, bt, p, io, rec);
 }
 
 // Compensated FP32 accumulator (TwoSum into a second float): GB300 issues FP64 at a small fraction of
@@ -275,7 +255,7 @@ __device__ __forceinline__ void face_atomic_add_f(double *gtheta, int32_t f, flo
 }
 
 // Table-driven reverse step (same arithmetic as k_adjoint_step), grid-stride over 256-node tiles.
-template <int WM, int PREC>
+template <int WM, int PREC, int TF>
 __global__ void __launch_bounds__(kThreads, 5) k_adjoint_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                             StateIO io, int64_t npad, const float *__restrict__ xk,
                                                             const float *__restrict__ y2k, double *__restrict__ gpart,
@@ -292,8 +272,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_adjoint_table(int64_t n, NbrTab
         for (int c = 0; c < 5; ++c) mu[c] = live ? vload<PREC>(io.in[c], io.lin[c], i) : V{0.0f, 0.0f};
         const float li = mu[1].h;
         const float yi = live ? __ldg(y2k + i) : 0.0f;
-        const Nb6 nl = gather6(tb, i, live, li, L2);
-        const Nb6 ny = gather6(tb, i, live, yi, y2k);
+        const Nb6 nl = gather6<TF>(tb, i, live, li, L2);
+        const Nb6 ny = gather6<TF>(tb, i, live, yi, y2k);
         const uint32_t bn = (WM == W_BLOCK && live) ? __ldg(bt.node + i) : 0u;
         float lsum = 0.0f, ysum = 0.0f;
         int32_t face[3] = {-1, -1, -1};
@@ -591,7 +571,7 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     if (table) VGA_TRY(sim_nbr_table(s, &tb));
     if (table && WM == W_BLOCK) VGA_TRY(sim_block_table(s, &bt, &table));
     const int Gt = (int)std::min<int64_t>(kAdjBlocks, (s->n + kThreads - 1) / kThreads);  // grid of the table kernels
-    const int Gf = (int)((s->n + kThreads - 1) / kThreads);
+    const int Gv = (int)(((s->n + 3) / 4 + kThreads - 1) / kThreads);  // four nodes per thread
     const int G = table ? Gt : s->chunks.count;  // blocks writing gradient partials
     const size_t smem = sizeof(uint32_t) * (size_t)s->chunks.cap * decode_words(WM == W_BLOCK);
     const int64_t npad = s->npad;
@@ -618,10 +598,12 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
             rec.x = a->rec_x + (size_t)j * 5 * npad;
             rec.y2 = a->rec_y2 + (size_t)j * npad;
             timing_begin(s, VGA_KERNEL_FUSED_STEP);
-            if (table)
-                k_fused_rec_table<WM, PREC><<<Gf, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
-                                                                   io_from(a->work[wb], a->work[1 - wb], npad), npad, rec);
-            else
+            if (table) {
+                const PassRecord pr = {rec.x, rec.y2, npad};
+                const StateIO io = io_from(a->work[wb], a->work[1 - wb], npad);
+                if (tb.tz) k_fused_rec_vec<WM, PREC, 1><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr);
+                else k_fused_rec_vec<WM, PREC, 0><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr);
+            } else
                 k_fused_rec<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
                                                                 io_from(a->work[wb], a->work[1 - wb], npad), npad, rec);
             timing_end(s);
@@ -633,10 +615,14 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
         for (int64_t j = len - 1; j >= 0; --j) {
             const float *xk = (j == 0) ? cks.h : a->rec_x + (size_t)j * 5 * npad;
             timing_begin(s, VGA_KERNEL_ADJOINT);
-            if (table)
-                k_adjoint_table<WM, PREC><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
-                                                                 io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
-                                                                 a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
+            if (table && tb.tz)
+                k_adjoint_table<WM, PREC, 1><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
+                                                                    io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
+                                                                    a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
+            else if (table)
+                k_adjoint_table<WM, PREC, 0><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
+                                                                    io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
+                                                                    a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
             else
                 k_adjoint_step<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
                                                                    io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,

@@ -381,9 +381,32 @@ __device__ __forceinline__ void group_load(uint32_t i0, uint32_t n, const NbrTab
 }
 
 // Transformation and stores of a group (MODE 1), or the DOM store alone (MODE 2).
-template <int MODE, int TR, int PREC, int K, bool FULL>
+// Record of one fused pass for the discrete adjoint: X (after the diffusion, before the
+// transformation; 5 rows of npad FP32 values h + l) and the transformed DOM.
+struct PassRecord {
+    float *x;
+    float *y2;
+    int64_t npad;
+};
+
+// h + l of K values into dst[i0 ..] (vector store when FULL).
+template <int K, bool FULL>
+__device__ __forceinline__ void record_k(float *dst, uint32_t i0, uint32_t n, const V (&v)[K]) {
+    float h[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) h[k] = __fadd_rn(v[k].h, v[k].l);
+    if (FULL) {
+        st_floats<K>(dst + i0, h);
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (i0 + k < n) dst[i0 + k] = h[k];
+    }
+}
+
+template <int MODE, int TR, int PREC, int K, bool FULL, bool REC = false>
 __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const StepParams &p, const StateIO &io,
-                                             V (&x2)[K]) {
+                                             V (&x2)[K], const PassRecord &rec = PassRecord{}) {
     if (MODE == 1) {
         V x1[K], x3[K], x4[K], x5[K];
         vload_k<PREC, K, FULL>(io.in[0], io.lin[0], i0, n, x1);
@@ -391,10 +414,17 @@ __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const Step
         vload_k<PREC, K, FULL>(io.in[3], io.lin[3], i0, n, x4);
         vload_k<PREC, K, FULL>(io.in[4], io.lin[4], i0, n, x5);
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            vround<PREC>(x2[k]);
-            transform_n<TR, PREC>(x1[k], x2[k], x3[k], x4[k], x5[k], p);
+        for (int k = 0; k < K; ++k) vround<PREC>(x2[k]);
+        if (REC) {
+            record_k<K, FULL>(rec.x, i0, n, x1);
+            record_k<K, FULL>(rec.x + rec.npad, i0, n, x2);
+            record_k<K, FULL>(rec.x + 2 * rec.npad, i0, n, x3);
+            record_k<K, FULL>(rec.x + 3 * rec.npad, i0, n, x4);
+            record_k<K, FULL>(rec.x + 4 * rec.npad, i0, n, x5);
         }
+#pragma unroll
+        for (int k = 0; k < K; ++k) transform_n<TR, PREC>(x1[k], x2[k], x3[k], x4[k], x5[k], p);
+        if (REC) record_k<K, FULL>(rec.y2, i0, n, x2);
         vstore_k<PREC, K, FULL>(io.out[0], io.lout[0], i0, n, x1);
         vstore_k<PREC, K, FULL>(io.out[1], io.lout[1], i0, n, x2);
         vstore_k<PREC, K, FULL>(io.out[2], io.lout[2], i0, n, x3);
@@ -412,11 +442,13 @@ __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const Step
 // the last group of the range takes the per-node path.  The -x neighbour of the first node is the
 // previous lane's last node and the +x neighbour of the last node the next lane's first node.
 // Arithmetic and slot order per node are those of table_node, so the results are the same bits.
-// Rows and tables start on 16-byte boundaries (row strides are multiples of 64 values).  Must be
-// called by all 32 lanes of a warp.
-template <int MODE, int WM, int TR, int PREC, int TF, int K>
+// Rows and tables start on 16-byte boundaries (row strides are multiples of 64 values).  REC (fused
+// passes only): also writes the pass record of the discrete adjoint.  Must be called by all 32
+// lanes of a warp.
+template <int MODE, int WM, int TR, int PREC, int TF, int K, bool REC = false>
 __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTable &tb, const BlockTable &bt,
-                                          const StepParams &p, const StateIO &io) {
+                                          const StepParams &p, const StateIO &io,
+                                          const PassRecord &rec = PassRecord{}) {
     const bool full = i0 + K <= n;
     const float *__restrict__ Y2 = io.in[1];
     uint32_t ty[K], zm[K], zp[K], bn[K];
@@ -457,8 +489,8 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
         if (zp[k]) add(5, zw[k]);
         vadd<PREC>(x2[k], __fmul_rn(-p.c, acc));  // Scheme 1
     }
-    if (full) group_finish<MODE, TR, PREC, K, true>(i0, n, p, io, x2);
-    else group_finish<MODE, TR, PREC, K, false>(i0, n, p, io, x2);
+    if (full) group_finish<MODE, TR, PREC, K, true, REC>(i0, n, p, io, x2, rec);
+    else group_finish<MODE, TR, PREC, K, false, REC>(i0, n, p, io, x2, rec);
 }
 
 }  // namespace vga
