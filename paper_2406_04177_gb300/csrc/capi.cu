@@ -670,6 +670,7 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->nbr_tz);
     dfree(s->bnode);
     dfree(s->bface);
+    dfree(s->btheta6);
     if (s->h_totals) cudaFreeHost(s->h_totals);
     dfree(s->stage);
     dfree(s->theta);

@@ -130,8 +130,7 @@ __device__ __forceinline__ int64_t block_face(const BlockWeights &bw, int slot, 
 // Conductance of the edge leaving a node through `slot` under the block table (see BlockTable).
 __device__ __forceinline__ float table_theta(const BlockTable &bt, uint32_t bn, int slot) {
     if (!((bn >> (26 + slot)) & 1u)) return 1.0f;
-    const int32_t f = __ldg(bt.face + 6 * (size_t)(bn & 0x3ffffffu) + slot);
-    return f >= 0 ? __ldg(bt.theta + f) : 1.0f;
+    return __ldg(bt.theta6 + 6 * (size_t)(bn & 0x3ffffffu) + slot);
 }
 
 __device__ __forceinline__ int32_t table_face(const BlockTable &bt, uint32_t bn, int slot) {

@@ -263,6 +263,15 @@ __global__ void k_build_bface(BlockWeights bw, int32_t *__restrict__ face) {
     f[5] = bz < bw.nbz - 1 ? (int32_t)(bw.off_z + ((int64_t)bz * bw.nby + by) * bw.nbx + bx) : -1;
 }
 
+// theta6[k] = theta[face[k]] for the 6 slots of every block (1 where the face lies on the border).
+__global__ void k_build_theta6(int64_t m, const int32_t *__restrict__ face, const float *__restrict__ theta,
+                               float *__restrict__ theta6) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= m) return;
+    const int32_t f = face[k];
+    theta6[k] = f >= 0 ? theta[f] : 1.0f;
+}
+
 // One node per thread, neighbours from the offset table (table_node).
 template <int MODE, int WM, int TR, int PREC, int TF>
 __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
@@ -712,10 +721,22 @@ vga_status sim_block_table(vga_sim *s, BlockTable *out, bool *ok) {
         }
         s->launches += 2;
         s->btable_bs = s->bw.bs;
+        dfree(s->btheta6);
+        s->btheta6 = nullptr;
+        VGA_TRY(dmalloc((void **)&s->btheta6, sizeof(float) * 6 * (size_t)std::max<int64_t>(nb, 1), "block conductances"));
+        s->btheta6_gen = -1;
+    }
+    if (s->btheta6_gen != s->param_gen) {
+        k_build_theta6<<<(unsigned)((6 * nb + kThreads - 1) / kThreads), kThreads, 0, s->stream>>>(6 * nb, s->bface,
+                                                                                              s->bw.theta, s->btheta6);
+        VGA_CHECK_LAUNCH();
+        ++s->launches;
+        s->btheta6_gen = s->param_gen;
     }
     out->node = s->bnode;
     out->face = s->bface;
     out->theta = s->bw.theta;
+    out->theta6 = s->btheta6;
     *ok = true;
     return VGA_OK;
 }

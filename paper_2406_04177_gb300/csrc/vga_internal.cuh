@@ -76,11 +76,13 @@ struct NbrTable {
 
 // Block conductances in table form.  node[i] = block id (bits 0..25) | bit 26+d set when the edge
 // leaving node i through slot d crosses a block face; face[6*b + d] = index into theta of face d of
-// block b (or -1 at the image border).
+// block b (or -1 at the image border); theta6[6*b + d] = theta[face[6*b + d]] (1 at the border), so
+// a pass reads a crossing edge's conductance with one dependent load instead of two.
 struct BlockTable {
     const uint32_t *node = nullptr;
     const int32_t *face = nullptr;
     const float *theta = nullptr;
+    const float *theta6 = nullptr;
 };
 constexpr int64_t kMaxTableBlocks = (int64_t)1 << 26;
 
@@ -232,6 +234,8 @@ struct vga_sim {
     int nbr_tz_state = 0;           // 0 not examined, 1 built, 2 offsets too large
     uint32_t *bnode = nullptr;      // BlockTable.node (npad), built for the current block side
     int32_t *bface = nullptr;       // BlockTable.face (6 x blocks)
+    float *btheta6 = nullptr;       // BlockTable.theta6 (6 x blocks), rebuilt when param_gen moves
+    int64_t btheta6_gen = -1;       // param_gen btheta6 was built for
     int32_t btable_bs = 0;          // block side the block table was built for (0: none)
     double *loss_work = nullptr;  // block-mass objective scratch
     int64_t loss_cap = 0;
