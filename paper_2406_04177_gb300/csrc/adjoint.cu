@@ -234,24 +234,25 @@ __device__ __forceinline__ void cacc_add_prod(CAcc &a, float x, float y) {
     a.c = __fadd_rn(a.c, e);
 }
 
-// Adds v to gtheta[f] for every lane with f >= 0, combining lanes of the warp that hit the same
-// face first in FP32 (neighbouring nodes on one block face share it) so that one FP64 atomic per
-// face and warp reaches memory.  Must be called by all 32 lanes.
+// Adds v to gtheta[f] for every lane with f >= 0.  Lanes are consecutive nodes, so lanes that hit the
+// same face form contiguous runs (the nodes of one block along a row); each run is summed in FP32 by
+// a segmented shuffle reduction (five steps) and its first lane issues one FP64 atomic.  Must be
+// called by all 32 lanes.
 __device__ __forceinline__ void face_atomic_add_f(double *gtheta, int32_t f, float v) {
-    const unsigned act = __ballot_sync(0xffffffffu, f >= 0);
-    if (!act) return;
+    if (!__ballot_sync(0xffffffffu, f >= 0)) return;
     const int lane = threadIdx.x & 31;
-    const unsigned peers = __match_any_sync(0xffffffffu, f);
-    const bool leader = (f >= 0) && (lane == __ffs(peers) - 1);
+    const int32_t fp = __shfl_up_sync(0xffffffffu, f, 1);
+    const bool head = lane == 0 || f != fp;
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned after = lane == 31 ? 0u : heads >> (lane + 1);
+    const int end = after ? lane + __ffs(after) : 32;  // one past this lane's run
     float sum = v;
-    unsigned rest = act;
-    while (rest) {
-        const int src = __ffs(rest) - 1;
-        rest &= rest - 1;
-        const float t = __shfl_sync(0xffffffffu, v, src);
-        if (leader && src != lane && ((peers >> src) & 1u)) sum = __fadd_rn(sum, t);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const float t = __shfl_down_sync(0xffffffffu, sum, off);
+        if (lane + off < end) sum = __fadd_rn(sum, t);
     }
-    if (leader) atomicAdd(gtheta + f, (double)sum);
+    if (head && f >= 0) atomicAdd(gtheta + f, (double)sum);
 }
 
 // Table-driven reverse step (same arithmetic as k_adjoint_step), grid-stride over 256-node tiles.
