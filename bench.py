@@ -313,6 +313,8 @@ def bench_ours(a):
     sim.step(S)
     sim.get_state_f32(outh_np)
     torch.cuda.synchronize()
+    e2e_sampler = ClockSampler(bus)
+    e2e_sampler.start()
     w0 = time.perf_counter()
     for _ in range(e2e_iters):
         sim.set_state_f32(xh_np)
@@ -320,11 +322,13 @@ def bench_ours(a):
         sim.totals()
         sim.get_state_f32(outh_np)
     w1 = time.perf_counter()
+    e2e_clocks = e2e_sampler.stop()
     e2e_val = world * n * S * e2e_iters / (w1 - w0)
     e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 4),
            "d2h_bytes_per_step": int(outh.numel() * 4 + 5 * 8),
            "how": "per step: vga_sim_set_state_f32 from pinned host memory, vga_sim_step(substeps), "
-                  "vga_sim_totals, vga_sim_get_state_f32 to pinned host memory; wall clock"}
+                  "vga_sim_totals, vga_sim_get_state_f32 to pinned host memory; wall clock",
+           "steps": e2e_iters, "clocks": e2e_clocks}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
