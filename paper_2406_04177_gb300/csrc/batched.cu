@@ -45,110 +45,124 @@ struct BatchArgs {
     res_t *l[2];
     unsigned *bar;  // [0] arrivals, [1] generation
     int32_t *err;
+    StateIO io[2];  // a pass whose input is state buffer k reads io[k] (kept as kernel parameters)
 };
 
+// One fused pass over the whole batch, kBatchGroup consecutive nodes per thread (table_vec).
+// Instances start on tile boundaries, so a group never straddles two and the 32 K nodes of a warp
+// belong to one instance, whose parameters the warp reads from shared memory (per-thread copies
+// would hold a dozen registers); every thread of a block runs the same number of iterations (the
+// warp-wide shuffles need all lanes).
 template <int TR, int PREC, int TF>
+__device__ __forceinline__ void batch_fused_pass(const BatchArgs &a, const StateIO &io) {
+    constexpr int KG = kBatchGroup;
+    __shared__ StepParams wp[kTile / 32];
+    const int w = threadIdx.x >> 5;
+    const int64_t nsuper = (a.ntiles + KG - 1) / KG;  // kTile * KG nodes per block iteration
+    for (int64_t sup = blockIdx.x; sup < nsuper; sup += gridDim.x) {
+        const uint32_t i0 = (uint32_t)(sup * kTile * KG + (int64_t)threadIdx.x * KG);
+        const int64_t tile = (int64_t)i0 / kTile;
+        uint32_t end = 0;  // one past the instance's last node (0: no instance here)
+        int32_t k = -1;
+        if (tile < a.ntiles) {
+            k = __ldg(a.tile_inst + tile);
+            end = (uint32_t)(a.inst[k].start + a.inst[k].n);
+        }
+        __syncwarp();
+        if ((threadIdx.x & 31) == 0) wp[w] = k >= 0 ? a.inst[k].p : StepParams{};
+        __syncwarp();
+        table_vec<1, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, wp[w], io);
+    }
+}
+
+// FUSED_ONLY: an instantiation for launches whose passes are all fused ones (every launch but the
+// first and the last pass of a call); without the code of the other two kinds it needs fewer
+// registers, so more blocks are resident.
+template <int TR, int PREC, int TF, bool FUSED_ONLY>
 __global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
     for (int32_t pass = pass0; pass < pass1; ++pass) {
-        const int kind = (pass == 0) ? 0 : (pass == npass - 1 ? 2 : 1);  // transform / fused / diffuse
+        // transform / fused / diffuse
+        const int kind = FUSED_ONLY ? 1 : ((pass == 0) ? 0 : (pass == npass - 1 ? 2 : 1));
         const int bi = (cur0 + pass) & 1, bo = bi ^ 1;
         const float *__restrict__ Y2 = a.h[bi] + a.npad;
         if (kind == 1) {
             // fused pass: kBatchGroup consecutive nodes per thread (table_vec).  Instances start on
             // tile boundaries, so a group never straddles two; every thread of a block runs the
             // same number of iterations (the warp-wide shuffles need all lanes).
-            StateIO io;
-#pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                io.in[c] = a.h[bi] + c * a.npad;
-                io.lin[c] = a.l[bi] + c * a.npad;
-                io.out[c] = a.h[bo] + c * a.npad;
-                io.lout[c] = a.l[bo] + c * a.npad;
-            }
-            constexpr int KG = kBatchGroup;
-            const int64_t nsuper = (a.ntiles + KG - 1) / KG;  // kTile * KG nodes per block iteration
-            for (int64_t sup = blockIdx.x; sup < nsuper; sup += gridDim.x) {
-                const uint32_t i0 = (uint32_t)(sup * kTile * KG + (int64_t)threadIdx.x * KG);
-                const int64_t tile = (int64_t)i0 / kTile;
-                uint32_t end = 0;  // one past the instance's last node (0: no instance here)
-                StepParams p = {};
-                if (tile < a.ntiles) {
-                    const BInst &ins = a.inst[__ldg(a.tile_inst + tile)];
-                    end = (uint32_t)(ins.start + ins.n);
-                    p = ins.p;
-                }
-                table_vec<1, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, p, io);
-            }
+            if (bi == 0) batch_fused_pass<TR, PREC, TF>(a, a.io[0]);
+            else batch_fused_pass<TR, PREC, TF>(a, a.io[1]);
             if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err)) return;
             continue;
         }
-        for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-            const BInst &ins = a.inst[__ldg(a.tile_inst + tile)];
-            const uint32_t i = (uint32_t)(tile * kTile + threadIdx.x);
-            const bool live = (int64_t)i - ins.start < ins.n;
-            const StepParams p = ins.p;
-            V x[5];
-            if (kind == 0) {
-                if (!live) continue;
-#pragma unroll
-                for (int c = 0; c < 5; ++c) x[c] = vload<PREC>(a.h[bi] + c * a.npad, a.l[bi] + c * a.npad, i);
-                transform<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
-            } else {
-                const uint32_t ty = live ? __ldg(a.tb.ty + i) : 0u;
-                uint32_t dzm, dzp;
-                if (TF == 1) {  // compact z offsets
-                    const uint32_t tz = live ? __ldg(a.tb.tz + i) : 0u;
-                    dzm = tz & 0xffffu;
-                    dzp = tz >> 16;
+        if constexpr (!FUSED_ONLY) {  // first (transform) and last (diffuse-only) pass of a call
+            for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+                const BInst &ins = a.inst[__ldg(a.tile_inst + tile)];
+                const uint32_t i = (uint32_t)(tile * kTile + threadIdx.x);
+                const bool live = (int64_t)i - ins.start < ins.n;
+                const StepParams p = ins.p;
+                V x[5];
+                if (kind == 0) {
+                    if (!live) continue;
+    #pragma unroll
+                    for (int c = 0; c < 5; ++c) x[c] = vload<PREC>(a.h[bi] + c * a.npad, a.l[bi] + c * a.npad, i);
+                    transform<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
                 } else {
-                    dzm = live ? __ldg(a.tb.tzm + i) : 0u;
-                    dzp = live ? __ldg(a.tb.tzp + i) : 0u;
-                }
-                x[1] = live ? vload<PREC>(Y2, a.l[bi] + a.npad, i) : V{0.0f, 0.0f};
-                const float yi = x[1].h;
-                const int lane = threadIdx.x & 31;
-                float yl = __shfl_up_sync(0xffffffffu, yi, 1);
-                float yr = __shfl_down_sync(0xffffffffu, yi, 1);
-                const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
-                const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
-                if (lane == 0 && hxm) yl = __ldg(Y2 + (i - 1));
-                if (lane == 31 && hxp) yr = __ldg(Y2 + (i + 1));
-                float ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
-                if (dym) ym = __ldg(Y2 + (i - dym));
-                if (dyp) yp = __ldg(Y2 + (i + dyp));
-                if (dzm) zm = __ldg(Y2 + (i - dzm));
-                if (dzp) zp = __ldg(Y2 + (i + dzp));
-                if (!live) continue;
-                float acc = 0.0f;
-                if (hxm) acc = __fadd_rn(acc, __fsub_rn(yi, yl));
-                if (hxp) acc = __fadd_rn(acc, __fsub_rn(yi, yr));
-                if (dym) acc = __fadd_rn(acc, __fsub_rn(yi, ym));
-                if (dyp) acc = __fadd_rn(acc, __fsub_rn(yi, yp));
-                if (dzm) acc = __fadd_rn(acc, __fsub_rn(yi, zm));
-                if (dzp) acc = __fadd_rn(acc, __fsub_rn(yi, zp));
-                vadd<PREC>(x[1], __fmul_rn(-p.c, acc));
-                if (kind == 2) {
-                    // diffusion-only pass: DOM is new, the other compartments move bit for bit
-                    vstore<PREC>(a.h[bo] + a.npad, a.l[bo] + a.npad, i, x[1]);
-#pragma unroll
-                    for (int c = 0; c < 5; ++c) {
-                        if (c == 1) continue;
-                        a.h[bo][c * a.npad + i] = a.h[bi][c * a.npad + i];
-                        if (PREC == P_COMP) a.l[bo][c * a.npad + i] = a.l[bi][c * a.npad + i];
+                    const uint32_t ty = live ? __ldg(a.tb.ty + i) : 0u;
+                    uint32_t dzm, dzp;
+                    if (TF == 1) {  // compact z offsets
+                        const uint32_t tz = live ? __ldg(a.tb.tz + i) : 0u;
+                        dzm = tz & 0xffffu;
+                        dzp = tz >> 16;
+                    } else {
+                        dzm = live ? __ldg(a.tb.tzm + i) : 0u;
+                        dzp = live ? __ldg(a.tb.tzp + i) : 0u;
                     }
-                    continue;
+                    x[1] = live ? vload<PREC>(Y2, a.l[bi] + a.npad, i) : V{0.0f, 0.0f};
+                    const float yi = x[1].h;
+                    const int lane = threadIdx.x & 31;
+                    float yl = __shfl_up_sync(0xffffffffu, yi, 1);
+                    float yr = __shfl_down_sync(0xffffffffu, yi, 1);
+                    const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
+                    const bool hxm = (ty >> 15) & 1u, hxp = ty >> 31;
+                    if (lane == 0 && hxm) yl = __ldg(Y2 + (i - 1));
+                    if (lane == 31 && hxp) yr = __ldg(Y2 + (i + 1));
+                    float ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
+                    if (dym) ym = __ldg(Y2 + (i - dym));
+                    if (dyp) yp = __ldg(Y2 + (i + dyp));
+                    if (dzm) zm = __ldg(Y2 + (i - dzm));
+                    if (dzp) zp = __ldg(Y2 + (i + dzp));
+                    if (!live) continue;
+                    float acc = 0.0f;
+                    if (hxm) acc = __fadd_rn(acc, __fsub_rn(yi, yl));
+                    if (hxp) acc = __fadd_rn(acc, __fsub_rn(yi, yr));
+                    if (dym) acc = __fadd_rn(acc, __fsub_rn(yi, ym));
+                    if (dyp) acc = __fadd_rn(acc, __fsub_rn(yi, yp));
+                    if (dzm) acc = __fadd_rn(acc, __fsub_rn(yi, zm));
+                    if (dzp) acc = __fadd_rn(acc, __fsub_rn(yi, zp));
+                    vadd<PREC>(x[1], __fmul_rn(-p.c, acc));
+                    if (kind == 2) {
+                        // diffusion-only pass: DOM is new, the other compartments move bit for bit
+                        vstore<PREC>(a.h[bo] + a.npad, a.l[bo] + a.npad, i, x[1]);
+    #pragma unroll
+                        for (int c = 0; c < 5; ++c) {
+                            if (c == 1) continue;
+                            a.h[bo][c * a.npad + i] = a.h[bi][c * a.npad + i];
+                            if (PREC == P_COMP) a.l[bo][c * a.npad + i] = a.l[bi][c * a.npad + i];
+                        }
+                        continue;
+                    }
+                    x[0] = vload<PREC>(a.h[bi], a.l[bi], i);
+                    x[2] = vload<PREC>(a.h[bi] + 2 * a.npad, a.l[bi] + 2 * a.npad, i);
+                    x[3] = vload<PREC>(a.h[bi] + 3 * a.npad, a.l[bi] + 3 * a.npad, i);
+                    x[4] = vload<PREC>(a.h[bi] + 4 * a.npad, a.l[bi] + 4 * a.npad, i);
+                    vround<PREC>(x[1]);
+                    transform<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
                 }
-                x[0] = vload<PREC>(a.h[bi], a.l[bi], i);
-                x[2] = vload<PREC>(a.h[bi] + 2 * a.npad, a.l[bi] + 2 * a.npad, i);
-                x[3] = vload<PREC>(a.h[bi] + 3 * a.npad, a.l[bi] + 3 * a.npad, i);
-                x[4] = vload<PREC>(a.h[bi] + 4 * a.npad, a.l[bi] + 4 * a.npad, i);
-                vround<PREC>(x[1]);
-                transform<TR, PREC>(x[0], x[1], x[2], x[3], x[4], p);
+    #pragma unroll
+                for (int c = 0; c < 5; ++c) vstore<PREC>(a.h[bo] + c * a.npad, a.l[bo] + c * a.npad, i, x[c]);
             }
-#pragma unroll
-            for (int c = 0; c < 5; ++c) vstore<PREC>(a.h[bo] + c * a.npad, a.l[bo] + c * a.npad, i, x[c]);
+            if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err)) return;
         }
-        if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err)) return;
     }
 }
 
@@ -199,7 +213,8 @@ struct vga_batch {
     double *stage = nullptr;
     int64_t stage_n = 0;
     int cur = 0;
-    int grid = 0;          // blocks of a launch (resident on every SM)
+    int grid = 0;          // blocks of a fused-only launch (resident on every SM)
+    int grid_edge = 0;     // blocks of a launch of the first or the last pass
     int blocks_per_sm = 0;  // tuning knob (0: the occupancy maximum)
     int steps_per_launch = 100;
     bool use_graph = true;
@@ -210,33 +225,39 @@ struct vga_batch {
 
 namespace {
 
-template <int TFV>
+template <int TFV, bool FO>
 const void *batch_kernel(const vga_batch *b) {
-    return b->transform == 0 ? (b->precision == P_COMP ? (const void *)k_batch<0, P_COMP, TFV> : (const void *)k_batch<0, P_F32, TFV>)
-                             : (b->precision == P_COMP ? (const void *)k_batch<1, P_COMP, TFV> : (const void *)k_batch<1, P_F32, TFV>);
+    return b->transform == 0
+               ? (b->precision == P_COMP ? (const void *)k_batch<0, P_COMP, TFV, FO> : (const void *)k_batch<0, P_F32, TFV, FO>)
+               : (b->precision == P_COMP ? (const void *)k_batch<1, P_COMP, TFV, FO> : (const void *)k_batch<1, P_F32, TFV, FO>);
 }
 
-template <int TFV>
+template <int TFV, bool FO>
 cudaError_t batch_launch_tf(const vga_batch *b, const cudaLaunchConfig_t &cfg, const BatchArgs &a, int32_t pass0,
                             int32_t pass1, int32_t npass, int32_t cur0) {
     if (b->transform == 0) {
-        if (b->precision == P_COMP) return cudaLaunchKernelEx(&cfg, k_batch<0, P_COMP, TFV>, a, pass0, pass1, npass, cur0);
-        return cudaLaunchKernelEx(&cfg, k_batch<0, P_F32, TFV>, a, pass0, pass1, npass, cur0);
+        if (b->precision == P_COMP) return cudaLaunchKernelEx(&cfg, k_batch<0, P_COMP, TFV, FO>, a, pass0, pass1, npass, cur0);
+        return cudaLaunchKernelEx(&cfg, k_batch<0, P_F32, TFV, FO>, a, pass0, pass1, npass, cur0);
     }
-    if (b->precision == P_COMP) return cudaLaunchKernelEx(&cfg, k_batch<1, P_COMP, TFV>, a, pass0, pass1, npass, cur0);
-    return cudaLaunchKernelEx(&cfg, k_batch<1, P_F32, TFV>, a, pass0, pass1, npass, cur0);
+    if (b->precision == P_COMP) return cudaLaunchKernelEx(&cfg, k_batch<1, P_COMP, TFV, FO>, a, pass0, pass1, npass, cur0);
+    return cudaLaunchKernelEx(&cfg, k_batch<1, P_F32, TFV, FO>, a, pass0, pass1, npass, cur0);
 }
 
-vga_status batch_grid(vga_batch *b) {
+// Resident blocks of an instantiation, limited by blocks_per_sm and the tile count.
+vga_status batch_grid_of(vga_batch *b, const void *fn, int *grid) {
     int dev = 0, sms = 0, per_sm = 0;
     VGA_CUDA(cudaGetDevice(&dev));
     VGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const void *fn = b->tz ? batch_kernel<1>(b) : batch_kernel<0>(b);
     VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kTile, 0));
     if (per_sm < 1) return fail(VGA_ERR_CUDA, "batched kernel cannot be resident");
     const int want = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, per_sm) : per_sm;
-    b->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)want * sms, b->ntiles));
+    *grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)want * sms, b->ntiles));
     return VGA_OK;
+}
+
+vga_status batch_grid(vga_batch *b) {
+    VGA_TRY(batch_grid_of(b, b->tz ? batch_kernel<1, false>(b) : batch_kernel<0, false>(b), &b->grid_edge));
+    return batch_grid_of(b, b->tz ? batch_kernel<1, true>(b) : batch_kernel<0, true>(b), &b->grid);
 }
 
 vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
@@ -255,8 +276,18 @@ vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npas
     }
     a.bar = b->bar;
     a.err = b->err;
+    for (int k = 0; k < 2; ++k) {
+        for (int c = 0; c < 5; ++c) {
+            a.io[k].in[c] = b->h[k] + c * b->npad;
+            a.io[k].lin[c] = b->l[k] + c * b->npad;
+            a.io[k].out[c] = b->h[1 - k] + c * b->npad;
+            a.io[k].lout[c] = b->l[1 - k] + c * b->npad;
+        }
+    }
+    // the first and the last pass of a call need the full kernel; the others run the fused-only one
+    const bool fused_only = pass0 > 0 && pass1 < npass;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)b->grid);
+    cfg.gridDim = dim3((unsigned)(fused_only ? b->grid : b->grid_edge));
     cfg.blockDim = dim3(kTile);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = b->stream;
@@ -265,20 +296,30 @@ vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npas
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = b->tz ? batch_launch_tf<1>(b, cfg, a, pass0, pass1, npass, cur0)
-                                : batch_launch_tf<0>(b, cfg, a, pass0, pass1, npass, cur0);
+    const cudaError_t e = fused_only ? (b->tz ? batch_launch_tf<1, true>(b, cfg, a, pass0, pass1, npass, cur0)
+                                              : batch_launch_tf<0, true>(b, cfg, a, pass0, pass1, npass, cur0))
+                                     : (b->tz ? batch_launch_tf<1, false>(b, cfg, a, pass0, pass1, npass, cur0)
+                                              : batch_launch_tf<0, false>(b, cfg, a, pass0, pass1, npass, cur0));
     if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of k_batch", __FILE__, __LINE__);
     return VGA_OK;
+}
+
+// Launches of one call: the first pass alone, the fused passes in launches of steps_per_launch
+// passes, the last pass alone.
+int64_t launches_of(const vga_batch *b, int64_t n_steps) {
+    const int64_t S = std::max(1, b->steps_per_launch), mid = n_steps - 1;
+    return 2 + (mid > 0 ? (mid + S - 1) / S : 0);
 }
 
 vga_status enqueue_steps(vga_batch *b, int64_t n_steps, int cur0) {
     const int64_t npass = n_steps + 1;
     const int S = std::max(1, b->steps_per_launch);
-    for (int64_t p0 = 0; p0 < npass; p0 += S) {
-        const int64_t p1 = std::min(npass, p0 + S);
+    VGA_TRY(launch_batch(b, 0, 1, (int32_t)npass, cur0));
+    for (int64_t p0 = 1; p0 < npass - 1; p0 += S) {
+        const int64_t p1 = std::min(npass - 1, p0 + S);
         VGA_TRY(launch_batch(b, (int32_t)p0, (int32_t)p1, (int32_t)npass, cur0));
     }
-    return VGA_OK;
+    return launch_batch(b, (int32_t)(npass - 1), (int32_t)npass, (int32_t)npass, cur0);
 }
 
 vga_status check_err(vga_batch *b) {
@@ -510,7 +551,7 @@ vga_status vga_batch_step(vga_batch *b, int64_t n_steps) {
     } else {
         VGA_TRY(enqueue_steps(b, n_steps, cur0));
     }
-    b->launches += (n_steps + 1 + b->steps_per_launch - 1) / b->steps_per_launch;
+    b->launches += launches_of(b, n_steps);
     b->cur = (int)((cur0 + n_steps + 1) & 1);
     b->steps_done += n_steps;
     return check_err(b);
