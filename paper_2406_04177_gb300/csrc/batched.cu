@@ -43,31 +43,23 @@ struct BatchArgs {
     NbrTable tb;
     float *h[2];
     res_t *l[2];
-    unsigned *bar;  // [0] arrivals, [1] generation, [2 + (pass & 1)] work counter of a fused pass
+    unsigned *bar;  // [0] arrivals, [1] generation
     int32_t *err;
     StateIO io[2];  // a pass whose input is state buffer k reads io[k] (kept as kernel parameters)
 };
 
 // One fused pass over the whole batch, kBatchGroup consecutive nodes per thread (table_vec).
-// Blocks claim super-tiles of kTile * kBatchGroup nodes from the pass's work counter (a block that
-// is ahead takes more, so all arrive at the next barrier together).  Instances start on tile
-// boundaries, so a group never straddles two and the 32 K nodes of a warp belong to one instance,
-// whose parameters the warp reads from shared memory (per-thread copies would hold a dozen
-// registers); every thread of a block handles the same super-tiles (the warp-wide shuffles need
-// all lanes).
+// Instances start on tile boundaries, so a group never straddles two and the 32 K nodes of a warp
+// belong to one instance, whose parameters the warp reads from shared memory (per-thread copies
+// would hold a dozen registers); every thread of a block runs the same number of iterations (the
+// warp-wide shuffles need all lanes).
 template <int TR, int PREC, int TF>
-__device__ __forceinline__ void batch_fused_pass(const BatchArgs &a, const StateIO &io, unsigned *counter) {
+__device__ __forceinline__ void batch_fused_pass(const BatchArgs &a, const StateIO &io) {
     constexpr int KG = kBatchGroup;
     __shared__ StepParams wp[kTile / 32];
-    __shared__ int64_t claimed;
     const int w = threadIdx.x >> 5;
     const int64_t nsuper = (a.ntiles + KG - 1) / KG;  // kTile * KG nodes per block iteration
-    for (;;) {
-        __syncthreads();  // every thread has read the previous claim
-        if (threadIdx.x == 0) claimed = (int64_t)atomicAdd(counter, 1u);
-        __syncthreads();
-        const int64_t sup = claimed;
-        if (sup >= nsuper) break;
+    for (int64_t sup = blockIdx.x; sup < nsuper; sup += gridDim.x) {
         const uint32_t i0 = (uint32_t)(sup * kTile * KG + (int64_t)threadIdx.x * KG);
         const int64_t tile = (int64_t)i0 / kTile;
         uint32_t end = 0;  // one past the instance's last node (0: no instance here)
@@ -91,17 +83,14 @@ __global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int
     for (int32_t pass = pass0; pass < pass1; ++pass) {
         // transform / fused / diffuse
         const int kind = FUSED_ONLY ? 1 : ((pass == 0) ? 0 : (pass == npass - 1 ? 2 : 1));
-        // the next pass's work counter was last used two passes ago: clear it for the next pass
-        // (the barrier or the launch boundary after this pass publishes the store)
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.bar[2 + ((pass + 1) & 1)] = 0u;
         const int bi = (cur0 + pass) & 1, bo = bi ^ 1;
         const float *__restrict__ Y2 = a.h[bi] + a.npad;
         if (kind == 1) {
             // fused pass: kBatchGroup consecutive nodes per thread (table_vec).  Instances start on
             // tile boundaries, so a group never straddles two; every thread of a block runs the
             // same number of iterations (the warp-wide shuffles need all lanes).
-            if (bi == 0) batch_fused_pass<TR, PREC, TF>(a, a.io[0], a.bar + 2 + (pass & 1));
-            else batch_fused_pass<TR, PREC, TF>(a, a.io[1], a.bar + 2 + (pass & 1));
+            if (bi == 0) batch_fused_pass<TR, PREC, TF>(a, a.io[0]);
+            else batch_fused_pass<TR, PREC, TF>(a, a.io[1]);
             if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err)) return;
             continue;
         }
@@ -339,7 +328,7 @@ vga_status check_err(vga_batch *b) {
     VGA_CUDA(cudaStreamSynchronize(b->stream));
     if (h) {
         cudaMemsetAsync(b->err, 0, sizeof(int32_t), b->stream);
-        cudaMemsetAsync(b->bar, 0, 4 * sizeof(unsigned), b->stream);
+        cudaMemsetAsync(b->bar, 0, 2 * sizeof(unsigned), b->stream);
         cudaStreamSynchronize(b->stream);
         return fail(VGA_ERR_TIMEOUT, "a grid barrier of the batched kernel timed out");
     }
@@ -430,7 +419,7 @@ vga_status vga_batch_create(const vga_graph *const *graphs, const vga_params *pa
     if (st == VGA_OK) st = dmalloc((void **)&b->table, sizeof(uint32_t) * 3 * (size_t)b->npad, "batch table");
     if (st == VGA_OK) st = dmalloc((void **)&b->tile_inst, sizeof(int32_t) * std::max<size_t>(tinst.size(), 1), "tile map");
     if (st == VGA_OK) st = dmalloc((void **)&b->inst, sizeof(BInst) * (size_t)count, "instances");
-    if (st == VGA_OK) st = dmalloc((void **)&b->bar, sizeof(unsigned) * 4, "barrier");
+    if (st == VGA_OK) st = dmalloc((void **)&b->bar, sizeof(unsigned) * 2, "barrier");
     if (st == VGA_OK) st = dmalloc((void **)&b->err, sizeof(int32_t), "error flag");
     if (st == VGA_OK) {
         cudaError_t e = cudaSuccess;
@@ -444,7 +433,7 @@ vga_status vga_batch_create(const vga_graph *const *graphs, const vga_params *pa
                                 b->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(b->inst, hinst.data(), sizeof(BInst) * (size_t)count, cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * 4, b->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->bar, 0, sizeof(unsigned) * 2, b->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->err, 0, sizeof(int32_t), b->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "batch set-up", __FILE__, __LINE__);
