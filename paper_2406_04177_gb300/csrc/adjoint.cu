@@ -454,6 +454,7 @@ struct AdjointBuffers {
     int64_t npad = 0, nseg = 0, ckpt = 0, G = 0, ntheta = 0;
     // the forward pass the checkpoints belong to
     bool valid = false;
+    bool last_recorded = false;  // the records hold the last segment (written by the forward sweep)
     int64_t N = 0, cur_ckpt = 0, param_gen = -1;
     char *ck = nullptr;    // nseg checkpoints, each 5*npad floats + 5*npad u16
     float *rec_x = nullptr;   // ckpt x 5 x npad
@@ -541,14 +542,61 @@ static vga_status copy_state(vga_sim *s, PairBuf p, bool to_sim) {
     return VGA_OK;
 }
 
+// The steps of the last segment in the forward sweep, written as the backward sweep's
+// recomputation would write them: the same passes as sim_step_explicit (transformation pass, fused
+// passes on the four-node body, diffusion-only pass) with the records of X^k and y2^k, so the
+// backward sweep need not recompute that segment.  Needs the neighbour-offset table.
+template <int WM>
+static vga_status forward_recording(vga_sim *s, AdjointBuffers *a, int64_t len) {
+    constexpr int PREC = P_COMP;
+    const int64_t npad = s->npad;
+    NbrTable tb;
+    BlockTable bt;
+    bool ok = true;
+    VGA_TRY(sim_nbr_table(s, &tb));
+    if (WM == W_BLOCK) VGA_TRY(sim_block_table(s, &bt, &ok));
+    if (!ok) return VGA_ERR_UNSUPPORTED;  // the caller falls back to the plain forward
+    cudaStream_t st = s->stream;
+    const int Gv = (int)(((s->n + 3) / 4 + kThreads - 1) / kThreads);
+    timing_begin(s, VGA_KERNEL_TRANSFORM);
+    k_transform_rec<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->sp, state_io(s), a->rec_y2);
+    timing_end(s);
+    VGA_CHECK_LAUNCH();
+    ++s->launches;
+    for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
+    for (int64_t j = 1; j < len; ++j) {
+        const PassRecord pr = {a->rec_x + (size_t)j * 5 * npad, a->rec_y2 + (size_t)j * npad, npad};
+        timing_begin(s, VGA_KERNEL_FUSED_STEP);
+        if (tb.tz) k_fused_rec_vec<WM, PREC, 1><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, state_io(s), pr);
+        else k_fused_rec_vec<WM, PREC, 0><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, state_io(s), pr);
+        timing_end(s);
+        VGA_CHECK_LAUNCH();
+        ++s->launches;
+        for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
+    }
+    VGA_TRY(sim_diffuse_pass(s));
+    s->steps_done += len;
+    return VGA_OK;
+}
+
 vga_status sim_adjoint_forward(vga_sim *s, int64_t N, int64_t ckpt) {
     const int64_t nseg = N > 0 ? (N + ckpt - 1) / ckpt : 0;
     VGA_TRY(ensure_adjoint(s, std::max<int64_t>(nseg, 1), ckpt));
     AdjointBuffers *a = s->adj;
     a->valid = false;
+    a->last_recorded = false;
     for (int64_t sg = 0; sg < nseg; ++sg) {
         VGA_TRY(copy_state(s, ck_slot(a, sg), false));
         const int64_t len = std::min(ckpt, N - sg * ckpt);
+        if (sg == nseg - 1 && s->g->nx <= 32767) {
+            const vga_status r = s->wmode == W_BLOCK ? forward_recording<W_BLOCK>(s, a, len)
+                                                     : forward_recording<W_UNIT>(s, a, len);
+            if (r == VGA_OK) {
+                a->last_recorded = true;
+                continue;
+            }
+            if (r != VGA_ERR_UNSUPPORTED) return r;
+        }
         VGA_TRY(sim_step_explicit(s, len));
     }
     a->N = N;
@@ -585,32 +633,36 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     int lb = 0;
     for (int64_t sg = nseg - 1; sg >= 0; --sg) {
         const int64_t len = std::min(ckpt, N - sg * ckpt);
-        // recompute the segment, recording X^k and y2^k for k = 0 .. len-1 (relative to its start)
+        // recompute the segment, recording X^k and y2^k for k = 0 .. len-1 (relative to its start),
+        // unless the forward sweep recorded it (the last segment)
         PairBuf cks = ck_slot(a, sg);
         Rec rec;
-        timing_begin(s, VGA_KERNEL_TRANSFORM);
-        k_transform_rec<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->sp, io_from(cks, a->work[0], npad),
-                                                                            a->rec_y2);
-        timing_end(s);
-        VGA_CHECK_LAUNCH();
-        ++s->launches;
-        int wb = 0;
-        for (int64_t j = 1; j < len; ++j) {
-            rec.x = a->rec_x + (size_t)j * 5 * npad;
-            rec.y2 = a->rec_y2 + (size_t)j * npad;
-            timing_begin(s, VGA_KERNEL_FUSED_STEP);
-            if (table) {
-                const PassRecord pr = {rec.x, rec.y2, npad};
-                const StateIO io = io_from(a->work[wb], a->work[1 - wb], npad);
-                if (tb.tz) k_fused_rec_vec<WM, PREC, 1><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr);
-                else k_fused_rec_vec<WM, PREC, 0><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr);
-            } else
-                k_fused_rec<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
-                                                                io_from(a->work[wb], a->work[1 - wb], npad), npad, rec);
+        const bool recorded = sg == nseg - 1 && a->last_recorded;
+        if (!recorded) {
+            timing_begin(s, VGA_KERNEL_TRANSFORM);
+            k_transform_rec<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->sp, io_from(cks, a->work[0], npad),
+                                                                                a->rec_y2);
             timing_end(s);
             VGA_CHECK_LAUNCH();
             ++s->launches;
-            wb = 1 - wb;
+            int wb = 0;
+            for (int64_t j = 1; j < len; ++j) {
+                rec.x = a->rec_x + (size_t)j * 5 * npad;
+                rec.y2 = a->rec_y2 + (size_t)j * npad;
+                timing_begin(s, VGA_KERNEL_FUSED_STEP);
+                if (table) {
+                    const PassRecord pr = {rec.x, rec.y2, npad};
+                    const StateIO io = io_from(a->work[wb], a->work[1 - wb], npad);
+                    if (tb.tz) k_fused_rec_vec<WM, PREC, 1><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr);
+                    else k_fused_rec_vec<WM, PREC, 0><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr);
+                } else
+                    k_fused_rec<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
+                                                                    io_from(a->work[wb], a->work[1 - wb], npad), npad, rec);
+                timing_end(s);
+                VGA_CHECK_LAUNCH();
+                ++s->launches;
+                wb = 1 - wb;
+            }
         }
         // reverse
         for (int64_t j = len - 1; j >= 0; --j) {
@@ -631,6 +683,7 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
             lb = 1 - lb;
         }
     }
+    if (nseg > 1) a->last_recorded = false;  // the records now hold the first segment
     if (d_lam0) {
         k_lam_out<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, d_lam0, io_from(a->lam[lb], a->lam[lb], npad));
         VGA_CHECK_LAUNCH();

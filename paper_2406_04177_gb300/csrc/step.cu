@@ -584,6 +584,13 @@ vga_status sim_transform_pass(vga_sim *s) {
     return VGA_OK;
 }
 
+// The last pass of a step call: diffusion of the stored transformed DOM only.
+vga_status sim_diffuse_pass(vga_sim *s) {
+    VGA_TRY(launch_stencil<2>(s, state_io(s)));
+    s->cur[1] ^= 1;
+    return VGA_OK;
+}
+
 vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
     if (n_steps <= 0 || s->n == 0) {
         s->steps_done += std::max<int64_t>(n_steps, 0);

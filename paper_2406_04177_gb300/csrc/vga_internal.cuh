@@ -258,6 +258,7 @@ void timing_end_weighted(vga_sim *s, int64_t passes);  // the launch covered `pa
 // step.cu
 vga_status sim_prepare_params(vga_sim *s, const vga_params *p);
 vga_status sim_step_explicit(vga_sim *s, int64_t n_steps);
+vga_status sim_diffuse_pass(vga_sim *s);  // last pass of a step call (DOM diffusion only)
 vga_status sim_totals(vga_sim *s, double *h_out);
 vga_status sim_convert_in(vga_sim *s, const double *d_x);    // device FP64 (5 x n) -> state
 vga_status sim_convert_out(vga_sim *s, double *d_x);         // state -> device FP64 (5 x n)

@@ -38,6 +38,37 @@ def test_adjoint_forward_equals_plain_steps(vga, oracle_lib):
 
 
 @pytest.mark.parametrize("block", [False, True])
+@pytest.mark.parametrize("nsteps,ckpt", [(37, 5), (20, 20)])
+def test_backward_twice_and_recorded_segment(vga, oracle_lib, block, nsteps, ckpt):
+    """The forward sweep records the last segment and the backward sweep skips recomputing it.
+    Two backward sweeps over one forward (after the first, the records hold another segment when
+    there are several) and those of a second simulation run through the same calls give the same
+    bits; agreement with the oracle is test_adjoint_matches_oracle's."""
+    img, og, g, X0 = _setup(vga, oracle_lib)
+    bs = 8
+    theta = synth.block_conductances(oracle_lib.block_grid(img.shape, bs), 4) if block else None
+    p = synth.paper_params(dt=0.9 / (6 * synth.D_DOM * (theta.max() if block else 1.0)))
+    lamN = np.random.default_rng(9).standard_normal((5, og.n))
+    runs = []
+    for _ in range(2):
+        sim = vga.Sim(g, p)
+        if block:
+            sim.set_block_conductances(bs, theta.astype(np.float32))
+        sim.set_masses(X0)
+        sim.adjoint_forward(nsteps, ckpt)
+        for _ in range(2):
+            lam0 = np.empty((5, og.n))
+            grad, gth = sim.adjoint_backward(lamN, lam0, n_theta=0 if theta is None else theta.size)
+            runs.append((lam0, grad, gth))
+        sim.close()
+    for lam0, grad, gth in runs[1:]:
+        assert np.array_equal(lam0, runs[0][0])
+        assert grad == runs[0][1]
+        if block:
+            assert np.array_equal(gth, runs[0][2])
+
+
+@pytest.mark.parametrize("block", [False, True])
 def test_adjoint_matches_oracle(vga, oracle_lib, block):
     img, og, g, X0 = _setup(vga, oracle_lib)
     nsteps, ckpt, bs = 60, 7, 8
