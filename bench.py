@@ -8,8 +8,12 @@ largest 6-connected component kept), the Sec. IV.C parameters and initial masses
 (PVS/s): nodes x time steps / second.
 
 Printed: one JSON line (rank 0).  Keys beyond the base contract:
-  roofline       fused explicit kernel: algorithmic bytes (40 B per node) / mean launch time,
-                 timed with CUDA events on its stream during the timed region
+  roofline       fused explicit kernel: algorithmic bytes / mean launch time, timed with CUDA
+                 events on its stream during the timed region.  Algorithmic bytes of a pass: 40 B
+                 per node (five FP32 compartments read and written) for the dense pass; for the
+                 sparse pass (the default) 8 B per node (DOM) + 32 B per node the transformation
+                 can change (MB, SOM, FOM, CO2; `active_nodes`)
+  dense_pass     the same timed loop with the sparse pass switched off (every node transformed)
   cpu_baseline   the FP64 oracle on the host cores over a bounded number of time steps
   error_vs_fp64  GPU after those same steps against the oracle (relative L2 per compartment,
                  total-mass drift)
@@ -38,6 +42,7 @@ import numpy as np  # noqa: E402
 METRIC = "pore-voxel-steps/s fwd & adjoint at 512³, % HBM roofline, at stated err vs FP64"
 UNIT = "pore-voxel-steps/s"
 BYTES_PER_PVS = 40  # five FP32 compartments read and written per node and time step
+BYTES_DOM = 8       # the diffusing DOM read and written (FP32)
 
 
 def parse_args():
@@ -58,6 +63,8 @@ def parse_args():
                     help="comma-separated subset of the extra measurements to run")
     ap.add_argument("--adj-steps", type=int, default=200, help="time steps of the adjoint measurement")
     ap.add_argument("--adj-ckpt", type=int, default=100, help="checkpoint spacing of the adjoint measurement")
+    ap.add_argument("--dense", action="store_true",
+                    help="switch the sparse fused pass off (every node transformed every pass)")
     ap.add_argument("--kernel", default=None,
                     help="fix the explicit kernel instead of autotuning: 'variant:chunk' or '3:chunk:depth:ctas'")
     return ap.parse_args()
@@ -87,18 +94,19 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(n_nodes: int):
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary, scaled to this
-    workload by the node count; None when the kernel source changed since the capture."""
+def recorded_traffic(n_nodes: int, kind: str = "sparse"):
+    """DRAM bytes per launch of the fused kernel ("sparse" or "dense" pass) from the committed ncu
+    summary, scaled to this workload by the node count; None when the kernel source changed since
+    the capture."""
     path = os.path.join(ROOT, "profiles", "fused_step_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except Exception:
         return None
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash() or kind not in d.get("passes", {}):
         return None
-    return float(d["dram_bytes_per_node"]) * n_nodes
+    return float(d["passes"][kind]["dram_bytes_per_node"]) * n_nodes
 
 
 class ClockSampler:
@@ -226,6 +234,8 @@ def bench_ours(a):
     n = g.n
     params = synth.paper_params()
     sim = vga.Sim(g, params, stream=stream)
+    if a.dense:
+        sim.set_activity_skip(False)
     x0_dev = torch.from_numpy(X0).cuda()
     sim.set_masses(x0_dev)
     if a.kernel:
@@ -286,10 +296,13 @@ def bench_ours(a):
     fused_ms, fused_count = timing["fused_step"]
     mean_launch_s = fused_ms / max(fused_count, 1) / 1e3
     peak, peak_src = load_peaks()
-    achieved = BYTES_PER_PVS * n / mean_launch_s / 1e9
-    traffic = recorded_traffic(n)
     best = tune["best"] or {}
     variant = best.get("variant")
+    n_active = sim.stats()["active_nodes"]
+    sparse = variant == 5 and n_active >= 0
+    alg_bytes = (BYTES_DOM * n + (BYTES_PER_PVS - BYTES_DOM) * n_active) if sparse else BYTES_PER_PVS * n
+    achieved = alg_bytes / mean_launch_s / 1e9
+    traffic = recorded_traffic(n, "sparse" if sparse else "dense")
     kname = {0: "k_stencil (chunk decode, direct loads)", 1: "k_stencil_staged (chunk decode, bulk-copy staging)",
              2: "k_stencil_table (neighbour-offset table)",
              4: "k_stencil_tablev (neighbour-offset table, two nodes per thread, 8-byte vector streams)",
@@ -297,12 +310,45 @@ def bench_ours(a):
              3: f"k_wave (neighbour-offset table; {S - 1} fused passes per persistent launch as an L2 wavefront, "
                 f"chunks of {best.get('chunk')} nodes, {best.get('depth')} passes per block)"}.get(variant, "k_stencil")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": f"{kname}, fused pass (diffuse the stored transformed DOM, then transform)",
-                "algorithmic_bytes_per_pass": BYTES_PER_PVS * n, "mean_pass_ms": mean_launch_s * 1e3,
+                "traffic": traffic, "kernel": f"{kname}, fused pass (diffuse the stored transformed DOM, then transform)"
+                + (f"; sparse: {n_active} of {n} nodes can change under the transformation, the others only diffuse"
+                   if sparse else ""),
+                "algorithmic_bytes_per_pass": alg_bytes, "active_nodes": n_active if sparse else n,
+                "mean_pass_ms": mean_launch_s * 1e3,
                 "passes_timed": fused_count, "passes_per_launch": (S - 1) if variant == 3 else 1,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_src == "measured" else "fallback 6.8 TB/s",
-                "pvs_x40B_over_peak": value / world * BYTES_PER_PVS / (peak * 1e9)}
+                # PVS/s x 40 B over the peak: the bandwidth a dense pass would need for this rate
+                "dense_equivalent_frac": value / world * BYTES_PER_PVS / (peak * 1e9)}
+
+    # ---- the dense pass (every node transformed) on the same loop, for comparison ----
+    dense = None
+    if sparse:
+        sim.set_activity_skip(False)
+        sim.step(S)
+        sim.enable_timing(True)
+        sim.read_timing(reset=True)
+        dsteps = max(2, a.steps // 4)
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        for _ in range(dsteps):
+            sim.step(S)
+            sim.totals()
+        d1.record(stream)
+        torch.cuda.synchronize()
+        dtiming = sim.read_timing(reset=True)
+        sim.enable_timing(False)
+        sim.set_activity_skip(True)
+        dms = d0.elapsed_time(d1)
+        dfm, dfc = dtiming["fused_step"]
+        dmean = dfm / max(dfc, 1) / 1e3
+        dach = BYTES_PER_PVS * n / dmean / 1e9
+        dense = {"value": world * n * S * dsteps / (dms / 1e3), "unit": UNIT, "steps": dsteps,
+                 "ms_per_step": dms / dsteps, "mean_pass_ms": dmean * 1e3,
+                 "roofline": {"bound": "hbm", "achieved": dach, "peak": peak, "unit": "GB/s", "frac": dach / peak,
+                              "traffic": recorded_traffic(n, "dense"), "algorithmic_bytes_per_pass": BYTES_PER_PVS * n}}
 
     # ---- end to end through the C ABI with host buffers (outside the timed region) ----
     xh = torch.from_numpy(X0.astype(np.float32)).pin_memory()
@@ -337,6 +383,7 @@ def bench_ours(a):
                       "time_steps_per_step": S, "l2": "inputs larger than L2: two FP32 state buffers of "
                       f"{5 * 4 * n / 1e6:.0f} MB each", "parallelism": "replicas" if world > 1 else "single GPU"},
            "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+           "dense_pass": dense,
            "kernel_time_ms": {k: v[0] for k, v in timing.items() if v[1]},
            "autotune": tune,
            "drift_timed_region": float(abs(tot1.sum() - tot0.sum()) / tot0.sum())}

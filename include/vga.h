@@ -212,6 +212,7 @@ typedef struct vga_sim_stats {
     double cg_last_relres;    /* implicit scheme: final relative residual of the last solve */
     int64_t kernel_launches;  /* kernels launched since creation (inside a graph: kernels it ran) */
     int64_t graph_launches;   /* implicit scheme: CUDA graph launches of the mixed solve */
+    int64_t active_nodes;     /* nodes the sparse fused pass transforms (-1: no activity mask built) */
 } vga_sim_stats;
 vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out);
 
@@ -271,6 +272,16 @@ vga_status vga_loss_block_mass(vga_sim *s, int32_t block_side, uint32_t comp_mas
  *   5  as 2 with four consecutive nodes per thread, 16-byte and 8-byte vectors.
  * For 4 and 5 `chunk` is ignored.  The default is 5 (the fastest at 512^3 on GB300). */
 vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t chunk);
+
+/* Sparse fused pass of variant 5 (on by default).  Every flux of the transformation (Sec. II.C) is
+ * proportional to MB, SOM or FOM, so at nodes where MB, SOM, FOM and CO2 are all zero the
+ * transformation is the identity, and it stays so while stepping (no flux can make them nonzero).
+ * The first step after a state upload (vga_sim_set_masses, vga_sim_set_state_f32,
+ * vga_sim_load_state) marks the other nodes in a bit mask (one extra pass, one synchronisation);
+ * fused passes then diffuse only the DOM of groups of four unmarked nodes and leave their MB, SOM,
+ * FOM and CO2 unread and unwritten.  Results are bit-identical with the mask off (also a node whose
+ * values are negative zeros is marked).  on = 0 processes every node every pass. */
+vga_status vga_sim_set_activity_skip(vga_sim *s, int32_t on);
 
 /* Selects variant 3 with `chunk` nodes per work item (a power of two in [256, 8192]; CTAs of
  * min(chunk, 1024) threads), `depth`

@@ -79,7 +79,8 @@ class vga_batch_tune(C.Structure):
 
 class vga_sim_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("cg_iterations", C.c_int64),
-                ("cg_last_relres", C.c_double), ("kernel_launches", C.c_int64), ("graph_launches", C.c_int64)]
+                ("cg_last_relres", C.c_double), ("kernel_launches", C.c_int64), ("graph_launches", C.c_int64),
+                ("active_nodes", C.c_int64)]
 
 
 VGA_KERNEL_KINDS = 8
@@ -123,6 +124,7 @@ _SIGNATURES = {
     "vga_sim_get_block_conductances": [_P, _P, _I64],
     "vga_sim_set_kernel": [_P, _I32, _I32],
     "vga_sim_set_solver": [_P, _I32],
+    "vga_sim_set_activity_skip": [_P, _I32],
     "vga_sim_set_wavefront": [_P, _I32, _I32, _I32],
     "vga_sim_autotune": [_P, _I32, _P],
     "vga_sim_enable_timing": [_P, _I32],
@@ -400,6 +402,10 @@ def vga_sim_set_solver(s, solver: int):
     _check(load_library().vga_sim_set_solver(s, int(solver)), "vga_sim_set_solver")
 
 
+def vga_sim_set_activity_skip(s, on: bool):
+    _check(load_library().vga_sim_set_activity_skip(s, 1 if on else 0), "vga_sim_set_activity_skip")
+
+
 def vga_sim_set_wavefront(s, chunk: int, depth: int, ctas_per_sm: int = 0):
     _check(load_library().vga_sim_set_wavefront(s, int(chunk), int(depth), int(ctas_per_sm)), "vga_sim_set_wavefront")
 
@@ -620,6 +626,9 @@ class Sim:
 
     def set_solver(self, solver: int):
         vga_sim_set_solver(self.handle, solver)
+
+    def set_activity_skip(self, on: bool):
+        vga_sim_set_activity_skip(self.handle, on)
 
     def set_wavefront(self, chunk: int, depth: int, ctas_per_sm: int = 0):
         vga_sim_set_wavefront(self.handle, chunk, depth, ctas_per_sm)

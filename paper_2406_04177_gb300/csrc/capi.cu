@@ -515,6 +515,12 @@ vga_status vga_sim_load_state(vga_sim *s, const void *buf, int64_t bytes) {
     return VGA_OK;
 }
 
+vga_status vga_sim_set_activity_skip(vga_sim *s, int32_t on) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    s->activity_skip = on != 0;
+    return VGA_OK;
+}
+
 vga_status vga_sim_set_solver(vga_sim *s, int32_t solver) {
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
     if (solver != VGA_SOLVER_FP64_PCG && solver != VGA_SOLVER_MIXED_REFINEMENT && solver != VGA_SOLVER_MIXED_HOST_LOOP)
@@ -550,6 +556,7 @@ vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out) {
     out->cg_last_relres = s->cg_last_relres;
     out->kernel_launches = s->launches;
     out->graph_launches = s->graph_launches;
+    out->active_nodes = s->n_active;
     return VGA_OK;
 }
 
@@ -668,6 +675,7 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->d_err);
     dfree(s->nbr_table);
     dfree(s->nbr_tz);
+    dfree(s->active);
     dfree(s->bnode);
     dfree(s->bface);
     dfree(s->btheta6);

@@ -442,18 +442,23 @@ __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const Step
 // previous lane's last node and the +x neighbour of the last node the next lane's first node.
 // Arithmetic and slot order per node are those of table_node, so the results are the same bits.
 // Rows and tables start on 16-byte boundaries (row strides are multiples of 64 values).  REC (fused
-// passes only): also writes the pass record of the discrete adjoint.  Must be called by all 32
-// lanes of a warp.
-template <int MODE, int WM, int TR, int PREC, int TF, int K, bool REC = false>
+// passes only): also writes the pass record of the discrete adjoint.  SKIP (fused passes only):
+// groups whose K bits in `active` are all clear hold nodes where the transformation is the
+// identity (MB, SOM, FOM and CO2 zero: every flux vanishes), so only their DOM is diffused,
+// rounded and stored; MB, SOM, FOM and CO2 are neither read nor written (both state buffers hold
+// zeros there).  Must be called by all 32 lanes of a warp.
+template <int MODE, int WM, int TR, int PREC, int TF, int K, bool REC = false, bool SKIP = false>
 __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTable &tb, const BlockTable &bt,
                                           const StepParams &p, const StateIO &io,
-                                          const PassRecord &rec = PassRecord{}) {
+                                          const PassRecord &rec = PassRecord{}, const uint32_t *active = nullptr) {
     const bool full = i0 + K <= n;
     const float *__restrict__ Y2 = io.in[1];
     uint32_t ty[K], zm[K], zp[K], bn[K];
     V x2[K];
     if (full) group_load<WM, PREC, TF, K, true>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
     else group_load<WM, PREC, TF, K, false>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
+    uint32_t live_bits = 1u;  // SKIP: activity bits of the group (0: the transformation is the identity)
+    if (SKIP && MODE == 1 && i0 < n) live_bits = (__ldg(active + (i0 >> 5)) >> (i0 & 31)) & ((1u << K) - 1u);
     float y[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) y[k] = x2[k].h;
@@ -487,6 +492,13 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
         if (zm[k]) add(4, zv[k]);
         if (zp[k]) add(5, zw[k]);
         vadd<PREC>(x2[k], __fmul_rn(-p.c, acc));  // Scheme 1
+    }
+    if (SKIP && MODE == 1 && live_bits == 0u) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) vround<PREC>(x2[k]);
+        if (full) vstore_k<PREC, K, true>(io.out[1], io.lout[1], i0, n, x2);
+        else vstore_k<PREC, K, false>(io.out[1], io.lout[1], i0, n, x2);
+        return;
     }
     if (full) group_finish<MODE, TR, PREC, K, true, REC>(i0, n, p, io, x2, rec);
     else group_finish<MODE, TR, PREC, K, false, REC>(i0, n, p, io, x2, rec);

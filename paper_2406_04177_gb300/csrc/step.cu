@@ -281,11 +281,46 @@ __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable 
 }
 
 // K consecutive nodes per thread (table_vec); n < 2^31, so K * thread index fits 32 bits.
-template <int MODE, int WM, int TR, int PREC, int TF, int K>
+template <int MODE, int WM, int TR, int PREC, int TF, int K, bool SKIP>
 __global__ void __launch_bounds__(kThreads) k_stencil_tablev(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
-                                                             StateIO io) {
+                                                             StateIO io, const uint32_t *__restrict__ active) {
     const uint32_t i0 = (uint32_t)K * ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x);
-    table_vec<MODE, WM, TR, PREC, TF, K>(i0, (uint32_t)n, tb, bt, p, io);
+    table_vec<MODE, WM, TR, PREC, TF, K, false, SKIP>(i0, (uint32_t)n, tb, bt, p, io, PassRecord{}, active);
+}
+
+// Activity mask of the sparse fused pass (vga_sim.active): bit i set when node i may change under
+// the transformation: any bit of MB, SOM, FOM or CO2 (value or residual) nonzero, or a
+// negative-zero DOM (the transformation's zero increment would turn it into +0).  Every flux of
+// both transformations is proportional to MB, SOM or FOM, so at the other nodes the
+// transformation is the identity and stays so.  Those nodes also get zeros in the spare buffers
+// of MB, SOM, FOM and CO2 (their current values are zero), so that a pass may skip them.
+template <int PREC>
+__global__ void k_build_active(int64_t n, StateIO cur, StateIO spare, uint32_t *__restrict__ mask,
+                               unsigned long long *__restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool act = false;
+    if (i < n) {
+        const int cs[4] = {0, 2, 3, 4};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            act |= __float_as_uint(cur.in[cs[q]][i]) != 0u;
+            if (PREC == P_COMP) act |= cur.lin[cs[q]][i] != 0;
+        }
+        act |= __float_as_uint(cur.in[1][i]) == 0x80000000u;
+        if (PREC == P_COMP) act |= cur.lin[1][i] == (res_t)0x8000u;
+        if (!act) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                spare.out[cs[q]][i] = 0.0f;
+                if (PREC == P_COMP) spare.lout[cs[q]][i] = 0;
+            }
+        }
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, act);
+    if ((threadIdx.x & 31) == 0 && i < n) {
+        mask[i >> 5] = b;
+        atomicAdd(count, (unsigned long long)__popc(b));
+    }
 }
 
 // Largest z offset of the table (for the compact form).
@@ -421,16 +456,24 @@ void launch_staged_any(vga_sim *s, const StateIO &io) {
     }
 }
 
+template <int MODE, int WM, int PREC, int K, bool SKIP>
+void launch_tablev_s(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
+    const unsigned grid = grid_for((s->n + K - 1) / K, kThreads);
+    const uint32_t *act = s->active;
+    if (tb.tz) {
+        if (s->sp.transform == 0) k_stencil_tablev<MODE, WM, 0, PREC, 1, K, SKIP><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io, act);
+        else k_stencil_tablev<MODE, WM, 1, PREC, 1, K, SKIP><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io, act);
+    } else {
+        if (s->sp.transform == 0) k_stencil_tablev<MODE, WM, 0, PREC, 0, K, SKIP><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io, act);
+        else k_stencil_tablev<MODE, WM, 1, PREC, 0, K, SKIP><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io, act);
+    }
+}
+
+// Fused passes of the four-node kernel use the activity mask when it is valid for the state.
 template <int MODE, int WM, int PREC, int K>
 void launch_tablev(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
-    const unsigned grid = grid_for((s->n + K - 1) / K, kThreads);
-    if (tb.tz) {
-        if (s->sp.transform == 0) k_stencil_tablev<MODE, WM, 0, PREC, 1, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
-        else k_stencil_tablev<MODE, WM, 1, PREC, 1, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
-    } else {
-        if (s->sp.transform == 0) k_stencil_tablev<MODE, WM, 0, PREC, 0, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
-        else k_stencil_tablev<MODE, WM, 1, PREC, 0, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io);
-    }
+    if (MODE == 1 && K == 4 && s->activity_skip && s->active_valid) launch_tablev_s<MODE, WM, PREC, K, true>(s, io, tb, bt);
+    else launch_tablev_s<MODE, WM, PREC, K, false>(s, io, tb, bt);
 }
 
 template <int MODE, int WM, int PREC>
@@ -591,11 +634,44 @@ vga_status sim_diffuse_pass(vga_sim *s) {
     return VGA_OK;
 }
 
+// Builds the activity mask for the current state (once per state upload; stepping keeps it valid).
+vga_status sim_build_active(vga_sim *s) {
+    if (!s->active) {
+        const size_t words = (size_t)(std::max<int64_t>(s->npad, 64) + 31) / 32 + 8;
+        VGA_TRY(dmalloc((void **)&s->active, sizeof(uint32_t) * words + sizeof(unsigned long long), "activity mask"));
+        VGA_CUDA(cudaMemsetAsync(s->active, 0, sizeof(uint32_t) * words, s->stream));
+    }
+    const size_t words = (size_t)(std::max<int64_t>(s->npad, 64) + 31) / 32 + 8;
+    unsigned long long *count = reinterpret_cast<unsigned long long *>(s->active + words);
+    VGA_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s->stream));
+    StateIO cur = state_io(s), spare;
+    for (int c = 0; c < 5; ++c) {
+        spare.in[c] = s->spare(c);
+        spare.out[c] = s->spare(c);
+        spare.lin[c] = s->lspare(c);
+        spare.lout[c] = s->lspare(c);
+    }
+    if (s->precision() == P_COMP)
+        k_build_active<P_COMP><<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, cur, spare, s->active, count);
+    else
+        k_build_active<P_F32><<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, cur, spare, s->active, count);
+    VGA_CHECK_LAUNCH();
+    ++s->launches;
+    unsigned long long h = 0;
+    VGA_CUDA(cudaMemcpyAsync(&h, count, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    s->n_active = (int64_t)h;
+    s->active_valid = true;
+    return VGA_OK;
+}
+
 vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
     if (n_steps <= 0 || s->n == 0) {
         s->steps_done += std::max<int64_t>(n_steps, 0);
         return VGA_OK;
     }
+    if (s->activity_skip && !s->active_valid && (s->kernel_variant == 5) && s->g->nx <= 32767)
+        VGA_TRY(sim_build_active(s));
     const bool sub = s->subcycled();
     const int64_t k0 = s->steps_done;
     // ntrans is reset on every exit so that no other path sees a sub-cycled count
@@ -641,6 +717,7 @@ vga_status sim_totals(vga_sim *s, double *h_out) {
 }
 
 vga_status sim_convert_in(vga_sim *s, const double *d_x) {
+    s->active_valid = false;
     if (s->n == 0) return VGA_OK;
     k_convert_in<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, d_x, state_io_inplace(s),
                                                                      s->precision() == P_COMP);
@@ -659,6 +736,7 @@ vga_status sim_convert_out(vga_sim *s, double *d_x) {
 }
 
 vga_status sim_pack_f32(vga_sim *s, float *d_x, bool to_state) {
+    if (to_state) s->active_valid = false;
     if (s->n == 0) return VGA_OK;
     k_pack<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, d_x, state_io_inplace(s), to_state ? 1 : 0,
                                                                s->precision() == P_COMP);
@@ -678,6 +756,7 @@ vga_status sim_res_export(vga_sim *s, uint16_t *d_out) {
 }
 
 vga_status sim_res_import(vga_sim *s, const uint16_t *d_in) {
+    s->active_valid = false;
     if (s->n == 0) return VGA_OK;
     k_res_import<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, d_in, state_io_inplace(s));
     VGA_CHECK_LAUNCH();

@@ -201,6 +201,12 @@ struct vga_sim {
     bool mx_graph_failed = false;  // graph construction failed once: host-driven loop from then on
     void *mx_graph = nullptr;      // cached graphs of the mixed solve (pcg.cu)
     int64_t graph_launches = 0;    // CUDA graph launches of the mixed solve
+    // Sparse fused pass: bit i of `active` set when node i may change under the transformation
+    // (MB, SOM, FOM or CO2 nonzero, or a negative-zero DOM); such a set never grows while stepping.
+    uint32_t *active = nullptr;    // ceil(npad / 32) + 8 words
+    bool active_valid = false;     // built for the current state (cleared by every state upload)
+    bool activity_skip = true;     // use it (vga_sim_set_activity_skip)
+    int64_t n_active = -1;         // nodes marked in the last build (-1: none built)
     int64_t steps_done = 0;
     int64_t cg_iterations = 0;
     double cg_last_relres = 0.0;

@@ -304,3 +304,59 @@ def test_pair_kernel_ragged_rows(vga, oracle_lib, nx):
     last = vga.Sim(g, p)
     last.load_state(outs[1])
     _assert_close(last.get_masses(), oracle_lib.explicit_run(og.nbr, p, X0, 7))
+
+
+@pytest.mark.parametrize("block,transform,precision,organic", [(False, 0, 0, False), (False, 0, 0, True),
+                                                               (True, 0, 0, False), (False, 1, 0, False),
+                                                               (False, 0, 1, False)])
+def test_activity_skip_bit_identical(vga, oracle_lib, block, transform, precision, organic):
+    """The sparse fused pass (groups of four nodes with MB = SOM = FOM = CO2 = 0 only diffuse DOM)
+    gives the bits of the dense pass and of the one-node-per-thread kernel; the mask is rebuilt
+    after each state upload (set_masses, set_state_f32, load_state), including states with negative
+    zeros, and counts the nodes with any nonzero bit in MB, SOM, FOM or CO2."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (40, 48, 37), 0.24, 21, organic=organic)
+    p = synth.paper_params(transform=transform)
+    p["state_precision"] = precision
+    bs = 8
+    theta = synth.block_conductances(oracle_lib.block_grid(img.shape, bs), 4) if block else None
+    if block:
+        p["dt"] = 0.9 / (6 * synth.D_DOM * theta.max())
+    X1 = X0.copy()
+    rng = np.random.default_rng(3)
+    X1[0, rng.choice(g.n, 40, replace=False)] = -0.0  # negative zeros mark a node as well
+    X1[1, rng.choice(g.n, 40, replace=False)] = -0.0
+    X1[0, rng.choice(g.n, 200, replace=False)] = 1e-4  # more biomass: a second, denser mask
+
+    def run(variant, skip):
+        sim = vga.Sim(g, p)
+        sim.set_kernel(variant, 1024)
+        sim.set_activity_skip(skip)
+        if block:
+            sim.set_block_conductances(bs, theta.astype(np.float32))
+        sim.set_masses(X0)
+        sim.step(30)
+        a = sim.save_state()
+        n0 = sim.stats()["active_nodes"]
+        sim.set_masses(X1)
+        sim.step(17)
+        b = sim.save_state()
+        n1 = sim.stats()["active_nodes"]
+        sim.load_state(a)
+        sim.step(5)
+        c = sim.save_state()
+        sim.set_state_f32(X0.astype(np.float32))
+        sim.step(3)
+        d = sim.save_state()
+        sim.close()
+        return (a, b, c, d), (n0, n1)
+
+    ref, _ = run(2, False)
+    dense, nd = run(5, False)
+    sparse, ns = run(5, True)
+    assert dense == ref
+    assert sparse == ref
+    assert nd == (-1, -1)
+    marked = lambda X: int(np.count_nonzero((np.signbit(X[[0, 2, 3, 4]]) | (X[[0, 2, 3, 4]] != 0)).any(axis=0)
+                                            | (np.signbit(X[1]) & (X[1] == 0))))
+    assert ns == (marked(X0), marked(X1))
+    assert 0 < ns[0] < g.n
