@@ -442,12 +442,13 @@ __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const Step
 // previous lane's last node and the +x neighbour of the last node the next lane's first node.
 // Arithmetic and slot order per node are those of table_node, so the results are the same bits.
 // Rows and tables start on 16-byte boundaries (row strides are multiples of 64 values).  REC (fused
-// passes only): also writes the pass record of the discrete adjoint.  SKIP (fused passes only):
-// groups whose K bits in `active` are all clear hold nodes where the transformation is the
-// identity (MB, SOM, FOM and CO2 zero: every flux vanishes), so only their DOM is diffused,
-// rounded and stored; MB, SOM, FOM and CO2 are neither read nor written (both state buffers hold
-// zeros there).  Must be called by all 32 lanes of a warp.
-template <int MODE, int WM, int TR, int PREC, int TF, int K, bool REC = false, bool SKIP = false>
+// passes only): also writes the pass record of the discrete adjoint.  MODE 3 is the first half of
+// the sparse fused pass: the DOM is diffused and rounded as in MODE 1 and stored; a node whose bit
+// in `active` is set keeps the rounded pair as it is (the transformation pass reads it back
+// exactly as MODE 1 holds it in registers), the others are stored as MODE 1 stores a DOM that the
+// (identity) transformation left unchanged.  MB, SOM, FOM and CO2 are not touched.  Must be called
+// by all 32 lanes of a warp.
+template <int MODE, int WM, int TR, int PREC, int TF, int K, bool REC = false>
 __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTable &tb, const BlockTable &bt,
                                           const StepParams &p, const StateIO &io,
                                           const PassRecord &rec = PassRecord{}, const uint32_t *active = nullptr) {
@@ -457,8 +458,8 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
     V x2[K];
     if (full) group_load<WM, PREC, TF, K, true>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
     else group_load<WM, PREC, TF, K, false>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
-    uint32_t live_bits = 1u;  // SKIP: activity bits of the group (0: the transformation is the identity)
-    if (SKIP && MODE == 1 && i0 < n) live_bits = (__ldg(active + (i0 >> 5)) >> (i0 & 31)) & ((1u << K) - 1u);
+    uint32_t act_bits = 0u;  // MODE 3: activity bits of the group
+    if (MODE == 3 && i0 < n) act_bits = (__ldg(active + (i0 >> 5)) >> (i0 & 31)) & ((1u << K) - 1u);
     float y[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) y[k] = x2[k].h;
@@ -493,11 +494,33 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
         if (zp[k]) add(5, zw[k]);
         vadd<PREC>(x2[k], __fmul_rn(-p.c, acc));  // Scheme 1
     }
-    if (SKIP && MODE == 1 && live_bits == 0u) {
+    if (MODE == 3) {
+        float h[K];
+        res_t q[K];
 #pragma unroll
-        for (int k = 0; k < K; ++k) vround<PREC>(x2[k]);
-        if (full) vstore_k<PREC, K, true>(io.out[1], io.lout[1], i0, n, x2);
-        else vstore_k<PREC, K, false>(io.out[1], io.lout[1], i0, n, x2);
+        for (int k = 0; k < K; ++k) {
+            vround<PREC>(x2[k]);
+            if ((act_bits >> k) & 1u) {  // the rounded pair itself
+                h[k] = x2[k].h;
+                q[k] = PREC == P_COMP ? res_encode(x2[k].l, h[k]) : (res_t)0;
+            } else if (PREC == P_COMP) {  // renormalised as vstore does
+                h[k] = __fadd_rn(x2[k].h, x2[k].l);
+                q[k] = res_encode(__fadd_rn(__fsub_rn(x2[k].h, h[k]), x2[k].l), h[k]);
+            } else {
+                h[k] = x2[k].h;
+            }
+        }
+        if (full) {
+            st_floats<K>(io.out[1] + i0, h);
+            if (PREC == P_COMP) st_res<K>(io.lout[1] + i0, q);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (i0 + k < n) {
+                    io.out[1][i0 + k] = h[k];
+                    if (PREC == P_COMP) io.lout[1][i0 + k] = q[k];
+                }
+        }
         return;
     }
     if (full) group_finish<MODE, TR, PREC, K, true, REC>(i0, n, p, io, x2, rec);
