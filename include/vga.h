@@ -277,11 +277,11 @@ vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t chunk);
  * proportional to MB, SOM or FOM, so at nodes where MB, SOM, FOM and CO2 are all zero the
  * transformation is the identity, and it stays so while stepping (no flux can make them nonzero).
  * The first step after a state upload (vga_sim_set_masses, vga_sim_set_state_f32,
- * vga_sim_load_state) marks the other nodes in a bit mask and a list (one extra pass, one
- * synchronisation); a fused pass then runs as two kernels, the DOM diffusion of every node and the
- * transformation of the listed nodes, and leaves the MB, SOM, FOM and CO2 of the others unread and
+ * vga_sim_load_state) marks the other nodes in a bit mask (one extra pass, one synchronisation); a
+ * fused pass then diffuses the DOM of every node, transforms only the marked nodes (dealt out one
+ * per lane within each warp), and leaves the MB, SOM, FOM and CO2 of the others unread and
  * unwritten.  Results are bit-identical with the mask off (also a node whose values are negative
- * zeros is marked).  on = 0 processes every node every pass with the single fused kernel. */
+ * zeros is marked).  on = 0 transforms every node every pass. */
 vga_status vga_sim_set_activity_skip(vga_sim *s, int32_t on);
 
 /* Selects variant 3 with `chunk` nodes per work item (a power of two in [256, 8192]; CTAs of

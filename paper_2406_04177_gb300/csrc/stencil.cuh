@@ -442,12 +442,12 @@ __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const Step
 // previous lane's last node and the +x neighbour of the last node the next lane's first node.
 // Arithmetic and slot order per node are those of table_node, so the results are the same bits.
 // Rows and tables start on 16-byte boundaries (row strides are multiples of 64 values).  REC (fused
-// passes only): also writes the pass record of the discrete adjoint.  MODE 3 is the first half of
-// the sparse fused pass: the DOM is diffused and rounded as in MODE 1 and stored; a node whose bit
-// in `active` is set keeps the rounded pair as it is (the transformation pass reads it back
-// exactly as MODE 1 holds it in registers), the others are stored as MODE 1 stores a DOM that the
-// (identity) transformation left unchanged.  MB, SOM, FOM and CO2 are not touched.  Must be called
-// by all 32 lanes of a warp.
+// passes only): also writes the pass record of the discrete adjoint.  MODE 3 is the sparse fused
+// pass: the DOM of every node is diffused and rounded as in MODE 1 and stored as MODE 1 stores a
+// DOM that the (identity) transformation left unchanged; then the warp's nodes whose bit in
+// `active` is set are dealt out one per lane (their rounded DOM by shuffles), and each such lane
+// loads the node's MB, SOM, FOM and CO2, transforms and stores all five as MODE 1 does.  MB, SOM,
+// FOM and CO2 of the other nodes are not touched.  Must be called by all 32 lanes of a warp.
 template <int MODE, int WM, int TR, int PREC, int TF, int K, bool REC = false>
 __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTable &tb, const BlockTable &bt,
                                           const StepParams &p, const StateIO &io,
@@ -477,7 +477,7 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
         zv[k] = zm[k] ? __ldg(Y2 + (i0 + k - zm[k])) : 0.0f;
         zw[k] = zp[k] ? __ldg(Y2 + (i0 + k + zp[k])) : 0.0f;
     }
-    if (i0 >= n) return;
+    if (i0 >= n && MODE != 3) return;  // MODE 3 keeps every lane for the warp-wide deal below
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float acc = 0.0f;
@@ -495,31 +495,53 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
         vadd<PREC>(x2[k], __fmul_rn(-p.c, acc));  // Scheme 1
     }
     if (MODE == 3) {
-        float h[K];
-        res_t q[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) vround<PREC>(x2[k]);
+        if (full) vstore_k<PREC, K, true>(io.out[1], io.lout[1], i0, n, x2);
+        else vstore_k<PREC, K, false>(io.out[1], io.lout[1], i0, n, x2);
+        // the warp's active nodes, one per lane: pair m = (source lane, slot k), k-major
+        unsigned am[K];
+        int cnt[K], total = 0;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            vround<PREC>(x2[k]);
-            if ((act_bits >> k) & 1u) {  // the rounded pair itself
-                h[k] = x2[k].h;
-                q[k] = PREC == P_COMP ? res_encode(x2[k].l, h[k]) : (res_t)0;
-            } else if (PREC == P_COMP) {  // renormalised as vstore does
-                h[k] = __fadd_rn(x2[k].h, x2[k].l);
-                q[k] = res_encode(__fadd_rn(__fsub_rn(x2[k].h, h[k]), x2[k].l), h[k]);
-            } else {
-                h[k] = x2[k].h;
-            }
+            am[k] = __ballot_sync(0xffffffffu, (act_bits >> k) & 1u);
+            cnt[k] = __popc(am[k]);
+            total += cnt[k];
         }
-        if (full) {
-            st_floats<K>(io.out[1] + i0, h);
-            if (PREC == P_COMP) st_res<K>(io.lout[1] + i0, q);
-        } else {
+        if (total == 0) return;  // warp-uniform
+        __syncwarp();            // the DOM stores above come before the transformation's stores
+        for (int base = 0; base < total; base += 32) {
+            const int m = base + lane;
+            int k = 0, r = m;
 #pragma unroll
-            for (int k = 0; k < K; ++k)
-                if (i0 + k < n) {
-                    io.out[1][i0 + k] = h[k];
-                    if (PREC == P_COMP) io.lout[1][i0 + k] = q[k];
+            for (int kk = 0; kk < K - 1; ++kk)
+                if (k == kk && r >= cnt[kk]) {
+                    r -= cnt[kk];
+                    k = kk + 1;
                 }
+            unsigned mk = am[0];
+#pragma unroll
+            for (int kk = 1; kk < K; ++kk)
+                if (k == kk) mk = am[kk];
+            const int src = m < total ? (int)__fns(mk, 0u, r + 1) : lane;
+            V v2 = {0.0f, 0.0f};
+#pragma unroll
+            for (int kk = 0; kk < K; ++kk) {
+                const float hh = __shfl_sync(0xffffffffu, x2[kk].h, src);
+                const float ll = __shfl_sync(0xffffffffu, x2[kk].l, src);
+                if (k == kk) v2 = V{hh, ll};
+            }
+            if (m < total) {
+                const uint32_t i = i0 + (uint32_t)(K * (src - lane) + k);
+                V v1 = vload<PREC>(io.in[0], io.lin[0], i), v3 = vload<PREC>(io.in[2], io.lin[2], i),
+                  v4 = vload<PREC>(io.in[3], io.lin[3], i), v5 = vload<PREC>(io.in[4], io.lin[4], i);
+                transform_n<TR, PREC>(v1, v2, v3, v4, v5, p);
+                vstore<PREC>(io.out[0], io.lout[0], i, v1);
+                vstore<PREC>(io.out[1], io.lout[1], i, v2);
+                vstore<PREC>(io.out[2], io.lout[2], i, v3);
+                vstore<PREC>(io.out[3], io.lout[3], i, v4);
+                vstore<PREC>(io.out[4], io.lout[4], i, v5);
+            }
         }
         return;
     }

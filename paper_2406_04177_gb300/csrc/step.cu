@@ -288,28 +288,6 @@ __global__ void __launch_bounds__(kThreads) k_stencil_tablev(int64_t n, NbrTable
     table_vec<MODE, WM, TR, PREC, TF, K>(i0, (uint32_t)n, tb, bt, p, io, PassRecord{}, active);
 }
 
-// Second half of the sparse fused pass: the transformation of the nodes on the active list.  The
-// DOM comes from the first half's output (the rounded pair of MODE 1), MB, SOM, FOM and CO2 from
-// the pass input; all five are stored as MODE 1 stores them.
-template <int TR, int PREC>
-__global__ void __launch_bounds__(kThreads) k_transform_active(int64_t m, const uint32_t *__restrict__ list,
-                                                               StepParams p, StateIO io) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m) return;
-    const uint32_t i = __ldg(list + t);
-    V x2;
-    x2.h = io.out[1][i];
-    x2.l = PREC == P_COMP ? res_decode(io.lout[1][i], x2.h) : 0.0f;
-    V x1 = vload<PREC>(io.in[0], io.lin[0], i), x3 = vload<PREC>(io.in[2], io.lin[2], i),
-      x4 = vload<PREC>(io.in[3], io.lin[3], i), x5 = vload<PREC>(io.in[4], io.lin[4], i);
-    transform_n<TR, PREC>(x1, x2, x3, x4, x5, p);
-    vstore<PREC>(io.out[0], io.lout[0], i, x1);
-    vstore<PREC>(io.out[1], io.lout[1], i, x2);
-    vstore<PREC>(io.out[2], io.lout[2], i, x3);
-    vstore<PREC>(io.out[3], io.lout[3], i, x4);
-    vstore<PREC>(io.out[4], io.lout[4], i, x5);
-}
-
 // Activity mask of the sparse fused pass (vga_sim.active): bit i set when node i may change under
 // the transformation: any bit of MB, SOM, FOM or CO2 (value or residual) nonzero, or a
 // negative-zero DOM (the transformation's zero increment would turn it into +0).  Every flux of
@@ -318,7 +296,7 @@ __global__ void __launch_bounds__(kThreads) k_transform_active(int64_t m, const 
 // of MB, SOM, FOM and CO2 (their current values are zero), so that a pass may skip them.
 template <int PREC>
 __global__ void k_build_active(int64_t n, StateIO cur, StateIO spare, uint32_t *__restrict__ mask,
-                               unsigned long long *__restrict__ count, uint32_t *__restrict__ list) {
+                               unsigned long long *__restrict__ count) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     bool act = false;
     if (i < n) {
@@ -339,14 +317,10 @@ __global__ void k_build_active(int64_t n, StateIO cur, StateIO spare, uint32_t *
         }
     }
     const unsigned b = __ballot_sync(0xffffffffu, act);
-    const int lane = threadIdx.x & 31;
-    unsigned long long base = 0;
-    if (lane == 0 && i < n) {
+    if ((threadIdx.x & 31) == 0 && i < n) {
         mask[i >> 5] = b;
-        if (b) base = atomicAdd(count, (unsigned long long)__popc(b));
+        if (b) atomicAdd(count, (unsigned long long)__popc(b));
     }
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (act) list[base + __popc(b & ((1u << lane) - 1u))] = (uint32_t)i;  // the active list, in any order
 }
 
 // Largest z offset of the table (for the compact form).
@@ -495,21 +469,11 @@ void launch_tablev_m(vga_sim *s, const StateIO &io, const NbrTable &tb, const Bl
     }
 }
 
-// Fused passes of the four-node kernel run sparse when the activity mask is valid for the state:
-// the DOM half over every node, then the transformation over the active list.
+// Fused passes of the four-node kernel run sparse (MODE 3) when the activity mask is valid.
 template <int MODE, int WM, int PREC, int K>
 void launch_tablev(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
-    if (MODE == 1 && K == 4 && s->activity_skip && s->active_valid) {
-        launch_tablev_m<3, WM, PREC, K>(s, io, tb, bt);
-        if (s->n_active > 0) {
-            const unsigned g = grid_for(s->n_active, kThreads);
-            if (s->sp.transform == 0) k_transform_active<0, PREC><<<g, kThreads, 0, s->stream>>>(s->n_active, s->active_list, s->sp, io);
-            else k_transform_active<1, PREC><<<g, kThreads, 0, s->stream>>>(s->n_active, s->active_list, s->sp, io);
-            ++s->launches;
-        }
-        return;
-    }
-    launch_tablev_m<MODE, WM, PREC, K>(s, io, tb, bt);
+    if (MODE == 1 && K == 4 && s->activity_skip && s->active_valid) launch_tablev_m<3, WM, PREC, K>(s, io, tb, bt);
+    else launch_tablev_m<MODE, WM, PREC, K>(s, io, tb, bt);
 }
 
 template <int MODE, int WM, int PREC>
@@ -676,7 +640,6 @@ vga_status sim_build_active(vga_sim *s) {
         const size_t words = (size_t)(std::max<int64_t>(s->npad, 64) + 31) / 32 + 8;
         VGA_TRY(dmalloc((void **)&s->active, sizeof(uint32_t) * words + sizeof(unsigned long long), "activity mask"));
         VGA_CUDA(cudaMemsetAsync(s->active, 0, sizeof(uint32_t) * words, s->stream));
-        VGA_TRY(dmalloc((void **)&s->active_list, sizeof(uint32_t) * (size_t)std::max<int64_t>(s->n, 1), "active list"));
     }
     const size_t words = (size_t)(std::max<int64_t>(s->npad, 64) + 31) / 32 + 8;
     unsigned long long *count = reinterpret_cast<unsigned long long *>(s->active + words);
@@ -689,11 +652,9 @@ vga_status sim_build_active(vga_sim *s) {
         spare.lout[c] = s->lspare(c);
     }
     if (s->precision() == P_COMP)
-        k_build_active<P_COMP><<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, cur, spare, s->active, count,
-                                                                                   s->active_list);
+        k_build_active<P_COMP><<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, cur, spare, s->active, count);
     else
-        k_build_active<P_F32><<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, cur, spare, s->active, count,
-                                                                                  s->active_list);
+        k_build_active<P_F32><<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, cur, spare, s->active, count);
     VGA_CHECK_LAUNCH();
     ++s->launches;
     unsigned long long h = 0;

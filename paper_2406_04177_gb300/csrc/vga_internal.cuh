@@ -204,7 +204,6 @@ struct vga_sim {
     // Sparse fused pass: bit i of `active` set when node i may change under the transformation
     // (MB, SOM, FOM or CO2 nonzero, or a negative-zero DOM); such a set never grows while stepping.
     uint32_t *active = nullptr;    // ceil(npad / 32) + 8 words
-    uint32_t *active_list = nullptr;  // the marked nodes (n_active of them, in no particular order)
     bool active_valid = false;     // built for the current state (cleared by every state upload)
     bool activity_skip = true;     // use it (vga_sim_set_activity_skip)
     int64_t n_active = -1;         // nodes marked in the last build (-1: none built)
