@@ -676,6 +676,7 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->nbr_table);
     dfree(s->nbr_tz);
     dfree(s->active);
+    dfree(s->active_state);
     dfree(s->bnode);
     dfree(s->bface);
     dfree(s->btheta6);

@@ -444,14 +444,14 @@ __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const Step
 // Rows and tables start on 16-byte boundaries (row strides are multiples of 64 values).  REC (fused
 // passes only): also writes the pass record of the discrete adjoint.  MODE 3 is the sparse fused
 // pass: the DOM of every node is diffused and rounded as in MODE 1 and stored as MODE 1 stores a
-// DOM that the (identity) transformation left unchanged; then the warp's nodes whose bit in
-// `active` is set are dealt out one per lane (their rounded DOM by shuffles), and each such lane
-// loads the node's MB, SOM, FOM and CO2, transforms and stores all five as MODE 1 does.  MB, SOM,
-// FOM and CO2 of the other nodes are not touched.  Must be called by all 32 lanes of a warp.
+// DOM that the (identity) transformation left unchanged; then the warp's nodes whose bit in the
+// activity mask is set are dealt out one per lane (their rounded DOM by shuffles), and each such
+// lane transforms its node with MB, SOM, FOM and CO2 from the compact state (updated in place),
+// storing them there and the DOM as MODE 1 does.  Must be called by all 32 lanes of a warp.
 template <int MODE, int WM, int TR, int PREC, int TF, int K, bool REC = false>
 __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTable &tb, const BlockTable &bt,
                                           const StepParams &p, const StateIO &io,
-                                          const PassRecord &rec = PassRecord{}, const uint32_t *active = nullptr) {
+                                          const PassRecord &rec = PassRecord{}, const SparseState &ss = SparseState{}) {
     const bool full = i0 + K <= n;
     const float *__restrict__ Y2 = io.in[1];
     uint32_t ty[K], zm[K], zp[K], bn[K];
@@ -459,7 +459,7 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
     if (full) group_load<WM, PREC, TF, K, true>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
     else group_load<WM, PREC, TF, K, false>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
     uint32_t act_bits = 0u;  // MODE 3: activity bits of the group
-    if (MODE == 3 && i0 < n) act_bits = (__ldg(active + (i0 >> 5)) >> (i0 & 31)) & ((1u << K) - 1u);
+    if (MODE == 3 && i0 < n) act_bits = (__ldg(ss.mask + (i0 >> 5)) >> (i0 & 31)) & ((1u << K) - 1u);
     float y[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) y[k] = x2[k].h;
@@ -533,14 +533,18 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
             }
             if (m < total) {
                 const uint32_t i = i0 + (uint32_t)(K * (src - lane) + k);
-                V v1 = vload<PREC>(io.in[0], io.lin[0], i), v3 = vload<PREC>(io.in[2], io.lin[2], i),
-                  v4 = vload<PREC>(io.in[3], io.lin[3], i), v5 = vload<PREC>(io.in[4], io.lin[4], i);
-                transform_n<TR, PREC>(v1, v2, v3, v4, v5, p);
-                vstore<PREC>(io.out[0], io.lout[0], i, v1);
+                const uint32_t w = i >> 5;
+                const uint32_t r = __ldg(ss.prefix + w) + __popc(__ldg(ss.mask + w) & ((1u << (i & 31)) - 1u));
+                V v[4];  // MB, SOM, FOM, CO2 (written by this lane in earlier passes of the call)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    v[q].h = ss.h[q][r];
+                    v[q].l = PREC == P_COMP ? res_decode(ss.l[q][r], v[q].h) : 0.0f;
+                }
+                transform_n<TR, PREC>(v[0], v2, v[1], v[2], v[3], p);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) vstore<PREC>(ss.h[q], ss.l[q], r, v[q]);
                 vstore<PREC>(io.out[1], io.lout[1], i, v2);
-                vstore<PREC>(io.out[2], io.lout[2], i, v3);
-                vstore<PREC>(io.out[3], io.lout[3], i, v4);
-                vstore<PREC>(io.out[4], io.lout[4], i, v5);
             }
         }
         return;

@@ -283,9 +283,53 @@ __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable 
 // K consecutive nodes per thread (table_vec); n < 2^31, so K * thread index fits 32 bits.
 template <int MODE, int WM, int TR, int PREC, int TF, int K>
 __global__ void __launch_bounds__(kThreads) k_stencil_tablev(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
-                                                             StateIO io, const uint32_t *__restrict__ active) {
+                                                             StateIO io, SparseState ss) {
     const uint32_t i0 = (uint32_t)K * ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x);
-    table_vec<MODE, WM, TR, PREC, TF, K>(i0, (uint32_t)n, tb, bt, p, io, PassRecord{}, active);
+    table_vec<MODE, WM, TR, PREC, TF, K>(i0, (uint32_t)n, tb, bt, p, io, PassRecord{}, ss);
+}
+
+// Exclusive prefix of the marked nodes per mask word (one block; once per state upload).
+__global__ void __launch_bounds__(1024) k_scan_mask(int64_t words, const uint32_t *__restrict__ mask,
+                                                     uint32_t *__restrict__ prefix) {
+    __shared__ uint32_t part[1024];
+    const int64_t per = (words + 1023) / 1024, w0 = threadIdx.x * per, w1 = min(words, w0 + per);
+    uint32_t sum = 0;
+    for (int64_t w = w0; w < w1; ++w) sum += __popc(mask[w]);
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan of the per-thread sums
+        const uint32_t t = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - sum;
+    for (int64_t w = w0; w < w1; ++w) {
+        prefix[w] = run;
+        run += __popc(mask[w]);
+    }
+}
+
+// Marked nodes' MB, SOM, FOM, CO2 between the state arrays (io.in read, io.out written) and the
+// compact state: to_compact copies state -> compact, otherwise compact -> state.
+__global__ void k_active_copy(int64_t n, SparseState ss, StateIO io, int to_compact, int comp) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t w = (uint32_t)(i >> 5), bit = 1u << (i & 31);
+    const uint32_t m = __ldg(ss.mask + w);
+    if (!(m & bit)) return;
+    const uint32_t r = __ldg(ss.prefix + w) + __popc(m & (bit - 1u));
+    const int cs[4] = {0, 2, 3, 4};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (to_compact) {
+            ss.h[q][r] = io.in[cs[q]][i];
+            if (comp) ss.l[q][r] = io.lin[cs[q]][i];
+        } else {
+            io.out[cs[q]][i] = ss.h[q][r];
+            if (comp) io.lout[cs[q]][i] = ss.l[q][r];
+        }
+    }
 }
 
 // Activity mask of the sparse fused pass (vga_sim.active): bit i set when node i may change under
@@ -456,10 +500,26 @@ void launch_staged_any(vga_sim *s, const StateIO &io) {
     }
 }
 
+// The compact state of the running step call.
+SparseState sparse_state(vga_sim *s) {
+    SparseState ss;
+    const size_t words = (size_t)(std::max<int64_t>(s->npad, 64) + 31) / 32 + 8;
+    ss.mask = s->active;
+    ss.prefix = s->active ? s->active + words : nullptr;
+    const size_t cap = (size_t)std::max<int64_t>(s->active_state_cap, 1);
+    float *h = reinterpret_cast<float *>(s->active_state);
+    res_t *l = reinterpret_cast<res_t *>(h + 4 * cap);
+    for (int q = 0; q < 4; ++q) {
+        ss.h[q] = s->active_state ? h + q * cap : nullptr;
+        ss.l[q] = s->active_state ? l + q * cap : nullptr;
+    }
+    return ss;
+}
+
 template <int MODE, int WM, int PREC, int K>
 void launch_tablev_m(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
     const unsigned grid = grid_for((s->n + K - 1) / K, kThreads);
-    const uint32_t *act = s->active;
+    const SparseState act = sparse_state(s);
     if (tb.tz) {
         if (s->sp.transform == 0) k_stencil_tablev<MODE, WM, 0, PREC, 1, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io, act);
         else k_stencil_tablev<MODE, WM, 1, PREC, 1, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io, act);
@@ -469,10 +529,10 @@ void launch_tablev_m(vga_sim *s, const StateIO &io, const NbrTable &tb, const Bl
     }
 }
 
-// Fused passes of the four-node kernel run sparse (MODE 3) when the activity mask is valid.
+// Fused passes of the four-node kernel run sparse (MODE 3) inside a sparse step call.
 template <int MODE, int WM, int PREC, int K>
 void launch_tablev(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
-    if (MODE == 1 && K == 4 && s->activity_skip && s->active_valid) launch_tablev_m<3, WM, PREC, K>(s, io, tb, bt);
+    if (MODE == 1 && K == 4 && s->sparse_call) launch_tablev_m<3, WM, PREC, K>(s, io, tb, bt);
     else launch_tablev_m<MODE, WM, PREC, K>(s, io, tb, bt);
 }
 
@@ -636,13 +696,12 @@ vga_status sim_diffuse_pass(vga_sim *s) {
 
 // Builds the activity mask for the current state (once per state upload; stepping keeps it valid).
 vga_status sim_build_active(vga_sim *s) {
-    if (!s->active) {
-        const size_t words = (size_t)(std::max<int64_t>(s->npad, 64) + 31) / 32 + 8;
-        VGA_TRY(dmalloc((void **)&s->active, sizeof(uint32_t) * words + sizeof(unsigned long long), "activity mask"));
-        VGA_CUDA(cudaMemsetAsync(s->active, 0, sizeof(uint32_t) * words, s->stream));
-    }
     const size_t words = (size_t)(std::max<int64_t>(s->npad, 64) + 31) / 32 + 8;
-    unsigned long long *count = reinterpret_cast<unsigned long long *>(s->active + words);
+    if (!s->active) {  // mask words, their prefix, a counter
+        VGA_TRY(dmalloc((void **)&s->active, sizeof(uint32_t) * 2 * words + sizeof(unsigned long long), "activity mask"));
+        VGA_CUDA(cudaMemsetAsync(s->active, 0, sizeof(uint32_t) * 2 * words, s->stream));
+    }
+    unsigned long long *count = reinterpret_cast<unsigned long long *>(s->active + 2 * words);
     VGA_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s->stream));
     StateIO cur = state_io(s), spare;
     for (int c = 0; c < 5; ++c) {
@@ -657,10 +716,21 @@ vga_status sim_build_active(vga_sim *s) {
         k_build_active<P_F32><<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, cur, spare, s->active, count);
     VGA_CHECK_LAUNCH();
     ++s->launches;
+    k_scan_mask<<<1, 1024, 0, s->stream>>>((int64_t)words, s->active, s->active + words);
+    VGA_CHECK_LAUNCH();
+    ++s->launches;
     unsigned long long h = 0;
     VGA_CUDA(cudaMemcpyAsync(&h, count, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
     VGA_CUDA(cudaStreamSynchronize(s->stream));
     s->n_active = (int64_t)h;
+    if (s->active_state_cap < s->n_active) {  // compact MB, SOM, FOM, CO2 (values and residuals)
+        dfree(s->active_state);
+        s->active_state = nullptr;
+        s->active_state_cap = 0;
+        VGA_TRY(dmalloc((void **)&s->active_state, (sizeof(float) + sizeof(res_t)) * 4 * (size_t)s->n_active,
+                        "compact active state"));
+        s->active_state_cap = s->n_active;
+    }
     s->active_valid = true;
     return VGA_OK;
 }
@@ -670,8 +740,15 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
         s->steps_done += std::max<int64_t>(n_steps, 0);
         return VGA_OK;
     }
-    if (s->activity_skip && !s->active_valid && (s->kernel_variant == 5) && s->g->nx <= 32767)
-        VGA_TRY(sim_build_active(s));
+    // sparse fused passes: variant 5 on the neighbour-offset table (and the block table, if used)
+    bool sparse = s->activity_skip && s->kernel_variant == 5 && s->g->nx <= 32767 && n_steps > 1;
+    if (sparse && s->wmode == W_BLOCK) {
+        BlockTable bt;
+        bool ok = false;
+        VGA_TRY(sim_block_table(s, &bt, &ok));
+        sparse = ok;
+    }
+    if (sparse && !s->active_valid) VGA_TRY(sim_build_active(s));
     const bool sub = s->subcycled();
     const int64_t k0 = s->steps_done;
     // ntrans is reset on every exit so that no other path sees a sub-cycled count
@@ -684,10 +761,31 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
     if (s->kernel_variant == 3 && !sub && s->g->nx <= 32767 && n_steps > 1) {
         VGA_TRY(sim_wave_fused(s, n_steps - 1));
     } else {
+        // sparse call: the marked nodes' MB, SOM, FOM, CO2 live in the compact state during the
+        // fused passes and go back to the state arrays after them
+        struct SparseEnd {
+            vga_sim *s;
+            ~SparseEnd() { s->sparse_call = false; }
+        } sparse_end{s};
+        const bool copy = sparse && s->n_active > 0;
+        const int comp = s->precision() == P_COMP ? 1 : 0;
+        if (copy) {
+            k_active_copy<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, sparse_state(s), state_io(s), 1, comp);
+            VGA_CHECK_LAUNCH();
+            ++s->launches;
+        }
+        s->sparse_call = sparse;
         for (int64_t k = 1; k < n_steps; ++k) {
             if (sub) s->sp.ntrans = sim_ticks_of_step(s, k0 + k);
             VGA_TRY(launch_stencil<1>(s, state_io(s)));
             for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
+        }
+        s->sparse_call = false;
+        if (copy) {
+            k_active_copy<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, sparse_state(s),
+                                                                              state_io_inplace(s), 0, comp);
+            VGA_CHECK_LAUNCH();
+            ++s->launches;
         }
     }
     VGA_TRY(launch_stencil<2>(s, state_io(s)));

@@ -112,6 +112,16 @@ struct StateIO {
     res_t *lout[5];
 };
 
+// Compact state of the sparse fused pass (vga_sim_set_activity_skip): MB, SOM, FOM and CO2 of the
+// marked nodes, in the order of the activity mask (node i has rank prefix[i / 32] + the marked nodes
+// before it in its mask word), updated in place during one step call.
+struct SparseState {
+    const uint32_t *mask = nullptr;    // activity bits
+    const uint32_t *prefix = nullptr;  // marked nodes before each mask word
+    float *h[4] = {nullptr, nullptr, nullptr, nullptr};  // MB, SOM, FOM, CO2 values
+    res_t *l[4] = {nullptr, nullptr, nullptr, nullptr};  // and residuals
+};
+
 // Edge-weight modes of the stencil.
 enum WeightMode { W_UNIT = 0, W_BLOCK = 1 };
 
@@ -203,9 +213,12 @@ struct vga_sim {
     int64_t graph_launches = 0;    // CUDA graph launches of the mixed solve
     // Sparse fused pass: bit i of `active` set when node i may change under the transformation
     // (MB, SOM, FOM or CO2 nonzero, or a negative-zero DOM); such a set never grows while stepping.
-    uint32_t *active = nullptr;    // ceil(npad / 32) + 8 words
+    uint32_t *active = nullptr;    // ceil(npad / 32) + 8 words, then the prefix of each word, then a counter
+    char *active_state = nullptr;  // compact MB, SOM, FOM, CO2 of the marked nodes (SparseState)
+    int64_t active_state_cap = 0;  // nodes it holds
     bool active_valid = false;     // built for the current state (cleared by every state upload)
     bool activity_skip = true;     // use it (vga_sim_set_activity_skip)
+    bool sparse_call = false;      // the fused passes of the running step call are sparse
     int64_t n_active = -1;         // nodes marked in the last build (-1: none built)
     int64_t steps_done = 0;
     int64_t cg_iterations = 0;
