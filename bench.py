@@ -8,11 +8,13 @@ largest 6-connected component kept), the Sec. IV.C parameters and initial masses
 (PVS/s): nodes x time steps / second.
 
 Printed: one JSON line (rank 0).  Keys beyond the base contract:
-  roofline       fused explicit kernel: algorithmic bytes / mean launch time, timed with CUDA
-                 events on its stream during the timed region.  Algorithmic bytes of a pass: 40 B
-                 per node (five FP32 compartments read and written) for the dense pass; for the
-                 sparse pass (the default) 8 B per node (DOM) + 32 B per node the transformation
-                 can change (MB, SOM, FOM, CO2; `active_nodes`)
+  roofline       fused explicit kernel: algorithmic bytes (40 B per pore-voxel-step: five FP32
+                 compartments read and written) / mean launch time, timed with CUDA events on its
+                 stream during the timed region; `dram_frac`: the ncu-recorded physical DRAM bytes
+                 of the same pass over the same time.  The sparse pass (the default) moves fewer
+                 physical bytes than 40 B per node (`sparse_bytes_needed`: 8 B per node for the DOM
+                 plus 32 B per node the transformation can change), so `frac` may exceed what a
+                 dense pass can reach
   dense_pass     the same timed loop with the sparse pass switched off (every node transformed)
   cpu_baseline   the FP64 oracle on the host cores over a bounded number of time steps
   error_vs_fp64  GPU after those same steps against the oracle (relative L2 per compartment,
@@ -300,7 +302,7 @@ def bench_ours(a):
     variant = best.get("variant")
     n_active = sim.stats()["active_nodes"]
     sparse = variant == 5 and n_active >= 0
-    alg_bytes = (BYTES_DOM * n + (BYTES_PER_PVS - BYTES_DOM) * n_active) if sparse else BYTES_PER_PVS * n
+    alg_bytes = BYTES_PER_PVS * n
     achieved = alg_bytes / mean_launch_s / 1e9
     traffic = recorded_traffic(n, "sparse" if sparse else "dense")
     kname = {0: "k_stencil (chunk decode, direct loads)", 1: "k_stencil_staged (chunk decode, bulk-copy staging)",
@@ -313,13 +315,16 @@ def bench_ours(a):
                 "traffic": traffic, "kernel": f"{kname}, fused pass (diffuse the stored transformed DOM, then transform)"
                 + (f"; sparse: {n_active} of {n} nodes can change under the transformation, the others only diffuse"
                    if sparse else ""),
-                "algorithmic_bytes_per_pass": alg_bytes, "active_nodes": n_active if sparse else n,
+                "algorithmic_bytes_per_pass": alg_bytes,
+                "dram_frac": (traffic / mean_launch_s / 1e9 / peak) if traffic else None,
+                "active_nodes": n_active if sparse else n,
+                "sparse_bytes_needed": (BYTES_DOM * n + (BYTES_PER_PVS - BYTES_DOM) * n_active) if sparse else None,
                 "mean_pass_ms": mean_launch_s * 1e3,
                 "passes_timed": fused_count, "passes_per_launch": (S - 1) if variant == 3 else 1,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
                 if peak_src == "measured" else "fallback 6.8 TB/s",
-                # PVS/s x 40 B over the peak: the bandwidth a dense pass would need for this rate
-                "dense_equivalent_frac": value / world * BYTES_PER_PVS / (peak * 1e9)}
+                # PVS/s x 40 B over the peak for the whole step (all passes, totals included)
+                "step_frac": value / world * BYTES_PER_PVS / (peak * 1e9)}
 
     # ---- the dense pass (every node transformed) on the same loop, for comparison ----
     dense = None
@@ -348,7 +353,9 @@ def bench_ours(a):
         dense = {"value": world * n * S * dsteps / (dms / 1e3), "unit": UNIT, "steps": dsteps,
                  "ms_per_step": dms / dsteps, "mean_pass_ms": dmean * 1e3,
                  "roofline": {"bound": "hbm", "achieved": dach, "peak": peak, "unit": "GB/s", "frac": dach / peak,
-                              "traffic": recorded_traffic(n, "dense"), "algorithmic_bytes_per_pass": BYTES_PER_PVS * n}}
+                              "traffic": recorded_traffic(n, "dense"), "algorithmic_bytes_per_pass": BYTES_PER_PVS * n,
+                              "dram_frac": (recorded_traffic(n, "dense") / dmean / 1e9 / peak)
+                              if recorded_traffic(n, "dense") else None}}
 
     # ---- end to end through the C ABI with host buffers (outside the timed region) ----
     xh = torch.from_numpy(X0.astype(np.float32)).pin_memory()
