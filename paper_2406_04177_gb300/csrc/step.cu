@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable 
 
 // K consecutive nodes per thread (table_vec); n < 2^31, so K * thread index fits 32 bits.
 template <int MODE, int WM, int TR, int PREC, int TF, int K>
-__global__ void __launch_bounds__(kThreads, MODE == 3 ? 5 : 1) k_stencil_tablev(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+__global__ void __launch_bounds__(kThreads, MODE == 3 ? 5 : 4) k_stencil_tablev(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                              StateIO io, SparseState ss) {
     const uint32_t i0 = (uint32_t)K * ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x);
     table_vec<MODE, WM, TR, PREC, TF, K>(i0, (uint32_t)n, tb, bt, p, io, PassRecord{}, ss);
