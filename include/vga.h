@@ -335,6 +335,11 @@ vga_status vga_batch_step(vga_batch *b, int64_t n_steps);
  * CUDA-graph capture on or off. */
 vga_status vga_batch_set_launch(vga_batch *b, int32_t steps_per_launch, int32_t blocks_per_sm, int32_t use_graph);
 
+/* Sparse fused passes for the batch, as vga_sim_set_activity_skip (on by default): the first step
+ * call after vga_batch_set_masses marks the nodes where the transformation can change the state;
+ * the fused passes then transform only those.  Bit-identical with on = 0. */
+vga_status vga_batch_set_activity_skip(vga_batch *b, int32_t on);
+
 typedef struct vga_batch_stats {
     int32_t instances;
     int32_t grid_blocks;

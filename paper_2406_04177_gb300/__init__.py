@@ -125,6 +125,7 @@ _SIGNATURES = {
     "vga_sim_set_kernel": [_P, _I32, _I32],
     "vga_sim_set_solver": [_P, _I32],
     "vga_sim_set_activity_skip": [_P, _I32],
+    "vga_batch_set_activity_skip": [_P, _I32],
     "vga_sim_set_wavefront": [_P, _I32, _I32, _I32],
     "vga_sim_autotune": [_P, _I32, _P],
     "vga_sim_enable_timing": [_P, _I32],
@@ -404,6 +405,10 @@ def vga_sim_set_solver(s, solver: int):
 
 def vga_sim_set_activity_skip(s, on: bool):
     _check(load_library().vga_sim_set_activity_skip(s, 1 if on else 0), "vga_sim_set_activity_skip")
+
+
+def vga_batch_set_activity_skip(b, on: bool):
+    _check(load_library().vga_batch_set_activity_skip(b, 1 if on else 0), "vga_batch_set_activity_skip")
 
 
 def vga_sim_set_wavefront(s, chunk: int, depth: int, ctas_per_sm: int = 0):
@@ -688,6 +693,9 @@ class Batch:
 
     def step(self, n_steps: int):
         vga_batch_step(self.handle, n_steps)
+
+    def set_activity_skip(self, on: bool):
+        vga_batch_set_activity_skip(self.handle, on)
 
     def set_launch(self, steps_per_launch: int, blocks_per_sm: int = 0, use_graph: bool = True):
         vga_batch_set_launch(self.handle, steps_per_launch, blocks_per_sm, use_graph)

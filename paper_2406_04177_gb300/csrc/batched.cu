@@ -46,6 +46,8 @@ struct BatchArgs {
     unsigned *bar;  // [0] arrivals, [1] generation
     int32_t *err;
     StateIO io[2];  // a pass whose input is state buffer k reads io[k] (kept as kernel parameters)
+    SparseState ss;  // the sparse fused pass (stencil.cuh MODE 3), when `sparse`
+    int sparse;
 };
 
 // One fused pass over the whole batch, kBatchGroup consecutive nodes per thread (table_vec).
@@ -71,7 +73,8 @@ __device__ __forceinline__ void batch_fused_pass(const BatchArgs &a, const State
         __syncwarp();
         if ((threadIdx.x & 31) == 0) wp[w] = k >= 0 ? a.inst[k].p : StepParams{};
         __syncwarp();
-        table_vec<1, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, wp[w], io);
+        if (a.sparse) table_vec<3, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, wp[w], io, PassRecord{}, a.ss);
+        else table_vec<1, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, wp[w], io);
     }
 }
 
@@ -221,6 +224,8 @@ struct vga_batch {
     bool capture_failed = false;
     std::map<std::tuple<int64_t, int, int, int>, cudaGraphExec_t> graphs;
     int64_t launches = 0, graph_replays = 0, steps_done = 0;
+    Activity act;               // the sparse fused pass (as vga_sim_set_activity_skip)
+    bool activity_skip = true;
 };
 
 namespace {
@@ -260,7 +265,7 @@ vga_status batch_grid(vga_batch *b) {
     return batch_grid_of(b, b->tz ? batch_kernel<1, true>(b) : batch_kernel<0, true>(b), &b->grid);
 }
 
-vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
+vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0, bool sparse) {
     BatchArgs a;
     a.ntiles = b->ntiles;
     a.npad = b->npad;
@@ -276,6 +281,8 @@ vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npas
     }
     a.bar = b->bar;
     a.err = b->err;
+    a.ss = activity_state(b->act);
+    a.sparse = sparse ? 1 : 0;
     for (int k = 0; k < 2; ++k) {
         for (int c = 0; c < 5; ++c) {
             a.io[k].in[c] = b->h[k] + c * b->npad;
@@ -311,15 +318,34 @@ int64_t launches_of(const vga_batch *b, int64_t n_steps) {
     return 2 + (mid > 0 ? (mid + S - 1) / S : 0);
 }
 
-vga_status enqueue_steps(vga_batch *b, int64_t n_steps, int cur0) {
+// The state arrays as the input (in) of a pass reading buffer k and as its output (out).
+StateIO batch_io(const vga_batch *b, int k) {
+    StateIO io;
+    for (int c = 0; c < 5; ++c) {
+        io.in[c] = b->h[k] + c * b->npad;
+        io.lin[c] = b->l[k] + c * b->npad;
+        io.out[c] = b->h[1 - k] + c * b->npad;
+        io.lout[c] = b->l[1 - k] + c * b->npad;
+    }
+    return io;
+}
+
+// sparse: the fused passes run sparse; the marked nodes' MB, SOM, FOM, CO2 go to the compact state
+// after the first pass and back before the last.
+vga_status enqueue_steps(vga_batch *b, int64_t n_steps, int cur0, bool sparse) {
     const int64_t npass = n_steps + 1;
     const int S = std::max(1, b->steps_per_launch);
-    VGA_TRY(launch_batch(b, 0, 1, (int32_t)npass, cur0));
+    const bool comp = b->precision == P_COMP;
+    VGA_TRY(launch_batch(b, 0, 1, (int32_t)npass, cur0, false));
+    if (sparse) VGA_TRY(activity_copy(b->act, b->total, batch_io(b, (cur0 + 1) & 1), true, comp, b->stream));
     for (int64_t p0 = 1; p0 < npass - 1; p0 += S) {
         const int64_t p1 = std::min(npass - 1, p0 + S);
-        VGA_TRY(launch_batch(b, (int32_t)p0, (int32_t)p1, (int32_t)npass, cur0));
+        VGA_TRY(launch_batch(b, (int32_t)p0, (int32_t)p1, (int32_t)npass, cur0, sparse));
     }
-    return launch_batch(b, (int32_t)(npass - 1), (int32_t)npass, (int32_t)npass, cur0);
+    // the state after pass npass - 2 is buffer (cur0 + npass - 1) & 1: the out side of the other
+    if (sparse)
+        VGA_TRY(activity_copy(b->act, b->total, batch_io(b, 1 - (int)((cur0 + npass - 1) & 1)), false, comp, b->stream));
+    return launch_batch(b, (int32_t)(npass - 1), (int32_t)npass, (int32_t)npass, cur0, false);
 }
 
 vga_status check_err(vga_batch *b) {
@@ -358,6 +384,7 @@ vga_status vga_batch_free(vga_batch *b) {
     dfree(b->tile_inst);
     dfree(b->inst);
     dfree(b->bar);
+    activity_free(&b->act);
     dfree(b->err);
     dfree(b->stage);
     if (b->stream) cudaStreamDestroy(b->stream);
@@ -490,6 +517,7 @@ vga_status vga_batch_set_masses(vga_batch *b, int32_t instance, const double *x)
                                                                   b->start[instance], b->npad, b->precision == P_COMP);
     VGA_CHECK_LAUNCH();
     VGA_CUDA(cudaStreamSynchronize(b->stream));
+    b->act.valid = false;
     return VGA_OK;
 }
 
@@ -516,19 +544,34 @@ vga_status vga_batch_set_launch(vga_batch *b, int32_t steps_per_launch, int32_t 
     return batch_grid(b);
 }
 
+vga_status vga_batch_set_activity_skip(vga_batch *b, int32_t on) {
+    if (!b) return fail(VGA_ERR_INVALID_ARG, "batch is NULL");
+    b->activity_skip = on != 0;
+    return VGA_OK;
+}
+
 vga_status vga_batch_step(vga_batch *b, int64_t n_steps) {
     if (!b || n_steps < 0) return fail(VGA_ERR_INVALID_ARG, "bad batch or n_steps");
     if (n_steps == 0 || b->ntiles == 0) return VGA_OK;
     if (n_steps + 1 > (int64_t)INT32_MAX) return fail(VGA_ERR_INVALID_ARG, "n_steps too large for one call");
     const int cur0 = b->cur;
+    // sparse fused passes need a mask for the current state (a rebuild may move the compact state:
+    // the captured graphs go with it)
+    const bool sparse = b->activity_skip && n_steps > 1;
+    if (sparse && !b->act.valid) {
+        const StateIO cur = batch_io(b, cur0);
+        VGA_TRY(activity_build(&b->act, b->total, b->npad, cur, batch_io(b, 1 - cur0), b->precision == P_COMP,
+                               b->stream));
+        drop_graphs(b);
+    }
     if (b->use_graph) {
-        const auto key = std::make_tuple(n_steps, b->steps_per_launch, b->grid, cur0);
+        const auto key = std::make_tuple(n_steps, b->steps_per_launch, b->grid, cur0 + (sparse ? 2 : 0));
         auto it = b->graphs.find(key);
         if (it == b->graphs.end()) {
             cudaGraph_t graph = nullptr;
             cudaGraphExec_t exec = nullptr;
             VGA_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-            const vga_status st = enqueue_steps(b, n_steps, cur0);
+            const vga_status st = enqueue_steps(b, n_steps, cur0, sparse);
             const cudaError_t ec = cudaStreamEndCapture(b->stream, &graph);
             cudaError_t ei = cudaErrorUnknown;
             if (st == VGA_OK && ec == cudaSuccess) ei = cudaGraphInstantiate(&exec, graph, 0);
@@ -546,10 +589,10 @@ vga_status vga_batch_step(vga_batch *b, int64_t n_steps) {
             VGA_CUDA(cudaGraphLaunch(it->second, b->stream));
             ++b->graph_replays;
         } else {
-            VGA_TRY(enqueue_steps(b, n_steps, cur0));
+            VGA_TRY(enqueue_steps(b, n_steps, cur0, sparse));
         }
     } else {
-        VGA_TRY(enqueue_steps(b, n_steps, cur0));
+        VGA_TRY(enqueue_steps(b, n_steps, cur0, sparse));
     }
     b->launches += launches_of(b, n_steps);
     b->cur = (int)((cur0 + n_steps + 1) & 1);

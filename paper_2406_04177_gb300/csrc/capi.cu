@@ -556,7 +556,7 @@ vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out) {
     out->cg_last_relres = s->cg_last_relres;
     out->kernel_launches = s->launches;
     out->graph_launches = s->graph_launches;
-    out->active_nodes = s->n_active;
+    out->active_nodes = s->act.n_active;
     return VGA_OK;
 }
 
@@ -675,8 +675,7 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->d_err);
     dfree(s->nbr_table);
     dfree(s->nbr_tz);
-    dfree(s->active);
-    dfree(s->active_state);
+    activity_free(&s->act);
     dfree(s->bnode);
     dfree(s->bface);
     dfree(s->btheta6);

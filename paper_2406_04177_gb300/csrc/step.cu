@@ -501,20 +501,7 @@ void launch_staged_any(vga_sim *s, const StateIO &io) {
 }
 
 // The compact state of the running step call.
-SparseState sparse_state(vga_sim *s) {
-    SparseState ss;
-    const size_t words = (size_t)(std::max<int64_t>(s->npad, 64) + 31) / 32 + 8;
-    ss.mask = s->active;
-    ss.prefix = s->active ? s->active + words : nullptr;
-    const size_t cap = (size_t)std::max<int64_t>(s->active_state_cap, 1);
-    float *h = reinterpret_cast<float *>(s->active_state);
-    res_t *l = reinterpret_cast<res_t *>(h + 4 * cap);
-    for (int q = 0; q < 4; ++q) {
-        ss.h[q] = s->active_state ? h + q * cap : nullptr;
-        ss.l[q] = s->active_state ? l + q * cap : nullptr;
-    }
-    return ss;
-}
+SparseState sparse_state(vga_sim *s) { return activity_state(s->act); }
 
 template <int MODE, int WM, int PREC, int K>
 void launch_tablev_m(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
@@ -694,44 +681,81 @@ vga_status sim_diffuse_pass(vga_sim *s) {
     return VGA_OK;
 }
 
+SparseState activity_state(const Activity &a) {
+    SparseState ss;
+    ss.mask = a.words;
+    ss.prefix = a.words ? a.words + a.nw : nullptr;
+    const size_t cap = (size_t)std::max<int64_t>(a.cap, 1);
+    float *h = reinterpret_cast<float *>(a.state);
+    res_t *l = reinterpret_cast<res_t *>(h + 4 * cap);
+    for (int q = 0; q < 4; ++q) {
+        ss.h[q] = a.state ? h + q * cap : nullptr;
+        ss.l[q] = a.state ? l + q * cap : nullptr;
+    }
+    return ss;
+}
+
+vga_status activity_build(Activity *a, int64_t n, int64_t npad, const StateIO &cur, const StateIO &spare, bool comp,
+                          cudaStream_t st) {
+    const int64_t nw = (std::max<int64_t>(npad, 64) + 31) / 32 + 8;
+    if (!a->words || a->nw < nw) {  // mask words, their prefix, a counter
+        dfree(a->words);
+        a->words = nullptr;
+        VGA_TRY(dmalloc((void **)&a->words, sizeof(uint32_t) * 2 * (size_t)nw + sizeof(unsigned long long),
+                        "activity mask"));
+        a->nw = nw;
+        VGA_CUDA(cudaMemsetAsync(a->words, 0, sizeof(uint32_t) * 2 * (size_t)nw, st));
+    }
+    unsigned long long *count = reinterpret_cast<unsigned long long *>(a->words + 2 * a->nw);
+    VGA_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), st));
+    if (n > 0) {
+        if (comp) k_build_active<P_COMP><<<grid_for(n, kThreads), kThreads, 0, st>>>(n, cur, spare, a->words, count);
+        else k_build_active<P_F32><<<grid_for(n, kThreads), kThreads, 0, st>>>(n, cur, spare, a->words, count);
+        VGA_CHECK_LAUNCH();
+    }
+    k_scan_mask<<<1, 1024, 0, st>>>(a->nw, a->words, a->words + a->nw);
+    VGA_CHECK_LAUNCH();
+    unsigned long long h = 0;
+    VGA_CUDA(cudaMemcpyAsync(&h, count, sizeof(h), cudaMemcpyDeviceToHost, st));
+    VGA_CUDA(cudaStreamSynchronize(st));
+    a->n_active = (int64_t)h;
+    if (a->cap < a->n_active) {  // compact MB, SOM, FOM, CO2 (values and residuals)
+        dfree(a->state);
+        a->state = nullptr;
+        a->cap = 0;
+        VGA_TRY(dmalloc((void **)&a->state, (sizeof(float) + sizeof(res_t)) * 4 * (size_t)a->n_active,
+                        "compact active state"));
+        a->cap = a->n_active;
+    }
+    a->valid = true;
+    return VGA_OK;
+}
+
+vga_status activity_copy(const Activity &a, int64_t n, const StateIO &io, bool to_compact, bool comp, cudaStream_t st) {
+    if (n <= 0 || a.n_active <= 0) return VGA_OK;
+    k_active_copy<<<grid_for(n, kThreads), kThreads, 0, st>>>(n, activity_state(a), io, to_compact ? 1 : 0,
+                                                            comp ? 1 : 0);
+    VGA_CHECK_LAUNCH();
+    return VGA_OK;
+}
+
+void activity_free(Activity *a) {
+    dfree(a->words);
+    dfree(a->state);
+    *a = Activity{};
+}
+
 // Builds the activity mask for the current state (once per state upload; stepping keeps it valid).
 vga_status sim_build_active(vga_sim *s) {
-    const size_t words = (size_t)(std::max<int64_t>(s->npad, 64) + 31) / 32 + 8;
-    if (!s->active) {  // mask words, their prefix, a counter
-        VGA_TRY(dmalloc((void **)&s->active, sizeof(uint32_t) * 2 * words + sizeof(unsigned long long), "activity mask"));
-        VGA_CUDA(cudaMemsetAsync(s->active, 0, sizeof(uint32_t) * 2 * words, s->stream));
-    }
-    unsigned long long *count = reinterpret_cast<unsigned long long *>(s->active + 2 * words);
-    VGA_CUDA(cudaMemsetAsync(count, 0, sizeof(unsigned long long), s->stream));
-    StateIO cur = state_io(s), spare;
+    StateIO spare;
     for (int c = 0; c < 5; ++c) {
         spare.in[c] = s->spare(c);
         spare.out[c] = s->spare(c);
         spare.lin[c] = s->lspare(c);
         spare.lout[c] = s->lspare(c);
     }
-    if (s->precision() == P_COMP)
-        k_build_active<P_COMP><<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, cur, spare, s->active, count);
-    else
-        k_build_active<P_F32><<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, cur, spare, s->active, count);
-    VGA_CHECK_LAUNCH();
-    ++s->launches;
-    k_scan_mask<<<1, 1024, 0, s->stream>>>((int64_t)words, s->active, s->active + words);
-    VGA_CHECK_LAUNCH();
-    ++s->launches;
-    unsigned long long h = 0;
-    VGA_CUDA(cudaMemcpyAsync(&h, count, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
-    VGA_CUDA(cudaStreamSynchronize(s->stream));
-    s->n_active = (int64_t)h;
-    if (s->active_state_cap < s->n_active) {  // compact MB, SOM, FOM, CO2 (values and residuals)
-        dfree(s->active_state);
-        s->active_state = nullptr;
-        s->active_state_cap = 0;
-        VGA_TRY(dmalloc((void **)&s->active_state, (sizeof(float) + sizeof(res_t)) * 4 * (size_t)s->n_active,
-                        "compact active state"));
-        s->active_state_cap = s->n_active;
-    }
-    s->active_valid = true;
+    VGA_TRY(activity_build(&s->act, s->n, s->npad, state_io(s), spare, s->precision() == P_COMP, s->stream));
+    s->launches += 2;
     return VGA_OK;
 }
 
@@ -748,7 +772,7 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
         VGA_TRY(sim_block_table(s, &bt, &ok));
         sparse = ok;
     }
-    if (sparse && !s->active_valid) VGA_TRY(sim_build_active(s));
+    if (sparse && !s->act.valid) VGA_TRY(sim_build_active(s));
     const bool sub = s->subcycled();
     const int64_t k0 = s->steps_done;
     // ntrans is reset on every exit so that no other path sees a sub-cycled count
@@ -767,11 +791,10 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
             vga_sim *s;
             ~SparseEnd() { s->sparse_call = false; }
         } sparse_end{s};
-        const bool copy = sparse && s->n_active > 0;
-        const int comp = s->precision() == P_COMP ? 1 : 0;
+        const bool copy = sparse && s->act.n_active > 0;
+        const bool comp = s->precision() == P_COMP;
         if (copy) {
-            k_active_copy<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, sparse_state(s), state_io(s), 1, comp);
-            VGA_CHECK_LAUNCH();
+            VGA_TRY(activity_copy(s->act, s->n, state_io(s), true, comp, s->stream));
             ++s->launches;
         }
         s->sparse_call = sparse;
@@ -782,9 +805,7 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
         }
         s->sparse_call = false;
         if (copy) {
-            k_active_copy<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, sparse_state(s),
-                                                                              state_io_inplace(s), 0, comp);
-            VGA_CHECK_LAUNCH();
+            VGA_TRY(activity_copy(s->act, s->n, state_io_inplace(s), false, comp, s->stream));
             ++s->launches;
         }
     }
@@ -815,7 +836,7 @@ vga_status sim_totals(vga_sim *s, double *h_out) {
 }
 
 vga_status sim_convert_in(vga_sim *s, const double *d_x) {
-    s->active_valid = false;
+    s->act.valid = false;
     if (s->n == 0) return VGA_OK;
     k_convert_in<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, d_x, state_io_inplace(s),
                                                                      s->precision() == P_COMP);
@@ -834,7 +855,7 @@ vga_status sim_convert_out(vga_sim *s, double *d_x) {
 }
 
 vga_status sim_pack_f32(vga_sim *s, float *d_x, bool to_state) {
-    if (to_state) s->active_valid = false;
+    if (to_state) s->act.valid = false;
     if (s->n == 0) return VGA_OK;
     k_pack<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, d_x, state_io_inplace(s), to_state ? 1 : 0,
                                                                s->precision() == P_COMP);
@@ -854,7 +875,7 @@ vga_status sim_res_export(vga_sim *s, uint16_t *d_out) {
 }
 
 vga_status sim_res_import(vga_sim *s, const uint16_t *d_in) {
-    s->active_valid = false;
+    s->act.valid = false;
     if (s->n == 0) return VGA_OK;
     k_res_import<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, d_in, state_io_inplace(s));
     VGA_CHECK_LAUNCH();

@@ -122,6 +122,28 @@ struct SparseState {
     res_t *l[4] = {nullptr, nullptr, nullptr, nullptr};  // and residuals
 };
 
+// Activity mask of the sparse fused pass: bit i set when node i may change under the
+// transformation (MB, SOM, FOM or CO2 nonzero, or a negative-zero DOM; such a set never grows while
+// stepping), the marked nodes before each mask word, and the compact state they use during a step
+// call.  One per simulation or batch; built per state upload.
+struct Activity {
+    uint32_t *words = nullptr;  // nw mask words, nw prefix words, then a 64-bit counter
+    int64_t nw = 0;
+    char *state = nullptr;      // compact MB, SOM, FOM, CO2: 4 x cap values, then 4 x cap residuals
+    int64_t cap = 0;
+    int64_t n_active = -1;      // marked nodes (-1: not built)
+    bool valid = false;         // built for the current state
+};
+
+// Builds the mask, the prefix and the compact state for nodes [0, n) of the state `cur` (`spare`
+// gets zeros in MB, SOM, FOM, CO2 of the unmarked nodes).  One synchronisation.
+vga_status activity_build(Activity *a, int64_t n, int64_t npad, const StateIO &cur, const StateIO &spare, bool comp,
+                          cudaStream_t st);
+SparseState activity_state(const Activity &a);
+// Marked nodes' MB, SOM, FOM, CO2: state (io.in) -> compact, or compact -> state (io.out).
+vga_status activity_copy(const Activity &a, int64_t n, const StateIO &io, bool to_compact, bool comp, cudaStream_t st);
+void activity_free(Activity *a);
+
 // Edge-weight modes of the stencil.
 enum WeightMode { W_UNIT = 0, W_BLOCK = 1 };
 
@@ -211,15 +233,10 @@ struct vga_sim {
     bool mx_graph_failed = false;  // graph construction failed once: host-driven loop from then on
     void *mx_graph = nullptr;      // cached graphs of the mixed solve (pcg.cu)
     int64_t graph_launches = 0;    // CUDA graph launches of the mixed solve
-    // Sparse fused pass: bit i of `active` set when node i may change under the transformation
-    // (MB, SOM, FOM or CO2 nonzero, or a negative-zero DOM); such a set never grows while stepping.
-    uint32_t *active = nullptr;    // ceil(npad / 32) + 8 words, then the prefix of each word, then a counter
-    char *active_state = nullptr;  // compact MB, SOM, FOM, CO2 of the marked nodes (SparseState)
-    int64_t active_state_cap = 0;  // nodes it holds
-    bool active_valid = false;     // built for the current state (cleared by every state upload)
+    // Sparse fused pass (stencil.cuh MODE 3): activity mask and compact state
+    vga::Activity act;
     bool activity_skip = true;     // use it (vga_sim_set_activity_skip)
     bool sparse_call = false;      // the fused passes of the running step call are sparse
-    int64_t n_active = -1;         // nodes marked in the last build (-1: none built)
     int64_t steps_done = 0;
     int64_t cg_iterations = 0;
     double cg_last_relres = 0.0;

@@ -74,3 +74,45 @@ def test_batch_autotune_and_empty_instance(vga, oracle_lib):
     assert all(np.array_equal(b.get_masses(k), before[k]) for k in range(len(inst)))
     b.step(20)
     assert b.get_masses(len(inst)).shape == (5, 0)
+
+
+@pytest.mark.parametrize("organic", [False, True])
+def test_batch_sparse_equals_dense(vga, oracle_lib, organic):
+    """The batch's sparse fused passes (nodes with MB = SOM = FOM = CO2 = 0 only diffuse DOM) give
+    the bits of the dense passes and of single simulations with the sparse pass off, over calls of
+    several lengths and a second upload of the masses."""
+    specs = synth.batch_instances(6, 77, side_lo=16, side_hi=44)
+    inst = []
+    for sp in specs:
+        img = synth.pore_mask(sp["shape"], sp["porosity"], sp["mask_seed"])
+        og = oracle_lib.graph_build(img)
+        X0 = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), sp["mass_seed"],
+                                  with_organic_matter=organic)
+        inst.append((img, og, X0, sp["params"]))
+    graphs = [vga.Graph(img) for img, _, _, _ in inst]
+    params = [p for _, _, _, p in inst]
+    outs = []
+    for skip in (True, False):
+        b = vga.Batch(graphs, params)
+        b.set_activity_skip(skip)
+        for k, (_, _, X0, _) in enumerate(inst):
+            b.set_masses(k, X0)
+        b.step(40)
+        b.step(1)
+        b.step(7)
+        mid = [b.get_masses(k) for k in range(len(inst))]
+        for k, (_, _, X0, _) in enumerate(inst):
+            b.set_masses(k, 0.5 * X0)
+        b.step(23)
+        outs.append((mid, [b.get_masses(k) for k in range(len(inst))]))
+        b.close()
+    for a, c in zip(outs[0][0] + outs[0][1], outs[1][0] + outs[1][1]):
+        assert np.array_equal(a, c)
+    for k, (_, _, X0, p) in enumerate(inst):
+        sim = vga.Sim(graphs[k], p)
+        sim.set_activity_skip(False)
+        sim.set_masses(X0)
+        sim.step(40)
+        sim.step(1)
+        sim.step(7)
+        assert np.array_equal(sim.get_masses(), outs[0][0][k])
