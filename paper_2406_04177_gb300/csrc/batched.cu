@@ -46,8 +46,7 @@ struct BatchArgs {
     unsigned *bar;  // [0] arrivals, [1] generation
     int32_t *err;
     StateIO io[2];  // a pass whose input is state buffer k reads io[k] (kept as kernel parameters)
-    SparseState ss;  // the sparse fused pass (stencil.cuh MODE 3), when `sparse`
-    int sparse;
+    SparseState ss;  // the sparse fused pass (stencil.cuh MODE 3) of the SPARSE instantiations
 };
 
 // One fused pass over the whole batch, kBatchGroup consecutive nodes per thread (table_vec).
@@ -55,7 +54,7 @@ struct BatchArgs {
 // belong to one instance, whose parameters the warp reads from shared memory (per-thread copies
 // would hold a dozen registers); every thread of a block runs the same number of iterations (the
 // warp-wide shuffles need all lanes).
-template <int TR, int PREC, int TF>
+template <int TR, int PREC, int TF, bool SPARSE>
 __device__ __forceinline__ void batch_fused_pass(const BatchArgs &a, const StateIO &io) {
     constexpr int KG = kBatchGroup;
     __shared__ StepParams wp[kTile / 32];
@@ -73,7 +72,7 @@ __device__ __forceinline__ void batch_fused_pass(const BatchArgs &a, const State
         __syncwarp();
         if ((threadIdx.x & 31) == 0) wp[w] = k >= 0 ? a.inst[k].p : StepParams{};
         __syncwarp();
-        if (a.sparse) table_vec<3, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, wp[w], io, PassRecord{}, a.ss);
+        if (SPARSE) table_vec<3, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, wp[w], io, PassRecord{}, a.ss);
         else table_vec<1, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, wp[w], io);
     }
 }
@@ -81,8 +80,8 @@ __device__ __forceinline__ void batch_fused_pass(const BatchArgs &a, const State
 // FUSED_ONLY: an instantiation for launches whose passes are all fused ones (every launch but the
 // first and the last pass of a call); without the code of the other two kinds it needs fewer
 // registers, so more blocks are resident.
-template <int TR, int PREC, int TF, bool FUSED_ONLY>
-__global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
+template <int TR, int PREC, int TF, bool FUSED_ONLY, bool SPARSE>
+__global__ void __launch_bounds__(kTile, SPARSE ? 4 : 1) k_batch(BatchArgs a, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
     for (int32_t pass = pass0; pass < pass1; ++pass) {
         // transform / fused / diffuse
         const int kind = FUSED_ONLY ? 1 : ((pass == 0) ? 0 : (pass == npass - 1 ? 2 : 1));
@@ -92,8 +91,8 @@ __global__ void __launch_bounds__(kTile) k_batch(BatchArgs a, int32_t pass0, int
             // fused pass: kBatchGroup consecutive nodes per thread (table_vec).  Instances start on
             // tile boundaries, so a group never straddles two; every thread of a block runs the
             // same number of iterations (the warp-wide shuffles need all lanes).
-            if (bi == 0) batch_fused_pass<TR, PREC, TF>(a, a.io[0]);
-            else batch_fused_pass<TR, PREC, TF>(a, a.io[1]);
+            if (bi == 0) batch_fused_pass<TR, PREC, TF, SPARSE>(a, a.io[0]);
+            else batch_fused_pass<TR, PREC, TF, SPARSE>(a, a.io[1]);
             if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err)) return;
             continue;
         }
@@ -218,6 +217,7 @@ struct vga_batch {
     int cur = 0;
     int grid = 0;          // blocks of a fused-only launch (resident on every SM)
     int grid_edge = 0;     // blocks of a launch of the first or the last pass
+    int grid_sparse = 0;   // blocks of a sparse fused-only launch
     int blocks_per_sm = 0;  // tuning knob (0: the occupancy maximum)
     int steps_per_launch = 100;
     bool use_graph = true;
@@ -230,22 +230,24 @@ struct vga_batch {
 
 namespace {
 
-template <int TFV, bool FO>
+template <int TFV, bool FO, bool SP>
 const void *batch_kernel(const vga_batch *b) {
-    return b->transform == 0
-               ? (b->precision == P_COMP ? (const void *)k_batch<0, P_COMP, TFV, FO> : (const void *)k_batch<0, P_F32, TFV, FO>)
-               : (b->precision == P_COMP ? (const void *)k_batch<1, P_COMP, TFV, FO> : (const void *)k_batch<1, P_F32, TFV, FO>);
+    return b->transform == 0 ? (b->precision == P_COMP ? (const void *)k_batch<0, P_COMP, TFV, FO, SP>
+                                                       : (const void *)k_batch<0, P_F32, TFV, FO, SP>)
+                             : (b->precision == P_COMP ? (const void *)k_batch<1, P_COMP, TFV, FO, SP>
+                                                       : (const void *)k_batch<1, P_F32, TFV, FO, SP>);
 }
 
-template <int TFV, bool FO>
+template <int TFV, bool FO, bool SP>
 cudaError_t batch_launch_tf(const vga_batch *b, const cudaLaunchConfig_t &cfg, const BatchArgs &a, int32_t pass0,
                             int32_t pass1, int32_t npass, int32_t cur0) {
     if (b->transform == 0) {
-        if (b->precision == P_COMP) return cudaLaunchKernelEx(&cfg, k_batch<0, P_COMP, TFV, FO>, a, pass0, pass1, npass, cur0);
-        return cudaLaunchKernelEx(&cfg, k_batch<0, P_F32, TFV, FO>, a, pass0, pass1, npass, cur0);
+        if (b->precision == P_COMP)
+            return cudaLaunchKernelEx(&cfg, k_batch<0, P_COMP, TFV, FO, SP>, a, pass0, pass1, npass, cur0);
+        return cudaLaunchKernelEx(&cfg, k_batch<0, P_F32, TFV, FO, SP>, a, pass0, pass1, npass, cur0);
     }
-    if (b->precision == P_COMP) return cudaLaunchKernelEx(&cfg, k_batch<1, P_COMP, TFV, FO>, a, pass0, pass1, npass, cur0);
-    return cudaLaunchKernelEx(&cfg, k_batch<1, P_F32, TFV, FO>, a, pass0, pass1, npass, cur0);
+    if (b->precision == P_COMP) return cudaLaunchKernelEx(&cfg, k_batch<1, P_COMP, TFV, FO, SP>, a, pass0, pass1, npass, cur0);
+    return cudaLaunchKernelEx(&cfg, k_batch<1, P_F32, TFV, FO, SP>, a, pass0, pass1, npass, cur0);
 }
 
 // Resident blocks of an instantiation, limited by blocks_per_sm and the tile count.
@@ -261,8 +263,9 @@ vga_status batch_grid_of(vga_batch *b, const void *fn, int *grid) {
 }
 
 vga_status batch_grid(vga_batch *b) {
-    VGA_TRY(batch_grid_of(b, b->tz ? batch_kernel<1, false>(b) : batch_kernel<0, false>(b), &b->grid_edge));
-    return batch_grid_of(b, b->tz ? batch_kernel<1, true>(b) : batch_kernel<0, true>(b), &b->grid);
+    VGA_TRY(batch_grid_of(b, b->tz ? batch_kernel<1, false, false>(b) : batch_kernel<0, false, false>(b), &b->grid_edge));
+    VGA_TRY(batch_grid_of(b, b->tz ? batch_kernel<1, true, true>(b) : batch_kernel<0, true, true>(b), &b->grid_sparse));
+    return batch_grid_of(b, b->tz ? batch_kernel<1, true, false>(b) : batch_kernel<0, true, false>(b), &b->grid);
 }
 
 vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0, bool sparse) {
@@ -282,7 +285,6 @@ vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npas
     a.bar = b->bar;
     a.err = b->err;
     a.ss = activity_state(b->act);
-    a.sparse = sparse ? 1 : 0;
     for (int k = 0; k < 2; ++k) {
         for (int c = 0; c < 5; ++c) {
             a.io[k].in[c] = b->h[k] + c * b->npad;
@@ -294,7 +296,7 @@ vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npas
     // the first and the last pass of a call need the full kernel; the others run the fused-only one
     const bool fused_only = pass0 > 0 && pass1 < npass;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(fused_only ? b->grid : b->grid_edge));
+    cfg.gridDim = dim3((unsigned)(fused_only ? (sparse ? b->grid_sparse : b->grid) : b->grid_edge));
     cfg.blockDim = dim3(kTile);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = b->stream;
@@ -303,10 +305,16 @@ vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npas
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = fused_only ? (b->tz ? batch_launch_tf<1, true>(b, cfg, a, pass0, pass1, npass, cur0)
-                                              : batch_launch_tf<0, true>(b, cfg, a, pass0, pass1, npass, cur0))
-                                     : (b->tz ? batch_launch_tf<1, false>(b, cfg, a, pass0, pass1, npass, cur0)
-                                              : batch_launch_tf<0, false>(b, cfg, a, pass0, pass1, npass, cur0));
+    cudaError_t e;
+    if (fused_only && sparse)
+        e = b->tz ? batch_launch_tf<1, true, true>(b, cfg, a, pass0, pass1, npass, cur0)
+                  : batch_launch_tf<0, true, true>(b, cfg, a, pass0, pass1, npass, cur0);
+    else if (fused_only)
+        e = b->tz ? batch_launch_tf<1, true, false>(b, cfg, a, pass0, pass1, npass, cur0)
+                  : batch_launch_tf<0, true, false>(b, cfg, a, pass0, pass1, npass, cur0);
+    else
+        e = b->tz ? batch_launch_tf<1, false, false>(b, cfg, a, pass0, pass1, npass, cur0)
+                  : batch_launch_tf<0, false, false>(b, cfg, a, pass0, pass1, npass, cur0);
     if (e != cudaSuccess) return cuda_fail(e, "cooperative launch of k_batch", __FILE__, __LINE__);
     return VGA_OK;
 }
