@@ -613,7 +613,7 @@ vga_status vga_batch_get_stats(const vga_batch *b, vga_batch_stats *out) {
     out->instances = b->count;
     out->total_nodes = 0;
     for (int64_t v : b->nodes) out->total_nodes += v;
-    out->grid_blocks = b->grid;
+    out->grid_blocks = b->activity_skip ? b->grid_sparse : b->grid;
     out->steps_per_launch = b->steps_per_launch;
     out->kernel_launches = b->launches;
     out->graph_replays = b->graph_replays;
@@ -659,7 +659,7 @@ vga_status vga_batch_autotune(vga_batch *b, int32_t trial_steps, vga_batch_tune 
             vga_batch_tune_entry &en = out->entries[out->count];
             en.steps_per_launch = kSteps[si];
             en.blocks_per_sm = kBlocks[bi];
-            en.grid_blocks = b->grid;
+            en.grid_blocks = b->activity_skip ? b->grid_sparse : b->grid;
             en.ms_per_step = ms / trial_steps;
             if (ms < best) {
                 best = ms;
