@@ -447,7 +447,10 @@ __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const Step
 // DOM that the (identity) transformation left unchanged; then the warp's nodes whose bit in the
 // activity mask is set are dealt out one per lane (their rounded DOM by shuffles), and each such
 // lane transforms its node with MB, SOM, FOM and CO2 from the compact state (updated in place),
-// storing them there and the DOM as MODE 1 does.  Must be called by all 32 lanes of a warp.
+// storing them there and the DOM as MODE 1 does.  MODE 4 is the first half of the two-kernel sparse
+// pass: MODE 3 without the deal, a marked node's DOM stored as the rounded pair itself (the second
+// half, k_transform_compact, reads it back exactly as MODE 1 holds it in registers).  Must be
+// called by all 32 lanes of a warp.
 template <int MODE, int WM, int TR, int PREC, int TF, int K, bool REC = false>
 __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTable &tb, const BlockTable &bt,
                                           const StepParams &p, const StateIO &io,
@@ -459,7 +462,7 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
     if (full) group_load<WM, PREC, TF, K, true>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
     else group_load<WM, PREC, TF, K, false>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
     uint32_t act_bits = 0u;  // MODE 3: activity bits of the group
-    if (MODE == 3 && i0 < n) act_bits = (__ldg(ss.mask + (i0 >> 5)) >> (i0 & 31)) & ((1u << K) - 1u);
+    if ((MODE == 3 || MODE == 4) && i0 < n) act_bits = (__ldg(ss.mask + (i0 >> 5)) >> (i0 & 31)) & ((1u << K) - 1u);
     float y[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) y[k] = x2[k].h;
@@ -493,6 +496,35 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
         if (zm[k]) add(4, zv[k]);
         if (zp[k]) add(5, zw[k]);
         vadd<PREC>(x2[k], __fmul_rn(-p.c, acc));  // Scheme 1
+    }
+    if (MODE == 4) {
+        float h[K];
+        res_t q[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            vround<PREC>(x2[k]);
+            if ((act_bits >> k) & 1u) {  // the rounded pair itself
+                h[k] = x2[k].h;
+                q[k] = PREC == P_COMP ? res_encode(x2[k].l, h[k]) : (res_t)0;
+            } else if (PREC == P_COMP) {  // renormalised as vstore does
+                h[k] = __fadd_rn(x2[k].h, x2[k].l);
+                q[k] = res_encode(__fadd_rn(__fsub_rn(x2[k].h, h[k]), x2[k].l), h[k]);
+            } else {
+                h[k] = x2[k].h;
+            }
+        }
+        if (full) {
+            st_floats<K>(io.out[1] + i0, h);
+            if (PREC == P_COMP) st_res<K>(io.lout[1] + i0, q);
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (i0 + k < n) {
+                    io.out[1][i0 + k] = h[k];
+                    if (PREC == P_COMP) io.lout[1][i0 + k] = q[k];
+                }
+        }
+        return;
     }
     if (MODE == 3) {
 #pragma unroll

@@ -282,10 +282,42 @@ __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable 
 
 // K consecutive nodes per thread (table_vec); n < 2^31, so K * thread index fits 32 bits.
 template <int MODE, int WM, int TR, int PREC, int TF, int K>
-__global__ void __launch_bounds__(kThreads, MODE == 3 ? 5 : 4) k_stencil_tablev(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+__global__ void __launch_bounds__(kThreads, MODE >= 3 ? 5 : 4) k_stencil_tablev(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                              StateIO io, SparseState ss) {
     const uint32_t i0 = (uint32_t)K * ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x);
     table_vec<MODE, WM, TR, PREC, TF, K>(i0, (uint32_t)n, tb, bt, p, io, PassRecord{}, ss);
+}
+
+// Second half of the two-kernel sparse pass: one thread per marked node, in rank order, with its
+// MB, SOM, FOM, CO2 from the compact state (updated in place) and its DOM as the first half stored it
+// (the rounded pair); stores the DOM as MODE 1 does.
+template <int TR, int PREC>
+__global__ void __launch_bounds__(kThreads) k_transform_compact(int64_t m, SparseState ss, StepParams p, StateIO io) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    const uint32_t i = __ldg(ss.list + r);
+    V x2;
+    x2.h = io.out[1][i];
+    x2.l = PREC == P_COMP ? res_decode(io.lout[1][i], x2.h) : 0.0f;
+    V v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[q].h = ss.h[q][r];
+        v[q].l = PREC == P_COMP ? res_decode(ss.l[q][r], v[q].h) : 0.0f;
+    }
+    transform_n<TR, PREC>(v[0], x2, v[1], v[2], v[3], p);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) vstore<PREC>(ss.h[q], ss.l[q], r, v[q]);
+    vstore<PREC>(io.out[1], io.lout[1], i, x2);
+}
+
+// Node of each rank (once per state upload, after the prefix).
+__global__ void k_build_list(int64_t n, SparseState ss, uint32_t *__restrict__ list) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t w = (uint32_t)(i >> 5), bit = 1u << (i & 31);
+    const uint32_t m = __ldg(ss.mask + w);
+    if (m & bit) list[__ldg(ss.prefix + w) + __popc(m & (bit - 1u))] = (uint32_t)i;
 }
 
 // Exclusive prefix of the marked nodes per mask word (one block; once per state upload).
@@ -516,11 +548,23 @@ void launch_tablev_m(vga_sim *s, const StateIO &io, const NbrTable &tb, const Bl
     }
 }
 
-// Fused passes of the four-node kernel run sparse (MODE 3) inside a sparse step call.
+// Fused passes of the four-node kernel run sparse inside a sparse step call: the DOM of every node
+// (MODE 4), then the transformation of the marked nodes in rank order.
 template <int MODE, int WM, int PREC, int K>
 void launch_tablev(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
-    if (MODE == 1 && K == 4 && s->sparse_call) launch_tablev_m<3, WM, PREC, K>(s, io, tb, bt);
-    else launch_tablev_m<MODE, WM, PREC, K>(s, io, tb, bt);
+    if (MODE == 1 && K == 4 && s->sparse_call) {
+        launch_tablev_m<4, WM, PREC, K>(s, io, tb, bt);
+        const int64_t m = s->act.n_active;
+        if (m > 0) {
+            const unsigned g = grid_for(m, kThreads);
+            const SparseState ss = activity_state(s->act);
+            if (s->sp.transform == 0) k_transform_compact<0, PREC><<<g, kThreads, 0, s->stream>>>(m, ss, s->sp, io);
+            else k_transform_compact<1, PREC><<<g, kThreads, 0, s->stream>>>(m, ss, s->sp, io);
+            ++s->launches;
+        }
+        return;
+    }
+    launch_tablev_m<MODE, WM, PREC, K>(s, io, tb, bt);
 }
 
 template <int MODE, int WM, int PREC>
@@ -692,6 +736,7 @@ SparseState activity_state(const Activity &a) {
         ss.h[q] = a.state ? h + q * cap : nullptr;
         ss.l[q] = a.state ? l + q * cap : nullptr;
     }
+    ss.list = a.state ? reinterpret_cast<const uint32_t *>(l + 4 * cap) : nullptr;
     return ss;
 }
 
@@ -723,9 +768,15 @@ vga_status activity_build(Activity *a, int64_t n, int64_t npad, const StateIO &c
         dfree(a->state);
         a->state = nullptr;
         a->cap = 0;
-        VGA_TRY(dmalloc((void **)&a->state, (sizeof(float) + sizeof(res_t)) * 4 * (size_t)a->n_active,
+        VGA_TRY(dmalloc((void **)&a->state,
+                        ((sizeof(float) + sizeof(res_t)) * 4 + sizeof(uint32_t)) * (size_t)a->n_active + 16,
                         "compact active state"));
         a->cap = a->n_active;
+    }
+    if (n > 0 && a->n_active > 0) {
+        const SparseState ss = activity_state(*a);
+        k_build_list<<<grid_for(n, kThreads), kThreads, 0, st>>>(n, ss, const_cast<uint32_t *>(ss.list));
+        VGA_CHECK_LAUNCH();
     }
     a->valid = true;
     return VGA_OK;

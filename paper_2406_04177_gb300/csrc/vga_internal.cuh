@@ -118,6 +118,7 @@ struct StateIO {
 struct SparseState {
     const uint32_t *mask = nullptr;    // activity bits
     const uint32_t *prefix = nullptr;  // marked nodes before each mask word
+    const uint32_t *list = nullptr;    // node of each rank
     float *h[4] = {nullptr, nullptr, nullptr, nullptr};  // MB, SOM, FOM, CO2 values
     res_t *l[4] = {nullptr, nullptr, nullptr, nullptr};  // and residuals
 };
@@ -129,7 +130,7 @@ struct SparseState {
 struct Activity {
     uint32_t *words = nullptr;  // nw mask words, nw prefix words, then a 64-bit counter
     int64_t nw = 0;
-    char *state = nullptr;      // compact MB, SOM, FOM, CO2: 4 x cap values, then 4 x cap residuals
+    char *state = nullptr;      // compact MB, SOM, FOM, CO2: 4 x cap values, 4 x cap residuals, cap nodes
     int64_t cap = 0;
     int64_t n_active = -1;      // marked nodes (-1: not built)
     bool valid = false;         // built for the current state
