@@ -280,10 +280,23 @@ __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable 
     table_node<MODE, WM, TR, PREC, LD_NC, TF>(i, i < (uint64_t)n, tb, bt, p, io);
 }
 
+// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later). A grid launched with
+// programmatic stream serialisation may be scheduled while the kernel before it on the stream is
+// still running; pdl_wait, before the grid's first global access, holds it until that kernel has
+// completed and its writes are visible. For a grid launched without the attribute it returns at
+// once. pdl_trigger lets the next grid on the stream be scheduled once every block of this one has
+// issued it (its blocks then sit in their own pdl_wait).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // K consecutive nodes per thread (table_vec); n < 2^31, so K * thread index fits 32 bits.
 template <int MODE, int WM, int TR, int PREC, int TF, int K>
 __global__ void __launch_bounds__(kThreads, MODE >= 3 ? 5 : 4) k_stencil_tablev(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                              StateIO io, SparseState ss) {
+    if constexpr (MODE == 1 || MODE == 4) {
+        pdl_wait();
+        pdl_trigger();
+    }
     const uint32_t i0 = (uint32_t)K * ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x);
     table_vec<MODE, WM, TR, PREC, TF, K>(i0, (uint32_t)n, tb, bt, p, io, PassRecord{}, ss);
 }
@@ -293,6 +306,8 @@ __global__ void __launch_bounds__(kThreads, MODE >= 3 ? 5 : 4) k_stencil_tablev(
 // (the rounded pair); stores the DOM as MODE 1 does.
 template <int TR, int PREC>
 __global__ void __launch_bounds__(kThreads) k_transform_compact(int64_t m, SparseState ss, StepParams p, StateIO io) {
+    pdl_wait();
+    pdl_trigger();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= m) return;
     const uint32_t i = __ldg(ss.list + r);
@@ -535,10 +550,37 @@ void launch_staged_any(vga_sim *s, const StateIO &io) {
 // The compact state of the running step call.
 SparseState sparse_state(vga_sim *s) { return activity_state(s->act); }
 
+// Launch with programmatic stream serialisation: the grid may be scheduled during the tail of the
+// kernel before it on the stream and waits for it in pdl_wait (the kernel must call it first).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), unsigned grid, cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <int MODE, int WM, int PREC, int K>
 void launch_tablev_m(vga_sim *s, const StateIO &io, const NbrTable &tb, const BlockTable &bt) {
     const unsigned grid = grid_for((s->n + K - 1) / K, kThreads);
     const SparseState act = sparse_state(s);
+    if constexpr (MODE == 1 || MODE == 4) {
+        if (tb.tz) {
+            if (s->sp.transform == 0) launch_pdl(k_stencil_tablev<MODE, WM, 0, PREC, 1, K>, grid, s->stream, s->n, tb, bt, s->sp, io, act);
+            else launch_pdl(k_stencil_tablev<MODE, WM, 1, PREC, 1, K>, grid, s->stream, s->n, tb, bt, s->sp, io, act);
+        } else {
+            if (s->sp.transform == 0) launch_pdl(k_stencil_tablev<MODE, WM, 0, PREC, 0, K>, grid, s->stream, s->n, tb, bt, s->sp, io, act);
+            else launch_pdl(k_stencil_tablev<MODE, WM, 1, PREC, 0, K>, grid, s->stream, s->n, tb, bt, s->sp, io, act);
+        }
+        return;
+    }
     if (tb.tz) {
         if (s->sp.transform == 0) k_stencil_tablev<MODE, WM, 0, PREC, 1, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io, act);
         else k_stencil_tablev<MODE, WM, 1, PREC, 1, K><<<grid, kThreads, 0, s->stream>>>(s->n, tb, bt, s->sp, io, act);
@@ -558,8 +600,8 @@ void launch_tablev(vga_sim *s, const StateIO &io, const NbrTable &tb, const Bloc
         if (m > 0) {
             const unsigned g = grid_for(m, kThreads);
             const SparseState ss = activity_state(s->act);
-            if (s->sp.transform == 0) k_transform_compact<0, PREC><<<g, kThreads, 0, s->stream>>>(m, ss, s->sp, io);
-            else k_transform_compact<1, PREC><<<g, kThreads, 0, s->stream>>>(m, ss, s->sp, io);
+            if (s->sp.transform == 0) launch_pdl(k_transform_compact<0, PREC>, g, s->stream, m, ss, s->sp, io);
+            else launch_pdl(k_transform_compact<1, PREC>, g, s->stream, m, ss, s->sp, io);
             ++s->launches;
         }
         return;
