@@ -289,9 +289,17 @@ __global__ void __launch_bounds__(kThreads) k_stencil_table(int64_t n, NbrTable 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Resident blocks per SM the compiler must fit: the DOM half of the sparse pass (MODE 4) is bound
+// by the latency of its gathers and fits 40 registers (6 blocks) without spills, except with block
+// conductances (5).
+template <int MODE, int WM>
+constexpr int tablev_min_blocks() {
+    return MODE == 4 ? (WM == W_UNIT ? 6 : 5) : (MODE == 3 ? 5 : 4);
+}
+
 // K consecutive nodes per thread (table_vec); n < 2^31, so K * thread index fits 32 bits.
 template <int MODE, int WM, int TR, int PREC, int TF, int K>
-__global__ void __launch_bounds__(kThreads, MODE >= 3 ? 5 : 4) k_stencil_tablev(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+__global__ void __launch_bounds__(kThreads, tablev_min_blocks<MODE, WM>()) k_stencil_tablev(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                              StateIO io, SparseState ss) {
     if constexpr (MODE == 1 || MODE == 4) {
         pdl_wait();
