@@ -210,31 +210,66 @@ __global__ void k_compact_pairs(unsigned long long hsize, const unsigned long lo
 }
 
 // Primitive masses: out[label[i]] = sum of m_i over the primitive's nodes, summed exactly in fixed
-// point: every node's value becomes the integer round(m_i * scale), scale = 2^(61 - e) with
-// sum_i |m_i| < 2^e, so no partial sum can overflow int64 and the result does not depend on the
-// order of the atomic additions (the restriction is deterministic).  A CTA sums a segment of kSeg
-// consecutive nodes into a shared-memory hash of labels (warp-level pre-aggregation first) with
-// 64-bit integer atomics, then flushes one global atomic per distinct label; a label that finds no
-// free slot within kProbe probes goes straight to global memory.
+// point: every node's value becomes the integer round(h_i 2^k) + round(l_i 2^k) of its stored pair,
+// k = 61 - e with sum_i (|h_i| + |l_i|) < 2^e (up to the FP32 rounding of that bound; int64 holds
+// 2 more bits), so no partial sum can overflow int64 and the result does not depend on the order
+// of the atomic additions (the restriction is deterministic).  No FP64 arithmetic per node: the
+// FP64 rate of this part is a small fraction of its FP32 and integer rates.  A CTA sums a segment
+// of kSeg consecutive nodes into a shared-memory hash of labels (runs of equal labels over
+// consecutive lanes summed in the warp first) with 64-bit integer atomics, then flushes one global
+// atomic per distinct label; a label that finds no free slot within kProbe probes goes straight to
+// global memory.
 constexpr int kSeg = 4096;
 constexpr int kHash = 1024;
 constexpr int kProbe = 16;
 constexpr int kSumBlocks = 1024;
+static_assert(kSeg % (4 * kThreads) == 0, "a segment is a whole number of four-row batches");
+
+// round(x 2^k) of a finite FP32 x, ties to even, from the bits of x; the caller bounds |x| 2^k
+// below 2^62 (so a left shift stays below 64 bits; a shift of 64 or more, outside that bound, gives 0).
+__device__ __forceinline__ long long fixed_of_f32(float x, int k) {
+    const uint32_t b = __float_as_uint(x);
+    const int ex = (int)((b >> 23) & 0xffu);
+    const uint64_t m = ex ? (uint64_t)((b & 0x7fffffu) | 0x800000u) : (uint64_t)(b & 0x7fffffu);
+    const int sh = (ex ? ex - 150 : -149) + k;  // x 2^k = m 2^sh
+    uint64_t r;
+    if (sh >= 0) {
+        r = sh < 64 ? m << sh : 0ull;
+    } else if (sh < -40) {
+        r = 0ull;  // m 2^sh < 2^-16
+    } else {
+        const int t = -sh;
+        const uint64_t rem = m & ((1ull << t) - 1ull), half = 1ull << (t - 1);
+        r = m >> t;
+        if (rem > half || (rem == half && (r & 1ull))) ++r;
+    }
+    return (b >> 31) ? -(long long)r : (long long)r;
+}
 
 template <int PREC>
 __global__ void __launch_bounds__(kThreads) k_abs_sum(int64_t n, const float *__restrict__ H,
                                                       const res_t *__restrict__ L, double *__restrict__ part) {
-    double acc[1] = {0.0};
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const V x = vload<PREC>(H, L, i);
-        acc[0] += fabs((double)x.h + (double)x.l);
+    float acc32 = 0.0f;  // about n / (blocks x threads) terms per thread
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + 3 * stride < n; i += 4 * stride) {  // four independent loads in flight
+        V x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = vload<PREC>(H, L, i + u * stride);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc32 += fabsf(x[u].h) + fabsf(x[u].l);
     }
+    for (; i < n; i += stride) {
+        const V x = vload<PREC>(H, L, i);
+        acc32 += fabsf(x.h) + fabsf(x.l);
+    }
+    double acc[1] = {(double)acc32};
     __shared__ double out[1];
     block_sum_store<1>(acc, out);
     if (threadIdx.x == 0) part[blockIdx.x] = out[0];
 }
 
-// scale[0] = 2^(61 - e), sum |m| < 2^e; scale[1] = 1 / scale[0]
+// scale[0] = 2^(61 - e), sum |m| < 2^e; scale[1] = 1 / scale[0]; scale[2] = 61 - e
 __global__ void k_fx_scale(const double *__restrict__ part, int32_t count, double *__restrict__ scale) {
     double acc[1] = {0.0};
     for (int32_t k = threadIdx.x; k < count; k += blockDim.x) acc[0] += part[k];
@@ -245,11 +280,14 @@ __global__ void k_fx_scale(const double *__restrict__ part, int32_t count, doubl
         const int e = S > 0.0 ? ilogb(S) + 1 : 0;
         scale[0] = ldexp(1.0, 61 - e);
         scale[1] = ldexp(1.0, e - 61);
+        scale[2] = (double)(61 - e);
     }
 }
 
+constexpr int kRestrictBlocksPerSm = 6;  // resident blocks of k_restrict (at most 40 registers)
+
 template <int PREC>
-__global__ void __launch_bounds__(kThreads) k_restrict(int64_t n, const int32_t *__restrict__ lab,
+__global__ void __launch_bounds__(kThreads, kRestrictBlocksPerSm) k_restrict(int64_t n, const int32_t *__restrict__ lab,
                                                        const float *__restrict__ H, const res_t *__restrict__ L,
                                                        const double *__restrict__ scale,
                                                        unsigned long long *__restrict__ out) {
@@ -260,29 +298,51 @@ __global__ void __launch_bounds__(kThreads) k_restrict(int64_t n, const int32_t 
         hval[k] = 0ull;
     }
     __syncthreads();
-    const double sc = scale[0];
+    const int k2 = (int)scale[2];
+    const int lane = (int)(threadIdx.x & 31);
     const int64_t nseg = (n + kSeg - 1) / kSeg;
     for (int64_t seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
         const int64_t i0 = seg * kSeg;
-        for (int k = 0; k < kSeg; k += kThreads) {
-            const int64_t i = i0 + k + threadIdx.x;
+        for (int k4 = 0; k4 < kSeg; k4 += 4 * kThreads) {
+          // the loads of four rows of the segment first (independent), then their sums
+          int32_t a4[4];
+          float h4[4];
+          res_t l4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+              const int64_t i = i0 + k4 + u * kThreads + threadIdx.x;
+              a4[u] = i < n ? __ldg(lab + i) : -1;
+              h4[u] = i < n ? __ldg(H + i) : 0.0f;
+              l4[u] = (PREC == P_COMP && i < n) ? __ldg(L + i) : (res_t)0;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t i = i0 + k4 + u * kThreads + threadIdx.x;
             const bool live = i < n;
-            const int32_t a = live ? __ldg(lab + i) : -1;
-            unsigned long long v = 0ull;
+            const int32_t a = a4[u];
+            long long f = 0;
             if (live) {
-                const V x = vload<PREC>(H, L, i);
-                v = (unsigned long long)__double2ll_rn(((double)x.h + (double)x.l) * sc);
+                f = fixed_of_f32(h4[u], k2);
+                if (PREC == P_COMP) f += fixed_of_f32(res_decode(l4[u], h4[u]), k2);
             }
-            const unsigned act = __ballot_sync(0xffffffffu, live);
-            const unsigned peers = __match_any_sync(0xffffffffu, a);
-            const unsigned long long sum = peer_sum<unsigned long long>(act, peers, v);
-            if (live && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+            // inclusive sum over the run of equal labels that ends at this lane
+            const int32_t a_prev = __shfl_up_sync(0xffffffffu, a, 1);
+            const int32_t a_next = __shfl_down_sync(0xffffffffu, a, 1);
+            const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || a_prev != a);
+            const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+            unsigned long long sum = (unsigned long long)f;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long t = __shfl_up_sync(0xffffffffu, sum, d);
+                if (lane - d >= start) sum += t;
+            }
+            if (live && (lane == 31 || a_next != a)) {
                 const uint32_t h = (uint32_t)a * 2654435761u;
                 bool done = false;
                 for (int q = 0; q < kProbe; ++q) {
                     const int slot = (int)((h >> 22) + q) & (kHash - 1);
-                    const int32_t prev = atomicCAS(hkey + slot, -1, a);
-                    if (prev == -1 || prev == a) {
+                    const int32_t cur = atomicCAS(hkey + slot, -1, a);
+                    if (cur == -1 || cur == a) {
                         atomicAdd(hval + slot, sum);
                         done = true;
                         break;
@@ -290,6 +350,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict(int64_t n, const int32_t 
                 }
                 if (!done) atomicAdd(out + a, sum);
             }
+          }
         }
         __syncthreads();
         for (int k = threadIdx.x; k < kHash; k += blockDim.x) {
@@ -800,13 +861,17 @@ vga_status vga_pngm_restrict(vga_pngm *pg, vga_sim *s, int32_t comp, double *d_o
         VGA_CUDA(cudaMemsetAsync(d_out, 0, sizeof(double) * (size_t)pg->q, st));
         return VGA_OK;
     }
-    if (!pg->fx) VGA_TRY(dmalloc((void **)&pg->fx, sizeof(unsigned long long) * (size_t)pg->q + 2 * sizeof(double) +
+    if (!pg->fx) VGA_TRY(dmalloc((void **)&pg->fx, sizeof(unsigned long long) * (size_t)pg->q + 4 * sizeof(double) +
                                                        sizeof(double) * kSumBlocks, "restriction scratch"));
     double *scale = reinterpret_cast<double *>(pg->fx + pg->q);
-    double *part = scale + 2;
+    double *part = scale + 4;
     VGA_CUDA(cudaMemsetAsync(pg->fx, 0, sizeof(unsigned long long) * (size_t)pg->q, st));
     const unsigned Gs = (unsigned)std::min<int64_t>(kSumBlocks, grid_for(pg->n, kThreads));
-    const unsigned G = (unsigned)std::min<int64_t>((pg->n + kSeg - 1) / kSeg, 152 * 8);
+    int dev = 0, sms = 0;
+    VGA_CUDA(cudaGetDevice(&dev));
+    VGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // one resident wave of segment-striding blocks
+    const unsigned G = (unsigned)std::min<int64_t>((pg->n + kSeg - 1) / kSeg, (int64_t)sms * kRestrictBlocksPerSm);
     if (s->precision() == P_COMP) {
         k_abs_sum<P_COMP><<<Gs, kThreads, 0, st>>>(pg->n, s->comp(comp), s->lcomp(comp), part);
         k_fx_scale<<<1, kThreads, 0, st>>>(part, (int32_t)Gs, scale);
