@@ -46,7 +46,8 @@ struct BatchArgs {
     unsigned *bar;  // [0] arrivals, [1] generation
     int32_t *err;
     StateIO io[2];  // a pass whose input is state buffer k reads io[k] (kept as kernel parameters)
-    SparseState ss;  // the sparse fused pass (stencil.cuh MODE 3) of the SPARSE instantiations
+    SparseState ss;    // the sparse fused pass of the SPARSE instantiations (compact state, rank list)
+    int64_t n_active;  // marked nodes (ranks of the compact state)
 };
 
 // One fused pass over the whole batch, kBatchGroup consecutive nodes per thread (table_vec).
@@ -72,8 +73,35 @@ __device__ __forceinline__ void batch_fused_pass(const BatchArgs &a, const State
         __syncwarp();
         if ((threadIdx.x & 31) == 0) wp[w] = k >= 0 ? a.inst[k].p : StepParams{};
         __syncwarp();
-        if (SPARSE) table_vec<3, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, wp[w], io, PassRecord{}, a.ss);
+        if (SPARSE) table_vec<4, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, wp[w], io, PassRecord{}, a.ss);
         else table_vec<1, W_UNIT, TR, PREC, TF, KG>(i0, end, a.tb, BlockTable{}, wp[w], io);
+    }
+}
+
+// Second half of a sparse fused pass, after a grid barrier: the marked nodes in rank order, each with
+// its instance's parameters, MB, SOM, FOM, CO2 from the compact state (updated in place) and its DOM
+// as the first half (MODE 4) stored it; stores the DOM as the dense fused pass does.  The DOM and
+// the compact state were written inside this launch, so they are read with coherent loads.
+template <int TR, int PREC>
+__device__ __forceinline__ void batch_transform_marked(const BatchArgs &a, const StateIO &io) {
+    const SparseState &ss = a.ss;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < a.n_active; r += stride) {
+        const uint32_t i = __ldg(ss.list + r);
+        const StepParams p = a.inst[__ldg(a.tile_inst + i / kTile)].p;
+        V x2;
+        x2.h = io.out[1][i];
+        x2.l = PREC == P_COMP ? res_decode(io.lout[1][i], x2.h) : 0.0f;
+        V v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[q].h = ss.h[q][r];
+            v[q].l = PREC == P_COMP ? res_decode(ss.l[q][r], v[q].h) : 0.0f;
+        }
+        transform_n<TR, PREC>(v[0], x2, v[1], v[2], v[3], p);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) vstore<PREC>(ss.h[q], ss.l[q], r, v[q]);
+        vstore<PREC>(io.out[1], io.lout[1], i, x2);
     }
 }
 
@@ -81,7 +109,7 @@ __device__ __forceinline__ void batch_fused_pass(const BatchArgs &a, const State
 // first and the last pass of a call); without the code of the other two kinds it needs fewer
 // registers, so more blocks are resident.
 template <int TR, int PREC, int TF, bool FUSED_ONLY, bool SPARSE>
-__global__ void __launch_bounds__(kTile, SPARSE ? 4 : 1) k_batch(BatchArgs a, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
+__global__ void __launch_bounds__(kTile, SPARSE ? 5 : 1) k_batch(BatchArgs a, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
     for (int32_t pass = pass0; pass < pass1; ++pass) {
         // transform / fused / diffuse
         const int kind = FUSED_ONLY ? 1 : ((pass == 0) ? 0 : (pass == npass - 1 ? 2 : 1));
@@ -93,6 +121,11 @@ __global__ void __launch_bounds__(kTile, SPARSE ? 4 : 1) k_batch(BatchArgs a, in
             // same number of iterations (the warp-wide shuffles need all lanes).
             if (bi == 0) batch_fused_pass<TR, PREC, TF, SPARSE>(a, a.io[0]);
             else batch_fused_pass<TR, PREC, TF, SPARSE>(a, a.io[1]);
+            if constexpr (SPARSE) {
+                if (!grid_barrier(a.bar, a.err)) return;
+                if (bi == 0) batch_transform_marked<TR, PREC>(a, a.io[0]);
+                else batch_transform_marked<TR, PREC>(a, a.io[1]);
+            }
             if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err)) return;
             continue;
         }
@@ -285,6 +318,7 @@ vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npas
     a.bar = b->bar;
     a.err = b->err;
     a.ss = activity_state(b->act);
+    a.n_active = b->act.n_active;
     for (int k = 0; k < 2; ++k) {
         for (int c = 0; c < 5; ++c) {
             a.io[k].in[c] = b->h[k] + c * b->npad;
