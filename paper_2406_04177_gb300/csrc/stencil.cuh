@@ -442,14 +442,11 @@ __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const Step
 // previous lane's last node and the +x neighbour of the last node the next lane's first node.
 // Arithmetic and slot order per node are those of table_node, so the results are the same bits.
 // Rows and tables start on 16-byte boundaries (row strides are multiples of 64 values).  REC (fused
-// passes only): also writes the pass record of the discrete adjoint.  MODE 3 is the sparse fused
-// pass: the DOM of every node is diffused and rounded as in MODE 1 and stored as MODE 1 stores a
-// DOM that the (identity) transformation left unchanged; then the warp's nodes whose bit in the
-// activity mask is set are dealt out one per lane (their rounded DOM by shuffles), and each such
-// lane transforms its node with MB, SOM, FOM and CO2 from the compact state (updated in place),
-// storing them there and the DOM as MODE 1 does.  MODE 4 is the first half of the two-kernel sparse
-// pass: MODE 3 without the deal, a marked node's DOM stored as the rounded pair itself (the second
-// half, k_transform_compact, reads it back exactly as MODE 1 holds it in registers).  Must be
+// passes only): also writes the pass record of the discrete adjoint.  MODE 4 is the first half of
+// the sparse fused pass: the DOM of every node is diffused and rounded as in MODE 1; a node whose
+// bit in the activity mask is clear has its DOM stored as MODE 1 stores a DOM that the (identity)
+// transformation left unchanged, a marked node the rounded pair itself (the second half, over the
+// marked nodes in rank order, reads it back exactly as MODE 1 holds it in registers).  Must be
 // called by all 32 lanes of a warp.
 template <int MODE, int WM, int TR, int PREC, int TF, int K, bool REC = false>
 __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTable &tb, const BlockTable &bt,
@@ -461,8 +458,8 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
     V x2[K];
     if (full) group_load<WM, PREC, TF, K, true>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
     else group_load<WM, PREC, TF, K, false>(i0, n, tb, bt, io, ty, zm, zp, bn, x2);
-    uint32_t act_bits = 0u;  // MODE 3: activity bits of the group
-    if ((MODE == 3 || MODE == 4) && i0 < n) act_bits = (__ldg(ss.mask + (i0 >> 5)) >> (i0 & 31)) & ((1u << K) - 1u);
+    uint32_t act_bits = 0u;  // MODE 4: activity bits of the group
+    if (MODE == 4 && i0 < n) act_bits = (__ldg(ss.mask + (i0 >> 5)) >> (i0 & 31)) & ((1u << K) - 1u);
     float y[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) y[k] = x2[k].h;
@@ -480,7 +477,7 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
         zv[k] = zm[k] ? __ldg(Y2 + (i0 + k - zm[k])) : 0.0f;
         zw[k] = zp[k] ? __ldg(Y2 + (i0 + k + zp[k])) : 0.0f;
     }
-    if (i0 >= n && MODE != 3) return;  // MODE 3 keeps every lane for the warp-wide deal below
+    if (i0 >= n) return;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float acc = 0.0f;
@@ -523,61 +520,6 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
                     io.out[1][i0 + k] = h[k];
                     if (PREC == P_COMP) io.lout[1][i0 + k] = q[k];
                 }
-        }
-        return;
-    }
-    if (MODE == 3) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) vround<PREC>(x2[k]);
-        if (full) vstore_k<PREC, K, true>(io.out[1], io.lout[1], i0, n, x2);
-        else vstore_k<PREC, K, false>(io.out[1], io.lout[1], i0, n, x2);
-        // the warp's active nodes, one per lane: pair m = (source lane, slot k), k-major
-        unsigned am[K];
-        int cnt[K], total = 0;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            am[k] = __ballot_sync(0xffffffffu, (act_bits >> k) & 1u);
-            cnt[k] = __popc(am[k]);
-            total += cnt[k];
-        }
-        if (total == 0) return;  // warp-uniform
-        __syncwarp();            // the DOM stores above come before the transformation's stores
-        for (int base = 0; base < total; base += 32) {
-            const int m = base + lane;
-            int k = 0, r = m;
-#pragma unroll
-            for (int kk = 0; kk < K - 1; ++kk)
-                if (k == kk && r >= cnt[kk]) {
-                    r -= cnt[kk];
-                    k = kk + 1;
-                }
-            unsigned mk = am[0];
-#pragma unroll
-            for (int kk = 1; kk < K; ++kk)
-                if (k == kk) mk = am[kk];
-            const int src = m < total ? (int)__fns(mk, 0u, r + 1) : lane;
-            V v2 = {0.0f, 0.0f};
-#pragma unroll
-            for (int kk = 0; kk < K; ++kk) {
-                const float hh = __shfl_sync(0xffffffffu, x2[kk].h, src);
-                const float ll = __shfl_sync(0xffffffffu, x2[kk].l, src);
-                if (k == kk) v2 = V{hh, ll};
-            }
-            if (m < total) {
-                const uint32_t i = i0 + (uint32_t)(K * (src - lane) + k);
-                const uint32_t w = i >> 5;
-                const uint32_t r = __ldg(ss.prefix + w) + __popc(__ldg(ss.mask + w) & ((1u << (i & 31)) - 1u));
-                V v[4];  // MB, SOM, FOM, CO2 (written by this lane in earlier passes of the call)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    v[q].h = ss.h[q][r];
-                    v[q].l = PREC == P_COMP ? res_decode(ss.l[q][r], v[q].h) : 0.0f;
-                }
-                transform_n<TR, PREC>(v[0], v2, v[1], v[2], v[3], p);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) vstore<PREC>(ss.h[q], ss.l[q], r, v[q]);
-                vstore<PREC>(io.out[1], io.lout[1], i, v2);
-            }
         }
         return;
     }

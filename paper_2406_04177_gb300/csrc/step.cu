@@ -294,7 +294,7 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 // conductances (5).
 template <int MODE, int WM>
 constexpr int tablev_min_blocks() {
-    return MODE == 4 ? (WM == W_UNIT ? 6 : 5) : (MODE == 3 ? 5 : 4);
+    return MODE == 4 ? (WM == W_UNIT ? 6 : 5) : 4;
 }
 
 // K consecutive nodes per thread (table_vec); n < 2^31, so K * thread index fits 32 bits.

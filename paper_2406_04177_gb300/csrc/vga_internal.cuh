@@ -234,7 +234,7 @@ struct vga_sim {
     bool mx_graph_failed = false;  // graph construction failed once: host-driven loop from then on
     void *mx_graph = nullptr;      // cached graphs of the mixed solve (pcg.cu)
     int64_t graph_launches = 0;    // CUDA graph launches of the mixed solve
-    // Sparse fused pass (stencil.cuh MODE 3): activity mask and compact state
+    // Sparse fused pass (stencil.cuh MODE 4 and the marked-node half): activity mask and compact state
     vga::Activity act;
     bool activity_skip = true;     // use it (vga_sim_set_activity_skip)
     bool sparse_call = false;      // the fused passes of the running step call are sparse
