@@ -515,7 +515,8 @@ __global__ void __launch_bounds__(kThreads) k_mx_res(int64_t n, NbrTable tb, FF 
                                                      double *__restrict__ part, MxScalars *sc) {
     if (!FIRST && sc->done) return;
     if (FIRST && blockIdx.x == 0 && threadIdx.x == 0) sc->fresh = 1;
-    double rr = 0.0, bb = 0.0;
+    FF rr = {0.0f, 0.0f};  // |r|^2 per thread in float-float (no FP64 arithmetic per node)
+    double bb = 0.0;       // |b|^2, once per solve
     float rz = 0.0f;
     const int64_t ntile = (n + kThreads - 1) / kThreads;
     const float *__restrict__ sh = FIRST ? v.bh : v.xh;  // FIRST: x = b, neighbours read from b
@@ -546,7 +547,9 @@ __global__ void __launch_bounds__(kThreads) k_mx_res(int64_t n, NbrTable tb, FF 
             v.r[i] = r32;
             v.p[i] = __fmul_rn(ti, r32);
             v.d[i] = 0.0f;
-            rr = fma((double)r32, (double)r32, rr);
+            const float q = __fmul_rn(r32, r32);
+            const FF t = two_sum(rr.h, q);
+            rr = {t.h, __fadd_rn(rr.l, __fadd_rn(t.l, __fmaf_rn(r32, r32, -q)))};
             if (FIRST) {
                 const double b = (double)bi.h + (double)bi.l;
                 bb = fma(b, b, bb);
@@ -554,7 +557,7 @@ __global__ void __launch_bounds__(kThreads) k_mx_res(int64_t n, NbrTable tb, FF 
             rz = __fmaf_rn(r32, __fmul_rn(ti, r32), rz);
         }
     }
-    double acc[3] = {rr, bb, (double)rz};
+    double acc[3] = {(double)rr.h + (double)rr.l, bb, (double)rz};
     __shared__ double out[3];
     block_sum_store<3>(acc, out);
     if (threadIdx.x < 3) part[(int64_t)blockIdx.x * 3 + threadIdx.x] = out[threadIdx.x];
