@@ -69,6 +69,35 @@ def test_restriction(vga, oracle_lib):
         assert np.allclose(out.cpu().numpy(), ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("labels", ["blocks", "random"])
+def test_restriction_signed_tiny_and_zero_values(vga, oracle_lib, labels):
+    """The fixed-point restriction on values of both signs spread over 46 decades (down into the FP32
+    subnormal range, plus exact zeros), with block labels (runs of several nodes) and random labels
+    (runs of one).  Every node's pair is rounded to a multiple of the unit u = 2^(e - 61), sum |m|
+    < 2^e (e within one binade of the FP64 bound, as the device bound is an FP32 sum), so a
+    primitive's sum is within (its node count) x 2u of the exact sum, plus the FP64 rounding of the
+    oracle's own sum."""
+    torch = _torch()
+    img, og, g, lab, q, cg, pg = _case(vga, oracle_lib, labels=labels)
+    rng = np.random.default_rng(11)
+    n = og.n
+    X = np.zeros((5, n))
+    X[1] = rng.choice([-1.0, 1.0], n) * 10.0 ** rng.uniform(-44.0, 2.0, n)
+    X[1][rng.random(n) < 0.1] = 0.0
+    sim = vga.Sim(g, synth.paper_params())
+    sim.set_masses(X)
+    m = sim.get_masses()[1]  # the stored pairs, h + l, exactly in FP64
+    out = torch.empty(q, dtype=torch.float64, device="cuda")
+    pg.restrict(sim, 1, out)
+    ref = opn.restrict(lab, q, m)
+    S = np.abs(m).sum()
+    unit = 2.0 ** (np.floor(np.log2(S)) + 2 - 61)  # the larger of the two possible units
+    cnt = np.bincount(lab, minlength=q)
+    absum = np.bincount(lab, weights=np.abs(m), minlength=q)
+    err = np.abs(out.cpu().numpy() - ref)
+    assert np.all(err <= 2 * cnt * unit + 1e-13 * absum), float((err - 2 * cnt * unit).max())
+
+
 def test_scheme3_bit_exact_and_scheme4(vga, oracle_lib):
     torch = _torch()
     img, og, g, lab, q, cg, pg = _case(vga, oracle_lib)
