@@ -69,6 +69,10 @@ def test_explicit_sampled_nodes_512(vga, oracle_lib, full):
             assert abs(got[c, c0] - ref[c]) <= 1e-6 * scale, (int(c0), c, got[c, c0], ref[c])
     tot = sim.totals()
     assert abs(tot.sum() - X0.sum()) <= 1e-7 * X0.sum()
+    # the totals (float-float per thread over about 80 nodes each at this size, FP64 across
+    # threads) against the FP64 sum of the state as stored
+    exact = np.array([np.sum(got[c], dtype=np.float64) for c in range(5)])
+    assert np.allclose(tot, exact, rtol=1e-12, atol=0), (tot, exact)
 
 
 def test_implicit_properties_512(vga, full):
