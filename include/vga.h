@@ -278,9 +278,9 @@ vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t chunk);
  * transformation is the identity, and it stays so while stepping (no flux can make them nonzero).
  * The first step after a state upload (vga_sim_set_masses, vga_sim_set_state_f32,
  * vga_sim_load_state) marks the other nodes in a bit mask (one extra pass, one synchronisation); a
- * fused pass then diffuses the DOM of every node, transforms only the marked nodes (dealt out one
- * per lane within each warp), and leaves the MB, SOM, FOM and CO2 of the others unread and
- * unwritten.  Results are bit-identical with the mask off (also a node whose values are negative
+ * fused pass then diffuses the DOM of every node, transforms only the marked nodes (a second kernel
+ * over them in rank order, their MB, SOM, FOM and CO2 held in a compact rank-ordered copy during the
+ * call), and leaves the MB, SOM, FOM and CO2 of the others unread and unwritten.  Results are bit-identical with the mask off (also a node whose values are negative
  * zeros is marked).  on = 0 transforms every node every pass. */
 vga_status vga_sim_set_activity_skip(vga_sim *s, int32_t on);
 
