@@ -494,9 +494,13 @@ vga_status vga_pngm_free(vga_pngm *pg);
  * is a fixed 160 KiB array in the library's device memory (present on every GPU that loads the
  * library, until the process exits), which limits n to 33,554,432 nodes; larger n returns
  * VGA_ERR_INVALID_ARG.  The first call on a device looks up that array's address (with the device
- * current), so make that first call before any stream capture.  All calls share the array: calls
- * that overlap on the GPU race, so serialise them.  Errors: VGA_ERR_INVALID_ARG (NULL pointers,
- * n < 0, row_stride < n, n over the limit), VGA_ERR_CUDA. */
+ * current), so make that first call before any stream capture.  The address is kept per device
+ * ordinal for the rest of the process: it belongs to the device's primary context (the one the CUDA
+ * runtime uses), so it does not survive cudaDeviceReset and is wrong under another context made
+ * current through the driver API.  All calls share the array: calls that overlap on the GPU race,
+ * so serialise them.  The library cannot check the caller's buffers: values (and residuals) must
+ * hold 4*row_stride + n elements and totals 5.  Errors: VGA_ERR_INVALID_ARG (NULL pointers, n < 0,
+ * row_stride < n, n over the limit), VGA_ERR_CUDA. */
 vga_status vga_state_totals_noalloc(const float *values, const uint16_t *residuals, int64_t n,
                                     int64_t row_stride, double *totals, void *stream);
 

@@ -453,9 +453,26 @@ def vga_sim_free(s):
 
 def vga_state_totals_noalloc(values, residuals, n: int, row_stride: int, totals, stream=None):
     """values / residuals / totals are CUDA tensors (float32; 16-bit residual bits or None;
-    float64 with 5 entries); the call allocates nothing."""
+    float64 with at least 5 entries), contiguous; compartment c occupies
+    [c * row_stride, c * row_stride + n) of values (and residuals).  The call allocates nothing.
+    Sizes and layout are checked here, before any device access: the kernel itself has no bounds
+    to check against."""
     import torch
 
+    n, row_stride = int(n), int(row_stride)
+    if n < 0 or row_stride < n:
+        raise ValueError(f"need 0 <= n <= row_stride (n = {n}, row_stride = {row_stride})")
+    need = 4 * row_stride + n if n > 0 else 0
+    for name, t in (("values", values), ("residuals", residuals), ("totals", totals)):
+        if t is None:
+            continue
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        want = 5 if name == "totals" else need
+        if t.numel() < want:
+            raise ValueError(f"{name} holds {t.numel()} elements, the call reads or writes {want}")
     if not (isinstance(values, torch.Tensor) and values.is_cuda and values.dtype == torch.float32):
         raise TypeError("values must be a CUDA float32 tensor")
     if residuals is not None and not (isinstance(residuals, torch.Tensor) and residuals.is_cuda

@@ -391,6 +391,7 @@ struct MxScalars {
     uint32_t ticket_a, ticket_b;  // arrival counters of the last-block reductions (0 between launches)
     int32_t fresh;                // set by the first residual pass: the next k_mx_scal_out starts a solve
     int32_t guard;                // inner iterations of this solve (a bound on the device-side loops)
+    float scale, unscale;         // powers of two: the solve runs on b * scale; x leaves as x * unscale
 };
 
 // Device-side loops (the solve as one CUDA graph): the kernels that decide whether a loop goes on
@@ -563,16 +564,57 @@ __global__ void __launch_bounds__(kThreads) k_mx_res(int64_t n, NbrTable tb, FF 
     if (threadIdx.x < 3) part[(int64_t)blockIdx.x * 3 + threadIdx.x] = out[threadIdx.x];
 }
 
-// b = the stored DOM after the transformation: FP32 value and its residual as hi and lo.
+// Scale of the solve.  The system (I + c L) x = b is linear, so it may be solved for b * 2^-e and
+// the solution multiplied by 2^e.  With 2^e the binade of max |b| every vector of the solve is at
+// most about 1 in magnitude, whatever unit the caller stores masses in: the FP32 squares of the
+// residual and the inner dot products stay far from underflow (they would vanish below |r| ~ 1e-19,
+// and with them the stop test and alpha).  Scaling by a power of two is exact, so the iterations and
+// the result are the same bits as an unscaled solve wherever that one neither underflows nor
+// overflows.  k_mx_bmax stores the maximum of each block, k_mx_bscale turns them into the scale.
+__global__ void __launch_bounds__(kThreads) k_mx_bmax(int64_t n, const float *__restrict__ y2,
+                                                      double *__restrict__ part) {
+    float m = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(__ldg(y2 + i)));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ float wm[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kThreads / 32; ++w) m = fmaxf(m, wm[w]);
+        part[blockIdx.x] = (double)m;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mx_bscale(const double *__restrict__ part, int count, MxScalars *sc) {
+    double m = 0.0;
+    for (int b = threadIdx.x; b < count; b += blockDim.x) m = fmax(m, part[b]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double wm[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, wm[w]);
+        int e = 0;
+        if (m > 0.0 && m <= 3.0e38) frexp(m, &e);  // m = f 2^e, f in [0.5, 1)
+        e = max(-120, min(120, e));
+        sc->scale = ldexpf(1.0f, -e);
+        sc->unscale = ldexpf(1.0f, e);
+    }
+}
+
+// b = the stored DOM after the transformation, times the scale: FP32 value and its residual as hi
+// and lo.
 template <int PREC>
 __global__ void __launch_bounds__(kThreads) k_mx_rhs(int64_t n, const float *__restrict__ y2,
                                                      const res_t *__restrict__ y2l, float *__restrict__ bh,
-                                                     float *__restrict__ bl) {
+                                                     float *__restrict__ bl, const MxScalars *__restrict__ sc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const float s = sc->scale;
     const float h = __ldg(y2 + i);
-    bh[i] = h;
-    bl[i] = (PREC == P_COMP) ? res_decode(__ldg(y2l + i), h) : 0.0f;
+    bh[i] = __fmul_rn(h, s);
+    bl[i] = (PREC == P_COMP) ? __fmul_rn(res_decode(__ldg(y2l + i), h), s) : 0.0f;
 }
 
 // Start of an outer iteration: the residual norms, the outer stop test, the next inner solve's
@@ -842,18 +884,19 @@ __global__ void __launch_bounds__(kThreads) k_mx_x(int64_t n, MxVecs v, const Mx
 // The solution as the new stored DOM: h = RN(xh + xl) and the exact remainder as residual.
 template <int PREC>
 __global__ void __launch_bounds__(kThreads) k_mx_out(int64_t n, MxVecs v, float *__restrict__ out,
-                                                     res_t *__restrict__ outl) {
+                                                     res_t *__restrict__ outl, const MxScalars *__restrict__ sc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const FF s = two_sum(v.xh[i], v.xl[i]);
+    const float u = sc->unscale;  // back to the caller's units (exact: a power of two)
+    const FF s = two_sum(__fmul_rn(v.xh[i], u), __fmul_rn(v.xl[i], u));
     out[i] = s.h;
     if (PREC == P_COMP) outl[i] = res_encode(s.l, s.h);
 }
 
 // ---- the mixed solve as one CUDA graph -------------------------------------------------------
 //
-//   k_mx_rhs -> k_mx_res<first> -> WHILE(outer) { k_mx_scal_out -> WHILE(inner) { k_mx_spmv ->
-//   k_mx_upd -> k_mx_p } -> k_mx_x -> k_mx_res } -> k_mx_out
+//   k_mx_bmax -> k_mx_bscale -> k_mx_rhs -> k_mx_res<first> -> WHILE(outer) { k_mx_scal_out ->
+//   WHILE(inner) { k_mx_spmv -> k_mx_upd -> k_mx_p } -> k_mx_x -> k_mx_res } -> k_mx_out
 //
 // k_mx_scal_out sets both conditions to "not done" at the start of every outer iteration and
 // k_mx_upd clears the inner one when the inner solve stops, so the host launches the graph and
@@ -925,7 +968,7 @@ cudaError_t mx_graph_build(vga_sim *s, const MxVecs &v, const NbrTable &tb, FF c
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return e;
     MxLoop loop = {0, 0, 1};
-    cudaGraphNode_t n_rhs, n_res0, n_outer, n_out, n_scal, n_inner, n_x, n_res, n_spmv, n_upd, n_p;
+    cudaGraphNode_t n_bm, n_bs, n_rhs, n_res0, n_outer, n_out, n_scal, n_inner, n_x, n_res, n_spmv, n_upd, n_p;
     cudaGraph_t body_o = nullptr, body_i = nullptr;
     const unsigned ge = grid_for(s->n, kThreads);
     const double rtol = s->params.cg_rtol;
@@ -937,10 +980,12 @@ cudaError_t mx_graph_build(vga_sim *s, const MxVecs &v, const NbrTable &tb, FF c
         if (e != cudaSuccess) goto fail; \
     } while (0)
     MX_TRY(cudaGraphConditionalHandleCreate(&loop.outer, g, 1u, cudaGraphCondAssignDefault));
-    MX_TRY(add_kernel(&n_rhs, g, nullptr, k_mx_rhs<PREC>, ge, s->n, s->comp(1), s->lcomp(1), v.bh, v.bl));
+    MX_TRY(add_kernel(&n_bm, g, nullptr, k_mx_bmax, G, s->n, s->comp(1), part_a));
+    MX_TRY(add_kernel(&n_bs, g, &n_bm, k_mx_bscale, 1u, part_a, G, sc));
+    MX_TRY(add_kernel(&n_rhs, g, &n_bs, k_mx_rhs<PREC>, ge, s->n, s->comp(1), s->lcomp(1), v.bh, v.bl, sc));
     MX_TRY(add_kernel(&n_res0, g, &n_rhs, k_mx_res<true, TF>, G, s->n, tb, cff, v, part_a, sc));
     MX_TRY(add_while(&n_outer, g, &n_res0, loop.outer, &body_o));
-    MX_TRY(add_kernel(&n_out, g, &n_outer, k_mx_out<PREC>, ge, s->n, v, s->spare(1), s->lspare(1)));
+    MX_TRY(add_kernel(&n_out, g, &n_outer, k_mx_out<PREC>, ge, s->n, v, s->spare(1), s->lspare(1), sc));
     MX_TRY(cudaGraphConditionalHandleCreate(&loop.inner, body_o, 0u, 0u));
     MX_TRY(add_kernel(&n_scal, body_o, nullptr, k_mx_scal_out, 1u, part_a, (int64_t)G, sc, rtol, maxit, loop));
     MX_TRY(add_while(&n_inner, body_o, &n_scal, loop.inner, &body_i));
@@ -1019,7 +1064,7 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
                 VGA_CUDA(cudaMemcpyAsync(h, sc, sizeof(MxScalars), cudaMemcpyDeviceToHost, st));
                 VGA_CUDA(cudaStreamSynchronize(st));
                 s->graph_launches += 1;
-                s->launches += 3 + 3 * (int64_t)h->outer + 3 * (int64_t)h->iters;  // kernels the graph ran
+                s->launches += 5 + 3 * (int64_t)h->outer + 3 * (int64_t)h->iters;  // kernels the graph ran
                 s->cur[1] ^= 1;
                 s->cg_iterations += h->iters;
                 s->cg_last_relres = h->relres;
@@ -1031,13 +1076,15 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
     // host-driven loop: the same kernels, the done flags polled every kBatch inner iterations
     const MxLoop noloop = {0, 0, 0};
     timing_begin(s, VGA_KERNEL_PCG_STENCIL);
-    k_mx_rhs<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->comp(1), s->lcomp(1), v.bh, v.bl);
+    k_mx_bmax<<<G, kThreads, 0, st>>>(s->n, s->comp(1), part_a);
+    k_mx_bscale<<<1, kThreads, 0, st>>>(part_a, G, sc);
+    k_mx_rhs<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, s->comp(1), s->lcomp(1), v.bh, v.bl, sc);
     if (tb.tz) k_mx_res<true, 1><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
     else k_mx_res<true, 0><<<G, kThreads, 0, st>>>(s->n, tb, cff, v, part_a, sc);
     timing_end(s);
     k_mx_scal_out<<<1, kThreads, 0, st>>>(part_a, G, sc, s->params.cg_rtol, s->params.cg_maxit, noloop);
     VGA_CHECK_LAUNCH();
-    s->launches += 3;
+    s->launches += 5;
     for (int guard = 0; guard < 100000; ++guard) {
         for (int k = 0; k < kBatch; ++k) {
             timing_begin(s, VGA_KERNEL_PCG_STENCIL);
@@ -1066,7 +1113,7 @@ vga_status solve_mixed(vga_sim *s, double *base, double *part_a, double *part_b,
             s->launches += 3;
         }
     }
-    k_mx_out<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, v, s->spare(1), s->lspare(1));
+    k_mx_out<PREC><<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, v, s->spare(1), s->lspare(1), sc);
     VGA_CHECK_LAUNCH();
     ++s->launches;
     s->cur[1] ^= 1;

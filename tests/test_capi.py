@@ -93,3 +93,30 @@ def test_no_cpu_fallback_when_library_missing(tmp_path):
             mod.load_library(str(tmp_path / "missing.so"))
     finally:
         importlib.reload(v)
+
+
+def test_noalloc_wrapper_rejects_short_or_strided_buffers():
+    """The Python wrapper of the allocation-free totals checks sizes and layout before any device
+    access (the kernel has no bounds of its own to check); no GPU is needed to see the rejections."""
+    import torch
+
+    import paper_2406_04177_gb300 as v
+
+    n, stride = 100, 120
+    ok_vals = torch.zeros(4 * stride + n, dtype=torch.float32)
+    ok_tot = torch.zeros(5, dtype=torch.float64)
+    with pytest.raises(ValueError, match="values holds"):
+        v.vga_state_totals_noalloc(torch.zeros(4 * stride + n - 1), None, n, stride, ok_tot)
+    with pytest.raises(ValueError, match="residuals holds"):
+        v.vga_state_totals_noalloc(ok_vals, torch.zeros(4 * stride, dtype=torch.int16), n, stride, ok_tot)
+    with pytest.raises(ValueError, match="totals holds"):
+        v.vga_state_totals_noalloc(ok_vals, None, n, stride, torch.zeros(4, dtype=torch.float64))
+    with pytest.raises(ValueError, match="contiguous"):
+        v.vga_state_totals_noalloc(torch.zeros(2 * (4 * stride + n))[::2], None, n, stride, ok_tot)
+    with pytest.raises(ValueError, match="row_stride"):
+        v.vga_state_totals_noalloc(ok_vals, None, n, n - 1, ok_tot)
+    with pytest.raises(ValueError, match="row_stride"):
+        v.vga_state_totals_noalloc(ok_vals, None, -1, stride, ok_tot)
+    # sizes right, but host tensors: refused before the library is called
+    with pytest.raises(TypeError, match="CUDA"):
+        v.vga_state_totals_noalloc(ok_vals, None, n, stride, ok_tot)

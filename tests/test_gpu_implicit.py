@@ -139,3 +139,33 @@ def test_mixed_graph_loop_matches_host_loop(vga, oracle_lib):
     got = last.get_masses()
     for c in range(5):
         assert rel_l2(got[c], ref[c]) <= 1e-5, c
+
+
+@pytest.mark.parametrize("solver", [1, 2])
+def test_mixed_solve_does_not_depend_on_the_mass_unit(vga, oracle_lib, solver):
+    """The FP32 inner solve squares residuals; in a small mass unit (masses x 2^-40, e.g. grams
+    instead of micrograms) those squares would underflow and the solve would stop at once on a
+    zero residual norm.  The solve runs on a power-of-two scaled right-hand side, so with masses and
+    K_DOM both x 2^-40 every result is the unscaled one x 2^-40 bit for bit, with the same iteration
+    count and residual; with a factor 1e-12 (not a power of two) it still converges to rtol."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (32, 36, 28), 0.22, 13)
+    p = synth.paper_params(dt=10 * 0.9 / (6 * synth.D_DOM), scheme=1, cg_rtol=1e-8, cg_maxit=2000)
+    runs = {}
+    for name, f in (("one", 1.0), ("pow2", 2.0 ** -40), ("1e-12", 1e-12)):
+        q = dict(p)
+        q["K_dom"] = p["K_dom"] * f
+        sim = vga.Sim(g, q)
+        sim.set_solver(solver)
+        sim.set_masses(X0 * f)
+        sim.step(3)
+        runs[name] = (sim.get_masses(), sim.stats())
+        sim.close()
+    (x1, s1), (x2, s2), (x3, s3) = runs["one"], runs["pow2"], runs["1e-12"]
+    assert s1["cg_iterations"] > 0
+    assert np.array_equal(x2 * 2.0 ** 40, x1)
+    assert s2["cg_iterations"] == s1["cg_iterations"]
+    assert s2["cg_last_relres"] == s1["cg_last_relres"]
+    assert s3["cg_last_relres"] <= 1e-8
+    assert abs(s3["cg_iterations"] - s1["cg_iterations"]) <= 3
+    for c in range(5):
+        assert rel_l2(x3[c] / 1e-12, x1[c]) <= 1e-6, c

@@ -55,3 +55,57 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(vga):
     assert "no-allocation limit" in vga.vga_last_error()
     assert lib.vga_state_totals_noalloc(dummy, None, 10, 9, dummy, None) == -1
     assert lib.vga_state_totals_noalloc(None, None, 10, 10, dummy, None) == -1
+
+
+def _host_totals(vals, res, n, stride):
+    """Exact sums (math.fsum) of value + decoded BF16 residual per compartment."""
+    import math
+
+    out = []
+    for c in range(5):
+        v = vals[c * stride: c * stride + n].astype(np.float64)
+        if res is not None:
+            r = (res[c * stride: c * stride + n].astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+            v = np.concatenate([v, r])
+        out.append(math.fsum(v.tolist()))
+    return np.array(out)
+
+
+def test_noalloc_strided_empty_and_block_boundary(vga):
+    """Row strides above n with the padding filled with NaN (it must never be read), n = 0 (only the
+    final reduction runs: exact zeros), and n = 2 * 8192 + 1 (one node past a block boundary), each
+    twice in a row, against exact host sums of the same values."""
+    import torch
+
+    img = synth.pore_mask((48, 48, 48), 0.26, 5)
+    g = vga.Graph(img)
+    kept = synth.kept_mask_from_nodes(img.shape, g.export(labels=False, nbr=False)["voxel_of_node"])
+    sim = vga.Sim(g, synth.paper_params())
+    sim.set_masses(synth.initial_masses(kept, 5, with_organic_matter=True))
+    sim.step(20)
+    N = g.n
+    assert N > 2 * 8192 + 1
+    raw = sim.save_state()
+    vals = np.frombuffer(raw, dtype=np.float32, count=5 * N, offset=HEADER_BYTES).reshape(5, N)
+    res = np.frombuffer(raw, dtype=np.uint16, count=5 * N, offset=HEADER_BYTES + 20 * N).reshape(5, N)
+    stream = torch.cuda.current_stream()
+    totals = torch.empty((5,), dtype=torch.float64, device="cuda")
+    for n, pad in ((N, 37), (2 * 8192 + 1, 0), (2 * 8192 + 1, 91), (0, 0), (0, 5)):
+        stride = n + pad
+        hv = np.full((5, stride), np.nan, dtype=np.float32)
+        hr = np.full((5, stride), 0x7fc0, dtype=np.uint16)  # BF16 NaN in the padding
+        hv[:, :n] = vals[:, :n]
+        hr[:, :n] = res[:, :n]
+        hv, hr = hv.ravel(), hr.ravel()
+        want = _host_totals(hv, hr, n, stride)
+        d_vals = torch.from_numpy(hv.copy()).cuda()
+        d_res = torch.from_numpy(hr.view(np.int16).copy()).cuda()
+        for _ in range(2):
+            totals.fill_(np.nan)
+            vga.vga_state_totals_noalloc(d_vals, d_res, n, stride, totals, stream)
+            torch.cuda.synchronize()
+            got = totals.cpu().numpy()
+            if n == 0:
+                assert got.tolist() == [0.0] * 5
+            else:
+                assert np.allclose(got, want, rtol=1e-12, atol=0), (n, stride, got, want)
