@@ -90,7 +90,8 @@ def test_noalloc_strided_empty_and_block_boundary(vga):
     res = np.frombuffer(raw, dtype=np.uint16, count=5 * N, offset=HEADER_BYTES + 20 * N).reshape(5, N)
     stream = torch.cuda.current_stream()
     totals = torch.empty((5,), dtype=torch.float64, device="cuda")
-    for n, pad in ((N, 37), (2 * 8192 + 1, 0), (2 * 8192 + 1, 91), (0, 0), (0, 5)):
+    # (n = 0 still passes real buffers: the entry point rejects NULL pointers whatever n is)
+    for n, pad in ((N, 37), (2 * 8192 + 1, 0), (2 * 8192 + 1, 91), (0, 1), (0, 5)):
         stride = n + pad
         hv = np.full((5, stride), np.nan, dtype=np.float32)
         hr = np.full((5, stride), 0x7fc0, dtype=np.uint16)  # BF16 NaN in the padding
