@@ -200,7 +200,11 @@ vga_status vga_sim_load_state(vga_sim *s, const void *buf, int64_t bytes);
  * iterate). */
 vga_status vga_sim_step(vga_sim *s, int64_t n_steps);
 
-/* FP64 totals of the 5 compartments over all nodes, into totals[5] (host).  Deterministic. */
+/* FP64 totals of the 5 compartments over all nodes, into totals[5] (host).  Deterministic.  The
+ * same pass scans the state: a non-finite value returns VGA_ERR_NONFINITE (totals still written);
+ * a negative one counts in vga_sim_stats.negative_reports (within the stability bound the schemes
+ * keep every compartment >= 0 in exact arithmetic; at the bound itself rounding can leave a value
+ * a few ulps below zero, so a negative value is reported, not an error). */
 vga_status vga_sim_totals(vga_sim *s, double *totals);
 
 /* Waits for the simulation's stream; reports errors of previously enqueued work. */
@@ -213,6 +217,8 @@ typedef struct vga_sim_stats {
     int64_t kernel_launches;  /* kernels launched since creation (inside a graph: kernels it ran) */
     int64_t graph_launches;   /* implicit scheme: CUDA graph launches of the mixed solve */
     int64_t active_nodes;     /* nodes the sparse fused pass transforms (-1: no activity mask built) */
+    int64_t blocked_passes;   /* fused passes run temporally blocked (kernel variant 6) since creation */
+    int64_t negative_reports; /* vga_sim_totals calls whose scan of the state found a negative mass */
 } vga_sim_stats;
 vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out);
 
@@ -269,8 +275,15 @@ vga_status vga_loss_block_mass(vga_sim *s, int32_t block_side, uint32_t comp_mas
  *      vga_sim_set_wavefront).  Not used when dt_transform differs from dt (variant 2 runs);
  *   4  as 2 with two consecutive nodes per thread, the per-node streams moved as 8-byte vectors
  *      (FP32 values, table words) and 4-byte vectors (residuals);
- *   5  as 2 with four consecutive nodes per thread, 16-byte and 8-byte vectors.
- * For 4 and 5 `chunk` is ignored.  The default is 5 (the fastest at 512^3 on GB300). */
+ *   5  as 2 with four consecutive nodes per thread, 16-byte and 8-byte vectors;
+ *   6  as 5, except that the fused passes of a sparse step call (see vga_sim_set_activity_skip) run
+ *      temporally blocked: the DOM is permuted into tile order (tiles of 32 x 16 x 16 voxels) for the
+ *      call, and each launch advances every tile by up to 3 passes in shared memory, recomputing a
+ *      3-voxel halo (Scheme 1 applied repeatedly, Sec. II.B.3a; the transformation of the marked
+ *      nodes of Sec. II.C between the diffusions).  Unit conductances and equal transformation and
+ *      diffusion steps only; otherwise, and when a tile's halo region holds more nodes or marked
+ *      nodes than its shared-memory capacity, the call runs as 5.
+ * For 4, 5 and 6 `chunk` is ignored.  The default is 5. */
 vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t chunk);
 
 /* Sparse fused pass of variant 5 (on by default).  Every flux of the transformation (Sec. II.C) is
@@ -339,6 +352,15 @@ vga_status vga_batch_set_launch(vga_batch *b, int32_t steps_per_launch, int32_t 
  * call after vga_batch_set_masses marks the nodes where the transformation can change the state;
  * the fused passes then transform only those.  Bit-identical with on = 0. */
 vga_status vga_batch_set_activity_skip(vga_batch *b, int32_t on);
+
+/* Test hook of the bounded waits (no counterpart in the paper).  The batched launches are
+ * cooperative and separate their passes by grid-wide barriers whose waits are bounded.  With
+ * skip_block >= 0, block skip_block of every launch of the batch returns before its first barrier
+ * arrival, so the other blocks' waits run out after spin_limit polls of 64 ns each (0: the default
+ * limit, 2^26 polls) and vga_batch_step returns VGA_ERR_TIMEOUT; the device error flag and the
+ * barrier words are reset then, and the state is undefined until the next vga_batch_set_masses.
+ * skip_block = -1 switches the hook off (spin_limit still applies).  Nothing faults, traps or hangs. */
+vga_status vga_batch_set_wait_test(vga_batch *b, int32_t skip_block, uint32_t spin_limit);
 
 typedef struct vga_batch_stats {
     int32_t instances;

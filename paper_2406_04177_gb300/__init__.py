@@ -80,7 +80,7 @@ class vga_batch_tune(C.Structure):
 class vga_sim_stats(C.Structure):
     _fields_ = [("steps_done", C.c_int64), ("cg_iterations", C.c_int64),
                 ("cg_last_relres", C.c_double), ("kernel_launches", C.c_int64), ("graph_launches", C.c_int64),
-                ("active_nodes", C.c_int64)]
+                ("active_nodes", C.c_int64), ("blocked_passes", C.c_int64), ("negative_reports", C.c_int64)]
 
 
 VGA_KERNEL_KINDS = 8
@@ -141,6 +141,7 @@ _SIGNATURES = {
     "vga_batch_autotune": [_P, _I32, _P],
     "vga_batch_free": [_P],
     "vga_state_totals_noalloc": [_P, _P, _I64, _I64, _P, _P],
+    "vga_batch_set_wait_test": [_P, _I32, C.c_uint32],
     "vga_pngm_create": [_P, _P, _I32, _I32, _P, _P],
     "vga_pngm_get_info": [_P, _P],
     "vga_pngm_export": [_P, _P, _P, _P, _P, _P, _P, _P],
@@ -719,6 +720,11 @@ class Batch:
 
     def stats(self) -> dict:
         return vga_batch_get_stats(self.handle)
+
+    def set_wait_test(self, skip_block: int, spin_limit: int = 0):
+        """Bounded-wait test hook (vga_batch_set_wait_test); skip_block = -1 switches it off."""
+        _check(load_library().vga_batch_set_wait_test(self.handle, int(skip_block), int(spin_limit)),
+               "vga_batch_set_wait_test")
 
     def autotune(self, trial_steps: int = 50) -> dict:
         return vga_batch_autotune(self.handle, trial_steps)

@@ -17,7 +17,7 @@ struct Candidate {
     int variant, cap, depth, ctas;  // depth, ctas: wavefront passes per block and CTAs per SM
 };
 
-constexpr Candidate kCandidates[] = {{2, 1024, 0, 0}, {4, 1024, 0, 0}, {5, 1024, 0, 0}, {1, 1024, 0, 0}, {1, 512, 0, 0},  {1, 2048, 0, 0},
+constexpr Candidate kCandidates[] = {{2, 1024, 0, 0}, {4, 1024, 0, 0}, {5, 1024, 0, 0}, {6, 1024, 0, 0}, {1, 1024, 0, 0}, {1, 512, 0, 0},  {1, 2048, 0, 0},
                                      {0, 1024, 0, 0}, {0, 512, 0, 0},  {0, 2048, 0, 0}, {3, 1024, 2, 0},
                                      {3, 512, 4, 0},  {3, 256, 4, 0}};
 
@@ -57,8 +57,8 @@ using namespace vga;
 
 extern "C" vga_status vga_sim_set_kernel(vga_sim *s, int32_t variant, int32_t chunk) {
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
-    if (variant < 0 || variant > 5 || chunk < 32 || chunk > 8192 || (chunk & 31))
-        return fail(VGA_ERR_INVALID_ARG, "variant must lie in [0, 5] and chunk be a multiple of 32 in [32, 8192]");
+    if (variant < 0 || variant > 6 || chunk < 32 || chunk > 8192 || (chunk & 31))
+        return fail(VGA_ERR_INVALID_ARG, "variant must lie in [0, 6] and chunk be a multiple of 32 in [32, 8192]");
     if (variant == 3) {
         if (!wave_params_valid(chunk, 4, 0)) return fail(VGA_ERR_INVALID_ARG, "wavefront chunks are powers of two >= 256");
         VGA_TRY(select_kernel(s, 3, chunk, 4, 0));

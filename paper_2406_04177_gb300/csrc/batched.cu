@@ -48,6 +48,8 @@ struct BatchArgs {
     StateIO io[2];  // a pass whose input is state buffer k reads io[k] (kept as kernel parameters)
     SparseState ss;    // the sparse fused pass of the SPARSE instantiations (compact state, rank list)
     int64_t n_active;  // marked nodes (ranks of the compact state)
+    int32_t skip_block;   // test of the bounded waits: this block leaves before any barrier (-1: none)
+    uint32_t spin_limit;  // polls of a grid barrier before it gives up
 };
 
 // One fused pass over the whole batch, kBatchGroup consecutive nodes per thread (table_vec).
@@ -110,6 +112,7 @@ __device__ __forceinline__ void batch_transform_marked(const BatchArgs &a, const
 // registers, so more blocks are resident.
 template <int TR, int PREC, int TF, bool FUSED_ONLY, bool SPARSE>
 __global__ void __launch_bounds__(kTile, SPARSE ? 5 : 1) k_batch(BatchArgs a, int32_t pass0, int32_t pass1, int32_t npass, int32_t cur0) {
+    if ((int32_t)blockIdx.x == a.skip_block) return;  // the other blocks' barrier waits then run out
     for (int32_t pass = pass0; pass < pass1; ++pass) {
         // transform / fused / diffuse
         const int kind = FUSED_ONLY ? 1 : ((pass == 0) ? 0 : (pass == npass - 1 ? 2 : 1));
@@ -122,11 +125,11 @@ __global__ void __launch_bounds__(kTile, SPARSE ? 5 : 1) k_batch(BatchArgs a, in
             if (bi == 0) batch_fused_pass<TR, PREC, TF, SPARSE>(a, a.io[0]);
             else batch_fused_pass<TR, PREC, TF, SPARSE>(a, a.io[1]);
             if constexpr (SPARSE) {
-                if (!grid_barrier(a.bar, a.err)) return;
+                if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
                 if (bi == 0) batch_transform_marked<TR, PREC>(a, a.io[0]);
                 else batch_transform_marked<TR, PREC>(a, a.io[1]);
             }
-            if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err)) return;
+            if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err, a.spin_limit)) return;
             continue;
         }
         if constexpr (!FUSED_ONLY) {  // first (transform) and last (diffuse-only) pass of a call
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(kTile, SPARSE ? 5 : 1) k_batch(BatchArgs a, in
     #pragma unroll
                 for (int c = 0; c < 5; ++c) vstore<PREC>(a.h[bo] + c * a.npad, a.l[bo] + c * a.npad, i, x[c]);
             }
-            if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err)) return;
+            if (pass + 1 < pass1 && !grid_barrier(a.bar, a.err, a.spin_limit)) return;
         }
     }
 }
@@ -259,6 +262,8 @@ struct vga_batch {
     int64_t launches = 0, graph_replays = 0, steps_done = 0;
     Activity act;               // the sparse fused pass (as vga_sim_set_activity_skip)
     bool activity_skip = true;
+    int32_t wait_test_block = -1;  // vga_batch_set_wait_test
+    uint32_t wait_test_spin = 0;
 };
 
 namespace {
@@ -319,6 +324,8 @@ vga_status launch_batch(vga_batch *b, int32_t pass0, int32_t pass1, int32_t npas
     a.err = b->err;
     a.ss = activity_state(b->act);
     a.n_active = b->act.n_active;
+    a.skip_block = b->wait_test_block;
+    a.spin_limit = b->wait_test_spin ? b->wait_test_spin : kBarrierSpin;
     for (int k = 0; k < 2; ++k) {
         for (int c = 0; c < 5; ++c) {
             a.io[k].in[c] = b->h[k] + c * b->npad;
@@ -589,6 +596,15 @@ vga_status vga_batch_set_launch(vga_batch *b, int32_t steps_per_launch, int32_t 
 vga_status vga_batch_set_activity_skip(vga_batch *b, int32_t on) {
     if (!b) return fail(VGA_ERR_INVALID_ARG, "batch is NULL");
     b->activity_skip = on != 0;
+    return VGA_OK;
+}
+
+vga_status vga_batch_set_wait_test(vga_batch *b, int32_t skip_block, uint32_t spin_limit) {
+    if (!b) return fail(VGA_ERR_INVALID_ARG, "batch is NULL");
+    if (skip_block < -1) return fail(VGA_ERR_INVALID_ARG, "skip_block must be -1 or a block index");
+    b->wait_test_block = skip_block;
+    b->wait_test_spin = spin_limit;
+    drop_graphs(b);  // captured launches hold the old parameters
     return VGA_OK;
 }
 

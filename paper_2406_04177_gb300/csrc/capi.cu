@@ -557,6 +557,8 @@ vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out) {
     out->kernel_launches = s->launches;
     out->graph_launches = s->graph_launches;
     out->active_nodes = s->act.n_active;
+    out->blocked_passes = s->blocked_passes;
+    out->negative_reports = s->negative_reports;
     return VGA_OK;
 }
 
@@ -688,6 +690,7 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->loss_work);
     dfree(s->wave_dep);
     dfree(s->wave_order);
+    block_free(s);
     adjoint_free(s->adj);
     if (s->h_cg) cudaFreeHost(s->h_cg);
     free_chunks(&s->chunks);

@@ -11,9 +11,9 @@ namespace vga {
 constexpr uint32_t kBarrierSpin = 1u << 26;  // polls (64 ns sleeps) before a barrier gives up
 
 // Grid-wide barrier for a cooperative launch.  bar[0] counts arrivals, bar[1] is the generation
-// (both start at zero).  Bounded: on timeout (or an earlier error) it sets *err and returns false;
-// callers then stop.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *err) {
+// (both start at zero).  Bounded: after `limit` polls (or on an earlier error) it sets *err and
+// returns false; callers then stop.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *err, uint32_t limit = kBarrierSpin) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -33,7 +33,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int32_t *err) {
             } else {
                 uint32_t it = 0;
                 while (*vgen == gen) {
-                    if (*verr || ++it > kBarrierSpin) {
+                    if (*verr || ++it > limit) {
                         atomicExch(err, 2);
                         ok = 0;
                         break;

@@ -434,6 +434,63 @@ __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const Step
     }
 }
 
+// First half of the sparse fused pass (MODE 4, unit conductances, compensated state) for a full
+// group of four nodes, in packed pairs (0, 1) and (2, 3): the flux sum in slot order -x, +x, -y, +y,
+// -z, +z (an absent neighbour carries the node's own value, adding +0), Scheme 1's increment by
+// TwoSum, the rounding of vround, and the store of MODE 4 (a marked node's rounded pair itself, the
+// others renormalised as vstore).  Every lane does the scalar path's operations in its order, so the
+// results are the same bits.
+__device__ __forceinline__ void dom4_packed(uint32_t i0, const uint32_t (&ty)[4], const float (&y)[4], float yl,
+                                            float yr, const float (&ym)[4], const float (&yp)[4], const float (&zv)[4],
+                                            const float (&zw)[4], const V (&x2)[4], uint32_t act_bits,
+                                            const StepParams &p, const StateIO &io) {
+    float xm[4], xp[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        xm[k] = ((ty[k] >> 15) & 1u) ? (k == 0 ? yl : y[k > 0 ? k - 1 : 0]) : y[k];
+        xp[k] = (ty[k] >> 31) ? (k == 3 ? yr : y[k < 3 ? k + 1 : 0]) : y[k];
+    }
+    float hw[4];
+    uint32_t qw[2];
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+        const int a = 2 * h2, b = a + 1;
+        const float2 Y = make_float2(y[a], y[b]);
+        float2 acc = make_float2(0.0f, 0.0f);
+        acc = add2_rn(acc, sub2_rn(Y, make_float2(xm[a], xm[b])));
+        acc = add2_rn(acc, sub2_rn(Y, make_float2(xp[a], xp[b])));
+        acc = add2_rn(acc, sub2_rn(Y, make_float2(ym[a], ym[b])));
+        acc = add2_rn(acc, sub2_rn(Y, make_float2(yp[a], yp[b])));
+        acc = add2_rn(acc, sub2_rn(Y, make_float2(zv[a], zv[b])));
+        acc = add2_rn(acc, sub2_rn(Y, make_float2(zw[a], zw[b])));
+        // Scheme 1: -D dt sum_j (y_i - y_j), in scalar (see add2_rn: a packed product would be fused)
+        const float2 d = make_float2(__fmul_rn(-p.c, acc.x), __fmul_rn(-p.c, acc.y));
+        float2 H = Y, L = make_float2(x2[a].l, x2[b].l);
+        // vadd: TwoSum, the rounding error into the residual
+        float2 s = add2_rn(H, d);
+        const float2 bp = sub2_rn(s, H);
+        const float2 e = add2_rn(sub2_rn(H, sub2_rn(s, bp)), sub2_rn(d, bp));
+        L = add2_rn(L, e);
+        H = s;
+        // vround: as if stored and loaded
+        s = add2_rn(H, L);
+        const float2 r = add2_rn(sub2_rn(H, s), L);
+        const uint32_t rq = bf16x2_bits(r.x, r.y);
+        L = make_float2(__uint_as_float(rq << 16), __uint_as_float(rq & 0xffff0000u));
+        H = s;
+        // store: renormalised (unmarked) or the rounded pair itself (marked)
+        const float2 hn = add2_rn(H, L);
+        const float2 rn = add2_rn(sub2_rn(H, hn), L);
+        const uint32_t qn = bf16x2_bits(rn.x, rn.y);
+        const bool ma = (act_bits >> a) & 1u, mb = (act_bits >> b) & 1u;
+        hw[a] = ma ? H.x : hn.x;
+        hw[b] = mb ? H.y : hn.y;
+        qw[h2] = ((ma ? rq : qn) & 0xffffu) | ((mb ? rq : qn) & 0xffff0000u);
+    }
+    st_floats<4>(io.out[1] + i0, hw);
+    *reinterpret_cast<uint2 *>(io.lout[1] + i0) = make_uint2(qw[0], qw[1]);
+}
+
 // K consecutive nodes per thread (i0 a multiple of K, K = 2 or 4): table_node for nodes i0 ..
 // i0 + K - 1, the per-node streams (offset table, block ids, the five compartments) read and
 // written as 8- or 16-byte FP32 / table vectors and 4- or 8-byte residual vectors, so a warp moves
@@ -468,16 +525,24 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
     float yr = __shfl_down_sync(0xffffffffu, y[0], 1);    // node i0 + K
     if (lane == 0 && ((ty[0] >> 15) & 1u)) yl = __ldg(Y2 + (i0 - 1));
     if (lane == 31 && (ty[K - 1] >> 31)) yr = __ldg(Y2 + (i0 + K));
+    // an absent neighbour reads the node's own value: the scalar path below skips it, the packed
+    // path adds y - y = +0, which leaves a sum that starts at +0 unchanged (it is never -0)
     float ym[K], yp[K], zv[K], zw[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const uint32_t dym = ty[k] & 0x7fffu, dyp = (ty[k] >> 16) & 0x7fffu;
-        ym[k] = dym ? __ldg(Y2 + (i0 + k - dym)) : 0.0f;
-        yp[k] = dyp ? __ldg(Y2 + (i0 + k + dyp)) : 0.0f;
-        zv[k] = zm[k] ? __ldg(Y2 + (i0 + k - zm[k])) : 0.0f;
-        zw[k] = zp[k] ? __ldg(Y2 + (i0 + k + zp[k])) : 0.0f;
+        ym[k] = dym ? __ldg(Y2 + (i0 + k - dym)) : y[k];
+        yp[k] = dyp ? __ldg(Y2 + (i0 + k + dyp)) : y[k];
+        zv[k] = zm[k] ? __ldg(Y2 + (i0 + k - zm[k])) : y[k];
+        zw[k] = zp[k] ? __ldg(Y2 + (i0 + k + zp[k])) : y[k];
     }
     if (i0 >= n) return;
+    if constexpr (MODE == 4 && WM == W_UNIT && PREC == P_COMP && K == 4) {
+        if (full) {
+            dom4_packed(i0, ty, y, yl, yr, ym, yp, zv, zw, x2, act_bits, p, io);
+            return;
+        }
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float acc = 0.0f;

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "physics.cuh"
@@ -444,12 +445,17 @@ template <int PREC>
 // errors added in FP32), about 2^-48 relative for the tens of terms a thread takes; threads and
 // blocks are summed in FP64.  No FP64 arithmetic per node: the FP64 rate of this part is a small
 // fraction of its FP32 rate, and the FP64 form took 0.8 ms for 21 M nodes.
-__global__ void __launch_bounds__(kThreads) k_totals(int64_t n, StateIO io, double *__restrict__ partials) {
+// The same pass scans the state: flags bit 0 is set when a value is not finite, bit 1 when one is
+// negative (the schemes keep every compartment >= 0 within the stability bound).
+__global__ void __launch_bounds__(kThreads) k_totals(int64_t n, StateIO io, double *__restrict__ partials,
+                                                     int32_t *__restrict__ flags) {
     float sh[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, sl[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    uint32_t f = 0u;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
             const V v = vload<PREC>(io.in[c], io.lin[c], i);
+            f |= ((__float_as_uint(v.h) & 0x7f800000u) == 0x7f800000u ? 1u : 0u) | (v.h < 0.0f ? 2u : 0u);
             const float t = __fadd_rn(sh[c], v.h);
             const float bb = __fsub_rn(t, sh[c]);
             const float e = __fadd_rn(__fsub_rn(sh[c], __fsub_rn(t, bb)), __fsub_rn(v.h, bb));
@@ -457,6 +463,8 @@ __global__ void __launch_bounds__(kThreads) k_totals(int64_t n, StateIO io, doub
             sl[c] = __fadd_rn(sl[c], __fadd_rn(e, v.l));
         }
     }
+    f = __reduce_or_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0 && f) atomicOr(flags, (int32_t)f);
     double s[5];
 #pragma unroll
     for (int c = 0; c < 5; ++c) s[c] = (double)sh[c] + (double)sl[c];
@@ -634,7 +642,7 @@ vga_status launch_table(vga_sim *s, const StateIO &io, const NbrTable &tb, const
         launch_tablev<MODE, WM, PREC, 2>(s, io, tb, bt);
         return VGA_OK;
     }
-    if (s->kernel_variant == 5) {
+    if (s->kernel_variant == 5 || s->kernel_variant == 6) {  // 6: its unblocked passes are variant 5's
         launch_tablev<MODE, WM, PREC, 4>(s, io, tb, bt);
         return VGA_OK;
     }
@@ -840,6 +848,8 @@ vga_status activity_build(Activity *a, int64_t n, int64_t npad, const StateIO &c
         VGA_CHECK_LAUNCH();
     }
     a->valid = true;
+    static std::atomic<int64_t> next_build{0};  // unique over the process, so a freed mask never matches
+    a->builds = ++next_build;
     return VGA_OK;
 }
 
@@ -877,7 +887,8 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
         return VGA_OK;
     }
     // sparse fused passes: variant 5 on the neighbour-offset table (and the block table, if used)
-    bool sparse = s->activity_skip && s->kernel_variant == 5 && s->g->nx <= 32767 && n_steps > 1;
+    bool sparse = s->activity_skip && (s->kernel_variant == 5 || s->kernel_variant == 6) && s->g->nx <= 32767 &&
+                  n_steps > 1;
     if (sparse && s->wmode == W_BLOCK) {
         BlockTable bt;
         bool ok = false;
@@ -910,7 +921,9 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
             ++s->launches;
         }
         s->sparse_call = sparse;
-        for (int64_t k = 1; k < n_steps; ++k) {
+        bool blocked = false;  // variant 6: the fused passes as temporally blocked launches
+        if (sparse && s->kernel_variant == 6 && !sub) VGA_TRY(sim_block_fused(s, n_steps - 1, &blocked));
+        for (int64_t k = 1; k < n_steps && !blocked; ++k) {
             if (sub) s->sp.ntrans = sim_ticks_of_step(s, k0 + k);
             VGA_TRY(launch_stencil<1>(s, state_io(s)));
             for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
@@ -935,15 +948,25 @@ vga_status sim_totals(vga_sim *s, double *h_out) {
     const int nb = (int)std::min<int64_t>(kTotBlocks, (int64_t)grid_for(s->n, kThreads));
     StateIO io = state_io(s);
     timing_begin(s, VGA_KERNEL_TOTALS);
-    if (s->precision() == P_COMP) k_totals<P_COMP><<<nb, kThreads, 0, s->stream>>>(s->n, io, s->partials);
-    else k_totals<P_F32><<<nb, kThreads, 0, s->stream>>>(s->n, io, s->partials);
+    int32_t *flags = s->d_err + 1;  // state scan of the totals pass
+    if (s->precision() == P_COMP) k_totals<P_COMP><<<nb, kThreads, 0, s->stream>>>(s->n, io, s->partials, flags);
+    else k_totals<P_F32><<<nb, kThreads, 0, s->stream>>>(s->n, io, s->partials, flags);
     k_totals_final<<<1, kThreads, 0, s->stream>>>(s->partials, nb, s->d_totals);
     timing_end(s);
     VGA_CHECK_LAUNCH();
     s->launches += 2;
+    int32_t *h_flags = reinterpret_cast<int32_t *>(s->h_totals + 6);
     VGA_CUDA(cudaMemcpyAsync(s->h_totals, s->d_totals, 5 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    VGA_CUDA(cudaMemcpyAsync(h_flags, flags, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
     VGA_CUDA(cudaStreamSynchronize(s->stream));
     for (int c = 0; c < 5; ++c) h_out[c] = s->h_totals[c];
+    if (*h_flags) {
+        const int32_t fl = *h_flags;
+        VGA_CUDA(cudaMemsetAsync(flags, 0, sizeof(int32_t), s->stream));
+        VGA_CUDA(cudaStreamSynchronize(s->stream));
+        if (fl & 2) ++s->negative_reports;
+        if (fl & 1) return fail(VGA_ERR_NONFINITE, "the state holds a non-finite mass (found by the totals pass)");
+    }
     return VGA_OK;
 }
 
@@ -1103,7 +1126,7 @@ vga_status build_compact_z(int64_t n, int64_t cap, const uint32_t *tzm, const ui
 }
 
 bool stencil_variant_supported(int variant, int cap) {
-    return variant == 0 || variant == 2 || variant == 4 || variant == 5 || staged_cap_supported(cap);
+    return variant == 0 || variant == 2 || variant == 4 || variant == 5 || variant == 6 || staged_cap_supported(cap);
 }
 
 }  // namespace vga

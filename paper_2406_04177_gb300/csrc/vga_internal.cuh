@@ -134,6 +134,7 @@ struct Activity {
     int64_t cap = 0;
     int64_t n_active = -1;      // marked nodes (-1: not built)
     bool valid = false;         // built for the current state
+    int64_t builds = 0;         // id of the last build, unique in the process (consumers cache per build)
 };
 
 // Builds the mask, the prefix and the compact state for nodes [0, n) of the state `cur` (`spare`
@@ -262,6 +263,9 @@ struct vga_sim {
                                   // 3 table passes as an L2 wavefront (wave.cu), 4 / 5 table, two /
                                   // four nodes per thread
     int wave_chunk = 512, wave_depth = 4, wave_ctas = 0;  // wavefront chunk, passes per block, CTAs/SM
+    void *blk = nullptr;          // tile-order layout of the temporally blocked passes (block.cu)
+    int64_t blocked_passes = 0;   // fused passes run by it
+    int64_t negative_reports = 0;  // totals passes that found a negative mass
     int32_t *wave_dep = nullptr;      // per chunk: lowest and highest chunk its neighbours lie in; flags
     int32_t *wave_order = nullptr;    // skewed item order of one block of passes
     int wave_built_chunk = 0, wave_built_depth = 0, wave_built_lag = -1;
@@ -307,6 +311,10 @@ vga_status sim_transform_pass(vga_sim *s);  // Y = T(X) for every node, all comp
 int64_t sim_ticks_before(const vga_sim *s, int64_t k);  // transformations in the first k steps
 int sim_ticks_of_step(const vga_sim *s, int64_t k);      // transformations before diffusion step k
 vga_status sim_nbr_table(vga_sim *s, NbrTable *out);  // builds the table on first use
+// block.cu: P fused passes of a sparse step call as temporally blocked launches (variant 6); *done
+// is false (and nothing ran) when the graph, the conductances or the marked nodes do not allow it.
+vga_status sim_block_fused(vga_sim *s, int64_t P, bool *done);
+void block_free(vga_sim *s);
 // wave.cu: P fused passes as one wavefront launch (flips the buffers when P is odd)
 vga_status sim_wave_fused(vga_sim *s, int64_t P);
 bool wave_params_valid(int chunk, int depth, int ctas_per_sm);

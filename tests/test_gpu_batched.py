@@ -116,3 +116,34 @@ def test_batch_sparse_equals_dense(vga, oracle_lib, organic):
         sim.step(1)
         sim.step(7)
         assert np.array_equal(sim.get_masses(), outs[0][0][k])
+
+
+@pytest.mark.parametrize("skip", [0, 5])
+def test_barrier_wait_runs_out_and_batch_recovers(vga, oracle_lib, skip):
+    """Bounded waits: one block of every launch leaves before its first grid-barrier arrival, so the
+    others' waits run out after 4096 polls; the step returns VGA_ERR_TIMEOUT (no fault, no hang).
+    With the hook off, the same batch handle, given its masses again, runs bit-identical to a fresh
+    batch and matches the oracle."""
+    inst = _instances(oracle_lib, count=3, seed=47)
+    graphs = [vga.Graph(img) for img, _, _, _ in inst]
+    params = [p for _, _, _, p in inst]
+    b = vga.Batch(graphs, params)
+    fresh = vga.Batch(graphs, params)
+    for k, (_, _, X0, _) in enumerate(inst):
+        b.set_masses(k, X0)
+        fresh.set_masses(k, X0)
+    b.set_wait_test(skip, 4096)
+    with pytest.raises(vga.VgaError) as e:
+        b.step(20)
+    assert e.value.name == "VGA_ERR_TIMEOUT"
+    b.set_wait_test(-1, 0)
+    for k, (_, _, X0, _) in enumerate(inst):
+        b.set_masses(k, X0)
+    b.step(20)
+    fresh.step(20)
+    for k, (img, og, X0, p) in enumerate(inst):
+        got = b.get_masses(k)
+        assert np.array_equal(got, fresh.get_masses(k)), k
+        ref = oracle_lib.explicit_run(og.nbr, p, X0, 20)
+        for c in range(5):
+            assert rel_l2(got[c], ref[c]) <= 1e-5, (k, c)

@@ -251,7 +251,8 @@ def test_autotune_keeps_state(vga, oracle_lib):
     sim.step(3)
     before = sim.save_state()
     res = sim.autotune(4)
-    assert res["best"] is not None and len(res["entries"]) == 12
+    assert res["best"] is not None and len(res["entries"]) == 13
+    assert sorted({e["variant"] for e in res["entries"]}) == [0, 1, 2, 3, 4, 5, 6]
     assert all(e["ms_per_step"] > 0 for e in res["entries"])
     assert sim.save_state() == before
     with pytest.raises(vga.VgaError):
@@ -360,3 +361,124 @@ def test_activity_skip_bit_identical(vga, oracle_lib, block, transform, precisio
                                             | (np.signbit(X[1]) & (X[1] == 0))))
     assert ns == (marked(X0), marked(X1))
     assert 0 < ns[0] < g.n
+
+
+@pytest.mark.parametrize("shape,por,transform,precision,organic", [
+    ((40, 48, 37), 0.24, 0, 0, False),   # ragged in every axis (tiles of 32 x 16 x 16 cut at the borders)
+    ((64, 64, 64), 0.17, 0, 0, True),    # every DOM node also holds SOM and FOM: 5% of nodes marked
+    ((33, 20, 100), 0.3, 1, 0, False),   # asynchronous transformation, four tile columns in x
+    ((50, 17, 31), 0.2, 0, 1, False),    # plain FP32 state, one tile column narrower than a word
+])
+def test_blocked_passes_bit_identical(vga, oracle_lib, shape, por, transform, precision, organic):
+    """Variant 6 runs the fused passes of a sparse step call temporally blocked (3 passes per launch
+    over tiles with a 3-voxel halo in shared memory).  Its state is the bits of variant 5 after every
+    step count (1, 2, 3, 4 and 11 fused passes: every remainder of the 3-pass launches), after a
+    state upload that rebuilds the mask, and across a save/load; the blocked path really ran."""
+    img, og, g, X0 = _setup(vga, oracle_lib, shape, por, 31, organic=organic)
+    p = synth.paper_params(transform=transform)
+    p["state_precision"] = precision
+    X1 = X0.copy()
+    X1[0, np.random.default_rng(5).choice(g.n, 60, replace=False)] = 2e-4
+
+    def run(variant):
+        sim = vga.Sim(g, p)
+        sim.set_kernel(variant, 1024)
+        sim.set_masses(X0)
+        out = []
+        for k in (2, 3, 4, 5, 12):
+            sim.step(k)
+            out.append(sim.save_state())
+        sim.set_masses(X1)
+        sim.step(9)
+        out.append(sim.save_state())
+        sim.load_state(out[2])
+        sim.step(6)
+        out.append(sim.save_state())
+        st = sim.stats()
+        sim.close()
+        return out, st
+
+    ref, st5 = run(5)
+    got, st6 = run(6)
+    assert st5["blocked_passes"] == 0
+    assert st6["blocked_passes"] == (1 + 2 + 3 + 4 + 11) + 8 + 5
+    for k, (a, b) in enumerate(zip(ref, got)):
+        assert a == b, k
+    last = vga.Sim(g, p)
+    last.load_state(got[-1])
+    n_steps = 2 + 3 + 4 + 6
+    _assert_close(last.get_masses(), oracle_lib.explicit_run(og.nbr, p, X0, n_steps, transform=transform),
+                  tol=TOL_L2 if precision == 0 else 1e-4)
+
+
+def test_blocked_passes_fall_back_when_marked_nodes_overflow(vga, oracle_lib):
+    """With biomass in most nodes the marked nodes of a tile's region exceed its shared-memory list:
+    the call runs unblocked (variant 5's passes) and the state is still the same bits."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (32, 32, 64), 0.3, 8)
+    X0[0] = np.where(np.arange(g.n) % 2 == 0, 1e-5, 0.0)
+    p = synth.paper_params()
+    outs = []
+    for variant in (5, 6):
+        sim = vga.Sim(g, p)
+        sim.set_kernel(variant, 1024)
+        sim.set_masses(X0)
+        sim.step(10)
+        outs.append(sim.save_state())
+        assert sim.stats()["blocked_passes"] == 0
+        sim.close()
+    assert outs[0] == outs[1]
+
+
+def test_blocked_c1_against_oracle(vga, oracle_lib):
+    """Variant 6 at the 64^3 reference configuration (1000 steps) against the FP64 oracle, with the
+    per-node relative error of the marked nodes checked on its own (their DOM error would be diluted
+    about 100x in the relative L2 over all nodes)."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (64, 64, 64), 0.17, 1)
+    p = synth.paper_params()
+    sim = vga.Sim(g, p)
+    sim.set_kernel(6, 1024)
+    sim.set_masses(X0)
+    sim.step(1000)
+    assert sim.stats()["blocked_passes"] == 999
+    got = sim.get_masses()
+    ref = oracle_lib.explicit_run(og.nbr, p, X0, 1000)
+    _assert_close(got, ref)
+    marked = (X0[[0, 2, 3, 4]] != 0).any(axis=0)
+    assert marked.sum() > 10
+    for c in range(5):
+        r, m = ref[c, marked], got[c, marked]
+        big = np.abs(r) > 1e-6 * np.abs(ref[c]).max()
+        if big.any():
+            assert np.max(np.abs(m[big] - r[big]) / np.abs(r[big])) <= 1e-5, c
+    assert abs(sim.totals().sum() - X0.sum()) <= TOL_DRIFT * X0.sum()
+
+
+def test_totals_scan_reports_nonfinite_and_negative(vga):
+    """The totals pass scans the state: a negative mass is counted in the stats, a non-finite one
+    (uploaded from device memory, which the host cannot check) makes vga_sim_totals return
+    VGA_ERR_NONFINITE; the flags are cleared, so a clean state passes again."""
+    import torch
+
+    g = vga.Graph(np.zeros((8, 8, 8), dtype=np.uint8))
+    sim = vga.Sim(g, synth.paper_params())
+    X = np.zeros((5, g.n))
+    X[1] = 1e-5
+    X[0, ::7] = 2e-6
+    sim.set_masses(X)
+    sim.totals()
+    assert sim.stats()["negative_reports"] == 0
+    Xn = X.copy()
+    Xn[3, 7] = -1e-9
+    sim.set_masses(Xn)
+    sim.totals()
+    assert sim.stats()["negative_reports"] == 1
+    Xd = torch.from_numpy(X).cuda()
+    Xd[1, 3] = float("nan")
+    sim.set_masses(Xd)
+    with pytest.raises(vga.VgaError) as e:
+        sim.totals()
+    assert e.value.name == "VGA_ERR_NONFINITE"
+    sim.set_masses(X)
+    sim.step(5)
+    assert np.isfinite(sim.totals()).all()
+    assert sim.stats()["negative_reports"] == 1
