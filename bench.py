@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the graph-build, implicit, adjoint and batched measurements")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (for profiler runs)")
-    ap.add_argument("--extras", default="graph_build,implicit,adjoint,batched,pngm",
+    ap.add_argument("--extras", default="graph_build,implicit,adjoint,batched,pngm,adjoint_fit",
                     help="comma-separated subset of the extra measurements to run")
     ap.add_argument("--adj-steps", type=int, default=200, help="time steps of the adjoint measurement")
     ap.add_argument("--adj-ckpt", type=int, default=100, help="checkpoint spacing of the adjoint measurement")
@@ -196,9 +196,18 @@ def run_cpu_baseline(a, img, X0, gpu_after=None):
     Xm = oracle.explicit_run(og.nbr, p, X1, m - 1)
     dt = time.time() - t0
     rate = og.n * (m - 1) / dt
-    base = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # one thread, on a shorter sample of the same workload
+    oracle.set_num_threads(1)
+    t0 = time.time()
+    oracle.explicit_run(og.nbr, p, X1, 2)
+    dt1 = time.time() - t0
+    oracle.set_num_threads(cores)
+    base = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{m - 1} explicit steps of the {a.side}^3 workload (after 1 untimed step), FP64, "
-                      f"OpenMP over the host cores"}
+                      f"OpenMP over the host cores",
+            "single_thread": {"value": og.n * 2 / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"2 explicit steps of the {a.side}^3 workload, FP64, one thread"}}
     return base, og, Xm, m
 
 
@@ -217,6 +226,17 @@ def bench_ours(a):
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
+    # the FP64 reference of the adjoint configuration runs in a spawned process while the GPU legs run
+    c5_job = None
+    if (world == 1 and not a.no_cpu and not a.no_extras and "adjoint_fit" in a.extras.split(",")):
+        import multiprocessing as mp
+
+        ctx = mp.get_context("spawn")
+        c5_q = ctx.Queue()
+        c5_proc = ctx.Process(target=_oracle_c5_reference, args=(c5_q, max(1, (os.cpu_count() or 2) // 2)),
+                              daemon=True)
+        c5_proc.start()
+        c5_job = (c5_proc, c5_q)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -301,7 +321,7 @@ def bench_ours(a):
     best = tune["best"] or {}
     variant = best.get("variant")
     n_active = sim.stats()["active_nodes"]
-    sparse = variant == 5 and n_active >= 0
+    sparse = variant in (5, 6) and n_active >= 0
     # algorithmic bytes of the pass as it runs: the sparse pass needs the DOM of every node read and
     # written plus the other four compartments of the nodes the transformation can change; the
     # dense pass the five compartments of every node
@@ -312,6 +332,8 @@ def bench_ours(a):
              2: "k_stencil_table (neighbour-offset table)",
              4: "k_stencil_tablev (neighbour-offset table, two nodes per thread, 8-byte vector streams)",
              5: "k_stencil_tablev (neighbour-offset table, four nodes per thread, 16-byte vector streams)",
+             6: "k_dom_block (temporally blocked: tiles of 32x16x16 voxels with a 3-voxel halo in shared memory, "
+                "up to 3 fused passes per launch; tile-order permutation of the DOM per step call included)",
              3: f"k_wave (neighbour-offset table; {S - 1} fused passes per persistent launch as an L2 wavefront, "
                 f"chunks of {best.get('chunk')} nodes, {best.get('depth')} passes per block)"}.get(variant, "k_stencil")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -404,6 +426,7 @@ def bench_ours(a):
            "autotune": tune,
            "drift_timed_region": float(abs(tot1.sum() - tot0.sum()) / tot0.sum())}
 
+    held = {}  # GPU results kept for the FP64 comparisons after the GPU legs
     if not a.no_extras:
         extras = {}
         want = set(a.extras.split(","))
@@ -411,18 +434,29 @@ def bench_ours(a):
             extras["graph_build"] = {"seconds": t_graph, "n_nodes": n, "n_components": g.n_components,
                                      "mask_seconds": t_mask, "note": "device image input, includes one stream sync"}
         if "implicit" in want:
-            extras["implicit"] = bench_implicit(vga, g, x0_dev, n, stream)
+            extras["implicit"] = bench_implicit(vga, g, x0_dev, n, stream, held)
         if "adjoint" in want:
             extras["adjoint"] = bench_adjoint(vga, g, params, x0_dev, n, stream, a.adj_steps, a.adj_ckpt)
         if "batched" in want:
-            extras["batched"] = bench_batched(vga, a)
+            extras["batched"] = bench_batched(vga, a, held)
         if "pngm" in want:
             extras["pngm"] = bench_pngm(vga, g, n, stream)
+        if "adjoint_fit" in want:
+            extras["adjoint_fit"] = bench_adjoint_fit(vga, stream)
         out.update(extras)
 
     if rank == 0 and world == 1 or (rank == 0 and world > 1):
         # cpu baseline (rank 0, N = 1 only) and the FP64 error of the same steps
         if world == 1 and not a.no_cpu:
+            if c5_job is not None:  # the spawned reference first: the timed CPU leg gets every core
+                c5_proc, c5_q = c5_job
+                try:
+                    ref = c5_q.get(timeout=900)
+                except Exception:
+                    ref = None
+                c5_proc.join(timeout=30)
+                if "adjoint_fit" in out:
+                    out["adjoint_fit"]["error_vs_fp64"] = c5_compare(out["adjoint_fit"], ref)
             base, og, Xm, m = run_cpu_baseline(a, img, X0)
             assert og.n == n
             simc = vga.Sim(g, params, stream=stream)
@@ -434,6 +468,11 @@ def bench_ours(a):
                                     "drift": float(abs(simc.totals().sum() - X0.sum()) / X0.sum()),
                                     "compared": "every node, every compartment, against the FP64 oracle"}
             simc.close()
+            del got, Xm
+            if "implicit_state" in held and "implicit" in out:
+                out["implicit"]["error_vs_fp64"] = implicit_error(og, held.pop("implicit_state"), X0)
+            if "batched_states" in held and "batched" in out:
+                out["batched"]["error_vs_fp64"] = batched_error(held.pop("batched_states"))
         print(json.dumps(out), flush=True)
     sim.close()
     g.close()
@@ -441,18 +480,25 @@ def bench_ours(a):
         dist.destroy_process_group()
 
 
-def bench_implicit(vga, g, x0_dev, n, stream, nimp=3):
-    """Scheme 2 at 10x the explicit limit, rtol 1e-8, default solver (float-float refinement around FP32
-    PCG); kernel times by kind from the library's CUDA-event timing."""
-    import torch
-
+def implicit_params():
     import synth
 
-    pi = synth.paper_params(dt=10 * 0.9 / (6 * synth.D_DOM), scheme=1, cg_rtol=1e-8, cg_maxit=500)
+    return synth.paper_params(dt=10 * 0.9 / (6 * synth.D_DOM), scheme=1, cg_rtol=1e-8, cg_maxit=500)
+
+
+def bench_implicit(vga, g, x0_dev, n, stream, held=None, nimp=3):
+    """Scheme 2 at 10x the explicit limit, rtol 1e-8, default solver (float-float refinement around FP32
+    PCG); kernel times by kind from the library's CUDA-event timing.  The state after the first step
+    is kept in `held` for the comparison with the FP64 oracle."""
+    import torch
+
+    pi = implicit_params()
     simi = vga.Sim(g, pi, stream=stream)
     simi.set_masses(x0_dev)
     simi.step(1)
     simi.sync()
+    if held is not None:
+        held["implicit_state"] = simi.get_masses()
     it0 = simi.stats()["cg_iterations"]
     torch.cuda.synchronize()
     w0 = time.perf_counter()
@@ -514,9 +560,14 @@ def bench_adjoint(vga, g, params, x0_dev, n, stream, nsteps=200, ckpt=100, bs=8)
             "reverse_kernel_launches": kt["adjoint"][1], "grad_D": grad["D"], "n_theta": n_theta}
 
 
-def bench_batched(vga, a, count=64, nsteps=5000):
+BATCH_CHECK_STEPS = 200
+
+
+def bench_batched(vga, a, held=None, count=64, nsteps=5000):
     """64 subvolumes, side U{64..192}, porosity U(10%, 35%), rates log-uniform in [0.5, 1.5] x the
-    paper's, 5000 steps in persistent graph-captured launches (launch shape autotuned)."""
+    paper's, 5000 steps in persistent graph-captured launches (launch shape autotuned).  For the FP64
+    comparison the same batch then runs BATCH_CHECK_STEPS steps from the initial masses and the
+    states of a size-stratified sample of instances are kept in `held`."""
     import synth
 
     t0 = time.time()
@@ -542,6 +593,13 @@ def bench_batched(vga, a, count=64, nsteps=5000):
     t1 = time.perf_counter()
     st = b.stats()
     total = sum(gk.n for gk in graphs)
+    if held is not None:
+        for k, X in enumerate(masses):
+            b.set_masses(k, X)
+        b.step(BATCH_CHECK_STEPS)
+        order = np.argsort([gk.n for gk in graphs])
+        sample = sorted(set(order[[0, 1, 21, 42, 62, 63]].tolist()))
+        held["batched_states"] = [(specs[k], masses[k], b.get_masses(k)) for k in sample]
     b.close()
     return {"value": total * nsteps / (t1 - t0), "unit": UNIT, "instances": count, "total_nodes": total,
             "time_steps": nsteps, "seconds": t1 - t0, "setup_seconds": t_setup, "launch": tune["best"],
@@ -618,6 +676,151 @@ def bench_pngm(vga, g, n, stream, bs=16, scenarios=2, records=12, epochs=1000):
                     "loss_last": float(res["loss"][-1]), "loss_min": float(np.min(res["loss"]))},
             "scheme4": {"steps": 10, "dt_s": 10.0, "seconds": t8 - t7,
                         "cg_iterations": info["last_cg_iterations"], "last_relres": info["last_cg_relres"]}}
+
+
+def implicit_error(og, got, X0):
+    """One Scheme 2 step of the FP64 oracle (PCG to 1e-11) from the same initial state."""
+    import oracle
+
+    t0 = time.time()
+    ref, status, iters, worst = oracle.implicit_run(og.nbr, implicit_params(), X0, 1, rtol=1e-11)
+    return {"time_steps": 1, "rel_l2": [rel_l2(got[c], ref[c]) for c in range(5)],
+            "drift": float(abs(got.sum() - X0.sum()) / X0.sum()), "oracle_status": status,
+            "oracle_seconds": time.time() - t0,
+            "compared": "every node, every compartment, after one step, against the FP64 oracle's PCG"}
+
+
+def batched_error(states):
+    """The sampled instances of the batch after BATCH_CHECK_STEPS steps against the FP64 oracle run of
+    each instance (its own graph, from the same mask)."""
+    import oracle
+    import synth
+
+    t0 = time.time()
+    rows = []
+    for spec, X0, got in states:
+        img = synth.pore_mask(spec["shape"], spec["porosity"], spec["mask_seed"])
+        og = oracle.graph_build(img, keep_largest=True)
+        ref = oracle.explicit_run(og.nbr, spec["params"], X0, BATCH_CHECK_STEPS)
+        rows.append({"side": spec["shape"][0], "n_nodes": og.n,
+                     "rel_l2": [rel_l2(got[c], ref[c]) if np.abs(ref[c]).max() > 0 else float(np.abs(got[c]).max())
+                                for c in range(5)],
+                     "drift": float(abs(got.sum() - X0.sum()) / X0.sum())})
+    worst = [max(r["rel_l2"][c] for r in rows) for c in range(5)]
+    return {"time_steps": BATCH_CHECK_STEPS, "instances": rows, "worst_rel_l2": worst,
+            "worst_drift": max(r["drift"] for r in rows), "oracle_seconds": time.time() - t0,
+            "compared": "every node of the two smallest, two largest and two middle instances"}
+
+
+def c5_config():
+    """The adjoint configuration: 128^3 at 17% porosity (seed 5), 2000 explicit steps, loss = squared
+    error of the final 8^3-block DOM and CO2 masses against a target run with seeded block-face
+    conductances theta* (log-uniform within +-50%), checkpoints every 100 steps, 200 normalised SGD
+    epochs (Sec. V.A update, Sec. V.B schedule: lr 0.1 halved every 10 epochs) from theta = 1."""
+    import synth
+
+    side, bs = 128, 8
+    nb = (-(-side // bs),) * 3
+    n_theta = nb[0] * nb[1] * (nb[2] - 1) + nb[0] * (nb[1] - 1) * nb[2] + (nb[0] - 1) * nb[1] * nb[2]
+    return dict(shape=(side, side, side), porosity=0.17, seed=5, bs=bs, nb=nb, n_theta=n_theta, steps=2000,
+                ckpt=100, epochs=200, comp_mask=(1 << 1) | (1 << 4),
+                params=synth.paper_params(dt=0.9 / (6 * synth.D_DOM * 1.5)),
+                theta_star=synth.block_conductances(nb, 5))
+
+
+def _oracle_c5_reference(q, threads):
+    """Spawned child: the FP64 oracle's loss and gradients of the adjoint configuration at theta = 1
+    (epoch 0), against the oracle's own target run with theta*."""
+    import oracle
+    import synth
+
+    t0 = time.time()
+    oracle.set_num_threads(threads)
+    cfg = c5_config()
+    img = synth.pore_mask(cfg["shape"], cfg["porosity"], cfg["seed"])
+    og = oracle.graph_build(img)
+    X0 = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), cfg["seed"],
+                              with_organic_matter=True)
+    shape, bs, p, N = cfg["shape"], cfg["bs"], cfg["params"], cfg["steps"]
+    g6s = oracle.block_face_weights(shape, bs, og.voxel_of_node, og.nbr, cfg["theta_star"])
+    target = oracle.block_masses(shape, bs, og.voxel_of_node, oracle.explicit_run(og.nbr, p, X0, N, g6=g6s))
+    theta = np.ones(cfg["n_theta"])
+    g6 = oracle.block_face_weights(shape, bs, og.voxel_of_node, og.nbr, theta)
+    XN = oracle.explicit_run(og.nbr, p, X0, N, g6=g6)
+    L, lamN = oracle.block_mass_loss(shape, bs, og.voxel_of_node, XN, target)
+    ref = oracle.adjoint_run(og.nbr, p, X0, N, lamN, ckpt=cfg["ckpt"], g6=g6, want_gface=True)
+    gth = oracle.block_theta_grad(shape, bs, og.voxel_of_node, og.nbr, ref["gface"], cfg["n_theta"])
+    q.put(dict(loss=L, grad=ref["grad"], gtheta=gth, seconds=time.time() - t0, threads=threads))
+
+
+def bench_adjoint_fit(vga, stream):
+    """The adjoint configuration end to end on the GPU: target run with theta*, the epoch-0 loss and
+    gradients (D, the seven rates, every block-face theta), then 200 normalised SGD epochs of
+    checkpointed forward + loss + reverse sweep + update, all in the library's kernels."""
+    import torch
+
+    import synth
+    from paper_2406_04177_gb300.fit import fit_block_conductances
+
+    cfg = c5_config()
+    img = synth.pore_mask(cfg["shape"], cfg["porosity"], cfg["seed"])
+    g = vga.Graph(img, stream=stream)
+    kept = synth.kept_mask_from_nodes(img.shape, g.export(labels=False, nbr=False)["voxel_of_node"])
+    X0 = synth.initial_masses(kept, cfg["seed"], with_organic_matter=True)
+    bs, p, N, nI, mask = cfg["bs"], cfg["params"], cfg["steps"], cfg["n_theta"], cfg["comp_mask"]
+    nblk = cfg["nb"][0] * cfg["nb"][1] * cfg["nb"][2]
+    sim = vga.Sim(g, p, stream=stream)
+    sim.set_block_conductances(bs, cfg["theta_star"].astype(np.float32))
+    sim.set_masses(X0)
+    sim.step(N)
+    _, target = sim.loss_block_mass(bs, mask, np.zeros((2, nblk)), want_mass=True)
+    sim.set_block_conductances(bs, np.ones(nI, dtype=np.float32))
+    sim.set_masses(X0)
+    dldx = torch.empty((5, g.n), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.adjoint_forward(N, cfg["ckpt"])
+    L0, _ = sim.loss_block_mass(bs, mask, target, dL_dX=dldx)
+    grad0, gth0 = sim.adjoint_backward(dldx, n_theta=nI)
+    t_epoch0 = time.perf_counter() - t0
+    sim.close()
+    t0 = time.perf_counter()
+    res = fit_block_conductances(g, p, X0, bs, target, nI, n_steps=N, ckpt=cfg["ckpt"], epochs=cfg["epochs"],
+                                 lr0=0.1, halve_every=10, stream=stream)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    th, ts = res["theta"].astype(np.float64), cfg["theta_star"]
+    moved = np.abs(gth0) > 0
+    g.close()
+    return {"workload": "128^3 at 17% porosity (seed 5), 2000 explicit steps per epoch, checkpoints every 100, "
+                        f"8^3-block DOM and CO2 loss, {nI} block-face conductances, 200 sign-SGD epochs "
+                        "(lr 0.1 halved every 10)",
+            "n_nodes": g.n, "epochs": cfg["epochs"], "seconds": t_fit, "epochs_per_s": cfg["epochs"] / t_fit,
+            "value": g.n * N * cfg["epochs"] / t_fit,
+            "unit": UNIT + " (each epoch: checkpointed forward + loss + reverse sweep + update)",
+            "epoch0_seconds": t_epoch0, "loss_first": float(res["loss"][0]), "loss_last": float(res["loss"][-1]),
+            "loss_every_20": [float(v) for v in res["loss"][::20]],
+            "theta_rel_err_start": float(np.linalg.norm(1.0 - ts) / np.linalg.norm(ts)),
+            "theta_rel_err_end": float(np.linalg.norm(th - ts) / np.linalg.norm(ts)),
+            "theta_rel_err_end_informative": float(np.linalg.norm((th - ts)[moved]) / np.linalg.norm(ts[moved])),
+            "informative_faces": int(moved.sum()),
+            "epoch0": {"loss": L0, "grad": grad0, "gtheta": gth0}}
+
+
+def c5_compare(fit, ref):
+    """Epoch-0 loss and gradients of the GPU run against the oracle's FP64 adjoint (each side with its
+    own target run)."""
+    e0 = fit.pop("epoch0")
+    if ref is None:
+        return {"available": False}
+    gt, rt = np.asarray(e0["gtheta"]), np.asarray(ref["gtheta"])
+    return {"loss_rel": abs(e0["loss"] - ref["loss"]) / abs(ref["loss"]),
+            "grad_theta_rel_l2": float(np.linalg.norm(gt - rt) / np.linalg.norm(rt)),
+            "grad_params_rel": {k: abs(e0["grad"][k] - ref["grad"][k]) / max(abs(ref["grad"][k]), 1e-300)
+                                for k in ref["grad"]},
+            "oracle_seconds": ref["seconds"], "oracle_threads": ref["threads"],
+            "compared": "epoch 0 (theta = 1): loss, dL/dtheta of every face, dL/d(D and the seven rates), "
+                        "against the FP64 discrete adjoint"}
 
 
 def bench_reference(a):

@@ -73,6 +73,7 @@ def _load():
             lib.vo_adjoint_run.restype = C.c_int
             lib.vo_adjoint_run.argtypes = [I64, P, P, P, P, I64, I64, P, P, P, P, P]
             lib.vo_num_threads.restype = C.c_int
+            lib.vo_set_num_threads.argtypes = [C.c_int]
             lib.vo_ticks_before.restype = I64
             lib.vo_ticks_before.argtypes = [I64, D, D]
             lib.vo_run_subcycled.restype = C.c_int
@@ -92,6 +93,11 @@ def _params(p: dict) -> _Params:
 def num_threads() -> int:
     """OpenMP threads the oracle's parallel loops use."""
     return int(_load().vo_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Thread count of the oracle's parallel loops from now on (k >= 1)."""
+    _load().vo_set_num_threads(int(k))
 
 
 class Graph:

@@ -58,6 +58,11 @@ int vo_num_threads(void) {
 #endif
 }
 
+/* Thread count of the parallel loops from here on (the benchmark times one thread and all cores). */
+void vo_set_num_threads(int k) {
+    if (k > 0) omp_set_num_threads(k);
+}
+
 /* ------------------------------------------------------------------------------------------
  * Graph construction (Sec. II.A; Sec. III first paragraph; Fig. 2).
  * V = voxels with I == 0; edges join face-adjacent voxels of V.  Components are labelled by a

@@ -255,6 +255,170 @@ __device__ __forceinline__ void face_atomic_add_f(double *gtheta, int32_t f, flo
     if (head && f >= 0) atomicAdd(gtheta + f, (double)sum);
 }
 
+// Reverse step with four consecutive nodes per thread: the per-node streams (offset table, block
+// ids, the five adjoint compartments, the recorded X^k and y2^k) move as 16-byte FP32 / table vectors
+// and 8-byte residual vectors, so a warp issues a quarter of the memory instructions and address
+// computations of the one-node kernel; the -x / +x neighbours of a group's end nodes come from the
+// adjacent lanes.  Per node the arithmetic is k_adjoint_table's (same slot order, same operations),
+// so dL/dX^k is the same bits; the per-thread gradient sums take the nodes in another order.
+// Block-face gradients: for each position k of the group the lanes hold nodes 4 lane + k, so nodes
+// that cross one face are still a contiguous run of lanes and face_atomic_add_f applies per k.
+template <int WM, int PREC, int TF>
+__global__ void __launch_bounds__(kThreads, 2) k_adjoint_vec(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+                                                          StateIO io, int64_t npad, const float *__restrict__ xk,
+                                                          const float *__restrict__ y2k, double *__restrict__ gpart,
+                                                          double *__restrict__ gtheta) {
+    constexpr int K = 4;
+    const float *__restrict__ L2 = io.in[1];
+    CAcc acc[kPar];
+    const float mc = -p.c;
+    const uint32_t nn = (uint32_t)n;
+    const int lane = threadIdx.x & 31;
+    const int64_t nsup = (n + (int64_t)kThreads * K - 1) / ((int64_t)kThreads * K);
+    for (int64_t sup = blockIdx.x; sup < nsup; sup += gridDim.x) {
+        const uint32_t i0 = (uint32_t)(sup * kThreads * K + (int64_t)threadIdx.x * K);
+        const bool full = i0 + K <= nn;
+        uint32_t ty[K], zm[K], zp[K], bn[K];
+        V l2[K], yv[K];
+        if (full) {
+            group_load<WM, PREC, TF, K, true>(i0, nn, tb, bt, io, ty, zm, zp, bn, l2);
+            vload_k<P_F32, K, true>(y2k, nullptr, i0, nn, yv);
+        } else {
+            group_load<WM, PREC, TF, K, false>(i0, nn, tb, bt, io, ty, zm, zp, bn, l2);
+            vload_k<P_F32, K, false>(y2k, nullptr, i0, nn, yv);
+        }
+        float li[K], yi[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            li[k] = l2[k].h;
+            yi[k] = yv[k].h;
+        }
+        float ll = __shfl_up_sync(0xffffffffu, li[K - 1], 1), lr = __shfl_down_sync(0xffffffffu, li[0], 1);
+        float yl = __shfl_up_sync(0xffffffffu, yi[K - 1], 1), yr = __shfl_down_sync(0xffffffffu, yi[0], 1);
+        if (lane == 0 && ((ty[0] >> 15) & 1u)) {
+            ll = __ldg(L2 + (i0 - 1));
+            yl = __ldg(y2k + (i0 - 1));
+        }
+        if (lane == 31 && (ty[K - 1] >> 31)) {
+            lr = __ldg(L2 + (i0 + K));
+            yr = __ldg(y2k + (i0 + K));
+        }
+        float lsum[K];
+        int32_t face[K][3];
+        float fval[K][3];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const bool live = i0 + k < nn;
+            const uint32_t dym = ty[k] & 0x7fffu, dyp = (ty[k] >> 16) & 0x7fffu;
+            const uint32_t mask = live ? (((ty[k] >> 15) & 1u) | ((ty[k] >> 31) << 1) | ((uint32_t)(dym != 0) << 2) |
+                                          ((uint32_t)(dyp != 0) << 3) | ((uint32_t)(zm[k] != 0) << 4) |
+                                          ((uint32_t)(zp[k] != 0) << 5))
+                                       : 0u;
+            float lv[6], yw[6];
+            lv[0] = k == 0 ? ll : li[k > 0 ? k - 1 : 0];
+            yw[0] = k == 0 ? yl : yi[k > 0 ? k - 1 : 0];
+            lv[1] = k == K - 1 ? lr : li[k < K - 1 ? k + 1 : 0];
+            yw[1] = k == K - 1 ? yr : yi[k < K - 1 ? k + 1 : 0];
+            const uint32_t off[4] = {i0 + k - dym, i0 + k + dyp, i0 + k - zm[k], i0 + k + zp[k]};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool ex = (mask >> (q + 2)) & 1u;
+                lv[q + 2] = ex ? __ldg(L2 + off[q]) : 0.0f;
+                yw[q + 2] = ex ? __ldg(y2k + off[q]) : 0.0f;
+            }
+            float ls = 0.0f, ys = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                face[k][q] = -1;
+                fval[k][q] = 0.0f;
+            }
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                if (!((mask >> d) & 1u)) continue;
+                const float g = (WM == W_UNIT) ? 1.0f : table_theta(bt, bn[k], d);
+                const float dl = __fsub_rn(li[k], lv[d]);
+                const float dy = __fsub_rn(yi[k], yw[d]);
+                ls = __fmaf_rn(g, dl, ls);
+                ys = __fmaf_rn(g, dy, ys);
+                if (WM == W_BLOCK && (d & 1)) {  // +x, +y, +z: each edge once
+                    face[k][d >> 1] = table_face(bt, bn[k], d);
+                    fval[k][d >> 1] = __fmul_rn(__fmul_rn(mc, dy), dl);
+                }
+            }
+            lsum[k] = ls;
+            if (live) cacc_add_prod(acc[GR_COUNT], -li[k], ys);
+        }
+        if (WM == W_BLOCK) {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) face_atomic_add_f(gtheta, face[k][q], fval[k][q]);
+        }
+        if (i0 >= nn) continue;
+        // the other compartments and the recorded X^k; the reverse transformation per node
+        V m0[K], m2[K], m3[K], m4[K], x0[K], x1[K], x2v[K], x3[K], x4[K];
+        if (full) {
+            vload_k<PREC, K, true>(io.in[0], io.lin[0], i0, nn, m0);
+            vload_k<PREC, K, true>(io.in[2], io.lin[2], i0, nn, m2);
+            vload_k<PREC, K, true>(io.in[3], io.lin[3], i0, nn, m3);
+            vload_k<PREC, K, true>(io.in[4], io.lin[4], i0, nn, m4);
+            vload_k<P_F32, K, true>(xk, nullptr, i0, nn, x0);
+            vload_k<P_F32, K, true>(xk + npad, nullptr, i0, nn, x1);
+            vload_k<P_F32, K, true>(xk + 2 * npad, nullptr, i0, nn, x2v);
+            vload_k<P_F32, K, true>(xk + 3 * npad, nullptr, i0, nn, x3);
+            vload_k<P_F32, K, true>(xk + 4 * npad, nullptr, i0, nn, x4);
+        } else {
+            vload_k<PREC, K, false>(io.in[0], io.lin[0], i0, nn, m0);
+            vload_k<PREC, K, false>(io.in[2], io.lin[2], i0, nn, m2);
+            vload_k<PREC, K, false>(io.in[3], io.lin[3], i0, nn, m3);
+            vload_k<PREC, K, false>(io.in[4], io.lin[4], i0, nn, m4);
+            vload_k<P_F32, K, false>(xk, nullptr, i0, nn, x0);
+            vload_k<P_F32, K, false>(xk + npad, nullptr, i0, nn, x1);
+            vload_k<P_F32, K, false>(xk + 2 * npad, nullptr, i0, nn, x2v);
+            vload_k<P_F32, K, false>(xk + 3 * npad, nullptr, i0, nn, x3);
+            vload_k<P_F32, K, false>(xk + 4 * npad, nullptr, i0, nn, x4);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (i0 + k >= nn) continue;
+            vadd<PREC>(l2[k], __fmul_rn(-p.c, lsum[k]));
+            const float xs[5] = {x0[k].h, x1[k].h, x2v[k].h, x3[k].h, x4[k].h};
+            const V mu[5] = {m0[k], l2[k], m2[k], m3[k], m4[k]};
+            float gr[GR_COUNT];
+#pragma unroll
+            for (int q = 0; q < GR_COUNT; ++q) gr[q] = 0.0f;
+            V lam[5];
+            transform_sync_reverse<PREC>(xs, mu, lam, gr, p);
+#pragma unroll
+            for (int q = 0; q < GR_COUNT; ++q) cacc_add(acc[q], gr[q]);
+            m0[k] = lam[0];
+            l2[k] = lam[1];
+            m2[k] = lam[2];
+            m3[k] = lam[3];
+            m4[k] = lam[4];
+        }
+        if (full) {
+            vstore_k<PREC, K, true>(io.out[0], io.lout[0], i0, nn, m0);
+            vstore_k<PREC, K, true>(io.out[1], io.lout[1], i0, nn, l2);
+            vstore_k<PREC, K, true>(io.out[2], io.lout[2], i0, nn, m2);
+            vstore_k<PREC, K, true>(io.out[3], io.lout[3], i0, nn, m3);
+            vstore_k<PREC, K, true>(io.out[4], io.lout[4], i0, nn, m4);
+        } else {
+            vstore_k<PREC, K, false>(io.out[0], io.lout[0], i0, nn, m0);
+            vstore_k<PREC, K, false>(io.out[1], io.lout[1], i0, nn, l2);
+            vstore_k<PREC, K, false>(io.out[2], io.lout[2], i0, nn, m2);
+            vstore_k<PREC, K, false>(io.out[3], io.lout[3], i0, nn, m3);
+            vstore_k<PREC, K, false>(io.out[4], io.lout[4], i0, nn, m4);
+        }
+    }
+    double accd[kPar];
+#pragma unroll
+    for (int q = 0; q < kPar; ++q) accd[q] = (double)acc[q].s + (double)acc[q].c;
+    __shared__ double out[kPar];
+    block_sum_store<kPar>(accd, out);
+    if (threadIdx.x < kPar) gpart[(int64_t)blockIdx.x * kPar + threadIdx.x] += out[threadIdx.x];
+}
+
 // Table-driven reverse step (same arithmetic as k_adjoint_step), grid-stride over 256-node tiles.
 template <int WM, int PREC, int TF>
 __global__ void __launch_bounds__(kThreads, 5) k_adjoint_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
@@ -668,11 +832,11 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
         for (int64_t j = len - 1; j >= 0; --j) {
             const float *xk = (j == 0) ? cks.h : a->rec_x + (size_t)j * 5 * npad;
             timing_begin(s, VGA_KERNEL_ADJOINT);
-            // 12-byte neighbour entries: with the compact ones the reverse step measured 2% slower
+            // four nodes per thread, 12-byte neighbour entries
             if (table)
-                k_adjoint_table<WM, PREC, 0><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
-                                                                    io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
-                                                                    a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
+                k_adjoint_vec<WM, PREC, 0><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
+                                                                  io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
+                                                                  a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
             else
                 k_adjoint_step<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
                                                                    io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
