@@ -452,6 +452,11 @@ def vga_sim_free(s):
     _check(load_library().vga_sim_free(s), "vga_sim_free")
 
 
+def vga_batch_set_wait_test(b, skip_block: int, spin_limit: int = 0):
+    """Bounded-wait test hook of the batched launches; skip_block = -1 switches it off."""
+    _check(load_library().vga_batch_set_wait_test(b, int(skip_block), int(spin_limit)), "vga_batch_set_wait_test")
+
+
 def vga_state_totals_noalloc(values, residuals, n: int, row_stride: int, totals, stream=None):
     """values / residuals / totals are CUDA tensors (float32; 16-bit residual bits or None;
     float64 with at least 5 entries), contiguous; compartment c occupies
@@ -723,8 +728,7 @@ class Batch:
 
     def set_wait_test(self, skip_block: int, spin_limit: int = 0):
         """Bounded-wait test hook (vga_batch_set_wait_test); skip_block = -1 switches it off."""
-        _check(load_library().vga_batch_set_wait_test(self.handle, int(skip_block), int(spin_limit)),
-               "vga_batch_set_wait_test")
+        vga_batch_set_wait_test(self.handle, skip_block, spin_limit)
 
     def autotune(self, trial_steps: int = 50) -> dict:
         return vga_batch_autotune(self.handle, trial_steps)
