@@ -157,6 +157,19 @@ vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const 
 /* Returns to unit conductances (g_ij = 1, Sec. II.B). */
 vga_status vga_sim_clear_conductances(vga_sim *s);
 
+/* Per-face conductances: the weighted flux of Sec. V.A, J_ij = -D g_ij (m_i - m_j) dt, with one
+ * conductance per voxel edge (the voxel form of the alpha_ij of the coarse model).  g_face: host,
+ * 6 x n FP32, g_face[6 i + d] = g of the edge leaving node i through slot d, slot order -x, +x, -y,
+ * +y, -z, +z (as vga_graph_export's nbr); entries of absent edges are ignored.  Every value must be
+ * finite and >= 0 and both slots of an edge must hold the same value (checked on the device:
+ * VGA_ERR_INVALID_ARG otherwise); the explicit scheme needs D dt sum_j g_ij <= 1 at every node
+ * (VGA_ERR_UNSTABLE_DT otherwise, Sec. II.B.3a).  Replaces block conductances.  Every scheme and
+ * the adjoint use them; vga_adjoint_backward then returns dL/dg in grad_theta as 6 x n doubles in the
+ * same layout (both slots of an edge hold the edge's derivative).  Requires nx <= 32767 and fewer
+ * than 2^26 nodes (VGA_ERR_UNSUPPORTED).  vga_sgd_block_conductances and
+ * vga_sim_get_block_conductances return VGA_ERR_UNSUPPORTED while they are set. */
+vga_status vga_sim_set_face_conductances(vga_sim *s, const float *g_face);
+
 /* Initial or replacement state X (5 x n, FP64, SoA).  Values are rounded to FP32.  on_device != 0
  * means x is a device pointer.  Errors: VGA_ERR_NONFINITE if a value is not finite (host input
  * only; device input is converted unchecked). */

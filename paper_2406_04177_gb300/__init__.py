@@ -142,6 +142,7 @@ _SIGNATURES = {
     "vga_batch_free": [_P],
     "vga_state_totals_noalloc": [_P, _P, _I64, _I64, _P, _P],
     "vga_batch_set_wait_test": [_P, _I32, C.c_uint32],
+    "vga_sim_set_face_conductances": [_P, _P],
     "vga_pngm_create": [_P, _P, _I32, _I32, _P, _P],
     "vga_pngm_get_info": [_P, _P],
     "vga_pngm_export": [_P, _P, _P, _P, _P, _P, _P, _P],
@@ -452,6 +453,12 @@ def vga_sim_free(s):
     _check(load_library().vga_sim_free(s), "vga_sim_free")
 
 
+def vga_sim_set_face_conductances(s, g_face: np.ndarray):
+    """g_face: (n, 6) float32 host array, slot order -x, +x, -y, +y, -z, +z; symmetric across edges."""
+    g = np.ascontiguousarray(g_face, dtype=np.float32)
+    _check(load_library().vga_sim_set_face_conductances(s, g.ctypes.data_as(C.c_void_p)), "vga_sim_set_face_conductances")
+
+
 def vga_batch_set_wait_test(b, skip_block: int, spin_limit: int = 0):
     """Bounded-wait test hook of the batched launches; skip_block = -1 switches it off."""
     _check(load_library().vga_batch_set_wait_test(b, int(skip_block), int(spin_limit)), "vga_batch_set_wait_test")
@@ -610,6 +617,13 @@ class Sim:
 
     def clear_conductances(self):
         vga_sim_clear_conductances(self.handle)
+
+    def set_face_conductances(self, g_face):
+        """Per-face conductances, (n, 6) float32 in the slot order of Graph.export's nbr."""
+        g = np.ascontiguousarray(g_face, dtype=np.float32)
+        if g.shape != (self.n, 6):
+            raise ValueError(f"g_face must have shape ({self.n}, 6)")
+        vga_sim_set_face_conductances(self.handle, g)
 
     def set_masses(self, x):
         if isinstance(x, np.ndarray):

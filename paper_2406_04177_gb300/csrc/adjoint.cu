@@ -31,8 +31,10 @@ namespace vga {
 namespace {
 
 constexpr int kThreads = 256;
+#ifndef VGA_ADJ_MIN_BLOCKS
+#define VGA_ADJ_MIN_BLOCKS 2  // resident blocks per SM the reverse step is compiled for
+#endif
 constexpr int kPar = GR_COUNT + 1;  // per-block partial slots: 7 rate slots + D
-constexpr int kAdjBlocks = 2432;     // grid of the table-driven reverse step (16 per SM on 152 SMs)
 
 struct Rec {
     float *x;   // 5 x npad FP32 values of X^k (recording target, or NULL)
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(kThreads) k_fused_rec(Topo t, const int32_t *_
         for_each_neighbour(i, k, fl, s_nb, cap, [&](int slot, int64_t j) {
             const float d = __fsub_rn(yi, __ldg(Y2 + j));
             if (WM == W_UNIT) acc = __fadd_rn(acc, d);
-            else acc = __fmaf_rn(block_theta(bw, slot, x, y, z), d, acc);
+            else acc = __fmaf_rn(edge_g(bw, i, slot, x, y, z), d, acc);
         });
         vadd<PREC>(x2, __fmul_rn(-p.c, acc));
         vround<PREC>(x2);
@@ -134,13 +136,13 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_step(Topo t, const int32_t
         const float yi = __ldg(y2k + i);
         float lsum = 0.0f, ysum = 0.0f;
         for_each_neighbour(i, k, fl, s_nb, cap, [&](int slot, int64_t j) {
-            const float g = (WM == W_UNIT) ? 1.0f : block_theta(bw, slot, x, y, z);
+            const float g = (WM == W_UNIT) ? 1.0f : edge_g(bw, i, slot, x, y, z);
             const float dl = __fsub_rn(li, __ldg(L2 + j));
             const float dy = __fsub_rn(yi, __ldg(y2k + j));
             lsum = __fmaf_rn(g, dl, lsum);
             ysum = __fmaf_rn(g, dy, ysum);
             if (WM == W_BLOCK && (slot & 1)) {  // +x, +y, +z: each edge once
-                const int64_t f = block_face(bw, slot, x, y, z);
+                const int64_t f = edge_face(bw, i, slot, x, y, z);
                 if (f >= 0) atomicAdd(gtheta + f, mc * (double)dy * (double)dl);
             }
         });
@@ -212,6 +214,46 @@ __global__ void __launch_bounds__(kThreads) k_fused_rec_vec(int64_t n, NbrTable 
     table_vec<1, WM, 0, PREC, TF, 4, true>(i0, (uint32_t)n, tb, bt, p, io, rec);
 }
 
+// Sparse fused pass with recording, first half: the forward's MODE 4 body (every node's DOM diffused,
+// marked nodes left for the second half), writing h + l of every node's diffused DOM to rec.y2.  At
+// an unmarked node the transformation is the identity, so that value is both X^k_2 and y2^k.
+template <int WM, int PREC, int TF>
+__global__ void __launch_bounds__(kThreads) k_dom_rec_vec(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+                                                          StateIO io, PassRecord rec, SparseState ss) {
+    const uint32_t i0 = 4u * ((uint32_t)blockIdx.x * blockDim.x + threadIdx.x);
+    table_vec<4, WM, 0, PREC, TF, 4, true>(i0, (uint32_t)n, tb, bt, p, io, rec, ss);
+}
+
+// Second half: the marked nodes in rank order (k_transform_compact's arithmetic), recording their
+// X^k (MB, DOM, SOM, FOM, FP32 h + l; xc row q at q * xcap) and overwriting y2^k with the
+// transformed DOM.
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) k_transform_compact_rec(int64_t m, SparseState ss, StepParams p,
+                                                                    StateIO io, float *__restrict__ y2,
+                                                                    float *__restrict__ xc, int64_t xcap) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    const uint32_t i = __ldg(ss.list + r);
+    V x2;
+    x2.h = io.out[1][i];
+    x2.l = PREC == P_COMP ? res_decode(io.lout[1][i], x2.h) : 0.0f;
+    V v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        v[q].h = ss.h[q][r];
+        v[q].l = PREC == P_COMP ? res_decode(ss.l[q][r], v[q].h) : 0.0f;
+    }
+    xc[r] = __fadd_rn(v[0].h, v[0].l);
+    xc[xcap + r] = __fadd_rn(x2.h, x2.l);
+    xc[2 * xcap + r] = __fadd_rn(v[1].h, v[1].l);
+    xc[3 * xcap + r] = __fadd_rn(v[2].h, v[2].l);
+    transform_sync<PREC>(v[0], x2, v[1], v[2], v[3], p);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) vstore<PREC>(ss.h[q], ss.l[q], r, v[q]);
+    vstore<PREC>(io.out[1], io.lout[1], i, x2);
+    y2[i] = __fadd_rn(x2.h, x2.l);
+}
+
 // Compensated FP32 accumulator (TwoSum into a second float): GB300 issues FP64 at a small fraction of
 // its FP32 rate, and a per-thread sum of ~100 terms carried this way keeps ~45 significant bits.
 struct CAcc {
@@ -234,25 +276,29 @@ __device__ __forceinline__ void cacc_add_prod(CAcc &a, float x, float y) {
     a.c = __fadd_rn(a.c, e);
 }
 
-// Adds v to gtheta[f] for every lane with f >= 0.  Lanes are consecutive nodes, so lanes that hit the
-// same face form contiguous runs (the nodes of one block along a row); each run is summed in FP32 by
-// a segmented shuffle reduction (five steps) and its first lane issues one FP64 atomic.  Must be
-// called by all 32 lanes.
-__device__ __forceinline__ void face_atomic_add_f(double *gtheta, int32_t f, float v) {
-    if (!__ballot_sync(0xffffffffu, f >= 0)) return;
-    const int lane = threadIdx.x & 31;
-    const int32_t fp = __shfl_up_sync(0xffffffffu, f, 1);
-    const bool head = lane == 0 || f != fp;
-    const unsigned heads = __ballot_sync(0xffffffffu, head);
-    const unsigned after = lane == 31 ? 0u : heads >> (lane + 1);
-    const int end = after ? lane + __ffs(after) : 32;  // one past this lane's run
-    float sum = v;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const float t = __shfl_down_sync(0xffffffffu, sum, off);
-        if (lane + off < end) sum = __fadd_rn(sum, t);
+// FP32 value as FP64, built with integer operations: exact for normal values, infinities and NaN;
+// subnormal values (below 2^-126 in magnitude) become zeros of their sign.  The conversion
+// instruction would issue on the FP64 pipe, which GB300 runs at a small fraction of its FP32 rate.
+__device__ __forceinline__ double f32_to_f64_alu(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    const uint32_t sign = u & 0x80000000u;
+    uint32_t hi = sign, lo = 0u;
+    if (e != 0u) {
+        const uint32_t ed = e == 0xffu ? 0x7ffu : e + 896u;  // rebias 127 -> 1023
+        hi = sign | (ed << 20) | ((u & 0x7fffffu) >> 3);
+        lo = u << 29;
     }
-    if (head && f >= 0) atomicAdd(gtheta + f, (double)sum);
+    return __hiloint2double((int)hi, (int)lo);
+}
+
+// Adds v to gtheta[f] when f >= 0: one FP64 atomic per crossing edge.  At the porosities of the
+// workloads a block face carries a few edges per step, spread over rows far apart in node order, so
+// lanes of one warp rarely share a face and a warp-level pre-reduction would cost more instructions
+// than it saves atomics.  The FP64 sums of FP32 terms are exact while the terms of a face span fewer
+// than 29 binary orders, so the result does not depend on the atomics' order there.
+__device__ __forceinline__ void face_atomic_add_f(double *gtheta, int32_t f, float v) {
+    if (f >= 0) atomicAdd(gtheta + f, f32_to_f64_alu(v));
 }
 
 // Reverse step with four consecutive nodes per thread: the per-node streams (offset table, block
@@ -261,13 +307,19 @@ __device__ __forceinline__ void face_atomic_add_f(double *gtheta, int32_t f, flo
 // computations of the one-node kernel; the -x / +x neighbours of a group's end nodes come from the
 // adjacent lanes.  Per node the arithmetic is k_adjoint_table's (same slot order, same operations),
 // so dL/dX^k is the same bits; the per-thread gradient sums take the nodes in another order.
-// Block-face gradients: for each position k of the group the lanes hold nodes 4 lane + k, so nodes
-// that cross one face are still a contiguous run of lanes and face_atomic_add_f applies per k.
-template <int WM, int PREC, int TF>
-__global__ void __launch_bounds__(kThreads, 2) k_adjoint_vec(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
+// The CO2 adjoint is read (respiration's weight) but not stored: no flux depends on CO2, so a step
+// leaves it unchanged and the caller passes one buffer as its input and output.
+// SP 0: X^k of every node from xk (rows of npad values).  SP 1 (sparse): X^k of the marked nodes of
+// the activity mask `ss` from the compact record xk (rows of xcap values, in rank order); at an
+// unmarked node MB, SOM and FOM are +0 and the DOM is y2^k (the transformation there is the
+// identity), and the reverse transformation runs with those values and without the rate-gradient
+// sums, whose terms are all products with MB, SOM, FOM or the mortality (zero there).  dL/dX^k and
+// the gradients are the bits of SP 0.
+template <int WM, int PREC, int TF, int SP>
+__global__ void __launch_bounds__(kThreads, VGA_ADJ_MIN_BLOCKS) k_adjoint_vec(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                           StateIO io, int64_t npad, const float *__restrict__ xk,
-                                                          const float *__restrict__ y2k, double *__restrict__ gpart,
-                                                          double *__restrict__ gtheta) {
+                                                          const float *__restrict__ y2k, SparseState ss, int64_t xcap,
+                                                          double *__restrict__ gpart, double *__restrict__ gtheta) {
     constexpr int K = 4;
     const float *__restrict__ L2 = io.in[1];
     CAcc acc[kPar];
@@ -314,34 +366,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_adjoint_vec(int64_t n, NbrTable
                                           ((uint32_t)(dyp != 0) << 3) | ((uint32_t)(zm[k] != 0) << 4) |
                                           ((uint32_t)(zp[k] != 0) << 5))
                                        : 0u;
+            // an absent neighbour carries the node's own values: its terms are g * (+0), which leave
+            // a sum that started at +0 unchanged (under round-to-nearest such a sum is never -0), so
+            // every slot is visited without a branch and the sums are those of the existing edges
             float lv[6], yw[6];
-            lv[0] = k == 0 ? ll : li[k > 0 ? k - 1 : 0];
-            yw[0] = k == 0 ? yl : yi[k > 0 ? k - 1 : 0];
-            lv[1] = k == K - 1 ? lr : li[k < K - 1 ? k + 1 : 0];
-            yw[1] = k == K - 1 ? yr : yi[k < K - 1 ? k + 1 : 0];
+            lv[0] = (mask & 1u) ? (k == 0 ? ll : li[k > 0 ? k - 1 : 0]) : li[k];
+            yw[0] = (mask & 1u) ? (k == 0 ? yl : yi[k > 0 ? k - 1 : 0]) : yi[k];
+            lv[1] = (mask & 2u) ? (k == K - 1 ? lr : li[k < K - 1 ? k + 1 : 0]) : li[k];
+            yw[1] = (mask & 2u) ? (k == K - 1 ? yr : yi[k < K - 1 ? k + 1 : 0]) : yi[k];
             const uint32_t off[4] = {i0 + k - dym, i0 + k + dyp, i0 + k - zm[k], i0 + k + zp[k]};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const bool ex = (mask >> (q + 2)) & 1u;
-                lv[q + 2] = ex ? __ldg(L2 + off[q]) : 0.0f;
-                yw[q + 2] = ex ? __ldg(y2k + off[q]) : 0.0f;
+                lv[q + 2] = ex ? __ldg(L2 + off[q]) : li[k];
+                yw[q + 2] = ex ? __ldg(y2k + off[q]) : yi[k];
             }
             float ls = 0.0f, ys = 0.0f;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                face[k][q] = -1;
-                fval[k][q] = 0.0f;
-            }
-#pragma unroll
             for (int d = 0; d < 6; ++d) {
-                if (!((mask >> d) & 1u)) continue;
-                const float g = (WM == W_UNIT) ? 1.0f : table_theta(bt, bn[k], d);
+                const float g = (WM == W_UNIT) ? 1.0f : table_theta_sel(bt, bn[k], d);
                 const float dl = __fsub_rn(li[k], lv[d]);
                 const float dy = __fsub_rn(yi[k], yw[d]);
                 ls = __fmaf_rn(g, dl, ls);
                 ys = __fmaf_rn(g, dy, ys);
                 if (WM == W_BLOCK && (d & 1)) {  // +x, +y, +z: each edge once
-                    face[k][d >> 1] = table_face(bt, bn[k], d);
+                    face[k][d >> 1] = table_face_sel(bt, bn[k], d, (mask >> d) & 1u);
                     fval[k][d >> 1] = __fmul_rn(__fmul_rn(mc, dy), dl);
                 }
             }
@@ -355,60 +404,87 @@ __global__ void __launch_bounds__(kThreads, 2) k_adjoint_vec(int64_t n, NbrTable
                 for (int q = 0; q < 3; ++q) face_atomic_add_f(gtheta, face[k][q], fval[k][q]);
         }
         if (i0 >= nn) continue;
-        // the other compartments and the recorded X^k; the reverse transformation per node
-        V m0[K], m2[K], m3[K], m4[K], x0[K], x1[K], x2v[K], x3[K], x4[K];
+        // the other compartments and the recorded X^k (MB, DOM, SOM, FOM: the reverse transformation
+        // reads no CO2); the reverse transformation per node
+        V m0[K], m2[K], m3[K], m4[K], x0[K], x1[K], x2v[K], x3[K];
         if (full) {
             vload_k<PREC, K, true>(io.in[0], io.lin[0], i0, nn, m0);
             vload_k<PREC, K, true>(io.in[2], io.lin[2], i0, nn, m2);
             vload_k<PREC, K, true>(io.in[3], io.lin[3], i0, nn, m3);
             vload_k<PREC, K, true>(io.in[4], io.lin[4], i0, nn, m4);
-            vload_k<P_F32, K, true>(xk, nullptr, i0, nn, x0);
-            vload_k<P_F32, K, true>(xk + npad, nullptr, i0, nn, x1);
-            vload_k<P_F32, K, true>(xk + 2 * npad, nullptr, i0, nn, x2v);
-            vload_k<P_F32, K, true>(xk + 3 * npad, nullptr, i0, nn, x3);
-            vload_k<P_F32, K, true>(xk + 4 * npad, nullptr, i0, nn, x4);
+            if (SP == 0) {
+                vload_k<P_F32, K, true>(xk, nullptr, i0, nn, x0);
+                vload_k<P_F32, K, true>(xk + npad, nullptr, i0, nn, x1);
+                vload_k<P_F32, K, true>(xk + 2 * npad, nullptr, i0, nn, x2v);
+                vload_k<P_F32, K, true>(xk + 3 * npad, nullptr, i0, nn, x3);
+            }
         } else {
             vload_k<PREC, K, false>(io.in[0], io.lin[0], i0, nn, m0);
             vload_k<PREC, K, false>(io.in[2], io.lin[2], i0, nn, m2);
             vload_k<PREC, K, false>(io.in[3], io.lin[3], i0, nn, m3);
             vload_k<PREC, K, false>(io.in[4], io.lin[4], i0, nn, m4);
-            vload_k<P_F32, K, false>(xk, nullptr, i0, nn, x0);
-            vload_k<P_F32, K, false>(xk + npad, nullptr, i0, nn, x1);
-            vload_k<P_F32, K, false>(xk + 2 * npad, nullptr, i0, nn, x2v);
-            vload_k<P_F32, K, false>(xk + 3 * npad, nullptr, i0, nn, x3);
-            vload_k<P_F32, K, false>(xk + 4 * npad, nullptr, i0, nn, x4);
+            if (SP == 0) {
+                vload_k<P_F32, K, false>(xk, nullptr, i0, nn, x0);
+                vload_k<P_F32, K, false>(xk + npad, nullptr, i0, nn, x1);
+                vload_k<P_F32, K, false>(xk + 2 * npad, nullptr, i0, nn, x2v);
+                vload_k<P_F32, K, false>(xk + 3 * npad, nullptr, i0, nn, x3);
+            }
+        }
+        uint32_t act = 0u, r0 = 0u;  // SP 1: activity bits of the group, rank of its first node
+        if (SP == 1) {
+            const uint32_t w = __ldg(ss.mask + (i0 >> 5));
+            act = (w >> (i0 & 31u)) & ((1u << K) - 1u);
+            if (act) r0 = __ldg(ss.prefix + (i0 >> 5)) + __popc(w & ((1u << (i0 & 31u)) - 1u));
         }
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if (i0 + k >= nn) continue;
             vadd<PREC>(l2[k], __fmul_rn(-p.c, lsum[k]));
-            const float xs[5] = {x0[k].h, x1[k].h, x2v[k].h, x3[k].h, x4[k].h};
             const V mu[5] = {m0[k], l2[k], m2[k], m3[k], m4[k]};
-            float gr[GR_COUNT];
-#pragma unroll
-            for (int q = 0; q < GR_COUNT; ++q) gr[q] = 0.0f;
             V lam[5];
-            transform_sync_reverse<PREC>(xs, mu, lam, gr, p);
+            if (SP == 0 || ((act >> k) & 1u)) {
+                float xs[5];
+                if (SP == 0) {
+                    xs[0] = x0[k].h;
+                    xs[1] = x1[k].h;
+                    xs[2] = x2v[k].h;
+                    xs[3] = x3[k].h;
+                } else {
+                    const uint32_t r = r0 + __popc(act & ((1u << k) - 1u));
+                    xs[0] = __ldg(xk + r);
+                    xs[1] = __ldg(xk + xcap + r);
+                    xs[2] = __ldg(xk + 2 * xcap + r);
+                    xs[3] = __ldg(xk + 3 * xcap + r);
+                }
+                xs[4] = 0.0f;
+                float gr[GR_COUNT];
 #pragma unroll
-            for (int q = 0; q < GR_COUNT; ++q) cacc_add(acc[q], gr[q]);
+                for (int q = 0; q < GR_COUNT; ++q) gr[q] = 0.0f;
+                transform_sync_reverse<PREC>(xs, mu, lam, gr, p);
+#pragma unroll
+                for (int q = 0; q < GR_COUNT; ++q) cacc_add(acc[q], gr[q]);
+            } else {
+                const float xs[5] = {0.0f, yi[k], 0.0f, 0.0f, 0.0f};
+                float gr[GR_COUNT];  // every term is +-0 here; not accumulated
+#pragma unroll
+                for (int q = 0; q < GR_COUNT; ++q) gr[q] = 0.0f;
+                transform_sync_reverse<PREC>(xs, mu, lam, gr, p);
+            }
             m0[k] = lam[0];
             l2[k] = lam[1];
             m2[k] = lam[2];
             m3[k] = lam[3];
-            m4[k] = lam[4];
         }
         if (full) {
             vstore_k<PREC, K, true>(io.out[0], io.lout[0], i0, nn, m0);
             vstore_k<PREC, K, true>(io.out[1], io.lout[1], i0, nn, l2);
             vstore_k<PREC, K, true>(io.out[2], io.lout[2], i0, nn, m2);
             vstore_k<PREC, K, true>(io.out[3], io.lout[3], i0, nn, m3);
-            vstore_k<PREC, K, true>(io.out[4], io.lout[4], i0, nn, m4);
         } else {
             vstore_k<PREC, K, false>(io.out[0], io.lout[0], i0, nn, m0);
             vstore_k<PREC, K, false>(io.out[1], io.lout[1], i0, nn, l2);
             vstore_k<PREC, K, false>(io.out[2], io.lout[2], i0, nn, m2);
             vstore_k<PREC, K, false>(io.out[3], io.lout[3], i0, nn, m3);
-            vstore_k<PREC, K, false>(io.out[4], io.lout[4], i0, nn, m4);
         }
     }
     double accd[kPar];
@@ -572,16 +648,32 @@ __global__ void __launch_bounds__(kThreads) k_block_mass_grad(Topo t, const int3
     }
 }
 
-// FP64 (5 x n) -> compensated buffers with row stride npad
+// FP64 (5 x n) -> compensated buffers with row stride npad.  The CO2 adjoint, which the reverse
+// steps read but never store (no flux depends on CO2), is stored in the form that a load, a zero
+// increment and a store leave unchanged: that cycle, applied until it changes nothing.  A cycle
+// moves h only on a residual tie, after which h is even and the residual exact, so two cycles suffice
+// and the third is a check.
 __global__ void k_lam_in(int64_t n, const double *__restrict__ x, StateIO io) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
 #pragma unroll
     for (int c = 0; c < 5; ++c) {
         const double v = x[c * n + i];
-        const float h = (float)v;
+        float h = (float)v;
+        res_t q = res_encode((float)(v - (double)h), h);
+        if (c == 4) {
+#pragma unroll 1
+            for (int t = 0; t < 3; ++t) {
+                V u = {h, res_decode(q, h)};
+                vadd<P_COMP>(u, 0.0f);
+                const float s = __fadd_rn(u.h, u.l);
+                const float r = __fadd_rn(__fsub_rn(u.h, s), u.l);
+                h = s;
+                q = res_encode(r, s);
+            }
+        }
         io.out[c][i] = h;
-        io.lout[c][i] = res_encode((float)(v - (double)h), h);
+        io.lout[c][i] = q;
     }
 }
 
@@ -611,6 +703,15 @@ StateIO io_from(PairBuf in, PairBuf out, int64_t npad) {
     return io;
 }
 
+// The adjoint state lam[lb] -> lam[1 - lb], with the CO2 row of lam[0] as both input and output
+// (the reverse steps leave it unchanged).
+StateIO lam_io(const PairBuf *lam, int lb, int64_t npad) {
+    StateIO io = io_from(lam[lb], lam[1 - lb], npad);
+    io.in[4] = io.out[4] = lam[0].h + 4 * (size_t)npad;
+    io.lin[4] = io.lout[4] = lam[0].l + 4 * (size_t)npad;
+    return io;
+}
+
 }  // namespace
 
 // Adjoint work buffers, owned by the simulation and kept between calls.
@@ -621,8 +722,15 @@ struct AdjointBuffers {
     bool last_recorded = false;  // the records hold the last segment (written by the forward sweep)
     int64_t N = 0, cur_ckpt = 0, param_gen = -1;
     char *ck = nullptr;    // nseg checkpoints, each 5*npad floats + 5*npad u16
-    float *rec_x = nullptr;   // ckpt x 5 x npad
+    float *rec_x = nullptr;   // ckpt x 5 x npad (dense records, allocated when first used)
+    int64_t rec_x_ckpt = 0;
     float *rec_y2 = nullptr;  // ckpt x npad
+    // Sparse records: the activity mask of X^0 (the marked set never grows, so it covers every
+    // step), and X^k of its marked nodes, ckpt x 4 x xcap (MB, DOM, SOM, FOM in rank order).
+    bool sparse = false;
+    Activity act;
+    float *rec_xc = nullptr;
+    int64_t rec_xc_count = 0, xcap = 1;
     PairBuf work[2];
     PairBuf lam[2];
     double *gpart = nullptr;  // G x kPar
@@ -636,6 +744,8 @@ void adjoint_free(AdjointBuffers *a) {
     dfree(a->ck);
     dfree(a->rec_x);
     dfree(a->rec_y2);
+    dfree(a->rec_xc);
+    activity_free(&a->act);
     for (int b = 0; b < 2; ++b) {
         dfree(a->work[b].h);
         dfree(a->work[b].l);
@@ -666,7 +776,6 @@ static vga_status ensure_adjoint(vga_sim *s, int64_t nseg, int64_t ckpt) {
     a->ntheta = ntheta;
     const size_t pairb = 5 * (size_t)npad * (sizeof(float) + sizeof(res_t));
     VGA_TRY(dmalloc((void **)&a->ck, pairb * (size_t)nseg, "adjoint checkpoints"));
-    VGA_TRY(dmalloc((void **)&a->rec_x, sizeof(float) * 5 * (size_t)npad * (size_t)ckpt, "adjoint records"));
     VGA_TRY(dmalloc((void **)&a->rec_y2, sizeof(float) * (size_t)npad * (size_t)ckpt, "adjoint records"));
     for (int b = 0; b < 2; ++b) {
         VGA_TRY(dmalloc((void **)&a->work[b].h, sizeof(float) * 5 * (size_t)npad, "adjoint work"));
@@ -677,6 +786,27 @@ static vga_status ensure_adjoint(vga_sim *s, int64_t nseg, int64_t ckpt) {
     VGA_TRY(dmalloc((void **)&a->gpart, sizeof(double) * kPar * (size_t)std::max<int64_t>(G, 1), "gradient partials"));
     VGA_TRY(dmalloc((void **)&a->gtheta, sizeof(double) * (size_t)ntheta, "theta gradient"));
     VGA_TRY(dmalloc((void **)&a->gsum, sizeof(double) * kPar, "gradient sums"));
+    return VGA_OK;
+}
+
+// Records of X^k for the current mode: every node (dense) or the marked nodes (sparse).
+static vga_status ensure_records(AdjointBuffers *a) {
+    if (a->sparse) {
+        const int64_t count = 4 * a->xcap * a->ckpt;
+        if (a->rec_xc && a->rec_xc_count >= count) return VGA_OK;
+        dfree(a->rec_xc);
+        a->rec_xc = nullptr;
+        a->rec_xc_count = 0;
+        VGA_TRY(dmalloc((void **)&a->rec_xc, sizeof(float) * (size_t)count, "adjoint records"));
+        a->rec_xc_count = count;
+        return VGA_OK;
+    }
+    if (a->rec_x && a->rec_x_ckpt >= a->ckpt) return VGA_OK;
+    dfree(a->rec_x);
+    a->rec_x = nullptr;
+    a->rec_x_ckpt = 0;
+    VGA_TRY(dmalloc((void **)&a->rec_x, sizeof(float) * 5 * (size_t)a->npad * (size_t)a->ckpt, "adjoint records"));
+    a->rec_x_ckpt = a->ckpt;
     return VGA_OK;
 }
 
@@ -720,6 +850,7 @@ static vga_status forward_recording(vga_sim *s, AdjointBuffers *a, int64_t len) 
     VGA_TRY(sim_nbr_table(s, &tb));
     if (WM == W_BLOCK) VGA_TRY(sim_block_table(s, &bt, &ok));
     if (!ok) return VGA_ERR_UNSUPPORTED;  // the caller falls back to the plain forward
+    VGA_TRY(ensure_records(a));
     cudaStream_t st = s->stream;
     const int Gv = (int)(((s->n + 3) / 4 + kThreads - 1) / kThreads);
     timing_begin(s, VGA_KERNEL_TRANSFORM);
@@ -728,15 +859,39 @@ static vga_status forward_recording(vga_sim *s, AdjointBuffers *a, int64_t len) 
     VGA_CHECK_LAUNCH();
     ++s->launches;
     for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
-    for (int64_t j = 1; j < len; ++j) {
-        const PassRecord pr = {a->rec_x + (size_t)j * 5 * npad, a->rec_y2 + (size_t)j * npad, npad};
-        timing_begin(s, VGA_KERNEL_FUSED_STEP);
-        if (tb.tz) k_fused_rec_vec<WM, PREC, 1><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, state_io(s), pr);
-        else k_fused_rec_vec<WM, PREC, 0><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, state_io(s), pr);
-        timing_end(s);
-        VGA_CHECK_LAUNCH();
-        ++s->launches;
-        for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
+    if (a->sparse) {
+        // the sparse fused passes: the marked nodes' MB, SOM, FOM, CO2 in the compact state, the
+        // DOM rows alternating; MB, SOM, FOM, CO2 stay in the current rows (zero at the unmarked nodes)
+        const SparseState ss = activity_state(a->act);
+        const int64_t m = a->act.n_active;
+        if (m > 0) VGA_TRY(activity_copy(a->act, s->n, state_io_inplace(s), true, true, st));
+        for (int64_t j = 1; j < len; ++j) {
+            const PassRecord pr = {nullptr, a->rec_y2 + (size_t)j * npad, npad};
+            const StateIO io = state_io(s);
+            timing_begin(s, VGA_KERNEL_FUSED_STEP);
+            if (tb.tz) k_dom_rec_vec<WM, PREC, 1><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr, ss);
+            else k_dom_rec_vec<WM, PREC, 0><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr, ss);
+            if (m > 0)
+                k_transform_compact_rec<PREC><<<grid_for(m, kThreads), kThreads, 0, st>>>(
+                    m, ss, s->sp, io, pr.y2, a->rec_xc + (size_t)j * 4 * a->xcap, a->xcap);
+            timing_end(s);
+            VGA_CHECK_LAUNCH();
+            s->launches += m > 0 ? 2 : 1;
+            s->cur[1] ^= 1;
+        }
+        if (m > 0) VGA_TRY(activity_copy(a->act, s->n, state_io_inplace(s), false, true, st));
+        s->launches += m > 0 ? 2 : 0;
+    } else {
+        for (int64_t j = 1; j < len; ++j) {
+            const PassRecord pr = {a->rec_x + (size_t)j * 5 * npad, a->rec_y2 + (size_t)j * npad, npad};
+            timing_begin(s, VGA_KERNEL_FUSED_STEP);
+            if (tb.tz) k_fused_rec_vec<WM, PREC, 1><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, state_io(s), pr);
+            else k_fused_rec_vec<WM, PREC, 0><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, state_io(s), pr);
+            timing_end(s);
+            VGA_CHECK_LAUNCH();
+            ++s->launches;
+            for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
+        }
     }
     VGA_TRY(sim_diffuse_pass(s));
     s->steps_done += len;
@@ -749,6 +904,22 @@ vga_status sim_adjoint_forward(vga_sim *s, int64_t N, int64_t ckpt) {
     AdjointBuffers *a = s->adj;
     a->valid = false;
     a->last_recorded = false;
+    // sparse records and reverse steps: the activity mask of X^0 on the neighbour-offset table
+    a->sparse = false;
+    if (s->activity_skip && s->g->nx <= 32767 && s->n > 0) {
+        bool ok = true;
+        if (s->wmode == W_BLOCK) {
+            BlockTable bt;
+            VGA_TRY(sim_block_table(s, &bt, &ok));
+        }
+        if (ok) {
+            // the current rows as the "spare" too: the zeros it writes at unmarked nodes are there already
+            VGA_TRY(activity_build(&a->act, s->n, s->npad, state_io_inplace(s), state_io_inplace(s), true, s->stream));
+            s->launches += 2;
+            a->sparse = true;
+            a->xcap = std::max<int64_t>(a->act.n_active, 1);
+        }
+    }
     for (int64_t sg = 0; sg < nseg; ++sg) {
         VGA_TRY(copy_state(s, ck_slot(a, sg), false));
         const int64_t len = std::min(ckpt, N - sg * ckpt);
@@ -783,13 +954,37 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     bool table = s->g->nx <= 32767;
     if (table) VGA_TRY(sim_nbr_table(s, &tb));
     if (table && WM == W_BLOCK) VGA_TRY(sim_block_table(s, &bt, &table));
-    const int Gt = (int)std::min<int64_t>(kAdjBlocks, (s->n + kThreads - 1) / kThreads);  // grid of the table kernels
+    // grid of the table kernels: the blocks that fit on the GPU at once (grid-stride over groups of
+    // kThreads x 4 nodes), so every thread's FP64 partial-sum tail is paid once per launch
+    int Gt = 1;
+    if (table) {
+        int dev = 0, sms = 0, occ0 = 0, occ1 = 0;
+        VGA_CUDA(cudaGetDevice(&dev));
+        VGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (tb.tz) {
+            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_adjoint_vec<WM, PREC, 1, 0>, kThreads, 0));
+            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_adjoint_vec<WM, PREC, 1, 1>, kThreads, 0));
+        } else {
+            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_adjoint_vec<WM, PREC, 0, 0>, kThreads, 0));
+            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_adjoint_vec<WM, PREC, 0, 1>, kThreads, 0));
+        }
+        const int64_t groups = (s->n + 4 * kThreads - 1) / (4 * kThreads);
+        Gt = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, std::min(occ0, occ1)) * sms, groups));
+    }
     const int Gv = (int)(((s->n + 3) / 4 + kThreads - 1) / kThreads);  // four nodes per thread
     const int G = table ? Gt : s->chunks.count;  // blocks writing gradient partials
     const size_t smem = sizeof(uint32_t) * (size_t)s->chunks.cap * decode_words(WM == W_BLOCK);
     const int64_t npad = s->npad;
     cudaStream_t st = s->stream;
 
+    const bool sparse = a->sparse && table;
+    const SparseState ss = sparse ? activity_state(a->act) : SparseState{};
+    const int64_t m = sparse ? a->act.n_active : 0;
+    if (a->sparse && !sparse) {  // (not reached: the forward sweep checked the same tables) dense form
+        a->sparse = false;
+        a->last_recorded = false;
+    }
+    VGA_TRY(ensure_records(a));
     k_lam_in<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, d_lamN, io_from(a->lam[0], a->lam[0], npad));
     VGA_CHECK_LAUNCH();
     VGA_CUDA(cudaMemsetAsync(a->gpart, 0, sizeof(double) * kPar * (size_t)std::max(G, 1), st));
@@ -810,7 +1005,25 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
             VGA_CHECK_LAUNCH();
             ++s->launches;
             int wb = 0;
-            for (int64_t j = 1; j < len; ++j) {
+            if (sparse && m > 0) {
+                VGA_TRY(activity_copy(a->act, s->n, io_from(a->work[0], a->work[0], npad), true, true, st));
+                ++s->launches;
+            }
+            for (int64_t j = 1; j < len && sparse; ++j) {
+                const PassRecord pr = {nullptr, a->rec_y2 + (size_t)j * npad, npad};
+                const StateIO io = io_from(a->work[wb], a->work[1 - wb], npad);
+                timing_begin(s, VGA_KERNEL_FUSED_STEP);
+                if (tb.tz) k_dom_rec_vec<WM, PREC, 1><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr, ss);
+                else k_dom_rec_vec<WM, PREC, 0><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr, ss);
+                if (m > 0)
+                    k_transform_compact_rec<PREC><<<grid_for(m, kThreads), kThreads, 0, st>>>(
+                        m, ss, s->sp, io, pr.y2, a->rec_xc + (size_t)j * 4 * a->xcap, a->xcap);
+                timing_end(s);
+                VGA_CHECK_LAUNCH();
+                s->launches += m > 0 ? 2 : 1;
+                wb = 1 - wb;
+            }
+            for (int64_t j = 1; j < len && !sparse; ++j) {
                 rec.x = a->rec_x + (size_t)j * 5 * npad;
                 rec.y2 = a->rec_y2 + (size_t)j * npad;
                 timing_begin(s, VGA_KERNEL_FUSED_STEP);
@@ -830,17 +1043,29 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
         }
         // reverse
         for (int64_t j = len - 1; j >= 0; --j) {
-            const float *xk = (j == 0) ? cks.h : a->rec_x + (size_t)j * 5 * npad;
+            const bool sp = sparse && j > 0;  // X^0 of a segment is its checkpoint (every node)
+            const float *xk = (j == 0) ? cks.h : sp ? a->rec_xc + (size_t)j * 4 * a->xcap : a->rec_x + (size_t)j * 5 * npad;
+            const float *y2k = a->rec_y2 + (size_t)j * npad;
+            const StateIO io = lam_io(a->lam, lb, npad);
             timing_begin(s, VGA_KERNEL_ADJOINT);
-            // four nodes per thread, 12-byte neighbour entries
-            if (table)
-                k_adjoint_vec<WM, PREC, 0><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp,
-                                                                  io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
-                                                                  a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
-            else
-                k_adjoint_step<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw,
-                                                                   io_from(a->lam[lb], a->lam[1 - lb], npad), npad, xk,
-                                                                   a->rec_y2 + (size_t)j * npad, a->gpart, a->gtheta);
+            // four nodes per thread
+            if (table && sp) {
+                if (tb.tz)
+                    k_adjoint_vec<WM, PREC, 1, 1><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, npad, xk, y2k, ss,
+                                                                         a->xcap, a->gpart, a->gtheta);
+                else
+                    k_adjoint_vec<WM, PREC, 0, 1><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, npad, xk, y2k, ss,
+                                                                         a->xcap, a->gpart, a->gtheta);
+            } else if (table) {
+                if (tb.tz)
+                    k_adjoint_vec<WM, PREC, 1, 0><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, npad, xk, y2k,
+                                                                         SparseState{}, 1, a->gpart, a->gtheta);
+                else
+                    k_adjoint_vec<WM, PREC, 0, 0><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, npad, xk, y2k,
+                                                                         SparseState{}, 1, a->gpart, a->gtheta);
+            } else
+                k_adjoint_step<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw, io,
+                                                                   npad, xk, y2k, a->gpart, a->gtheta);
             timing_end(s);
             VGA_CHECK_LAUNCH();
             ++s->launches;
@@ -849,7 +1074,10 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     }
     if (nseg > 1) a->last_recorded = false;  // the records now hold the first segment
     if (d_lam0) {
-        k_lam_out<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, d_lam0, io_from(a->lam[lb], a->lam[lb], npad));
+        StateIO io = io_from(a->lam[lb], a->lam[lb], npad);  // CO2 from lam[0]
+        io.in[4] = a->lam[0].h + 4 * (size_t)npad;
+        io.lin[4] = a->lam[0].l + 4 * (size_t)npad;
+        k_lam_out<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, d_lam0, io);
         VGA_CHECK_LAUNCH();
     }
     k_reduce_gpart<<<1, kThreads, 0, st>>>(a->gpart, G, a->gsum);
@@ -857,6 +1085,7 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     s->launches += 2;
     double h[kPar];
     VGA_CUDA(cudaMemcpyAsync(h, a->gsum, sizeof(double) * kPar, cudaMemcpyDeviceToHost, st));
+    if (s->face_mode) VGA_TRY(sim_face_mirror(s, a->gtheta));  // both slots of every edge
     if (h_gtheta && s->n_theta > 0 && s->wmode == W_BLOCK)
         VGA_CUDA(cudaMemcpyAsync(h_gtheta, a->gtheta, sizeof(double) * (size_t)s->n_theta, cudaMemcpyDeviceToHost, st));
     VGA_CUDA(cudaStreamSynchronize(st));
@@ -938,6 +1167,7 @@ __global__ void k_sgd_sign(int64_t n, float *__restrict__ theta, const double *_
 vga_status sim_sgd_theta(vga_sim *s, double lr, double lo, double hi) {
     if (!s->adj || !s->adj->valid) return fail(VGA_ERR_INVALID_ARG, "no adjoint gradient to step along");
     if (s->wmode != W_BLOCK || s->n_theta == 0) return fail(VGA_ERR_INVALID_ARG, "no block conductances set");
+    if (s->face_mode) return fail(VGA_ERR_UNSUPPORTED, "the sign-SGD update covers block conductances");
     k_sgd_sign<<<(unsigned)((s->n_theta + 255) / 256), 256, 0, s->stream>>>(s->n_theta, s->theta, s->adj->gtheta, lr, lo,
                                                                           hi);
     VGA_CHECK_LAUNCH();

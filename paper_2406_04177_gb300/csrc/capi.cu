@@ -373,7 +373,9 @@ vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const 
     if (n_theta > 0)
         VGA_CUDA(cudaMemcpyAsync(s->theta, theta, sizeof(float) * (size_t)n_theta, cudaMemcpyHostToDevice, s->stream));
     VGA_CUDA(cudaStreamSynchronize(s->stream));
-    if (s->bw.bs != block_side) s->btable_bs = 0;
+    if (s->bw.bs != block_side || s->face_mode) s->btable_bs = 0;
+    s->face_mode = false;
+    s->bw.g6 = nullptr;
     s->bw.bs = block_side;
     s->bw.nbx = nbx;
     s->bw.nby = nby;
@@ -390,7 +392,48 @@ vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const 
 vga_status vga_sim_clear_conductances(vga_sim *s) {
     if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
     s->wmode = W_UNIT;
+    s->face_mode = false;
+    s->bw.g6 = nullptr;
     s->max_g = 1.0f;
+    ++s->param_gen;
+    return VGA_OK;
+}
+
+vga_status vga_sim_set_face_conductances(vga_sim *s, const float *g_face) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    if (!g_face && s->n > 0) return fail(VGA_ERR_INVALID_ARG, "g_face is NULL");
+    if (s->g->nx > 32767 || s->n >= kMaxTableBlocks)
+        return fail(VGA_ERR_UNSUPPORTED, "per-face conductances need nx <= 32767 and fewer than 2^26 nodes");
+    const int64_t m = 6 * s->n;
+    for (int64_t k = 0; k < m; ++k)
+        if (!(std::isfinite(g_face[k]) && g_face[k] >= 0.0f))
+            return fail(VGA_ERR_INVALID_ARG, "face conductances must be finite and >= 0");
+    float *d = nullptr;
+    VGA_TRY(dmalloc((void **)&d, sizeof(float) * (size_t)std::max<int64_t>(m, 6), "face conductances"));
+    vga_status st = VGA_OK;
+    if (m > 0) {
+        const cudaError_t e = cudaMemcpyAsync(d, g_face, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, s->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "face conductances upload", __FILE__, __LINE__);
+    }
+    bool sym = true;
+    float rowmax = 0.0f;
+    if (st == VGA_OK) st = sim_face_check(s, d, &sym, &rowmax);
+    if (st == VGA_OK && !sym)
+        st = fail(VGA_ERR_INVALID_ARG, "face conductances differ between the two slots of an edge (g_ij != g_ji)");
+    if (st == VGA_OK && s->params.scheme == VGA_SCHEME_EXPLICIT && s->params.D * s->params.dt * rowmax > 1.0 + 1e-12)
+        st = fail(VGA_ERR_UNSTABLE_DT, "explicit scheme unstable with these conductances (D dt sum_j g_ij > 1)");
+    if (st != VGA_OK) {
+        dfree(d);
+        return st;
+    }
+    dfree(s->g6);
+    s->g6 = d;
+    s->bw = BlockWeights{};
+    s->bw.g6 = d;
+    s->face_mode = true;
+    s->wmode = W_BLOCK;
+    s->n_theta = m;
+    s->max_g = std::max(rowmax / 6.0f, 0.0f);  // the 6 D dt max_g bound of the parameter checks
     ++s->param_gen;
     return VGA_OK;
 }
@@ -608,6 +651,7 @@ vga_status vga_sgd_block_conductances(vga_sim *s, double lr, double theta_min, d
 }
 
 vga_status vga_sim_get_block_conductances(vga_sim *s, float *theta, int64_t n_theta) {
+    if (s && s->face_mode) return fail(VGA_ERR_UNSUPPORTED, "per-face conductances are set: no block conductances to read");
     if (!s || !theta) return fail(VGA_ERR_INVALID_ARG, "sim or theta is NULL");
     if (s->wmode != W_BLOCK || n_theta != s->n_theta) return fail(VGA_ERR_INVALID_ARG, "no block conductances of that size");
     VGA_CUDA(cudaMemcpyAsync(theta, s->theta, sizeof(float) * (size_t)n_theta, cudaMemcpyDeviceToHost, s->stream));
@@ -690,6 +734,8 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->loss_work);
     dfree(s->wave_dep);
     dfree(s->wave_order);
+    dfree(s->g6);
+    dfree(s->fnode);
     block_free(s);
     adjoint_free(s->adj);
     if (s->h_cg) cudaFreeHost(s->h_cg);

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(Topo t, const int32_t *__r
         const double bi = ld_value_d<PREC>(y2, y2l, i);
         double lb = 0.0, deg = 0.0;
         for_each_neighbour(i, k, fl, s_nb, cap, [&](int slot, int64_t j) {
-            const double g = (WM == W_UNIT) ? 1.0 : (double)block_theta(bw, slot, x, y, z);
+            const double g = (WM == W_UNIT) ? 1.0 : (double)edge_g(bw, i, slot, x, y, z);
             const double bj =
                 ld_value_d<PREC>(y2, y2l, j);
             lb += g * (bi - bj);
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) k_spmv(Topo t, const int32_t *__rest
         const double pi = p[i];
         double lp = 0.0;
         for_each_neighbour(i, k, fl, s_nb, cap, [&](int slot, int64_t j) {
-            const double g = (WM == W_UNIT) ? 1.0 : (double)block_theta(bw, slot, x, y, z);
+            const double g = (WM == W_UNIT) ? 1.0 : (double)edge_g(bw, i, slot, x, y, z);
             lp += g * (pi - p[j]);
         });
         const double qi = pi + c * lp;

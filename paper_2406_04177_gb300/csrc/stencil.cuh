@@ -128,14 +128,42 @@ __device__ __forceinline__ int64_t block_face(const BlockWeights &bw, int slot, 
 }
 
 // Conductance of the edge leaving a node through `slot` under the block table (see BlockTable).
+// Per-face conductances use the same table with one "block" per node (every slot crossing) and
+// theta6 = the 6 x n conductances.
 __device__ __forceinline__ float table_theta(const BlockTable &bt, uint32_t bn, int slot) {
     if (!((bn >> (26 + slot)) & 1u)) return 1.0f;
     return __ldg(bt.theta6 + 6 * (size_t)(bn & 0x3ffffffu) + slot);
 }
 
+// Gradient index of that edge: the block face, or (per-face table: face == NULL) 6 node + slot.
 __device__ __forceinline__ int32_t table_face(const BlockTable &bt, uint32_t bn, int slot) {
     if (!((bn >> (26 + slot)) & 1u)) return -1;
+    if (!bt.face) return (int32_t)(6 * (bn & 0x3ffffffu)) + slot;
     return __ldg(bt.face + 6 * (size_t)(bn & 0x3ffffffu) + slot);
+}
+
+// Branch-free forms for loops that visit every slot: the loads are made for every node (the
+// address is valid for any block id, including the 0 of a lane past the end), then selected.
+__device__ __forceinline__ float table_theta_sel(const BlockTable &bt, uint32_t bn, int slot) {
+    const float t = __ldg(bt.theta6 + 6 * (size_t)(bn & 0x3ffffffu) + slot);
+    return ((bn >> (26 + slot)) & 1u) ? t : 1.0f;
+}
+
+// table_face for an edge that exists, -1 otherwise.
+__device__ __forceinline__ int32_t table_face_sel(const BlockTable &bt, uint32_t bn, int slot, bool exists) {
+    const uint32_t b = bn & 0x3ffffffu;
+    const int32_t f = bt.face ? __ldg(bt.face + 6 * (size_t)b + slot) : (int32_t)(6 * b) + slot;
+    return (exists && ((bn >> (26 + slot)) & 1u)) ? f : -1;
+}
+
+// Conductance of the edge leaving node i (at x, y, z) through `slot`: per-face, else per block face.
+__device__ __forceinline__ float edge_g(const BlockWeights &bw, int64_t i, int slot, int x, int y, int z) {
+    return bw.g6 ? __ldg(bw.g6 + 6 * i + slot) : block_theta(bw, slot, x, y, z);
+}
+
+// Gradient index of that edge (see table_face), or -1 when it lies inside a block.
+__device__ __forceinline__ int64_t edge_face(const BlockWeights &bw, int64_t i, int slot, int x, int y, int z) {
+    return bw.g6 ? 6 * i + slot : block_face(bw, slot, x, y, z);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -439,18 +467,20 @@ __device__ __forceinline__ void group_finish(uint32_t i0, uint32_t n, const Step
 // -z, +z (an absent neighbour carries the node's own value, adding +0), Scheme 1's increment by
 // TwoSum, the rounding of vround, and the store of MODE 4 (a marked node's rounded pair itself, the
 // others renormalised as vstore).  Every lane does the scalar path's operations in its order, so the
-// results are the same bits.
+// results are the same bits.  REC: also writes h + l of the rounded pairs to rec_y2 (the adjoint's
+// record of the diffused DOM; at an unmarked node it is also the transformed DOM).
+template <bool REC = false>
 __device__ __forceinline__ void dom4_packed(uint32_t i0, const uint32_t (&ty)[4], const float (&y)[4], float yl,
                                             float yr, const float (&ym)[4], const float (&yp)[4], const float (&zv)[4],
                                             const float (&zw)[4], const V (&x2)[4], uint32_t act_bits,
-                                            const StepParams &p, const StateIO &io) {
+                                            const StepParams &p, const StateIO &io, float *rec_y2 = nullptr) {
     float xm[4], xp[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         xm[k] = ((ty[k] >> 15) & 1u) ? (k == 0 ? yl : y[k > 0 ? k - 1 : 0]) : y[k];
         xp[k] = (ty[k] >> 31) ? (k == 3 ? yr : y[k < 3 ? k + 1 : 0]) : y[k];
     }
-    float hw[4];
+    float hw[4], hr[4];
     uint32_t qw[2];
 #pragma unroll
     for (int h2 = 0; h2 < 2; ++h2) {
@@ -485,10 +515,13 @@ __device__ __forceinline__ void dom4_packed(uint32_t i0, const uint32_t (&ty)[4]
         const bool ma = (act_bits >> a) & 1u, mb = (act_bits >> b) & 1u;
         hw[a] = ma ? H.x : hn.x;
         hw[b] = mb ? H.y : hn.y;
+        hr[a] = hn.x;
+        hr[b] = hn.y;
         qw[h2] = ((ma ? rq : qn) & 0xffffu) | ((mb ? rq : qn) & 0xffff0000u);
     }
     st_floats<4>(io.out[1] + i0, hw);
     *reinterpret_cast<uint2 *>(io.lout[1] + i0) = make_uint2(qw[0], qw[1]);
+    if (REC) st_floats<4>(rec_y2 + i0, hr);
 }
 
 // K consecutive nodes per thread (i0 a multiple of K, K = 2 or 4): table_node for nodes i0 ..
@@ -498,8 +531,10 @@ __device__ __forceinline__ void dom4_packed(uint32_t i0, const uint32_t (&ty)[4]
 // the last group of the range takes the per-node path.  The -x neighbour of the first node is the
 // previous lane's last node and the +x neighbour of the last node the next lane's first node.
 // Arithmetic and slot order per node are those of table_node, so the results are the same bits.
-// Rows and tables start on 16-byte boundaries (row strides are multiples of 64 values).  REC (fused
-// passes only): also writes the pass record of the discrete adjoint.  MODE 4 is the first half of
+// Rows and tables start on 16-byte boundaries (row strides are multiples of 64 values).  REC: also
+// writes the pass record of the discrete adjoint (MODE 1: X and the transformed DOM; MODE 4: h + l of
+// every node's rounded DOM pair into rec.y2, which the second half overwrites at the marked nodes
+// with their transformed DOM).  MODE 4 is the first half of
 // the sparse fused pass: the DOM of every node is diffused and rounded as in MODE 1; a node whose
 // bit in the activity mask is clear has its DOM stored as MODE 1 stores a DOM that the (identity)
 // transformation left unchanged, a marked node the rounded pair itself (the second half, over the
@@ -539,32 +574,37 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
     if (i0 >= n) return;
     if constexpr (MODE == 4 && WM == W_UNIT && PREC == P_COMP && K == 4) {
         if (full) {
-            dom4_packed(i0, ty, y, yl, yr, ym, yp, zv, zw, x2, act_bits, p, io);
+            dom4_packed<REC>(i0, ty, y, yl, yr, ym, yp, zv, zw, x2, act_bits, p, io, rec.y2);
             return;
         }
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float acc = 0.0f;
-        auto add = [&](int slot, float yj) {
-            const float d = __fsub_rn(y[k], yj);
-            if (WM == W_UNIT) acc = __fadd_rn(acc, d);
-            else acc = __fmaf_rn(table_theta(bt, bn[k], slot), d, acc);
-        };
-        if ((ty[k] >> 15) & 1u) add(0, k == 0 ? yl : y[k > 0 ? k - 1 : 0]);
-        if (ty[k] >> 31) add(1, k == K - 1 ? yr : y[k < K - 1 ? k + 1 : 0]);
-        if (ty[k] & 0x7fffu) add(2, ym[k]);
-        if ((ty[k] >> 16) & 0x7fffu) add(3, yp[k]);
-        if (zm[k]) add(4, zv[k]);
-        if (zp[k]) add(5, zw[k]);
+        if (WM == W_BLOCK) {  // every slot, branch-free: an absent one adds g * (+0), which changes nothing
+            const float nb[6] = {((ty[k] >> 15) & 1u) ? (k == 0 ? yl : y[k > 0 ? k - 1 : 0]) : y[k],
+                                 (ty[k] >> 31) ? (k == K - 1 ? yr : y[k < K - 1 ? k + 1 : 0]) : y[k],
+                                 ym[k], yp[k], zv[k], zw[k]};
+#pragma unroll
+            for (int d = 0; d < 6; ++d) acc = __fmaf_rn(table_theta_sel(bt, bn[k], d), __fsub_rn(y[k], nb[d]), acc);
+        } else {
+            auto add = [&](float yj) { acc = __fadd_rn(acc, __fsub_rn(y[k], yj)); };
+            if ((ty[k] >> 15) & 1u) add(k == 0 ? yl : y[k > 0 ? k - 1 : 0]);
+            if (ty[k] >> 31) add(k == K - 1 ? yr : y[k < K - 1 ? k + 1 : 0]);
+            if (ty[k] & 0x7fffu) add(ym[k]);
+            if ((ty[k] >> 16) & 0x7fffu) add(yp[k]);
+            if (zm[k]) add(zv[k]);
+            if (zp[k]) add(zw[k]);
+        }
         vadd<PREC>(x2[k], __fmul_rn(-p.c, acc));  // Scheme 1
     }
     if (MODE == 4) {
-        float h[K];
+        float h[K], hr[K];
         res_t q[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             vround<PREC>(x2[k]);
+            hr[k] = __fadd_rn(x2[k].h, x2[k].l);  // REC: the adjoint's record of the rounded pair
             if ((act_bits >> k) & 1u) {  // the rounded pair itself
                 h[k] = x2[k].h;
                 q[k] = PREC == P_COMP ? res_encode(x2[k].l, h[k]) : (res_t)0;
@@ -578,12 +618,14 @@ __device__ __forceinline__ void table_vec(uint32_t i0, uint32_t n, const NbrTabl
         if (full) {
             st_floats<K>(io.out[1] + i0, h);
             if (PREC == P_COMP) st_res<K>(io.lout[1] + i0, q);
+            if (REC) st_floats<K>(rec.y2 + i0, hr);
         } else {
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 if (i0 + k < n) {
                     io.out[1][i0 + k] = h[k];
                     if (PREC == P_COMP) io.lout[1][i0 + k] = q[k];
+                    if (REC) rec.y2[i0 + k] = hr[k];
                 }
         }
         return;

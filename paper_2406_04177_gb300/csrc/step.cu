@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 
 #include "physics.cuh"
 #include "stencil.cuh"
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_stencil(Topo t, const int32_t *__r
         for_each_neighbour(i, k, fl, s_nb, cap, [&](int slot, int64_t j) {
             const float d = __fsub_rn(yi, __ldg(Y2 + j));
             if (WM == W_UNIT) acc = __fadd_rn(acc, d);
-            else acc = __fmaf_rn(block_theta(bw, slot, x, y, z), d, acc);
+            else acc = __fmaf_rn(edge_g(bw, i, slot, x, y, z), d, acc);
         });
         vadd<PREC>(x2, __fmul_rn(-p.c, acc));  // Scheme 1: y_i - D dt sum_j g_ij (y_i - y_j)
         if (MODE == 1) {
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(NT) k_stencil_staged(Topo t, const int32_t *__
             const float yj = (jj >= 0 && jj < nv) ? sh2[jj] : __ldg(Y2 + j);
             const float d = __fsub_rn(yi, yj);
             if (WM == W_UNIT) a = __fadd_rn(a, d);
-            else a = __fmaf_rn(block_theta(bw, slot, x, y, z), d, a);
+            else a = __fmaf_rn(edge_g(bw, i, slot, x, y, z), d, a);
         });
         acc[u] = a;
     }
@@ -1032,9 +1033,31 @@ vga_status build_nbr_table(const Topo &t, uint32_t *ty, uint32_t *tzm, uint32_t 
     return VGA_OK;
 }
 
+// The per-face table: node i is its own block with every slot crossing (table_theta reads g6[6 i + d],
+// table_face gives 6 i + d).
+__global__ void k_face_nodes(int64_t n, uint32_t *__restrict__ node) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) node[i] = (uint32_t)i | 0xfc000000u;
+}
+
 vga_status sim_block_table(vga_sim *s, BlockTable *out, bool *ok) {
     *ok = false;
     if (s->wmode != W_BLOCK) return VGA_OK;
+    if (s->face_mode) {
+        if (s->n >= kMaxTableBlocks) return VGA_OK;
+        if (!s->fnode) {
+            VGA_TRY(dmalloc((void **)&s->fnode, sizeof(uint32_t) * (size_t)std::max<int64_t>(s->npad, 64), "face table"));
+            if (s->n > 0) k_face_nodes<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, s->fnode);
+            VGA_CHECK_LAUNCH();
+            ++s->launches;
+        }
+        out->node = s->fnode;
+        out->face = nullptr;
+        out->theta = nullptr;
+        out->theta6 = s->g6;
+        *ok = true;
+        return VGA_OK;
+    }
     const int64_t nb = (int64_t)s->bw.nbx * s->bw.nby * s->bw.nbz;
     if (nb >= kMaxTableBlocks) return VGA_OK;
     if (s->btable_bs != s->bw.bs) {
@@ -1078,6 +1101,79 @@ vga_status sim_block_table(vga_sim *s, BlockTable *out, bool *ok) {
     out->theta = s->bw.theta;
     out->theta6 = s->btheta6;
     *ok = true;
+    return VGA_OK;
+}
+
+// Per-face conductances: flags |= 1 where g6[6 i + d] differs from the opposite slot of the
+// neighbour (the flux of Sec. V.A is symmetric), and the largest sum over a node's edges.
+__global__ void k_face_check(int64_t n, NbrTable tb, const float *__restrict__ g6, int32_t *__restrict__ flags,
+                             unsigned int *__restrict__ rowmax) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float sum = 0.0f;
+    bool bad = false;
+    if (i < n) {
+        const uint32_t ty = __ldg(tb.ty + i), dzm = __ldg(tb.tzm + i), dzp = __ldg(tb.tzp + i);
+        const int64_t j[6] = {(ty >> 15) & 1u ? i - 1 : -1, (ty >> 31) ? i + 1 : -1,
+                              (ty & 0x7fffu) ? i - (int64_t)(ty & 0x7fffu) : -1,
+                              ((ty >> 16) & 0x7fffu) ? i + (int64_t)((ty >> 16) & 0x7fffu) : -1,
+                              dzm ? i - (int64_t)dzm : -1, dzp ? i + (int64_t)dzp : -1};
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            if (j[d] < 0) continue;
+            const float g = __ldg(g6 + 6 * i + d);
+            sum += g;
+            bad |= __float_as_uint(g) != __float_as_uint(__ldg(g6 + 6 * j[d] + (d ^ 1)));
+        }
+    }
+    if (bad) atomicOr(flags, 1);
+    unsigned int m = __float_as_uint(sum);  // sums are >= 0: their bits order like the values
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(rowmax, m);
+}
+
+// Gradients of per-face conductances are accumulated in the +x, +y, +z slot of each edge; this copies
+// each into the opposite slot of the neighbour, so both slots of an edge hold its derivative.
+__global__ void k_face_mirror(int64_t n, NbrTable tb, double *__restrict__ g) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t ty = __ldg(tb.ty + i), dzp = __ldg(tb.tzp + i);
+    if (ty >> 31) g[6 * (i + 1) + 0] = g[6 * i + 1];
+    if ((ty >> 16) & 0x7fffu) g[6 * (i + (int64_t)((ty >> 16) & 0x7fffu)) + 2] = g[6 * i + 3];
+    if (dzp) g[6 * (i + (int64_t)dzp) + 4] = g[6 * i + 5];
+}
+
+vga_status sim_face_check(vga_sim *s, const float *d_g6, bool *symmetric, float *rowmax) {
+    *symmetric = true;
+    *rowmax = 0.0f;
+    if (s->n == 0) return VGA_OK;
+    NbrTable tb;
+    VGA_TRY(sim_nbr_table(s, &tb));
+    unsigned int *d = nullptr;
+    VGA_TRY(dmalloc((void **)&d, 2 * sizeof(unsigned int), "face check"));
+    unsigned int h[2] = {0u, 0u};
+    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(unsigned int), s->stream);
+    if (e == cudaSuccess) {
+        k_face_check<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, tb, d_g6, reinterpret_cast<int32_t *>(d),
+                                                                        d + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    dfree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "k_face_check", __FILE__, __LINE__);
+    ++s->launches;
+    *symmetric = h[0] == 0u;
+    std::memcpy(rowmax, &h[1], sizeof(float));
+    return VGA_OK;
+}
+
+vga_status sim_face_mirror(vga_sim *s, double *d_g) {
+    if (s->n == 0) return VGA_OK;
+    NbrTable tb;
+    VGA_TRY(sim_nbr_table(s, &tb));
+    k_face_mirror<<<grid_for(s->n, kThreads), kThreads, 0, s->stream>>>(s->n, tb, d_g);
+    VGA_CHECK_LAUNCH();
+    ++s->launches;
     return VGA_OK;
 }
 

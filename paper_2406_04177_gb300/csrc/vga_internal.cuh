@@ -154,6 +154,10 @@ struct BlockWeights {
     int32_t nbx = 0, nby = 0, nbz = 0;
     int64_t off_y = 0, off_z = 0;  // offsets of the y- and z-normal faces in theta
     const float *theta = nullptr;  // device
+    // Per-face conductances (vga_sim_set_face_conductances): g6[6 i + d] is the conductance of the edge
+    // leaving node i through slot d; when set, it replaces the block lookup and the gradient of that
+    // edge goes to index 6 i + d (odd slots: each edge once).
+    const float *g6 = nullptr;
 };
 
 // ---------------------------------------------------------------------------------------------
@@ -218,6 +222,9 @@ struct vga_sim {
     float *theta = nullptr;
     int64_t n_theta = 0;
     float max_g = 1.0f;
+    float *g6 = nullptr;            // per-face conductances (6 x n, device) when face_mode
+    bool face_mode = false;         // W_BLOCK kernels read g6 instead of the block faces
+    uint32_t *fnode = nullptr;      // BlockTable.node of the per-face table (node i, every slot crossing)
     // reductions
     double *partials = nullptr;  // per-block FP64 partial sums
     int64_t partials_cap = 0;
@@ -311,6 +318,10 @@ vga_status sim_transform_pass(vga_sim *s);  // Y = T(X) for every node, all comp
 int64_t sim_ticks_before(const vga_sim *s, int64_t k);  // transformations in the first k steps
 int sim_ticks_of_step(const vga_sim *s, int64_t k);      // transformations before diffusion step k
 vga_status sim_nbr_table(vga_sim *s, NbrTable *out);  // builds the table on first use
+// Per-face conductances (6 x n, device): symmetric across every edge?, largest sum over a node's edges.
+vga_status sim_face_check(vga_sim *s, const float *d_g6, bool *symmetric, float *rowmax);
+// Copies each edge's gradient from its +x/+y/+z slot into the neighbour's opposite slot (6 x n, device).
+vga_status sim_face_mirror(vga_sim *s, double *d_g);
 // block.cu: P fused passes of a sparse step call as temporally blocked launches (variant 6); *done
 // is false (and nothing ran) when the graph, the conductances or the marked nodes do not allow it.
 vga_status sim_block_fused(vga_sim *s, int64_t P, bool *done);

@@ -221,3 +221,44 @@ def test_block_fit_reduced_config(vga, oracle_lib):
     grad, gth = sim.adjoint_backward(dldx, n_theta=theta.size)
     assert rel_l2(gth, gref) <= GRAD_TOL
     assert _close(grad["D"], ref["grad"]["D"], GRAD_TOL)
+
+
+@pytest.mark.parametrize("block", [False, True])
+@pytest.mark.parametrize("marked", ["paper", "organic", "none"])
+def test_sparse_reverse_matches_dense(vga, oracle_lib, block, marked):
+    """Records of the marked nodes only and reverse steps that skip the rate-gradient terms at the
+    unmarked nodes (activity mask of X^0) give the bits of the dense records and reverse steps:
+    dL/dX^0 and the eight parameter gradients exactly, the block-face gradients up to the order of
+    their FP64 atomic sums.  Marked sets: the Sec. IV.C state (biomass on 1% of the nodes), biomass
+    and organic matter wherever DOM sits, and none (DOM only: every node unmarked)."""
+    img = synth.pore_mask((40, 36, 44), 0.25, 7)
+    og = oracle_lib.graph_build(img)
+    g = vga.Graph(img)
+    kept = synth.kept_mask_from_nodes(img.shape, og.voxel_of_node)
+    X0 = synth.initial_masses(kept, 7, with_organic_matter=(marked == "organic"))
+    if marked == "organic":
+        X0[0] = np.where(X0[1] > 0, 0.3 * X0[1], X0[0]).astype(np.float32)
+    if marked == "none":
+        X0[[0, 2, 3, 4]] = 0.0
+    bs = 8
+    theta = synth.block_conductances(oracle_lib.block_grid(img.shape, bs), 4) if block else None
+    p = synth.paper_params(dt=0.9 / (6 * synth.D_DOM * (theta.max() if block else 1.0)))
+    lamN = np.random.default_rng(19).standard_normal((5, og.n))
+    out = []
+    for skip in (True, False):
+        sim = vga.Sim(g, p)
+        sim.set_activity_skip(skip)
+        if block:
+            sim.set_block_conductances(bs, theta.astype(np.float32))
+        sim.set_masses(X0)
+        sim.adjoint_forward(45, 8)  # six recomputed segments and the recorded last one (5 steps)
+        lam0 = np.empty((5, og.n))
+        grad, gth = sim.adjoint_backward(lamN, lam0, n_theta=0 if theta is None else theta.size)
+        out.append((lam0, grad, gth, sim.save_state()))
+        sim.close()
+    (l_s, g_s, t_s, x_s), (l_d, g_d, t_d, x_d) = out
+    assert x_s == x_d
+    assert np.array_equal(l_s, l_d)
+    assert g_s == g_d
+    if block:
+        assert np.allclose(t_s, t_d, rtol=1e-12, atol=1e-15 * np.abs(t_d).max())
