@@ -246,7 +246,9 @@ vga_status vga_sim_get_stats(vga_sim *s, vga_sim_stats *out);
 
 /* Advances n_steps from the current state X^0, storing a checkpoint every ckpt_every steps; the
  * simulation ends at X^N exactly as vga_sim_step would leave it.  Device memory: one state per
- * checkpoint (30 bytes per node) plus ckpt_every recorded steps (24 bytes per node each).
+ * checkpoint (30 bytes per node) plus ckpt_every recorded steps: 4 bytes per node each when the
+ * activity skip is on (the default: X^k is recorded for the nodes with MB, SOM, FOM or CO2 at X^0,
+ * 16 bytes per such node), else 24 bytes per node each.
  * Errors: VGA_ERR_UNSUPPORTED unless scheme = explicit, transform = sync and state_precision =
  * compensated; VGA_ERR_INVALID_ARG for n_steps < 0 or ckpt_every < 1. */
 vga_status vga_adjoint_forward(vga_sim *s, int64_t n_steps, int32_t ckpt_every);
@@ -255,8 +257,10 @@ vga_status vga_adjoint_forward(vga_sim *s, int64_t n_steps, int32_t ckpt_every);
  * last vga_adjoint_forward.  Outputs: dL_dX0 (5 x n FP64 in the same memory space, or NULL);
  * grad_params[8] (host) = dL/d(D, rho, mu, beta, v_som, v_fom, v_dom, K_dom); grad_theta (host,
  * n_theta doubles in the layout of vga_sim_set_block_conductances, or NULL; zero without block
- * conductances).  The state stays at X^N.  Errors: VGA_ERR_INVALID_ARG if no forward pass was run
- * or the parameters or conductances changed since. */
+ * conductances).  dL_dX0 and grad_params are the same bits on every run; the conductance gradients
+ * are sums of FP64 atomics, whose last bits can depend on their order.  The state stays at X^N.
+ * Errors: VGA_ERR_INVALID_ARG if no forward pass was run or the parameters or conductances changed
+ * since. */
 vga_status vga_adjoint_backward(vga_sim *s, const double *dL_dXN, int32_t on_device, double *dL_dX0,
                                 double *grad_params, double *grad_theta);
 

@@ -32,8 +32,13 @@ namespace {
 
 constexpr int kThreads = 256;
 #ifndef VGA_ADJ_MIN_BLOCKS
-#define VGA_ADJ_MIN_BLOCKS 2  // resident blocks per SM the reverse step is compiled for
+#define VGA_ADJ_MIN_BLOCKS 4  // resident blocks per SM the reverse step is compiled for
 #endif
+#ifndef VGA_ADJ_K
+#define VGA_ADJ_K 2  // consecutive nodes per thread in the reverse step (2 or 4)
+#endif
+constexpr int kAdjK = VGA_ADJ_K;
+static_assert(kAdjK == 2 || kAdjK == 4, "the reverse step takes 2 or 4 nodes per thread");
 constexpr int kPar = GR_COUNT + 1;  // per-block partial slots: 7 rate slots + D
 
 struct Rec {
@@ -320,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, VGA_ADJ_MIN_BLOCKS) k_adjoint_vec(in
                                                           StateIO io, int64_t npad, const float *__restrict__ xk,
                                                           const float *__restrict__ y2k, SparseState ss, int64_t xcap,
                                                           double *__restrict__ gpart, double *__restrict__ gtheta) {
-    constexpr int K = 4;
+    constexpr int K = kAdjK;
     const float *__restrict__ L2 = io.in[1];
     CAcc acc[kPar];
     const float mc = -p.c;
@@ -356,8 +361,6 @@ __global__ void __launch_bounds__(kThreads, VGA_ADJ_MIN_BLOCKS) k_adjoint_vec(in
             yr = __ldg(y2k + (i0 + K));
         }
         float lsum[K];
-        int32_t face[K][3];
-        float fval[K][3];
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             const bool live = i0 + k < nn;
@@ -389,19 +392,12 @@ __global__ void __launch_bounds__(kThreads, VGA_ADJ_MIN_BLOCKS) k_adjoint_vec(in
                 const float dy = __fsub_rn(yi[k], yw[d]);
                 ls = __fmaf_rn(g, dl, ls);
                 ys = __fmaf_rn(g, dy, ys);
-                if (WM == W_BLOCK && (d & 1)) {  // +x, +y, +z: each edge once
-                    face[k][d >> 1] = table_face_sel(bt, bn[k], d, (mask >> d) & 1u);
-                    fval[k][d >> 1] = __fmul_rn(__fmul_rn(mc, dy), dl);
-                }
+                if (WM == W_BLOCK && (d & 1))  // +x, +y, +z: each edge once
+                    face_atomic_add_f(gtheta, table_face_sel(bt, bn[k], d, (mask >> d) & 1u),
+                                      __fmul_rn(__fmul_rn(mc, dy), dl));
             }
             lsum[k] = ls;
             if (live) cacc_add_prod(acc[GR_COUNT], -li[k], ys);
-        }
-        if (WM == W_BLOCK) {
-#pragma unroll
-            for (int k = 0; k < K; ++k)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) face_atomic_add_f(gtheta, face[k][q], fval[k][q]);
         }
         if (i0 >= nn) continue;
         // the other compartments and the recorded X^k (MB, DOM, SOM, FOM: the reverse transformation
@@ -968,7 +964,7 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
             VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_adjoint_vec<WM, PREC, 0, 0>, kThreads, 0));
             VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_adjoint_vec<WM, PREC, 0, 1>, kThreads, 0));
         }
-        const int64_t groups = (s->n + 4 * kThreads - 1) / (4 * kThreads);
+        const int64_t groups = (s->n + kAdjK * kThreads - 1) / (kAdjK * kThreads);
         Gt = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, std::min(occ0, occ1)) * sms, groups));
     }
     const int Gv = (int)(((s->n + 3) / 4 + kThreads - 1) / kThreads);  // four nodes per thread

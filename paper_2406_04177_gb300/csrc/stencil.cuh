@@ -142,11 +142,10 @@ __device__ __forceinline__ int32_t table_face(const BlockTable &bt, uint32_t bn,
     return __ldg(bt.face + 6 * (size_t)(bn & 0x3ffffffu) + slot);
 }
 
-// Branch-free forms for loops that visit every slot: the loads are made for every node (the
-// address is valid for any block id, including the 0 of a lane past the end), then selected.
+// Forms for loops that visit every slot without branching: the lookups are selects (the addresses
+// are valid for any block id, including the 0 of a lane past the end).
 __device__ __forceinline__ float table_theta_sel(const BlockTable &bt, uint32_t bn, int slot) {
-    const float t = __ldg(bt.theta6 + 6 * (size_t)(bn & 0x3ffffffu) + slot);
-    return ((bn >> (26 + slot)) & 1u) ? t : 1.0f;
+    return ((bn >> (26 + slot)) & 1u) ? __ldg(bt.theta6 + 6 * (size_t)(bn & 0x3ffffffu) + slot) : 1.0f;
 }
 
 // table_face for an edge that exists, -1 otherwise.
