@@ -148,11 +148,12 @@ __device__ __forceinline__ float table_theta_sel(const BlockTable &bt, uint32_t 
     return ((bn >> (26 + slot)) & 1u) ? __ldg(bt.theta6 + 6 * (size_t)(bn & 0x3ffffffu) + slot) : 1.0f;
 }
 
-// table_face for an edge that exists, -1 otherwise.
+// table_face for an edge that exists, -1 otherwise (the face table is read only for a crossing edge).
 __device__ __forceinline__ int32_t table_face_sel(const BlockTable &bt, uint32_t bn, int slot, bool exists) {
     const uint32_t b = bn & 0x3ffffffu;
-    const int32_t f = bt.face ? __ldg(bt.face + 6 * (size_t)b + slot) : (int32_t)(6 * b) + slot;
-    return (exists && ((bn >> (26 + slot)) & 1u)) ? f : -1;
+    const bool cross = exists && ((bn >> (26 + slot)) & 1u);
+    if (!bt.face) return cross ? (int32_t)(6 * b) + slot : -1;
+    return cross ? __ldg(bt.face + 6 * (size_t)b + slot) : -1;
 }
 
 // Conductance of the edge leaving node i (at x, y, z) through `slot`: per-face, else per block face.
