@@ -171,45 +171,6 @@ __global__ void __launch_bounds__(kThreads) k_adjoint_step(Topo t, const int32_t
     if (threadIdx.x < kPar) gpart[(int64_t)blockIdx.x * kPar + threadIdx.x] += out[threadIdx.x];
 }
 
-// Values of the six neighbours of node i from the offset table (0 where absent); +-x by shuffles.
-struct Nb6 {
-    float v[6];
-    uint32_t mask;  // bit d: neighbour in slot d exists
-};
-
-// TF 1: compact z offsets (NbrTable.tz).
-template <int TF>
-__device__ __forceinline__ Nb6 gather6(const NbrTable &tb, uint32_t i, bool live, float vi,
-                                       const float *__restrict__ a) {
-    Nb6 r;
-    const uint32_t ty = live ? __ldg(tb.ty + i) : 0u;
-    uint32_t dzm, dzp;
-    if (TF == 1) {
-        const uint32_t tz = live ? __ldg(tb.tz + i) : 0u;
-        dzm = tz & 0xffffu;
-        dzp = tz >> 16;
-    } else {
-        dzm = live ? __ldg(tb.tzm + i) : 0u;
-        dzp = live ? __ldg(tb.tzp + i) : 0u;
-    }
-    const int lane = threadIdx.x & 31;
-    float vl = __shfl_up_sync(0xffffffffu, vi, 1);
-    float vr = __shfl_down_sync(0xffffffffu, vi, 1);
-    const uint32_t dym = ty & 0x7fffu, dyp = (ty >> 16) & 0x7fffu;
-    const uint32_t hxm = (ty >> 15) & 1u, hxp = ty >> 31;
-    if (lane == 0 && hxm) vl = __ldg(a + (i - 1));
-    if (lane == 31 && hxp) vr = __ldg(a + (i + 1));
-    r.v[0] = vl;
-    r.v[1] = vr;
-    r.v[2] = dym ? __ldg(a + (i - dym)) : 0.0f;
-    r.v[3] = dyp ? __ldg(a + (i + dyp)) : 0.0f;
-    r.v[4] = dzm ? __ldg(a + (i - dzm)) : 0.0f;
-    r.v[5] = dzp ? __ldg(a + (i + dzp)) : 0.0f;
-    r.mask = hxm | (hxp << 1) | ((uint32_t)(dym != 0) << 2) | ((uint32_t)(dyp != 0) << 3) |
-             ((uint32_t)(dzm != 0) << 4) | ((uint32_t)(dzp != 0) << 5);
-    return r;
-}
-
 // Table-driven fused pass with recording: four nodes per thread (table_vec, the forward's own body, so the recomputed
 // trajectory is the forward's bit for bit), recording X^k and y2^k as vectors.
 template <int WM, int PREC, int TF>
@@ -310,7 +271,7 @@ __device__ __forceinline__ void face_atomic_add_f(double *gtheta, int32_t f, flo
 // ids, the five adjoint compartments, the recorded X^k and y2^k) move as 16-byte FP32 / table vectors
 // and 8-byte residual vectors, so a warp issues a quarter of the memory instructions and address
 // computations of the one-node kernel; the -x / +x neighbours of a group's end nodes come from the
-// adjacent lanes.  Per node the arithmetic is k_adjoint_table's (same slot order, same operations),
+// adjacent lanes.  Per node the arithmetic is k_adjoint_step's (same slot order, same operations),
 // so dL/dX^k is the same bits; the per-thread gradient sums take the nodes in another order.
 // The CO2 adjoint is read (respiration's weight) but not stored: no flux depends on CO2, so a step
 // leaves it unchanged and the caller passes one buffer as its input and output.
@@ -482,73 +443,6 @@ __global__ void __launch_bounds__(kThreads, VGA_ADJ_MIN_BLOCKS) k_adjoint_vec(in
             vstore_k<PREC, K, false>(io.out[2], io.lout[2], i0, nn, m2);
             vstore_k<PREC, K, false>(io.out[3], io.lout[3], i0, nn, m3);
         }
-    }
-    double accd[kPar];
-#pragma unroll
-    for (int q = 0; q < kPar; ++q) accd[q] = (double)acc[q].s + (double)acc[q].c;
-    __shared__ double out[kPar];
-    block_sum_store<kPar>(accd, out);
-    if (threadIdx.x < kPar) gpart[(int64_t)blockIdx.x * kPar + threadIdx.x] += out[threadIdx.x];
-}
-
-// Table-driven reverse step (same arithmetic as k_adjoint_step), grid-stride over 256-node tiles.
-template <int WM, int PREC, int TF>
-__global__ void __launch_bounds__(kThreads, 5) k_adjoint_table(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
-                                                            StateIO io, int64_t npad, const float *__restrict__ xk,
-                                                            const float *__restrict__ y2k, double *__restrict__ gpart,
-                                                            double *__restrict__ gtheta) {
-    const float *__restrict__ L2 = io.in[1];
-    CAcc acc[kPar];  // compensated FP32 per thread, reduced in FP64 per block
-    const float mc = -p.c;
-    const int64_t ntile = (n + kThreads - 1) / kThreads;
-    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const uint32_t i = (uint32_t)(tile * kThreads + threadIdx.x);
-        const bool live = i < (uint64_t)n;
-        V mu[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) mu[c] = live ? vload<PREC>(io.in[c], io.lin[c], i) : V{0.0f, 0.0f};
-        const float li = mu[1].h;
-        const float yi = live ? __ldg(y2k + i) : 0.0f;
-        const Nb6 nl = gather6<TF>(tb, i, live, li, L2);
-        const Nb6 ny = gather6<TF>(tb, i, live, yi, y2k);
-        const uint32_t bn = (WM == W_BLOCK && live) ? __ldg(bt.node + i) : 0u;
-        float lsum = 0.0f, ysum = 0.0f;
-        int32_t face[3] = {-1, -1, -1};
-        float fval[3] = {0.0f, 0.0f, 0.0f};
-        if (live) {
-#pragma unroll
-            for (int d = 0; d < 6; ++d) {
-                if (!((nl.mask >> d) & 1u)) continue;
-                const float g = (WM == W_UNIT) ? 1.0f : table_theta(bt, bn, d);
-                const float dl = __fsub_rn(li, nl.v[d]);
-                const float dy = __fsub_rn(yi, ny.v[d]);
-                lsum = __fmaf_rn(g, dl, lsum);
-                ysum = __fmaf_rn(g, dy, ysum);
-                if (WM == W_BLOCK && (d & 1)) {  // +x, +y, +z: each edge once
-                    face[d >> 1] = table_face(bt, bn, d);
-                    fval[d >> 1] = __fmul_rn(__fmul_rn(mc, dy), dl);
-                }
-            }
-        }
-        if (WM == W_BLOCK) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) face_atomic_add_f(gtheta, face[q], fval[q]);
-        }
-        if (!live) continue;
-        cacc_add_prod(acc[GR_COUNT], -li, ysum);
-        vadd<PREC>(mu[1], __fmul_rn(-p.c, lsum));
-        float xs[5];
-#pragma unroll
-        for (int c = 0; c < 5; ++c) xs[c] = __ldg(xk + c * npad + i);
-        float gr[GR_COUNT];
-#pragma unroll
-        for (int q = 0; q < GR_COUNT; ++q) gr[q] = 0.0f;
-        V lam[5];
-        transform_sync_reverse<PREC>(xs, mu, lam, gr, p);
-#pragma unroll
-        for (int q = 0; q < GR_COUNT; ++q) cacc_add(acc[q], gr[q]);
-#pragma unroll
-        for (int c = 0; c < 5; ++c) vstore<PREC>(io.out[c], io.lout[c], i, lam[c]);
     }
     double accd[kPar];
 #pragma unroll

@@ -345,25 +345,89 @@ __global__ void k_build_list(int64_t n, SparseState ss, uint32_t *__restrict__ l
     if (m & bit) list[__ldg(ss.prefix + w) + __popc(m & (bit - 1u))] = (uint32_t)i;
 }
 
-// Exclusive prefix of the marked nodes per mask word (one block; once per state upload).
-__global__ void __launch_bounds__(1024) k_scan_mask(int64_t words, const uint32_t *__restrict__ mask,
-                                                     uint32_t *__restrict__ prefix) {
-    __shared__ uint32_t part[1024];
-    const int64_t per = (words + 1023) / 1024, w0 = threadIdx.x * per, w1 = min(words, w0 + per);
-    uint32_t sum = 0;
-    for (int64_t w = w0; w < w1; ++w) sum += __popc(mask[w]);
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {  // inclusive scan of the per-thread sums
-        const uint32_t t = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += t;
-        __syncthreads();
+// Exclusive prefix of the marked nodes per mask word (once per state upload), in three coalesced
+// phases over tiles of kScanTile words: the popcount of every tile, the exclusive scan of those
+// counts, then each tile's words scanned from its tile's offset.  Thread t of a tile holds its
+// words 8 t .. 8 t + 7 (32 contiguous bytes).
+constexpr int kScanWords = 8;
+constexpr int kScanTile = kThreads * kScanWords;
+
+inline int64_t mask_tiles(int64_t words) { return (words + kScanTile - 1) / kScanTile; }
+
+// Exclusive scan over the block of one value per thread; *total gets the block's sum.
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t *total) {
+    __shared__ uint32_t ws[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
     }
-    uint32_t run = part[threadIdx.x] - sum;
-    for (int64_t w = w0; w < w1; ++w) {
-        prefix[w] = run;
-        run += __popc(mask[w]);
+    if (lane == 31) ws[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t y = lane < nwarp ? ws[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += t;
+        }
+        ws[lane] = y;
+    }
+    __syncthreads();
+    const uint32_t before = (wid > 0 ? ws[wid - 1] : 0u) + x - v;
+    *total = ws[nwarp - 1];
+    __syncthreads();
+    return before;
+}
+
+__device__ __forceinline__ void mask_words(int64_t words, const uint32_t *__restrict__ mask, int64_t w0,
+                                           uint32_t (&m)[kScanWords]) {
+#pragma unroll
+    for (int j = 0; j < kScanWords; ++j) m[j] = w0 + j < words ? __ldg(mask + w0 + j) : 0u;
+}
+
+__global__ void __launch_bounds__(kThreads) k_mask_tile_count(int64_t words, const uint32_t *__restrict__ mask,
+                                                              uint32_t *__restrict__ tile_sum) {
+    uint32_t m[kScanWords];
+    mask_words(words, mask, (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanWords, m);
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < kScanWords; ++j) c += __popc(m[j]);
+    uint32_t total;
+    block_excl_scan_u32(c, &total);
+    if (threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+// In place: tile_sum[t] <- the sum of the tiles before t (one block).
+__global__ void __launch_bounds__(kThreads) k_mask_tile_scan(int64_t tiles, uint32_t *__restrict__ tile_sum) {
+    uint32_t run = 0;
+    for (int64_t t0 = 0; t0 < tiles; t0 += kThreads) {
+        const int64_t t = t0 + threadIdx.x;
+        const uint32_t v = t < tiles ? tile_sum[t] : 0u;
+        uint32_t total;
+        const uint32_t before = block_excl_scan_u32(v, &total);
+        if (t < tiles) tile_sum[t] = run + before;
+        run += total;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mask_prefix(int64_t words, const uint32_t *__restrict__ mask,
+                                                          const uint32_t *__restrict__ tile_sum,
+                                                          uint32_t *__restrict__ prefix) {
+    const int64_t w0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanWords;
+    uint32_t m[kScanWords];
+    mask_words(words, mask, w0, m);
+    uint32_t c = 0;
+#pragma unroll
+    for (int j = 0; j < kScanWords; ++j) c += __popc(m[j]);
+    uint32_t total;
+    uint32_t run = __ldg(tile_sum + blockIdx.x) + block_excl_scan_u32(c, &total);
+#pragma unroll
+    for (int j = 0; j < kScanWords; ++j) {
+        if (w0 + j < words) prefix[w0 + j] = run;
+        run += __popc(m[j]);
     }
 }
 
@@ -813,10 +877,11 @@ SparseState activity_state(const Activity &a) {
 vga_status activity_build(Activity *a, int64_t n, int64_t npad, const StateIO &cur, const StateIO &spare, bool comp,
                           cudaStream_t st) {
     const int64_t nw = (std::max<int64_t>(npad, 64) + 31) / 32 + 8;
-    if (!a->words || a->nw < nw) {  // mask words, their prefix, a counter
+    if (!a->words || a->nw < nw) {  // mask words, their prefix, a counter, the tile sums of the prefix
         dfree(a->words);
         a->words = nullptr;
-        VGA_TRY(dmalloc((void **)&a->words, sizeof(uint32_t) * 2 * (size_t)nw + sizeof(unsigned long long),
+        VGA_TRY(dmalloc((void **)&a->words,
+                        sizeof(uint32_t) * (2 * (size_t)nw + (size_t)mask_tiles(nw)) + sizeof(unsigned long long),
                         "activity mask"));
         a->nw = nw;
         VGA_CUDA(cudaMemsetAsync(a->words, 0, sizeof(uint32_t) * 2 * (size_t)nw, st));
@@ -828,8 +893,14 @@ vga_status activity_build(Activity *a, int64_t n, int64_t npad, const StateIO &c
         else k_build_active<P_F32><<<grid_for(n, kThreads), kThreads, 0, st>>>(n, cur, spare, a->words, count);
         VGA_CHECK_LAUNCH();
     }
-    k_scan_mask<<<1, 1024, 0, st>>>(a->nw, a->words, a->words + a->nw);
-    VGA_CHECK_LAUNCH();
+    {
+        const int64_t tiles = mask_tiles(a->nw);
+        uint32_t *tile_sum = a->words + 2 * a->nw + 2;  // after the 64-bit counter
+        k_mask_tile_count<<<(unsigned)tiles, kThreads, 0, st>>>(a->nw, a->words, tile_sum);
+        k_mask_tile_scan<<<1, kThreads, 0, st>>>(tiles, tile_sum);
+        k_mask_prefix<<<(unsigned)tiles, kThreads, 0, st>>>(a->nw, a->words, tile_sum, a->words + a->nw);
+        VGA_CHECK_LAUNCH();
+    }
     unsigned long long h = 0;
     VGA_CUDA(cudaMemcpyAsync(&h, count, sizeof(h), cudaMemcpyDeviceToHost, st));
     VGA_CUDA(cudaStreamSynchronize(st));
