@@ -47,6 +47,25 @@ BYTES_PER_PVS = 40  # five FP32 compartments read and written per node and time 
 BYTES_DOM = 8       # the diffusing DOM read and written (FP32)
 
 
+def max_over_ranks(ms: float, world: int, device: str = "cuda") -> float:
+    """The whole job's time: the slowest rank's (all-reduce MAX over the process group); a single
+    rank's own time at world 1."""
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, units_per_rank: float, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed (each rank runs the same workload, a
+    replica) over the job's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -309,11 +328,8 @@ def bench_ours(a):
     timing = sim.read_timing(reset=True)
     sim.enable_timing(False)
     tot1 = sim.totals()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * S * a.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, world, "cuda")
+    value = job_value(world, n * S * a.steps, ms)
 
     fused_ms, fused_count = timing["fused_step"]
     mean_launch_s = fused_ms / max(fused_count, 1) / 1e3
@@ -377,11 +393,11 @@ def bench_ours(a):
         dtiming = sim.read_timing(reset=True)
         sim.enable_timing(False)
         sim.set_activity_skip(True)
-        dms = d0.elapsed_time(d1)
+        dms = max_over_ranks(d0.elapsed_time(d1), world, "cuda")
         dfm, dfc = dtiming["fused_step"]
         dmean = dfm / max(dfc, 1) / 1e3
         dach = BYTES_PER_PVS * n / dmean / 1e9
-        dense = {"value": world * n * S * dsteps / (dms / 1e3), "unit": UNIT, "steps": dsteps,
+        dense = {"value": job_value(world, n * S * dsteps, dms), "unit": UNIT, "steps": dsteps,
                  "ms_per_step": dms / dsteps, "mean_pass_ms": dmean * 1e3,
                  "roofline": {"bound": "hbm", "achieved": dach, "peak": peak, "unit": "GB/s", "frac": dach / peak,
                               "traffic": recorded_traffic(n, "dense"), "algorithmic_bytes_per_pass": BYTES_PER_PVS * n,
@@ -399,6 +415,8 @@ def bench_ours(a):
     torch.cuda.synchronize()
     e2e_sampler = ClockSampler(bus)
     e2e_sampler.start()
+    if world > 1:
+        dist.barrier()
     w0 = time.perf_counter()
     for _ in range(e2e_iters):
         sim.set_state_f32(xh_np)
@@ -407,7 +425,7 @@ def bench_ours(a):
         sim.get_state_f32(outh_np)
     w1 = time.perf_counter()
     e2e_clocks = e2e_sampler.stop()
-    e2e_val = world * n * S * e2e_iters / (w1 - w0)
+    e2e_val = job_value(world, n * S * e2e_iters, max_over_ranks((w1 - w0) * 1e3, world, "cuda"))
     e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 4),
            "d2h_bytes_per_step": int(outh.numel() * 4 + 5 * 8),
            "how": "per step: vga_sim_set_state_f32 from pinned host memory, vga_sim_step(substeps), "

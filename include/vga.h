@@ -154,6 +154,12 @@ vga_status vga_sim_set_params(vga_sim *s, const vga_params *p);
  * call fails with VGA_ERR_UNSTABLE_DT when 6 D dt max(1, max theta) > 1. */
 vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const float *theta,
                                           int64_t n_theta);
+/* The same with theta in device memory (d_theta, FP32, n_theta values, read on the simulation's
+ * stream): the values are checked on the device before they are copied (VGA_ERR_INVALID_ARG for a
+ * value that is not finite or is negative, leaving the previous conductances in place), and only a
+ * flag and the largest value come back to the host.  The caller keeps d_theta. */
+vga_status vga_sim_set_block_conductances_device(vga_sim *s, int32_t block_side, const float *d_theta,
+                                                 int64_t n_theta);
 /* Returns to unit conductances (g_ij = 1, Sec. II.B). */
 vga_status vga_sim_clear_conductances(vga_sim *s);
 
@@ -263,6 +269,13 @@ vga_status vga_adjoint_forward(vga_sim *s, int64_t n_steps, int32_t ckpt_every);
  * since. */
 vga_status vga_adjoint_backward(vga_sim *s, const double *dL_dXN, int32_t on_device, double *dL_dX0,
                                 double *grad_params, double *grad_theta);
+
+/* Copies the conductance gradient of the last vga_adjoint_backward (block or per-face conductances,
+ * FP64, the layout of grad_theta there) into grad_theta: n doubles, n = the number of conductances
+ * set (n_theta, or 6 n for per-face conductances), in device memory if on_device != 0, else host.
+ * Errors: VGA_ERR_INVALID_ARG without a completed backward sweep with conductances set, or for
+ * another n. */
+vga_status vga_adjoint_grad_theta(vga_sim *s, double *grad_theta, int32_t on_device, int64_t n);
 
 /* Normalised gradient step of Sec. V.A on the block conductances, using the theta gradient of the
  * last vga_adjoint_backward: theta <- clamp(theta - lr * g/|g|, theta_min, theta_max) element-wise

@@ -105,6 +105,7 @@ _SIGNATURES = {
     "vga_sim_create": [_P, _P, _P, _P],
     "vga_sim_set_params": [_P, _P],
     "vga_sim_set_block_conductances": [_P, _I32, _P, _I64],
+    "vga_sim_set_block_conductances_device": [_P, _I32, _P, _I64],
     "vga_sim_clear_conductances": [_P],
     "vga_sim_set_masses": [_P, _P, _I32],
     "vga_sim_get_masses": [_P, _P, _I32],
@@ -119,6 +120,7 @@ _SIGNATURES = {
     "vga_sim_get_stats": [_P, _P],
     "vga_adjoint_forward": [_P, _I64, _I32],
     "vga_adjoint_backward": [_P, _P, _I32, _P, _P, _P],
+    "vga_adjoint_grad_theta": [_P, _P, _I32, _I64],
     "vga_loss_block_mass": [_P, _I32, _U32, _P, _P, _P, _P],
     "vga_sgd_block_conductances": [_P, C.c_double, C.c_double, C.c_double],
     "vga_sim_get_block_conductances": [_P, _P, _I64],
@@ -288,6 +290,13 @@ def vga_sim_set_block_conductances(s, block_side: int, theta: np.ndarray):
                                                          theta.size), "vga_sim_set_block_conductances")
 
 
+def vga_sim_set_block_conductances_device(s, block_side: int, d_theta):
+    """d_theta: contiguous CUDA float32 tensor (checked on the device)."""
+    _check(load_library().vga_sim_set_block_conductances_device(s, int(block_side), _dev_ptr(d_theta, "float32"),
+                                                                d_theta.numel()),
+           "vga_sim_set_block_conductances_device")
+
+
 def vga_sim_clear_conductances(s):
     _check(load_library().vga_sim_clear_conductances(s), "vga_sim_clear_conductances")
 
@@ -382,6 +391,17 @@ def vga_adjoint_backward(s, dL_dXN, n: int, dL_dX0=None, n_theta: int = 0):
                                                None if gth is None else gth.ctypes.data_as(C.c_void_p)),
            "vga_adjoint_backward")
     return dict(zip(GRAD_NAMES, grad.tolist())), gth
+
+
+def vga_adjoint_grad_theta(s, out):
+    """Conductance gradient of the last backward sweep into `out` (numpy float64 array, or CUDA
+    float64 tensor), whose size is the number of conductances."""
+    if isinstance(out, np.ndarray):
+        ptr, dev, n = _host_ptr(out, np.float64), 0, out.size
+    else:
+        ptr, dev, n = _dev_ptr(out, "float64"), 1, out.numel()
+    _check(load_library().vga_adjoint_grad_theta(s, ptr, dev, int(n)), "vga_adjoint_grad_theta")
+    return out
 
 
 def vga_loss_block_mass(s, block_side: int, comp_mask: int, target: np.ndarray, n: int, dL_dX=None,
@@ -613,7 +633,11 @@ class Sim:
         self._base_params = dict(params)
 
     def set_block_conductances(self, block_side: int, theta):
-        vga_sim_set_block_conductances(self.handle, block_side, theta)
+        """theta: numpy array (host), or CUDA float32 tensor (device form)."""
+        if isinstance(theta, np.ndarray):
+            vga_sim_set_block_conductances(self.handle, block_side, theta)
+        else:
+            vga_sim_set_block_conductances_device(self.handle, block_side, theta)
 
     def clear_conductances(self):
         vga_sim_clear_conductances(self.handle)
@@ -683,6 +707,9 @@ class Sim:
 
     def adjoint_backward(self, dL_dXN, dL_dX0=None, n_theta: int = 0):
         return vga_adjoint_backward(self.handle, dL_dXN, self.n, dL_dX0, n_theta)
+
+    def adjoint_grad_theta(self, out):
+        return vga_adjoint_grad_theta(self.handle, out)
 
     def loss_block_mass(self, block_side: int, comp_mask: int, target, dL_dX=None, want_mass: bool = False):
         return vga_loss_block_mass(self.handle, block_side, comp_mask, target, self.n, dL_dX, want_mass)

@@ -2,7 +2,8 @@
 
     XN = VoxelGraphRun.apply(theta, rates, X0, sim, n_steps, ckpt, block_side)
 
-theta: block conductances (CUDA float64 tensor, or an empty tensor for unit conductances);
+theta: block conductances (CUDA tensor, or an empty tensor for unit conductances; it stays on the
+device: the library checks and copies it there, and the gradient comes back there);
 rates: CPU float64 tensor (D, rho, mu, beta, v_som, v_fom, v_dom, K_dom); X0: CUDA float64 (5, n).
 The forward runs the checkpointed forward pass of the library; the backward runs its discrete
 adjoint and returns dL/dtheta, dL/drates and dL/dX0.  The simulation object must not be used in
@@ -10,7 +11,6 @@ between (its checkpoints belong to the pending backward).
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import GRAD_NAMES
@@ -25,7 +25,7 @@ class VoxelGraphRun(torch.autograd.Function):
         params = dict(base, **{k: float(v) for k, v in zip(RATE_NAMES, rates.tolist())})
         sim.set_params(params)
         if theta.numel() > 0:
-            sim.set_block_conductances(block_side, theta.detach().cpu().numpy().astype(np.float32))
+            sim.set_block_conductances(block_side, theta.detach().to(torch.float32).contiguous())
         else:
             sim.clear_conductances()
         sim.set_masses(X0.detach().contiguous())
@@ -44,10 +44,11 @@ class VoxelGraphRun(torch.autograd.Function):
         g = grad_XN.detach().contiguous().to(torch.float64)
         dX0 = torch.empty_like(g)
         torch.cuda.current_stream(g.device).synchronize()
-        grad, gth = sim.adjoint_backward(g, dX0, n_theta=ctx.n_theta)
-        torch.cuda.synchronize(g.device)
-        gtheta = (torch.from_numpy(gth).to(ctx.theta_device) if ctx.n_theta > 0
-                  else torch.zeros(0, dtype=torch.float64, device=ctx.theta_device))
+        grad, _ = sim.adjoint_backward(g, dX0)
+        gtheta = torch.zeros(ctx.n_theta, dtype=torch.float64, device=g.device)
+        if ctx.n_theta > 0:
+            sim.adjoint_grad_theta(gtheta)
+        gtheta = gtheta.to(ctx.theta_device)
         grates = torch.tensor([grad[k] for k in RATE_NAMES], dtype=torch.float64)
         return gtheta, grates, dX0, None, None, None, None
 

@@ -610,6 +610,7 @@ struct AdjointBuffers {
     // the forward pass the checkpoints belong to
     bool valid = false;
     bool last_recorded = false;  // the records hold the last segment (written by the forward sweep)
+    bool grad_ready = false;     // gtheta holds the conductance gradient of a completed backward sweep
     int64_t N = 0, cur_ckpt = 0, param_gen = -1;
     char *ck = nullptr;    // nseg checkpoints, each 5*npad floats + 5*npad u16
     float *rec_x = nullptr;   // ckpt x 5 x npad (dense records, allocated when first used)
@@ -794,6 +795,7 @@ vga_status sim_adjoint_forward(vga_sim *s, int64_t N, int64_t ckpt) {
     AdjointBuffers *a = s->adj;
     a->valid = false;
     a->last_recorded = false;
+    a->grad_ready = false;
     // sparse records and reverse steps: the activity mask of X^0 on the neighbour-offset table
     a->sparse = false;
     if (s->activity_skip && s->g->nx <= 32767 && s->n > 0) {
@@ -979,6 +981,7 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     if (h_gtheta && s->n_theta > 0 && s->wmode == W_BLOCK)
         VGA_CUDA(cudaMemcpyAsync(h_gtheta, a->gtheta, sizeof(double) * (size_t)s->n_theta, cudaMemcpyDeviceToHost, st));
     VGA_CUDA(cudaStreamSynchronize(st));
+    a->grad_ready = s->wmode == W_BLOCK && s->n_theta > 0;
     const double dt = s->params.dt;
     // order: D, rho, mu, beta, v_som, v_fom, v_dom, K_dom
     grad8[0] = h[GR_COUNT] * dt;
@@ -989,6 +992,17 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     grad8[5] = h[GR_F] * dt;
     grad8[6] = h[GR_A] * dt;
     grad8[7] = h[GR_K];
+    return VGA_OK;
+}
+
+vga_status sim_adjoint_grad_theta(vga_sim *s, double *out, bool on_device, int64_t n) {
+    AdjointBuffers *a = s->adj;
+    if (!a || !a->valid || !a->grad_ready)
+        return fail(VGA_ERR_INVALID_ARG, "no conductance gradient: run vga_adjoint_backward with conductances set");
+    if (n != s->n_theta) return fail(VGA_ERR_INVALID_ARG, "n must be the number of conductances");
+    VGA_CUDA(cudaMemcpyAsync(out, a->gtheta, sizeof(double) * (size_t)n,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
     return VGA_OK;
 }
 

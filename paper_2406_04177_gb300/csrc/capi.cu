@@ -341,28 +341,33 @@ vga_status vga_sim_set_params(vga_sim *s, const vga_params *p) {
     return sim_prepare_params(s, p);
 }
 
-vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const float *theta, int64_t n_theta) {
-    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
-    if (block_side < 1 || !theta) return fail(VGA_ERR_INVALID_ARG, "block_side must be >= 1 and theta non-NULL");
+// Shared by the host and device forms of vga_sim_set_block_conductances: the block grid of the
+// image and its interface count, checked against n_theta.
+static vga_status block_grid_check(const vga_sim *s, int32_t block_side, int64_t n_theta, int32_t (&nb)[3],
+                                   int64_t (&cnt)[3]) {
     const vga_graph *g = s->g;
-    const int32_t nbx = (g->nx + block_side - 1) / block_side, nby = (g->ny + block_side - 1) / block_side,
-                  nbz = (g->nz + block_side - 1) / block_side;
-    const int64_t cx = (int64_t)nbz * nby * (nbx - 1), cy = (int64_t)nbz * (nby - 1) * nbx,
-                  cz = (int64_t)(nbz - 1) * nby * nbx;
-    if (n_theta != cx + cy + cz) {
+    nb[0] = (g->nx + block_side - 1) / block_side;
+    nb[1] = (g->ny + block_side - 1) / block_side;
+    nb[2] = (g->nz + block_side - 1) / block_side;
+    cnt[0] = (int64_t)nb[2] * nb[1] * (nb[0] - 1);
+    cnt[1] = (int64_t)nb[2] * (nb[1] - 1) * nb[0];
+    cnt[2] = (int64_t)(nb[2] - 1) * nb[1] * nb[0];
+    if (n_theta != cnt[0] + cnt[1] + cnt[2]) {
         char buf[160];
         std::snprintf(buf, sizeof(buf), "n_theta = %lld but the block grid has %lld interfaces", (long long)n_theta,
-                      (long long)(cx + cy + cz));
+                      (long long)(cnt[0] + cnt[1] + cnt[2]));
         return fail(VGA_ERR_INVALID_ARG, buf);
     }
-    float mx = 1.0f;
-    for (int64_t k = 0; k < n_theta; ++k) {
-        if (!(std::isfinite(theta[k]) && theta[k] >= 0.0f))
-            return fail(VGA_ERR_INVALID_ARG, "theta values must be finite and >= 0");
-        mx = std::max(mx, theta[k]);
-    }
+    return VGA_OK;
+}
+
+static vga_status block_stability_check(const vga_sim *s, float mx) {
     if (s->params.scheme == VGA_SCHEME_EXPLICIT && 6.0 * s->params.D * s->params.dt * mx > 1.0 + 1e-12)
         return fail(VGA_ERR_UNSTABLE_DT, "explicit scheme unstable with these conductances (6 D dt max theta > 1)");
+    return VGA_OK;
+}
+
+static vga_status block_theta_buffer(vga_sim *s, int64_t n_theta) {
     if (s->n_theta < n_theta) {
         dfree(s->theta);
         s->theta = nullptr;
@@ -370,22 +375,66 @@ vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const 
         VGA_TRY(dmalloc((void **)&s->theta, sizeof(float) * (size_t)std::max<int64_t>(n_theta, 1), "theta"));
         s->n_theta = n_theta;
     }
-    if (n_theta > 0)
-        VGA_CUDA(cudaMemcpyAsync(s->theta, theta, sizeof(float) * (size_t)n_theta, cudaMemcpyHostToDevice, s->stream));
-    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    return VGA_OK;
+}
+
+static void block_apply(vga_sim *s, int32_t block_side, const int32_t (&nb)[3], const int64_t (&cnt)[3], float mx) {
     if (s->bw.bs != block_side || s->face_mode) s->btable_bs = 0;
     s->face_mode = false;
     s->bw.g6 = nullptr;
     s->bw.bs = block_side;
-    s->bw.nbx = nbx;
-    s->bw.nby = nby;
-    s->bw.nbz = nbz;
-    s->bw.off_y = cx;
-    s->bw.off_z = cx + cy;
+    s->bw.nbx = nb[0];
+    s->bw.nby = nb[1];
+    s->bw.nbz = nb[2];
+    s->bw.off_y = cnt[0];
+    s->bw.off_z = cnt[0] + cnt[1];
     s->bw.theta = s->theta;
     s->wmode = W_BLOCK;
     s->max_g = mx;
     ++s->param_gen;
+}
+
+vga_status vga_sim_set_block_conductances(vga_sim *s, int32_t block_side, const float *theta, int64_t n_theta) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    if (block_side < 1 || !theta) return fail(VGA_ERR_INVALID_ARG, "block_side must be >= 1 and theta non-NULL");
+    int32_t nb[3];
+    int64_t cnt[3];
+    VGA_TRY(block_grid_check(s, block_side, n_theta, nb, cnt));
+    float mx = 1.0f;
+    for (int64_t k = 0; k < n_theta; ++k) {
+        if (!(std::isfinite(theta[k]) && theta[k] >= 0.0f))
+            return fail(VGA_ERR_INVALID_ARG, "theta values must be finite and >= 0");
+        mx = std::max(mx, theta[k]);
+    }
+    VGA_TRY(block_stability_check(s, mx));
+    VGA_TRY(block_theta_buffer(s, n_theta));
+    if (n_theta > 0)
+        VGA_CUDA(cudaMemcpyAsync(s->theta, theta, sizeof(float) * (size_t)n_theta, cudaMemcpyHostToDevice, s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    block_apply(s, block_side, nb, cnt, mx);
+    return VGA_OK;
+}
+
+vga_status vga_sim_set_block_conductances_device(vga_sim *s, int32_t block_side, const float *d_theta,
+                                                 int64_t n_theta) {
+    if (!s) return fail(VGA_ERR_INVALID_ARG, "sim is NULL");
+    if (block_side < 1 || (!d_theta && n_theta > 0))
+        return fail(VGA_ERR_INVALID_ARG, "block_side must be >= 1 and d_theta non-NULL");
+    int32_t nb[3];
+    int64_t cnt[3];
+    VGA_TRY(block_grid_check(s, block_side, n_theta, nb, cnt));
+    bool valid = true;
+    float vmax = 0.0f;
+    VGA_TRY(sim_theta_check(s, d_theta, n_theta, &valid, &vmax));  // the caller's buffer, before any copy
+    if (!valid) return fail(VGA_ERR_INVALID_ARG, "theta values must be finite and >= 0");
+    const float mx = std::max(1.0f, vmax);
+    VGA_TRY(block_stability_check(s, mx));
+    VGA_TRY(block_theta_buffer(s, n_theta));
+    if (n_theta > 0)
+        VGA_CUDA(cudaMemcpyAsync(s->theta, d_theta, sizeof(float) * (size_t)n_theta, cudaMemcpyDeviceToDevice,
+                                 s->stream));
+    VGA_CUDA(cudaStreamSynchronize(s->stream));
+    block_apply(s, block_side, nb, cnt, mx);
     return VGA_OK;
 }
 
@@ -635,6 +684,11 @@ vga_status vga_adjoint_backward(vga_sim *s, const double *dL_dXN, int32_t on_dev
         VGA_CUDA(cudaStreamSynchronize(s->stream));
     }
     return VGA_OK;
+}
+
+vga_status vga_adjoint_grad_theta(vga_sim *s, double *grad_theta, int32_t on_device, int64_t n) {
+    if (!s || (!grad_theta && n > 0)) return fail(VGA_ERR_INVALID_ARG, "sim or grad_theta is NULL");
+    return sim_adjoint_grad_theta(s, grad_theta, on_device != 0, n);
 }
 
 vga_status vga_sgd_block_conductances(vga_sim *s, double lr, double theta_min, double theta_max) {

@@ -1238,6 +1238,45 @@ vga_status sim_face_check(vga_sim *s, const float *d_g6, bool *symmetric, float 
     return VGA_OK;
 }
 
+// Block conductances in device memory: flags |= 1 for a value that is not finite or is negative; the
+// largest value (as the bits of a non-negative float, which order like the values) into *mx.
+__global__ void k_theta_check(int64_t n, const float *__restrict__ theta, unsigned int *__restrict__ flags,
+                              unsigned int *__restrict__ mx) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    unsigned int bits = 0u;
+    if (k < n) {
+        const float t = theta[k];
+        bad = !(isfinite(t) && t >= 0.0f);
+        bits = bad ? 0u : __float_as_uint(t + 0.0f);  // +0 for -0
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, 1u);
+    for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_down_sync(0xffffffffu, bits, o));
+    if ((threadIdx.x & 31) == 0 && bits) atomicMax(mx, bits);
+}
+
+vga_status sim_theta_check(vga_sim *s, const float *d_theta, int64_t n, bool *valid, float *maxv) {
+    *valid = true;
+    *maxv = 0.0f;
+    if (n <= 0) return VGA_OK;
+    unsigned int *d = nullptr;
+    VGA_TRY(dmalloc((void **)&d, 2 * sizeof(unsigned int), "conductance check"));
+    unsigned int h[2] = {0u, 0u};
+    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(unsigned int), s->stream);
+    if (e == cudaSuccess) {
+        k_theta_check<<<grid_for(n, kThreads), kThreads, 0, s->stream>>>(n, d_theta, d, d + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    dfree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "k_theta_check", __FILE__, __LINE__);
+    ++s->launches;
+    *valid = h[0] == 0u;
+    std::memcpy(maxv, &h[1], sizeof(float));
+    return VGA_OK;
+}
+
 vga_status sim_face_mirror(vga_sim *s, double *d_g) {
     if (s->n == 0) return VGA_OK;
     NbrTable tb;

@@ -321,6 +321,7 @@ vga_status sim_nbr_table(vga_sim *s, NbrTable *out);  // builds the table on fir
 // Per-face conductances (6 x n, device): symmetric across every edge?, largest sum over a node's edges.
 vga_status sim_face_check(vga_sim *s, const float *d_g6, bool *symmetric, float *rowmax);
 // Copies each edge's gradient from its +x/+y/+z slot into the neighbour's opposite slot (6 x n, device).
+vga_status sim_theta_check(vga_sim *s, const float *d_theta, int64_t n, bool *valid, float *maxv);
 vga_status sim_face_mirror(vga_sim *s, double *d_g);
 // block.cu: P fused passes of a sparse step call as temporally blocked launches (variant 6); *done
 // is false (and nothing ran) when the graph, the conductances or the marked nodes do not allow it.
@@ -346,6 +347,7 @@ vga_status sim_step_implicit(vga_sim *s, int64_t n_steps);
 void sim_mx_graph_release(vga_sim *s);  // the cached graphs of the mixed solve
 // adjoint.cu
 vga_status sim_adjoint_forward(vga_sim *s, int64_t N, int64_t ckpt);
+vga_status sim_adjoint_grad_theta(vga_sim *s, double *out, bool on_device, int64_t n);
 vga_status sim_adjoint_backward(vga_sim *s, const double *d_lamN, double *d_lam0, double *grad8, double *h_gtheta);
 vga_status sim_sgd_theta(vga_sim *s, double lr, double lo, double hi);
 vga_status sim_block_mass_loss(vga_sim *s, int32_t bs, uint32_t comp_mask, const double *d_target, double *d_work,

@@ -263,3 +263,60 @@ def test_sparse_reverse_matches_dense(vga, oracle_lib, block, marked):
     assert g_s == g_d
     if block:
         assert np.allclose(t_s, t_d, rtol=1e-12, atol=1e-15 * np.abs(t_d).max())
+
+
+def test_device_conductances_and_device_gradient(vga, oracle_lib):
+    """vga_sim_set_block_conductances_device gives the run of the host form (same bits); a NaN or
+    negative device value is rejected and leaves the previous conductances in place; the stability
+    check sees the device maximum; vga_adjoint_grad_theta copies the last backward's conductance
+    gradient to device or host memory, equal to the one vga_adjoint_backward returns."""
+    import torch
+
+    img, og, g, X0 = _setup(vga, oracle_lib)
+    bs = 8
+    theta = synth.block_conductances(oracle_lib.block_grid(img.shape, bs), 4).astype(np.float32)
+    p = synth.paper_params(dt=0.9 / (6 * synth.D_DOM * theta.max()))
+    lamN = np.random.default_rng(3).standard_normal((5, og.n))
+    runs = []
+    for dev in (False, True):
+        sim = vga.Sim(g, p)
+        sim.set_block_conductances(bs, torch.from_numpy(theta).cuda() if dev else theta)
+        sim.set_masses(X0)
+        sim.adjoint_forward(25, 6)
+        lam0 = np.empty((5, og.n))
+        grad, gth = sim.adjoint_backward(lamN, lam0, n_theta=theta.size)
+        d = torch.zeros(theta.size, dtype=torch.float64, device="cuda")
+        sim.adjoint_grad_theta(d)
+        h = sim.adjoint_grad_theta(np.zeros(theta.size))
+        assert np.array_equal(d.cpu().numpy(), gth) and np.array_equal(h, gth)
+        runs.append((sim.save_state(), lam0, grad, gth))
+        if dev:
+            bad = torch.from_numpy(theta).cuda()
+            bad[3] = float("nan")
+            with pytest.raises(vga.VgaError) as e:
+                sim.set_block_conductances(bs, bad)
+            assert e.value.name == "VGA_ERR_INVALID_ARG"
+            bad[3] = -1.0
+            with pytest.raises(vga.VgaError) as e:
+                sim.set_block_conductances(bs, bad)
+            assert e.value.name == "VGA_ERR_INVALID_ARG"
+            with pytest.raises(vga.VgaError) as e:  # 6 D dt max theta > 1 at this time step
+                sim.set_block_conductances(bs, torch.from_numpy(theta * 3).cuda())
+            assert e.value.name == "VGA_ERR_UNSTABLE_DT"
+            with pytest.raises(vga.VgaError):  # wrong count
+                sim.set_block_conductances(bs, torch.from_numpy(theta[:-1]).cuda())
+            assert np.array_equal(sim.get_block_conductances(theta.size), theta)
+            with pytest.raises(vga.VgaError):  # wrong gradient size
+                sim.adjoint_grad_theta(np.zeros(theta.size + 1))
+        sim.close()
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert runs[0][2] == runs[1][2]
+    assert np.allclose(runs[0][3], runs[1][3], rtol=1e-12, atol=1e-15 * np.abs(runs[0][3]).max())
+    sim = vga.Sim(g, p)
+    sim.set_block_conductances(bs, theta)
+    sim.set_masses(X0)
+    sim.adjoint_forward(5, 5)
+    with pytest.raises(vga.VgaError):  # no backward sweep yet
+        sim.adjoint_grad_theta(np.zeros(theta.size))
+    sim.close()
