@@ -210,7 +210,8 @@ def run_cpu_baseline(a, img, X0, gpu_after=None):
     t0 = time.time()
     X1 = oracle.explicit_run(og.nbr, p, X0, 1)
     t1 = time.time() - t0
-    m = int(max(2, min(60, round(a.cpu_seconds / max(t1, 1e-3)))))
+    # the 100-step prefix (after one untimed step), shorter only if that would exceed cpu_seconds
+    m = 1 + int(max(1, min(100, round(a.cpu_seconds / max(t1, 1e-3)))))
     t0 = time.time()
     Xm = oracle.explicit_run(og.nbr, p, X1, m - 1)
     dt = time.time() - t0
