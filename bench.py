@@ -158,6 +158,16 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def once(self) -> bool:
+        """One sample now (no sampling process left running)."""
+        try:
+            r = subprocess.run(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                               capture_output=True, text=True, timeout=20)
+        except Exception:
+            return False
+        self.lines += [line.strip() for line in r.stdout.splitlines()]
+        return True
+
     def stop(self) -> dict | None:
         if self.proc is None:
             return None
@@ -168,6 +178,9 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
+        return self.summary()
+
+    def summary(self) -> dict:
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in self.lines:
@@ -246,17 +259,6 @@ def bench_ours(a):
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
-    # the FP64 reference of the adjoint configuration runs in a spawned process while the GPU legs run
-    c5_job = None
-    if (world == 1 and not a.no_cpu and not a.no_extras and "adjoint_fit" in a.extras.split(",")):
-        import multiprocessing as mp
-
-        ctx = mp.get_context("spawn")
-        c5_q = ctx.Queue()
-        c5_proc = ctx.Process(target=_oracle_c5_reference, args=(c5_q, max(1, (os.cpu_count() or 2) // 2)),
-                              daemon=True)
-        c5_proc.start()
-        c5_job = (c5_proc, c5_q)
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -414,8 +416,10 @@ def bench_ours(a):
     sim.step(S)
     sim.get_state_f32(outh_np)
     torch.cuda.synchronize()
+    # clocks read just before and just after (an nvidia-smi sampling process running during this
+    # leg stalls its host copies by several ms at a time)
     e2e_sampler = ClockSampler(bus)
-    e2e_sampler.start()
+    e2e_sampler.once()
     if world > 1:
         dist.barrier()
     w0 = time.perf_counter()
@@ -425,7 +429,8 @@ def bench_ours(a):
         sim.totals()
         sim.get_state_f32(outh_np)
     w1 = time.perf_counter()
-    e2e_clocks = e2e_sampler.stop()
+    e2e_sampler.once()
+    e2e_clocks = dict(e2e_sampler.summary(), when="one sample just before and one just after the timed loop")
     e2e_val = job_value(world, n * S * e2e_iters, max_over_ranks((w1 - w0) * 1e3, world, "cuda"))
     e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(xh.numel() * 4),
            "d2h_bytes_per_step": int(outh.numel() * 4 + 5 * 8),
@@ -444,6 +449,19 @@ def bench_ours(a):
            "kernel_time_ms": {k: v[0] for k, v in timing.items() if v[1]},
            "autotune": tune,
            "drift_timed_region": float(abs(tot1.sum() - tot0.sum()) / tot0.sum())}
+
+    # the FP64 reference of the adjoint configuration runs in a spawned process while the extra GPU
+    # legs run (started after the timed and end-to-end legs, whose host copies it would slow down)
+    c5_job = None
+    if (world == 1 and not a.no_cpu and not a.no_extras and "adjoint_fit" in a.extras.split(",")):
+        import multiprocessing as mp
+
+        ctx = mp.get_context("spawn")
+        c5_q = ctx.Queue()
+        c5_proc = ctx.Process(target=_oracle_c5_reference, args=(c5_q, max(1, (os.cpu_count() or 2) // 2)),
+                              daemon=True)
+        c5_proc.start()
+        c5_job = (c5_proc, c5_q)
 
     held = {}  # GPU results kept for the FP64 comparisons after the GPU legs
     if not a.no_extras:
