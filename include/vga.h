@@ -423,7 +423,9 @@ vga_status vga_batch_free(vga_batch *b);
 
 /* Kernel timing.  When enabled, the library records a CUDA event pair on the simulation's stream
  * around every kernel it launches and accumulates the elapsed times per kernel kind; reading them
- * synchronises the stream.  Kinds: */
+ * synchronises the stream.  The fused passes of one explicit step call are timed as one span and
+ * counted as that many launches (an event pair between two passes would keep the second from being
+ * scheduled during the first's tail), so ms / launches is their live mean per pass.  Kinds: */
 #define VGA_KERNEL_FUSED_STEP 0    /* explicit pass: diffuse stored transformed DOM, transform */
 #define VGA_KERNEL_TRANSFORM 1     /* transformation-only pass (first pass of a step call) */
 #define VGA_KERNEL_DIFFUSE 2       /* diffusion-only pass (last pass of a step call) */
@@ -435,7 +437,7 @@ vga_status vga_batch_free(vga_batch *b);
 #define VGA_KERNEL_KINDS 8
 typedef struct vga_kernel_timing {
     double ms[VGA_KERNEL_KINDS];        /* summed event-to-event milliseconds per kind */
-    int64_t launches[VGA_KERNEL_KINDS]; /* timed launches per kind */
+    int64_t launches[VGA_KERNEL_KINDS]; /* timed launches (fused passes: passes) per kind */
 } vga_kernel_timing;
 vga_status vga_sim_enable_timing(vga_sim *s, int32_t on);
 /* Copies the accumulated timings into *out (after synchronising); reset != 0 clears them. */

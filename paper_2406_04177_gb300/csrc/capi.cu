@@ -76,14 +76,14 @@ static cudaEvent_t pool_event(vga_sim *s) {
 }
 
 void timing_begin(vga_sim *s, int kind) {
-    if (!s->timing) return;
+    if (!s->timing || s->timing_hold) return;
     s->timing_a = pool_event(s);
     s->timing_kind = kind;
     if (s->timing_a) cudaEventRecord(s->timing_a, s->stream);
 }
 
 void timing_end_weighted(vga_sim *s, int64_t passes) {
-    if (!s->timing || !s->timing_a) return;
+    if (!s->timing || s->timing_hold || !s->timing_a) return;
     cudaEvent_t b = pool_event(s);
     if (!b) return;
     cudaEventRecord(b, s->stream);

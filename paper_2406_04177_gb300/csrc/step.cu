@@ -993,12 +993,28 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
             ++s->launches;
         }
         s->sparse_call = sparse;
+        // with timing on, the fused passes of the call are timed as one span (credited as n_steps - 1
+        // passes): an event pair around every launch would stop each grid from being scheduled in the
+        // tail of the one before it (programmatic dependent launch)
+        struct Span {
+            vga_sim *s;
+            bool on;
+            ~Span() { s->timing_hold = false; }
+        } span{s, s->timing && n_steps > 1};
+        if (span.on) {
+            timing_begin(s, VGA_KERNEL_FUSED_STEP);
+            s->timing_hold = true;
+        }
         bool blocked = false;  // variant 6: the fused passes as temporally blocked launches
         if (sparse && s->kernel_variant == 6 && !sub) VGA_TRY(sim_block_fused(s, n_steps - 1, &blocked));
         for (int64_t k = 1; k < n_steps && !blocked; ++k) {
             if (sub) s->sp.ntrans = sim_ticks_of_step(s, k0 + k);
             VGA_TRY(launch_stencil<1>(s, state_io(s)));
             for (int c = 0; c < 5; ++c) s->cur[c] ^= 1;
+        }
+        if (span.on) {
+            s->timing_hold = false;
+            timing_end_weighted(s, n_steps - 1);
         }
         s->sparse_call = false;
         if (copy) {

@@ -263,6 +263,7 @@ struct vga_sim {
     int64_t kt_count[VGA_KERNEL_KINDS] = {};
     cudaEvent_t timing_a = nullptr;
     int timing_kind = -1;
+    bool timing_hold = false;      // inside a span timed as a whole (per-launch events off)
     // adjoint work buffers (adjoint.cu), allocated on first use
     vga::AdjointBuffers *adj = nullptr;
     int32_t *d_err = nullptr;     // device error flag of bounded waits (nonzero: timed out)

@@ -482,3 +482,28 @@ def test_totals_scan_reports_nonfinite_and_negative(vga):
     sim.step(5)
     assert np.isfinite(sim.totals()).all()
     assert sim.stats()["negative_reports"] == 1
+
+
+@pytest.mark.parametrize("variant", [5, 2, 6])
+def test_kernel_timing_spans_the_fused_passes(vga, oracle_lib, variant):
+    """With timing on, a step call's fused passes count as n_steps - 1 timed launches of the fused
+    kind and the first and last passes as one each; the state is the same bits as without timing."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (40, 36, 44), 0.2, 9)
+    p = synth.paper_params()
+    out = []
+    for timing in (False, True):
+        sim = vga.Sim(g, p)
+        sim.set_kernel(variant, 1024)
+        sim.set_masses(X0)
+        sim.enable_timing(timing)
+        sim.read_timing(reset=True)
+        sim.step(37)
+        sim.step(1)
+        kt = sim.read_timing(reset=True)
+        if timing:
+            assert kt["fused_step"][1] == 36
+            assert kt["fused_step"][0] > 0.0
+            assert kt["transform"][1] == 2 and kt["diffuse"][1] == 2
+        out.append(sim.save_state())
+        sim.close()
+    assert out[0] == out[1]
