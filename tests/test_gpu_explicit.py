@@ -507,3 +507,28 @@ def test_kernel_timing_spans_the_fused_passes(vga, oracle_lib, variant):
         out.append(sim.save_state())
         sim.close()
     assert out[0] == out[1]
+
+
+def test_rows_of_very_different_length(vga, oracle_lib):
+    """Rows alternating between full pore rows and rows with a few pores: neighbouring nodes of one
+    warp have +-y and +-z offsets hundreds apart. The sparse pass on the offset table matches the
+    dense one-node kernel bit for bit, and the oracle."""
+    nz, ny, nx = 6, 10, 600
+    img = np.ones((nz, ny, nx), dtype=np.uint8)
+    img[:, 0::2, :] = 0            # full pore rows
+    img[:, 1::2, ::97] = 0         # a few pores between them, joining the full rows
+    og = oracle_lib.graph_build(img)
+    g = vga.Graph(img)
+    X0 = synth.initial_masses(synth.kept_mask_from_nodes(img.shape, og.voxel_of_node), 3, with_organic_matter=True)
+    p = synth.paper_params()
+    out = []
+    for variant in (5, 0):
+        sim = vga.Sim(g, p)
+        sim.set_kernel(variant, 1024)
+        sim.set_masses(X0)
+        sim.step(40)
+        out.append((sim.save_state(), sim.get_masses()))
+        sim.close()
+    assert out[0][0] == out[1][0]
+    ref = oracle_lib.explicit_run(og.nbr, p, X0, 40)
+    _assert_close(out[0][1], ref)
