@@ -258,6 +258,41 @@ __device__ __forceinline__ double f32_to_f64_alu(float f) {
     return __hiloint2double((int)hi, (int)lo);
 }
 
+// Block sums of K compensated per-thread accumulators into out[0..K) (FP64, by thread 0 .. K-1): a
+// warp butterfly of the (sum, error) pairs in FP32, merged by TwoSum at each level, then one FP64
+// conversion per value and warp and the warps' sums in FP64.  The FP64 work is a few instructions
+// per warp instead of five FP64 shuffle-adds per value and thread, which at one warp-group of nodes
+// per thread (small graphs) cost more than the step itself.
+template <int K>
+__device__ __forceinline__ void block_sum_cacc(const CAcc (&a)[K], double *out) {
+    __shared__ double sh[K][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    double mine = 0.0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float s = a[k].s, c = a[k].c;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+            const float t = __fadd_rn(s, s2);
+            const float bp = __fsub_rn(t, s);
+            const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+            s = t;
+            c = __fadd_rn(__fadd_rn(c, c2), err);
+        }
+        if (lane == k) mine = (double)s + (double)c;  // every lane holds the warp's pair
+    }
+    if (lane < K) sh[lane][wid] = mine;
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double b = 0.0;
+        for (int w = 0; w < nw; ++w) b += sh[threadIdx.x][w];
+        out[threadIdx.x] = b;
+    }
+    __syncthreads();
+}
+
 // Adds v to gtheta[f] when f >= 0: one FP64 atomic per crossing edge.  At the porosities of the
 // workloads a block face carries a few edges per step, spread over rows far apart in node order, so
 // lanes of one warp rarely share a face and a warp-level pre-reduction would cost more instructions
@@ -444,11 +479,8 @@ __global__ void __launch_bounds__(kThreads, VGA_ADJ_MIN_BLOCKS) k_adjoint_vec(in
             vstore_k<PREC, K, false>(io.out[3], io.lout[3], i0, nn, m3);
         }
     }
-    double accd[kPar];
-#pragma unroll
-    for (int q = 0; q < kPar; ++q) accd[q] = (double)acc[q].s + (double)acc[q].c;
     __shared__ double out[kPar];
-    block_sum_store<kPar>(accd, out);
+    block_sum_cacc<kPar>(acc, out);
     if (threadIdx.x < kPar) gpart[(int64_t)blockIdx.x * kPar + threadIdx.x] += out[threadIdx.x];
 }
 
