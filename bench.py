@@ -422,12 +422,18 @@ def bench_ours(a):
     e2e_sampler.once()
     if world > 1:
         dist.barrier()
+    phase = np.zeros(4)  # host wall time of each call (each returns after its work completes)
     w0 = time.perf_counter()
     for _ in range(e2e_iters):
+        t0 = time.perf_counter()
         sim.set_state_f32(xh_np)
+        t1 = time.perf_counter()
         sim.step(S)
         sim.totals()
+        t2 = time.perf_counter()
         sim.get_state_f32(outh_np)
+        t3 = time.perf_counter()
+        phase += (t1 - t0, t2 - t1, t3 - t2, 0.0)
     w1 = time.perf_counter()
     e2e_sampler.once()
     e2e_clocks = dict(e2e_sampler.summary(), when="one sample just before and one just after the timed loop")
@@ -436,7 +442,10 @@ def bench_ours(a):
            "d2h_bytes_per_step": int(outh.numel() * 4 + 5 * 8),
            "how": "per step: vga_sim_set_state_f32 from pinned host memory, vga_sim_step(substeps), "
                   "vga_sim_totals, vga_sim_get_state_f32 to pinned host memory; wall clock",
-           "steps": e2e_iters, "clocks": e2e_clocks}
+           "steps": e2e_iters, "clocks": e2e_clocks,
+           "ms_per_step_by_call": {"set_state_f32": 1e3 * phase[0] / e2e_iters,
+                                   "step_and_totals": 1e3 * phase[1] / e2e_iters,
+                                   "get_state_f32": 1e3 * phase[2] / e2e_iters}}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
            "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -433,13 +433,10 @@ __global__ void __launch_bounds__(kThreads) k_mask_prefix(int64_t words, const u
 
 // Marked nodes' MB, SOM, FOM, CO2 between the state arrays (io.in read, io.out written) and the
 // compact state: to_compact copies state -> compact, otherwise compact -> state.
-__global__ void k_active_copy(int64_t n, SparseState ss, StateIO io, int to_compact, int comp) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t w = (uint32_t)(i >> 5), bit = 1u << (i & 31);
-    const uint32_t m = __ldg(ss.mask + w);
-    if (!(m & bit)) return;
-    const uint32_t r = __ldg(ss.prefix + w) + __popc(m & (bit - 1u));
+__global__ void k_active_copy(int64_t m, SparseState ss, StateIO io, int to_compact, int comp) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // rank: one thread per marked node
+    if (r >= m) return;
+    const uint32_t i = __ldg(ss.list + r);
     const int cs[4] = {0, 2, 3, 4};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -927,8 +924,8 @@ vga_status activity_build(Activity *a, int64_t n, int64_t npad, const StateIO &c
 
 vga_status activity_copy(const Activity &a, int64_t n, const StateIO &io, bool to_compact, bool comp, cudaStream_t st) {
     if (n <= 0 || a.n_active <= 0) return VGA_OK;
-    k_active_copy<<<grid_for(n, kThreads), kThreads, 0, st>>>(n, activity_state(a), io, to_compact ? 1 : 0,
-                                                            comp ? 1 : 0);
+    k_active_copy<<<grid_for(a.n_active, kThreads), kThreads, 0, st>>>(a.n_active, activity_state(a), io,
+                                                                     to_compact ? 1 : 0, comp ? 1 : 0);
     VGA_CHECK_LAUNCH();
     return VGA_OK;
 }
