@@ -38,6 +38,9 @@ constexpr int kThreads = 256;
 #define VGA_ADJ_K 2  // consecutive nodes per thread in the reverse step (2 or 4)
 #endif
 constexpr int kAdjK = VGA_ADJ_K;
+// The reverse steps keep their partial sums in per-thread slots across a sweep when a thread takes
+// at most this many groups of nodes per launch (small graphs), else reduce them per launch.
+constexpr int64_t kSlotGroups = 8;
 static_assert(kAdjK == 2 || kAdjK == 4, "the reverse step takes 2 or 4 nodes per thread");
 constexpr int kPar = GR_COUNT + 1;  // per-block partial slots: 7 rate slots + D
 
@@ -316,14 +319,28 @@ __device__ __forceinline__ void face_atomic_add_f(double *gtheta, int32_t f, flo
 // identity), and the reverse transformation runs with those values and without the rate-gradient
 // sums, whose terms are all products with MB, SOM, FOM or the mortality (zero there).  dL/dX^k and
 // the gradients are the bits of SP 0.
-template <int WM, int PREC, int TF, int SP>
+template <int WM, int PREC, int TF, int SP, int SL>
 __global__ void __launch_bounds__(kThreads, VGA_ADJ_MIN_BLOCKS) k_adjoint_vec(int64_t n, NbrTable tb, BlockTable bt, StepParams p,
                                                           StateIO io, int64_t npad, const float *__restrict__ xk,
                                                           const float *__restrict__ y2k, SparseState ss, int64_t xcap,
-                                                          double *__restrict__ gpart, double *__restrict__ gtheta) {
+                                                          float *__restrict__ tacc, double *__restrict__ gpart,
+                                                          double *__restrict__ gtheta) {
     constexpr int K = kAdjK;
     const float *__restrict__ L2 = io.in[1];
+    // The thread's compensated partial sums.  SL 1 (graphs where a thread takes few groups per
+    // launch): carried from launch to launch of one backward sweep in the thread's own slots of
+    // tacc (value q: rows 2q, 2q + 1 of T = grid threads), reduced once after the sweep; otherwise
+    // summed per block at the end of every launch into gpart.  The grid and the thread of each node
+    // are fixed for a sweep, so either way the sums are the same bits on every run.
+    const int64_t T = (int64_t)gridDim.x * blockDim.x, t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     CAcc acc[kPar];
+    if (SL) {
+#pragma unroll
+        for (int q = 0; q < kPar; ++q) {
+            acc[q].s = tacc[(2 * q) * T + t];
+            acc[q].c = tacc[(2 * q + 1) * T + t];
+        }
+    }
     const float mc = -p.c;
     const uint32_t nn = (uint32_t)n;
     const int lane = threadIdx.x & 31;
@@ -479,9 +496,47 @@ __global__ void __launch_bounds__(kThreads, VGA_ADJ_MIN_BLOCKS) k_adjoint_vec(in
             vstore_k<PREC, K, false>(io.out[3], io.lout[3], i0, nn, m3);
         }
     }
+    if (SL) {
+#pragma unroll
+        for (int q = 0; q < kPar; ++q) {
+            tacc[(2 * q) * T + t] = acc[q].s;
+            tacc[(2 * q + 1) * T + t] = acc[q].c;
+        }
+        return;
+    }
     __shared__ double out[kPar];
     block_sum_cacc<kPar>(acc, out);
     if (threadIdx.x < kPar) gpart[(int64_t)blockIdx.x * kPar + threadIdx.x] += out[threadIdx.x];
+}
+
+// One reverse step on the offset table: compact z offsets or not, per-thread slots or per-launch
+// block sums for the partials.
+template <int WM, int PREC, int SP>
+void launch_reverse(int G, cudaStream_t st, bool tz, bool slots, int64_t n, const NbrTable &tb, const BlockTable &bt,
+                    const StepParams &p, const StateIO &io, int64_t npad, const float *xk, const float *y2k,
+                    const SparseState &ss, int64_t xcap, float *tacc, double *gpart, double *gtheta) {
+    if (tz) {
+        if (slots) k_adjoint_vec<WM, PREC, 1, SP, 1><<<G, kThreads, 0, st>>>(n, tb, bt, p, io, npad, xk, y2k, ss, xcap, tacc, gpart, gtheta);
+        else k_adjoint_vec<WM, PREC, 1, SP, 0><<<G, kThreads, 0, st>>>(n, tb, bt, p, io, npad, xk, y2k, ss, xcap, tacc, gpart, gtheta);
+    } else {
+        if (slots) k_adjoint_vec<WM, PREC, 0, SP, 1><<<G, kThreads, 0, st>>>(n, tb, bt, p, io, npad, xk, y2k, ss, xcap, tacc, gpart, gtheta);
+        else k_adjoint_vec<WM, PREC, 0, SP, 0><<<G, kThreads, 0, st>>>(n, tb, bt, p, io, npad, xk, y2k, ss, xcap, tacc, gpart, gtheta);
+    }
+}
+
+// After a backward sweep: the per-thread slots of the reverse steps' partial sums (grid G x kThreads)
+// into per-block FP64 partials gpart[G x kPar] (the block sums of block_sum_cacc).
+__global__ void __launch_bounds__(kThreads) k_reduce_tacc(const float *__restrict__ tacc, double *__restrict__ gpart) {
+    const int64_t T = (int64_t)gridDim.x * blockDim.x, t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    CAcc acc[kPar];
+#pragma unroll
+    for (int q = 0; q < kPar; ++q) {
+        acc[q].s = tacc[(2 * q) * T + t];
+        acc[q].c = tacc[(2 * q + 1) * T + t];
+    }
+    __shared__ double out[kPar];
+    block_sum_cacc<kPar>(acc, out);
+    if (threadIdx.x < kPar) gpart[(int64_t)blockIdx.x * kPar + threadIdx.x] = out[threadIdx.x];
 }
 
 __global__ void __launch_bounds__(kThreads) k_reduce_gpart(const double *__restrict__ gpart, int G,
@@ -657,6 +712,8 @@ struct AdjointBuffers {
     PairBuf work[2];
     PairBuf lam[2];
     double *gpart = nullptr;  // G x kPar
+    float *tacc = nullptr;    // per-thread partial sums of the table reverse steps: 2 kPar x (grid threads)
+    int64_t tacc_count = 0;
     double *gtheta = nullptr; // ntheta
     double *gsum = nullptr;   // kPar
     double *lamstage = nullptr;  // 5 n FP64 (host-pointer staging)
@@ -676,6 +733,7 @@ void adjoint_free(AdjointBuffers *a) {
         dfree(a->lam[b].l);
     }
     dfree(a->gpart);
+    dfree(a->tacc);
     dfree(a->gtheta);
     dfree(a->gsum);
     dfree(a->lamstage);
@@ -886,11 +944,11 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
         VGA_CUDA(cudaGetDevice(&dev));
         VGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         if (tb.tz) {
-            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_adjoint_vec<WM, PREC, 1, 0>, kThreads, 0));
-            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_adjoint_vec<WM, PREC, 1, 1>, kThreads, 0));
+            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_adjoint_vec<WM, PREC, 1, 0, 0>, kThreads, 0));
+            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_adjoint_vec<WM, PREC, 1, 1, 0>, kThreads, 0));
         } else {
-            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_adjoint_vec<WM, PREC, 0, 0>, kThreads, 0));
-            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_adjoint_vec<WM, PREC, 0, 1>, kThreads, 0));
+            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_adjoint_vec<WM, PREC, 0, 0, 0>, kThreads, 0));
+            VGA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_adjoint_vec<WM, PREC, 0, 1, 0>, kThreads, 0));
         }
         const int64_t groups = (s->n + kAdjK * kThreads - 1) / (kAdjK * kThreads);
         Gt = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)std::max(1, std::min(occ0, occ1)) * sms, groups));
@@ -912,6 +970,21 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     k_lam_in<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, d_lamN, io_from(a->lam[0], a->lam[0], npad));
     VGA_CHECK_LAUNCH();
     VGA_CUDA(cudaMemsetAsync(a->gpart, 0, sizeof(double) * kPar * (size_t)std::max(G, 1), st));
+    // per-thread slots when a thread takes at most kSlotGroups groups of nodes per reverse launch
+    const int64_t groups_per_thread = table ? ((s->n + kAdjK * kThreads - 1) / (kAdjK * kThreads) + Gt - 1) / Gt : 0;
+    float *tacc = nullptr;
+    if (table && groups_per_thread <= kSlotGroups) {  // zeroed for this sweep
+        const int64_t count = 2 * kPar * (int64_t)Gt * kThreads;
+        if (a->tacc_count < count) {
+            dfree(a->tacc);
+            a->tacc = nullptr;
+            a->tacc_count = 0;
+            VGA_TRY(dmalloc((void **)&a->tacc, sizeof(float) * (size_t)count, "gradient partials"));
+            a->tacc_count = count;
+        }
+        VGA_CUDA(cudaMemsetAsync(a->tacc, 0, sizeof(float) * (size_t)count, st));
+        tacc = a->tacc;
+    }
     VGA_CUDA(cudaMemsetAsync(a->gtheta, 0, sizeof(double) * (size_t)a->ntheta, st));
     int lb = 0;
     for (int64_t sg = nseg - 1; sg >= 0; --sg) {
@@ -973,21 +1046,13 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
             const StateIO io = lam_io(a->lam, lb, npad);
             timing_begin(s, VGA_KERNEL_ADJOINT);
             // four nodes per thread
-            if (table && sp) {
-                if (tb.tz)
-                    k_adjoint_vec<WM, PREC, 1, 1><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, npad, xk, y2k, ss,
-                                                                         a->xcap, a->gpart, a->gtheta);
-                else
-                    k_adjoint_vec<WM, PREC, 0, 1><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, npad, xk, y2k, ss,
-                                                                         a->xcap, a->gpart, a->gtheta);
-            } else if (table) {
-                if (tb.tz)
-                    k_adjoint_vec<WM, PREC, 1, 0><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, npad, xk, y2k,
-                                                                         SparseState{}, 1, a->gpart, a->gtheta);
-                else
-                    k_adjoint_vec<WM, PREC, 0, 0><<<G, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, npad, xk, y2k,
-                                                                         SparseState{}, 1, a->gpart, a->gtheta);
-            } else
+            if (table && sp)
+                launch_reverse<WM, PREC, 1>(G, st, tb.tz != nullptr, tacc != nullptr, s->n, tb, bt, s->sp, io, npad, xk,
+                                            y2k, ss, a->xcap, tacc, a->gpart, a->gtheta);
+            else if (table)
+                launch_reverse<WM, PREC, 0>(G, st, tb.tz != nullptr, tacc != nullptr, s->n, tb, bt, s->sp, io, npad, xk,
+                                            y2k, SparseState{}, 1, tacc, a->gpart, a->gtheta);
+            else
                 k_adjoint_step<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw, io,
                                                                    npad, xk, y2k, a->gpart, a->gtheta);
             timing_end(s);
@@ -1003,6 +1068,10 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
         io.lin[4] = a->lam[0].l + 4 * (size_t)npad;
         k_lam_out<<<grid_for(s->n, kThreads), kThreads, 0, st>>>(s->n, d_lam0, io);
         VGA_CHECK_LAUNCH();
+    }
+    if (tacc) {
+        k_reduce_tacc<<<Gt, kThreads, 0, st>>>(tacc, a->gpart);
+        ++s->launches;
     }
     k_reduce_gpart<<<1, kThreads, 0, st>>>(a->gpart, G, a->gsum);
     VGA_CHECK_LAUNCH();
