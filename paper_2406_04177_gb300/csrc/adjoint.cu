@@ -714,6 +714,7 @@ struct AdjointBuffers {
     double *gpart = nullptr;  // G x kPar
     float *tacc = nullptr;    // per-thread partial sums of the table reverse steps: 2 kPar x (grid threads)
     int64_t tacc_count = 0;
+    cudaStream_t cap_stream = nullptr;  // private stream the backward sweep's loops are captured on
     double *gtheta = nullptr; // ntheta
     double *gsum = nullptr;   // kPar
     double *lamstage = nullptr;  // 5 n FP64 (host-pointer staging)
@@ -734,6 +735,7 @@ void adjoint_free(AdjointBuffers *a) {
     }
     dfree(a->gpart);
     dfree(a->tacc);
+    if (a->cap_stream) cudaStreamDestroy(a->cap_stream);
     dfree(a->gtheta);
     dfree(a->gsum);
     dfree(a->lamstage);
@@ -923,6 +925,47 @@ vga_status sim_adjoint_forward(vga_sim *s, int64_t N, int64_t ckpt) {
     return VGA_OK;
 }
 
+// The loops of a backward sweep (recording passes, reverse steps) repeat with the same kernels and
+// arguments for every segment of one length: each is captured once per sweep as a CUDA graph, on a
+// private stream (the simulation's may be the legacy default stream, which cannot be captured), and
+// replayed on the simulation's stream.  Kernel timing and a failed capture run the loops directly.
+struct SweepGraphs {
+    cudaStream_t st = nullptr, cap = nullptr;
+    bool on = false;
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    int64_t key[2] = {-1, -1};
+    ~SweepGraphs() {
+        for (auto &e : exec)
+            if (e) cudaGraphExecDestroy(e);
+    }
+    template <class F>
+    vga_status run(int slot, int64_t k, F &&issue) {
+        if (!on) return issue(st);
+        if (!exec[slot] || key[slot] != k) {
+            if (exec[slot]) cudaGraphExecDestroy(exec[slot]);
+            exec[slot] = nullptr;
+            key[slot] = -1;
+            VGA_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+            const vga_status r = issue(cap);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(cap, &g);
+            cudaError_t ei = cudaErrorUnknown;
+            if (r == VGA_OK && ec == cudaSuccess) ei = cudaGraphInstantiate(&exec[slot], g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (r != VGA_OK) return r;
+            if (ec != cudaSuccess || ei != cudaSuccess) {  // run the loops directly from now on
+                cudaGetLastError();
+                exec[slot] = nullptr;
+                on = false;
+                return issue(st);
+            }
+            key[slot] = k;
+        }
+        VGA_CUDA(cudaGraphLaunch(exec[slot], st));
+        return VGA_OK;
+    }
+};
+
 template <int WM>
 static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double *d_lam0, double *grad8,
                                         double *h_gtheta) {
@@ -959,6 +1002,15 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
     const int64_t npad = s->npad;
     cudaStream_t st = s->stream;
 
+    SweepGraphs graphs;
+    graphs.st = st;
+    graphs.on = table && !s->timing;
+    if (graphs.on && !a->cap_stream && cudaStreamCreateWithFlags(&a->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        a->cap_stream = nullptr;
+    }
+    graphs.cap = a->cap_stream;
+    graphs.on = graphs.on && graphs.cap;
     const bool sparse = a->sparse && table;
     const SparseState ss = sparse ? activity_state(a->act) : SparseState{};
     const int64_t m = sparse ? a->act.n_active : 0;
@@ -1006,19 +1058,26 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
                 VGA_TRY(activity_copy(a->act, s->n, io_from(a->work[0], a->work[0], npad), true, true, st));
                 ++s->launches;
             }
-            for (int64_t j = 1; j < len && sparse; ++j) {
-                const PassRecord pr = {nullptr, a->rec_y2 + (size_t)j * npad, npad};
-                const StateIO io = io_from(a->work[wb], a->work[1 - wb], npad);
-                timing_begin(s, VGA_KERNEL_FUSED_STEP);
-                if (tb.tz) k_dom_rec_vec<WM, PREC, 1><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr, ss);
-                else k_dom_rec_vec<WM, PREC, 0><<<Gv, kThreads, 0, st>>>(s->n, tb, bt, s->sp, io, pr, ss);
-                if (m > 0)
-                    k_transform_compact_rec<PREC><<<grid_for(m, kThreads), kThreads, 0, st>>>(
-                        m, ss, s->sp, io, pr.y2, a->rec_xc + (size_t)j * 4 * a->xcap, a->xcap);
-                timing_end(s);
-                VGA_CHECK_LAUNCH();
-                s->launches += m > 0 ? 2 : 1;
-                wb = 1 - wb;
+            if (sparse) {  // the recording passes j = 1 .. len-1: one graph per sweep and segment length
+                auto issue = [&](cudaStream_t cs) -> vga_status {
+                    int w = 0;
+                    for (int64_t j = 1; j < len; ++j) {
+                        const PassRecord pr = {nullptr, a->rec_y2 + (size_t)j * npad, npad};
+                        const StateIO io = io_from(a->work[w], a->work[1 - w], npad);
+                        timing_begin(s, VGA_KERNEL_FUSED_STEP);
+                        if (tb.tz) k_dom_rec_vec<WM, PREC, 1><<<Gv, kThreads, 0, cs>>>(s->n, tb, bt, s->sp, io, pr, ss);
+                        else k_dom_rec_vec<WM, PREC, 0><<<Gv, kThreads, 0, cs>>>(s->n, tb, bt, s->sp, io, pr, ss);
+                        if (m > 0)
+                            k_transform_compact_rec<PREC><<<grid_for(m, kThreads), kThreads, 0, cs>>>(
+                                m, ss, s->sp, io, pr.y2, a->rec_xc + (size_t)j * 4 * a->xcap, a->xcap);
+                        timing_end(s);
+                        VGA_CHECK_LAUNCH();
+                        w = 1 - w;
+                    }
+                    return VGA_OK;
+                };
+                VGA_TRY(graphs.run(0, len, issue));
+                s->launches += (len - 1) * (m > 0 ? 2 : 1);
             }
             for (int64_t j = 1; j < len && !sparse; ++j) {
                 rec.x = a->rec_x + (size_t)j * 5 * npad;
@@ -1038,27 +1097,53 @@ static vga_status adjoint_backward_impl(vga_sim *s, const double *d_lamN, double
                 wb = 1 - wb;
             }
         }
-        // reverse
-        for (int64_t j = len - 1; j >= 0; --j) {
-            const bool sp = sparse && j > 0;  // X^0 of a segment is its checkpoint (every node)
-            const float *xk = (j == 0) ? cks.h : sp ? a->rec_xc + (size_t)j * 4 * a->xcap : a->rec_x + (size_t)j * 5 * npad;
-            const float *y2k = a->rec_y2 + (size_t)j * npad;
+        // reverse: steps len-1 .. 1 (on the table: one graph per sweep, segment length and parity of
+        // the adjoint buffers), then step 0, whose X^0 is the segment's checkpoint
+        if (table) {
+            const int lb0 = lb;
+            auto issue = [&](cudaStream_t cs) -> vga_status {
+                int l = lb0;
+                for (int64_t j = len - 1; j >= 1; --j) {
+                    const float *xk = sparse ? a->rec_xc + (size_t)j * 4 * a->xcap : a->rec_x + (size_t)j * 5 * npad;
+                    const float *y2k = a->rec_y2 + (size_t)j * npad;
+                    const StateIO io = lam_io(a->lam, l, npad);
+                    timing_begin(s, VGA_KERNEL_ADJOINT);
+                    if (sparse)
+                        launch_reverse<WM, PREC, 1>(G, cs, tb.tz != nullptr, tacc != nullptr, s->n, tb, bt, s->sp, io,
+                                                    npad, xk, y2k, ss, a->xcap, tacc, a->gpart, a->gtheta);
+                    else
+                        launch_reverse<WM, PREC, 0>(G, cs, tb.tz != nullptr, tacc != nullptr, s->n, tb, bt, s->sp, io,
+                                                    npad, xk, y2k, SparseState{}, 1, tacc, a->gpart, a->gtheta);
+                    timing_end(s);
+                    VGA_CHECK_LAUNCH();
+                    l = 1 - l;
+                }
+                return VGA_OK;
+            };
+            VGA_TRY(graphs.run(1, 2 * len + lb0, issue));
+            s->launches += len - 1;
+            lb = (int)(lb0 ^ ((len - 1) & 1));
             const StateIO io = lam_io(a->lam, lb, npad);
             timing_begin(s, VGA_KERNEL_ADJOINT);
-            // four nodes per thread
-            if (table && sp)
-                launch_reverse<WM, PREC, 1>(G, st, tb.tz != nullptr, tacc != nullptr, s->n, tb, bt, s->sp, io, npad, xk,
-                                            y2k, ss, a->xcap, tacc, a->gpart, a->gtheta);
-            else if (table)
-                launch_reverse<WM, PREC, 0>(G, st, tb.tz != nullptr, tacc != nullptr, s->n, tb, bt, s->sp, io, npad, xk,
-                                            y2k, SparseState{}, 1, tacc, a->gpart, a->gtheta);
-            else
-                k_adjoint_step<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw, io,
-                                                                   npad, xk, y2k, a->gpart, a->gtheta);
+            launch_reverse<WM, PREC, 0>(G, st, tb.tz != nullptr, tacc != nullptr, s->n, tb, bt, s->sp, io, npad, cks.h,
+                                        a->rec_y2, SparseState{}, 1, tacc, a->gpart, a->gtheta);
             timing_end(s);
             VGA_CHECK_LAUNCH();
             ++s->launches;
             lb = 1 - lb;
+        } else {
+            for (int64_t j = len - 1; j >= 0; --j) {
+                const float *xk = (j == 0) ? cks.h : a->rec_x + (size_t)j * 5 * npad;
+                const float *y2k = a->rec_y2 + (size_t)j * npad;
+                const StateIO io = lam_io(a->lam, lb, npad);
+                timing_begin(s, VGA_KERNEL_ADJOINT);
+                k_adjoint_step<WM, PREC><<<G, kThreads, smem, st>>>(t, s->chunks.row, s->chunks.cap, s->sp, s->bw, io,
+                                                                   npad, xk, y2k, a->gpart, a->gtheta);
+                timing_end(s);
+                VGA_CHECK_LAUNCH();
+                ++s->launches;
+                lb = 1 - lb;
+            }
         }
     }
     if (nseg > 1) a->last_recorded = false;  // the records now hold the first segment
