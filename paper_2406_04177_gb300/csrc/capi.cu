@@ -774,6 +774,7 @@ vga_status vga_sim_free(vga_sim *s) {
     dfree(s->d_totals);
     dfree(s->d_err);
     dfree(s->nbr_table);
+    step_graphs_free(s);
     dfree(s->nbr_tz);
     activity_free(&s->act);
     dfree(s->bnode);

@@ -950,6 +950,104 @@ vga_status sim_build_active(vga_sim *s) {
     return VGA_OK;
 }
 
+static vga_status step_body(vga_sim *s, int64_t n_steps, bool sparse);
+
+// ---- CUDA graphs of whole step calls on small graphs ----------------------------------------------
+// Below kStepGraphNodes a pass takes a few microseconds on the GPU and the call is bound by the host's
+// launch rate.  A call whose shape was seen before (step count, state-buffer parity, parameters and
+// conductances, activity mask, variant) is captured as a graph (on a private stream: the simulation's
+// may be the legacy default stream) and later replayed; a replay reapplies the call's host-side
+// changes (buffer parity, step count, launch count).  Timing, sub-cycling, the wavefront and blocked
+// variants and a failed capture run the launches directly.
+constexpr int64_t kStepGraphNodes = (int64_t)1 << 21;
+
+static bool step_graph_eligible(const vga_sim *s, int64_t n_steps) {
+    return s->n < kStepGraphNodes && n_steps > 1 && !s->timing && !s->subcycled() && s->step_graphs_ok &&
+           s->kernel_variant != 3 && s->kernel_variant != 6;
+}
+
+static uint32_t cur_mask(const vga_sim *s) {
+    uint32_t m = 0;
+    for (int c = 0; c < 5; ++c) m |= (uint32_t)(s->cur[c] & 1) << c;
+    return m;
+}
+
+void step_graphs_free(vga_sim *s) {
+    for (auto &g : s->step_graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = StepGraph{};
+    }
+    if (s->step_cap) cudaStreamDestroy(s->step_cap);
+    s->step_cap = nullptr;
+}
+
+static vga_status step_graphed(vga_sim *s, int64_t n_steps, bool sparse) {
+    StepGraph key;
+    key.n_steps = n_steps;
+    key.cur_in = cur_mask(s);
+    key.param_gen = s->param_gen;
+    key.builds = sparse ? s->act.builds : -1;
+    key.variant = s->kernel_variant;
+    key.sparse = sparse;
+    StepGraph *hit = nullptr, *lru = &s->step_graphs[0];
+    for (auto &g : s->step_graphs) {
+        if (g.n_steps == key.n_steps && g.cur_in == key.cur_in && g.param_gen == key.param_gen &&
+            g.builds == key.builds && g.variant == key.variant && g.sparse == key.sparse) {
+            hit = &g;
+            break;
+        }
+        if (g.use < lru->use) lru = &g;
+    }
+    ++s->step_graph_clock;
+    if (!hit) {  // first time: remember the shape, run directly
+        if (lru->exec) cudaGraphExecDestroy(lru->exec);
+        *lru = key;
+        lru->use = s->step_graph_clock;
+        return step_body(s, n_steps, sparse);
+    }
+    hit->use = s->step_graph_clock;
+    if (!hit->exec) {  // seen before: capture this call and keep the graph
+        if (!s->step_cap && cudaStreamCreateWithFlags(&s->step_cap, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            s->step_cap = nullptr;
+            s->step_graphs_ok = false;
+            return step_body(s, n_steps, sparse);
+        }
+        int cur0[5];
+        for (int c = 0; c < 5; ++c) cur0[c] = s->cur[c];
+        const int64_t done0 = s->steps_done, launches0 = s->launches;
+        cudaStream_t real = s->stream;
+        VGA_CUDA(cudaStreamBeginCapture(s->step_cap, cudaStreamCaptureModeThreadLocal));
+        s->stream = s->step_cap;
+        const vga_status r = step_body(s, n_steps, sparse);
+        s->stream = real;
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(s->step_cap, &graph);
+        cudaError_t ei = cudaErrorUnknown;
+        if (r == VGA_OK && ec == cudaSuccess) ei = cudaGraphInstantiate(&hit->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (r != VGA_OK || ec != cudaSuccess || ei != cudaSuccess) {  // nothing ran: undo the host changes
+            cudaGetLastError();
+            hit->exec = nullptr;
+            for (int c = 0; c < 5; ++c) s->cur[c] = cur0[c];
+            s->steps_done = done0;
+            s->launches = launches0;
+            if (r != VGA_OK) return r;
+            s->step_graphs_ok = false;
+            return step_body(s, n_steps, sparse);
+        }
+        hit->cur_xor = cur_mask(s) ^ key.cur_in;
+        hit->launches = s->launches - launches0;
+        VGA_CUDA(cudaGraphLaunch(hit->exec, s->stream));
+        return VGA_OK;
+    }
+    VGA_CUDA(cudaGraphLaunch(hit->exec, s->stream));
+    for (int c = 0; c < 5; ++c) s->cur[c] ^= (int)((hit->cur_xor >> c) & 1u);
+    s->steps_done += n_steps;
+    s->launches += hit->launches;
+    return VGA_OK;
+}
+
 vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
     if (n_steps <= 0 || s->n == 0) {
         s->steps_done += std::max<int64_t>(n_steps, 0);
@@ -965,6 +1063,12 @@ vga_status sim_step_explicit(vga_sim *s, int64_t n_steps) {
         sparse = ok;
     }
     if (sparse && !s->act.valid) VGA_TRY(sim_build_active(s));
+    if (step_graph_eligible(s, n_steps)) return step_graphed(s, n_steps, sparse);
+    return step_body(s, n_steps, sparse);
+}
+
+// The passes of one explicit step call (the host logic and the launches; no host synchronisation).
+static vga_status step_body(vga_sim *s, int64_t n_steps, bool sparse) {
     const bool sub = s->subcycled();
     const int64_t k0 = s->steps_done;
     // ntrans is reset on every exit so that no other path sees a sub-cycled count

@@ -205,6 +205,16 @@ struct vga_graph {
     vga::Topo topo() const;
 };
 
+// A captured explicit step call and its shape (sim_step_explicit on small graphs).
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t n_steps = -1, param_gen = -1, builds = -1, launches = 0;
+    uint32_t cur_in = 0, cur_xor = 0;
+    int variant = -1;
+    bool sparse = false;
+    uint64_t use = 0;
+};
+
 struct vga_sim {
     const vga_graph *g = nullptr;
     vga_params params{};
@@ -215,6 +225,10 @@ struct vga_sim {
     float *buf[2] = {nullptr, nullptr};     // two state buffers of 5*npad FP32 values
     vga::res_t *lbuf[2] = {nullptr, nullptr};  // their residuals (compensated precision)
     int cur[5] = {0, 0, 0, 0, 0};           // which buffer holds compartment c
+    StepGraph step_graphs[4];               // graphs of whole explicit step calls (small graphs)
+    uint64_t step_graph_clock = 0;
+    bool step_graphs_ok = true;             // cleared when a capture fails
+    cudaStream_t step_cap = nullptr;        // private capture stream
     vga::Chunks chunks;
     // conductances
     int wmode = vga::W_UNIT;
@@ -306,6 +320,7 @@ void timing_end(vga_sim *s);
 void timing_end_weighted(vga_sim *s, int64_t passes);  // the launch covered `passes` time steps
 // step.cu
 vga_status sim_prepare_params(vga_sim *s, const vga_params *p);
+void step_graphs_free(vga_sim *s);
 vga_status sim_step_explicit(vga_sim *s, int64_t n_steps);
 vga_status sim_diffuse_pass(vga_sim *s);  // last pass of a step call (DOM diffusion only)
 vga_status sim_totals(vga_sim *s, double *h_out);

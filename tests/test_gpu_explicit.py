@@ -532,3 +532,34 @@ def test_rows_of_very_different_length(vga, oracle_lib):
     assert out[0][0] == out[1][0]
     ref = oracle_lib.explicit_run(og.nbr, p, X0, 40)
     _assert_close(out[0][1], ref)
+
+
+@pytest.mark.parametrize("variant", [5, 2, 0])
+def test_step_graphs_replay_bit_identical(vga, oracle_lib, variant):
+    """On a small graph, a step call of a shape seen before is captured as a CUDA graph and later ones
+    replay it (with the state-buffer parity and step count carried on the host); interleaved shapes,
+    a parameter change and a new state between calls all give the bits of the same calls run
+    launch by launch (kernel timing on turns the graphs off)."""
+    img, og, g, X0 = _setup(vga, oracle_lib, (40, 36, 44), 0.2, 9)
+    p = synth.paper_params()
+    p2 = dict(p, rho=p["rho"] * 1.3)
+    out = []
+    for timing in (True, False):
+        sim = vga.Sim(g, p)
+        sim.set_kernel(variant, 1024)
+        sim.enable_timing(timing)
+        sim.set_masses(X0)
+        for k in (7, 7, 7, 6, 7, 6, 7, 7):
+            sim.step(k)
+        mid = sim.save_state()
+        sim.set_params(p2)
+        for k in (7, 7, 7):
+            sim.step(k)
+        sim.set_masses(X0)
+        for k in (9, 9, 9, 9):
+            sim.step(k)
+        out.append((mid, sim.save_state(), sim.stats()["steps_done"]))
+        sim.close()
+    assert out[0][0] == out[1][0]
+    assert out[0][1] == out[1][1]
+    assert out[0][2] == out[1][2]
