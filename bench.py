@@ -411,7 +411,7 @@ def bench_ours(a):
     xh = torch.from_numpy(X0.astype(np.float32)).pin_memory()
     outh = torch.empty((5, n), dtype=torch.float32).pin_memory()
     xh_np, outh_np = xh.numpy(), outh.numpy()
-    e2e_iters = max(2, min(a.steps, 5))
+    e2e_iters = max(2, min(a.steps, 10))
     sim.set_state_f32(xh_np)
     sim.step(S)
     sim.get_state_f32(outh_np)
